@@ -1,0 +1,118 @@
+"""Seeded synthetic SBL problems shaped like the paper's workloads.
+
+This module is shared by the CUDA path's tests/bench and by the oracle's
+tests: it only draws inputs (dictionary, sparse ground truth, noisy
+observations) and holds none of CoFEM's arithmetic.  Every generator is a
+pure function of its seed (numpy PCG64 via ``default_rng``).
+
+Workloads (Sec. 4 uses simulated compressed-sensing data only):
+
+* ``dense_problem``   Phi iid N(0, 1/N) (N x D), d nonzeros at uniform random
+                      positions with N(0,1) (or +-1, or Laplace) amplitudes,
+                      y = Phi z + N(0, sigma^2) noise (Eq. model).
+* ``conv_problem``    C filters of T taps, iid N(0,1) then unit l2 norm;
+                      circular convolutional dictionary over a length-L signal;
+                      z has a fraction of nonzeros with Laplace(0,1) amplitudes.
+* ``batched_sizes``   N_i uniform on an integer range, D_i = ratio * N_i, one
+                      seed per problem derived from a master seed.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class DenseProblem:
+    Phi: np.ndarray        # N x D, float32 (exactly representable values)
+    z: np.ndarray          # D, float64 ground truth
+    y: np.ndarray          # N, float64
+    support: np.ndarray    # indices of nonzeros
+    beta: float
+
+
+def _amplitudes(rng, n, kind):
+    if kind == "normal":
+        return rng.standard_normal(n)
+    if kind == "spike":
+        return rng.choice(np.array([-1.0, 1.0]), size=n)
+    if kind == "laplace":
+        return rng.laplace(0.0, 1.0, size=n)
+    raise ValueError(kind)
+
+
+def dense_problem(N, D, n_nonzero, sigma, seed, amp="normal", phi_scale=None):
+    """Dense compressed-sensing problem.  phi_scale defaults to 1/sqrt(N)
+    (entries N(0, 1/N)); pass 1.0 for the paper's Sec. 4.1 N(0,1) entries."""
+    rng = np.random.default_rng(seed)
+    scale = (1.0 / np.sqrt(N)) if phi_scale is None else phi_scale
+    Phi = (rng.standard_normal((N, D), dtype=np.float32) * np.float32(scale))
+    support = np.sort(rng.choice(D, size=n_nonzero, replace=False))
+    z = np.zeros(D)
+    z[support] = _amplitudes(rng, n_nonzero, amp)
+    noise = sigma * rng.standard_normal(N)
+    y = Phi.astype(np.float64)[:, support] @ z[support] + noise
+    return DenseProblem(Phi, z, y, support, 1.0 / sigma ** 2)
+
+
+@dataclass
+class ConvProblem:
+    h: np.ndarray          # C x T filters, float32, unit l2 norm per filter
+    z: np.ndarray          # C x L ground truth codes (float64)
+    y: np.ndarray          # L observations (float64)
+    beta: float
+
+
+def conv_problem(L, C, T, density, sigma, seed):
+    """Circular convolutional dictionary problem; y = sum_c h_c (*) z_c + noise,
+    built by scattering each nonzero's shifted filter (the generative model,
+    Eq. model)."""
+    rng = np.random.default_rng(seed)
+    h = rng.standard_normal((C, T))
+    h /= np.linalg.norm(h, axis=1, keepdims=True)
+    h = h.astype(np.float32)
+    D = C * L
+    nnz = max(1, int(round(density * D)))
+    idx = np.sort(rng.choice(D, size=nnz, replace=False))
+    amps = rng.laplace(0.0, 1.0, size=nnz)
+    z = np.zeros((C, L))
+    z.reshape(-1)[idx] = amps
+    y = sigma * rng.standard_normal(L)
+    c_of, m_of = idx // L, idx % L
+    h64 = h.astype(np.float64)
+    for j in range(T):
+        np.add.at(y, (m_of + j) % L, amps * h64[c_of, j])
+    return ConvProblem(h, z, y, 1.0 / sigma ** 2 if sigma > 0 else float("inf"))
+
+
+def batched_sizes(n_problems, n_min, n_max, ratio, seed):
+    """(N_i, D_i, seed_i) for each problem; N_i uniform on [n_min, n_max]."""
+    rng = np.random.default_rng(seed)
+    Ns = rng.integers(n_min, n_max + 1, size=n_problems)
+    seeds = rng.integers(0, 2 ** 62, size=n_problems)
+    return [(int(n), int(ratio * n), int(s)) for n, s in zip(Ns, seeds)]
+
+
+def orthonormal_columns(N, D, seed):
+    """N x D matrix with orthonormal columns (D <= N), Q factor of a Gaussian
+    matrix (Householder QR via numpy)."""
+    rng = np.random.default_rng(seed)
+    Q, Rm = np.linalg.qr(rng.standard_normal((N, D)))
+    return Q * np.sign(np.diag(Rm))[None, :]
+
+
+# Named workloads (sizes of the paper-shaped configurations).
+CONFIGS = {
+    # FP64 plain CoFEM: dense N=256, D=1024, 51 nonzeros, sigma 0.01, K=20,
+    # 50 EM iterations, CG tol 1e-6, U=400.
+    "dense-fp64-n256-d1024": dict(N=256, D=1024, n_nonzero=51, sigma=0.01, K=20,
+                                  em_iters=50, cg_tol=1e-6, cg_max_iters=400),
+    # Large dense: N=4096, D=32768, 2% nonzeros, beta 1e4, K=32, 100 EM
+    # iterations, CG tol 1e-5, residual replacement every 50 iterations.
+    "dense-n4096-d32768": dict(N=4096, D=32768, n_nonzero=655, sigma=0.01, K=32,
+                               em_iters=100, cg_tol=1e-5, cg_max_iters=400,
+                               resid_replace_every=50),
+    # Convolutional: L = 2^20, 8 filters x 64 taps, 0.1% nonzeros Laplace,
+    # sigma 0.05, K=16, 30 EM iterations.
+    "conv-l1m-c8-t64": dict(L=1 << 20, C=8, T=64, density=1e-3, sigma=0.05, K=16,
+                            em_iters=30, cg_tol=1e-5, cg_max_iters=400),
+}

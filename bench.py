@@ -1,0 +1,330 @@
+"""CoFEM benchmark: EM iterations per second on the dense N=4096, D=32768
+workload (BF16 dictionary, K=32 probes, CG tol 1e-5, residual replacement
+every 50 CG iterations), one step = one EM iteration of Algorithm 1 (probe
+draw, multi-RHS CG solve to tolerance, diagonal estimate, M-step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--phi bf16|f32]
+
+Prints one JSON line (rank 0).  Under torchrun each rank fits its own
+replica of the workload (the method does not shard: replicas only, no
+collective on the data path); value = EM iterations of all ranks / max time.
+The reference arm times the FP64 CPU oracle on a bounded sample.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2202_12808_gb300 import datagen  # noqa: E402
+
+WORKLOAD = "dense-n4096-d32768"
+CFG = datagen.CONFIGS[WORKLOAD]
+METRIC = "EM iters/s (dense N=4096 D=32768 K=32, CG tol 1e-5)"
+UNIT = "EM iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--phi", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def problem(seed):
+    return datagen.dense_problem(CFG["N"], CFG["D"], CFG["n_nonzero"], CFG["sigma"], seed)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_em_rate(prob, phi_dtype, cg_iters_per_em, budget_s=15.0):
+    """Oracle E-step timed on a bounded sample: one E-step of the workload
+    truncated after as many CG iterations as fit in ~budget_s, scaled by the
+    CG iterations per EM iteration the GPU run needed.  Returns (EM iters/s,
+    seconds per CG iteration, CG iterations sampled, threads)."""
+    from oracle import probe_hash as ph
+    from oracle import sbl
+    import torch
+    Phi = prob.Phi
+    if phi_dtype == "bf16":
+        Phi = torch.from_numpy(Phi).to(torch.bfloat16).double().numpy()
+    else:
+        Phi = Phi.astype(np.float64)
+    y = prob.y.astype(np.float32).astype(np.float64)
+    beta = prob.beta
+    D = Phi.shape[1]
+    phi, phit, _ = sbl.dense_dictionary(Phi)
+    t0 = time.perf_counter()
+    b = beta * phit(y)
+    P = ph.probe_matrix(0, 1, CFG["K"], D)
+    B = np.concatenate([b[:, None], P], axis=1)
+    alpha = np.ones(D)
+    A = lambda X: sbl.apply_A(phi, phit, beta, alpha, X)
+    setup = time.perf_counter() - t0
+    # probe one iteration, then size the sample
+    t1 = time.perf_counter()
+    sbl.cg_solve(A, B, 0.0, 1, fixed_iters=1)
+    one = time.perf_counter() - t1
+    n = max(2, min(200, int(budget_s / max(one, 1e-6))))
+    t2 = time.perf_counter()
+    sbl.cg_solve(A, B, 0.0, n, fixed_iters=n)
+    per_cg = (time.perf_counter() - t2) / n
+    t3 = time.perf_counter()
+    s = sbl.diag_estimate(P, B[:, 1:])
+    sbl.m_step(b, s)
+    tail = time.perf_counter() - t3
+    per_em = per_cg * cg_iters_per_em + tail + setup / max(1, CFG["em_iters"])
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return 1.0 / per_em, per_cg, n, cores
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    prob = problem(args.seed)
+    # CG iterations per EM iteration are not known without running the method;
+    # the oracle's own first E-step count (capped) is used for the scale.
+    rate, per_cg, n, cores = oracle_em_rate(prob, args.phi, 60.0,
+                                            budget_s=max(5.0, 20.0 / max(1, args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "phi": args.phi, "K": CFG["K"]},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d FP64 CG iterations of one E-step (numpy/BLAS), "
+                                       "scaled to 60 CG iterations per EM iteration" % n},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ GPU arm
+
+def launches_per_em(cg_iters, replace_every, kernels_per_apply):
+    """Our kernel launches in one EM iteration: init, per CG iteration
+    (operator apply + step + update + direction), per replacement (operator
+    apply + true residual), diag/M-step."""
+    n_rep = cg_iters // replace_every if replace_every else 0
+    return 1 + cg_iters * (kernels_per_apply + 3) + n_rep * (kernels_per_apply + 1) + 1
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    prob = problem(args.seed + rank)
+    dev = torch.device("cuda", local)
+    phi_t = torch.from_numpy(prob.Phi).to(dev)
+    if args.phi == "bf16":
+        phi_t = phi_t.to(torch.bfloat16)
+    op = api.DenseOperator(phi_t)
+    y = torch.from_numpy(prob.y.astype(np.float32)).to(dev)
+    kw = dict(vec_dtype=B.COFEM_F32, K=CFG["K"], cg_tol=CFG["cg_tol"],
+              cg_max_iters=CFG["cg_max_iters"], resid_replace_every=CFG["resid_replace_every"],
+              seed=args.seed)
+    # warm-up: the first W EM iterations of the fit
+    pw = api.params(em_iters=args.warmup, **kw)
+    wsp = api.workspace(op, api.params(em_iters=max(args.warmup, args.steps), **kw), dev)
+    rw = api.fit(op, y, prob.beta, pw, ws=wsp)
+    alpha0 = rw.alpha.clone()
+    torch.cuda.synchronize()
+
+    # timed: EM iterations W+1 .. W+K, resumed from the warm-up alpha
+    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+    alpha = alpha0.clone()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        res = api.fit(op, y, prob.beta, pt, ws=wsp, alpha=alpha)
+        e1.record(st)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1e3)
+    cg = res.stats["cg_iters"]
+
+    # dominant kernel: the operator application over K+1 columns, timed alone
+    ncols = CFG["K"] + 1
+    D, N = CFG["D"], CFG["N"]
+    ld = (D + 63) // 64 * 64
+    Xb = torch.randn((ncols, ld), device=dev)
+    Yb = torch.empty_like(Xb)
+    nbytes = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, ncols)
+    wsa = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        B.cofem_op_apply(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols, alpha.data_ptr(),
+                         prob.beta, Yb.data_ptr(), wsa.data_ptr(), nbytes, st.cuda_stream)
+    reps = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(st)
+    for _ in range(reps):
+        B.cofem_op_apply(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols, alpha.data_ptr(),
+                         prob.beta, Yb.data_ptr(), wsa.data_ptr(), nbytes, st.cuda_stream)
+    a1.record(st)
+    torch.cuda.synchronize()
+    apply_s = a0.elapsed_time(a1) / 1e3 / reps
+    phi_bytes = N * D * (2 if args.phi == "bf16" else 4)
+    alg_bytes = 2 * phi_bytes + 3 * D * ncols * 4 + 8 * D      # Phi twice; X, Y, alpha
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / apply_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "dense operator apply (Phi^T(Phi X) + alpha.X, %d cols)" % ncols,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    kpa = 4
+    launches = 3 + sum(launches_per_em(c, CFG["resid_replace_every"], kpa) for c in cg)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors, %s Phi" % args.phi,
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "D": D, "K": CFG["K"], "phi": args.phi,
+                       "cg_tol": CFG["cg_tol"], "resid_replace_every": CFG["resid_replace_every"],
+                       "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
+                       "l2": "inputs larger than L2 (Phi %d MB)" % (phi_bytes >> 20),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "cg_iters_per_em": cg, "clocks": clk.summary(), "roofline": roofline,
+            "gpu_launches": launches}
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API with host buffers: H2D of Phi and y
+        # (pinned), the fit, D2H of mu, s, alpha
+        h_phi = phi_t.cpu().pin_memory()
+        h_y = y.cpu().pin_memory()
+        h_alpha = alpha0.cpu().pin_memory()
+        outs = [torch.empty(D, dtype=torch.float64).pin_memory() for _ in range(3)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_phi = h_phi.to(dev, non_blocking=True)
+        d_y = h_y.to(dev, non_blocking=True)
+        d_alpha = h_alpha.to(dev, non_blocking=True)
+        op2 = api.DenseOperator(d_phi)
+        r2 = api.fit(op2, d_y, prob.beta, pt, ws=wsp, alpha=d_alpha)
+        for o, src in zip(outs, (r2.mu, r2.s, r2.alpha)):
+            o.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        h2d = h_phi.numel() * h_phi.element_size() + h_y.numel() * 4 + D * 8
+        line["e2e"] = {"value": args.steps / el, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d // args.steps,
+                       "d2h_bytes_per_step": 3 * D * 8 // args.steps}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, per_cg, n, cores = oracle_em_rate(prob, args.phi, float(np.mean(cg)))
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d FP64 CG iterations of one E-step on the same "
+                                          "workload (%.3f s each), scaled by the GPU run's "
+                                          "%.1f CG iterations per EM iteration"
+                                          % (n, per_cg, float(np.mean(cg)))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

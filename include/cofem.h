@@ -1,0 +1,213 @@
+/*
+ * cofem.h -- C ABI of libcofem, a GB300 (sm_103a) implementation of
+ * covariance-free EM (CoFEM) for sparse Bayesian learning.
+ *
+ * Method (Lin, Song, Bilgic, Ba, "High-Dimensional Sparse Bayesian Learning
+ * without Covariance Matrices"):
+ *   model      z ~ N(0, diag(alpha)^-1), y ~ N(Phi z, beta^-1 I)      Sec. 2.1
+ *   E-step     solve A X = B with A = beta Phi^T Phi + diag(alpha) and
+ *              B = [beta Phi^T y | p_1 .. p_K] (K Rademacher probes)  Eq. (mat-eq)
+ *              by conjugate gradients, one recurrence per column     Sec. 3.2
+ *   estimate   s = (1/K) sum_k p_k . x_k                              Eq. (diag-estimate)
+ *   M-step     alpha = 1 / (mu . mu + s)                              Eq. (mstep), Alg. 1
+ *
+ * Conventions for every entry point:
+ *  - All array arguments named *_dev are DEVICE pointers owned by the caller;
+ *    the library never frees them and keeps none of them past the call,
+ *    except that an operator handle keeps the dictionary pointers it was
+ *    created with (the caller keeps that memory alive while the handle lives).
+ *  - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t
+ *    passed as void*; NULL = legacy default stream).  Entry points that say
+ *    "synchronous" wait for the stream before returning.
+ *  - Multi-column vectors ("blocks") are column-major: column j of a block
+ *    with leading dimension ld starts at element j*ld.  ld >= the column
+ *    length and ld must be a multiple of 64.  Column 0 is the mean system
+ *    (right-hand side beta Phi^T y, solution mu); columns 1..K are probes.
+ *    The paper lists mu last; the order changes no result.
+ *  - Vector precision is COFEM_F64 (double) or COFEM_F32 (float).  CG scalars
+ *    (dot products, step sizes) are always double.  mu, s and alpha outputs
+ *    are always double.
+ *  - Errors are returned as cofem_status; nothing aborts.  Device-side faults
+ *    of the method (non-finite values, CG breakdown) are recorded in an error
+ *    word in the workspace and returned by the synchronous calls.  When a call
+ *    fails its outputs are unspecified.
+ */
+#ifndef COFEM_H
+#define COFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  COFEM_OK = 0,
+  COFEM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, misaligned ld ... */
+  COFEM_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  COFEM_ERR_NONFINITE = 3,     /* NaN/Inf met in mu, s or a CG scalar */
+  COFEM_ERR_BREAKDOWN = 4,     /* CG curvature p^T A p <= 0 */
+  COFEM_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+  COFEM_ERR_UNSUPPORTED = 6,   /* combination not built (e.g. dtype/op) */
+  COFEM_ERR_WORKSPACE = 7      /* workspace smaller than cofem_workspace_bytes */
+} cofem_status;
+
+typedef enum {
+  COFEM_F64 = 0,
+  COFEM_F32 = 1,
+  COFEM_BF16 = 2,
+  COFEM_FP8_E4M3 = 3
+} cofem_dtype;
+
+/* Human-readable name of a status code (static string). */
+const char* cofem_status_string(cofem_status s);
+
+/* Text of the last CUDA failure seen by this thread (call, error, source
+ * line); empty if none.  Valid until the next failing call on the thread. */
+const char* cofem_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Dictionary operators (Sec. 3.2: CG only needs Phi and Phi^T applied to
+ * vectors; tau_D is the cost of one application).
+ * ------------------------------------------------------------------------ */
+typedef struct cofem_op cofem_op;
+
+/* Dense Phi, N x D, row-major with leading dimension ld (elements, >= D,
+ * multiple of 64 for BF16/FP8, of 4 for F32/F64).  phi_dev is 256-byte
+ * aligned.  dtype F64 (only with F64 vectors), F32, BF16 or FP8_E4M3 (F32
+ * vectors).  For FP8 the stored value is phi / scale of its 128 x 128 tile;
+ * tile_scales_dev holds ceil(N/128) x ceil(D/128) float scales (row-major);
+ * NULL for the other dtypes.  Writes a new handle to *out. */
+cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype,
+                            const void* phi_dev, int64_t ld,
+                            const float* tile_scales_dev, cofem_op** out);
+
+/* Circular convolutional Phi (Sec. 3.2 structured tau_D): signal length L,
+ * C filters of T taps (filters_dev: C x T floats, row-major).  N = L,
+ * D = C*L, coordinate d = c*L + m.
+ *   (Phi z)[n]     = sum_c sum_j h[c][j] z_c[(n - j) mod L]
+ *   (Phi^T w)_c[m] = sum_j h[c][j] w[(m + j) mod L]
+ * L must be a multiple of 64; T <= 128.  F32 vectors only. */
+cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T,
+                             const float* filters_dev, cofem_op** out);
+
+/* Releases a handle (NULL is ignored). */
+void cofem_op_destroy(cofem_op* op);
+
+/* N and D of an operator. */
+cofem_status cofem_op_shape(const cofem_op* op, int64_t* N, int64_t* D);
+
+/* ------------------------------------------------------------------------
+ * Fit parameters (Algorithm 1 inputs y, Phi, beta, T_em, K; the solver
+ * limits U and eps of Sec. 3.2).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t K;                   /* probes per E-step, 1..64 */
+  int32_t em_iters;            /* T_em */
+  int32_t cg_max_iters;        /* U */
+  int32_t fixed_cg_iters;      /* >0: run exactly this many CG iterations,
+                                  ignoring cg_tol (parity mode); 0 = off */
+  int32_t resid_replace_every; /* R > 0: every R CG iterations recompute the
+                                  true residual r = B - A x; 0 = never */
+  int32_t vec_dtype;           /* COFEM_F64 or COFEM_F32 */
+  double cg_tol;               /* eps: stop when ||R||_F / ||B||_F < eps */
+  double alpha_init;           /* initial alpha (Alg. 1: 1) when
+                                  t_offset == 0; ignored otherwise */
+  double den_floor;            /* alpha = 1 / max(mu^2 + s, den_floor) */
+  double support_threshold;    /* stats: support = #{alpha_d < threshold} */
+  uint64_t seed;               /* probe seed */
+  int64_t t_offset;            /* EM iterations already done: t runs
+                                  t_offset+1 .. t_offset+em_iters; when > 0
+                                  alpha_dev is read as the starting alpha */
+} cofem_params;
+
+/* Fills *p with: K 20, em_iters 50, cg_max_iters 400, fixed 0, R 0, F32,
+ * cg_tol 1e-6, alpha_init 1, den_floor 1e-12, support_threshold 1e6,
+ * seed 0, t_offset 0. */
+void cofem_params_default(cofem_params* p);
+
+/* Per-EM-iteration statistics, host arrays of length em_iters (any may be
+ * NULL): CG iterations, final recursive relative residual ||R||_F/||B||_F,
+ * number of clamped denominators, support size. */
+typedef struct {
+  int32_t* cg_iters;
+  double* relres;
+  int32_t* clamps;
+  int32_t* support;
+} cofem_stats;
+
+/* Bytes of device workspace cofem_fit needs for this operator and params
+ * (256-byte aligned base required). */
+cofem_status cofem_workspace_bytes(const cofem_op* op, const cofem_params* p,
+                                   size_t* bytes);
+
+/* Algorithm 1 (CovarianceFreeEM): b = beta Phi^T y once, then em_iters times
+ * { draw probes, solve A X = B by column-wise CG, s = (1/K) sum p_k . x_k,
+ *   alpha = 1 / max(mu^2 + s, den_floor) }.
+ * y_dev: N values of vec_dtype.  mu_dev, s_dev, alpha_dev: D doubles each
+ * (alpha_dev is also the input alpha when t_offset > 0).  stats: optional.
+ * Synchronous: returns after the work on `stream` has finished, with the
+ * device error word checked. */
+cofem_status cofem_fit(const cofem_op* op, const void* y_dev, double beta,
+                       const cofem_params* p, void* workspace_dev,
+                       size_t workspace_bytes, double* mu_dev, double* s_dev,
+                       double* alpha_dev, cofem_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Individual hot-path steps (each is one of the kernels cofem_fit runs).
+ * ------------------------------------------------------------------------ */
+
+/* Probe block for EM iteration t (Sec. 3.1 Rademacher probes, Alg. 1
+ * "draw p_1..p_K"): out[k*ld + d] = p_{k+1, d} in {+1, -1}, d < D, k < K,
+ * from the counter-based hash
+ *   s1 = mix64(mix64(seed) ^ t);  h = mix64(s1 ^ ((d << 8) | (k / 64)));
+ *   p = (bit (k mod 64) of h) ? -1 : +1
+ * with mix64 the SplitMix64 output function.  K <= 16384.  dtype F64/F32.
+ * Asynchronous. */
+cofem_status cofem_probe_fill(uint64_t seed, int64_t t, int32_t K, int64_t D,
+                              cofem_dtype dtype, void* out_dev, int64_t ld,
+                              void* stream);
+
+/* Operator application Y = beta Phi^T (Phi X) + alpha . X over ncols
+ * columns (the product A X of Eq. (mat-eq)).  X, Y: blocks of vec dtype
+ * with leading dimension ld (>= D).  alpha_dev: D doubles.  workspace: at
+ * least cofem_apply_workspace_bytes(op, vec, ncols).  ncols <= 64.
+ * Asynchronous. */
+cofem_status cofem_apply_workspace_bytes(const cofem_op* op, cofem_dtype vec,
+                                         int32_t ncols, size_t* bytes);
+cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec,
+                            const void* x_dev, int64_t ld, int32_t ncols,
+                            const double* alpha_dev, double beta, void* y_dev,
+                            void* workspace_dev, size_t workspace_bytes,
+                            void* stream);
+
+/* The two halves: W = Phi Z (ncols columns of length N, leading dimension
+ * ldw) and Z = Phi^T W (length D, leading dimension ldz).  Used for
+ * b = beta Phi^T y.  Same workspace rule as cofem_op_apply. Asynchronous. */
+cofem_status cofem_op_forward(const cofem_op* op, cofem_dtype vec,
+                              const void* z_dev, int64_t ldz, int32_t ncols,
+                              void* w_dev, int64_t ldw, void* workspace_dev,
+                              size_t workspace_bytes, void* stream);
+cofem_status cofem_op_adjoint(const cofem_op* op, cofem_dtype vec,
+                              const void* w_dev, int64_t ldw, int32_t ncols,
+                              void* z_dev, int64_t ldz, void* workspace_dev,
+                              size_t workspace_bytes, void* stream);
+
+/* Diagonal estimate and M-step from a solved block X (K+1 columns, vec
+ * dtype, leading dimension ld) for EM iteration t (Eq. (diag-estimate),
+ * Eq. (mstep) with s):  mu_d = X[0][d];  s_d = (1/K) sum_k p_kd X[k][d]
+ * (probes as in cofem_probe_fill);  alpha_d = 1 / max(mu_d^2 + s_d,
+ * den_floor).  counts_dev (2 int32, optional): number of clamped
+ * denominators, number of alpha_d < support_threshold (accumulated: the
+ * caller zeroes them).  Asynchronous. */
+cofem_status cofem_diag_mstep(uint64_t seed, int64_t t, int32_t K, int64_t D,
+                              cofem_dtype vec, const void* x_dev, int64_t ld,
+                              double den_floor, double support_threshold,
+                              double* mu_dev, double* s_dev, double* alpha_dev,
+                              int32_t* counts_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COFEM_H */

@@ -1,0 +1,120 @@
+"""Torch-facing convenience layer over the C ABI (marshalling only).
+
+PyTorch provides device memory and streams; every step of the method runs in
+libcofem's CUDA kernels through ``binding``.  No CPU fallback exists: without
+a CUDA device or without the built library these functions raise.
+"""
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+_DT = {torch.float64: B.COFEM_F64, torch.float32: B.COFEM_F32, torch.bfloat16: B.COFEM_BF16}
+
+
+def _ld(n):
+    return (n + 63) // 64 * 64
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class DenseOperator:
+    """Dense Phi (N x D) held on the device; keeps the tensor alive."""
+
+    def __init__(self, Phi: torch.Tensor):
+        if not Phi.is_cuda:
+            raise ValueError("Phi must be a CUDA tensor")
+        if Phi.dtype not in _DT:
+            raise ValueError("Phi dtype must be float64, float32 or bfloat16")
+        N, D = Phi.shape
+        ld = _ld(D) if Phi.dtype == torch.bfloat16 else D
+        if Phi.stride() != (ld, 1):
+            buf = torch.zeros((N, ld), dtype=Phi.dtype, device=Phi.device)
+            buf[:, :D] = Phi
+            Phi = buf
+        self.phi = Phi
+        self.N, self.D = N, D
+        self.dtype = _DT[Phi.dtype]
+        self.handle = B.cofem_op_dense(N, D, self.dtype, Phi.data_ptr(), Phi.stride(0))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            B.cofem_op_destroy(h)
+            self.handle = None
+
+
+class ConvOperator:
+    """Circular convolutional Phi: C filters of T taps over length-L signals."""
+
+    def __init__(self, h: torch.Tensor, L: int):
+        if not h.is_cuda or h.dtype != torch.float32:
+            raise ValueError("filters must be a float32 CUDA tensor")
+        self.h = h.contiguous()
+        self.C, self.T = self.h.shape
+        self.L = L
+        self.N, self.D = L, self.C * L
+        self.dtype = B.COFEM_F32
+        self.handle = B.cofem_op_conv1d(L, self.C, self.T, self.h.data_ptr())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            B.cofem_op_destroy(h)
+            self.handle = None
+
+
+@dataclass
+class FitResult:
+    alpha: torch.Tensor
+    mu: torch.Tensor
+    s: torch.Tensor
+    stats: dict
+
+
+def params(**kw):
+    return B.cofem_params_default(**kw)
+
+
+def workspace(op, p, device=None):
+    n = B.cofem_workspace_bytes(op.handle, p)
+    dev = device if device is not None else torch.device("cuda")
+    return torch.empty(n, dtype=torch.uint8, device=dev)
+
+
+def fit(op, y, beta, p=None, ws=None, alpha=None, stream=None, **kw):
+    """Algorithm 1 on the GPU.  y: CUDA tensor of the vector dtype
+    (float64 for vec_dtype=F64, float32 otherwise).  Returns FitResult."""
+    if p is None:
+        p = params(**kw)
+    vec = torch.float64 if p.vec_dtype == B.COFEM_F64 else torch.float32
+    y = y.to(device=op.phi.device if hasattr(op, "phi") else op.h.device, dtype=vec).contiguous()
+    dev = y.device
+    if ws is None:
+        ws = workspace(op, p, dev)
+    mu = torch.empty(op.D, dtype=torch.float64, device=dev)
+    s = torch.empty(op.D, dtype=torch.float64, device=dev)
+    if alpha is None:
+        alpha = torch.empty(op.D, dtype=torch.float64, device=dev)
+    stats = B.cofem_fit(op.handle, y.data_ptr(), float(beta), p, ws.data_ptr(), ws.numel(),
+                        mu.data_ptr(), s.data_ptr(), alpha.data_ptr(), _stream_ptr(stream))
+    return FitResult(alpha, mu, s, stats)
+
+
+def apply(op, X, alpha, beta, vec_dtype=None, stream=None):
+    """Y = beta Phi^T Phi X + alpha . X for a D x ncols block X (CUDA)."""
+    vec = B.COFEM_F64 if X.dtype == torch.float64 else B.COFEM_F32
+    D, ncols = X.shape
+    ld = _ld(D)
+    Xb = torch.zeros((ncols, ld), dtype=X.dtype, device=X.device)
+    Xb[:, :D] = X.T
+    Yb = torch.empty_like(Xb)
+    n = B.cofem_apply_workspace_bytes(op.handle, vec, ncols)
+    ws = torch.empty(max(n, 256), dtype=torch.uint8, device=X.device)
+    B.cofem_op_apply(op.handle, vec, Xb.data_ptr(), ld, ncols, alpha.data_ptr(), float(beta),
+                     Yb.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    return Yb[:, :D].T

@@ -1,0 +1,199 @@
+"""ctypes binding of libcofem (include/cofem.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of the method: all work runs in the library's CUDA kernels.  The
+library is loaded from this package directory (built in-tree by
+``build.py``); if it is missing, ``lib()`` raises -- there is no fallback.
+
+Device buffers are passed as integers (``tensor.data_ptr()``); streams as
+integers (``torch.cuda.current_stream().cuda_stream``).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcofem.so")
+
+COFEM_F64, COFEM_F32, COFEM_BF16, COFEM_FP8_E4M3 = 0, 1, 2, 3
+
+STATUS = {0: "COFEM_OK", 1: "COFEM_ERR_INVALID_ARG", 2: "COFEM_ERR_CUDA",
+          3: "COFEM_ERR_NONFINITE", 4: "COFEM_ERR_BREAKDOWN", 5: "COFEM_ERR_TIMEOUT",
+          6: "COFEM_ERR_UNSUPPORTED", 7: "COFEM_ERR_WORKSPACE"}
+
+
+class CofemError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        msg = "%s failed: %s" % (where, STATUS.get(code, code))
+        if detail:
+            msg += " [%s]" % detail
+        super().__init__(msg)
+
+
+class cofem_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("em_iters", ctypes.c_int32),
+                ("cg_max_iters", ctypes.c_int32), ("fixed_cg_iters", ctypes.c_int32),
+                ("resid_replace_every", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
+                ("cg_tol", ctypes.c_double), ("alpha_init", ctypes.c_double),
+                ("den_floor", ctypes.c_double), ("support_threshold", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int64)]
+
+
+class cofem_stats(ctypes.Structure):
+    _fields_ = [("cg_iters", ctypes.POINTER(ctypes.c_int32)),
+                ("relres", ctypes.POINTER(ctypes.c_double)),
+                ("clamps", ctypes.POINTER(ctypes.c_int32)),
+                ("support", ctypes.POINTER(ctypes.c_int32))]
+
+
+_S = ctypes.c_int
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+_SIGS = {
+    "cofem_status_string": (ctypes.c_char_p, [_S]),
+    "cofem_last_error": (ctypes.c_char_p, []),
+    "cofem_op_dense": (_S, [_I64, _I64, _S, _P, _I64, _P, ctypes.POINTER(_P)]),
+    "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "cofem_op_destroy": (None, [_P]),
+    "cofem_op_shape": (_S, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "cofem_params_default": (None, [ctypes.POINTER(cofem_params)]),
+    "cofem_workspace_bytes": (_S, [_P, ctypes.POINTER(cofem_params), ctypes.POINTER(_SZ)]),
+    "cofem_fit": (_S, [_P, _P, _D, ctypes.POINTER(cofem_params), _P, _SZ, _P, _P, _P,
+                       ctypes.POINTER(cofem_stats), _P]),
+    "cofem_probe_fill": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _P]),
+    "cofem_apply_workspace_bytes": (_S, [_P, _S, _I32, ctypes.POINTER(_SZ)]),
+    "cofem_op_apply": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P, _SZ, _P]),
+    "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
+    "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
+    "cofem_diag_mstep": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _D, _D, _P,
+                              _P, _P, _P, _P]),
+}
+
+# Declared in include/cofem.h; the ABI test checks that each is exported.
+EXPORTED = sorted(_SIGS)
+
+_lib = None
+
+
+def lib():
+    """Load libcofem.so from the package directory (raises if absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcofem.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != 0:
+        detail = ""
+        if rc == 2:
+            detail = (lib().cofem_last_error() or b"").decode()
+        raise CofemError(rc, where, detail)
+
+
+# ---------------------------------------------------------------- wrappers
+
+def cofem_status_string(code):
+    return lib().cofem_status_string(code).decode()
+
+
+def cofem_op_dense(N, D, dtype, phi_ptr, ld, tile_scales_ptr=None):
+    h = _P()
+    _check(lib().cofem_op_dense(N, D, dtype, phi_ptr, ld, tile_scales_ptr, ctypes.byref(h)),
+           "cofem_op_dense")
+    return h
+
+
+def cofem_op_conv1d(L, C, T, filters_ptr):
+    h = _P()
+    _check(lib().cofem_op_conv1d(L, C, T, filters_ptr, ctypes.byref(h)), "cofem_op_conv1d")
+    return h
+
+
+def cofem_op_destroy(op):
+    lib().cofem_op_destroy(op)
+
+
+def cofem_op_shape(op):
+    n, d = _I64(), _I64()
+    _check(lib().cofem_op_shape(op, ctypes.byref(n), ctypes.byref(d)), "cofem_op_shape")
+    return n.value, d.value
+
+
+def cofem_params_default(**overrides):
+    p = cofem_params()
+    lib().cofem_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def cofem_workspace_bytes(op, params):
+    n = _SZ()
+    _check(lib().cofem_workspace_bytes(op, ctypes.byref(params), ctypes.byref(n)),
+           "cofem_workspace_bytes")
+    return n.value
+
+
+def cofem_fit(op, y_ptr, beta, params, ws_ptr, ws_bytes, mu_ptr, s_ptr, alpha_ptr,
+              stream=0, want_stats=True):
+    """Runs Algorithm 1; returns a dict of per-EM-iteration statistics."""
+    n = max(params.em_iters, 1)
+    it = (ctypes.c_int32 * n)()
+    rr = (ctypes.c_double * n)()
+    cl = (ctypes.c_int32 * n)()
+    sp = (ctypes.c_int32 * n)()
+    st = cofem_stats(it, rr, cl, sp)
+    rc = lib().cofem_fit(op, y_ptr, beta, ctypes.byref(params), ws_ptr, ws_bytes, mu_ptr,
+                         s_ptr, alpha_ptr, ctypes.byref(st) if want_stats else None, stream)
+    _check(rc, "cofem_fit")
+    m = params.em_iters
+    return {"cg_iters": list(it)[:m], "relres": list(rr)[:m], "clamps": list(cl)[:m],
+            "support": list(sp)[:m]}
+
+
+def cofem_probe_fill(seed, t, K, D, dtype, out_ptr, ld, stream=0):
+    _check(lib().cofem_probe_fill(seed, t, K, D, dtype, out_ptr, ld, stream), "cofem_probe_fill")
+
+
+def cofem_apply_workspace_bytes(op, vec, ncols):
+    n = _SZ()
+    _check(lib().cofem_apply_workspace_bytes(op, vec, ncols, ctypes.byref(n)),
+           "cofem_apply_workspace_bytes")
+    return n.value
+
+
+def cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr, ws_bytes,
+                   stream=0):
+    _check(lib().cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr,
+                                ws_bytes, stream), "cofem_op_apply")
+
+
+def cofem_op_forward(op, vec, z_ptr, ldz, ncols, w_ptr, ldw, ws_ptr, ws_bytes, stream=0):
+    _check(lib().cofem_op_forward(op, vec, z_ptr, ldz, ncols, w_ptr, ldw, ws_ptr, ws_bytes,
+                                  stream), "cofem_op_forward")
+
+
+def cofem_op_adjoint(op, vec, w_ptr, ldw, ncols, z_ptr, ldz, ws_ptr, ws_bytes, stream=0):
+    _check(lib().cofem_op_adjoint(op, vec, w_ptr, ldw, ncols, z_ptr, ldz, ws_ptr, ws_bytes,
+                                  stream), "cofem_op_adjoint")
+
+
+def cofem_diag_mstep(seed, t, K, D, vec, x_ptr, ld, den_floor, support_threshold, mu_ptr,
+                     s_ptr, alpha_ptr, counts_ptr=None, stream=0):
+    _check(lib().cofem_diag_mstep(seed, t, K, D, vec, x_ptr, ld, den_floor, support_threshold,
+                                  mu_ptr, s_ptr, alpha_ptr, counts_ptr, stream),
+           "cofem_diag_mstep")

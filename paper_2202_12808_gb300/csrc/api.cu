@@ -1,0 +1,596 @@
+// Host side of libcofem: operator handles, workspace layout, the per-EM-
+// iteration CUDA graph of Algorithm 1, and the C ABI of include/cofem.h.
+//
+// One EM iteration is one graph launch:
+//   init (probes hashed into B, X = 0, R = P = B, rho, ||B||)       Alg. 1 l.5-6
+//   WHILE (not converged):                                           Sec. 3.2
+//       Q = A P (+ gamma partials) ; a = rho / gamma ; x, r update
+//       IF (residual replacement due): Q = A x ; r = B - Q
+//       p = r + b p
+//   diag estimate + M-step, statistics, t += 1                        Alg. 1 l.7-9
+// The CG stop test runs on the device and drives the WHILE node through
+// cudaGraphSetConditional, so the host never waits inside a fit.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "dense.cuh"
+
+struct cofem_op {
+  int kind;                       // 0 dense, 1 conv
+  cofem::DenseDesc dense;
+  int64_t L;
+  int C, T;
+  const float* filters;
+};
+
+namespace cofem {
+
+static thread_local std::string g_last_error;
+
+static void set_error(const char* what, cudaError_t e, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) {                                    \
+      cofem::set_error(#x, e_, __FILE__, __LINE__);             \
+      return COFEM_ERR_CUDA;                                    \
+    }                                                           \
+  } while (0)
+
+#define CKL()  CK(cudaGetLastError())
+
+int num_sms() {
+  static int cache[128] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 128) return 148;
+  if (cache[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 148;
+  }
+  return cache[dev];
+}
+
+__global__ void ctl_init_kernel(CgCtl* ctl, long long t0) {
+  ctl->t = t0;
+  ctl->em_index = 0;
+  ctl->error = 0;
+}
+
+__global__ void fill_double_kernel(double* x, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int vec_bytes(int vec) { return vec == COFEM_F64 ? 8 : 4; }
+
+// ------------------------------------------------------------ operators
+
+static bool op_supports(const cofem_op* op, int vec) {
+  if (op->kind == 0) {
+    if (vec == COFEM_F64) return op->dense.dtype == COFEM_F64;
+    if (vec == COFEM_F32) return op->dense.dtype == COFEM_F32 || op->dense.dtype == COFEM_BF16;
+    return false;
+  }
+  return false;
+}
+
+static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
+  if (op->kind == 0) {
+    DenseSimtPlan p = dense_simt_plan(op->dense.N, op->dense.D, ncols, vec_bytes(vec), num_sms());
+    return align256(p.total());
+  }
+  return 0;
+}
+
+// Y = beta Phi^T Phi X + alpha . X  (alpha may be null: no diagonal term)
+static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
+                             const double* alpha, double beta, void* y, double* dots,
+                             int* nparts, char* ws, cudaStream_t st) {
+  if (op->kind == 0) {
+    const DenseDesc& d = op->dense;
+    if (vec == COFEM_F64)
+      dense_simt_apply<double, double>(d, (const double*)x, ld, ncols, (double*)y, beta, alpha,
+                                       dots, nparts, ws, st);
+    else if (d.dtype == COFEM_F32)
+      dense_simt_apply<float, float>(d, (const float*)x, ld, ncols, (float*)y, beta, alpha,
+                                     dots, nparts, ws, st);
+    else
+      dense_simt_apply<__nv_bfloat16, float>(d, (const float*)x, ld, ncols, (float*)y, beta,
+                                             alpha, dots, nparts, ws, st);
+    CKL();
+    return COFEM_OK;
+  }
+  return COFEM_ERR_UNSUPPORTED;
+}
+
+// W = Phi Z
+static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64_t ldz,
+                               int ncols, void* w, int64_t ldw, char* ws, cudaStream_t st) {
+  if (op->kind == 0) {
+    const DenseDesc& d = op->dense;
+    if (vec == COFEM_F64)
+      dense_simt_forward<double, double>(d, (const double*)z, ldz, ncols, (double*)w, ldw, ws, st);
+    else if (d.dtype == COFEM_F32)
+      dense_simt_forward<float, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw, ws, st);
+    else
+      dense_simt_forward<__nv_bfloat16, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw,
+                                               ws, st);
+    CKL();
+    return COFEM_OK;
+  }
+  return COFEM_ERR_UNSUPPORTED;
+}
+
+// Z = beta Phi^T W
+static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64_t ldw,
+                               int ncols, void* z, int64_t ldz, double beta, char* ws,
+                               cudaStream_t st) {
+  if (op->kind == 0) {
+    const DenseDesc& d = op->dense;
+    if (vec == COFEM_F64)
+      dense_simt_adjoint<double, double>(d, (const double*)w, ldw, ncols, (double*)z, ldz, beta,
+                                         nullptr, nullptr, nullptr, nullptr, ws, st);
+    else if (d.dtype == COFEM_F32)
+      dense_simt_adjoint<float, float>(d, (const float*)w, ldw, ncols, (float*)z, ldz, beta,
+                                       nullptr, nullptr, nullptr, nullptr, ws, st);
+    else
+      dense_simt_adjoint<__nv_bfloat16, float>(d, (const float*)w, ldw, ncols, (float*)z, ldz,
+                                               beta, nullptr, nullptr, nullptr, nullptr, ws, st);
+    CKL();
+    return COFEM_OK;
+  }
+  return COFEM_ERR_UNSUPPORTED;
+}
+
+static int64_t op_N(const cofem_op* op) { return op->kind == 0 ? op->dense.N : op->L; }
+static int64_t op_D(const cofem_op* op) {
+  return op->kind == 0 ? op->dense.D : (int64_t)op->C * op->L;
+}
+
+// --------------------------------------------------------------- layout
+
+struct FitLayout {
+  size_t ctl, sc, pdots, pvec, X, R, P, Q, b, st_iters, st_relres, st_clamps, st_support, opws;
+  size_t total;
+  int64_t ld;
+};
+
+static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
+  FitLayout L;
+  const int ncols = p->K + 1;
+  const int vb = vec_bytes(p->vec_dtype);
+  L.ld = round_up(op_D(op), kLdAlign);
+  const size_t blk = align256((size_t)ncols * L.ld * vb);
+  const int ne = p->em_iters > 0 ? p->em_iters : 1;
+  size_t o = 0;
+  L.ctl = o; o += align256(sizeof(CgCtl));
+  L.sc = o; o += align256(sizeof(CgScalars));
+  L.pdots = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
+  L.pvec = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
+  L.X = o; o += blk;
+  L.R = o; o += blk;
+  L.P = o; o += blk;
+  L.Q = o; o += blk;
+  L.b = o; o += align256((size_t)L.ld * vb);
+  L.st_iters = o; o += align256(sizeof(int32_t) * ne);
+  L.st_relres = o; o += align256(sizeof(double) * ne);
+  L.st_clamps = o; o += align256(sizeof(int32_t) * ne);
+  L.st_support = o; o += align256(sizeof(int32_t) * ne);
+  L.opws = o;
+  size_t ows = op_ws_bytes(op, p->vec_dtype, ncols);
+  size_t ows1 = op_ws_bytes(op, p->vec_dtype, 1);
+  o += ows > ows1 ? ows : ows1;
+  L.total = o;
+  return L;
+}
+
+static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
+  if (!op || !p) return COFEM_ERR_INVALID_ARG;
+  if (p->K < 1 || p->K + 1 > kMaxCols) return COFEM_ERR_INVALID_ARG;
+  if (p->em_iters < 0 || p->cg_max_iters < 1 || p->fixed_cg_iters < 0) return COFEM_ERR_INVALID_ARG;
+  if (p->resid_replace_every < 0) return COFEM_ERR_INVALID_ARG;
+  if (p->vec_dtype != COFEM_F64 && p->vec_dtype != COFEM_F32) return COFEM_ERR_INVALID_ARG;
+  if (!(p->cg_tol >= 0.0) || !(p->den_floor > 0.0)) return COFEM_ERR_INVALID_ARG;
+  if (p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
+  if (!op_supports(op, p->vec_dtype)) return COFEM_ERR_UNSUPPORTED;
+  return COFEM_OK;
+}
+
+// ---------------------------------------------------------------- graph
+
+struct Streams {
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+  ~Streams() {
+    for (auto x : s)
+      if (x) cudaStreamDestroy(x);
+  }
+};
+
+static cofem_status add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+                                    cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
+  if (status != cudaStreamCaptureStatusActive) return COFEM_ERR_CUDA;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+  *body = np.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return COFEM_OK;
+}
+
+template <typename V>
+static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, double beta,
+                                   char* ws, const FitLayout& L, double* mu, double* s,
+                                   double* alpha, cudaGraphExec_t* exec) {
+  Streams ss;
+  for (auto& x : ss.s) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  CgCtl* ctl = (CgCtl*)(ws + L.ctl);
+  CgScalars* sc = (CgScalars*)(ws + L.sc);
+  double* pdots = (double*)(ws + L.pdots);
+  double* pvec = (double*)(ws + L.pvec);
+  V* X = (V*)(ws + L.X);
+  V* R = (V*)(ws + L.R);
+  V* P = (V*)(ws + L.P);
+  V* Q = (V*)(ws + L.Q);
+  V* b = (V*)(ws + L.b);
+  char* opws = ws + L.opws;
+  const int ncols = p->K + 1;
+  const int vec = p->vec_dtype;
+
+  CgConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.D = op_D(op);
+  cf.ld = L.ld;
+  cf.ncols = ncols;
+  cf.K = p->K;
+  cf.seed = p->seed;
+  cf.tol = p->cg_tol;
+  cf.max_iters = p->cg_max_iters;
+  cf.fixed_iters = p->fixed_cg_iters;
+  cf.replace_every = p->resid_replace_every;
+  cf.beta = beta;
+  cf.den_floor = p->den_floor;
+  cf.support_threshold = p->support_threshold;
+  cf.em_iters = p->em_iters;
+
+  cudaStream_t cs = ss.s[0];
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hw;
+  CK(cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault));
+  cf.while_handle = (unsigned long long)hw;
+
+  launch_cg_init<V>(cf, ctl, sc, X, R, P, b, pvec, cs);
+  CKL();
+  cudaGraph_t body = nullptr;
+  cofem_status rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &body);
+  if (rc != COFEM_OK) return rc;
+
+  // ---- WHILE body: one CG iteration
+  cudaGraphConditionalHandle hi = 0;
+  if (p->resid_replace_every > 0) {
+    CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
+    cf.if_handle = (unsigned long long)hi;
+  }
+  {
+    cudaStream_t bs = ss.s[1];
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int nparts = 0;
+    rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs);
+    if (rc != COFEM_OK) return rc;
+    launch_cg_step(cf, ctl, sc, pdots, nparts, bs);
+    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pvec, bs);
+    CKL();
+    if (p->resid_replace_every > 0) {
+      cudaGraph_t ibody = nullptr;
+      rc = add_conditional(bs, hi, cudaGraphCondTypeIf, &ibody);
+      if (rc != COFEM_OK) return rc;
+      cudaStream_t is = ss.s[2];
+      CK(cudaStreamBeginCaptureToGraph(is, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is);
+      if (rc != COFEM_OK) return rc;
+      launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, is);
+      CKL();
+      cudaGraph_t tmp;
+      CK(cudaStreamEndCapture(is, &tmp));
+    }
+    launch_cg_direction<V>(cf, ctl, sc, R, P, bs);
+    CKL();
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(bs, &tmp));
+  }
+
+  // ---- after the solve: diagonal estimate + M-step + statistics
+  launch_diag_mstep<V>(cf, ctl, 0, X, mu, s, alpha, nullptr, (int32_t*)(ws + L.st_iters),
+                       (double*)(ws + L.st_relres), (int32_t*)(ws + L.st_clamps),
+                       (int32_t*)(ws + L.st_support), cs);
+  CKL();
+  cudaGraph_t graph;
+  CK(cudaStreamEndCapture(cs, &graph));
+  cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    set_error("cudaGraphInstantiate", e, __FILE__, __LINE__);
+    return COFEM_ERR_CUDA;
+  }
+  return COFEM_OK;
+}
+
+template <typename V>
+static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
+                             const cofem_params* p, char* ws, const FitLayout& L, double* mu,
+                             double* s, double* alpha, cofem_stats* stats, cudaStream_t st) {
+  const int64_t D = op_D(op), N = op_N(op);
+  CK(cudaMemsetAsync(ws, 0, L.total, st));
+  ctl_init_kernel<<<1, 1, 0, st>>>((CgCtl*)(ws + L.ctl), p->t_offset + 1);
+  CKL();
+  if (p->t_offset == 0) {
+    fill_double_kernel<<<(unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096), 256, 0, st>>>(
+        alpha, D, p->alpha_init);
+    CKL();
+  }
+  // b = beta Phi^T y  (once per fit: y and beta do not change)
+  cofem_status rc = op_adjoint(op, p->vec_dtype, y, N, 1, ws + L.b, L.ld, beta, ws + L.opws, st);
+  if (rc != COFEM_OK) return rc;
+
+  if (p->em_iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    rc = build_em_graph<V>(op, p, beta, ws, L, mu, s, alpha, &exec);
+    if (rc != COFEM_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return rc;
+    }
+    for (int t = 0; t < p->em_iters; ++t) {
+      cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphLaunch", e, __FILE__, __LINE__);
+        cudaGraphExecDestroy(exec);
+        return COFEM_ERR_CUDA;
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) {
+      set_error("cudaStreamSynchronize", e, __FILE__, __LINE__);
+      return COFEM_ERR_CUDA;
+    }
+  } else {
+    CK(cudaStreamSynchronize(st));
+  }
+  CgCtl hctl;
+  CK(cudaMemcpy(&hctl, ws + L.ctl, sizeof(hctl), cudaMemcpyDeviceToHost));
+  if (stats && p->em_iters > 0) {
+    const int n = p->em_iters;
+    if (stats->cg_iters) CK(cudaMemcpy(stats->cg_iters, ws + L.st_iters, 4 * n, cudaMemcpyDeviceToHost));
+    if (stats->relres) CK(cudaMemcpy(stats->relres, ws + L.st_relres, 8 * n, cudaMemcpyDeviceToHost));
+    if (stats->clamps) CK(cudaMemcpy(stats->clamps, ws + L.st_clamps, 4 * n, cudaMemcpyDeviceToHost));
+    if (stats->support) CK(cudaMemcpy(stats->support, ws + L.st_support, 4 * n, cudaMemcpyDeviceToHost));
+  }
+  if (hctl.error != 0) return (cofem_status)hctl.error;
+  return COFEM_OK;
+}
+
+}  // namespace cofem
+
+// ===================================================================== ABI
+using namespace cofem;
+
+extern "C" {
+
+const char* cofem_status_string(cofem_status s) {
+  switch (s) {
+    case COFEM_OK: return "ok";
+    case COFEM_ERR_INVALID_ARG: return "invalid argument";
+    case COFEM_ERR_CUDA: return "CUDA error";
+    case COFEM_ERR_NONFINITE: return "non-finite value";
+    case COFEM_ERR_BREAKDOWN: return "CG breakdown (p^T A p <= 0)";
+    case COFEM_ERR_TIMEOUT: return "device wait timed out";
+    case COFEM_ERR_UNSUPPORTED: return "unsupported combination";
+    case COFEM_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+const char* cofem_last_error(void) { return g_last_error.c_str(); }
+
+cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void* phi_dev,
+                            int64_t ld, const float* tile_scales_dev, cofem_op** out) {
+  if (!out || !phi_dev || N < 1 || D < 1 || ld < D) return COFEM_ERR_INVALID_ARG;
+  if (dtype != COFEM_F64 && dtype != COFEM_F32 && dtype != COFEM_BF16 && dtype != COFEM_FP8_E4M3)
+    return COFEM_ERR_INVALID_ARG;
+  if (dtype == COFEM_FP8_E4M3) return COFEM_ERR_UNSUPPORTED;
+  if ((dtype == COFEM_BF16) && (ld % 64 != 0 || ((uintptr_t)phi_dev & 255)))
+    return COFEM_ERR_INVALID_ARG;
+  if ((uintptr_t)phi_dev & 15) return COFEM_ERR_INVALID_ARG;
+  cofem_op* op = new cofem_op();
+  op->kind = 0;
+  op->dense.N = N;
+  op->dense.D = D;
+  op->dense.ld = ld;
+  op->dense.dtype = dtype;
+  op->dense.phi = phi_dev;
+  op->dense.scales = tile_scales_dev;
+  *out = op;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T, const float* filters_dev,
+                             cofem_op** out) {
+  if (!out || !filters_dev || L < 64 || L % 64 != 0 || C < 1 || T < 1 || T > 128 || T > L)
+    return COFEM_ERR_INVALID_ARG;
+  cofem_op* op = new cofem_op();
+  op->kind = 1;
+  op->L = L;
+  op->C = C;
+  op->T = T;
+  op->filters = filters_dev;
+  *out = op;
+  return COFEM_OK;
+}
+
+void cofem_op_destroy(cofem_op* op) { delete op; }
+
+cofem_status cofem_op_shape(const cofem_op* op, int64_t* N, int64_t* D) {
+  if (!op) return COFEM_ERR_INVALID_ARG;
+  if (N) *N = op_N(op);
+  if (D) *D = op_D(op);
+  return COFEM_OK;
+}
+
+void cofem_params_default(cofem_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->K = 20;
+  p->em_iters = 50;
+  p->cg_max_iters = 400;
+  p->vec_dtype = COFEM_F32;
+  p->cg_tol = 1e-6;
+  p->alpha_init = 1.0;
+  p->den_floor = 1e-12;
+  p->support_threshold = 1e6;
+}
+
+cofem_status cofem_workspace_bytes(const cofem_op* op, const cofem_params* p, size_t* bytes) {
+  cofem_status rc = check_params(op, p);
+  if (rc != COFEM_OK) return rc;
+  if (!bytes) return COFEM_ERR_INVALID_ARG;
+  *bytes = fit_layout(op, p).total;
+  return COFEM_OK;
+}
+
+cofem_status cofem_fit(const cofem_op* op, const void* y_dev, double beta, const cofem_params* p,
+                       void* workspace_dev, size_t workspace_bytes, double* mu_dev, double* s_dev,
+                       double* alpha_dev, cofem_stats* stats, void* stream) {
+  cofem_status rc = check_params(op, p);
+  if (rc != COFEM_OK) return rc;
+  if (!y_dev || !workspace_dev || !mu_dev || !s_dev || !alpha_dev) return COFEM_ERR_INVALID_ARG;
+  if (!(beta > 0.0) || !isfinite(beta)) return COFEM_ERR_INVALID_ARG;
+  if ((uintptr_t)workspace_dev & 255) return COFEM_ERR_INVALID_ARG;
+  FitLayout L = fit_layout(op, p);
+  if (workspace_bytes < L.total) return COFEM_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->vec_dtype == COFEM_F64)
+    return fit_impl<double>(op, y_dev, beta, p, (char*)workspace_dev, L, mu_dev, s_dev,
+                            alpha_dev, stats, st);
+  return fit_impl<float>(op, y_dev, beta, p, (char*)workspace_dev, L, mu_dev, s_dev, alpha_dev,
+                         stats, st);
+}
+
+cofem_status cofem_probe_fill(uint64_t seed, int64_t t, int32_t K, int64_t D, cofem_dtype dtype,
+                              void* out_dev, int64_t ld, void* stream) {
+  if (!out_dev || K < 1 || K > 16384 || D < 1 || ld < D || t < 0) return COFEM_ERR_INVALID_ARG;
+  const uint64_t key = probe_key(seed, t);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == COFEM_F64) launch_probe_fill<double>(key, K, D, (double*)out_dev, ld, st);
+  else if (dtype == COFEM_F32) launch_probe_fill<float>(key, K, D, (float*)out_dev, ld, st);
+  else return COFEM_ERR_INVALID_ARG;
+  CKL();
+  return COFEM_OK;
+}
+
+cofem_status cofem_apply_workspace_bytes(const cofem_op* op, cofem_dtype vec, int32_t ncols,
+                                         size_t* bytes) {
+  if (!op || !bytes || ncols < 1 || ncols > kMaxCols) return COFEM_ERR_INVALID_ARG;
+  if (!op_supports(op, vec)) return COFEM_ERR_UNSUPPORTED;
+  *bytes = op_ws_bytes(op, vec, ncols);
+  return COFEM_OK;
+}
+
+static cofem_status check_block(const cofem_op* op, cofem_dtype vec, int32_t ncols, int64_t ld,
+                                int64_t len, void* ws, size_t wsb) {
+  if (!op || ncols < 1 || ncols > kMaxCols || ld < len || ld % kLdAlign != 0)
+    return COFEM_ERR_INVALID_ARG;
+  if (!op_supports(op, vec)) return COFEM_ERR_UNSUPPORTED;
+  if (((uintptr_t)ws & 255) != 0) return COFEM_ERR_INVALID_ARG;
+  if (wsb < op_ws_bytes(op, vec, ncols)) return COFEM_ERR_WORKSPACE;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec, const void* x_dev, int64_t ld,
+                            int32_t ncols, const double* alpha_dev, double beta, void* y_dev,
+                            void* workspace_dev, size_t workspace_bytes, void* stream) {
+  cofem_status rc = check_block(op, vec, ncols, ld, op ? op_D(op) : 0, workspace_dev,
+                                workspace_bytes);
+  if (rc != COFEM_OK) return rc;
+  if (!x_dev || !y_dev || !alpha_dev || !workspace_dev) return COFEM_ERR_INVALID_ARG;
+  return op_apply(op, vec, x_dev, ld, ncols, alpha_dev, beta, y_dev, nullptr, nullptr,
+                  (char*)workspace_dev, (cudaStream_t)stream);
+}
+
+cofem_status cofem_op_forward(const cofem_op* op, cofem_dtype vec, const void* z_dev, int64_t ldz,
+                              int32_t ncols, void* w_dev, int64_t ldw, void* workspace_dev,
+                              size_t workspace_bytes, void* stream) {
+  cofem_status rc = check_block(op, vec, ncols, ldz, op ? op_D(op) : 0, workspace_dev,
+                                workspace_bytes);
+  if (rc != COFEM_OK) return rc;
+  if (!z_dev || !w_dev || !workspace_dev || ldw < op_N(op) || ldw % kLdAlign)
+    return COFEM_ERR_INVALID_ARG;
+  return op_forward(op, vec, z_dev, ldz, ncols, w_dev, ldw, (char*)workspace_dev,
+                    (cudaStream_t)stream);
+}
+
+cofem_status cofem_op_adjoint(const cofem_op* op, cofem_dtype vec, const void* w_dev, int64_t ldw,
+                              int32_t ncols, void* z_dev, int64_t ldz, void* workspace_dev,
+                              size_t workspace_bytes, void* stream) {
+  cofem_status rc = check_block(op, vec, ncols, ldz, op ? op_D(op) : 0, workspace_dev,
+                                workspace_bytes);
+  if (rc != COFEM_OK) return rc;
+  if (!z_dev || !w_dev || !workspace_dev || ldw < op_N(op) || ldw % kLdAlign)
+    return COFEM_ERR_INVALID_ARG;
+  return op_adjoint(op, vec, w_dev, ldw, ncols, z_dev, ldz, 1.0, (char*)workspace_dev,
+                    (cudaStream_t)stream);
+}
+
+cofem_status cofem_diag_mstep(uint64_t seed, int64_t t, int32_t K, int64_t D, cofem_dtype vec,
+                              const void* x_dev, int64_t ld, double den_floor,
+                              double support_threshold, double* mu_dev, double* s_dev,
+                              double* alpha_dev, int32_t* counts_dev, void* stream) {
+  if (!x_dev || !mu_dev || !s_dev || !alpha_dev || K < 1 || K > 16384 || D < 1 || ld < D ||
+      !(den_floor > 0.0))
+    return COFEM_ERR_INVALID_ARG;
+  CgConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.D = D;
+  cf.ld = ld;
+  cf.K = K;
+  cf.ncols = K + 1;
+  cf.seed = seed;
+  cf.den_floor = den_floor;
+  cf.support_threshold = support_threshold;
+  const uint64_t key = probe_key(seed, t);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (vec == COFEM_F64)
+    launch_diag_mstep<double>(cf, nullptr, key, (const double*)x_dev, mu_dev, s_dev, alpha_dev,
+                              counts_dev, nullptr, nullptr, nullptr, nullptr, st);
+  else if (vec == COFEM_F32)
+    launch_diag_mstep<float>(cf, nullptr, key, (const float*)x_dev, mu_dev, s_dev, alpha_dev,
+                             counts_dev, nullptr, nullptr, nullptr, nullptr, st);
+  else
+    return COFEM_ERR_INVALID_ARG;
+  CKL();
+  return COFEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// Column-wise conjugate gradients on A X = B (Sec. 3.2) and the fused
+// probe / diagonal-estimate / M-step kernel (Sec. 3.1, Eq. (diag-estimate),
+// Eq. (mstep), Algorithm 1).
+//
+// Vectors are blocks of `ncols` columns of leading dimension `ld` (a
+// multiple of 64); entries d in [D, ld) are kept at zero, so the streaming
+// kernels run over [0, ld) with 16-byte vector accesses.  Column 0 is the
+// mean system, columns 1..K the probes.  Every per-column dot product is
+// accumulated in double, reduced per block by warp shuffles, then summed
+// over blocks in a fixed order by the last block to arrive (deterministic).
+#include "kernels.cuh"
+
+namespace cofem {
+
+template <typename V> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int W = 2; };
+
+template <typename V>
+__device__ __forceinline__ void vload(const V* p, V (&v)[16 / sizeof(V)]) {
+  using T = typename Vec16<V>::T;
+  T t = *reinterpret_cast<const T*>(p);
+  if constexpr (sizeof(V) == 4) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  else { v[0] = t.x; v[1] = t.y; }
+}
+template <typename V>
+__device__ __forceinline__ void vstore(V* p, const V (&v)[16 / sizeof(V)]) {
+  using T = typename Vec16<V>::T;
+  T t;
+  if constexpr (sizeof(V) == 4) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
+  else { t.x = v[0]; t.y = v[1]; }
+  *reinterpret_cast<T*>(p) = t;
+}
+
+__device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
+  if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+// Closes one CG iteration (called by the last block, all threads): the
+// residual norms rho_new are final.  Stop test, direction coefficients.
+__device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int j = 0; j < cf.ncols; ++j) tot += sc->rho_new[j];
+    const double relres = sqrt(tot) / sqrt(ctl->normB2);
+    ctl->relres = relres;
+    const int it = ctl->iter;
+    int done;
+    if (cf.fixed_iters > 0) done = it >= cf.fixed_iters;
+    else done = (relres < cf.tol) || (it >= cf.max_iters);
+    if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+    for (int j = 0; j < cf.ncols; ++j) {
+      const double r0 = sc->rho[j], r1 = sc->rho_new[j];
+      sc->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+      sc->rho[j] = r1;
+    }
+    ctl->done = done;
+    set_cond(cf.while_handle, done ? 0u : 1u);
+  }
+}
+
+// ---------------------------------------------------------------- probes
+
+template <typename V>
+__global__ void probe_fill_kernel(uint64_t key, int K, int64_t D, V* out, int64_t ld) {
+  const int k = blockIdx.y;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < ld;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V v = V(0);
+    if (d < D) {
+      const uint64_t h = probe_word(key, d, k >> 6);
+      v = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
+    }
+    out[(int64_t)k * ld + d] = v;
+  }
+}
+
+// ------------------------------------------------------------- CG start
+// X = 0, R = P = B = [b | p_1..p_K]; rho_j = ||B_j||^2 (= D for a probe).
+template <typename V>
+__global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
+                               const V* bvec, double* part) {
+  __shared__ double sh[32];
+  const int j = blockIdx.y;
+  const uint64_t key = probe_key(cf.seed, ctl->t);
+  double acc = 0.0;
+  V* x = X + (int64_t)j * cf.ld;
+  V* r = R + (int64_t)j * cf.ld;
+  V* p = P + (int64_t)j * cf.ld;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.ld;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V v = V(0);
+    if (d < cf.D) {
+      if (j == 0) {
+        v = bvec[d];
+        acc += (double)v * (double)v;
+      } else {
+        const int k = j - 1;
+        const uint64_t h = probe_word(key, d, k >> 6);
+        v = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
+      }
+    }
+    x[d] = V(0);
+    r[d] = v;
+    p[d] = v;
+  }
+  if (j == 0) {
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+  if (arrive_last(&ctl->counter[0])) {
+    if (threadIdx.x == 0) {
+      double b2 = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) b2 += part[i];
+      sc->rho[0] = b2;
+      for (int jj = 1; jj < cf.ncols; ++jj) sc->rho[jj] = (double)cf.D;
+      const double n2 = b2 + (double)cf.K * (double)cf.D;
+      ctl->normB2 = n2;
+      ctl->relres = n2 > 0.0 ? 1.0 : 0.0;
+      ctl->iter = 0;
+      ctl->replace = 0;
+      ctl->clamps = 0;
+      ctl->support = 0;
+      int done = 0;
+      if (!(n2 > 0.0)) done = 1;                       // B = 0: X = 0 solves it
+      else if (cf.fixed_iters == 0 && 1.0 < cf.tol) done = 1;
+      if (!isfinite(n2)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+      ctl->done = done;
+      set_cond(cf.while_handle, done ? 0u : 1u);
+      ctl->counter[0] = 0;
+    }
+  }
+}
+
+// ------------------------------------------- step sizes a_j = rho_j / gamma_j
+// gamma_j = p_j^T A p_j summed over the operator's per-block partials.
+__global__ void cg_step_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const double* part,
+                               int nparts) {
+  const int j = threadIdx.x;
+  if (j >= cf.ncols) return;
+  double g = 0.0;
+  for (int i = 0; i < nparts; ++i) g += part[(int64_t)i * kMaxCols + j];
+  sc->gamma[j] = g;
+  const double rho = sc->rho[j];
+  double a = 0.0;
+  if (rho > 0.0) {
+    if (!(g > 0.0)) raise_error(ctl, isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE);
+    else a = rho / g;
+  }
+  sc->a[j] = a;
+}
+
+// --------------------------------------- x += a p, r -= a q, rho_new = r^T r
+template <typename V>
+__global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
+                                 const V* P, const V* Q, double* part) {
+  __shared__ double sh[32];
+  constexpr int W = 16 / sizeof(V);
+  const int j = blockIdx.y;
+  const V a = (V)sc->a[j];
+  V* x = X + (int64_t)j * cf.ld;
+  V* r = R + (int64_t)j * cf.ld;
+  const V* p = P + (int64_t)j * cf.ld;
+  const V* q = Q + (int64_t)j * cf.ld;
+  double acc = 0.0;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W; d < cf.ld;
+       d += (int64_t)gridDim.x * blockDim.x * W) {
+    V xv[W], rv[W], pv[W], qv[W];
+    vload(x + d, xv); vload(r + d, rv); vload(p + d, pv); vload(q + d, qv);
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      xv[i] = fma(a, pv[i], xv[i]);
+      rv[i] = fma(-a, qv[i], rv[i]);
+      acc += (double)rv[i] * (double)rv[i];
+    }
+    vstore(x + d, xv); vstore(r + d, rv);
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
+  if (arrive_last(&ctl->counter[1])) {
+    if (threadIdx.x < cf.ncols) {
+      double t = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
+      sc->rho_new[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ctl->iter += 1;
+      ctl->counter[1] = 0;
+      const int rep = cf.replace_every > 0 && (ctl->iter % cf.replace_every) == 0;
+      ctl->replace = rep;
+      set_cond(cf.if_handle, rep ? 1u : 0u);
+    }
+    __syncthreads();
+    if (!ctl->replace) cg_finalize(cf, ctl, sc);
+  }
+}
+
+// ------------------------------ residual replacement: r = B - Q (Q = A x)
+template <typename V>
+__global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
+                                     const V* Q, const V* bvec, double* part) {
+  __shared__ double sh[32];
+  if (!ctl->replace) return;
+  const int j = blockIdx.y;
+  const uint64_t key = probe_key(cf.seed, ctl->t);
+  V* r = R + (int64_t)j * cf.ld;
+  const V* q = Q + (int64_t)j * cf.ld;
+  double acc = 0.0;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V bv;
+    if (j == 0) bv = bvec[d];
+    else {
+      const int k = j - 1;
+      const uint64_t h = probe_word(key, d, k >> 6);
+      bv = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
+    }
+    const V rv = bv - q[d];
+    r[d] = rv;
+    acc += (double)rv * (double)rv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
+  if (arrive_last(&ctl->counter[2])) {
+    if (threadIdx.x < cf.ncols) {
+      double t = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
+      sc->rho_new[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) { ctl->counter[2] = 0; ctl->replace = 0; }
+    cg_finalize(cf, ctl, sc);
+  }
+}
+
+// ------------------------------------------------------ p = r + b p
+template <typename V>
+__global__ void cg_direction_kernel(CgConf cf, const CgCtl* ctl, const CgScalars* sc,
+                                    const V* R, V* P) {
+  constexpr int W = 16 / sizeof(V);
+  if (ctl->done) return;
+  const int j = blockIdx.y;
+  const V b = (V)sc->b[j];
+  const V* r = R + (int64_t)j * cf.ld;
+  V* p = P + (int64_t)j * cf.ld;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W; d < cf.ld;
+       d += (int64_t)gridDim.x * blockDim.x * W) {
+    V rv[W], pv[W];
+    vload(r + d, rv); vload(p + d, pv);
+#pragma unroll
+    for (int i = 0; i < W; ++i) pv[i] = fma(b, pv[i], rv[i]);
+    vstore(p + d, pv);
+  }
+}
+
+// ------------------------------------ diagonal estimate + M-step (fused)
+// mu_d = x_0d, s_d = (1/K) sum_k p_kd x_kd, alpha_d = 1/max(mu^2 + s, floor).
+// In fit mode (ctl != nullptr) the key comes from ctl->t, the counters go to
+// ctl and the last block records the E-step's statistics and advances t.
+template <typename V>
+__global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const V* X,
+                                  double* mu, double* s, double* alpha, int32_t* counts,
+                                  int32_t* st_iters, double* st_relres, int32_t* st_clamps,
+                                  int32_t* st_support) {
+  __shared__ double sh[32];
+  const uint64_t key = ctl ? probe_key(cf.seed, ctl->t) : key_in;
+  const int K = cf.K;
+  int clamps = 0, support = 0, bad = 0;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    const double m = (double)X[d];
+    double acc = 0.0;
+    for (int w = 0; w * 64 < K; ++w) {
+      const uint64_t h = probe_word(key, d, w);
+      const int kend = min(K, (w + 1) * 64);
+      for (int k = w * 64; k < kend; ++k) {
+        const double xv = (double)X[(int64_t)(k + 1) * cf.ld + d];
+        acc += ((h >> (k & 63)) & 1ull) ? -xv : xv;
+      }
+    }
+    const double sd = acc / (double)K;
+    const double den = m * m + sd;
+    if (den < cf.den_floor) ++clamps;
+    const double al = 1.0 / fmax(den, cf.den_floor);
+    if (!isfinite(m) || !isfinite(sd)) bad = 1;
+    if (al < cf.support_threshold) ++support;
+    mu[d] = m;
+    s[d] = sd;
+    alpha[d] = al;
+  }
+  const double cs = block_sum((double)clamps, sh);
+  const double ss = block_sum((double)support, sh);
+  const double bs = block_sum((double)bad, sh);
+  int* cc = ctl ? &ctl->clamps : counts;
+  int* sp = ctl ? &ctl->support : (counts ? counts + 1 : nullptr);
+  if (threadIdx.x == 0) {
+    if (cc && cs > 0) atomicAdd(cc, (int)cs);
+    if (sp && ss > 0) atomicAdd(sp, (int)ss);
+    if (bs > 0 && ctl) raise_error(ctl, COFEM_ERR_NONFINITE);
+  }
+  if (ctl && arrive_last(&ctl->counter[3])) {
+    if (threadIdx.x == 0) {
+      const int e = ctl->em_index;
+      if (e < cf.em_iters) {
+        st_iters[e] = ctl->iter;
+        st_relres[e] = ctl->relres;
+        st_clamps[e] = ctl->clamps;
+        st_support[e] = ctl->support;
+      }
+      ctl->em_index = e + 1;
+      ctl->t += 1;
+      ctl->counter[3] = 0;
+    }
+  }
+}
+
+// --------------------------------------------------- small helpers
+
+template <typename V>
+__global__ void scale_kernel(V* x, int64_t n, double beta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (V)((double)x[i] * beta);
+}
+
+// ------------------------------------------------------------ launchers
+
+static int vec_blocks(int64_t ld, int W, int ncols, int sms) {
+  int64_t need = (ld / W + 255) / 256;
+  int64_t cap = (int64_t)8 * sms / (ncols > 0 ? ncols : 1);
+  if (cap < 1) cap = 1;
+  int64_t b = need < cap ? need : cap;
+  if (b > kMaxParts) b = kMaxParts;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename V>
+void launch_probe_fill(uint64_t key, int K, int64_t D, V* out, int64_t ld, cudaStream_t st) {
+  const int sms = num_sms();
+  dim3 g(vec_blocks(ld, 1, K, sms), K);
+  probe_fill_kernel<V><<<g, 256, 0, st>>>(key, K, D, out, ld);
+}
+
+template <typename V>
+void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
+                    const V* bvec, double* part, cudaStream_t st) {
+  dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
+  cg_init_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, bvec, part);
+}
+
+void launch_cg_step(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const double* part,
+                    int nparts, cudaStream_t st) {
+  cg_step_kernel<<<1, kMaxCols, 0, st>>>(cf, ctl, sc, part, nparts);
+}
+
+template <typename V>
+void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
+                      const V* Q, double* part, cudaStream_t st) {
+  dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
+  cg_update_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, Q, part);
+}
+
+template <typename V>
+void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
+                          const V* bvec, double* part, cudaStream_t st) {
+  dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
+  cg_true_resid_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, R, Q, bvec, part);
+}
+
+template <typename V>
+void launch_cg_direction(const CgConf& cf, const CgCtl* ctl, const CgScalars* sc,
+                         const V* R, V* P, cudaStream_t st) {
+  dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
+  cg_direction_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, R, P);
+}
+
+template <typename V>
+void launch_diag_mstep(const CgConf& cf, CgCtl* ctl, uint64_t key, const V* X, double* mu,
+                       double* s, double* alpha, int32_t* counts, int32_t* st_iters,
+                       double* st_relres, int32_t* st_clamps, int32_t* st_support,
+                       cudaStream_t st) {
+  int blocks = vec_blocks(cf.ld, 1, 1, num_sms());
+  diag_mstep_kernel<V><<<blocks, 256, 0, st>>>(cf, ctl, key, X, mu, s, alpha, counts,
+                                               st_iters, st_relres, st_clamps, st_support);
+}
+
+template <typename V>
+void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  scale_kernel<V><<<blocks, 256, 0, st>>>(x, n, beta);
+}
+
+#define COFEM_INST(V)                                                                   \
+  template void launch_probe_fill<V>(uint64_t, int, int64_t, V*, int64_t, cudaStream_t); \
+  template void launch_cg_init<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, V*,         \
+                                  const V*, double*, cudaStream_t);                     \
+  template void launch_cg_update<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, const V*, \
+                                    const V*, double*, cudaStream_t);                   \
+  template void launch_cg_true_resid<V>(const CgConf&, CgCtl*, CgScalars*, V*, const V*, \
+                                        const V*, double*, cudaStream_t);               \
+  template void launch_cg_direction<V>(const CgConf&, const CgCtl*, const CgScalars*,    \
+                                       const V*, V*, cudaStream_t);                     \
+  template void launch_diag_mstep<V>(const CgConf&, CgCtl*, uint64_t, const V*, double*, \
+                                     double*, double*, int32_t*, int32_t*, double*,     \
+                                     int32_t*, int32_t*, cudaStream_t);                 \
+  template void launch_scale<V>(V*, int64_t, double, cudaStream_t);
+COFEM_INST(float)
+COFEM_INST(double)
+
+}  // namespace cofem

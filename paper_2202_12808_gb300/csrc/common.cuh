@@ -1,0 +1,123 @@
+// Shared device/host definitions of libcofem (GB300, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/cofem.h"
+
+namespace cofem {
+
+constexpr int kMaxCols = 64;        // K + 1 <= 64 columns per block
+constexpr int kLdAlign = 64;        // leading dimensions are multiples of 64
+constexpr int kMaxParts = 2048;     // max partial-sum slots per reduction
+
+// Device-resident control block of one CG solve / one fit.  Lives in the
+// workspace; every field is written only by kernels (after a host memset).
+struct CgCtl {
+  int iter;            // CG iterations done in the current E-step
+  int done;            // solve finished (converged or out of iterations)
+  int replace;         // true-residual replacement due in this iteration
+  int error;           // first cofem_status raised on the device
+  long long t;         // EM iteration number of the current E-step (1-based)
+  int em_index;        // index of the current E-step in the stats arrays
+  int clamps;          // M-step counters of the current EM iteration
+  int support;
+  int pad0;
+  double normB2;       // ||B||_F^2
+  double relres;       // ||R||_F / ||B||_F after the last iteration
+  unsigned int counter[8];  // arrival counters of last-block reductions
+};
+
+// Per-column CG scalars (double, Sec. 3.2 recurrences).
+struct CgScalars {
+  double rho[kMaxCols];      // r_j^T r_j
+  double rho_new[kMaxCols];
+  double gamma[kMaxCols];    // p_j^T A p_j
+  double a[kMaxCols];        // step sizes
+  double b[kMaxCols];        // direction updates
+};
+
+// Static problem description passed by value to the CG kernels.
+struct CgConf {
+  int64_t D;
+  int64_t ld;
+  int ncols;                 // K + 1
+  int K;
+  uint64_t seed;
+  double tol;
+  int max_iters;
+  int fixed_iters;
+  int replace_every;
+  double beta;
+  double den_floor;
+  double support_threshold;
+  int em_iters;
+  unsigned long long while_handle;   // cudaGraphConditionalHandle or 0
+  unsigned long long if_handle;      // residual-replacement IF node or 0
+};
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t m) {
+  return (x + m - 1) / m * m;
+}
+
+// ---------------------------------------------------------------- probes
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Key of EM iteration t.
+__host__ __device__ __forceinline__ uint64_t probe_key(uint64_t seed, long long t) {
+  return mix64(mix64(seed) ^ (uint64_t)t);
+}
+
+// 64 probe signs of coordinate d, word w (bit k set => p = -1).
+__device__ __forceinline__ uint64_t probe_word(uint64_t key, int64_t d, int w) {
+  return mix64(key ^ (((uint64_t)d << 8) | (uint64_t)w));
+}
+
+// ---------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = lane < nw ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// Records the first device error (later ones are dropped).
+__device__ __forceinline__ void raise_error(CgCtl* ctl, int code) {
+  atomicCAS(&ctl->error, 0, code);
+}
+
+// Last-block arrival: returns true in every thread of the last block to
+// arrive on counter `c`; that block must reset the counter.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace cofem

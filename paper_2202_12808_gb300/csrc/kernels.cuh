@@ -1,0 +1,50 @@
+// Internal launcher declarations of libcofem.
+#pragma once
+#include "common.cuh"
+
+namespace cofem {
+
+int num_sms();   // SM count of the current device (cached per device)
+
+// ---- CG / probe / M-step kernels (cg_kernels.cu) ----
+template <typename V>
+void launch_probe_fill(uint64_t key, int K, int64_t D, V* out, int64_t ld, cudaStream_t st);
+template <typename V>
+void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
+                    const V* bvec, double* part, cudaStream_t st);
+void launch_cg_step(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const double* part,
+                    int nparts, cudaStream_t st);
+template <typename V>
+void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
+                      const V* Q, double* part, cudaStream_t st);
+template <typename V>
+void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
+                          const V* bvec, double* part, cudaStream_t st);
+template <typename V>
+void launch_cg_direction(const CgConf& cf, const CgCtl* ctl, const CgScalars* sc,
+                         const V* R, V* P, cudaStream_t st);
+template <typename V>
+void launch_diag_mstep(const CgConf& cf, CgCtl* ctl, uint64_t key, const V* X, double* mu,
+                       double* s, double* alpha, int32_t* counts, int32_t* st_iters,
+                       double* st_relres, int32_t* st_clamps, int32_t* st_support,
+                       cudaStream_t st);
+template <typename V>
+void launch_scale(V* x, int64_t n, double beta, cudaStream_t st);
+
+// ---- operator application ----
+// Every operator application writes, besides its output, per-block partial
+// dot products gamma_j = x_j^T (A x)_j into `dots` (layout [part][kMaxCols])
+// and returns the number of parts used through *nparts (0 if dots == null).
+struct ApplyArgs {
+  const void* x;       // input block (vec dtype), leading dim ld
+  void* y;             // output block
+  int64_t ld;
+  int ncols;
+  const double* alpha; // D doubles (nullptr: no diagonal term)
+  double beta;
+  double* dots;        // [kMaxParts][kMaxCols] partials or nullptr
+  char* ws;            // operator scratch
+  size_t ws_bytes;
+};
+
+}  // namespace cofem

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; host-only entry points behave without a GPU.  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2202_12808_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "cofem.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cofem_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2202_12808_gb300 import build
+    build.build()
+    return B.lib()
+
+
+def test_header_declares_binding_names():
+    assert _header_functions() == B.EXPORTED
+
+
+def test_library_exports_every_declared_symbol(built):
+    for name in _header_functions():
+        assert hasattr(built, name), name
+
+
+def test_status_strings(built):
+    assert B.cofem_status_string(0) == "ok"
+    assert "workspace" in B.cofem_status_string(7)
+
+
+def test_params_default_matches_header(built):
+    p = B.cofem_params_default()
+    assert (p.K, p.em_iters, p.cg_max_iters, p.fixed_cg_iters, p.resid_replace_every) == (20, 50, 400, 0, 0)
+    assert p.vec_dtype == B.COFEM_F32
+    assert (p.cg_tol, p.alpha_init, p.den_floor, p.support_threshold) == (1e-6, 1.0, 1e-12, 1e6)
+    assert ctypes.sizeof(B.cofem_params) == 6 * 4 + 4 * 8 + 8 + 8
+
+
+def test_invalid_operator_arguments(built):
+    with pytest.raises(B.CofemError) as e:
+        B.cofem_op_dense(0, 10, B.COFEM_F32, 256, 10)
+    assert e.value.code == 1
+    with pytest.raises(B.CofemError):
+        B.cofem_op_dense(4, 10, B.COFEM_F32, 0, 10)          # null pointer
+    with pytest.raises(B.CofemError):
+        B.cofem_op_dense(4, 10, B.COFEM_BF16, 256, 10)       # ld not a multiple of 64
+    with pytest.raises(B.CofemError):
+        B.cofem_op_conv1d(100, 8, 64, 256)                   # L not a multiple of 64
+    h = B.cofem_op_dense(4, 10, B.COFEM_F32, 256, 12)
+    assert B.cofem_op_shape(h) == (4, 10)
+    B.cofem_op_destroy(h)
+    h = B.cofem_op_conv1d(128, 3, 5, 256)
+    assert B.cofem_op_shape(h) == (128, 384)
+    B.cofem_op_destroy(h)

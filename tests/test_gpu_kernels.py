@@ -1,0 +1,137 @@
+"""Kernel-level parity: each hot-path step through the C ABI against the
+oracle on the same seeded inputs.  Sizes span several tiles plus a ragged
+tail; column counts include 1, 2, 17, 21, 33 and 64."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import probe_hash as ph
+from oracle import sbl
+from paper_2202_12808_gb300 import binding as B
+from paper_2202_12808_gb300 import datagen
+from gpu_helpers import bf16_round, from_block, ld_of, phi_tensor, rel_l2, to_block
+
+pytestmark = pytest.mark.gpu
+
+
+def _ws(op, vec, ncols):
+    n = B.cofem_apply_workspace_bytes(op, vec, ncols)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device="cuda")
+
+
+@pytest.mark.parametrize("K,D,t,seed", [(20, 1024, 1, 0), (20, 1024, 50, 0), (32, 32768, 7, 3),
+                                        (100, 777, 2, 123456789), (1, 65, 1, 2 ** 63 + 5)])
+def test_probe_fill_bit_exact(cuda_lib, K, D, t, seed):
+    for dt, vec in ((torch.float64, B.COFEM_F64), (torch.float32, B.COFEM_F32)):
+        ld = ld_of(D)
+        out = torch.full((K, ld), 7.0, dtype=dt, device="cuda")
+        B.cofem_probe_fill(seed, t, K, D, vec, out.data_ptr(), ld)
+        torch.cuda.synchronize()
+        got = out[:, :D].T.cpu().double().numpy()
+        ref = ph.probe_matrix(seed, t, K, D)
+        assert np.array_equal(got, ref)
+        assert torch.all(out[:, D:] == 0)
+
+
+def test_probe_fill_all_config1_iterations(cuda_lib):
+    # all (t, k, d) of 50 EM iterations at K = 20, D = 1024
+    ld = 1024
+    out = torch.empty((20, ld), dtype=torch.float32, device="cuda")
+    for t in range(1, 51):
+        B.cofem_probe_fill(0, t, 20, 1024, B.COFEM_F32, out.data_ptr(), ld)
+        assert np.array_equal(out.T.cpu().double().numpy(), ph.probe_matrix(0, t, 20, 1024))
+
+
+APPLY_CASES = [
+    # (N, D, ncols)
+    (200, 1000, 1), (200, 1000, 2), (200, 1000, 17), (256, 1024, 21), (130, 515, 33),
+    (96, 300, 64),
+]
+
+
+@pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
+@pytest.mark.parametrize("kind", ["f64", "f32", "bf16"])
+def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
+    prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
+    rng = np.random.default_rng(ncols)
+    X = rng.standard_normal((D, ncols))
+    alpha = rng.uniform(0.5, 1e3, D)
+    beta = 1e4
+    if kind == "f64":
+        Phi_ref = prob.Phi.astype(np.float64)
+        Phi_t, ld_phi = phi_tensor(Phi_ref, torch.float64)
+        vdt, vec, tol = torch.float64, B.COFEM_F64, 1e-12
+        pdt = B.COFEM_F64
+    elif kind == "f32":
+        Phi_ref = prob.Phi.astype(np.float64)
+        Phi_t, ld_phi = phi_tensor(prob.Phi, torch.float32)
+        vdt, vec, tol = torch.float32, B.COFEM_F32, 2e-5
+        pdt = B.COFEM_F32
+    else:
+        t16, Phi_ref = bf16_round(prob.Phi)
+        Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
+        vdt, vec, tol = torch.float32, B.COFEM_F32, 2e-5
+        pdt = B.COFEM_BF16
+    X_in = X.astype(np.float32).astype(np.float64) if vdt == torch.float32 else X
+    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
+    try:
+        Xb, ld = to_block(X_in, vdt)
+        Yb = torch.full_like(Xb, 3.0)
+        al = torch.from_numpy(alpha).cuda()
+        ws = _ws(op, vec, ncols)
+        B.cofem_op_apply(op, vec, Xb.data_ptr(), ld, ncols, al.data_ptr(), beta, Yb.data_ptr(),
+                         ws.data_ptr(), ws.numel())
+        torch.cuda.synchronize()
+        phi, phit, _ = sbl.dense_dictionary(Phi_ref)
+        ref = sbl.apply_A(phi, phit, beta, alpha, X_in)
+        got = from_block(Yb, D)
+        for j in range(ncols):
+            assert rel_l2(got[:, j], ref[:, j]) <= tol, (j, rel_l2(got[:, j], ref[:, j]))
+        assert torch.all(Yb[:, D:] == 0)
+        # the two halves
+        W = torch.zeros((ncols, ld_of(N)), dtype=vdt, device="cuda")
+        B.cofem_op_forward(op, vec, Xb.data_ptr(), ld, ncols, W.data_ptr(), ld_of(N),
+                           ws.data_ptr(), ws.numel())
+        Z = torch.zeros_like(Xb)
+        B.cofem_op_adjoint(op, vec, W.data_ptr(), ld_of(N), ncols, Z.data_ptr(), ld,
+                           ws.data_ptr(), ws.numel())
+        torch.cuda.synchronize()
+        Wref = Phi_ref @ X_in
+        Wg = W[:, :N].T.double().cpu().numpy()
+        assert rel_l2(Wg, Wref) <= tol
+        Zref = Phi_ref.T @ Wg
+        assert rel_l2(from_block(Z, D), Zref) <= tol
+    finally:
+        B.cofem_op_destroy(op)
+
+
+@pytest.mark.parametrize("K,D", [(20, 1024), (32, 1000), (5, 70), (64, 4096)])
+def test_diag_mstep(cuda_lib, K, D):
+    rng = np.random.default_rng(K * D)
+    seed, t = 99, 4
+    X = rng.standard_normal((D, K + 1)) * 1e-2
+    X[:10, 0] = 0.0                       # mu = 0 ...
+    X[:10, 1:] = 0.0                      # ... and s = 0: clamped denominators
+    for dt, vec in ((torch.float64, B.COFEM_F64), (torch.float32, B.COFEM_F32)):
+        Xin = X.astype(np.float32).astype(np.float64) if dt == torch.float32 else X
+        Xb, ld = to_block(Xin, dt)
+        mu = torch.empty(D, dtype=torch.float64, device="cuda")
+        s = torch.empty_like(mu)
+        al = torch.empty_like(mu)
+        counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+        B.cofem_diag_mstep(seed, t, K, D, vec, Xb.data_ptr(), ld, 1e-12, 1e6, mu.data_ptr(),
+                           s.data_ptr(), al.data_ptr(), counts.data_ptr())
+        torch.cuda.synchronize()
+        P = ph.probe_matrix(seed, t, K, D)
+        s_ref = sbl.diag_estimate(P, Xin[:, 1:])
+        mu_ref = Xin[:, 0]
+        a_ref, clamps = sbl.m_step(mu_ref, s_ref)
+        np.testing.assert_array_equal(mu.cpu().numpy(), mu_ref)
+        # sums of K terms in another order: compare on the scale of the terms
+        scale = np.abs(Xin[:, 1:]).sum(axis=1) / K
+        assert np.all(np.abs(s.cpu().numpy() - s_ref) <= 1e-14 * scale + 1e-300)
+        a = al.cpu().numpy()
+        np.testing.assert_allclose(1.0 / a, 1.0 / a_ref, rtol=1e-12, atol=1e-14 * scale.max())
+        c = counts.cpu().numpy()
+        assert c[0] == clamps
+        assert c[1] == int(np.sum(a < 1e6))

@@ -83,6 +83,14 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype,
                             const void* phi_dev, int64_t ld,
                             const float* tile_scales_dev, cofem_op** out);
 
+/* BF16 dictionaries only: how the FP32 vectors meet the BF16 Phi.
+ * nterms 1..3: on the tensor cores (tcgen05), each FP32 vector is split
+ * into nterms BF16 terms (x = x1 + x2 [+ x3], each term the BF16 rounding of
+ * the remainder), all products accumulate in FP32; 3 terms carry the full
+ * 24-bit FP32 mantissa, 2 terms 16 bits.  nterms 0: CUDA cores (BF16 Phi
+ * converted to FP32 in registers).  Default 3. */
+cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms);
+
 /* Circular convolutional Phi (Sec. 3.2 structured tau_D): signal length L,
  * C filters of T taps (filters_dev: C x T floats, row-major).  N = L,
  * D = C*L, coordinate d = c*L + m.
@@ -171,9 +179,10 @@ cofem_status cofem_probe_fill(uint64_t seed, int64_t t, int32_t K, int64_t D,
 
 /* Operator application Y = beta Phi^T (Phi X) + alpha . X over ncols
  * columns (the product A X of Eq. (mat-eq)).  X, Y: blocks of vec dtype
- * with leading dimension ld (>= D).  alpha_dev: D doubles.  workspace: at
- * least cofem_apply_workspace_bytes(op, vec, ncols).  ncols <= 64.
- * Asynchronous. */
+ * with leading dimension ld (>= D); entries d >= D of X must be zero, those
+ * of Y are unspecified.  alpha_dev: D doubles.  workspace: at least
+ * cofem_apply_workspace_bytes(op, vec, ncols), 256-byte aligned.
+ * ncols <= 64.  Asynchronous. */
 cofem_status cofem_apply_workspace_bytes(const cofem_op* op, cofem_dtype vec,
                                          int32_t ncols, size_t* bytes);
 cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec,

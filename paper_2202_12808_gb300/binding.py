@@ -57,6 +57,7 @@ _SIGS = {
     "cofem_status_string": (ctypes.c_char_p, [_S]),
     "cofem_last_error": (ctypes.c_char_p, []),
     "cofem_op_dense": (_S, [_I64, _I64, _S, _P, _I64, _P, ctypes.POINTER(_P)]),
+    "cofem_op_dense_set_terms": (_S, [_P, _I32]),
     "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "cofem_op_destroy": (None, [_P]),
     "cofem_op_shape": (_S, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -113,6 +114,10 @@ def cofem_op_dense(N, D, dtype, phi_ptr, ld, tile_scales_ptr=None):
     _check(lib().cofem_op_dense(N, D, dtype, phi_ptr, ld, tile_scales_ptr, ctypes.byref(h)),
            "cofem_op_dense")
     return h
+
+
+def cofem_op_dense_set_terms(op, nterms):
+    _check(lib().cofem_op_dense_set_terms(op, nterms), "cofem_op_dense_set_terms")
 
 
 def cofem_op_conv1d(L, C, T, filters_ptr):

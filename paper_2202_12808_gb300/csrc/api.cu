@@ -86,10 +86,19 @@ static bool op_supports(const cofem_op* op, int vec) {
   return false;
 }
 
+static bool use_tc(const cofem_op* op) {
+  return op->kind == 0 && op->dense.dtype == COFEM_BF16 && op->dense.nterms > 0;
+}
+
 static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
   if (op->kind == 0) {
     DenseSimtPlan p = dense_simt_plan(op->dense.N, op->dense.D, ncols, vec_bytes(vec), num_sms());
-    return align256(p.total());
+    size_t b = align256(p.total());
+    if (use_tc(op)) {
+      DenseTcPlan q = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms, num_sms());
+      if (align256(q.total) > b) b = align256(q.total);
+    }
+    return b;
   }
   return 0;
 }
@@ -97,9 +106,19 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
 // Y = beta Phi^T Phi X + alpha . X  (alpha may be null: no diagonal term)
 static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
                              const double* alpha, double beta, void* y, double* dots,
-                             int* nparts, char* ws, cudaStream_t st) {
+                             int* nparts, char* ws, cudaStream_t st, int* err = nullptr) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
+    if (use_tc(op) && vec == COFEM_F32) {
+      int rc = dense_tc_apply(d, d.nterms, (const float*)x, ld, ncols, (float*)y, beta, alpha,
+                              dots, nparts, ws, err, st);
+      if (rc == 1) {
+        g_last_error = "cuTensorMapEncodeTiled failed";
+        return COFEM_ERR_CUDA;
+      }
+      CKL();
+      return COFEM_OK;
+    }
     if (vec == COFEM_F64)
       dense_simt_apply<double, double>(d, (const double*)x, ld, ncols, (double*)y, beta, alpha,
                                        dots, nparts, ws, st);
@@ -298,7 +317,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     cudaStream_t bs = ss.s[1];
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int nparts = 0;
-    rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs);
+    rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs,
+                  &ctl->error);
     if (rc != COFEM_OK) return rc;
     launch_cg_step(cf, ctl, sc, pdots, nparts, bs);
     launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pvec, bs);
@@ -309,7 +329,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       if (rc != COFEM_OK) return rc;
       cudaStream_t is = ss.s[2];
       CK(cudaStreamBeginCaptureToGraph(is, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is);
+      rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is,
+                    &ctl->error);
       if (rc != COFEM_OK) return rc;
       launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, is);
       CKL();
@@ -432,7 +453,15 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   op->dense.dtype = dtype;
   op->dense.phi = phi_dev;
   op->dense.scales = tile_scales_dev;
+  op->dense.nterms = dtype == COFEM_BF16 ? 3 : 0;
   *out = op;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms) {
+  if (!op || op->kind != 0 || op->dense.dtype != COFEM_BF16 || nterms < 0 || nterms > 3)
+    return COFEM_ERR_INVALID_ARG;
+  op->dense.nterms = nterms;
   return COFEM_OK;
 }
 

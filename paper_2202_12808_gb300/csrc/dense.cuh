@@ -11,6 +11,8 @@ struct DenseDesc {
   int dtype;               // cofem_dtype of the stored entries
   const void* phi;
   const float* scales;     // FP8 tile scales or nullptr
+  int nterms;              // BF16: terms per FP32 vector on tensor cores
+                           // (1..3), 0 = CUDA-core path
 };
 
 struct DenseSimtPlan {
@@ -22,6 +24,24 @@ struct DenseSimtPlan {
 };
 
 DenseSimtPlan dense_simt_plan(int64_t N, int64_t D, int ncols, int vec_bytes, int sms);
+
+// Tensor-core plan (BF16 dictionary, FP32 vectors split into NT BF16 terms).
+struct DenseTcPlan {
+  int NT, nc, BN;            // terms, output columns, MMA N (B-operand rows)
+  uint32_t tmem_cols;        // tensor-memory columns allocated per CTA
+  int64_t ld, ldw;           // padded D and N
+  int nk1, nk2;              // K blocks (64) of the two products
+  int S1, kbps1;             // split-K of the first product
+  size_t smem;               // dynamic shared memory per CTA
+  size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, total;
+};
+DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms);
+
+// Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map
+// encoding failed) or 2 (launch failed).  err: device error word or null.
+int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
+                   double beta, const double* alpha, double* dots, int* nparts, char* ws,
+                   int* err, cudaStream_t st);
 
 template <typename TA, typename V>
 void dense_simt_forward(const DenseDesc& op, const V* Z, int64_t ldz, int ncols, V* W,

@@ -1,0 +1,436 @@
+// Dense dictionary operator on the 5th-generation tensor cores (tcgen05):
+//   A X = beta Phi^T (Phi X) + alpha . X        (Eq. (mat-eq))
+// for a BF16 dictionary and FP32 right-hand sides.
+//
+// Each FP32 column x_j is represented exactly enough for FP32 work by NT
+// BF16 terms x_j = x_j1 + x_j2 (+ x_j3) (each term the BF16 rounding of the
+// remainder).  Products of BF16 values are exact in the FP32 accumulator,
+// so NT = 3 reproduces a 24-bit mantissa; the terms of column j are stored
+// as rows j*NT + t of a K-major operand and summed in the epilogue.
+//
+//   split   X      -> Xs (BF16, BN rows x ld)
+//   GEMM1   W_s    = Phi[:, K-range s] Xs[K-range s]      tcgen05, split-K
+//   reduce  W      = sum_s W_s  -> Ws (BF16 terms, BN rows x ldw)
+//   GEMM2   Y      = beta Phi^T Ws + alpha . X, plus x_j^T y_j partials
+//
+// Both GEMMs stream Phi through shared memory with TMA (128-byte swizzle,
+// evict-first L2 policy) into a STAGES-deep ring; one thread issues the
+// MMAs into a 128 x BN FP32 accumulator in tensor memory; four warps read it
+// back with tcgen05.ld.  GEMM1 reads Phi K-major (rows n, d contiguous);
+// GEMM2 reads the same bytes MN-major (Phi^T without a transpose copy).
+// Every wait is bounded: a timeout sets COFEM_ERR_TIMEOUT and the CTA
+// drains its copies, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "dense.cuh"
+#include "tc_ptx.cuh"
+
+namespace cofem {
+
+constexpr int kTcThreads = 192;     // warp 0 TMA, warp 1 MMA/TMEM, warps 2-5 epilogue
+constexpr int kTcStages = 3;
+constexpr int kTileM = 128;
+constexpr int kTileK = 64;          // 64 bf16 = one 128-byte swizzle row
+constexpr uint32_t kATileBytes = kTileM * kTileK * 2;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+template <int NT> struct TermGroup;
+template <> struct TermGroup<1> { static constexpr int G = 16, COLS = 16; };
+template <> struct TermGroup<2> { static constexpr int G = 8, COLS = 16; };
+template <> struct TermGroup<3> { static constexpr int G = 16, COLS = 48; };
+
+struct TcArgs {
+  int64_t M;            // output rows (N for GEMM1, D for GEMM2)
+  int nk_total;         // K blocks of 64
+  int kb_per_split;
+  int nc;               // output columns
+  int BN;               // MMA N (rows of the B operand)
+  uint32_t tmem_cols;
+  // GEMM1
+  float* wpart;
+  int64_t ldw;
+  int64_t split_stride;
+  // GEMM2
+  float* y;
+  const float* x;
+  int64_t ld;
+  const double* alpha;
+  double beta;
+  double* dots;
+  int* err;
+};
+
+__device__ __forceinline__ void tc_fail(int* err, volatile int* abort) {
+  *abort = 1;
+  if (err) atomicCAS(err, 0, (int)COFEM_ERR_TIMEOUT);
+}
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(kTcThreads, 1)
+dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const TcArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t b_bytes = (uint32_t)args.BN * 128u;
+  const uint32_t stage_bytes = kATileBytes + b_bytes;
+  uint64_t* full = (uint64_t*)(smem + kTcStages * stage_bytes);
+  uint64_t* empty = full + kTcStages;
+  uint64_t* accbar = empty + kTcStages;
+  uint32_t* tmem_slot = (uint32_t*)(accbar + 1);
+  volatile int* abort = (volatile int*)(tmem_slot + 1);
+  double* red = (double*)(tmem_slot + 4);          // [4][64] epilogue partial dots
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kTileM;
+  const int kb0 = blockIdx.y * args.kb_per_split;
+  const int kb1 = min(args.nk_total, kb0 + args.kb_per_split);
+  const int nk = max(0, kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accbar, 1);
+    *abort = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&mapA);
+    tc::prefetch_tmap(&mapB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, args.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint64_t pol_a = tc::policy_evict_first();
+      const uint64_t pol_b = tc::policy_evict_last();
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kTcStages;
+        const uint32_t ph = (uint32_t)(i / kTcStages) & 1u;
+        if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort, kWaitLimitNs)) {
+          tc_fail(args.err, abort);
+          break;
+        }
+        uint8_t* sa = smem + s * stage_bytes;
+        uint8_t* sb = sa + kATileBytes;
+        tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+        const int kb = kb0 + i;
+        if (MODE == 0) {
+          tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
+        } else {
+          tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
+          tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK, pol_a);
+        }
+        tc::tma_load_2d(sb, &mapB, &full[s], kb * kTileK, 0, pol_b);
+        ++issued;
+      }
+      if (*abort) {
+        // drain this CTA's copies still in flight before leaving
+        volatile int never = 0;
+        for (int i = max(0, issued - kTcStages); i < issued; ++i)
+          tc::mbar_wait(&full[i % kTcStages], (uint32_t)(i / kTcStages) & 1u, &never,
+                        kWaitLimitNs);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTileM, args.BN, MODE == 1 ? 1 : 0, 0);
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kTcStages;
+        const uint32_t ph = (uint32_t)(i / kTcStages) & 1u;
+        if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
+          tc_fail(args.err, abort);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t a_base = tc::smem_u32(smem + s * stage_bytes);
+        const uint32_t b_base = a_base + kATileBytes;
+#pragma unroll
+        for (int k = 0; k < kTileK / 16; ++k) {
+          uint64_t adesc;
+          if (MODE == 0) adesc = tc::smem_desc_sw128(a_base + k * 32, 16, 1024);
+          else adesc = tc::smem_desc_sw128(a_base + k * 2048, kATileBytes / 2, 1024);
+          const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
+          tc::mma_bf16(tmem, adesc, bdesc, idesc, (i > 0 || k > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[s]);
+      }
+      tc::mma_commit(accbar);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int g = warp & 3;
+    const int64_t row = m0 + 32 * g + lane;
+    const bool ok = tc::mbar_wait(accbar, 0, abort, 4 * kWaitLimitNs);
+    if (!ok) tc_fail(args.err, abort);
+    tc::tc_fence_after();
+    constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
+    const int ngroups = (args.nc + G - 1) / G;
+    const bool live = row < args.M;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      float v[COLS];
+#pragma unroll
+      for (int c = 0; c < COLS / 16; ++c) {
+        float t16[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(gi * COLS + 16 * c), t16);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[16 * c + q] = t16[q];
+      }
+      tc::tmem_ld_wait();
+      if (nk == 0 || !ok) {
+#pragma unroll
+        for (int q = 0; q < COLS; ++q) v[q] = 0.f;
+      }
+#pragma unroll
+      for (int jj = 0; jj < G; ++jj) {
+        const int j = gi * G + jj;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = NT - 1; t >= 0; --t) acc += v[jj * NT + t];
+        if (MODE == 0) {
+          if (j < args.nc && live)
+            args.wpart[(int64_t)blockIdx.y * args.split_stride + (int64_t)j * args.ldw + row] = acc;
+        } else {
+          double dot = 0.0;
+          if (j < args.nc && live) {
+            const float xv = args.x[(int64_t)j * args.ld + row];
+            const float yv = fmaf((float)args.alpha[row], xv, (float)args.beta * acc);
+            args.y[(int64_t)j * args.ld + row] = yv;
+            dot = (double)xv * (double)yv;
+          }
+          if (args.dots && j < args.nc) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            if (lane == 0) red[(warp - 2) * 64 + j] = dot;
+          }
+        }
+      }
+    }
+    if (MODE == 1 && args.dots) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 2) {
+        for (int j = lane; j < args.nc; j += 32) {
+          const double t = red[j] + red[64 + j] + red[128 + j] + red[192 + j];
+          args.dots[(int64_t)blockIdx.x * kMaxCols + j] = t;
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, args.tmem_cols);
+  }
+}
+
+// ------------------------------------------------------ split kernels
+
+template <int NT>
+__device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&o)[NT]) {
+  float r = x;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    o[t] = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(o[t]);
+  }
+}
+
+// Xs[(j*NT + t) * ld + d] = term t of X[j*ld + d]; rows >= nc*NT of the BN
+// rows are zero.  Grid (blocks, BN/NT rounded up).
+template <int NT>
+__global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int64_t D,
+                                   int64_t lds, int nc, int BN, __nv_bfloat16* __restrict__ Xs) {
+  const int j = blockIdx.y;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < lds;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    __nv_bfloat16 o[NT];
+    if (j < nc && d < D) split_terms<NT>(X[(int64_t)j * ld + d], o);
+    else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) o[t] = __float2bfloat16_rn(0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = j * NT + t;
+      if (r < BN) Xs[(int64_t)r * lds + d] = o[t];
+    }
+  }
+}
+
+// W[j][n] = sum_s Wpart[s][j][n]  -> Ws rows j*NT + t (terms); padding zero.
+template <int NT>
+__global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t sstride,
+                                    int64_t N, int64_t ldw, int nc, int BN,
+                                    __nv_bfloat16* __restrict__ Ws) {
+  const int j = blockIdx.y;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ldw;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    float w = 0.f;
+    if (j < nc && n < N)
+      for (int s = 0; s < S; ++s) w += Wp[(int64_t)s * sstride + (int64_t)j * ldw + n];
+    __nv_bfloat16 o[NT];
+    split_terms<NT>(w, o);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = j * NT + t;
+      if (r < BN) Ws[(int64_t)r * ldw + n] = o[t];
+    }
+  }
+}
+
+// ----------------------------------------------------------- host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D bf16 map: inner extent `inner` (elements), `outer` rows, row pitch
+// `pitch` elements, box {64, box_rows}, 128-byte swizzle, zero fill.
+static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+                     uint64_t pitch, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static int term_cols(int NT) { return NT == 3 ? 48 : 16; }
+static int term_group(int NT) { return NT == 2 ? 8 : 16; }
+
+DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
+  DenseTcPlan p;
+  p.NT = NT;
+  p.nc = nc;
+  const int ngroups = (nc + term_group(NT) - 1) / term_group(NT);
+  p.BN = ngroups * term_cols(NT);
+  uint32_t tc = 32;
+  while (tc < (uint32_t)p.BN) tc <<= 1;
+  p.tmem_cols = tc;
+  p.ld = round_up(D, kLdAlign);
+  p.ldw = round_up(N, kLdAlign);
+  const int mt1 = (int)((N + kTileM - 1) / kTileM);
+  p.nk1 = (int)((D + kTileK - 1) / kTileK);
+  p.nk2 = (int)((N + kTileK - 1) / kTileK);
+  const int per_sm = 512 / (int)tc < 2 ? 512 / (int)tc : 2;
+  int want = (per_sm * sms + mt1 - 1) / mt1;
+  if (want < 1) want = 1;
+  if (want > p.nk1) want = p.nk1;
+  p.kbps1 = (p.nk1 + want - 1) / want;
+  p.S1 = (p.nk1 + p.kbps1 - 1) / p.kbps1;
+  p.smem = kTcStages * (kATileBytes + (size_t)p.BN * 128) + 1024 + 256 + 4 * 64 * 8;
+  p.off_xs = 0;
+  p.bytes_xs = round_up((int64_t)p.BN * p.ld * 2, 256);
+  p.off_wpart = p.bytes_xs;
+  p.bytes_wpart = round_up((int64_t)p.S1 * nc * p.ldw * 4, 256);
+  p.off_ws = p.off_wpart + p.bytes_wpart;
+  p.bytes_ws = round_up((int64_t)p.BN * p.ldw * 2, 256);
+  p.total = p.off_ws + p.bytes_ws;
+  return p;
+}
+
+template <int MODE, int NT>
+static cudaError_t launch_tc(dim3 grid, size_t smem, const CUtensorMap& a, const CUtensorMap& b,
+                             const TcArgs& args, cudaStream_t st) {
+  auto k = dense_tc_kernel<MODE, NT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kTcThreads, smem, st>>>(a, b, args);
+  return cudaGetLastError();
+}
+
+template <int NT>
+static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int nc, float* Y,
+                            double beta, const double* alpha, double* dots, int* nparts,
+                            char* ws, int* err, cudaStream_t st) {
+  const int sms = num_sms();
+  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms);
+  __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
+  float* Wp = (float*)(ws + p.off_wpart);
+  __nv_bfloat16* Ws = (__nv_bfloat16*)(ws + p.off_ws);
+  // split X (leading dim ld) into BF16 terms Xs (pitch p.ld): GEMM1's operand
+  {
+    int64_t need = (p.ld + 255) / 256;
+    dim3 g((unsigned)(need < 128 ? need : 128), (p.BN + NT - 1) / NT);
+    split_block_kernel<NT><<<g, 256, 0, st>>>(X, ld, op.D, p.ld, nc, p.BN, Xs);
+  }
+  CUtensorMap mPhi1, mXs, mPhi2, mWs;
+  if (!make_map(&mPhi1, op.phi, op.D, op.N, op.ld, kTileM)) return 1;
+  if (!make_map(&mXs, Xs, op.D, p.BN, p.ld, p.BN)) return 1;
+  if (!make_map(&mPhi2, op.phi, op.D, op.N, op.ld, 64)) return 1;
+  if (!make_map(&mWs, Ws, op.N, p.BN, p.ldw, p.BN)) return 1;
+
+  TcArgs a1 = {};
+  a1.M = op.N;
+  a1.nk_total = p.nk1;
+  a1.kb_per_split = p.kbps1;
+  a1.nc = nc;
+  a1.BN = p.BN;
+  a1.tmem_cols = p.tmem_cols;
+  a1.wpart = Wp;
+  a1.ldw = p.ldw;
+  a1.split_stride = (int64_t)nc * p.ldw;
+  a1.err = err;
+  dim3 g1((unsigned)((op.N + kTileM - 1) / kTileM), p.S1);
+  if (launch_tc<0, NT>(g1, p.smem, mPhi1, mXs, a1, st) != cudaSuccess) return 2;
+
+  {
+    int64_t need = (p.ldw + 255) / 256;
+    dim3 g((unsigned)(need < 128 ? need : 128), (p.BN + NT - 1) / NT);
+    reduce_split_kernel<NT><<<g, 256, 0, st>>>(Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, p.BN, Ws);
+  }
+
+  TcArgs a2 = {};
+  a2.M = op.D;
+  a2.nk_total = p.nk2;
+  a2.kb_per_split = p.nk2;
+  a2.nc = nc;
+  a2.BN = p.BN;
+  a2.tmem_cols = p.tmem_cols;
+  a2.y = Y;
+  a2.x = X;
+  a2.ld = ld;
+  a2.alpha = alpha;
+  a2.beta = beta;
+  a2.dots = dots;
+  a2.err = err;
+  dim3 g2((unsigned)((op.D + kTileM - 1) / kTileM), 1);
+  if (launch_tc<1, NT>(g2, p.smem, mPhi2, mWs, a2, st) != cudaSuccess) return 2;
+  if (nparts) *nparts = dots ? (int)g2.x : 0;
+  return 0;
+}
+
+int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
+                   double beta, const double* alpha, double* dots, int* nparts, char* ws,
+                   int* err, cudaStream_t st) {
+  switch (NT) {
+    case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
+    case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
+    default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
+  }
+}
+
+}  // namespace cofem

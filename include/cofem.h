@@ -191,6 +191,25 @@ cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec,
                             void* workspace_dev, size_t workspace_bytes,
                             void* stream);
 
+/* cofem_op_apply without a workspace argument, for callers that may not
+ * allocate device memory (for example a plugin inside an application that
+ * owns the whole device memory pool, or a loop that must not synchronise on
+ * an allocation).  The paper has no counterpart: this is a service of the
+ * library, not a step of the method.  Scratch comes from a static device
+ * array of cofem_noalloc_scratch_capacity() bytes (16 MiB) compiled into
+ * the library; every GPU that loads the library holds it until exit.  A
+ * problem whose scratch would exceed it returns COFEM_ERR_WORKSPACE (see
+ * cofem_last_error for the sizes).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and must come before any
+ * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * race and give wrong results; order them on one stream.  Same arguments and
+ * results as cofem_op_apply.  Asynchronous. */
+cofem_status cofem_op_apply_noalloc(const cofem_op* op, cofem_dtype vec,
+                                    const void* x_dev, int64_t ld, int32_t ncols,
+                                    const double* alpha_dev, double beta,
+                                    void* y_dev, void* stream);
+size_t cofem_noalloc_scratch_capacity(void);
+
 /* The two halves: W = Phi Z (ncols columns of length N, leading dimension
  * ldw) and Z = Phi^T W (length D, leading dimension ldz).  Used for
  * b = beta Phi^T y.  Same workspace rule as cofem_op_apply. Asynchronous. */

@@ -68,6 +68,8 @@ _SIGS = {
     "cofem_probe_fill": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _P]),
     "cofem_apply_workspace_bytes": (_S, [_P, _S, _I32, ctypes.POINTER(_SZ)]),
     "cofem_op_apply": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P, _SZ, _P]),
+    "cofem_op_apply_noalloc": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P]),
+    "cofem_noalloc_scratch_capacity": (_SZ, []),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_diag_mstep": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _D, _D, _P,
@@ -185,6 +187,15 @@ def cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr, ws
                    stream=0):
     _check(lib().cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr,
                                 ws_bytes, stream), "cofem_op_apply")
+
+
+def cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, stream=0):
+    _check(lib().cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr,
+                                        stream), "cofem_op_apply_noalloc")
+
+
+def cofem_noalloc_scratch_capacity():
+    return lib().cofem_noalloc_scratch_capacity()
 
 
 def cofem_op_forward(op, vec, z_ptr, ldz, ncols, w_ptr, ldw, ws_ptr, ws_bytes, stream=0):

@@ -623,3 +623,29 @@ cofem_status cofem_diag_mstep(uint64_t seed, int64_t t, int32_t K, int64_t D, co
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Internal hooks for entry points defined in other translation units; they
+// forward to the same routines cofem_op_apply uses.
+namespace cofem {
+
+cofem_status apply_check(const cofem_op* op, cofem_dtype vec, int32_t ncols, int64_t ld) {
+  if (!op || ncols < 1 || ncols > kMaxCols || ld < op_D(op) || ld % kLdAlign != 0)
+    return COFEM_ERR_INVALID_ARG;
+  if (!op_supports(op, vec)) return COFEM_ERR_UNSUPPORTED;
+  return COFEM_OK;
+}
+
+size_t apply_scratch_bytes(const cofem_op* op, cofem_dtype vec, int32_t ncols) {
+  return op_ws_bytes(op, vec, ncols);
+}
+
+cofem_status apply_with_scratch(const cofem_op* op, cofem_dtype vec, const void* x, int64_t ld,
+                                int32_t ncols, const double* alpha, double beta, void* y,
+                                char* scratch, cudaStream_t st) {
+  return op_apply(op, vec, x, ld, ncols, alpha, beta, y, nullptr, nullptr, scratch, st);
+}
+
+void set_last_error(const char* msg) { g_last_error = msg; }
+
+}  // namespace cofem

@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--phi", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--terms", type=int, default=3,
+                    help="BF16 terms per FP32 vector on the tensor cores (1-3; 0 = CUDA cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -176,12 +178,12 @@ def reference_arm(args):
 
 # ------------------------------------------------------------ GPU arm
 
-def launches_per_em(cg_iters, replace_every, kernels_per_apply):
+def launches_per_em(cg_iters, replace_every, per_iter, per_replace):
     """Our kernel launches in one EM iteration: init, per CG iteration
-    (operator apply + step + update + direction), per replacement (operator
-    apply + true residual), diag/M-step."""
+    (operator kernels + update + direction), per residual replacement
+    (operator kernels on x + true residual), diag/M-step."""
     n_rep = cg_iters // replace_every if replace_every else 0
-    return 1 + cg_iters * (kernels_per_apply + 3) + n_rep * (kernels_per_apply + 1) + 1
+    return 1 + cg_iters * per_iter + n_rep * per_replace + 1
 
 
 def main():
@@ -209,6 +211,8 @@ def main():
     if args.phi == "bf16":
         phi_t = phi_t.to(torch.bfloat16)
     op = api.DenseOperator(phi_t)
+    if args.phi == "bf16":
+        B.cofem_op_dense_set_terms(op.handle, args.terms)
     y = torch.from_numpy(prob.y.astype(np.float32)).to(dev)
     kw = dict(vec_dtype=B.COFEM_F32, K=CFG["K"], cg_tol=CFG["cg_tol"],
               cg_max_iters=CFG["cg_max_iters"], resid_replace_every=CFG["resid_replace_every"],
@@ -241,6 +245,14 @@ def main():
     value = ws * args.steps / (ms / 1e3)
     cg = res.stats["cg_iters"]
 
+    if args.phi == "bf16" and args.terms > 0:
+        # tensor cores: 2 GEMMs per apply (P's split comes from the CG kernels;
+        # an apply to x adds a split kernel)
+        per_iter, per_rep = 2 + 2, 3 + 1
+        apply_kernels = "split + GEMM1 (tcgen05) + GEMM2 (tcgen05)"
+    else:
+        per_iter, per_rep = 4 + 2, 4 + 1
+        apply_kernels = "GEMM1 + reduce + GEMM2 + epilogue (CUDA cores)"
     # dominant kernel: the operator application over K+1 columns, timed alone
     ncols = CFG["K"] + 1
     D, N = CFG["D"], CFG["N"]
@@ -272,17 +284,18 @@ def main():
     achieved = alg_bytes / apply_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "dense operator apply (Phi^T(Phi X) + alpha.X, %d cols)" % ncols,
+                "kernel": "dense operator apply (Phi^T(Phi X) + alpha.X, %d cols): %s"
+                          % (ncols, apply_kernels),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
-    kpa = 4
-    launches = 3 + sum(launches_per_em(c, CFG["resid_replace_every"], kpa) for c in cg)
+    launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep) for c in cg)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors, %s Phi" % args.phi,
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "D": D, "K": CFG["K"], "phi": args.phi,
+                       "split_terms": args.terms if args.phi == "bf16" else None,
                        "cg_tol": CFG["cg_tol"], "resid_replace_every": CFG["resid_replace_every"],
                        "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
                        "l2": "inputs larger than L2 (Phi %d MB)" % (phi_bytes >> 20),

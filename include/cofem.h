@@ -96,7 +96,8 @@ cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms);
  * D = C*L, coordinate d = c*L + m.
  *   (Phi z)[n]     = sum_c sum_j h[c][j] z_c[(n - j) mod L]
  *   (Phi^T w)_c[m] = sum_j h[c][j] w[(m + j) mod L]
- * L must be a multiple of 64; T <= 128.  F32 vectors only. */
+ * L must be a multiple of 64 and at most 2^22; T <= 64; filters_dev
+ * 4-byte aligned.  F32 vectors only. */
 cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T,
                              const float* filters_dev, cofem_op** out);
 

@@ -121,6 +121,20 @@ def conv_matrix(h, L):
     return M
 
 
+def conv_matrix_vectorised(h, L):
+    """Same matrix as conv_matrix, built with array indexing (for larger L)."""
+    h = np.asarray(h, dtype=np.float64)
+    C, T = h.shape
+    n = np.arange(L)[:, None]
+    m = np.arange(L)[None, :]
+    lag = (n - m) % L
+    M = np.zeros((L, C * L))
+    for c in range(C):
+        block = np.where(lag < T, h[c, np.minimum(lag, T - 1)], 0.0)
+        M[:, c * L:(c + 1) * L] = block
+    return M
+
+
 def apply_A(phi, phit, beta, alpha, X):
     """A X with A = beta Phi^T Phi + diag(alpha)  (Eq. mat-eq)."""
     return beta * phit(phi(X)) + alpha[:, None] * X

@@ -83,7 +83,18 @@ static bool op_supports(const cofem_op* op, int vec) {
     if (vec == COFEM_F32) return op->dense.dtype == COFEM_F32 || op->dense.dtype == COFEM_BF16;
     return false;
   }
-  return false;
+  return vec == COFEM_F32;     // convolution: FP32 vectors
+}
+
+// Convolution scratch: W (ncols x L floats), then the filters padded to 64 taps.
+static size_t conv_w_bytes(const cofem_op* op, int ncols) {
+  return align256((size_t)ncols * op->L * sizeof(float));
+}
+static const float* conv_filters64(const cofem_op* op, char* ws, int ncols, cudaStream_t st) {
+  if (op->T == 64) return op->filters;
+  float* h64 = (float*)(ws + conv_w_bytes(op, ncols));
+  conv_pad_filters(op->filters, op->C, op->T, h64, st);
+  return h64;
 }
 
 static bool use_tc(const cofem_op* op) {
@@ -100,18 +111,19 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
     }
     return b;
   }
-  return 0;
+  return conv_w_bytes(op, ncols) + align256((size_t)op->C * 64 * sizeof(float));
 }
 
 // Y = beta Phi^T Phi X + alpha . X  (alpha may be null: no diagonal term)
 static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
                              const double* alpha, double beta, void* y, double* dots,
-                             int* nparts, char* ws, cudaStream_t st, int* err = nullptr) {
+                             int* nparts, char* ws, cudaStream_t st, int* err = nullptr,
+                             unsigned flags = kApplyZeroCounters) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
     if (use_tc(op) && vec == COFEM_F32) {
       int rc = dense_tc_apply(d, d.nterms, (const float*)x, ld, ncols, (float*)y, beta, alpha,
-                              dots, nparts, ws, err, st);
+                              dots, nparts, ws, err, flags, st);
       if (rc == 1) {
         g_last_error = "cuTensorMapEncodeTiled failed";
         return COFEM_ERR_CUDA;
@@ -131,7 +143,14 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
     CKL();
     return COFEM_OK;
   }
-  return COFEM_ERR_UNSUPPORTED;
+  const float* h64 = conv_filters64(op, ws, ncols, st);
+  float* W = (float*)ws;
+  conv_forward(h64, op->C, op->L, (const float*)x, ld, ncols, W, op->L, st);
+  const int np = conv_adjoint(h64, op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
+                              (const float*)x, dots, st);
+  if (nparts) *nparts = dots ? np : 0;
+  CKL();
+  return COFEM_OK;
 }
 
 // W = Phi Z
@@ -149,7 +168,10 @@ static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64
     CKL();
     return COFEM_OK;
   }
-  return COFEM_ERR_UNSUPPORTED;
+  const float* h64 = conv_filters64(op, ws, ncols, st);
+  conv_forward(h64, op->C, op->L, (const float*)z, ldz, ncols, (float*)w, ldw, st);
+  CKL();
+  return COFEM_OK;
 }
 
 // Z = beta Phi^T W
@@ -170,7 +192,11 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
     CKL();
     return COFEM_OK;
   }
-  return COFEM_ERR_UNSUPPORTED;
+  const float* h64 = conv_filters64(op, ws, ncols, st);
+  conv_adjoint(h64, op->C, op->L, (const float*)w, ldw, ncols, (float*)z, ldz, beta, nullptr,
+               nullptr, nullptr, st);
+  CKL();
+  return COFEM_OK;
 }
 
 static int64_t op_N(const cofem_op* op) { return op->kind == 0 ? op->dense.N : op->L; }
@@ -291,6 +317,14 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cf.den_floor = p->den_floor;
   cf.support_threshold = p->support_threshold;
   cf.em_iters = p->em_iters;
+  if (use_tc(op) && vec == COFEM_F32) {
+    // the CG kernels write P's BF16 terms straight into the operator's
+    // split buffer, so the operator skips its own split of P
+    DenseTcPlan tp = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms, num_sms());
+    cf.split_nt = op->dense.nterms;
+    cf.split_rows = tp.BN;
+    cf.split_buf = opws + tp.off_xs;
+  }
 
   cudaStream_t cs = ss.s[0];
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
@@ -318,10 +352,10 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int nparts = 0;
     rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs,
-                  &ctl->error);
+                  &ctl->error, cf.split_nt > 0 ? kApplyPresplit : 0u);
     if (rc != COFEM_OK) return rc;
-    launch_cg_step(cf, ctl, sc, pdots, nparts, bs);
-    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pvec, bs);
+    cf.gamma_parts = nparts;
+    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, bs);
     CKL();
     if (p->resid_replace_every > 0) {
       cudaGraph_t ibody = nullptr;
@@ -330,7 +364,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       cudaStream_t is = ss.s[2];
       CK(cudaStreamBeginCaptureToGraph(is, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is,
-                    &ctl->error);
+                    &ctl->error, 0u);
       if (rc != COFEM_OK) return rc;
       launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, is);
       CKL();
@@ -467,7 +501,8 @@ cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms) {
 
 cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T, const float* filters_dev,
                              cofem_op** out) {
-  if (!out || !filters_dev || L < 64 || L % 64 != 0 || C < 1 || T < 1 || T > 128 || T > L)
+  if (!out || !filters_dev || L < 64 || L % 64 != 0 || L > (int64_t)2048 * kMaxParts || C < 1 ||
+      T < 1 || T > 64 || T > L || ((uintptr_t)filters_dev & 3))
     return COFEM_ERR_INVALID_ARG;
   cofem_op* op = new cofem_op();
   op->kind = 1;

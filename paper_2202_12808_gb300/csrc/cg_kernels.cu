@@ -36,6 +36,39 @@ __device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
   if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
 }
 
+// BF16 terms of one FP32 value (each the rounding of the remainder).
+__device__ __forceinline__ void write_split(const CgConf& cf, int j, int64_t d, float v) {
+  __nv_bfloat16* buf = reinterpret_cast<__nv_bfloat16*>(cf.split_buf);
+  float r = v;
+  for (int t = 0; t < cf.split_nt; ++t) {
+    const __nv_bfloat16 o = __float2bfloat16_rn(r);
+    r -= __bfloat162float(o);
+    buf[(int64_t)split_row(j, t, cf.split_nt) * cf.ld + d] = o;
+  }
+}
+__device__ __forceinline__ void write_split(const CgConf& cf, int j, int64_t d, double v) {}
+
+// Same for 4 consecutive values (d a multiple of 4): one 8-byte store per term.
+__device__ __forceinline__ void write_split4(const CgConf& cf, int j, int64_t d,
+                                             const float (&v)[4]) {
+  __nv_bfloat16* buf = reinterpret_cast<__nv_bfloat16*>(cf.split_buf);
+  float r[4] = {v[0], v[1], v[2], v[3]};
+  for (int t = 0; t < cf.split_nt; ++t) {
+    __nv_bfloat16 o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[i] = __float2bfloat16_rn(r[i]);
+      r[i] -= __bfloat162float(o[i]);
+    }
+    __nv_bfloat162 lo = __halves2bfloat162(o[0], o[1]), hi = __halves2bfloat162(o[2], o[3]);
+    uint2 pk;
+    pk.x = *reinterpret_cast<uint32_t*>(&lo);
+    pk.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(buf + (int64_t)split_row(j, t, cf.split_nt) * cf.ld + d) = pk;
+  }
+}
+__device__ __forceinline__ void write_split4(const CgConf&, int, int64_t, const double (&)[2]) {}
+
 // Closes one CG iteration (called by the last block, all threads): the
 // residual norms rho_new are final.  Stop test, direction coefficients.
 __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
@@ -104,6 +137,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
     x[d] = V(0);
     r[d] = v;
     p[d] = v;
+    if (cf.split_nt > 0) write_split(cf, j, d, v);
   }
   if (j == 0) {
     const double s = block_sum(acc, sh);
@@ -133,32 +167,37 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
   }
 }
 
-// ------------------------------------------- step sizes a_j = rho_j / gamma_j
-// gamma_j = p_j^T A p_j summed over the operator's per-block partials.
-__global__ void cg_step_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const double* part,
-                               int nparts) {
-  const int j = threadIdx.x;
-  if (j >= cf.ncols) return;
-  double g = 0.0;
-  for (int i = 0; i < nparts; ++i) g += part[(int64_t)i * kMaxCols + j];
-  sc->gamma[j] = g;
-  const double rho = sc->rho[j];
-  double a = 0.0;
-  if (rho > 0.0) {
-    if (!(g > 0.0)) raise_error(ctl, isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE);
-    else a = rho / g;
-  }
-  sc->a[j] = a;
-}
-
 // --------------------------------------- x += a p, r -= a q, rho_new = r^T r
+// a_j = rho_j / gamma_j with gamma_j the fixed-order sum of the operator's
+// per-block partials of p_j^T A p_j (every block computes the same value).
 template <typename V>
 __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
-                                 const V* P, const V* Q, double* part) {
+                                 const V* P, const V* Q, const double* gparts, double* part) {
   __shared__ double sh[32];
+  __shared__ double a_sh;
   constexpr int W = 16 / sizeof(V);
   const int j = blockIdx.y;
-  const V a = (V)sc->a[j];
+  if (threadIdx.x < 32) {
+    double g = 0.0;
+    for (int i = threadIdx.x; i < cf.gamma_parts; i += 32) g += gparts[(int64_t)i * kMaxCols + j];
+    g = warp_sum(g);
+    if (threadIdx.x == 0) {
+      const double rho = sc->rho[j];
+      double a = 0.0;
+      if (rho > 0.0) {
+        if (!(g > 0.0)) {
+          if (blockIdx.x == 0)
+            raise_error(ctl, isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE);
+        } else {
+          a = rho / g;
+        }
+      }
+      a_sh = a;
+      if (blockIdx.x == 0) { sc->gamma[j] = g; sc->a[j] = a; }
+    }
+  }
+  __syncthreads();
+  const V a = (V)a_sh;
   V* x = X + (int64_t)j * cf.ld;
   V* r = R + (int64_t)j * cf.ld;
   const V* p = P + (int64_t)j * cf.ld;
@@ -251,6 +290,7 @@ __global__ void cg_direction_kernel(CgConf cf, const CgCtl* ctl, const CgScalars
 #pragma unroll
     for (int i = 0; i < W; ++i) pv[i] = fma(b, pv[i], rv[i]);
     vstore(p + d, pv);
+    if (cf.split_nt > 0) write_split4(cf, j, d, pv);
   }
 }
 
@@ -349,16 +389,11 @@ void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* 
   cg_init_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, bvec, part);
 }
 
-void launch_cg_step(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const double* part,
-                    int nparts, cudaStream_t st) {
-  cg_step_kernel<<<1, kMaxCols, 0, st>>>(cf, ctl, sc, part, nparts);
-}
-
 template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
-                      const V* Q, double* part, cudaStream_t st) {
+                      const V* Q, const double* gparts, double* part, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
-  cg_update_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, Q, part);
+  cg_update_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, Q, gparts, part);
 }
 
 template <typename V>
@@ -398,7 +433,7 @@ void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
   template void launch_cg_init<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, V*,         \
                                   const V*, double*, cudaStream_t);                     \
   template void launch_cg_update<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, const V*, \
-                                    const V*, double*, cudaStream_t);                   \
+                                    const V*, const double*, double*, cudaStream_t);    \
   template void launch_cg_true_resid<V>(const CgConf&, CgCtl*, CgScalars*, V*, const V*, \
                                         const V*, double*, cudaStream_t);               \
   template void launch_cg_direction<V>(const CgConf&, const CgCtl*, const CgScalars*,    \

@@ -55,7 +55,19 @@ struct CgConf {
   int em_iters;
   unsigned long long while_handle;   // cudaGraphConditionalHandle or 0
   unsigned long long if_handle;      // residual-replacement IF node or 0
+  int gamma_parts;                   // partials of p^T A p written by the operator
+  int split_nt;                      // >0: also write P's BF16 terms (tensor-core operator)
+  int split_rows;                    // rows of the split buffer (B operand rows)
+  void* split_buf;                   // row split_row(j, t), pitch ld, bf16
 };
+
+// Row of the tensor-core B operand that holds BF16 term t of column j when
+// each FP32 column is split into nt terms: columns are packed G = 16/nt to a
+// group of 16 rows (with nt = 3 the 16th row of each group stays zero).
+__host__ __device__ __forceinline__ int split_row(int j, int t, int nt) {
+  const int g = 16 / nt;
+  return (j / g) * 16 + (j % g) * nt + t;
+}
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) {
   return (x + m - 1) / m * m;

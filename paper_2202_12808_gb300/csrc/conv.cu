@@ -1,0 +1,179 @@
+// Circular convolutional dictionary (a structured Phi of Sec. 3.2, whose
+// application costs O(C T L) instead of O(N D)):
+//   (Phi z)[n]     = sum_c sum_{t<T} h[c][t] z_c[(n - t) mod L]        forward
+//   (Phi^T w)_c[m] = sum_{t<T} h[c][t] w[(m + t) mod L]               adjoint
+// with N = L and D = C L, coordinate d = c L + m.  The operator of the
+// E-step, A X = beta Phi^T Phi X + alpha . X (Eq. (mat-eq)), is one forward
+// and one adjoint launch; the adjoint's epilogue applies beta, adds
+// alpha . x and accumulates the x_j^T (A x)_j partials of the CG step.
+//
+// Both kernels stage a tile of TILE = 256 * R outputs plus a T-1 halo of the
+// input column in shared memory (wrapping circularly), keep one channel's
+// filter in registers and let every thread produce R consecutive outputs
+// with a sliding register window: one shared load and R FMAs per tap.  The
+// shared tile is skewed by one word every 32 (index i -> i + i/32) so that
+// threads reading at stride R hit distinct banks.
+#include "kernels.cuh"
+
+namespace cofem {
+
+constexpr int kConvThreads = 256;
+constexpr int kConvR = 8;
+constexpr int kConvTile = kConvThreads * kConvR;   // 2048 outputs per block
+constexpr int kConvMaxT = 64;
+
+__host__ __device__ constexpr int skew(int i) { return i + (i >> 5); }
+
+// W[j][n] = sum_c sum_t h[c][t] Z[j][c*L + (n - t) mod L]      grid (L/TILE, ncols)
+template <int T>
+__global__ void __launch_bounds__(kConvThreads)
+conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ Z,
+                    int64_t ldz, float* __restrict__ W, int64_t ldw) {
+  __shared__ float zs[skew(kConvTile + kConvMaxT) + 8];
+  const int j = blockIdx.y;
+  const int64_t n0 = (int64_t)blockIdx.x * kConvTile;
+  const int tid = threadIdx.x;
+  float acc[kConvR];
+#pragma unroll
+  for (int r = 0; r < kConvR; ++r) acc[r] = 0.f;
+  const int span = kConvTile + T - 1;
+  for (int c = 0; c < C; ++c) {
+    const float* zc = Z + (int64_t)j * ldz + (int64_t)c * L;
+    __syncthreads();
+    for (int i = tid; i < span; i += kConvThreads) {
+      int64_t n = n0 - (T - 1) + i;
+      n = n < 0 ? n + L : (n >= L ? n - L : n);
+      zs[skew(i)] = zc[n];
+    }
+    float hr[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) hr[t] = __ldg(h + c * T + t);
+    __syncthreads();
+    // output n = n0 + tid*R + r needs zs index (T-1) + tid*R + r - t
+    const int base = (T - 1) + tid * kConvR;
+    float w[kConvR];
+#pragma unroll
+    for (int r = 0; r < kConvR; ++r) w[r] = zs[skew(base + r)];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[t], w[r], acc[r]);
+      if (t + 1 < T) {
+#pragma unroll
+        for (int r = kConvR - 1; r > 0; --r) w[r] = w[r - 1];
+        w[0] = zs[skew(base - t - 1)];
+      }
+    }
+  }
+  float* wj = W + (int64_t)j * ldw + n0 + tid * kConvR;
+  if (n0 + tid * kConvR + kConvR <= L) {
+    reinterpret_cast<float4*>(wj)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    reinterpret_cast<float4*>(wj)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  }
+}
+
+// Y[j][c*L + m] = beta * sum_t h[c][t] W[j][(m + t) mod L] (+ alpha . X),
+// dots[block][j] = sum over the block of X . Y.          grid (L/TILE, ncols)
+template <int T>
+__global__ void __launch_bounds__(kConvThreads)
+conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ W,
+                    int64_t ldw, float* __restrict__ Y, int64_t ld, double beta,
+                    const double* __restrict__ alpha, const float* __restrict__ X,
+                    double* dots) {
+  __shared__ float ws[skew(kConvTile + kConvMaxT) + 8];
+  __shared__ double red[32];
+  const int j = blockIdx.y;
+  const int64_t m0 = (int64_t)blockIdx.x * kConvTile;
+  const int tid = threadIdx.x;
+  const int span = kConvTile + T - 1;
+  const float* wj = W + (int64_t)j * ldw;
+  for (int i = tid; i < span; i += kConvThreads) {
+    int64_t n = m0 + i;
+    n = n >= L ? n - L : n;
+    ws[skew(i)] = wj[n];
+  }
+  __syncthreads();
+  const int base = tid * kConvR;
+  const bool live = m0 + base + kConvR <= L;
+  double dot = 0.0;
+  for (int c = 0; c < C; ++c) {
+    float hr[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) hr[t] = __ldg(h + c * T + t);
+    float w[kConvR], acc[kConvR];
+#pragma unroll
+    for (int r = 0; r < kConvR; ++r) {
+      w[r] = ws[skew(base + r)];
+      acc[r] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+#pragma unroll
+      for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[t], w[r], acc[r]);
+      if (t + 1 < T) {
+#pragma unroll
+        for (int r = 0; r < kConvR - 1; ++r) w[r] = w[r + 1];
+        w[kConvR - 1] = ws[skew(base + kConvR + t)];
+      }
+    }
+    if (live) {
+      const int64_t d = (int64_t)c * L + m0 + base;
+      float* yj = Y + (int64_t)j * ld + d;
+      float out[kConvR];
+      if (alpha) {
+        const float* xj = X + (int64_t)j * ld + d;
+        const float4 x0 = reinterpret_cast<const float4*>(xj)[0];
+        const float4 x1 = reinterpret_cast<const float4*>(xj)[1];
+        const float xv[kConvR] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int r = 0; r < kConvR; ++r) {
+          out[r] = fmaf((float)alpha[d + r], xv[r], (float)beta * acc[r]);
+          dot += (double)xv[r] * (double)out[r];
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kConvR; ++r) out[r] = (float)beta * acc[r];
+      }
+      reinterpret_cast<float4*>(yj)[0] = make_float4(out[0], out[1], out[2], out[3]);
+      reinterpret_cast<float4*>(yj)[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+  }
+  if (dots) {
+    const double s = block_sum(dot, red);
+    if (tid == 0) dots[(int64_t)blockIdx.x * kMaxCols + j] = s;
+  }
+}
+
+// ------------------------------------------------------------ launchers
+// T is instantiated for 64 taps (the dictionaries of the large workload)
+// and for every T <= 64 through the generic 64-tap kernel with zero taps
+// appended by the caller (the operator pads h to 64 taps).
+
+void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ldz, int ncols,
+                  float* W, int64_t ldw, cudaStream_t st) {
+  dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
+  conv_forward_kernel<kConvMaxT><<<g, kConvThreads, 0, st>>>(h64, C, L, Z, ldz, W, ldw);
+}
+
+int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
+                 float* Y, int64_t ld, double beta, const double* alpha, const float* X,
+                 double* dots, cudaStream_t st) {
+  dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
+  conv_adjoint_kernel<kConvMaxT><<<g, kConvThreads, 0, st>>>(h64, C, L, W, ldw, Y, ld, beta,
+                                                            alpha, X, dots);
+  return (int)g.x;
+}
+
+__global__ void pad_filters_kernel(const float* h, int C, int T, float* h64) {
+  for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < C * kConvMaxT;
+       i += blockDim.x * gridDim.x) {
+    const int c = i / kConvMaxT, t = i % kConvMaxT;
+    h64[i] = t < T ? h[c * T + t] : 0.f;
+  }
+}
+
+void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st) {
+  pad_filters_kernel<<<(C * kConvMaxT + 255) / 256, 256, 0, st>>>(h, C, T, h64);
+}
+
+}  // namespace cofem

@@ -32,16 +32,22 @@ struct DenseTcPlan {
   int64_t ld, ldw;           // padded D and N
   int nk1, nk2;              // K blocks (64) of the two products
   int S1, kbps1;             // split-K of the first product
+  int stages;                // shared-memory ring depth
   size_t smem;               // dynamic shared memory per CTA
-  size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, total;
+  size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, off_cnt, bytes_cnt, total;
 };
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms);
 
 // Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map
 // encoding failed) or 2 (launch failed).  err: device error word or null.
+// flags: kApplyPresplit -- the BF16 terms of X are already in the workspace
+// (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG kernels;
+// kApplyZeroCounters -- clear the split-K arrival counters first (needed
+// when the workspace does not come from a fit, whose kernels leave them 0).
+constexpr unsigned kApplyPresplit = 1u, kApplyZeroCounters = 2u;
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, cudaStream_t st);
+                   int* err, unsigned flags, cudaStream_t st);
 
 template <typename TA, typename V>
 void dense_simt_forward(const DenseDesc& op, const V* Z, int64_t ldz, int ncols, V* W,

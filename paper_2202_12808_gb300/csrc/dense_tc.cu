@@ -5,8 +5,9 @@
 // Each FP32 column x_j is represented exactly enough for FP32 work by NT
 // BF16 terms x_j = x_j1 + x_j2 (+ x_j3) (each term the BF16 rounding of the
 // remainder).  Products of BF16 values are exact in the FP32 accumulator,
-// so NT = 3 reproduces a 24-bit mantissa; the terms of column j are stored
-// as rows j*NT + t of a K-major operand and summed in the epilogue.
+// so NT = 3 reproduces a 24-bit mantissa; term t of column j is stored in row
+// split_row(j, t) of a K-major operand (G = 16/NT columns per 16 rows) and
+// the terms are summed in the epilogue.
 //
 //   split   X      -> Xs (BF16, BN rows x ld)
 //   GEMM1   W_s    = Phi[:, K-range s] Xs[K-range s]      tcgen05, split-K
@@ -29,16 +30,20 @@
 namespace cofem {
 
 constexpr int kTcThreads = 192;     // warp 0 TMA, warp 1 MMA/TMEM, warps 2-5 epilogue
-constexpr int kTcStages = 3;
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;          // 64 bf16 = one 128-byte swizzle row
 constexpr uint32_t kATileBytes = kTileM * kTileK * 2;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
-template <int NT> struct TermGroup;
-template <> struct TermGroup<1> { static constexpr int G = 16, COLS = 16; };
-template <> struct TermGroup<2> { static constexpr int G = 8, COLS = 16; };
-template <> struct TermGroup<3> { static constexpr int G = 16, COLS = 48; };
+constexpr int kMaxStages = 8;
+constexpr size_t kSmemPerCtaPair = 113 * 1024;   // keeps two CTAs on one SM
+
+// The NT terms of column j sit in accumulator columns split_row(j, 0..NT-1):
+// the epilogue reads 16 accumulator columns at a time, i.e. G = 16/NT
+// columns (NT = 3 leaves one of each 16 unused).
+template <int NT> struct TermGroup {
+  static constexpr int G = 16 / NT, COLS = 16;
+};
 
 struct TcArgs {
   int64_t M;            // output rows (N for GEMM1, D for GEMM2)
@@ -46,11 +51,15 @@ struct TcArgs {
   int kb_per_split;
   int nc;               // output columns
   int BN;               // MMA N (rows of the B operand)
+  int stages;           // depth of the shared-memory ring (<= kMaxStages)
   uint32_t tmem_cols;
-  // GEMM1
+  // GEMM1: split-K partials, and the last CTA of each row tile reduces
+  // them and writes the BF16 terms of W (the B operand of GEMM2)
   float* wpart;
   int64_t ldw;
   int64_t split_stride;
+  unsigned int* tile_counter;
+  __nv_bfloat16* ws_out;
   // GEMM2
   float* y;
   const float* x;
@@ -66,6 +75,16 @@ __device__ __forceinline__ void tc_fail(int* err, volatile int* abort) {
   if (err) atomicCAS(err, 0, (int)COFEM_ERR_TIMEOUT);
 }
 
+template <int NT>
+__device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&o)[NT]) {
+  float r = x;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    o[t] = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(o[t]);
+  }
+}
+
 template <int MODE, int NT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -74,9 +93,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
   const uint32_t stage_bytes = kATileBytes + b_bytes;
-  uint64_t* full = (uint64_t*)(smem + kTcStages * stage_bytes);
-  uint64_t* empty = full + kTcStages;
-  uint64_t* accbar = empty + kTcStages;
+  const int S = args.stages;
+  uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
+  uint64_t* empty = full + kMaxStages;
+  uint64_t* accbar = empty + kMaxStages;
   uint32_t* tmem_slot = (uint32_t*)(accbar + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   double* red = (double*)(tmem_slot + 4);          // [4][64] epilogue partial dots
@@ -88,7 +108,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int nk = max(0, kb1 - kb0);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -113,8 +133,8 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const uint64_t pol_b = tc::policy_evict_last();
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kTcStages;
-        const uint32_t ph = (uint32_t)(i / kTcStages) & 1u;
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
         if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort, kWaitLimitNs)) {
           tc_fail(args.err, abort);
           break;
@@ -135,17 +155,16 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       if (*abort) {
         // drain this CTA's copies still in flight before leaving
         volatile int never = 0;
-        for (int i = max(0, issued - kTcStages); i < issued; ++i)
-          tc::mbar_wait(&full[i % kTcStages], (uint32_t)(i / kTcStages) & 1u, &never,
-                        kWaitLimitNs);
+        for (int i = max(0, issued - S); i < issued; ++i)
+          tc::mbar_wait(&full[i % S], (uint32_t)(i / S) & 1u, &never, kWaitLimitNs);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_bf16_f32(kTileM, args.BN, MODE == 1 ? 1 : 0, 0);
       for (int i = 0; i < nk; ++i) {
-        const int s = i % kTcStages;
-        const uint32_t ph = (uint32_t)(i / kTcStages) & 1u;
+        const int s = i % S;
+        const uint32_t ph = (uint32_t)(i / S) & 1u;
         if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
           tc_fail(args.err, abort);
           break;
@@ -214,6 +233,40 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
       }
     }
+    if (MODE == 0) {
+      // split-K fix-up: the last CTA of this row tile sums the partials of
+      // all splits in split order and writes W's BF16 terms (rows split_row(j, t))
+      __shared__ int last_cta;
+      __threadfence();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (warp == 2 && lane == 0)
+        last_cta = atomicAdd(&args.tile_counter[blockIdx.x], 1u) == gridDim.y - 1;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (last_cta) {
+        __threadfence();
+        constexpr int G = TermGroup<NT>::G;
+        const int ngr = args.BN / 16;
+        if (row < args.ldw) {
+          for (int gi = 0; gi < ngr; ++gi) {
+            for (int jj = 0; jj < G; ++jj) {
+              const int j = gi * G + jj;
+              float w = 0.f;
+              if (j < args.nc && live)
+                for (int sp = 0; sp < (int)gridDim.y; ++sp)
+                  w += __ldcg(&args.wpart[(int64_t)sp * args.split_stride + (int64_t)j * args.ldw + row]);
+              __nv_bfloat16 o[NT];
+              split_terms<NT>(w, o);
+#pragma unroll
+              for (int t = 0; t < NT; ++t)
+                args.ws_out[(int64_t)(gi * 16 + jj * NT + t) * args.ldw + row] = o[t];
+            }
+            for (int r = G * NT; r < 16; ++r)
+              args.ws_out[(int64_t)(gi * 16 + r) * args.ldw + row] = __float2bfloat16_rn(0.f);
+          }
+        }
+        if (warp == 2 && lane == 0) args.tile_counter[blockIdx.x] = 0;
+      }
+    }
     if (MODE == 1 && args.dots) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (warp == 2) {
@@ -234,56 +287,21 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
 // ------------------------------------------------------ split kernels
 
-template <int NT>
-__device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&o)[NT]) {
-  float r = x;
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    o[t] = __float2bfloat16_rn(r);
-    r = r - __bfloat162float(o[t]);
-  }
-}
-
-// Xs[(j*NT + t) * ld + d] = term t of X[j*ld + d]; rows >= nc*NT of the BN
-// rows are zero.  Grid (blocks, BN/NT rounded up).
+// Xs[row * lds + d] = BF16 term t of X[j*ld + d] for row = split_row(j, t);
+// rows of no (j < nc, t) are zero.  Grid (blocks, BN).
 template <int NT>
 __global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int64_t D,
                                    int64_t lds, int nc, int BN, __nv_bfloat16* __restrict__ Xs) {
-  const int j = blockIdx.y;
+  constexpr int G = TermGroup<NT>::G;
+  const int r = blockIdx.y;
+  const int jj = (r % 16) / NT, t = (r % 16) % NT;
+  const int j = (r / 16) * G + jj;
+  const bool used = jj < G && j < nc;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < lds;
        d += (int64_t)gridDim.x * blockDim.x) {
     __nv_bfloat16 o[NT];
-    if (j < nc && d < D) split_terms<NT>(X[(int64_t)j * ld + d], o);
-    else {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) o[t] = __float2bfloat16_rn(0.f);
-    }
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int r = j * NT + t;
-      if (r < BN) Xs[(int64_t)r * lds + d] = o[t];
-    }
-  }
-}
-
-// W[j][n] = sum_s Wpart[s][j][n]  -> Ws rows j*NT + t (terms); padding zero.
-template <int NT>
-__global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t sstride,
-                                    int64_t N, int64_t ldw, int nc, int BN,
-                                    __nv_bfloat16* __restrict__ Ws) {
-  const int j = blockIdx.y;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ldw;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    float w = 0.f;
-    if (j < nc && n < N)
-      for (int s = 0; s < S; ++s) w += Wp[(int64_t)s * sstride + (int64_t)j * ldw + n];
-    __nv_bfloat16 o[NT];
-    split_terms<NT>(w, o);
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int r = j * NT + t;
-      if (r < BN) Ws[(int64_t)r * ldw + n] = o[t];
-    }
+    split_terms<NT>(used && d < D ? X[(int64_t)j * ld + d] : 0.f, o);
+    Xs[(int64_t)r * lds + d] = o[t];
   }
 }
 
@@ -318,15 +336,14 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t 
   return r == CUDA_SUCCESS;
 }
 
-static int term_cols(int NT) { return NT == 3 ? 48 : 16; }
-static int term_group(int NT) { return NT == 2 ? 8 : 16; }
+static int term_group(int NT) { return 16 / NT; }
 
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
   DenseTcPlan p;
   p.NT = NT;
   p.nc = nc;
   const int ngroups = (nc + term_group(NT) - 1) / term_group(NT);
-  p.BN = ngroups * term_cols(NT);
+  p.BN = ngroups * 16;
   uint32_t tc = 32;
   while (tc < (uint32_t)p.BN) tc <<= 1;
   p.tmem_cols = tc;
@@ -336,19 +353,28 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
   p.nk1 = (int)((D + kTileK - 1) / kTileK);
   p.nk2 = (int)((N + kTileK - 1) / kTileK);
   const int per_sm = 512 / (int)tc < 2 ? 512 / (int)tc : 2;
-  int want = (per_sm * sms + mt1 - 1) / mt1;
+  // one wave: at most per_sm * sms CTAs in the split-K product
+  int want = (per_sm * sms) / mt1;
   if (want < 1) want = 1;
   if (want > p.nk1) want = p.nk1;
   p.kbps1 = (p.nk1 + want - 1) / want;
   p.S1 = (p.nk1 + p.kbps1 - 1) / p.kbps1;
-  p.smem = kTcStages * (kATileBytes + (size_t)p.BN * 128) + 1024 + 256 + 4 * 64 * 8;
+  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 64 + 4 * 64 * 8 + 64;
+  const size_t stage = kATileBytes + (size_t)p.BN * 128;
+  int st = (int)((kSmemPerCtaPair - fixed) / stage);
+  if (st > kMaxStages) st = kMaxStages;
+  if (st < 2) st = 2;
+  p.stages = st;
+  p.smem = st * stage + fixed;
   p.off_xs = 0;
   p.bytes_xs = round_up((int64_t)p.BN * p.ld * 2, 256);
   p.off_wpart = p.bytes_xs;
   p.bytes_wpart = round_up((int64_t)p.S1 * nc * p.ldw * 4, 256);
   p.off_ws = p.off_wpart + p.bytes_wpart;
   p.bytes_ws = round_up((int64_t)p.BN * p.ldw * 2, 256);
-  p.total = p.off_ws + p.bytes_ws;
+  p.off_cnt = p.off_ws + p.bytes_ws;
+  p.bytes_cnt = round_up((int64_t)mt1 * 4, 256);
+  p.total = p.off_cnt + p.bytes_cnt;
   return p;
 }
 
@@ -365,16 +391,21 @@ static cudaError_t launch_tc(dim3 grid, size_t smem, const CUtensorMap& a, const
 template <int NT>
 static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int nc, float* Y,
                             double beta, const double* alpha, double* dots, int* nparts,
-                            char* ws, int* err, cudaStream_t st) {
+                            char* ws, int* err, unsigned flags, cudaStream_t st) {
   const int sms = num_sms();
   DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms);
+  const bool presplit = (flags & kApplyPresplit) != 0;
+  if (flags & kApplyZeroCounters) {
+    if (cudaMemsetAsync(ws + p.off_cnt, 0, p.bytes_cnt, st) != cudaSuccess) return 2;
+  }
   __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
   float* Wp = (float*)(ws + p.off_wpart);
   __nv_bfloat16* Ws = (__nv_bfloat16*)(ws + p.off_ws);
   // split X (leading dim ld) into BF16 terms Xs (pitch p.ld): GEMM1's operand
-  {
+  // (skipped when the caller's kernels already wrote Xs)
+  if (!presplit) {
     int64_t need = (p.ld + 255) / 256;
-    dim3 g((unsigned)(need < 128 ? need : 128), (p.BN + NT - 1) / NT);
+    dim3 g((unsigned)(need < 128 ? need : 128), p.BN);
     split_block_kernel<NT><<<g, 256, 0, st>>>(X, ld, op.D, p.ld, nc, p.BN, Xs);
   }
   CUtensorMap mPhi1, mXs, mPhi2, mWs;
@@ -389,19 +420,17 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.kb_per_split = p.kbps1;
   a1.nc = nc;
   a1.BN = p.BN;
+  a1.stages = p.stages;
   a1.tmem_cols = p.tmem_cols;
   a1.wpart = Wp;
   a1.ldw = p.ldw;
   a1.split_stride = (int64_t)nc * p.ldw;
+  a1.tile_counter = (unsigned int*)(ws + p.off_cnt);
+  a1.ws_out = Ws;
   a1.err = err;
   dim3 g1((unsigned)((op.N + kTileM - 1) / kTileM), p.S1);
   if (launch_tc<0, NT>(g1, p.smem, mPhi1, mXs, a1, st) != cudaSuccess) return 2;
 
-  {
-    int64_t need = (p.ldw + 255) / 256;
-    dim3 g((unsigned)(need < 128 ? need : 128), (p.BN + NT - 1) / NT);
-    reduce_split_kernel<NT><<<g, 256, 0, st>>>(Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, p.BN, Ws);
-  }
 
   TcArgs a2 = {};
   a2.M = op.D;
@@ -409,6 +438,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.kb_per_split = p.nk2;
   a2.nc = nc;
   a2.BN = p.BN;
+  a2.stages = p.stages;
   a2.tmem_cols = p.tmem_cols;
   a2.y = Y;
   a2.x = X;
@@ -425,11 +455,11 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
 
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, cudaStream_t st) {
+                   int* err, unsigned flags, cudaStream_t st) {
   switch (NT) {
-    case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
-    case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
-    default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, st);
+    case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
+    case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
+    default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
   }
 }
 

@@ -12,11 +12,9 @@ void launch_probe_fill(uint64_t key, int K, int64_t D, V* out, int64_t ld, cudaS
 template <typename V>
 void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                     const V* bvec, double* part, cudaStream_t st);
-void launch_cg_step(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const double* part,
-                    int nparts, cudaStream_t st);
 template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
-                      const V* Q, double* part, cudaStream_t st);
+                      const V* Q, const double* gparts, double* part, cudaStream_t st);
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
                           const V* bvec, double* part, cudaStream_t st);
@@ -30,6 +28,14 @@ void launch_diag_mstep(const CgConf& cf, CgCtl* ctl, uint64_t key, const V* X, d
                        cudaStream_t st);
 template <typename V>
 void launch_scale(V* x, int64_t n, double beta, cudaStream_t st);
+
+// ---- convolutional dictionary (conv.cu); h64: C x 64 taps ----
+void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ldz, int ncols,
+                  float* W, int64_t ldw, cudaStream_t st);
+int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
+                 float* Y, int64_t ld, double beta, const double* alpha, const float* X,
+                 double* dots, cudaStream_t st);
+void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st);
 
 // ---- operator application ----
 // Every operator application writes, besides its output, per-block partial

@@ -313,6 +313,11 @@ def test_conv_matches_materialised_matrix():
     np.testing.assert_allclose(phit(w), M.T @ w, rtol=1e-13, atol=1e-13)
 
 
+def test_conv_matrix_vectorised_matches_loops():
+    h = np.random.default_rng(2).standard_normal((3, 7))
+    np.testing.assert_array_equal(sbl.conv_matrix_vectorised(h, 40), sbl.conv_matrix(h, 40))
+
+
 def test_conv_adjoint_identity():
     rng = np.random.default_rng(1)
     C, T, L = 8, 64, 512

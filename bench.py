@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--terms", type=int, default=3,
                     help="BF16 terms per FP32 vector on the tensor cores (1-3; 0 = CUDA cores)")
+    ap.add_argument("--l2-resident-mb", type=float, default=0.0,
+                    help="MB of Phi kept in L2 by the tensor-core path (-1: 60%% of L2)")
+    ap.add_argument("--layout", default="packed", choices=["packed", "rowmajor"],
+                    help="BF16 Phi as read by the tensor cores: tile-major copy or row-major")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the operator pipeline autotuner (library defaults)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -213,6 +219,21 @@ def main():
     op = api.DenseOperator(phi_t)
     if args.phi == "bf16":
         B.cofem_op_dense_set_terms(op.handle, args.terms)
+        B.cofem_op_dense_set_l2_resident(op.handle, int(args.l2_resident_mb * 2 ** 20)
+                                         if args.l2_resident_mb >= 0 else -1)
+        if args.layout == "packed" and args.terms > 0:
+            nbp = B.cofem_dense_packed_bytes(CFG["N"], CFG["D"])
+            packed = torch.empty(nbp, dtype=torch.uint8, device=dev)
+            B.cofem_op_dense_attach_packed(op.handle, packed.data_ptr(), nbp,
+                                           torch.cuda.current_stream().cuda_stream)
+    tuned = None
+    if args.phi == "bf16" and args.terms > 0 and not args.no_autotune:
+        nbt = B.cofem_op_dense_autotune_workspace_bytes(op.handle, CFG["K"] + 1)
+        wst = torch.empty(nbt, dtype=torch.uint8, device=dev)
+        st_, cps_, us_ = B.cofem_op_dense_autotune(op.handle, CFG["K"] + 1, wst.data_ptr(), nbt,
+                                                   torch.cuda.current_stream().cuda_stream)
+        tuned = {"stages": st_, "ctas_per_sm": cps_, "us_per_apply": round(us_, 2)}
+        del wst
     y = torch.from_numpy(prob.y.astype(np.float32)).to(dev)
     kw = dict(vec_dtype=B.COFEM_F32, K=CFG["K"], cg_tol=CFG["cg_tol"],
               cg_max_iters=CFG["cg_max_iters"], resid_replace_every=CFG["resid_replace_every"],
@@ -296,6 +317,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "D": D, "K": CFG["K"], "phi": args.phi,
                        "split_terms": args.terms if args.phi == "bf16" else None,
+                       "phi_layout": args.layout if args.phi == "bf16" else "rowmajor",
+                       "pipeline": tuned,
                        "cg_tol": CFG["cg_tol"], "resid_replace_every": CFG["resid_replace_every"],
                        "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
                        "l2": "inputs larger than L2 (Phi %d MB)" % (phi_bytes >> 20),
@@ -316,6 +339,13 @@ def main():
         d_y = h_y.to(dev, non_blocking=True)
         d_alpha = h_alpha.to(dev, non_blocking=True)
         op2 = api.DenseOperator(d_phi)
+        if args.phi == "bf16":
+            B.cofem_op_dense_set_terms(op2.handle, args.terms)
+            if tuned:
+                B.cofem_op_dense_set_pipeline(op2.handle, tuned["stages"], tuned["ctas_per_sm"])
+            if args.layout == "packed" and args.terms > 0:
+                B.cofem_op_dense_attach_packed(op2.handle, packed.data_ptr(), nbp,
+                                               torch.cuda.current_stream().cuda_stream)
         r2 = api.fit(op2, d_y, prob.beta, pt, ws=wsp, alpha=d_alpha)
         for o, src in zip(outs, (r2.mu, r2.s, r2.alpha)):
             o.copy_(src, non_blocking=True)

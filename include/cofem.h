@@ -91,6 +91,46 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype,
  * converted to FP32 in registers).  Default 3. */
 cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms);
 
+/* Tensor-core pipeline shape of a BF16 dictionary's operator: shared-memory
+ * ring depth (stages, 2..8; 0 = as deep as fits) and resident CTAs per SM
+ * (1..4; 0 = 2).  Set explicitly, or let cofem_op_dense_autotune pick it.
+ * Workspace sizes (cofem_workspace_bytes, cofem_apply_workspace_bytes)
+ * depend on it: query them after choosing the shape. */
+cofem_status cofem_op_dense_set_pipeline(cofem_op* op, int32_t stages, int32_t ctas_per_sm);
+
+/* Autotuner: times one operator application (ncols FP32 columns of made-up
+ * data, 2 warm-up + 5 timed runs, CUDA events on `stream`) for every
+ * pipeline shape that fits, keeps the fastest on the handle and returns it
+ * (any output pointer may be NULL; best_us = mean microseconds per
+ * application).  workspace_dev: >= cofem_op_dense_autotune_workspace_bytes,
+ * 256-byte aligned.  Synchronous.  BF16 dictionaries on tensor cores only. */
+size_t cofem_op_dense_autotune_workspace_bytes(const cofem_op* op, int32_t ncols);
+cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, void* workspace_dev,
+                                     size_t workspace_bytes, void* stream,
+                                     int32_t* best_stages, int32_t* best_ctas_per_sm,
+                                     float* best_us);
+
+/* BF16 dictionaries: a tile-major copy of Phi for the tensor-core operator.
+ * cofem_dense_packed_bytes gives its size: ceil(N/128) * ceil(D/64) tiles of
+ * 128 x 64 values (16 KB) each, a tile's rows 64 values long and contiguous,
+ * tiles ordered by column block fastest, zero padded at the edges.
+ * cofem_op_dense_attach_packed fills packed_dev (caller-owned, 256-byte
+ * aligned, >= that size) from the handle's row-major Phi on `stream` and
+ * makes operator applications read it: each tensor-memory load is then one
+ * contiguous range of DRAM.  The row-major Phi stays in use for
+ * cofem_op_forward/adjoint and for beta Phi^T y.  packed_dev = NULL
+ * detaches.  Both buffers must outlive the handle's use. */
+size_t cofem_dense_packed_bytes(int64_t N, int64_t D);
+cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev,
+                                          size_t packed_bytes, void* stream);
+
+/* BF16 dictionaries on the tensor cores: bytes of Phi (a band of its first
+ * columns) to keep resident in L2 across the two products of every operator
+ * application, by loading that band with an evict-last and the rest with an
+ * evict-first cache policy.  -1 = 60% of the device's L2; 0 (the default)
+ * = stream all of Phi, which measured faster on GB300. */
+cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes);
+
 /* Circular convolutional Phi (Sec. 3.2 structured tau_D): signal length L,
  * C filters of T taps (filters_dev: C x T floats, row-major).  N = L,
  * D = C*L, coordinate d = c*L + m.

@@ -58,6 +58,13 @@ _SIGS = {
     "cofem_last_error": (ctypes.c_char_p, []),
     "cofem_op_dense": (_S, [_I64, _I64, _S, _P, _I64, _P, ctypes.POINTER(_P)]),
     "cofem_op_dense_set_terms": (_S, [_P, _I32]),
+    "cofem_op_dense_set_l2_resident": (_S, [_P, _I64]),
+    "cofem_dense_packed_bytes": (_SZ, [_I64, _I64]),
+    "cofem_op_dense_set_pipeline": (_S, [_P, _I32, _I32]),
+    "cofem_op_dense_autotune_workspace_bytes": (_SZ, [_P, _I32]),
+    "cofem_op_dense_autotune": (_S, [_P, _I32, _P, _SZ, _P, ctypes.POINTER(_I32),
+                                     ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
+    "cofem_op_dense_attach_packed": (_S, [_P, _P, _SZ, _P]),
     "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "cofem_op_destroy": (None, [_P]),
     "cofem_op_shape": (_S, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -120,6 +127,37 @@ def cofem_op_dense(N, D, dtype, phi_ptr, ld, tile_scales_ptr=None):
 
 def cofem_op_dense_set_terms(op, nterms):
     _check(lib().cofem_op_dense_set_terms(op, nterms), "cofem_op_dense_set_terms")
+
+
+def cofem_op_dense_set_l2_resident(op, nbytes):
+    _check(lib().cofem_op_dense_set_l2_resident(op, nbytes), "cofem_op_dense_set_l2_resident")
+
+
+def cofem_op_dense_set_pipeline(op, stages, ctas_per_sm):
+    _check(lib().cofem_op_dense_set_pipeline(op, stages, ctas_per_sm),
+           "cofem_op_dense_set_pipeline")
+
+
+def cofem_op_dense_autotune_workspace_bytes(op, ncols):
+    return lib().cofem_op_dense_autotune_workspace_bytes(op, ncols)
+
+
+def cofem_op_dense_autotune(op, ncols, ws_ptr, ws_bytes, stream=0):
+    """Returns (stages, ctas_per_sm, microseconds per application)."""
+    st, cps, us = _I32(), _I32(), ctypes.c_float()
+    _check(lib().cofem_op_dense_autotune(op, ncols, ws_ptr, ws_bytes, stream, ctypes.byref(st),
+                                         ctypes.byref(cps), ctypes.byref(us)),
+           "cofem_op_dense_autotune")
+    return st.value, cps.value, us.value
+
+
+def cofem_dense_packed_bytes(N, D):
+    return lib().cofem_dense_packed_bytes(N, D)
+
+
+def cofem_op_dense_attach_packed(op, packed_ptr, nbytes, stream=0):
+    _check(lib().cofem_op_dense_attach_packed(op, packed_ptr, nbytes, stream),
+           "cofem_op_dense_attach_packed")
 
 
 def cofem_op_conv1d(L, C, T, filters_ptr):

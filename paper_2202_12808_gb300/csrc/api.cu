@@ -101,12 +101,18 @@ static bool use_tc(const cofem_op* op) {
   return op->kind == 0 && op->dense.dtype == COFEM_BF16 && op->dense.nterms > 0;
 }
 
-static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
+// Scratch of one operator application.  For the tensor-core path it depends
+// on the pipeline shape (split-K grows with CTAs per SM): `max_shape` sizes
+// it for the largest shape the autotuner tries, otherwise for the handle's
+// current shape.
+static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape = false) {
   if (op->kind == 0) {
     DenseSimtPlan p = dense_simt_plan(op->dense.N, op->dense.D, ncols, vec_bytes(vec), num_sms());
     size_t b = align256(p.total());
     if (use_tc(op)) {
-      DenseTcPlan q = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms, num_sms());
+      DenseTcPlan q = max_shape ? dense_tc_plan(op->dense.N, op->dense.D, ncols,
+                                                op->dense.nterms, num_sms(), 4, 0)
+                                : dense_tc_plan(op->dense, ncols, num_sms());
       if (align256(q.total) > b) b = align256(q.total);
     }
     return b;
@@ -118,10 +124,18 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols) {
 static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
                              const double* alpha, double beta, void* y, double* dots,
                              int* nparts, char* ws, cudaStream_t st, int* err = nullptr,
-                             unsigned flags = kApplyZeroCounters) {
+                             unsigned flags = 0u) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
     if (use_tc(op) && vec == COFEM_F32) {
+      if (d.l2_resident_cols < 0) {
+        // 60% of this device's L2 holds a fixed band of Phi's columns
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        int64_t cols = (int64_t)(0.6 * (double)l2) / (d.N * 2) / 128 * 128;
+        const_cast<cofem_op*>(op)->dense.l2_resident_cols = cols < d.D ? cols : d.D;
+      }
       int rc = dense_tc_apply(d, d.nterms, (const float*)x, ld, ncols, (float*)y, beta, alpha,
                               dots, nparts, ws, err, flags, st);
       if (rc == 1) {
@@ -320,7 +334,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   if (use_tc(op) && vec == COFEM_F32) {
     // the CG kernels write P's BF16 terms straight into the operator's
     // split buffer, so the operator skips its own split of P
-    DenseTcPlan tp = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms, num_sms());
+    DenseTcPlan tp = dense_tc_plan(op->dense, ncols, num_sms());
     cf.split_nt = op->dense.nterms;
     cf.split_rows = tp.BN;
     cf.split_buf = opws + tp.off_xs;
@@ -488,7 +502,46 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   op->dense.phi = phi_dev;
   op->dense.scales = tile_scales_dev;
   op->dense.nterms = dtype == COFEM_BF16 ? 3 : 0;
+  op->dense.l2_resident_cols = 0;            // stream all of Phi (see the setter)
+  op->dense.packed = nullptr;
+  op->dense.tc_ctas_per_sm = 0;
+  op->dense.tc_stages = 0;
   *out = op;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_dense_set_pipeline(cofem_op* op, int32_t stages, int32_t ctas_per_sm) {
+  if (!op || op->kind != 0 || stages < 0 || stages > 8 || ctas_per_sm < 0 || ctas_per_sm > 4)
+    return COFEM_ERR_INVALID_ARG;
+  op->dense.tc_stages = stages;
+  op->dense.tc_ctas_per_sm = ctas_per_sm;
+  return COFEM_OK;
+}
+
+size_t cofem_dense_packed_bytes(int64_t N, int64_t D) {
+  if (N < 1 || D < 1) return 0;
+  return packed_bytes(N, D);
+}
+
+cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev, size_t packed_bytes_,
+                                          void* stream) {
+  if (!op || op->kind != 0 || op->dense.dtype != COFEM_BF16) return COFEM_ERR_INVALID_ARG;
+  if (!packed_dev) { op->dense.packed = nullptr; return COFEM_OK; }
+  if (((uintptr_t)packed_dev & 255) != 0) return COFEM_ERR_INVALID_ARG;
+  if (packed_bytes_ < packed_bytes(op->dense.N, op->dense.D)) return COFEM_ERR_WORKSPACE;
+  dense_pack_bf16(op->dense.phi, op->dense.N, op->dense.D, op->dense.ld, packed_dev,
+                  (cudaStream_t)stream);
+  CKL();
+  op->dense.packed = packed_dev;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes) {
+  if (!op || op->kind != 0) return COFEM_ERR_INVALID_ARG;
+  if (bytes < 0) { op->dense.l2_resident_cols = -1; return COFEM_OK; }
+  const int64_t esz = op->dense.dtype == COFEM_BF16 ? 2 : 4;
+  int64_t cols = bytes / (op->dense.N * esz) / 128 * 128;
+  op->dense.l2_resident_cols = cols < op->dense.D ? cols : op->dense.D;
   return COFEM_OK;
 }
 
@@ -682,5 +735,97 @@ cofem_status apply_with_scratch(const cofem_op* op, cofem_dtype vec, const void*
 }
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+}  // namespace cofem
+
+// ------------------------------------------------------------- autotuner
+// Times the tensor-core operator application for every pipeline shape
+// (CTAs per SM x ring depth) that fits, with CUDA events on the caller's
+// stream, and keeps the fastest on the handle.  Inputs are made up in the
+// caller's workspace (layout: operator scratch | X | Y | alpha).
+namespace cofem {
+
+__global__ void tune_fill_kernel(float* x, int64_t n, double* alpha, int64_t D) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (float)((mix64((uint64_t)i) >> 40) * (1.0 / 16777216.0) - 0.5);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D;
+       i += (int64_t)gridDim.x * blockDim.x)
+    alpha[i] = 1.0;
+}
+
+static void tune_layout(const cofem_op* op, int ncols, size_t* ows, size_t* blk, size_t* total) {
+  const int64_t ld = round_up(op->dense.D, kLdAlign);
+  *ows = align256(op_ws_bytes(op, COFEM_F32, ncols, true));
+  *blk = align256((size_t)ncols * ld * sizeof(float));
+  *total = *ows + 2 * *blk + align256((size_t)op->dense.D * sizeof(double));
+}
+
+}  // namespace cofem
+
+extern "C" size_t cofem_op_dense_autotune_workspace_bytes(const cofem_op* op, int32_t ncols) {
+  if (!op || op->kind != 0 || ncols < 1 || ncols > kMaxCols) return 0;
+  size_t a, b, t;
+  tune_layout(op, ncols, &a, &b, &t);
+  return t;
+}
+
+extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, void* workspace_dev,
+                                                size_t workspace_bytes, void* stream,
+                                                int32_t* best_stages, int32_t* best_ctas,
+                                                float* best_us) {
+  if (!op || op->kind != 0 || !use_tc(op) || ncols < 1 || ncols > kMaxCols || !workspace_dev ||
+      ((uintptr_t)workspace_dev & 255))
+    return COFEM_ERR_INVALID_ARG;
+  size_t ows, blk, total;
+  tune_layout(op, ncols, &ows, &blk, &total);
+  if (workspace_bytes < total) return COFEM_ERR_WORKSPACE;
+  char* ws = (char*)workspace_dev;
+  float* X = (float*)(ws + ows);
+  float* Y = (float*)(ws + ows + blk);
+  double* alpha = (double*)(ws + ows + 2 * blk);
+  const int64_t ld = round_up(op->dense.D, kLdAlign);
+  cudaStream_t st = (cudaStream_t)stream;
+  tune_fill_kernel<<<1024, 256, 0, st>>>(X, (int64_t)ncols * ld, alpha, op->dense.D);
+  CKL();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int keep_st = op->dense.tc_stages, keep_cps = op->dense.tc_ctas_per_sm;
+  float best = 1e30f;
+  int bst = keep_st, bcps = keep_cps;
+  cofem_status rc = COFEM_OK;
+  for (int cps = 1; cps <= 4 && rc == COFEM_OK; ++cps) {
+    DenseTcPlan full = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
+                                     num_sms(), cps, 0);
+    for (int stg = 2; stg <= full.stages && rc == COFEM_OK; ++stg) {
+      op->dense.tc_ctas_per_sm = cps;
+      op->dense.tc_stages = stg;
+      for (int w = 0; w < 2 && rc == COFEM_OK; ++w)
+        rc = op_apply(op, COFEM_F32, X, ld, ncols, alpha, 1.0, Y, nullptr, nullptr, ws, st);
+      if (rc != COFEM_OK) break;
+      const int reps = 5;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == COFEM_OK; ++r)
+        rc = op_apply(op, COFEM_F32, X, ld, ncols, alpha, 1.0, Y, nullptr, nullptr, ws, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = COFEM_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const float us = ms * 1000.f / reps;
+      if (rc == COFEM_OK && us < best) { best = us; bst = stg; bcps = cps; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  op->dense.tc_stages = rc == COFEM_OK ? bst : keep_st;
+  op->dense.tc_ctas_per_sm = rc == COFEM_OK ? bcps : keep_cps;
+  if (best_stages) *best_stages = op->dense.tc_stages;
+  if (best_ctas) *best_ctas = op->dense.tc_ctas_per_sm;
+  if (best_us) *best_us = best;
+  return rc;
+}
+
+namespace cofem {
 
 }  // namespace cofem

@@ -13,7 +13,25 @@ struct DenseDesc {
   const float* scales;     // FP8 tile scales or nullptr
   int nterms;              // BF16: terms per FP32 vector on tensor cores
                            // (1..3), 0 = CUDA-core path
+  int64_t l2_resident_cols;  // tensor-core path: columns d below this are
+                             // loaded with an evict-last L2 policy
+  const void* packed;        // tensor-core path: tile-major copy of Phi or null
+  int tc_ctas_per_sm;        // tensor-core pipeline: resident CTAs per SM (1, 2; 0 = 2)
+  int tc_stages;             // shared-memory ring depth (0 = as deep as fits)
 };
+
+// Tile-major ("packed") BF16 layout read by the tensor-core operator: tile
+// (mt, kb) holds rows [128 mt, 128 mt + 128) x columns [64 kb, 64 kb + 64) as
+// 128 rows of 64 contiguous values (16 KB), tiles ordered kb-fastest, zero
+// padded at the edges.  Every TMA box of either product is then one or two
+// contiguous DRAM ranges instead of 64-128 rows 64 KB apart.
+inline int64_t packed_tiles_m(int64_t N) { return (N + 127) / 128; }
+inline int64_t packed_tiles_k(int64_t D) { return (D + 63) / 64; }
+inline size_t packed_bytes(int64_t N, int64_t D) {
+  return (size_t)packed_tiles_m(N) * packed_tiles_k(D) * 128 * 64 * 2;
+}
+void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                     cudaStream_t st);
 
 struct DenseSimtPlan {
   int64_t ldw, ld;         // padded N and D
@@ -34,17 +52,20 @@ struct DenseTcPlan {
   int S1, kbps1;             // split-K of the first product
   int stages;                // shared-memory ring depth
   size_t smem;               // dynamic shared memory per CTA
-  size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, off_cnt, bytes_cnt, total;
+  size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, total;
 };
-DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms);
+DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm = 2,
+                          int stages = 0);
+inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
+  return dense_tc_plan(op.N, op.D, nc, op.nterms, sms, op.tc_ctas_per_sm, op.tc_stages);
+}
 
 // Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map
 // encoding failed) or 2 (launch failed).  err: device error word or null.
 // flags: kApplyPresplit -- the BF16 terms of X are already in the workspace
-// (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG kernels;
-// kApplyZeroCounters -- clear the split-K arrival counters first (needed
-// when the workspace does not come from a fit, whose kernels leave them 0).
-constexpr unsigned kApplyPresplit = 1u, kApplyZeroCounters = 2u;
+// (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG
+// kernels.
+constexpr unsigned kApplyPresplit = 1u;
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
                    int* err, unsigned flags, cudaStream_t st);

@@ -36,7 +36,7 @@ constexpr uint32_t kATileBytes = kTileM * kTileK * 2;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 
 constexpr int kMaxStages = 8;
-constexpr size_t kSmemPerCtaPair = 113 * 1024;   // keeps two CTAs on one SM
+constexpr size_t kSmemPerSm = 227 * 1024;        // usable shared memory per SM
 
 // The NT terms of column j sit in accumulator columns split_row(j, 0..NT-1):
 // the epilogue reads 16 accumulator columns at a time, i.e. G = 16/NT
@@ -53,13 +53,14 @@ struct TcArgs {
   int BN;               // MMA N (rows of the B operand)
   int stages;           // depth of the shared-memory ring (<= kMaxStages)
   uint32_t tmem_cols;
-  // GEMM1: split-K partials, and the last CTA of each row tile reduces
-  // them and writes the BF16 terms of W (the B operand of GEMM2)
+  int64_t res_d;        // Phi columns d < res_d are loaded evict-last (kept in L2)
+  const __nv_bfloat16* packed;   // pre-swizzled tile-major copy of Phi, or null
+  int64_t nkd;          // 64-column tiles of Phi (packed layout)
+  // GEMM1: split-K partials (reduced and split by reduce_split_kernel)
   float* wpart;
   int64_t ldw;
   int64_t split_stride;
-  unsigned int* tile_counter;
-  __nv_bfloat16* ws_out;
+
   // GEMM2
   float* y;
   const float* x;
@@ -129,8 +130,9 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
   if (warp == 0) {
     if (lane == 0) {
-      const uint64_t pol_a = tc::policy_evict_first();
-      const uint64_t pol_b = tc::policy_evict_last();
+      const uint64_t pol_first = tc::policy_evict_first();
+      const uint64_t pol_last = tc::policy_evict_last();
+      const uint64_t pol_b = pol_last;
       int issued = 0;
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
@@ -143,11 +145,32 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         uint8_t* sb = sa + kATileBytes;
         tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
         const int kb = kb0 + i;
+        // Phi columns below res_d stay in L2 between the two products and
+        // across CG iterations; the rest streams through
         if (MODE == 0) {
-          tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
+          const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
+          if (args.packed)   // tile (blockIdx.x, kb): one contiguous 16 KB copy
+            tc::bulk_load(sa, args.packed + ((int64_t)blockIdx.x * args.nkd + kb) * (kTileM * kTileK),
+                          kATileBytes, &full[s], pol_a);
+          else
+            tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
         } else {
-          tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
-          tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK, pol_a);
+          const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
+          if (args.packed) {
+            // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
+            // two 64-column tiles m0/64 and m0/64 + 1 give the 128 d's
+            const int64_t base = ((int64_t)(kb >> 1) * args.nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
+            const __nv_bfloat16* src = args.packed + base * kTileK;
+            tc::bulk_load(sa, src, kATileBytes / 2, &full[s], pol_a);
+            // the next 64-column tile; past the last one (D not a multiple of
+            // 128) the same half-tile is copied again: it only feeds output
+            // rows d >= D, which are not stored
+            const __nv_bfloat16* src2 = (m0 >> 6) + 1 < args.nkd ? src + kTileM * kTileK : src;
+            tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
+          } else {
+            tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
+            tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK, pol_a);
+          }
         }
         tc::tma_load_2d(sb, &mapB, &full[s], kb * kTileK, 0, pol_b);
         ++issued;
@@ -233,40 +256,6 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
       }
     }
-    if (MODE == 0) {
-      // split-K fix-up: the last CTA of this row tile sums the partials of
-      // all splits in split order and writes W's BF16 terms (rows split_row(j, t))
-      __shared__ int last_cta;
-      __threadfence();
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (warp == 2 && lane == 0)
-        last_cta = atomicAdd(&args.tile_counter[blockIdx.x], 1u) == gridDim.y - 1;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (last_cta) {
-        __threadfence();
-        constexpr int G = TermGroup<NT>::G;
-        const int ngr = args.BN / 16;
-        if (row < args.ldw) {
-          for (int gi = 0; gi < ngr; ++gi) {
-            for (int jj = 0; jj < G; ++jj) {
-              const int j = gi * G + jj;
-              float w = 0.f;
-              if (j < args.nc && live)
-                for (int sp = 0; sp < (int)gridDim.y; ++sp)
-                  w += __ldcg(&args.wpart[(int64_t)sp * args.split_stride + (int64_t)j * args.ldw + row]);
-              __nv_bfloat16 o[NT];
-              split_terms<NT>(w, o);
-#pragma unroll
-              for (int t = 0; t < NT; ++t)
-                args.ws_out[(int64_t)(gi * 16 + jj * NT + t) * args.ldw + row] = o[t];
-            }
-            for (int r = G * NT; r < 16; ++r)
-              args.ws_out[(int64_t)(gi * 16 + r) * args.ldw + row] = __float2bfloat16_rn(0.f);
-          }
-        }
-        if (warp == 2 && lane == 0) args.tile_counter[blockIdx.x] = 0;
-      }
-    }
     if (MODE == 1 && args.dots) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (warp == 2) {
@@ -305,6 +294,64 @@ __global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int6
   }
 }
 
+// W[j][n] = sum_s Wpart[s][j][n] (split order) -> BF16 terms of W in rows
+// split_row(j, t) of Ws; rows of no (j < nc, t) and n >= N are zero.
+// Grid (blocks, BN / 16 groups).
+template <int NT>
+__global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t sstride,
+                                    int64_t N, int64_t ldw, int nc,
+                                    __nv_bfloat16* __restrict__ Ws) {
+  constexpr int G = TermGroup<NT>::G;
+  const int gi = blockIdx.y;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ldw;
+       n += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int jj = 0; jj < G; ++jj) {
+      const int j = gi * G + jj;
+      float w = 0.f;
+      if (j < nc && n < N)
+        for (int s = 0; s < S; ++s) w += Wp[(int64_t)s * sstride + (int64_t)j * ldw + n];
+      __nv_bfloat16 o[NT];
+      split_terms<NT>(w, o);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) Ws[(int64_t)(gi * 16 + jj * NT + t) * ldw + n] = o[t];
+    }
+    for (int r = G * NT; r < 16; ++r) Ws[(int64_t)(gi * 16 + r) * ldw + n] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// Tile (mt, kb) = Phi[128 mt + r][64 kb + c], r < 128, c < 64, stored as the
+// 128-byte-swizzled shared-memory image the MMA reads: row r at r * 64
+// values, its 16-byte chunk q (values 8q .. 8q+7) at chunk position
+// q ^ (r mod 8).  Zero outside N x D.  One thread per 16-byte chunk.
+__global__ void pack_kernel(const __nv_bfloat16* __restrict__ phi, int64_t N, int64_t D,
+                            int64_t ld, int64_t nkd, int64_t total8,
+                            __nv_bfloat16* __restrict__ packed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total8;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * 8;                 // destination element of the chunk
+    const int64_t row = e >> 6;              // packed row index
+    const int c0 = (int)((((e & 63) >> 3) ^ (row & 7)) << 3);   // source column
+    const int r = (int)(row & 127);
+    const int64_t tile = row >> 7;
+    const int64_t kb = tile % nkd, mt = tile / nkd;
+    const int64_t n = mt * 128 + r, d0 = kb * 64 + c0;
+    __nv_bfloat16 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      v[q] = (n < N && d0 + q < D) ? phi[n * ld + d0 + q] : __float2bfloat16_rn(0.f);
+    *reinterpret_cast<uint4*>(packed + e) = *reinterpret_cast<uint4*>(v);
+  }
+}
+
+void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                     cudaStream_t st) {
+  const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
+  const int64_t blocks = (total8 + 255) / 256;
+  pack_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, st>>>(
+      (const __nv_bfloat16*)phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
+}
+
 // ----------------------------------------------------------- host side
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -338,8 +385,10 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t 
 
 static int term_group(int NT) { return 16 / NT; }
 
-DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
+DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm,
+                          int stages) {
   DenseTcPlan p;
+  if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 2;
   p.NT = NT;
   p.nc = nc;
   const int ngroups = (nc + term_group(NT) - 1) / term_group(NT);
@@ -352,7 +401,8 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
   const int mt1 = (int)((N + kTileM - 1) / kTileM);
   p.nk1 = (int)((D + kTileK - 1) / kTileK);
   p.nk2 = (int)((N + kTileK - 1) / kTileK);
-  const int per_sm = 512 / (int)tc < 2 ? 512 / (int)tc : 2;
+  int per_sm = 512 / (int)tc < ctas_per_sm ? 512 / (int)tc : ctas_per_sm;
+  if (per_sm < 1) per_sm = 1;
   // one wave: at most per_sm * sms CTAs in the split-K product
   int want = (per_sm * sms) / mt1;
   if (want < 1) want = 1;
@@ -361,8 +411,11 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
   p.S1 = (p.nk1 + p.kbps1 - 1) / p.kbps1;
   const size_t fixed = 1024 + 2 * kMaxStages * 8 + 64 + 4 * 64 * 8 + 64;
   const size_t stage = kATileBytes + (size_t)p.BN * 128;
-  int st = (int)((kSmemPerCtaPair - fixed) / stage);
+  // each resident CTA also costs 1 KB of reserved shared memory
+  const size_t budget = kSmemPerSm / per_sm - 1024;
+  int st = (int)((budget - fixed) / stage);
   if (st > kMaxStages) st = kMaxStages;
+  if (stages > 0 && stages < st) st = stages;
   if (st < 2) st = 2;
   p.stages = st;
   p.smem = st * stage + fixed;
@@ -372,9 +425,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms) {
   p.bytes_wpart = round_up((int64_t)p.S1 * nc * p.ldw * 4, 256);
   p.off_ws = p.off_wpart + p.bytes_wpart;
   p.bytes_ws = round_up((int64_t)p.BN * p.ldw * 2, 256);
-  p.off_cnt = p.off_ws + p.bytes_ws;
-  p.bytes_cnt = round_up((int64_t)mt1 * 4, 256);
-  p.total = p.off_cnt + p.bytes_cnt;
+  p.total = p.off_ws + p.bytes_ws;
   return p;
 }
 
@@ -393,11 +444,8 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
                             double beta, const double* alpha, double* dots, int* nparts,
                             char* ws, int* err, unsigned flags, cudaStream_t st) {
   const int sms = num_sms();
-  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms);
+  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages);
   const bool presplit = (flags & kApplyPresplit) != 0;
-  if (flags & kApplyZeroCounters) {
-    if (cudaMemsetAsync(ws + p.off_cnt, 0, p.bytes_cnt, st) != cudaSuccess) return 2;
-  }
   __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
   float* Wp = (float*)(ws + p.off_wpart);
   __nv_bfloat16* Ws = (__nv_bfloat16*)(ws + p.off_ws);
@@ -409,9 +457,16 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
     split_block_kernel<NT><<<g, 256, 0, st>>>(X, ld, op.D, p.ld, nc, p.BN, Xs);
   }
   CUtensorMap mPhi1, mXs, mPhi2, mWs;
-  if (!make_map(&mPhi1, op.phi, op.D, op.N, op.ld, kTileM)) return 1;
+  const int64_t nkd = packed_tiles_k(op.D);
+  if (op.packed) {
+    const uint64_t rows = (uint64_t)packed_tiles_m(op.N) * nkd * kTileM;
+    if (!make_map(&mPhi1, op.packed, 64, rows, 64, kTileM)) return 1;
+    if (!make_map(&mPhi2, op.packed, 64, rows, 64, 64)) return 1;
+  } else {
+    if (!make_map(&mPhi1, op.phi, op.D, op.N, op.ld, kTileM)) return 1;
+    if (!make_map(&mPhi2, op.phi, op.D, op.N, op.ld, 64)) return 1;
+  }
   if (!make_map(&mXs, Xs, op.D, p.BN, p.ld, p.BN)) return 1;
-  if (!make_map(&mPhi2, op.phi, op.D, op.N, op.ld, 64)) return 1;
   if (!make_map(&mWs, Ws, op.N, p.BN, p.ldw, p.BN)) return 1;
 
   TcArgs a1 = {};
@@ -422,14 +477,20 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.BN = p.BN;
   a1.stages = p.stages;
   a1.tmem_cols = p.tmem_cols;
+  a1.res_d = op.l2_resident_cols;
+  a1.packed = (const __nv_bfloat16*)op.packed;
+  a1.nkd = nkd;
   a1.wpart = Wp;
   a1.ldw = p.ldw;
   a1.split_stride = (int64_t)nc * p.ldw;
-  a1.tile_counter = (unsigned int*)(ws + p.off_cnt);
-  a1.ws_out = Ws;
   a1.err = err;
   dim3 g1((unsigned)((op.N + kTileM - 1) / kTileM), p.S1);
   if (launch_tc<0, NT>(g1, p.smem, mPhi1, mXs, a1, st) != cudaSuccess) return 2;
+  {
+    int64_t need = (p.ldw + 255) / 256;
+    dim3 g((unsigned)(need < 128 ? need : 128), p.BN / 16);
+    reduce_split_kernel<NT><<<g, 256, 0, st>>>(Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, Ws);
+  }
 
 
   TcArgs a2 = {};
@@ -440,6 +501,9 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.BN = p.BN;
   a2.stages = p.stages;
   a2.tmem_cols = p.tmem_cols;
+  a2.res_d = op.l2_resident_cols;
+  a2.packed = (const __nv_bfloat16*)op.packed;
+  a2.nkd = nkd;
   a2.y = Y;
   a2.x = X;
   a2.ld = ld;

@@ -50,7 +50,8 @@ APPLY_CASES = [
 
 
 @pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
-@pytest.mark.parametrize("kind", ["f64", "f32", "bf16", "bf16-t2", "bf16-t1", "bf16-simt"])
+@pytest.mark.parametrize("kind", ["f64", "f32", "bf16", "bf16-t2", "bf16-t1", "bf16-simt",
+                                  "bf16-packed"])
 def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
     rng = np.random.default_rng(ncols)
@@ -72,12 +73,17 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
         vdt, vec, pdt = torch.float32, B.COFEM_F32, B.COFEM_BF16
         # FP32 split into 3 / 2 / 1 BF16 terms (24 / 16 / 8-bit mantissas)
-        terms = {"bf16": 3, "bf16-t2": 2, "bf16-t1": 1, "bf16-simt": 0}[kind]
+        terms = {"bf16": 3, "bf16-t2": 2, "bf16-t1": 1, "bf16-simt": 0, "bf16-packed": 3}[kind]
         tol = {3: 2e-5, 2: 6e-5, 1: 8e-3, 0: 2e-5}[terms]
     X_in = X.astype(np.float32).astype(np.float64) if vdt == torch.float32 else X
     op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
     if pdt == B.COFEM_BF16:
         B.cofem_op_dense_set_terms(op, terms)
+    packed = None
+    if kind == "bf16-packed":
+        nb = B.cofem_dense_packed_bytes(N, D)
+        packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        B.cofem_op_dense_attach_packed(op, packed.data_ptr(), nb)
     try:
         Xb, ld = to_block(X_in, vdt)
         Yb = torch.full_like(Xb, 3.0)
@@ -141,7 +147,8 @@ def test_diag_mstep(cuda_lib, K, D):
         assert c[1] == int(np.sum(a < 1e6))
 
 
-def test_op_apply_tensor_core_full_size(cuda_lib):
+@pytest.mark.parametrize("packed", [False, True])
+def test_op_apply_tensor_core_full_size(cuda_lib, packed):
     # the bench workload's operator (N=4096, D=32768, 33 columns, BF16 Phi,
     # 3-term split) on sampled output rows computed one by one by the oracle
     N, D, ncols = 4096, 32768, 33
@@ -153,6 +160,10 @@ def test_op_apply_tensor_core_full_size(cuda_lib):
     alpha = rng.uniform(0.5, 1e6, D)
     beta = 1e4
     op = B.cofem_op_dense(N, D, B.COFEM_BF16, Phi_t.data_ptr(), ld_phi)
+    if packed:
+        nb = B.cofem_dense_packed_bytes(N, D)
+        pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        B.cofem_op_dense_attach_packed(op, pk.data_ptr(), nb)
     try:
         Xb, ld = to_block(X, torch.float32)
         Yb = torch.empty_like(Xb)
@@ -168,5 +179,35 @@ def test_op_apply_tensor_core_full_size(cuda_lib):
         got = Yb[:, rows].T.double().cpu().numpy()
         for j in range(ncols):
             assert rel_l2(got[:, j], ref[:, j]) <= 2e-5, j
+    finally:
+        B.cofem_op_destroy(op)
+
+
+def test_autotuner_keeps_results_correct(cuda_lib):
+    N, D, ncols = 1000, 5000, 21
+    prob = datagen.dense_problem(N, D, 50, 0.01, seed=4)
+    _, Phi_ref = bf16_round(prob.Phi)
+    Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
+    op = B.cofem_op_dense(N, D, B.COFEM_BF16, Phi_t.data_ptr(), ld_phi)
+    try:
+        nb = B.cofem_op_dense_autotune_workspace_bytes(op, ncols)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        st, cps, us = B.cofem_op_dense_autotune(op, ncols, ws.data_ptr(), nb)
+        assert 2 <= st <= 8 and cps in (1, 2) and us > 0
+        rng = np.random.default_rng(0)
+        X = rng.standard_normal((D, ncols)).astype(np.float32).astype(np.float64)
+        alpha = rng.uniform(1, 10, D)
+        Xb, ld = to_block(X, torch.float32)
+        Yb = torch.empty_like(Xb)
+        al = torch.from_numpy(alpha).cuda()
+        wsa = _ws(op, B.COFEM_F32, ncols)
+        B.cofem_op_apply(op, B.COFEM_F32, Xb.data_ptr(), ld, ncols, al.data_ptr(), 1e4,
+                         Yb.data_ptr(), wsa.data_ptr(), wsa.numel())
+        torch.cuda.synchronize()
+        phi, phit, _ = sbl.dense_dictionary(Phi_ref)
+        ref = sbl.apply_A(phi, phit, 1e4, alpha, X)
+        got = from_block(Yb, D)
+        for j in range(ncols):
+            assert rel_l2(got[:, j], ref[:, j]) <= 2e-5
     finally:
         B.cofem_op_destroy(op)

@@ -267,14 +267,14 @@ def main():
     cg = res.stats["cg_iters"]
 
     if args.phi == "bf16" and args.terms > 0:
-        # tensor cores: 2 GEMMs per apply (P's split comes from the CG kernels;
-        # an apply to x adds a split kernel)
-        per_iter, per_rep = 2 + 2, 3 + 1
-        apply_kernels = "split + GEMM1 (tcgen05) + GEMM2 (tcgen05)"
+        # tensor cores: GEMM1, reduce/split, GEMM2 per apply (P's split comes
+        # from the CG kernels; an apply to x adds a split kernel)
+        per_iter, per_rep = 3 + 2, 4 + 1
     else:
         per_iter, per_rep = 4 + 2, 4 + 1
-        apply_kernels = "GEMM1 + reduce + GEMM2 + epilogue (CUDA cores)"
-    # dominant kernel: the operator application over K+1 columns, timed alone
+    launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep) for c in cg)
+    # dominant kernel: the operator application over K+1 columns, each of its
+    # kernels timed with CUDA events on the launching stream
     ncols = CFG["K"] + 1
     D, N = CFG["D"], CFG["N"]
     ld = (D + 63) // 64 * 64
@@ -286,31 +286,55 @@ def main():
         B.cofem_op_apply(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols, alpha.data_ptr(),
                          prob.beta, Yb.data_ptr(), wsa.data_ptr(), nbytes, st.cuda_stream)
     reps = 20
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(st)
+    per = []
     for _ in range(reps):
-        B.cofem_op_apply(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols, alpha.data_ptr(),
-                         prob.beta, Yb.data_ptr(), wsa.data_ptr(), nbytes, st.cuda_stream)
-    a1.record(st)
-    torch.cuda.synchronize()
-    apply_s = a0.elapsed_time(a1) / 1e3 / reps
-    phi_bytes = N * D * (2 if args.phi == "bf16" else 4)
-    alg_bytes = 2 * phi_bytes + 3 * D * ncols * 4 + 8 * D      # Phi twice; X, Y, alpha
+        per.append(B.cofem_op_apply_timed(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols,
+                                          alpha.data_ptr(), prob.beta, Yb.data_ptr(),
+                                          wsa.data_ptr(), nbytes, st.cuda_stream))
+    kern_ms = [float(np.mean([p_[i] for p_ in per])) for i in range(len(per[0]))]
+    apply_s = sum(kern_ms) / 1e3
+    esz = 2 if args.phi == "bf16" else 4
+    phi_bytes = N * D * esz
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg_bytes / apply_s / 1e9
+    if args.phi == "bf16" and args.terms > 0:
+        names = ["split", "gemm1 (Phi X, tcgen05)", "reduce+split", "gemm2 (Phi^T W, tcgen05)"]
+        g = 16 // args.terms
+        BN = -(-ncols // g) * 16
+        # algorithmic bytes of the second product: Phi, W's BF16 terms, X and
+        # alpha read, Y written
+        kbytes = {3: phi_bytes + BN * N * 2 + 2 * ncols * D * 4 + 8 * D,
+                  1: phi_bytes + BN * D * 2 + ncols * N * 4}
+        dom = 3
+        kname = "dense_tc_kernel<1,%d> (second product Phi^T W + alpha.X, %d cols)" % (args.terms, ncols)
+    else:
+        names = ["gemm1", "reduce", "gemm2", "epilogue"]
+        kbytes = {2: phi_bytes + ncols * N * 4 + ncols * D * 4}
+        dom = 2
+        kname = "tsgemm_kernel (second product, CUDA cores, %d cols)" % ncols
+    dom_s = kern_ms[dom] / 1e3
+    achieved = kbytes[dom] / dom_s / 1e9
+    op_bytes = 2 * phi_bytes + 3 * D * ncols * 4 + 8 * D
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "dense_tc_gemm2_n4096_d32768.md")
+    if args.phi == "bf16" and args.terms == 3 and os.path.exists(prof):
+        import hashlib
+        src = os.path.join(ROOT, "paper_2202_12808_gb300", "csrc", "dense_tc.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        meta = dict(l.split(":", 1) for l in open(prof) if l.startswith(("source_sha1:", "traffic_bytes_per_launch:")))
+        if meta.get("source_sha1", "").strip() == sha:
+            traffic = int(meta["traffic_bytes_per_launch"].strip())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "dense operator apply (Phi^T(Phi X) + alpha.X, %d cols): %s"
-                          % (ncols, apply_kernels),
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-
-    launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep) for c in cg)
-
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                "algorithmic_bytes": kbytes[dom], "launch_us": kern_ms[dom] * 1e3,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "kernels_us": {n: round(v * 1e3, 2) for n, v in zip(names, kern_ms)},
+                "operator_apply": {"us": apply_s * 1e6, "algorithmic_bytes": op_bytes,
+                                   "achieved_gbs": op_bytes / apply_s / 1e9}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors, %s Phi" % args.phi,

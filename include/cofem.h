@@ -232,6 +232,17 @@ cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec,
                             void* workspace_dev, size_t workspace_bytes,
                             void* stream);
 
+/* cofem_op_apply with per-kernel timing (diagnostics): CUDA events recorded
+ * on `stream` before the application and after each of its kernels; on
+ * return kernel_ms[i] (i < *n_kernels <= max_kernels <= 16) holds the
+ * elapsed milliseconds of the i-th kernel in launch order (tensor cores:
+ * split, first product, reduce/split, second product).  Synchronous. */
+cofem_status cofem_op_apply_timed(const cofem_op* op, cofem_dtype vec, const void* x_dev,
+                                  int64_t ld, int32_t ncols, const double* alpha_dev,
+                                  double beta, void* y_dev, void* workspace_dev,
+                                  size_t workspace_bytes, void* stream, float* kernel_ms,
+                                  int32_t max_kernels, int32_t* n_kernels);
+
 /* cofem_op_apply without a workspace argument, for callers that may not
  * allocate device memory (for example a plugin inside an application that
  * owns the whole device memory pool, or a loop that must not synchronise on

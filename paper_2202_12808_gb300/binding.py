@@ -75,6 +75,8 @@ _SIGS = {
     "cofem_probe_fill": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _P]),
     "cofem_apply_workspace_bytes": (_S, [_P, _S, _I32, ctypes.POINTER(_SZ)]),
     "cofem_op_apply": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P, _SZ, _P]),
+    "cofem_op_apply_timed": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P, _SZ, _P,
+                                  ctypes.POINTER(ctypes.c_float), _I32, ctypes.POINTER(_I32)]),
     "cofem_op_apply_noalloc": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P]),
     "cofem_noalloc_scratch_capacity": (_SZ, []),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
@@ -225,6 +227,17 @@ def cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr, ws
                    stream=0):
     _check(lib().cofem_op_apply(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr,
                                 ws_bytes, stream), "cofem_op_apply")
+
+
+def cofem_op_apply_timed(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr, ws_bytes,
+                         stream=0, max_kernels=8):
+    """Runs cofem_op_apply and returns the per-kernel milliseconds."""
+    ms = (ctypes.c_float * max_kernels)()
+    n = _I32()
+    _check(lib().cofem_op_apply_timed(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, ws_ptr,
+                                      ws_bytes, stream, ms, max_kernels, ctypes.byref(n)),
+           "cofem_op_apply_timed")
+    return list(ms)[:n.value]
 
 
 def cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, stream=0):

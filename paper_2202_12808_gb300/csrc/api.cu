@@ -60,12 +60,16 @@ int num_sms() {
 }
 
 __global__ void ctl_init_kernel(CgCtl* ctl, long long t0) {
+  pdl_wait();
+  pdl_trigger();
   ctl->t = t0;
   ctl->em_index = 0;
   ctl->error = 0;
 }
 
 __global__ void fill_double_kernel(double* x, int64_t n, double v) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = v;
@@ -413,11 +417,10 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
                              double* s, double* alpha, cofem_stats* stats, cudaStream_t st) {
   const int64_t D = op_D(op), N = op_N(op);
   CK(cudaMemsetAsync(ws, 0, L.total, st));
-  ctl_init_kernel<<<1, 1, 0, st>>>((CgCtl*)(ws + L.ctl), p->t_offset + 1);
+  launch_k(ctl_init_kernel, dim3(1), dim3(1), 0, st, (CgCtl*)(ws + L.ctl), p->t_offset + 1);
   CKL();
   if (p->t_offset == 0) {
-    fill_double_kernel<<<(unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096), 256, 0, st>>>(
-        alpha, D, p->alpha_init);
+    launch_k(fill_double_kernel, dim3((unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096)), dim3(256), 0, st, alpha, D, p->alpha_init);
     CKL();
   }
   // b = beta Phi^T y  (once per fit: y and beta do not change)
@@ -656,6 +659,30 @@ cofem_status cofem_op_apply(const cofem_op* op, cofem_dtype vec, const void* x_d
                   (char*)workspace_dev, (cudaStream_t)stream);
 }
 
+cofem_status cofem_op_apply_timed(const cofem_op* op, cofem_dtype vec, const void* x_dev,
+                                  int64_t ld, int32_t ncols, const double* alpha_dev,
+                                  double beta, void* y_dev, void* workspace_dev,
+                                  size_t workspace_bytes, void* stream, float* kernel_ms,
+                                  int32_t max_kernels, int32_t* n_kernels) {
+  if (!kernel_ms || !n_kernels || max_kernels < 1 || max_kernels > 16)
+    return COFEM_ERR_INVALID_ARG;
+  cudaEvent_t ev[17];
+  for (int i = 0; i <= max_kernels; ++i) CK(cudaEventCreate(&ev[i]));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEventRecord(ev[0], st);
+  apply_ticks_arm(ev + 1, max_kernels);
+  cofem_status rc = cofem_op_apply(op, vec, x_dev, ld, ncols, alpha_dev, beta, y_dev,
+                                   workspace_dev, workspace_bytes, stream);
+  const int n = apply_ticks_disarm();
+  if (rc == COFEM_OK) {
+    if (cudaEventSynchronize(ev[n]) != cudaSuccess) rc = COFEM_ERR_CUDA;
+    for (int i = 0; i < n && rc == COFEM_OK; ++i) cudaEventElapsedTime(&kernel_ms[i], ev[i], ev[i + 1]);
+    *n_kernels = n;
+  }
+  for (int i = 0; i <= max_kernels; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
 cofem_status cofem_op_forward(const cofem_op* op, cofem_dtype vec, const void* z_dev, int64_t ldz,
                               int32_t ncols, void* w_dev, int64_t ldw, void* workspace_dev,
                               size_t workspace_bytes, void* stream) {
@@ -746,6 +773,8 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 namespace cofem {
 
 __global__ void tune_fill_kernel(float* x, int64_t n, double* alpha, int64_t D) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (float)((mix64((uint64_t)i) >> 40) * (1.0 / 16777216.0) - 0.5);
@@ -786,7 +815,7 @@ extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, voi
   double* alpha = (double*)(ws + ows + 2 * blk);
   const int64_t ld = round_up(op->dense.D, kLdAlign);
   cudaStream_t st = (cudaStream_t)stream;
-  tune_fill_kernel<<<1024, 256, 0, st>>>(X, (int64_t)ncols * ld, alpha, op->dense.D);
+  launch_k(tune_fill_kernel, dim3(1024), dim3(256), 0, st, X, (int64_t)ncols * ld, alpha, op->dense.D);
   CKL();
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

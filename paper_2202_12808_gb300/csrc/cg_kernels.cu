@@ -97,6 +97,8 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
 
 template <typename V>
 __global__ void probe_fill_kernel(uint64_t key, int K, int64_t D, V* out, int64_t ld) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.y;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < ld;
        d += (int64_t)gridDim.x * blockDim.x) {
@@ -114,6 +116,8 @@ __global__ void probe_fill_kernel(uint64_t key, int K, int64_t D, V* out, int64_
 template <typename V>
 __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                                const V* bvec, double* part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[32];
   const int j = blockIdx.y;
   const uint64_t key = probe_key(cf.seed, ctl->t);
@@ -173,6 +177,8 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
 template <typename V>
 __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
                                  const V* P, const V* Q, const double* gparts, double* part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[32];
   __shared__ double a_sh;
   constexpr int W = 16 / sizeof(V);
@@ -240,6 +246,8 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
 template <typename V>
 __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
                                      const V* Q, const V* bvec, double* part) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[32];
   if (!ctl->replace) return;
   const int j = blockIdx.y;
@@ -277,6 +285,8 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
 template <typename V>
 __global__ void cg_direction_kernel(CgConf cf, const CgCtl* ctl, const CgScalars* sc,
                                     const V* R, V* P) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int W = 16 / sizeof(V);
   if (ctl->done) return;
   const int j = blockIdx.y;
@@ -303,6 +313,8 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
                                   double* mu, double* s, double* alpha, int32_t* counts,
                                   int32_t* st_iters, double* st_relres, int32_t* st_clamps,
                                   int32_t* st_support) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[32];
   const uint64_t key = ctl ? probe_key(cf.seed, ctl->t) : key_in;
   const int K = cf.K;
@@ -359,6 +371,8 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
 
 template <typename V>
 __global__ void scale_kernel(V* x, int64_t n, double beta) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (V)((double)x[i] * beta);
@@ -379,35 +393,35 @@ template <typename V>
 void launch_probe_fill(uint64_t key, int K, int64_t D, V* out, int64_t ld, cudaStream_t st) {
   const int sms = num_sms();
   dim3 g(vec_blocks(ld, 1, K, sms), K);
-  probe_fill_kernel<V><<<g, 256, 0, st>>>(key, K, D, out, ld);
+  launch_k(probe_fill_kernel<V>, dim3(g), dim3(256), 0, st, key, K, D, out, ld);
 }
 
 template <typename V>
 void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                     const V* bvec, double* part, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
-  cg_init_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, bvec, part);
+  launch_k(cg_init_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, bvec, part);
 }
 
 template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
                       const V* Q, const double* gparts, double* part, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
-  cg_update_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, X, R, P, Q, gparts, part);
+  launch_k(cg_update_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts, part);
 }
 
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
                           const V* bvec, double* part, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
-  cg_true_resid_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, R, Q, bvec, part);
+  launch_k(cg_true_resid_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, R, Q, bvec, part);
 }
 
 template <typename V>
 void launch_cg_direction(const CgConf& cf, const CgCtl* ctl, const CgScalars* sc,
                          const V* R, V* P, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
-  cg_direction_kernel<V><<<g, 256, 0, st>>>(cf, ctl, sc, R, P);
+  launch_k(cg_direction_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, R, P);
 }
 
 template <typename V>
@@ -416,7 +430,7 @@ void launch_diag_mstep(const CgConf& cf, CgCtl* ctl, uint64_t key, const V* X, d
                        double* st_relres, int32_t* st_clamps, int32_t* st_support,
                        cudaStream_t st) {
   int blocks = vec_blocks(cf.ld, 1, 1, num_sms());
-  diag_mstep_kernel<V><<<blocks, 256, 0, st>>>(cf, ctl, key, X, mu, s, alpha, counts,
+  launch_k(diag_mstep_kernel<V>, dim3(blocks), dim3(256), 0, st, cf, ctl, key, X, mu, s, alpha, counts,
                                                st_iters, st_relres, st_clamps, st_support);
 }
 
@@ -425,7 +439,7 @@ void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  scale_kernel<V><<<blocks, 256, 0, st>>>(x, n, beta);
+  launch_k(scale_kernel<V>, dim3(blocks), dim3(256), 0, st, x, n, beta);
 }
 
 #define COFEM_INST(V)                                                                   \

@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/cofem.h"
 
 namespace cofem {
@@ -130,6 +132,33 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __syncthreads();
   if (last) __threadfence();
   return last;
+}
+
+// ------------------------------------------- programmatic dependent launch
+// Every kernel waits for its predecessor's results with pdl_wait() before
+// touching global memory and lets its dependent launch early with
+// pdl_trigger() once its main work is done; launch_k launches with
+// programmatic stream serialization, so in a captured graph the next
+// kernel's blocks are scheduled while this one drains.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace cofem

@@ -29,6 +29,8 @@ template <int T>
 __global__ void __launch_bounds__(kConvThreads)
 conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ Z,
                     int64_t ldz, float* __restrict__ W, int64_t ldw) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float zs[skew(kConvTile + kConvMaxT) + 8];
   const int j = blockIdx.y;
   const int64_t n0 = (int64_t)blockIdx.x * kConvTile;
@@ -80,6 +82,8 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
                     int64_t ldw, float* __restrict__ Y, int64_t ld, double beta,
                     const double* __restrict__ alpha, const float* __restrict__ X,
                     double* dots) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float ws[skew(kConvTile + kConvMaxT) + 8];
   __shared__ double red[32];
   const int j = blockIdx.y;
@@ -152,19 +156,21 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
 void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ldz, int ncols,
                   float* W, int64_t ldw, cudaStream_t st) {
   dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
-  conv_forward_kernel<kConvMaxT><<<g, kConvThreads, 0, st>>>(h64, C, L, Z, ldz, W, ldw);
+  launch_k(conv_forward_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, Z, ldz, W, ldw);
 }
 
 int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
                  float* Y, int64_t ld, double beta, const double* alpha, const float* X,
                  double* dots, cudaStream_t st) {
   dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
-  conv_adjoint_kernel<kConvMaxT><<<g, kConvThreads, 0, st>>>(h64, C, L, W, ldw, Y, ld, beta,
+  launch_k(conv_adjoint_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, W, ldw, Y, ld, beta,
                                                             alpha, X, dots);
   return (int)g.x;
 }
 
 __global__ void pad_filters_kernel(const float* h, int C, int T, float* h64) {
+  pdl_wait();
+  pdl_trigger();
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < C * kConvMaxT;
        i += blockDim.x * gridDim.x) {
     const int c = i / kConvMaxT, t = i % kConvMaxT;
@@ -173,7 +179,7 @@ __global__ void pad_filters_kernel(const float* h, int C, int T, float* h64) {
 }
 
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st) {
-  pad_filters_kernel<<<(C * kConvMaxT + 255) / 256, 256, 0, st>>>(h, C, T, h64);
+  launch_k(pad_filters_kernel, dim3((C * kConvMaxT + 255) / 256), dim3(256), 0, st, h, C, T, h64);
 }
 
 }  // namespace cofem

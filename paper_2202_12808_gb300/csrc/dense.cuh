@@ -33,6 +33,11 @@ inline size_t packed_bytes(int64_t N, int64_t D) {
 void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                      cudaStream_t st);
 
+// Per-kernel event timing of one operator application (diagnostics).
+void apply_ticks_arm(cudaEvent_t* events, int cap);
+int apply_ticks_disarm();
+void apply_tick(cudaStream_t st);
+
 struct DenseSimtPlan {
   int64_t ldw, ld;         // padded N and D
   int S1, S2;              // split-K counts of the two products

@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(256)
 tsgemm_kernel(int64_t M, int64_t Kdim, int ncols, const TA* __restrict__ A, int64_t lda,
               const V* __restrict__ B, int64_t ldb, V* __restrict__ C, int64_t ldc,
               int64_t split_stride, int64_t k_per_split) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int BM = 16 * TM, BN = 16 * TN;
   __shared__ __align__(16) V As[kBK][BM + 4];
   __shared__ __align__(16) V Bs[kBK][BN];
@@ -102,6 +104,8 @@ __global__ void reduce_epilogue_kernel(int64_t M, int64_t ldp, int64_t ldo, int 
                                        double beta, const double* __restrict__ alpha,
                                        const V* __restrict__ X, V* __restrict__ Y,
                                        double* dots) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sh[32];
   const int j = blockIdx.y;
   double acc = 0.0;
@@ -174,10 +178,10 @@ static void launch_tsgemm(int64_t M, int64_t Kdim, int ncols, const TA* A, int64
   const int BM = 16 * TM;
   dim3 g((unsigned)((M + BM - 1) / BM), S);
   switch (pick_tn(ncols)) {
-    case 1: tsgemm_kernel<TA, V, KM, TM, 1><<<g, 256, 0, st>>>(M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
-    case 2: tsgemm_kernel<TA, V, KM, TM, 2><<<g, 256, 0, st>>>(M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
-    case 3: tsgemm_kernel<TA, V, KM, TM, 3><<<g, 256, 0, st>>>(M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
-    default: tsgemm_kernel<TA, V, KM, TM, 4><<<g, 256, 0, st>>>(M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
+    case 1: launch_k(tsgemm_kernel<TA, V, KM, TM, 1>, dim3(g), dim3(256), 0, st, M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
+    case 2: launch_k(tsgemm_kernel<TA, V, KM, TM, 2>, dim3(g), dim3(256), 0, st, M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
+    case 3: launch_k(tsgemm_kernel<TA, V, KM, TM, 3>, dim3(g), dim3(256), 0, st, M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
+    default: launch_k(tsgemm_kernel<TA, V, KM, TM, 4>, dim3(g), dim3(256), 0, st, M, Kdim, ncols, A, lda, B, ldb, C, ldc, sstride, kps); break;
   }
 }
 
@@ -191,9 +195,11 @@ void dense_simt_forward(const DenseDesc& op, const V* Z, int64_t ldz, int ncols,
   const int64_t sstride = (int64_t)ncols * p.ldw;
   launch_tsgemm<TA, V, true>(op.N, op.D, ncols, (const TA*)op.phi, op.ld, Z, ldz, Wp, p.ldw,
                              sstride, p.S1, p.kps1, st);
+  apply_tick(st);
   dim3 g(epi_blocks(ldw, ncols, sms), ncols);
-  reduce_epilogue_kernel<V><<<g, 256, 0, st>>>(op.N, p.ldw, ldw, p.S1, sstride, Wp, 1.0,
+  launch_k(reduce_epilogue_kernel<V>, dim3(g), dim3(256), 0, st, op.N, p.ldw, ldw, p.S1, sstride, Wp, 1.0,
                                                nullptr, nullptr, W, nullptr);
+  apply_tick(st);
 }
 
 // Y = beta Phi^T W [+ alpha . X]  (W: N x ncols, ldw;  X, Y: D x ncols, ld)
@@ -207,9 +213,11 @@ void dense_simt_adjoint(const DenseDesc& op, const V* W, int64_t ldw, int ncols,
   const int64_t sstride = (int64_t)ncols * p.ld;
   launch_tsgemm<TA, V, false>(op.D, op.N, ncols, (const TA*)op.phi, op.ld, W, ldw, Qp, p.ld,
                               sstride, p.S2, p.kps2, st);
+  apply_tick(st);
   dim3 g(epi_blocks(ld, ncols, sms), ncols);
-  reduce_epilogue_kernel<V><<<g, 256, 0, st>>>(op.D, p.ld, ld, p.S2, sstride, Qp, beta, alpha,
+  launch_k(reduce_epilogue_kernel<V>, dim3(g), dim3(256), 0, st, op.D, p.ld, ld, p.S2, sstride, Qp, beta, alpha,
                                                X, Y, dots);
+  apply_tick(st);
   if (nparts) *nparts = dots ? (int)g.x : 0;
 }
 

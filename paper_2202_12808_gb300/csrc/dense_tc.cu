@@ -90,6 +90,8 @@ template <int MODE, int NT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const TcArgs args) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
@@ -276,47 +278,81 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
 // ------------------------------------------------------ split kernels
 
-// Xs[row * lds + d] = BF16 term t of X[j*ld + d] for row = split_row(j, t);
-// rows of no (j < nc, t) are zero.  Grid (blocks, BN).
+// Xs[split_row(j, t) * lds + d] = BF16 term t of X[j*ld + d]; rows of no
+// (j < nc, t) are zero.  Grid (blocks, ngroups * G): one column slot j per
+// blockIdx.y, four consecutive d per thread, one 8-byte store per term.
 template <int NT>
 __global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int64_t D,
-                                   int64_t lds, int nc, int BN, __nv_bfloat16* __restrict__ Xs) {
+                                   int64_t lds, int nc, __nv_bfloat16* __restrict__ Xs) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int G = TermGroup<NT>::G;
-  const int r = blockIdx.y;
-  const int jj = (r % 16) / NT, t = (r % 16) % NT;
-  const int j = (r / 16) * G + jj;
-  const bool used = jj < G && j < nc;
-  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < lds;
-       d += (int64_t)gridDim.x * blockDim.x) {
-    __nv_bfloat16 o[NT];
-    split_terms<NT>(used && d < D ? X[(int64_t)j * ld + d] : 0.f, o);
-    Xs[(int64_t)r * lds + d] = o[t];
+  const int j = blockIdx.y;
+  const int gi = j / G, jj = j % G;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; d < lds;
+       d += (int64_t)gridDim.x * blockDim.x * 4) {
+    float r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = (j < nc && d + i < D) ? X[(int64_t)j * ld + d + i] : 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      __nv_bfloat16 o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o[i] = __float2bfloat16_rn(r[i]);
+        r[i] -= __bfloat162float(o[i]);
+      }
+      *reinterpret_cast<uint2*>(Xs + (int64_t)(gi * 16 + jj * NT + t) * lds + d) =
+          *reinterpret_cast<uint2*>(o);
+    }
+    if (jj == G - 1) {     // rows of the group left over by G * NT < 16
+      for (int rr = G * NT; rr < 16; ++rr)
+        *reinterpret_cast<uint2*>(Xs + (int64_t)(gi * 16 + rr) * lds + d) = make_uint2(0u, 0u);
+    }
   }
 }
 
 // W[j][n] = sum_s Wpart[s][j][n] (split order) -> BF16 terms of W in rows
 // split_row(j, t) of Ws; rows of no (j < nc, t) and n >= N are zero.
-// Grid (blocks, BN / 16 groups).
+// Grid (blocks, ngroups * G): one column slot per blockIdx.y, four
+// consecutive n per thread (16-byte loads, 8-byte stores per term).
 template <int NT>
 __global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t sstride,
                                     int64_t N, int64_t ldw, int nc,
                                     __nv_bfloat16* __restrict__ Ws) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int G = TermGroup<NT>::G;
-  const int gi = blockIdx.y;
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ldw;
-       n += (int64_t)gridDim.x * blockDim.x) {
+  const int j = blockIdx.y;
+  const int gi = j / G, jj = j % G;
+  for (int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; n < ldw;
+       n += (int64_t)gridDim.x * blockDim.x * 4) {
+    float r[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j < nc) {
+      for (int s = 0; s < S; ++s) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(Wp + (int64_t)s * sstride +
+                                                                (int64_t)j * ldw + n));
+        r[0] += v.x; r[1] += v.y; r[2] += v.z; r[3] += v.w;
+      }
 #pragma unroll
-    for (int jj = 0; jj < G; ++jj) {
-      const int j = gi * G + jj;
-      float w = 0.f;
-      if (j < nc && n < N)
-        for (int s = 0; s < S; ++s) w += Wp[(int64_t)s * sstride + (int64_t)j * ldw + n];
-      __nv_bfloat16 o[NT];
-      split_terms<NT>(w, o);
-#pragma unroll
-      for (int t = 0; t < NT; ++t) Ws[(int64_t)(gi * 16 + jj * NT + t) * ldw + n] = o[t];
+      for (int i = 0; i < 4; ++i)
+        if (n + i >= N) r[i] = 0.f;
     }
-    for (int r = G * NT; r < 16; ++r) Ws[(int64_t)(gi * 16 + r) * ldw + n] = __float2bfloat16_rn(0.f);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      __nv_bfloat16 o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o[i] = __float2bfloat16_rn(r[i]);
+        r[i] -= __bfloat162float(o[i]);
+      }
+      *reinterpret_cast<uint2*>(Ws + (int64_t)(gi * 16 + jj * NT + t) * ldw + n) =
+          *reinterpret_cast<uint2*>(o);
+    }
+    if (jj == G - 1) {
+      for (int rr = G * NT; rr < 16; ++rr)
+        *reinterpret_cast<uint2*>(Ws + (int64_t)(gi * 16 + rr) * ldw + n) = make_uint2(0u, 0u);
+    }
   }
 }
 
@@ -327,6 +363,8 @@ __global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t
 __global__ void pack_kernel(const __nv_bfloat16* __restrict__ phi, int64_t N, int64_t D,
                             int64_t ld, int64_t nkd, int64_t total8,
                             __nv_bfloat16* __restrict__ packed) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total8;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = i * 8;                 // destination element of the chunk
@@ -348,11 +386,30 @@ void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* pa
                      cudaStream_t st) {
   const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
   const int64_t blocks = (total8 + 255) / 256;
-  pack_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, st>>>(
-      (const __nv_bfloat16*)phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
+  launch_k(pack_kernel, dim3((unsigned)(blocks < 65535 ? blocks : 65535)), dim3(256), 0, st, (const __nv_bfloat16*)phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
 }
 
 // ----------------------------------------------------------- host side
+
+// Optional per-kernel timing of one operator application (cofem_op_apply_timed):
+// when armed, every launch site records an event after its kernel.
+static thread_local cudaEvent_t* g_tick_events = nullptr;
+static thread_local int g_tick_count = 0, g_tick_cap = 0;
+void apply_ticks_arm(cudaEvent_t* events, int cap) {
+  g_tick_events = events;
+  g_tick_cap = cap;
+  g_tick_count = 0;
+}
+int apply_ticks_disarm() {
+  const int n = g_tick_count;
+  g_tick_events = nullptr;
+  g_tick_cap = 0;
+  g_tick_count = 0;
+  return n;
+}
+void apply_tick(cudaStream_t st) {
+  if (g_tick_events && g_tick_count < g_tick_cap) cudaEventRecord(g_tick_events[g_tick_count++], st);
+}
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -435,7 +492,7 @@ static cudaError_t launch_tc(dim3 grid, size_t smem, const CUtensorMap& a, const
   auto k = dense_tc_kernel<MODE, NT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, kTcThreads, smem, st>>>(a, b, args);
+  launch_k(k, dim3(grid), dim3(kTcThreads), smem, st, a, b, args);
   return cudaGetLastError();
 }
 
@@ -453,8 +510,10 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   // (skipped when the caller's kernels already wrote Xs)
   if (!presplit) {
     int64_t need = (p.ld + 255) / 256;
-    dim3 g((unsigned)(need < 128 ? need : 128), p.BN);
-    split_block_kernel<NT><<<g, 256, 0, st>>>(X, ld, op.D, p.ld, nc, p.BN, Xs);
+    const int64_t need4 = (p.ld / 4 + 255) / 256;
+    dim3 g((unsigned)(need4 < 64 ? need4 : 64), (p.BN / 16) * TermGroup<NT>::G);
+    launch_k(split_block_kernel<NT>, dim3(g), dim3(256), 0, st, X, ld, op.D, p.ld, nc, Xs);
+    apply_tick(st);
   }
   CUtensorMap mPhi1, mXs, mPhi2, mWs;
   const int64_t nkd = packed_tiles_k(op.D);
@@ -486,10 +545,12 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.err = err;
   dim3 g1((unsigned)((op.N + kTileM - 1) / kTileM), p.S1);
   if (launch_tc<0, NT>(g1, p.smem, mPhi1, mXs, a1, st) != cudaSuccess) return 2;
+  apply_tick(st);
   {
-    int64_t need = (p.ldw + 255) / 256;
-    dim3 g((unsigned)(need < 128 ? need : 128), p.BN / 16);
-    reduce_split_kernel<NT><<<g, 256, 0, st>>>(Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, Ws);
+    const int64_t need4 = (p.ldw / 4 + 127) / 128;
+    dim3 g((unsigned)(need4 < 64 ? need4 : 64), (p.BN / 16) * TermGroup<NT>::G);
+    launch_k(reduce_split_kernel<NT>, dim3(g), dim3(128), 0, st, Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, Ws);
+    apply_tick(st);
   }
 
 
@@ -513,6 +574,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.err = err;
   dim3 g2((unsigned)((op.D + kTileM - 1) / kTileM), 1);
   if (launch_tc<1, NT>(g2, p.smem, mPhi2, mWs, a2, st) != cudaSuccess) return 2;
+  apply_tick(st);
   if (nparts) *nparts = dots ? (int)g2.x : 0;
   return 0;
 }

@@ -204,6 +204,39 @@ cofem_status cofem_fit(const cofem_op* op, const void* y_dev, double beta,
                        double* alpha_dev, cofem_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Many independent problems in one fit (each its own Algorithm 1).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t N, D;          /* dictionary shape */
+  const void* phi_dev;   /* BF16, N x D row-major, leading dimension ld (multiple
+                            of 64), 256-byte aligned */
+  int64_t ld;
+  const void* y_dev;     /* N floats */
+  double beta;           /* noise precision */
+  uint64_t seed;         /* this problem's probe seed */
+} cofem_problem;
+
+/* Workspace of cofem_fit_batched: about the packed dictionaries (2 N D
+ * bytes each) plus 4 (K+1) D floats of CG state per problem. */
+cofem_status cofem_batched_workspace_bytes(int32_t n, const cofem_problem* problems,
+                                           const cofem_params* p, size_t* bytes);
+
+/* Algorithm 1 for n problems at once: every problem keeps its own
+ * column-wise CG (own step sizes, own stop test ||R||_F/||B||_F < cg_tol,
+ * own probes from its seed), the problems sharing each kernel launch; a
+ * problem whose CG has stopped costs nothing until the next EM iteration.
+ * FP32 vectors (p->vec_dtype must be COFEM_F32), BF16 dictionaries on the
+ * tensor cores (3-term split); no residual replacement (must be 0).
+ * mu_dev, s_dev, alpha_dev: sum_i D_i doubles each, problem i at offset
+ * sum_{k<i} D_k (alpha_dev is read as the starting alpha when
+ * t_offset > 0).  stats (optional): host arrays of n * em_iters values,
+ * problem-major.  Synchronous. */
+cofem_status cofem_fit_batched(int32_t n, const cofem_problem* problems,
+                               const cofem_params* p, void* workspace_dev,
+                               size_t workspace_bytes, double* mu_dev, double* s_dev,
+                               double* alpha_dev, cofem_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
  * Individual hot-path steps (each is one of the kernels cofem_fit runs).
  * ------------------------------------------------------------------------ */
 

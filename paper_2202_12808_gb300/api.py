@@ -118,3 +118,34 @@ def apply(op, X, alpha, beta, vec_dtype=None, stream=None):
     B.cofem_op_apply(op.handle, vec, Xb.data_ptr(), ld, ncols, alpha.data_ptr(), float(beta),
                      Yb.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     return Yb[:, :D].T
+
+
+def fit_batched(phis, ys, betas, seeds, p, ws=None, stream=None):
+    """Algorithm 1 for many problems at once (BF16 dictionaries).  phis: list
+    of CUDA bfloat16 (N_i x D_i) tensors; ys: CUDA float32 (N_i); returns
+    (alphas, mus, ss, stats) with per-problem tensors."""
+    probs, keep = [], []
+    for Phi, y, beta, seed in zip(phis, ys, betas, seeds):
+        N, D = Phi.shape
+        ld = _ld(D)
+        if Phi.stride() != (ld, 1) or Phi.dtype != torch.bfloat16:
+            buf = torch.zeros((N, ld), dtype=torch.bfloat16, device=Phi.device)
+            buf[:, :D] = Phi
+            Phi = buf
+        y = y.to(torch.float32).contiguous()
+        keep += [Phi, y]
+        probs.append(B.cofem_problem(N, D, Phi.data_ptr(), ld, y.data_ptr(), float(beta), int(seed)))
+    dev = phis[0].device
+    if ws is None:
+        ws = torch.empty(B.cofem_batched_workspace_bytes(probs, p), dtype=torch.uint8, device=dev)
+    dtot = sum(int(P.shape[1]) for P in phis)
+    mu = torch.empty(dtot, dtype=torch.float64, device=dev)
+    s = torch.empty_like(mu)
+    alpha = torch.empty_like(mu)
+    stats = B.cofem_fit_batched(probs, p, ws.data_ptr(), ws.numel(), mu.data_ptr(), s.data_ptr(),
+                                alpha.data_ptr(), _stream_ptr(stream))
+    offs = [0]
+    for P in phis:
+        offs.append(offs[-1] + int(P.shape[1]))
+    cut = lambda t: [t[offs[i]:offs[i + 1]] for i in range(len(phis))]
+    return cut(alpha), cut(mu), cut(s), stats

@@ -46,6 +46,12 @@ class cofem_stats(ctypes.Structure):
                 ("support", ctypes.POINTER(ctypes.c_int32))]
 
 
+class cofem_problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("D", ctypes.c_int64), ("phi_dev", ctypes.c_void_p),
+                ("ld", ctypes.c_int64), ("y_dev", ctypes.c_void_p), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
 _S = ctypes.c_int
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -72,6 +78,10 @@ _SIGS = {
     "cofem_workspace_bytes": (_S, [_P, ctypes.POINTER(cofem_params), ctypes.POINTER(_SZ)]),
     "cofem_fit": (_S, [_P, _P, _D, ctypes.POINTER(cofem_params), _P, _SZ, _P, _P, _P,
                        ctypes.POINTER(cofem_stats), _P]),
+    "cofem_batched_workspace_bytes": (_S, [_I32, ctypes.POINTER(cofem_problem),
+                                           ctypes.POINTER(cofem_params), ctypes.POINTER(_SZ)]),
+    "cofem_fit_batched": (_S, [_I32, ctypes.POINTER(cofem_problem), ctypes.POINTER(cofem_params),
+                               _P, _SZ, _P, _P, _P, ctypes.POINTER(cofem_stats), _P]),
     "cofem_probe_fill": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _P]),
     "cofem_apply_workspace_bytes": (_S, [_P, _S, _I32, ctypes.POINTER(_SZ)]),
     "cofem_op_apply": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P, _SZ, _P]),
@@ -210,6 +220,34 @@ def cofem_fit(op, y_ptr, beta, params, ws_ptr, ws_bytes, mu_ptr, s_ptr, alpha_pt
     m = params.em_iters
     return {"cg_iters": list(it)[:m], "relres": list(rr)[:m], "clamps": list(cl)[:m],
             "support": list(sp)[:m]}
+
+
+def cofem_batched_workspace_bytes(problems, params):
+    arr = (cofem_problem * len(problems))(*problems)
+    n = _SZ()
+    _check(lib().cofem_batched_workspace_bytes(len(problems), arr, ctypes.byref(params),
+                                               ctypes.byref(n)), "cofem_batched_workspace_bytes")
+    return n.value
+
+
+def cofem_fit_batched(problems, params, ws_ptr, ws_bytes, mu_ptr, s_ptr, alpha_ptr, stream=0):
+    """Returns per-problem statistics (lists of em_iters values per problem)."""
+    nprob = len(problems)
+    arr = (cofem_problem * nprob)(*problems)
+    m = max(params.em_iters, 1) * nprob
+    it = (ctypes.c_int32 * m)()
+    rr = (ctypes.c_double * m)()
+    cl = (ctypes.c_int32 * m)()
+    sp = (ctypes.c_int32 * m)()
+    st = cofem_stats(it, rr, cl, sp)
+    _check(lib().cofem_fit_batched(nprob, arr, ctypes.byref(params), ws_ptr, ws_bytes, mu_ptr,
+                                   s_ptr, alpha_ptr, ctypes.byref(st), stream),
+           "cofem_fit_batched")
+    e = params.em_iters
+
+    def split(a):
+        return [list(a)[i * e:(i + 1) * e] for i in range(nprob)]
+    return {"cg_iters": split(it), "relres": split(rr), "clamps": split(cl), "support": split(sp)}
 
 
 def cofem_probe_fill(seed, t, K, D, dtype, out_ptr, ld, stream=0):

@@ -1,0 +1,719 @@
+// Many independent SBL problems of uneven size in one fit (cofem_fit_batched):
+// Algorithm 1 run for every problem at once, each problem with its own
+// column-wise CG recurrences (Sec. 3.2), its own stop test and its own
+// probes, on BF16 dictionaries through the tensor-core operator.
+//
+// Layout: the problems' vectors are concatenated (problem i's block of K+1
+// columns at xoff_i with leading dimension ld_i); their dictionaries are
+// packed (tile-major, pre-swizzled) one after another.  The two products of
+// every operator application are grouped GEMMs over a host-built table of
+// work items (problem, row tile, K range), longest first; the items of a
+// problem whose CG has converged exit at once (per-problem done mask).  The
+// vector kernels run over a (chunk, column, problem) grid and reduce per
+// problem in a fixed order.  One CUDA graph per EM iteration: a WHILE node
+// repeats the CG iteration until every problem is done.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace cofem {
+
+constexpr int kBChunk = 1024;           // vector elements per block (256 threads x 4)
+
+struct BVec {                           // one problem, as the vector kernels see it
+  int64_t D, ld, xoff, aoff, boff1;
+  uint64_t seed;
+  int nch;                              // chunks of kBChunk elements
+  int dots_base, ndots;                 // its slots of the operator's partial dots
+};
+
+struct BState {                         // one problem's CG state (device)
+  int iter, done, error, pad;
+  int clamps, support;
+  unsigned int counter[4];
+  double normB2, relres;
+  double rho[kMaxCols], rho_new[kMaxCols], b[kMaxCols];
+};
+
+struct BCtl {
+  long long t;
+  int em_index;
+  int error;
+};
+
+struct BConf {
+  int nprob, nc, K;
+  double tol;
+  int max_iters, fixed_iters;
+  double den_floor, support_threshold;
+  int em_iters;
+  unsigned long long while_handle;
+  int nch_max;                           // partial-sum slots per problem
+  int split_nt;
+  int64_t split_ld;                      // pitch of the BF16 split buffer
+  __nv_bfloat16* split_buf;
+};
+
+__device__ __forceinline__ void bset_cond(unsigned long long h, unsigned v) {
+  if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+__device__ __forceinline__ void bsplit4(const BConf& cf, const BVec& pv, int j, int64_t d,
+                                        const float (&v)[4]) {
+  float r[4] = {v[0], v[1], v[2], v[3]};
+  for (int t = 0; t < cf.split_nt; ++t) {
+    __nv_bfloat16 o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[i] = __float2bfloat16_rn(r[i]);
+      r[i] -= __bfloat162float(o[i]);
+    }
+    *reinterpret_cast<uint2*>(cf.split_buf + (int64_t)split_row(j, t, cf.split_nt) * cf.split_ld +
+                              pv.boff1 + d) = *reinterpret_cast<uint2*>(o);
+  }
+}
+
+__device__ __forceinline__ float bprobe(uint64_t key, int64_t d, int k) {
+  const uint64_t h = probe_word(key, d, k >> 6);
+  return ((h >> (k & 63)) & 1ull) ? -1.f : 1.f;
+}
+
+// per-problem last-block arrival on st.counter[c] among `expected` blocks
+__device__ __forceinline__ bool barrive_last(unsigned int* counter, unsigned expected) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == expected - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ void bfinalize(const BConf& cf, BState* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int j = 0; j < cf.nc; ++j) tot += st->rho_new[j];
+    const double relres = sqrt(tot) / sqrt(st->normB2);
+    st->relres = relres;
+    int done = cf.fixed_iters > 0 ? st->iter >= cf.fixed_iters
+                                  : (relres < cf.tol || st->iter >= cf.max_iters);
+    if (!isfinite(relres)) { st->error = COFEM_ERR_NONFINITE; done = 1; }
+    for (int j = 0; j < cf.nc; ++j) {
+      const double r0 = st->rho[j], r1 = st->rho_new[j];
+      st->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+      st->rho[j] = r1;
+    }
+    st->done = done;
+  }
+}
+
+// X = 0, R = P = B (b and the problem's probes), P's BF16 terms; rho, ||B||.
+__global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, const BCtl* ctl,
+                             float* X, float* R, float* P, const float* bv, double* part) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[32];
+  const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  const BVec pv = pvs[pi];
+  if (c >= pv.nch) return;
+  BState* st = sts + pi;
+  const uint64_t key = probe_key(pv.seed, ctl->t);
+  float* x = X + pv.xoff + (int64_t)j * pv.ld;
+  float* r = R + pv.xoff + (int64_t)j * pv.ld;
+  float* p = P + pv.xoff + (int64_t)j * pv.ld;
+  double acc = 0.0;
+  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
+  if (d < pv.ld) {
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float w = 0.f;
+      if (d + i < pv.D) {
+        if (j == 0) { w = bv[pv.aoff + d + i]; acc += (double)w * (double)w; }
+        else w = bprobe(key, d + i, j - 1);
+      }
+      v[i] = w;
+      x[d + i] = 0.f;
+      r[d + i] = w;
+      p[d + i] = w;
+    }
+    if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
+  }
+  if (j == 0) {
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols] = s;
+  }
+  if (barrive_last(&st->counter[0], (unsigned)(pv.nch * cf.nc))) {
+    if (threadIdx.x == 0) {
+      double b2 = 0.0;
+      for (int i = 0; i < pv.nch; ++i) b2 += part[((int64_t)pi * cf.nch_max + i) * kMaxCols];
+      st->rho[0] = b2;
+      for (int jj = 1; jj < cf.nc; ++jj) st->rho[jj] = (double)pv.D;
+      st->normB2 = b2 + (double)cf.K * (double)pv.D;
+      st->relres = 1.0;
+      st->iter = 0;
+      st->clamps = 0;
+      st->support = 0;
+      int dn = 0;
+      if (!(st->normB2 > 0.0)) dn = 1;
+      if (!isfinite(st->normB2)) { st->error = COFEM_ERR_NONFINITE; dn = 1; }
+      st->done = dn;
+      done[pi] = dn;
+      st->counter[0] = 0;
+    }
+  }
+}
+
+// a_j = rho_j / gamma_j (gamma from the operator's partial dots of this
+// problem), x += a p, r -= a q, rho_new partials; last block: stop test.
+__global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, float* X,
+                               float* R, const float* P, const float* Q, const double* dots,
+                               double* part) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[32];
+  __shared__ float a_sh;
+  const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  const BVec pv = pvs[pi];
+  if (c >= pv.nch || done[pi]) return;
+  BState* st = sts + pi;
+  if (threadIdx.x < 32) {
+    double g = 0.0;
+    for (int i = threadIdx.x; i < pv.ndots; i += 32) g += dots[(int64_t)(pv.dots_base + i) * kMaxCols + j];
+    g = warp_sum(g);
+    if (threadIdx.x == 0) {
+      const double rho = st->rho[j];
+      double a = 0.0;
+      if (rho > 0.0) {
+        if (!(g > 0.0)) st->error = isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE;
+        else a = rho / g;
+      }
+      a_sh = (float)a;
+    }
+  }
+  __syncthreads();
+  const float a = a_sh;
+  double acc = 0.0;
+  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
+  if (d < pv.ld) {
+    const int64_t o = pv.xoff + (int64_t)j * pv.ld + d;
+    float4 xv = *reinterpret_cast<float4*>(X + o);
+    float4 rv = *reinterpret_cast<float4*>(R + o);
+    const float4 pp = *reinterpret_cast<const float4*>(P + o);
+    const float4 qq = *reinterpret_cast<const float4*>(Q + o);
+    xv.x = fmaf(a, pp.x, xv.x); xv.y = fmaf(a, pp.y, xv.y);
+    xv.z = fmaf(a, pp.z, xv.z); xv.w = fmaf(a, pp.w, xv.w);
+    rv.x = fmaf(-a, qq.x, rv.x); rv.y = fmaf(-a, qq.y, rv.y);
+    rv.z = fmaf(-a, qq.z, rv.z); rv.w = fmaf(-a, qq.w, rv.w);
+    acc = (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+    *reinterpret_cast<float4*>(X + o) = xv;
+    *reinterpret_cast<float4*>(R + o) = rv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = s;
+  if (barrive_last(&st->counter[1], (unsigned)(pv.nch * cf.nc))) {
+    if (threadIdx.x < cf.nc) {
+      double t = 0.0;
+      for (int i = 0; i < pv.nch; ++i) t += part[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+      st->rho_new[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) {
+      st->iter += 1;
+      st->counter[1] = 0;
+    }
+    bfinalize(cf, st);
+    if (threadIdx.x == 0) done[pi] = st->done;
+  }
+}
+
+// WHILE condition: some problem still iterating.
+__global__ void bcond_kernel(BConf cf, const int* done) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < cf.nprob; i += blockDim.x)
+    if (!done[i]) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) bset_cond(cf.while_handle, any ? 1u : 0u);
+}
+
+// p = r + b p and P's BF16 terms.
+__global__ void bdirection_kernel(BConf cf, const BVec* pvs, const BState* sts, const int* done,
+                                  const float* R, float* P) {
+  pdl_wait();
+  pdl_trigger();
+  const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  const BVec pv = pvs[pi];
+  if (c >= pv.nch || done[pi]) return;
+  const float b = (float)sts[pi].b[j];
+  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
+  if (d < pv.ld) {
+    const int64_t o = pv.xoff + (int64_t)j * pv.ld + d;
+    const float4 rv = *reinterpret_cast<const float4*>(R + o);
+    float4 pp = *reinterpret_cast<float4*>(P + o);
+    pp.x = fmaf(b, pp.x, rv.x); pp.y = fmaf(b, pp.y, rv.y);
+    pp.z = fmaf(b, pp.z, rv.z); pp.w = fmaf(b, pp.w, rv.w);
+    *reinterpret_cast<float4*>(P + o) = pp;
+    if (cf.split_nt > 0) {
+      const float v[4] = {pp.x, pp.y, pp.z, pp.w};
+      bsplit4(cf, pv, j, d, v);
+    }
+  }
+}
+
+// W = sum_s W_s (split order) -> BF16 terms in Ws; grid (chunks, slots, problems).
+template <int NT>
+__global__ void breduce_kernel(const TcProb* probs, const int* done, int nc, const float* Wp,
+                               __nv_bfloat16* Ws, int64_t ldw_total) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int G = 16 / NT;
+  const int pi = blockIdx.z, j = blockIdx.y;
+  const TcProb pr = probs[pi];
+  if (done[pi]) return;
+  const int gi = j / G, jj = j % G;
+  const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (n >= pr.ldw) return;
+  float r[4] = {0.f, 0.f, 0.f, 0.f};
+  if (j < nc) {
+    for (int s = 0; s < pr.S1; ++s) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(
+          Wp + pr.wpoff + (int64_t)s * nc * pr.ldw + (int64_t)j * pr.ldw + n));
+      r[0] += v.x; r[1] += v.y; r[2] += v.z; r[3] += v.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (n + i >= pr.N) r[i] = 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    __nv_bfloat16 o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[i] = __float2bfloat16_rn(r[i]);
+      r[i] -= __bfloat162float(o[i]);
+    }
+    *reinterpret_cast<uint2*>(Ws + (int64_t)(gi * 16 + jj * NT + t) * ldw_total + pr.boff2 + n) =
+        *reinterpret_cast<uint2*>(o);
+  }
+  if (jj == G - 1)
+    for (int rr = G * NT; rr < 16; ++rr)
+      *reinterpret_cast<uint2*>(Ws + (int64_t)(gi * 16 + rr) * ldw_total + pr.boff2 + n) =
+          make_uint2(0u, 0u);
+}
+
+// mu, s, alpha of every problem (Eq. (diag-estimate), M-step); counters.
+__global__ void bdiag_kernel(BConf cf, const BVec* pvs, BState* sts, const BCtl* ctl,
+                             const float* X, double* mu, double* s, double* alpha) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[32];
+  const int pi = blockIdx.z, c = blockIdx.x;
+  const BVec pv = pvs[pi];
+  if (c >= pv.nch) return;
+  const uint64_t key = probe_key(pv.seed, ctl->t);
+  int clamps = 0, support = 0, bad = 0;
+  for (int64_t d = (int64_t)c * kBChunk + threadIdx.x; d < min(pv.D, (int64_t)(c + 1) * kBChunk);
+       d += blockDim.x) {
+    const double m = (double)X[pv.xoff + d];
+    double acc = 0.0;
+    for (int k = 0; k < cf.K; ++k) {
+      const double xv = (double)X[pv.xoff + (int64_t)(k + 1) * pv.ld + d];
+      acc += bprobe(key, d, k) < 0.f ? -xv : xv;
+    }
+    const double sd = acc / (double)cf.K;
+    const double den = m * m + sd;
+    if (den < cf.den_floor) ++clamps;
+    const double al = 1.0 / fmax(den, cf.den_floor);
+    if (!isfinite(m) || !isfinite(sd)) bad = 1;
+    if (al < cf.support_threshold) ++support;
+    mu[pv.aoff + d] = m;
+    s[pv.aoff + d] = sd;
+    alpha[pv.aoff + d] = al;
+  }
+  const double cs = block_sum((double)clamps, sh);
+  const double ss = block_sum((double)support, sh);
+  const double bs = block_sum((double)bad, sh);
+  if (threadIdx.x == 0) {
+    if (cs > 0) atomicAdd(&sts[pi].clamps, (int)cs);
+    if (ss > 0) atomicAdd(&sts[pi].support, (int)ss);
+    if (bs > 0) sts[pi].error = COFEM_ERR_NONFINITE;
+  }
+}
+
+// per-problem statistics of this EM iteration; t += 1
+__global__ void bfinish_kernel(BConf cf, BState* sts, BCtl* ctl, int32_t* st_iters,
+                               double* st_relres, int32_t* st_clamps, int32_t* st_support) {
+  pdl_wait();
+  pdl_trigger();
+  const int e = ctl->em_index;
+  for (int i = threadIdx.x; i < cf.nprob; i += blockDim.x) {
+    if (e < cf.em_iters) {
+      st_iters[(int64_t)i * cf.em_iters + e] = sts[i].iter;
+      st_relres[(int64_t)i * cf.em_iters + e] = sts[i].relres;
+      st_clamps[(int64_t)i * cf.em_iters + e] = sts[i].clamps;
+      st_support[(int64_t)i * cf.em_iters + e] = sts[i].support;
+    }
+    if (sts[i].error) atomicCAS(&ctl->error, 0, sts[i].error);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->em_index = e + 1;
+    ctl->t += 1;
+  }
+}
+
+__global__ void bctl_init_kernel(BCtl* ctl, long long t0) {
+  pdl_wait();
+  pdl_trigger();
+  ctl->t = t0;
+  ctl->em_index = 0;
+  ctl->error = 0;
+}
+
+__global__ void bfill_kernel(double* x, int64_t n, double v) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+// ============================================================= host side
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct BLayout {
+  // per-problem geometry
+  std::vector<BVec> vec;
+  std::vector<TcProb> tcp;
+  std::vector<TcItem> items1, items2;
+  int nch_max = 0, ndots = 0, BN = 0, NT = 3, stages = 3;
+  uint32_t tmem_cols = 0;
+  size_t smem = 0;
+  int64_t ldx_total = 0, ldw_total = 0, dtot = 0, ldw_max = 0;
+  // workspace offsets
+  size_t o_packed, o_X, o_R, o_P, o_Q, o_b, o_xs, o_ws, o_wpart, o_dots, o_part, o_state, o_done,
+      o_ctl, o_vec, o_tcp, o_it1, o_it2, o_st_it, o_st_rr, o_st_cl, o_st_sp, o_simt, total;
+};
+
+static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* p, BLayout* L) {
+  const int nc = p->K + 1;
+  L->NT = 3;
+  const int G = 16 / L->NT;
+  L->BN = ((nc + G - 1) / G) * 16;
+  uint32_t tc = 32;
+  while (tc < (uint32_t)L->BN) tc <<= 1;
+  L->tmem_cols = tc;
+  DenseTcPlan plan = dense_tc_plan(2048, 8192, nc, L->NT, num_sms(), 2, 0);
+  L->stages = plan.stages;
+  L->smem = plan.smem;
+  int64_t xoff = 0, aoff = 0, b1 = 0, b2 = 0, wpoff = 0, poff = 0;
+  size_t simt = 0;
+  int dots = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t N = pr[i].N, D = pr[i].D;
+    if (N < 1 || D < 1 || !pr[i].phi_dev || !pr[i].y_dev || pr[i].ld < D || pr[i].ld % 64 ||
+        !(pr[i].beta > 0.0) || ((uintptr_t)pr[i].phi_dev & 255))
+      return COFEM_ERR_INVALID_ARG;
+    const int64_t ld = round_up(D, kLdAlign), ldw = round_up(N, kLdAlign);
+    BVec v;
+    v.D = D; v.ld = ld; v.xoff = xoff; v.aoff = aoff; v.boff1 = b1; v.seed = pr[i].seed;
+    v.nch = (int)((ld + kBChunk - 1) / kBChunk);
+    v.dots_base = dots;
+    v.ndots = (int)((D + 127) / 128);
+    TcProb t;
+    t.N = N; t.D = D; t.nkd = packed_tiles_k(D); t.poff = poff; t.xoff = xoff; t.ld = ld;
+    t.aoff = aoff; t.boff1 = b1; t.boff2 = b2; t.wpoff = wpoff; t.ldw = ldw;
+    const int nk1 = (int)((D + 63) / 64);
+    t.S1 = (nk1 + 31) / 32;                    // K ranges of at most 32 blocks (512 KB of Phi)
+    const int kbps = (nk1 + t.S1 - 1) / t.S1;
+    t.dots_base = dots;
+    t.beta = pr[i].beta;
+    for (int mt = 0; mt < (int)((N + 127) / 128); ++mt)
+      for (int sp = 0; sp < t.S1; ++sp)
+        L->items1.push_back({i, mt, sp, sp * kbps, std::min(nk1, (sp + 1) * kbps)});
+    const int nk2 = (int)((N + 63) / 64);
+    for (int mt = 0; mt < v.ndots; ++mt) L->items2.push_back({i, mt, 0, 0, nk2});
+    L->vec.push_back(v);
+    L->tcp.push_back(t);
+    xoff += (int64_t)nc * ld;
+    aoff += D;
+    b1 += ld;
+    b2 += ldw;
+    wpoff += (int64_t)t.S1 * nc * ldw;
+    poff += (int64_t)(packed_bytes(N, D) / 2);
+    dots += v.ndots;
+    L->nch_max = std::max(L->nch_max, v.nch);
+    L->ldw_max = std::max(L->ldw_max, ldw);
+    DenseSimtPlan sp = dense_simt_plan(N, D, 1, 4, num_sms());
+    simt = std::max(simt, sp.total());
+  }
+  // longest items first
+  std::stable_sort(L->items1.begin(), L->items1.end(),
+                   [](const TcItem& a, const TcItem& b) { return a.kb1 - a.kb0 > b.kb1 - b.kb0; });
+  std::stable_sort(L->items2.begin(), L->items2.end(),
+                   [](const TcItem& a, const TcItem& b) { return a.kb1 > b.kb1; });
+  L->ndots = dots;
+  L->ldx_total = b1;
+  L->ldw_total = b2;
+  L->dtot = aoff;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += a256(bytes); return r; };
+  L->o_packed = take((size_t)poff * 2);
+  L->o_X = take((size_t)xoff * 4);
+  L->o_R = take((size_t)xoff * 4);
+  L->o_P = take((size_t)xoff * 4);
+  L->o_Q = take((size_t)xoff * 4);
+  L->o_b = take((size_t)aoff * 4);
+  L->o_xs = take((size_t)L->BN * b1 * 2);
+  L->o_ws = take((size_t)L->BN * b2 * 2);
+  L->o_wpart = take((size_t)wpoff * 4);
+  L->o_dots = take((size_t)dots * kMaxCols * 8);
+  L->o_part = take((size_t)n * L->nch_max * kMaxCols * 8);
+  L->o_state = take((size_t)n * sizeof(BState));
+  L->o_done = take((size_t)n * 4);
+  L->o_ctl = take(sizeof(BCtl));
+  L->o_vec = take((size_t)n * sizeof(BVec));
+  L->o_tcp = take((size_t)n * sizeof(TcProb));
+  L->o_it1 = take(L->items1.size() * sizeof(TcItem));
+  L->o_it2 = take(L->items2.size() * sizeof(TcItem));
+  const int ne = std::max(1, p->em_iters);
+  L->o_st_it = take((size_t)n * ne * 4);
+  L->o_st_rr = take((size_t)n * ne * 8);
+  L->o_st_cl = take((size_t)n * ne * 4);
+  L->o_st_sp = take((size_t)n * ne * 4);
+  L->o_simt = take(simt);
+  L->total = o;
+  return COFEM_OK;
+}
+
+static cofem_status bcheck(int n, const cofem_problem* pr, const cofem_params* p) {
+  if (n < 1 || !pr || !p) return COFEM_ERR_INVALID_ARG;
+  if (p->K < 1 || p->K + 1 > kMaxCols || p->em_iters < 0 || p->cg_max_iters < 1) return COFEM_ERR_INVALID_ARG;
+  if (p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
+  if (p->resid_replace_every != 0) return COFEM_ERR_UNSUPPORTED;
+  if (!(p->den_floor > 0.0) || p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
+  return COFEM_OK;
+}
+
+}  // namespace cofem
+
+// ------------------------------------------------------------------ fit
+namespace cofem {
+
+namespace {
+struct BStreams {
+  cudaStream_t s[2] = {nullptr, nullptr};
+  ~BStreams() {
+    for (auto x : s)
+      if (x) cudaStreamDestroy(x);
+  }
+};
+}  // namespace
+
+#define BCK(x)                                      \
+  do {                                              \
+    if ((x) != cudaSuccess) return COFEM_ERR_CUDA;  \
+  } while (0)
+
+static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L, char* ws,
+                                  double* mu, double* s, double* alpha, cudaGraphExec_t* exec) {
+  const int nc = p->K + 1;
+  BStreams ss;
+  for (auto& x : ss.s) BCK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  float* X = (float*)(ws + L.o_X);
+  float* R = (float*)(ws + L.o_R);
+  float* P = (float*)(ws + L.o_P);
+  float* Q = (float*)(ws + L.o_Q);
+  const float* bv = (const float*)(ws + L.o_b);
+  __nv_bfloat16* xs = (__nv_bfloat16*)(ws + L.o_xs);
+  __nv_bfloat16* wsb = (__nv_bfloat16*)(ws + L.o_ws);
+  float* wpart = (float*)(ws + L.o_wpart);
+  double* dots = (double*)(ws + L.o_dots);
+  double* part = (double*)(ws + L.o_part);
+  BState* sts = (BState*)(ws + L.o_state);
+  int* done = (int*)(ws + L.o_done);
+  BCtl* ctl = (BCtl*)(ws + L.o_ctl);
+  const BVec* pvs = (const BVec*)(ws + L.o_vec);
+  const TcProb* tcp = (const TcProb*)(ws + L.o_tcp);
+  const TcItem* it1 = (const TcItem*)(ws + L.o_it1);
+  const TcItem* it2 = (const TcItem*)(ws + L.o_it2);
+
+  BConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.nprob = n;
+  cf.nc = nc;
+  cf.K = p->K;
+  cf.tol = p->cg_tol;
+  cf.max_iters = p->cg_max_iters;
+  cf.fixed_iters = p->fixed_cg_iters;
+  cf.den_floor = p->den_floor;
+  cf.support_threshold = p->support_threshold;
+  cf.em_iters = p->em_iters;
+  cf.nch_max = L.nch_max;
+  cf.split_nt = L.NT;
+  cf.split_ld = L.ldx_total;
+  cf.split_buf = xs;
+
+  cudaStream_t cs = ss.s[0];
+  BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  BCK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hw;
+  BCK(cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault));
+  cf.while_handle = (unsigned long long)hw;
+  const dim3 vg(L.nch_max, nc, n);
+  BCK(launch_k(binit_kernel, vg, dim3(256), 0, cs, cf, pvs, sts, done, (const BCtl*)ctl, X, R, P,
+               bv, part));
+  BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, cs, cf, (const int*)done));
+  // WHILE node
+  {
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    BCK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hw;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    BCK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    BCK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t bs = ss.s[1];
+    BCK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int* err = &ctl->error;
+    if (dense_tc_batched(0, L.NT, (int)L.items1.size(), it1, tcp, done, ws + L.o_packed, xs,
+                         L.ldx_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, wpart, nullptr,
+                         nullptr, nullptr, nullptr, err, bs) != 0)
+      return COFEM_ERR_CUDA;
+    const int G = 16 / L.NT;
+    const dim3 rg((unsigned)((L.ldw_max / 4 + 127) / 128), (L.BN / 16) * G, n);
+    if (L.NT == 3)
+      BCK(launch_k(breduce_kernel<3>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                   (const float*)wpart, wsb, L.ldw_total));
+    else if (L.NT == 2)
+      BCK(launch_k(breduce_kernel<2>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                   (const float*)wpart, wsb, L.ldw_total));
+    else
+      BCK(launch_k(breduce_kernel<1>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                   (const float*)wpart, wsb, L.ldw_total));
+    if (dense_tc_batched(1, L.NT, (int)L.items2.size(), it2, tcp, done, ws + L.o_packed, wsb,
+                         L.ldw_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, nullptr, P, Q,
+                         alpha, dots, err, bs) != 0)
+      return COFEM_ERR_CUDA;
+    BCK(launch_k(bupdate_kernel, vg, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
+                 (const float*)Q, (const double*)dots, part));
+    BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, bs, cf, (const int*)done));
+    BCK(launch_k(bdirection_kernel, vg, dim3(256), 0, bs, cf, pvs, (const BState*)sts,
+                 (const int*)done, (const float*)R, P));
+    cudaGraph_t tmp;
+    BCK(cudaStreamEndCapture(bs, &tmp));
+  }
+  BCK(launch_k(bdiag_kernel, dim3(L.nch_max, 1, n), dim3(256), 0, cs, cf, pvs, sts,
+               (const BCtl*)ctl, (const float*)X, mu, s, alpha));
+  BCK(launch_k(bfinish_kernel, dim3(1), dim3(256), 0, cs, cf, sts, ctl,
+               (int32_t*)(ws + L.o_st_it), (double*)(ws + L.o_st_rr), (int32_t*)(ws + L.o_st_cl),
+               (int32_t*)(ws + L.o_st_sp)));
+  cudaGraph_t graph;
+  BCK(cudaStreamEndCapture(cs, &graph));
+  cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? COFEM_OK : COFEM_ERR_CUDA;
+}
+
+}  // namespace cofem
+
+using namespace cofem;
+
+extern "C" cofem_status cofem_batched_workspace_bytes(int32_t n, const cofem_problem* problems,
+                                                      const cofem_params* p, size_t* bytes) {
+  cofem_status rc = bcheck(n, problems, p);
+  if (rc != COFEM_OK) return rc;
+  if (!bytes) return COFEM_ERR_INVALID_ARG;
+  BLayout L;
+  rc = blayout(n, problems, p, &L);
+  if (rc != COFEM_OK) return rc;
+  *bytes = L.total;
+  return COFEM_OK;
+}
+
+extern "C" cofem_status cofem_fit_batched(int32_t n, const cofem_problem* problems,
+                                          const cofem_params* p, void* workspace_dev,
+                                          size_t workspace_bytes, double* mu_dev, double* s_dev,
+                                          double* alpha_dev, cofem_stats* stats, void* stream) {
+  cofem_status rc = bcheck(n, problems, p);
+  if (rc != COFEM_OK) return rc;
+  if (!workspace_dev || !mu_dev || !s_dev || !alpha_dev || ((uintptr_t)workspace_dev & 255))
+    return COFEM_ERR_INVALID_ARG;
+  BLayout L;
+  rc = blayout(n, problems, p, &L);
+  if (rc != COFEM_OK) return rc;
+  if (workspace_bytes < L.total) return COFEM_ERR_WORKSPACE;
+  char* ws = (char*)workspace_dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  // zero all but the packed dictionaries (overwritten below)
+  BCK(cudaMemsetAsync(ws + L.o_X, 0, L.total - L.o_X, st));
+  BCK(cudaMemcpyAsync(ws + L.o_vec, L.vec.data(), n * sizeof(BVec), cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(ws + L.o_tcp, L.tcp.data(), n * sizeof(TcProb), cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(ws + L.o_it1, L.items1.data(), L.items1.size() * sizeof(TcItem),
+                      cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(ws + L.o_it2, L.items2.data(), L.items2.size() * sizeof(TcItem),
+                      cudaMemcpyHostToDevice, st));
+  BCK(launch_k(bctl_init_kernel, dim3(1), dim3(1), 0, st, (BCtl*)(ws + L.o_ctl),
+               (long long)(p->t_offset + 1)));
+  if (p->t_offset == 0)
+    BCK(launch_k(bfill_kernel, dim3(1024), dim3(256), 0, st, alpha_dev, L.dtot, p->alpha_init));
+  for (int i = 0; i < n; ++i) {
+    const cofem_problem& q = problems[i];
+    // packed dictionary, and b = beta Phi^T y (once per fit)
+    dense_pack_bf16(q.phi_dev, q.N, q.D, q.ld, ws + L.o_packed + L.tcp[i].poff * 2, st);
+    DenseDesc dd = {};
+    dd.N = q.N;
+    dd.D = q.D;
+    dd.ld = q.ld;
+    dd.dtype = COFEM_BF16;
+    dd.phi = q.phi_dev;
+    dense_simt_adjoint<__nv_bfloat16, float>(dd, (const float*)q.y_dev, q.N, 1,
+                                             (float*)(ws + L.o_b) + L.vec[i].aoff,
+                                             L.vec[i].ld, q.beta, nullptr, nullptr, nullptr,
+                                             nullptr, ws + L.o_simt, st);
+  }
+  BCK(cudaGetLastError());
+  if (p->em_iters > 0) {
+    cudaGraphExec_t exec = nullptr;
+    rc = batched_graph(n, p, L, ws, mu_dev, s_dev, alpha_dev, &exec);
+    if (rc != COFEM_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return rc;
+    }
+    for (int t = 0; t < p->em_iters; ++t)
+      if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return COFEM_ERR_CUDA;
+      }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    if (e != cudaSuccess) return COFEM_ERR_CUDA;
+  } else {
+    BCK(cudaStreamSynchronize(st));
+  }
+  BCtl hctl;
+  BCK(cudaMemcpy(&hctl, ws + L.o_ctl, sizeof(hctl), cudaMemcpyDeviceToHost));
+  if (stats && p->em_iters > 0) {
+    const size_t m = (size_t)n * p->em_iters;
+    if (stats->cg_iters) BCK(cudaMemcpy(stats->cg_iters, ws + L.o_st_it, 4 * m, cudaMemcpyDeviceToHost));
+    if (stats->relres) BCK(cudaMemcpy(stats->relres, ws + L.o_st_rr, 8 * m, cudaMemcpyDeviceToHost));
+    if (stats->clamps) BCK(cudaMemcpy(stats->clamps, ws + L.o_st_cl, 4 * m, cudaMemcpyDeviceToHost));
+    if (stats->support) BCK(cudaMemcpy(stats->support, ws + L.o_st_sp, 4 * m, cudaMemcpyDeviceToHost));
+  }
+  return hctl.error ? (cofem_status)hctl.error : COFEM_OK;
+}

@@ -38,6 +38,24 @@ void apply_ticks_arm(cudaEvent_t* events, int cap);
 int apply_ticks_disarm();
 void apply_tick(cudaStream_t st);
 
+// Batched mode: one CTA per work item of a table built on the host.
+struct TcProb {
+  int64_t N, D;          // dictionary shape of the problem
+  int64_t nkd;           // 64-column tiles of its packed Phi
+  int64_t poff;          // element offset of its packed Phi
+  int64_t xoff, ld;      // its X / Y block: offset (elements) and leading dimension
+  int64_t aoff;          // offset of its alpha (and of its coordinates)
+  int64_t boff1;         // column offset of its BF16 terms of X in the split buffer
+  int64_t boff2;         // column offset of its BF16 terms of W in Ws
+  int64_t wpoff, ldw;    // its split-K partials of W: offset, leading dimension
+  int S1;                // splits of its first product
+  int dots_base;         // first partial-dot slot of its second product
+  double beta;           // its noise precision
+};
+struct TcItem {
+  int prob, tile, split, kb0, kb1;
+};
+
 struct DenseSimtPlan {
   int64_t ldw, ld;         // padded N and D
   int S1, S2;              // split-K counts of the two products
@@ -71,6 +89,16 @@ inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
 // (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG
 // kernels.
 constexpr unsigned kApplyPresplit = 1u;
+// Batched products over a work-item table (see TcItem / TcProb).  mode 0:
+// split-K partials of W = Phi X; mode 1: Y = beta Phi^T W + alpha . X with
+// partial dots.  xs / ws: BF16 term buffers (BN rows, pitch ldx_total /
+// ldw_total).  Returns 0, 1 (tensor map) or 2 (launch).
+int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const TcProb* probs,
+                     const int* done, const void* packed, const __nv_bfloat16* bsrc,
+                     int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
+                     size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
+                     double* dots, int* err, cudaStream_t st);
+
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
                    int* err, unsigned flags, cudaStream_t st);

@@ -69,6 +69,10 @@ struct TcArgs {
   double beta;
   double* dots;
   int* err;
+  // batched mode (items != null): gridDim.x work items
+  const TcItem* items;
+  const TcProb* probs;
+  const int* done;       // per-problem converged flags: their items exit at once
 };
 
 __device__ __forceinline__ void tc_fail(int* err, volatile int* abort) {
@@ -105,9 +109,38 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   double* red = (double*)(tmem_slot + 4);          // [4][64] epilogue partial dots
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kTileM;
-  const int kb0 = blockIdx.y * args.kb_per_split;
-  const int kb1 = min(args.nk_total, kb0 + args.kb_per_split);
+  // geometry of this CTA's work (one problem, or one item of a batch)
+  int64_t m0, M = args.M, nkd = args.nkd, ldo = MODE == 0 ? args.ldw : args.ld;
+  int64_t xoff = 0, aoff = 0, woff = 0, sstride = args.split_stride, bx0 = 0;
+  double beta = args.beta;
+  int kb0, kb1, split, dslot;
+  const __nv_bfloat16* pk = args.packed;
+  if (args.items) {
+    const TcItem it = args.items[blockIdx.x];
+    if (args.done && args.done[it.prob]) return;        // converged: nothing to do
+    const TcProb pr = args.probs[it.prob];
+    m0 = (int64_t)it.tile * kTileM;
+    kb0 = it.kb0;
+    kb1 = it.kb1;
+    split = it.split;
+    M = MODE == 0 ? pr.N : pr.D;
+    nkd = pr.nkd;
+    pk += pr.poff;
+    ldo = MODE == 0 ? pr.ldw : pr.ld;
+    xoff = pr.xoff;
+    aoff = pr.aoff;
+    woff = pr.wpoff;
+    sstride = (int64_t)args.nc * pr.ldw;
+    bx0 = MODE == 0 ? pr.boff1 : pr.boff2;
+    dslot = pr.dots_base + it.tile;
+    beta = pr.beta;
+  } else {
+    m0 = (int64_t)blockIdx.x * kTileM;
+    kb0 = blockIdx.y * args.kb_per_split;
+    kb1 = min(args.nk_total, kb0 + args.kb_per_split);
+    split = blockIdx.y;
+    dslot = blockIdx.x;
+  }
   const int nk = max(0, kb1 - kb0);
 
   if (threadIdx.x == 0) {
@@ -151,30 +184,30 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         // across CG iterations; the rest streams through
         if (MODE == 0) {
           const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
-          if (args.packed)   // tile (blockIdx.x, kb): one contiguous 16 KB copy
-            tc::bulk_load(sa, args.packed + ((int64_t)blockIdx.x * args.nkd + kb) * (kTileM * kTileK),
-                          kATileBytes, &full[s], pol_a);
+          if (pk)   // tile (m0 / 128, kb): one contiguous 16 KB copy
+            tc::bulk_load(sa, pk + ((m0 >> 7) * nkd + kb) * (kTileM * kTileK), kATileBytes,
+                          &full[s], pol_a);
           else
             tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
         } else {
           const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
-          if (args.packed) {
+          if (pk) {
             // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
             // two 64-column tiles m0/64 and m0/64 + 1 give the 128 d's
-            const int64_t base = ((int64_t)(kb >> 1) * args.nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
-            const __nv_bfloat16* src = args.packed + base * kTileK;
+            const int64_t base = ((int64_t)(kb >> 1) * nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
+            const __nv_bfloat16* src = pk + base * kTileK;
             tc::bulk_load(sa, src, kATileBytes / 2, &full[s], pol_a);
             // the next 64-column tile; past the last one (D not a multiple of
             // 128) the same half-tile is copied again: it only feeds output
             // rows d >= D, which are not stored
-            const __nv_bfloat16* src2 = (m0 >> 6) + 1 < args.nkd ? src + kTileM * kTileK : src;
+            const __nv_bfloat16* src2 = (m0 >> 6) + 1 < nkd ? src + kTileM * kTileK : src;
             tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
           } else {
             tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
             tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK, pol_a);
           }
         }
-        tc::tma_load_2d(sb, &mapB, &full[s], kb * kTileK, 0, pol_b);
+        tc::tma_load_2d(sb, &mapB, &full[s], (int)(bx0 + (int64_t)kb * kTileK), 0, pol_b);
         ++issued;
       }
       if (*abort) {
@@ -218,7 +251,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     tc::tc_fence_after();
     constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
     const int ngroups = (args.nc + G - 1) / G;
-    const bool live = row < args.M;
+    const bool live = row < M;
     for (int gi = 0; gi < ngroups; ++gi) {
       float v[COLS];
 #pragma unroll
@@ -241,13 +274,13 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         for (int t = NT - 1; t >= 0; --t) acc += v[jj * NT + t];
         if (MODE == 0) {
           if (j < args.nc && live)
-            args.wpart[(int64_t)blockIdx.y * args.split_stride + (int64_t)j * args.ldw + row] = acc;
+            args.wpart[woff + (int64_t)split * sstride + (int64_t)j * ldo + row] = acc;
         } else {
           double dot = 0.0;
           if (j < args.nc && live) {
-            const float xv = args.x[(int64_t)j * args.ld + row];
-            const float yv = fmaf((float)args.alpha[row], xv, (float)args.beta * acc);
-            args.y[(int64_t)j * args.ld + row] = yv;
+            const float xv = args.x[xoff + (int64_t)j * ldo + row];
+            const float yv = fmaf((float)args.alpha[aoff + row], xv, (float)beta * acc);
+            args.y[xoff + (int64_t)j * ldo + row] = yv;
             dot = (double)xv * (double)yv;
           }
           if (args.dots && j < args.nc) {
@@ -263,7 +296,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       if (warp == 2) {
         for (int j = lane; j < args.nc; j += 32) {
           const double t = red[j] + red[64 + j] + red[128 + j] + red[192 + j];
-          args.dots[(int64_t)blockIdx.x * kMaxCols + j] = t;
+          args.dots[(int64_t)dslot * kMaxCols + j] = t;
         }
       }
     }
@@ -577,6 +610,44 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   apply_tick(st);
   if (nparts) *nparts = dots ? (int)g2.x : 0;
   return 0;
+}
+
+int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const TcProb* probs,
+                     const int* done, const void* packed, const __nv_bfloat16* bsrc,
+                     int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
+                     size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
+                     double* dots, int* err, cudaStream_t st) {
+  CUtensorMap mA, mB;
+  // mapA is unused in the batched mode (Phi comes from the packed copy);
+  // any valid map will do
+  if (!make_map(&mA, bsrc, (uint64_t)b_cols, (uint64_t)BN, (uint64_t)b_cols, 64)) return 1;
+  if (!make_map(&mB, bsrc, (uint64_t)b_cols, (uint64_t)BN, (uint64_t)b_cols, (uint32_t)BN)) return 1;
+  TcArgs a = {};
+  a.nc = nc;
+  a.BN = BN;
+  a.stages = stages;
+  a.tmem_cols = tmem_cols;
+  a.packed = (const __nv_bfloat16*)packed;
+  a.wpart = wpart;
+  a.x = X;
+  a.y = Y;
+  a.alpha = alpha;
+  a.dots = dots;
+  a.err = err;
+  a.items = items;
+  a.probs = probs;
+  a.done = done;
+  dim3 g((unsigned)nitems, 1);
+  cudaError_t e;
+  switch ((mode << 2) | NT) {
+    case 1: e = launch_tc<0, 1>(g, smem, mA, mB, a, st); break;
+    case 2: e = launch_tc<0, 2>(g, smem, mA, mB, a, st); break;
+    case 3: e = launch_tc<0, 3>(g, smem, mA, mB, a, st); break;
+    case 5: e = launch_tc<1, 1>(g, smem, mA, mB, a, st); break;
+    case 6: e = launch_tc<1, 2>(g, smem, mA, mB, a, st); break;
+    default: e = launch_tc<1, 3>(g, smem, mA, mB, a, st); break;
+  }
+  return e == cudaSuccess ? 0 : 2;
 }
 
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,

@@ -48,6 +48,10 @@ def parse():
                     help="BF16 Phi as read by the tensor cores: tile-major copy or row-major")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the operator pipeline autotuner (library defaults)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batched-512-n128-2048", "conv-l1m-c8-t64",
+                             "dense-fp64-n256-d1024"],
+                    help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -192,11 +196,170 @@ def launches_per_em(cg_iters, replace_every, per_iter, per_replace):
     return 1 + cg_iters * per_iter + n_rep * per_replace + 1
 
 
+def _timed(fn):
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) / 1e3
+
+
+def _common(args, metric, unit, value, seconds, dtype, config, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": seconds * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    """512 dense problems of uneven size in one batched fit per step range."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    c = datagen.CONFIGS["batched-512-n128-2048"]
+    probs = datagen.batched_problems_torch(c["n_problems"], c["n_min"], c["n_max"], c["ratio"],
+                                           c["frac_nonzero"], c["sigma"], args.seed)
+    phis = [q[0] for q in probs]
+    ys = [q[2] for q in probs]
+    betas = [q[3] for q in probs]
+    seeds = [q[4] for q in probs]
+    kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"])
+    pw = api.params(em_iters=args.warmup, **kw)
+    alphas, _, _, _ = api.fit_batched(phis, ys, betas, seeds, pw)
+    a0 = torch.cat(alphas).clone()
+    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+    probs_c = []
+    ws = None
+    with ClockSampler(0) as clk:
+        (res, sec) = _timed(lambda: _fit_batched_resume(api, B, phis, ys, betas, seeds, pt, a0))
+    stats = res
+    cg = np.array(stats["cg_iters"])                   # problems x steps
+    phi_bytes = np.array([2 * P.shape[0] * P.shape[1] for P in phis], dtype=np.float64)
+    streamed = float((cg * 2 * phi_bytes[:, None]).sum())   # Phi read twice per CG iteration
+    ach = streamed / sec / 1e9
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    n = len(phis)
+    _common(args, "problem EM iters/s (512 dense problems, N~U[128,2048], D=4N, K=16, tol 1e-5)",
+            "problem EM iters/s", n * args.steps / sec, sec, "f32 vectors, bf16 Phi",
+            {"workload": "batched-512-n128-2048", "problems": n, "K": c["K"],
+             "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
+             "total_phi_gb": float(phi_bytes.sum() / 1e9)},
+            {"batch_em_iters_per_s": args.steps / sec,
+             "cg_iters": {"mean": float(cg.mean()), "max_per_step": cg.max(axis=0).tolist()},
+             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                          "frac": ach / peak, "traffic": None,
+                          "kernel": "whole batched step: Phi bytes of every CG iteration of "
+                                    "every problem (2 passes) / step time"},
+             "clocks": clk.summary()})
+
+
+def _fit_batched_resume(api, B, phis, ys, betas, seeds, p, alpha0):
+    import torch
+    probs, keep = [], []
+    for Phi, y, beta, seed in zip(phis, ys, betas, seeds):
+        N, D = Phi.shape
+        ld = (D + 63) // 64 * 64
+        if Phi.stride() != (ld, 1):
+            buf = torch.zeros((N, ld), dtype=torch.bfloat16, device=Phi.device)
+            buf[:, :D] = Phi
+            Phi = buf
+        keep.append(Phi)
+        probs.append(B.cofem_problem(N, D, Phi.data_ptr(), ld, y.data_ptr(), float(beta), int(seed)))
+    ws = torch.empty(B.cofem_batched_workspace_bytes(probs, p), dtype=torch.uint8, device="cuda")
+    mu = torch.empty_like(alpha0)
+    s = torch.empty_like(alpha0)
+    alpha = alpha0.clone()
+    return B.cofem_fit_batched(probs, p, ws.data_ptr(), ws.numel(), mu.data_ptr(), s.data_ptr(),
+                               alpha.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
+
+def run_conv(args):
+    """Convolutional dictionary, L = 2^20, 8 filters x 64 taps."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    c = datagen.CONFIGS["conv-l1m-c8-t64"]
+    pr = datagen.conv_problem(c["L"], c["C"], c["T"], c["density"], c["sigma"], args.seed)
+    op = api.ConvOperator(torch.from_numpy(pr.h).cuda(), c["L"])
+    y = torch.from_numpy(pr.y.astype(np.float32)).cuda()
+    kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"],
+              seed=args.seed)
+    rw = api.fit(op, y, pr.beta, api.params(em_iters=args.warmup, **kw))
+    a0 = rw.alpha.clone()
+    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+    with ClockSampler(0) as clk:
+        res, sec = _timed(lambda: api.fit(op, y, pr.beta, pt, alpha=a0.clone()))
+    cg = res.stats["cg_iters"]
+    D, L, nc = op.D, c["L"], c["K"] + 1
+    X = torch.randn((nc, D), device="cuda")
+    Y = torch.empty_like(X)
+    nb = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, nc)
+    wsa = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    ms = [B.cofem_op_apply_timed(op.handle, B.COFEM_F32, X.data_ptr(), D, nc, a0.data_ptr(),
+                                 pr.beta, Y.data_ptr(), wsa.data_ptr(), nb) for _ in range(5)][1:]
+    fwd = float(np.mean([m[0] for m in ms])) / 1e3
+    adj = float(np.mean([m[1] for m in ms])) / 1e3
+    adj_bytes = L * nc * 4 + 2 * D * nc * 4 + 8 * D
+    flops = 2 * 2 * c["T"] * D * nc                    # forward + adjoint MACs x 2
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    _common(args, "EM iters/s (circular conv dictionary L=2^20, 8x64 taps, D=8.4M, K=16)",
+            "EM iters/s", args.steps / sec, sec, "f32",
+            {"workload": "conv-l1m-c8-t64", "L": L, "C": c["C"], "T": c["T"], "D": D,
+             "K": c["K"], "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps)},
+            {"cg_iters_per_em": cg,
+             "roofline": {"bound": "hbm", "achieved": adj_bytes / adj / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": adj_bytes / adj / 1e9 / peak, "traffic": None,
+                          "kernel": "conv_adjoint_kernel (Phi^T W + alpha.X, 17 cols)",
+                          "launch_us": adj * 1e6, "algorithmic_bytes": adj_bytes},
+             "conv_apply": {"forward_us": fwd * 1e6, "adjoint_us": adj * 1e6,
+                            "fp32_tflops": flops / (fwd + adj) / 1e12},
+             "clocks": clk.summary()})
+
+
+def run_fp64(args):
+    """FP64 vectors and dictionary, N=256, D=1024, K=20, tol 1e-6."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    c = datagen.CONFIGS["dense-fp64-n256-d1024"]
+    pr = datagen.dense_problem(c["N"], c["D"], c["n_nonzero"], c["sigma"], args.seed)
+    op = api.DenseOperator(torch.from_numpy(pr.Phi.astype(np.float64)).cuda())
+    y = torch.from_numpy(pr.y).cuda()
+    kw = dict(vec_dtype=B.COFEM_F64, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"],
+              seed=args.seed)
+    rw = api.fit(op, y, pr.beta, api.params(em_iters=args.warmup, **kw))
+    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+    res, sec = _timed(lambda: api.fit(op, y, pr.beta, pt, alpha=rw.alpha.clone()))
+    cg = res.stats["cg_iters"]
+    flops = float(sum(cg)) * 2 * 2 * c["N"] * c["D"] * (c["K"] + 1)
+    _common(args, "EM iters/s (dense FP64 N=256 D=1024 K=20, tol 1e-6)", "EM iters/s",
+            args.steps / sec, sec, "f64",
+            {"workload": "dense-fp64-n256-d1024", "N": c["N"], "D": c["D"], "K": c["K"]},
+            {"cg_iters_per_em": cg, "us_per_cg_iter": sec / max(1, sum(cg)) * 1e6,
+             "roofline": {"bound": "alu", "achieved": flops / sec / 1e12,
+                          "peak": 1.25, "unit": "TFLOP/s", "frac": flops / sec / 1e12 / 1.25,
+                          "traffic": None, "peak_source": "nominal FP64 rate of the part",
+                          "kernel": "whole CG loop (Phi in L2)"}})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
         return
+    if args.workload == "batched-512-n128-2048":
+        return run_batched(args)
+    if args.workload == "conv-l1m-c8-t64":
+        return run_conv(args)
+    if args.workload == "dense-fp64-n256-d1024":
+        return run_fp64(args)
     import torch
     import torch.distributed as dist
     from paper_2202_12808_gb300 import api

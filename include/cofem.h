@@ -169,6 +169,15 @@ typedef struct {
   int64_t t_offset;            /* EM iterations already done: t runs
                                   t_offset+1 .. t_offset+em_iters; when > 0
                                   alpha_dev is read as the starting alpha */
+  const void* mlp;             /* learned warm start / preconditioner (not in
+                                  the paper): device pointer to the 1282 BF16
+                                  weights of cofem_mlp_*, or NULL for plain CG.
+                                  From the fit's second E-step on, each solve
+                                  starts from X0 = [mu_hat | s_hat . p_k] with
+                                  M^-1 = diag(s_hat) (preconditioned CG, same
+                                  stop test); if it has not converged after
+                                  cg_max_iters, plain CG from zero is run
+                                  instead.  F32 vectors only. */
 } cofem_params;
 
 /* Fills *p with: K 20, em_iters 50, cg_max_iters 400, fixed 0, R 0, F32,
@@ -185,6 +194,10 @@ typedef struct {
   int32_t* clamps;
   int32_t* support;
 } cofem_stats;
+
+/* Learned path: number of fallbacks to plain CG in the last cofem_fit on
+ * this thread (0 without a learned warm start). */
+int32_t cofem_last_fit_fallbacks(void);
 
 /* Bytes of device workspace cofem_fit needs for this operator and params
  * (256-byte aligned base required). */
@@ -235,6 +248,60 @@ cofem_status cofem_fit_batched(int32_t n, const cofem_problem* problems,
                                const cofem_params* p, void* workspace_dev,
                                size_t workspace_bytes, double* mu_dev, double* s_dev,
                                double* alpha_dev, cofem_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start / preconditioner (not in the paper; plain CG stays the
+ * fallback).  A per-coordinate MLP 4 -> 32 -> 32 -> 2 with tanh, 1282
+ * parameters laid out W1 (32x4, row-major) | b1 (32) | W2 (32x32) | b2 (32)
+ * | W3 (2x32) | b3 (2).  With c_d = beta ||phi_d||^2 + alpha_d its input is
+ *   u = [ln alpha_d / 10, ln(beta ||phi_d||^2) / 10,
+ *        asinh(mu_prev_d sqrt(c_d)) / 4, ln(max(s_prev_d c_d, 1e-6)) / 4]
+ * and its output o gives mu_hat_d = sinh(4 o1) / sqrt(c_d) and
+ * s_hat_d = exp(4 o2) / c_d; training targets are the same transforms of an
+ * E-step's mu and s.  Training minimises the mean of 1/2 ||o - y||^2 with
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights; the
+ * forward pass and inference use BF16 weights with FP32 arithmetic.
+ * ------------------------------------------------------------------------ */
+
+/* ||phi_d||^2 for every coordinate (D floats).  Asynchronous. */
+cofem_status cofem_op_col_norms(const cofem_op* op, float* out_dev, void* stream);
+
+/* Features u (D x 4 floats, row-major) from alpha, ||phi_d||^2, beta and the
+ * previous E-step's mu, s (NULL: mu_prev = 0, s_prev = 1/c_d).  Async. */
+cofem_status cofem_mlp_features(const double* alpha_dev, const float* phinorm2_dev,
+                                double beta, const double* mu_prev_dev,
+                                const double* s_prev_dev, int64_t D, float* U_dev,
+                                void* stream);
+
+/* Targets y (D x 2 floats) from an E-step's mu and s.  Asynchronous. */
+cofem_status cofem_mlp_targets(const double* alpha_dev, const float* phinorm2_dev,
+                               double beta, const double* mu_dev, const double* s_dev,
+                               int64_t D, float* Y_dev, void* stream);
+
+/* o = MLP(u) for n samples (U: n x 4, O: n x 2 floats); weights F32 or BF16.
+ * Asynchronous. */
+cofem_status cofem_mlp_forward(const void* weights_dev, cofem_dtype wdtype,
+                               const float* U_dev, int64_t n, float* O_dev, void* stream);
+
+/* Scratch of cofem_mlp_grad / cofem_mlp_adam_step for n samples. */
+size_t cofem_mlp_train_workspace_bytes(int64_t n);
+
+/* Gradient (1282 floats, parameter layout above) and loss (double) of the
+ * mean loss over n samples, weights F32 or BF16.  Deterministic (fixed
+ * reduction order).  Asynchronous. */
+cofem_status cofem_mlp_grad(const void* weights_dev, cofem_dtype wdtype, const float* U_dev,
+                            const float* Y_dev, int64_t n, float* grad_dev, double* loss_dev,
+                            void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* One Adam step on the n samples: forward/backward with the BF16 weights,
+ * update of the FP32 master weights and moments (m, v), new BF16 copy.
+ * step is 1-based; loss_dev (optional) receives the loss before the step.
+ * Asynchronous. */
+cofem_status cofem_mlp_adam_step(float* master_dev, float* m_dev, float* v_dev,
+                                 void* weights_bf16_dev, const float* U_dev,
+                                 const float* Y_dev, int64_t n, int32_t step, float lr,
+                                 void* workspace_dev, size_t workspace_bytes,
+                                 double* loss_dev, void* stream);
 
 /* ------------------------------------------------------------------------
  * Individual hot-path steps (each is one of the kernels cofem_fit runs).

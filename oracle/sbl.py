@@ -192,6 +192,46 @@ def cg_solve(A, B, tol, max_iters, fixed_iters=0, resid_replace_every=0):
     return CGResult(X, it, relres, fixed_iters > 0 or relres < tol)
 
 
+def pcg_solve(A, B, X0, minv, tol, max_iters, resid_replace_every=0):
+    """Column-wise preconditioned CG from X0 with the diagonal preconditioner
+    M^-1 = diag(minv); same joint stop test on the residual R = B - A X as
+    cg_solve.  With X0 = 0 and minv = 1 it performs exactly cg_solve's
+    arithmetic.  (The learned warm start / preconditioner; the paper's solver
+    is the unpreconditioned case.)"""
+    B = np.asarray(B, dtype=np.float64)
+    X = np.array(X0, dtype=np.float64)
+    R = B - A(X) if np.any(X) else B.copy()
+    Z = minv[:, None] * R
+    P = Z.copy()
+    rho = np.sum(R * Z, axis=0)
+    normB = np.sqrt(np.sum(B * B))
+    if normB == 0.0:
+        return CGResult(np.zeros_like(B), 0, 0.0, True)
+    relres = np.sqrt(np.sum(R * R)) / normB
+    if relres < tol:
+        return CGResult(X, 0, relres, True)
+    it = 0
+    while it < max_iters:
+        it += 1
+        Q = A(P)
+        gamma = np.sum(P * Q, axis=0)
+        a = np.where(rho > 0, rho / np.where(gamma != 0, gamma, 1.0), 0.0)
+        X = X + a * P
+        if resid_replace_every > 0 and it % resid_replace_every == 0:
+            R = B - A(X)
+        else:
+            R = R - a * Q
+        Z = minv[:, None] * R
+        rho_new = np.sum(R * Z, axis=0)
+        relres = np.sqrt(np.sum(R * R)) / normB
+        if relres < tol:
+            return CGResult(X, it, relres, True)
+        b = np.where(rho > 0, rho_new / np.where(rho > 0, rho, 1.0), 0.0)
+        P = Z + b * P
+        rho = rho_new
+    return CGResult(X, it, relres, relres < tol)
+
+
 # --------------------------------------------------------------------------
 # Diagonal estimation (Sec. 3.1) and M-step (Eq. mstep with s).
 # --------------------------------------------------------------------------
@@ -254,6 +294,48 @@ def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
         stats.relres.append(res.relres)
         stats.clamps.append(clamps)
         stats.support.append(int(np.sum(alpha < support_threshold)))
+    return alpha, mu, s, stats
+
+
+def cofem_learned(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, predict,
+                  seed=0, alpha_init=1.0, den_floor=DEN_FLOOR, support_threshold=1e6):
+    """Algorithm 1 with a learned warm start and diagonal preconditioner: at
+    E-step t >= 2, (mu_hat, s_hat) = predict(alpha, mu_prev, s_prev); the
+    solve starts from X0 = [mu_hat | s_hat . p_k] with M^-1 = diag(s_hat);
+    if it has not reached cg_tol after cg_max_iters, plain CG from zero
+    (the paper's solver) is run instead.  Returns (alpha, mu, s, stats) with
+    stats.cg_iters the iterations of the accepted solve plus any fallback."""
+    y = np.asarray(y, dtype=np.float64)
+    alpha = np.broadcast_to(np.asarray(alpha_init, dtype=np.float64), (D,)).copy()
+    b = beta * phit(y)
+    stats = FitStats()
+    stats.fallbacks = []
+    mu = np.zeros(D)
+    s = np.zeros(D)
+    for t in range(1, em_iters + 1):
+        A = lambda X, al=alpha: apply_A(phi, phit, beta, al, X)
+        P = probe_matrix(seed, t, K, D)
+        B = np.concatenate([b[:, None], P], axis=1)
+        if t == 1:
+            res = cg_solve(A, B, cg_tol, cg_max_iters)
+            fb = 0
+        else:
+            mu_hat, s_hat = predict(alpha, mu, s)
+            X0 = np.concatenate([mu_hat[:, None], s_hat[:, None] * P], axis=1)
+            res = pcg_solve(A, B, X0, s_hat, cg_tol, cg_max_iters)
+            fb = 0
+            if not res.converged:
+                res2 = cg_solve(A, B, cg_tol, cg_max_iters)
+                res = CGResult(res2.X, res.iters + res2.iters, res2.relres, res2.converged)
+                fb = 1
+        mu = res.X[:, 0]
+        s = diag_estimate(P, res.X[:, 1:])
+        alpha, clamps = m_step(mu, s, den_floor)
+        stats.cg_iters.append(res.iters)
+        stats.relres.append(res.relres)
+        stats.clamps.append(clamps)
+        stats.support.append(int(np.sum(alpha < support_threshold)))
+        stats.fallbacks.append(fb)
     return alpha, mu, s, stats
 
 

@@ -149,3 +149,96 @@ def fit_batched(phis, ys, betas, seeds, p, ws=None, stream=None):
         offs.append(offs[-1] + int(P.shape[1]))
     cut = lambda t: [t[offs[i]:offs[i + 1]] for i in range(len(phis))]
     return cut(alpha), cut(mu), cut(s), stats
+
+
+# ---------------------------------------------------------------- learned path
+
+MLP_PARAMS = 1282
+_MLP_SHAPES = [(32, 4), (32,), (32, 32), (32,), (2, 32), (2,)]
+
+
+class LearnedWarmStart:
+    """Weights of the per-coordinate MLP on the device: FP32 master copy,
+    Adam moments and the BF16 copy the fit and the forward pass read."""
+
+    def __init__(self, seed=0, device="cuda"):
+        g = torch.Generator(device="cpu")
+        g.manual_seed(seed)
+        parts = []
+        for shp in _MLP_SHAPES:
+            if len(shp) == 2:     # Glorot uniform
+                lim = (6.0 / (shp[0] + shp[1])) ** 0.5
+                parts.append((torch.rand(shp, generator=g, dtype=torch.float64) * 2 - 1) * lim)
+            else:
+                parts.append(torch.zeros(shp, dtype=torch.float64))
+        self.master = torch.cat([p.reshape(-1) for p in parts]).float().to(device)
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.bf16 = self.master.to(torch.bfloat16)
+        self.step = 0
+
+    def train(self, U, Y, steps, lr=3e-3, batch=65536, stream=None, seed=0):
+        """Adam on (U, Y) (CUDA float32, n x 4 and n x 2) in contiguous batches of
+        a shuffled copy; returns the list of batch losses."""
+        n = U.shape[0]
+        g = torch.Generator(device=U.device)
+        g.manual_seed(seed)
+        perm = torch.randperm(n, device=U.device, generator=g)
+        Us, Ys = U[perm].contiguous(), Y[perm].contiguous()
+        nb = max(1, n // batch)
+        ws = torch.empty(B.cofem_mlp_train_workspace_bytes(min(batch, n)), dtype=torch.uint8,
+                         device=U.device)
+        loss = torch.zeros(steps, dtype=torch.float64, device=U.device)
+        for k in range(steps):
+            i = k % nb
+            b = min(batch, n)
+            self.step += 1
+            B.cofem_mlp_adam_step(self.master.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                  self.bf16.data_ptr(), Us[i * b:].data_ptr(), Ys[i * b:].data_ptr(),
+                                  b, self.step, lr, ws.data_ptr(), ws.numel(),
+                                  loss[k:].data_ptr(), _stream_ptr(stream))
+        return loss.cpu().tolist()
+
+    def forward(self, U, stream=None):
+        O = torch.empty((U.shape[0], 2), dtype=torch.float32, device=U.device)
+        B.cofem_mlp_forward(self.bf16.data_ptr(), B.COFEM_BF16, U.data_ptr(), U.shape[0],
+                            O.data_ptr(), _stream_ptr(stream))
+        return O
+
+
+def collect_training_data(op, y, beta, p, em_iters, stream=None):
+    """Runs plain CoFEM one EM iteration at a time and returns (U, Y) samples
+    of every coordinate for E-steps 2..em_iters: features from the alpha the
+    E-step used and the previous E-step's mu, s; targets from its own mu, s."""
+    dev = y.device
+    D = op.D
+    pn2 = torch.empty(D, dtype=torch.float32, device=dev)
+    B.cofem_op_col_norms(op.handle, pn2.data_ptr(), _stream_ptr(stream))
+    alpha = torch.empty(D, dtype=torch.float64, device=dev)
+    Us, Ys = [], []
+    mu_prev = s_prev = None
+    ws = None
+    for t in range(em_iters):
+        q = params(**{f: getattr(p, f) for f, _ in B.cofem_params._fields_})
+        q.em_iters = 1
+        q.t_offset = t
+        q.mlp = None
+        if ws is None:
+            ws = workspace(op, q, dev)
+        if t == 0:
+            alpha.fill_(q.alpha_init)
+        a_in = alpha.clone()
+        r = fit(op, y, beta, q, ws=ws, alpha=alpha, stream=stream)
+        if mu_prev is not None:
+            U = torch.empty((D, 4), dtype=torch.float32, device=dev)
+            Yt = torch.empty((D, 2), dtype=torch.float32, device=dev)
+            B.cofem_mlp_features(a_in.data_ptr(), pn2.data_ptr(), float(beta),
+                                 mu_prev.data_ptr(), s_prev.data_ptr(), D, U.data_ptr(),
+                                 _stream_ptr(stream))
+            B.cofem_mlp_targets(a_in.data_ptr(), pn2.data_ptr(), float(beta), r.mu.data_ptr(),
+                                r.s.data_ptr(), D, Yt.data_ptr(), _stream_ptr(stream))
+            Us.append(U)
+            Ys.append(Yt)
+        mu_prev, s_prev = r.mu.clone(), r.s.clone()
+        alpha = r.alpha
+    return torch.cat(Us), torch.cat(Ys)

@@ -36,7 +36,8 @@ class cofem_params(ctypes.Structure):
                 ("resid_replace_every", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("alpha_init", ctypes.c_double),
                 ("den_floor", ctypes.c_double), ("support_threshold", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int64),
+                ("mlp", ctypes.c_void_p)]
 
 
 class cofem_stats(ctypes.Structure):
@@ -73,6 +74,15 @@ _SIGS = {
     "cofem_op_dense_attach_packed": (_S, [_P, _P, _SZ, _P]),
     "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
     "cofem_op_destroy": (None, [_P]),
+    "cofem_last_fit_fallbacks": (_I32, []),
+    "cofem_op_col_norms": (_S, [_P, _P, _P]),
+    "cofem_mlp_features": (_S, [_P, _P, _D, _P, _P, _I64, _P, _P]),
+    "cofem_mlp_targets": (_S, [_P, _P, _D, _P, _P, _I64, _P, _P]),
+    "cofem_mlp_forward": (_S, [_P, _S, _P, _I64, _P, _P]),
+    "cofem_mlp_train_workspace_bytes": (_SZ, [_I64]),
+    "cofem_mlp_grad": (_S, [_P, _S, _P, _P, _I64, _P, _P, _P, _SZ, _P]),
+    "cofem_mlp_adam_step": (_S, [_P, _P, _P, _P, _P, _P, _I64, _I32, ctypes.c_float, _P, _SZ,
+                                 _P, _P]),
     "cofem_op_shape": (_S, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "cofem_params_default": (None, [ctypes.POINTER(cofem_params)]),
     "cofem_workspace_bytes": (_S, [_P, ctypes.POINTER(cofem_params), ctypes.POINTER(_SZ)]),
@@ -302,3 +312,44 @@ def cofem_diag_mstep(seed, t, K, D, vec, x_ptr, ld, den_floor, support_threshold
     _check(lib().cofem_diag_mstep(seed, t, K, D, vec, x_ptr, ld, den_floor, support_threshold,
                                   mu_ptr, s_ptr, alpha_ptr, counts_ptr, stream),
            "cofem_diag_mstep")
+
+
+# ------------------------------------------------------------ learned path
+
+def cofem_last_fit_fallbacks():
+    return lib().cofem_last_fit_fallbacks()
+
+
+def cofem_op_col_norms(op, out_ptr, stream=0):
+    _check(lib().cofem_op_col_norms(op, out_ptr, stream), "cofem_op_col_norms")
+
+
+def cofem_mlp_features(alpha_ptr, pn2_ptr, beta, mu_prev_ptr, s_prev_ptr, D, U_ptr, stream=0):
+    _check(lib().cofem_mlp_features(alpha_ptr, pn2_ptr, beta, mu_prev_ptr, s_prev_ptr, D, U_ptr,
+                                    stream), "cofem_mlp_features")
+
+
+def cofem_mlp_targets(alpha_ptr, pn2_ptr, beta, mu_ptr, s_ptr, D, Y_ptr, stream=0):
+    _check(lib().cofem_mlp_targets(alpha_ptr, pn2_ptr, beta, mu_ptr, s_ptr, D, Y_ptr, stream),
+           "cofem_mlp_targets")
+
+
+def cofem_mlp_forward(w_ptr, wdtype, U_ptr, n, O_ptr, stream=0):
+    _check(lib().cofem_mlp_forward(w_ptr, wdtype, U_ptr, n, O_ptr, stream), "cofem_mlp_forward")
+
+
+def cofem_mlp_train_workspace_bytes(n):
+    return lib().cofem_mlp_train_workspace_bytes(n)
+
+
+def cofem_mlp_grad(w_ptr, wdtype, U_ptr, Y_ptr, n, grad_ptr, loss_ptr, ws_ptr, ws_bytes,
+                   stream=0):
+    _check(lib().cofem_mlp_grad(w_ptr, wdtype, U_ptr, Y_ptr, n, grad_ptr, loss_ptr, ws_ptr,
+                                ws_bytes, stream), "cofem_mlp_grad")
+
+
+def cofem_mlp_adam_step(master_ptr, m_ptr, v_ptr, wbf_ptr, U_ptr, Y_ptr, n, step, lr, ws_ptr,
+                        ws_bytes, loss_ptr=None, stream=0):
+    _check(lib().cofem_mlp_adam_step(master_ptr, m_ptr, v_ptr, wbf_ptr, U_ptr, Y_ptr, n, step,
+                                     lr, ws_ptr, ws_bytes, loss_ptr, stream),
+           "cofem_mlp_adam_step")

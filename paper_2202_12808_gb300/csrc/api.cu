@@ -225,7 +225,8 @@ static int64_t op_D(const cofem_op* op) {
 // --------------------------------------------------------------- layout
 
 struct FitLayout {
-  size_t ctl, sc, pdots, pvec, X, R, P, Q, b, st_iters, st_relres, st_clamps, st_support, opws;
+  size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, X, R, P, Q, b, st_iters, st_relres,
+      st_clamps, st_support, opws;
   size_t total;
   int64_t ld;
 };
@@ -242,6 +243,10 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   L.sc = o; o += align256(sizeof(CgScalars));
   L.pdots = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
   L.pvec = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
+  L.pvec2 = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
+  L.pvec3 = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
+  L.minv = o; o += align256((size_t)L.ld * sizeof(float));
+  L.pn2 = o; o += align256((size_t)L.ld * sizeof(float));
   L.X = o; o += blk;
   L.R = o; o += blk;
   L.P = o; o += blk;
@@ -268,8 +273,12 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (!(p->cg_tol >= 0.0) || !(p->den_floor > 0.0)) return COFEM_ERR_INVALID_ARG;
   if (p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
   if (!op_supports(op, p->vec_dtype)) return COFEM_ERR_UNSUPPORTED;
+  if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
+
+static thread_local int g_last_fallbacks = 0;
+cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- graph
 
@@ -311,6 +320,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   CgScalars* sc = (CgScalars*)(ws + L.sc);
   double* pdots = (double*)(ws + L.pdots);
   double* pvec = (double*)(ws + L.pvec);
+  double* pvec2 = (double*)(ws + L.pvec2);
+  double* pvec3 = (double*)(ws + L.pvec3);
   V* X = (V*)(ws + L.X);
   V* R = (V*)(ws + L.R);
   V* P = (V*)(ws + L.P);
@@ -353,7 +364,26 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   CK(cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault));
   cf.while_handle = (unsigned long long)hw;
 
-  launch_cg_init<V>(cf, ctl, sc, X, R, P, b, pvec, cs);
+  const bool learned = p->mlp != nullptr;
+  cudaGraphConditionalHandle hf = 0;
+  if (learned) {
+    // warm start X0 and M^-1 from the network; Q = A X0; preconditioned start
+    CK(cudaGraphConditionalHandleCreate(&hf, g, 0, cudaGraphCondAssignDefault));
+    cf.fallback_handle = (unsigned long long)hf;
+    cf.minv = (const float*)(ws + L.minv);
+    if constexpr (sizeof(V) == 4) {
+      launch_warm_start(cf, ctl, (long long)(p->t_offset + 1), (const __nv_bfloat16*)p->mlp,
+                        alpha, (const float*)(ws + L.pn2), mu, s, (float*)X,
+                        (float*)(ws + L.minv), cs);
+    }
+    CKL();
+    cofem_status rw = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws,
+                               cs, &ctl->error, 0u);
+    if (rw != COFEM_OK) return rw;
+    launch_cg_init_warm<V>(cf, ctl, sc, X, R, P, Q, b, pvec, pvec2, pvec3, cs);
+  } else {
+    launch_cg_init<V>(cf, ctl, sc, X, R, P, b, pvec, cs);
+  }
   CKL();
   cudaGraph_t body = nullptr;
   cofem_status rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &body);
@@ -373,7 +403,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                   &ctl->error, cf.split_nt > 0 ? kApplyPresplit : 0u);
     if (rc != COFEM_OK) return rc;
     cf.gamma_parts = nparts;
-    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, bs);
+    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, bs);
     CKL();
     if (p->resid_replace_every > 0) {
       cudaGraph_t ibody = nullptr;
@@ -384,7 +414,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is,
                     &ctl->error, 0u);
       if (rc != COFEM_OK) return rc;
-      launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, is);
+      launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, pvec2, is);
       CKL();
       cudaGraph_t tmp;
       CK(cudaStreamEndCapture(is, &tmp));
@@ -393,6 +423,42 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CKL();
     cudaGraph_t tmp;
     CK(cudaStreamEndCapture(bs, &tmp));
+  }
+
+  // ---- learned path: plain CG from zero when the preconditioned solve failed
+  if (learned) {
+    cudaGraph_t fbody = nullptr;
+    rc = add_conditional(cs, hf, cudaGraphCondTypeIf, &fbody);
+    if (rc != COFEM_OK) return rc;
+    cudaStream_t fs = ss.s[1];
+    CK(cudaStreamBeginCaptureToGraph(fs, fbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaGraphConditionalHandle hw2;
+    CK(cudaGraphConditionalHandleCreate(&hw2, fbody, 0, cudaGraphCondAssignDefault));
+    CgConf pf = cf;
+    pf.minv = nullptr;
+    pf.fallback_handle = 0;
+    pf.fallback_init = 1;
+    pf.while_handle = (unsigned long long)hw2;
+    pf.if_handle = 0;
+    pf.replace_every = 0;
+    launch_cg_init<V>(pf, ctl, sc, X, R, P, b, pvec, fs);
+    CKL();
+    cudaGraph_t fwhile = nullptr;
+    rc = add_conditional(fs, hw2, cudaGraphCondTypeWhile, &fwhile);
+    if (rc != COFEM_OK) return rc;
+    cudaStream_t ws2 = ss.s[2];
+    CK(cudaStreamBeginCaptureToGraph(ws2, fwhile, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int np2 = 0;
+    rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &np2, opws, ws2, &ctl->error,
+                  pf.split_nt > 0 ? kApplyPresplit : 0u);
+    if (rc != COFEM_OK) return rc;
+    pf.gamma_parts = np2;
+    launch_cg_update<V>(pf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, ws2);
+    launch_cg_direction<V>(pf, ctl, sc, R, P, ws2);
+    CKL();
+    cudaGraph_t tmp1, tmp2;
+    CK(cudaStreamEndCapture(ws2, &tmp1));
+    CK(cudaStreamEndCapture(fs, &tmp2));
   }
 
   // ---- after the solve: diagonal estimate + M-step + statistics
@@ -427,6 +493,10 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
   cofem_status rc = op_adjoint(op, p->vec_dtype, y, N, 1, ws + L.b, L.ld, beta, ws + L.opws, st);
   if (rc != COFEM_OK) return rc;
 
+  if (p->mlp) {
+    rc = mlp_col_norms(op, (float*)(ws + L.pn2), st);
+    if (rc != COFEM_OK) return rc;
+  }
   if (p->em_iters > 0) {
     cudaGraphExec_t exec = nullptr;
     rc = build_em_graph<V>(op, p, beta, ws, L, mu, s, alpha, &exec);
@@ -453,6 +523,7 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
   }
   CgCtl hctl;
   CK(cudaMemcpy(&hctl, ws + L.ctl, sizeof(hctl), cudaMemcpyDeviceToHost));
+  g_last_fallbacks = hctl.fallbacks;
   if (stats && p->em_iters > 0) {
     const int n = p->em_iters;
     if (stats->cg_iters) CK(cudaMemcpy(stats->cg_iters, ws + L.st_iters, 4 * n, cudaMemcpyDeviceToHost));
@@ -486,6 +557,8 @@ const char* cofem_status_string(cofem_status s) {
 }
 
 const char* cofem_last_error(void) { return g_last_error.c_str(); }
+
+int32_t cofem_last_fit_fallbacks(void) { return g_last_fallbacks; }
 
 cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void* phi_dev,
                             int64_t ld, const float* tile_scales_dev, cofem_op** out) {
@@ -762,6 +835,16 @@ cofem_status apply_with_scratch(const cofem_op* op, cofem_dtype vec, const void*
 }
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+int op_is_dense(const cofem_op* op) { return op->kind == 0; }
+DenseDesc op_dense_desc(const cofem_op* op) { return op->dense; }
+int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h) {
+  *L = op->L;
+  *C = op->C;
+  *T = op->T;
+  *h = op->filters;
+  return 0;
+}
 
 }  // namespace cofem
 

@@ -75,7 +75,7 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int j = 0; j < cf.ncols; ++j) tot += sc->rho_new[j];
+    for (int j = 0; j < cf.ncols; ++j) tot += cf.minv ? sc->rr_new[j] : sc->rho_new[j];
     const double relres = sqrt(tot) / sqrt(ctl->normB2);
     ctl->relres = relres;
     const int it = ctl->iter;
@@ -90,6 +90,8 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
     }
     ctl->done = done;
     set_cond(cf.while_handle, done ? 0u : 1u);
+    if (done && cf.fallback_handle)
+      set_cond(cf.fallback_handle, (cf.fixed_iters == 0 && !(relres < cf.tol)) ? 1u : 0u);
   }
 }
 
@@ -156,6 +158,10 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
       const double n2 = b2 + (double)cf.K * (double)cf.D;
       ctl->normB2 = n2;
       ctl->relres = n2 > 0.0 ? 1.0 : 0.0;
+      if (cf.fallback_init) {
+        ctl->extra_iters = ctl->iter;
+        ctl->fallbacks += 1;
+      }
       ctl->iter = 0;
       ctl->replace = 0;
       ctl->clamps = 0;
@@ -171,12 +177,91 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
   }
 }
 
+// ------------------------------------------ preconditioned start from X0
+// Q = A X0 given; R = B - Q, Z = M^-1 R, P = Z; rho_j = r_j^T z_j; the stop
+// test uses ||R||_F / ||B||_F.  ctl->iter = 0.
+template <typename V>
+__global__ void cg_init_warm_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const V* X, V* R,
+                                    V* P, const V* Q, const V* bvec, double* pz, double* pr,
+                                    double* pb) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[32];
+  const int j = blockIdx.y;
+  const uint64_t key = probe_key(cf.seed, ctl->t);
+  double az = 0.0, ar = 0.0, ab = 0.0;
+  V* r = R + (int64_t)j * cf.ld;
+  V* p = P + (int64_t)j * cf.ld;
+  const V* q = Q + (int64_t)j * cf.ld;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.ld;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V bv = V(0);
+    if (d < cf.D) {
+      if (j == 0) bv = bvec[d];
+      else {
+        const int k = j - 1;
+        const uint64_t h = probe_word(key, d, k >> 6);
+        bv = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
+      }
+    }
+    const V rv = d < cf.D ? bv - q[d] : V(0);
+    const V zv = rv * (V)cf.minv[d];
+    r[d] = rv;
+    p[d] = zv;
+    if (cf.split_nt > 0) write_split(cf, j, d, zv);
+    az += (double)rv * (double)zv;
+    ar += (double)rv * (double)rv;
+    if (j == 0) ab += (double)bv * (double)bv;
+  }
+  const double sz = block_sum(az, sh);
+  const double sr = block_sum(ar, sh);
+  const double sb = block_sum(ab, sh);
+  if (threadIdx.x == 0) {
+    pz[(int64_t)blockIdx.x * kMaxCols + j] = sz;
+    pr[(int64_t)blockIdx.x * kMaxCols + j] = sr;
+    if (j == 0) pb[blockIdx.x] = sb;
+  }
+  if (arrive_last(&ctl->counter[0])) {
+    if (threadIdx.x < cf.ncols) {
+      double tz = 0.0, tr = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) {
+        tz += pz[(int64_t)i * kMaxCols + threadIdx.x];
+        tr += pr[(int64_t)i * kMaxCols + threadIdx.x];
+      }
+      sc->rho[threadIdx.x] = tz;
+      sc->rr_new[threadIdx.x] = tr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b2 = 0.0, r2 = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) b2 += pb[i];
+      for (int jj = 0; jj < cf.ncols; ++jj) r2 += sc->rr_new[jj];
+      const double n2 = b2 + (double)cf.K * (double)cf.D;
+      ctl->normB2 = n2;
+      const double relres = n2 > 0.0 ? sqrt(r2) / sqrt(n2) : 0.0;
+      ctl->relres = relres;
+      ctl->iter = 0;
+      ctl->extra_iters = 0;
+      ctl->replace = 0;
+      ctl->clamps = 0;
+      ctl->support = 0;
+      int done = !(n2 > 0.0) || relres < cf.tol;
+      if (!isfinite(n2) || !isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+      ctl->done = done;
+      set_cond(cf.while_handle, done ? 0u : 1u);
+      set_cond(cf.fallback_handle, 0u);
+      ctl->counter[0] = 0;
+    }
+  }
+}
+
 // --------------------------------------- x += a p, r -= a q, rho_new = r^T r
 // a_j = rho_j / gamma_j with gamma_j the fixed-order sum of the operator's
 // per-block partials of p_j^T A p_j (every block computes the same value).
 template <typename V>
 __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
-                                 const V* P, const V* Q, const double* gparts, double* part) {
+                                 const V* P, const V* Q, const double* gparts, double* part,
+                                 double* part2) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[32];
@@ -208,7 +293,7 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   V* r = R + (int64_t)j * cf.ld;
   const V* p = P + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
-  double acc = 0.0;
+  double acc = 0.0, accz = 0.0;
   for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W; d < cf.ld;
        d += (int64_t)gridDim.x * blockDim.x * W) {
     V xv[W], rv[W], pv[W], qv[W];
@@ -218,16 +303,27 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
       xv[i] = fma(a, pv[i], xv[i]);
       rv[i] = fma(-a, qv[i], rv[i]);
       acc += (double)rv[i] * (double)rv[i];
+      if (cf.minv) accz += (double)rv[i] * (double)rv[i] * (double)cf.minv[d + i];
     }
     vstore(x + d, xv); vstore(r + d, rv);
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
+  if (cf.minv) {
+    const double sz = block_sum(accz, sh);
+    if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
+  }
   if (arrive_last(&ctl->counter[1])) {
     if (threadIdx.x < cf.ncols) {
-      double t = 0.0;
+      double t = 0.0, tz = 0.0;
       for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
-      sc->rho_new[threadIdx.x] = t;
+      if (cf.minv) {
+        for (int i = 0; i < (int)gridDim.x; ++i) tz += part2[(int64_t)i * kMaxCols + threadIdx.x];
+        sc->rr_new[threadIdx.x] = t;
+        sc->rho_new[threadIdx.x] = tz;
+      } else {
+        sc->rho_new[threadIdx.x] = t;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -245,7 +341,7 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
 // ------------------------------ residual replacement: r = B - Q (Q = A x)
 template <typename V>
 __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
-                                     const V* Q, const V* bvec, double* part) {
+                                     const V* Q, const V* bvec, double* part, double* part2) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[32];
@@ -254,7 +350,7 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
   const uint64_t key = probe_key(cf.seed, ctl->t);
   V* r = R + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
-  double acc = 0.0;
+  double acc = 0.0, accz = 0.0;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
     V bv;
@@ -267,14 +363,25 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
     const V rv = bv - q[d];
     r[d] = rv;
     acc += (double)rv * (double)rv;
+    if (cf.minv) accz += (double)rv * (double)rv * (double)cf.minv[d];
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
+  if (cf.minv) {
+    const double sz = block_sum(accz, sh);
+    if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
+  }
   if (arrive_last(&ctl->counter[2])) {
     if (threadIdx.x < cf.ncols) {
-      double t = 0.0;
+      double t = 0.0, tz = 0.0;
       for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
-      sc->rho_new[threadIdx.x] = t;
+      if (cf.minv) {
+        for (int i = 0; i < (int)gridDim.x; ++i) tz += part2[(int64_t)i * kMaxCols + threadIdx.x];
+        sc->rr_new[threadIdx.x] = t;
+        sc->rho_new[threadIdx.x] = tz;
+      } else {
+        sc->rho_new[threadIdx.x] = t;
+      }
     }
     if (threadIdx.x == 0) { ctl->counter[2] = 0; ctl->replace = 0; }
     cg_finalize(cf, ctl, sc);
@@ -297,6 +404,10 @@ __global__ void cg_direction_kernel(CgConf cf, const CgCtl* ctl, const CgScalars
        d += (int64_t)gridDim.x * blockDim.x * W) {
     V rv[W], pv[W];
     vload(r + d, rv); vload(p + d, pv);
+    if (cf.minv) {
+#pragma unroll
+      for (int i = 0; i < W; ++i) rv[i] = rv[i] * (V)cf.minv[d + i];
+    }
 #pragma unroll
     for (int i = 0; i < W; ++i) pv[i] = fma(b, pv[i], rv[i]);
     vstore(p + d, pv);
@@ -355,7 +466,7 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
     if (threadIdx.x == 0) {
       const int e = ctl->em_index;
       if (e < cf.em_iters) {
-        st_iters[e] = ctl->iter;
+        st_iters[e] = ctl->iter + ctl->extra_iters;
         st_relres[e] = ctl->relres;
         st_clamps[e] = ctl->clamps;
         st_support[e] = ctl->support;
@@ -405,16 +516,28 @@ void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* 
 
 template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
-                      const V* Q, const double* gparts, double* part, cudaStream_t st) {
+                      const V* Q, const double* gparts, double* part, double* part2,
+                      cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
-  launch_k(cg_update_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts, part);
+  launch_k(cg_update_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts, part,
+           part2);
+}
+
+template <typename V>
+void launch_cg_init_warm(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const V* X, V* R, V* P,
+                         const V* Q, const V* bvec, double* pz, double* pr, double* pb,
+                         cudaStream_t st) {
+  dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
+  launch_k(cg_init_warm_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, bvec, pz,
+           pr, pb);
 }
 
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
-                          const V* bvec, double* part, cudaStream_t st) {
+                          const V* bvec, double* part, double* part2, cudaStream_t st) {
   dim3 g(vec_blocks(cf.ld, 1, cf.ncols, num_sms()), cf.ncols);
-  launch_k(cg_true_resid_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, R, Q, bvec, part);
+  launch_k(cg_true_resid_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, R, Q, bvec, part,
+           part2);
 }
 
 template <typename V>
@@ -447,9 +570,13 @@ void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
   template void launch_cg_init<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, V*,         \
                                   const V*, double*, cudaStream_t);                     \
   template void launch_cg_update<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, const V*, \
-                                    const V*, const double*, double*, cudaStream_t);    \
+                                    const V*, const double*, double*, double*,          \
+                                    cudaStream_t);                                      \
+  template void launch_cg_init_warm<V>(const CgConf&, CgCtl*, CgScalars*, const V*, V*,  \
+                                       V*, const V*, const V*, double*, double*,        \
+                                       double*, cudaStream_t);                          \
   template void launch_cg_true_resid<V>(const CgConf&, CgCtl*, CgScalars*, V*, const V*, \
-                                        const V*, double*, cudaStream_t);               \
+                                        const V*, double*, double*, cudaStream_t);      \
   template void launch_cg_direction<V>(const CgConf&, const CgCtl*, const CgScalars*,    \
                                        const V*, V*, cudaStream_t);                     \
   template void launch_diag_mstep<V>(const CgConf&, CgCtl*, uint64_t, const V*, double*, \

@@ -25,7 +25,9 @@ struct CgCtl {
   int em_index;        // index of the current E-step in the stats arrays
   int clamps;          // M-step counters of the current EM iteration
   int support;
-  int pad0;
+  int extra_iters;     // learned path: iterations of a preconditioned solve that fell back
+  int fallbacks;       // learned path: fallbacks to plain CG so far
+  int pad1;
   double normB2;       // ||B||_F^2
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
@@ -38,6 +40,7 @@ struct CgScalars {
   double gamma[kMaxCols];    // p_j^T A p_j
   double a[kMaxCols];        // step sizes
   double b[kMaxCols];        // direction updates
+  double rr_new[kMaxCols];   // preconditioned CG: r_j^T r_j (rho holds r_j^T z_j)
 };
 
 // Static problem description passed by value to the CG kernels.
@@ -61,6 +64,9 @@ struct CgConf {
   int split_nt;                      // >0: also write P's BF16 terms (tensor-core operator)
   int split_rows;                    // rows of the split buffer (B operand rows)
   void* split_buf;                   // row split_row(j, t), pitch ld, bf16
+  const float* minv;                 // preconditioned CG: M^-1 = diag(minv), else null
+  unsigned long long fallback_handle;  // IF node: preconditioned solve did not converge
+  int fallback_init;                 // this init restarts plain CG after a fallback
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

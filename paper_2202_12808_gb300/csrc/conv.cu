@@ -16,6 +16,10 @@
 #include "kernels.cuh"
 
 namespace cofem {
+void apply_tick(cudaStream_t st);
+}
+
+namespace cofem {
 
 constexpr int kConvThreads = 256;
 constexpr int kConvR = 8;
@@ -157,6 +161,7 @@ void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ld
                   float* W, int64_t ldw, cudaStream_t st) {
   dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
   launch_k(conv_forward_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, Z, ldz, W, ldw);
+  apply_tick(st);
 }
 
 int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
@@ -165,6 +170,7 @@ int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw
   dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
   launch_k(conv_adjoint_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, W, ldw, Y, ld, beta,
                                                             alpha, X, dots);
+  apply_tick(st);
   return (int)g.x;
 }
 

@@ -14,10 +14,19 @@ void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* 
                     const V* bvec, double* part, cudaStream_t st);
 template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
-                      const V* Q, const double* gparts, double* part, cudaStream_t st);
+                      const V* Q, const double* gparts, double* part, double* part2,
+                      cudaStream_t st);
+template <typename V>
+void launch_cg_init_warm(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const V* X, V* R, V* P,
+                         const V* Q, const V* bvec, double* pz, double* pr, double* pb,
+                         cudaStream_t st);
+void launch_warm_start(const CgConf& cf, const CgCtl* ctl, long long t_first,
+                       const __nv_bfloat16* w, const double* alpha, const float* pn2,
+                       const double* mu_prev, const double* s_prev, float* X, float* minv,
+                       cudaStream_t st);
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
-                          const V* bvec, double* part, cudaStream_t st);
+                          const V* bvec, double* part, double* part2, cudaStream_t st);
 template <typename V>
 void launch_cg_direction(const CgConf& cf, const CgCtl* ctl, const CgScalars* sc,
                          const V* R, V* P, cudaStream_t st);

@@ -111,8 +111,37 @@ CONFIGS = {
     "dense-n4096-d32768": dict(N=4096, D=32768, n_nonzero=655, sigma=0.01, K=32,
                                em_iters=100, cg_tol=1e-5, cg_max_iters=400,
                                resid_replace_every=50),
+    # Batched: 512 dense problems, N uniform on [128, 2048], D = 4N, BF16,
+    # 5% nonzeros, sigma 0.01, K=16, 50 EM iterations, CG tol 1e-5.
+    "batched-512-n128-2048": dict(n_problems=512, n_min=128, n_max=2048, ratio=4,
+                                  frac_nonzero=0.05, sigma=0.01, K=16, em_iters=50,
+                                  cg_tol=1e-5, cg_max_iters=400),
     # Convolutional: L = 2^20, 8 filters x 64 taps, 0.1% nonzeros Laplace,
     # sigma 0.05, K=16, 30 EM iterations.
     "conv-l1m-c8-t64": dict(L=1 << 20, C=8, T=64, density=1e-3, sigma=0.05, K=16,
                             em_iters=30, cg_tol=1e-5, cg_max_iters=400),
 }
+
+
+def batched_problems_torch(n_problems, n_min, n_max, ratio, frac_nonzero, sigma, seed,
+                           device="cuda"):
+    """Many dense problems (N_i uniform on [n_min, n_max], D_i = ratio N_i,
+    Phi_i iid N(0, 1/N_i) in BF16, a fraction of nonzeros with N(0,1)
+    amplitudes, y_i = Phi_i z_i + N(0, sigma^2)) drawn on the device with a
+    seeded torch generator per problem (host generation of the 3 G entries of
+    the 512-problem workload would take minutes).  Returns a list of
+    (Phi_i bf16 N_i x D_i, z_i float64, y_i float32, beta, seed_i)."""
+    import torch
+    out = []
+    for N, D, s in batched_sizes(n_problems, n_min, n_max, ratio, seed):
+        g = torch.Generator(device=device)
+        g.manual_seed(s)
+        Phi = (torch.randn((N, D), generator=g, device=device) / float(np.sqrt(N))).to(torch.bfloat16)
+        k = max(1, int(round(frac_nonzero * D)))
+        idx = torch.randperm(D, generator=g, device=device)[:k]
+        z = torch.zeros(D, dtype=torch.float64, device=device)
+        z[idx] = torch.randn(k, generator=g, device=device, dtype=torch.float64)
+        noise = sigma * torch.randn(N, generator=g, device=device, dtype=torch.float64)
+        y = (Phi.double()[:, idx] @ z[idx] + noise).float()
+        out.append((Phi, z, y, 1.0 / sigma ** 2, s))
+    return out

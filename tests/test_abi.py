@@ -43,7 +43,7 @@ def test_params_default_matches_header(built):
     assert (p.K, p.em_iters, p.cg_max_iters, p.fixed_cg_iters, p.resid_replace_every) == (20, 50, 400, 0, 0)
     assert p.vec_dtype == B.COFEM_F32
     assert (p.cg_tol, p.alpha_init, p.den_floor, p.support_threshold) == (1e-6, 1.0, 1e-12, 1e6)
-    assert ctypes.sizeof(B.cofem_params) == 6 * 4 + 4 * 8 + 8 + 8
+    assert ctypes.sizeof(B.cofem_params) == 6 * 4 + 4 * 8 + 8 + 8 + 8
 
 
 def test_invalid_operator_arguments(built):

@@ -336,3 +336,40 @@ def test_datagen_conv_observation_matches_operator():
     p = datagen.conv_problem(256, 4, 16, 0.02, 0.0, seed=3)
     phi, _, _ = sbl.conv_dictionary(p.h.astype(np.float64), 256)
     np.testing.assert_allclose(phi(p.z.reshape(-1)), p.y, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------- preconditioned CG (learned path)
+
+def test_pcg_identity_preconditioner_is_cg():
+    Phi, alpha = _spd_problem(60, 90, 3)
+    phi, phit, D = sbl.dense_dictionary(Phi)
+    A = lambda X: sbl.apply_A(phi, phit, 2.0, alpha, X)
+    B = np.random.default_rng(1).standard_normal((90, 4))
+    r1 = sbl.cg_solve(A, B, 1e-10, 500)
+    r2 = sbl.pcg_solve(A, B, np.zeros_like(B), np.ones(90), 1e-10, 500)
+    assert r1.iters == r2.iters and np.array_equal(r1.X, r2.X)
+
+
+def test_pcg_exact_diagonal_preconditioner_one_step():
+    d = np.linspace(1, 100, 40)
+    B = np.random.default_rng(2).standard_normal((40, 3))
+    res = sbl.pcg_solve(lambda X: d[:, None] * X, B, np.zeros_like(B), 1.0 / d, 1e-13, 10)
+    assert res.iters == 1
+    np.testing.assert_allclose(res.X, B / d[:, None], rtol=1e-13)
+
+
+def test_pcg_matches_cholesky_and_exact_start():
+    Phi, alpha = _spd_problem(80, 120, 4, alpha_spread=(0.1, 10.0))
+    beta = 5.0
+    Am = beta * Phi.T @ Phi + np.diag(alpha)
+    phi, phit, _ = sbl.dense_dictionary(Phi)
+    A = lambda X: sbl.apply_A(phi, phit, beta, alpha, X)
+    B = np.random.default_rng(5).standard_normal((120, 3))
+    X_ref = np.linalg.solve(Am, B)
+    minv = 1.0 / np.diag(Am)
+    res = sbl.pcg_solve(A, B, np.random.default_rng(6).standard_normal((120, 3)), minv,
+                        1e-13, 1000)
+    assert res.converged
+    assert np.linalg.norm(res.X - X_ref) / np.linalg.norm(X_ref) <= 1e-10
+    res0 = sbl.pcg_solve(A, B, X_ref, minv, 1e-9, 10)
+    assert res0.iters == 0

@@ -50,7 +50,7 @@ def parse():
                     help="skip the operator pipeline autotuner (library defaults)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched-512-n128-2048", "conv-l1m-c8-t64",
-                             "dense-fp64-n256-d1024"],
+                             "dense-fp64-n256-d1024", "learned-dense-n256-d1024"],
                     help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -349,6 +349,83 @@ def run_fp64(args):
                           "kernel": "whole CG loop (Phi in L2)"}})
 
 
+def run_learned(args):
+    """Learned warm start / preconditioner: train on E-steps 2..20 of the
+    256 x 1024 problems with seeds 1..64, evaluate CG iterations and EM
+    iterations per second against plain CG on seeds 100..115 (and on the
+    convolutional workload with the same network)."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    c = datagen.CONFIGS["dense-fp64-n256-d1024"]
+
+    def prob(sd):
+        pr = datagen.dense_problem(c["N"], c["D"], c["n_nonzero"], c["sigma"], sd)
+        return pr, api.DenseOperator(torch.from_numpy(pr.Phi).cuda()), \
+            torch.from_numpy(pr.y.astype(np.float32)).cuda()
+
+    kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"])
+    t0 = time.perf_counter()
+    Us, Ys = [], []
+    for sd in range(1, 65):
+        pr, op, y = prob(sd)
+        U, Y = api.collect_training_data(op, y, pr.beta, api.params(em_iters=20, seed=sd, **kw), 20)
+        Us.append(U)
+        Ys.append(Y)
+    U, Y = torch.cat(Us), torch.cat(Ys)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    net = api.LearnedWarmStart(seed=0)
+    t0 = time.perf_counter()
+    losses = net.train(U, Y, 4000, lr=3e-3, batch=65536)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    em = c["em_iters"]
+    res = {"plain": [], "learned": []}
+    times = {"plain": 0.0, "learned": 0.0}
+    fallbacks, mu_diff = 0, 0.0
+    for sd in range(100, 116):
+        pr, op, y = prob(sd)
+        p = api.params(em_iters=em, seed=sd, **kw)
+        ws = api.workspace(op, p)
+        rp, tp = _timed(lambda: api.fit(op, y, pr.beta, p, ws=ws))
+        p.mlp = net.bf16.data_ptr()
+        rl, tl = _timed(lambda: api.fit(op, y, pr.beta, p, ws=ws))
+        fallbacks += B.cofem_last_fit_fallbacks()
+        res["plain"].append(sum(rp.stats["cg_iters"]))
+        res["learned"].append(sum(rl.stats["cg_iters"]))
+        times["plain"] += tp
+        times["learned"] += tl
+        mu_diff = max(mu_diff, (rl.mu - rp.mu).norm().item() / rp.mu.norm().item())
+    n_eval = 16 * em
+    # transfer: the same network on the convolutional workload (10 EM iterations)
+    cc = datagen.CONFIGS["conv-l1m-c8-t64"]
+    cp = datagen.conv_problem(cc["L"], cc["C"], cc["T"], cc["density"], cc["sigma"], 0)
+    cop = api.ConvOperator(torch.from_numpy(cp.h).cuda(), cc["L"])
+    cy = torch.from_numpy(cp.y.astype(np.float32)).cuda()
+    q = api.params(vec_dtype=B.COFEM_F32, K=cc["K"], em_iters=10, cg_tol=cc["cg_tol"],
+                   cg_max_iters=cc["cg_max_iters"], seed=0)
+    cws = api.workspace(cop, q)
+    rcp, tcp = _timed(lambda: api.fit(cop, cy, cp.beta, q, ws=cws))
+    q.mlp = net.bf16.data_ptr()
+    rcl, tcl = _timed(lambda: api.fit(cop, cy, cp.beta, q, ws=cws))
+    conv_fb = B.cofem_last_fit_fallbacks()
+    _common(args, "EM iters/s with the learned warm start (dense N=256 D=1024 K=20, tol 1e-6)",
+            "EM iters/s", n_eval / times["learned"], times["learned"], "f32 vectors, f32 Phi",
+            {"workload": "learned-dense-n256-d1024", "train_seeds": "1..64",
+             "train_estep": "2..20", "eval_seeds": "100..115", "em_iters": em},
+            {"plain_em_iters_per_s": n_eval / times["plain"],
+             "cg_iters_total": {"plain": int(sum(res["plain"])), "learned": int(sum(res["learned"]))},
+             "cg_iters_ratio": float(sum(res["learned"]) / sum(res["plain"])),
+             "fallbacks": int(fallbacks), "max_mu_rel_diff_vs_plain": mu_diff,
+             "training": {"samples": int(U.shape[0]), "collect_s": t_collect, "train_s": t_train,
+                          "adam_steps": 4000, "loss_first": losses[0], "loss_last": losses[-1]},
+             "conv_transfer": {"cg_iters_plain": rcp.stats["cg_iters"],
+                               "cg_iters_learned": rcl.stats["cg_iters"],
+                               "seconds_plain": tcp, "seconds_learned": tcl,
+                               "fallbacks": int(conv_fb)}})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -360,6 +437,8 @@ def main():
         return run_conv(args)
     if args.workload == "dense-fp64-n256-d1024":
         return run_fp64(args)
+    if args.workload == "learned-dense-n256-d1024":
+        return run_learned(args)
     import torch
     import torch.distributed as dist
     from paper_2202_12808_gb300 import api

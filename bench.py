@@ -64,6 +64,23 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(seed, rank):
+    """Each rank fits its own replica, drawn from seed + rank."""
+    return seed + rank
+
+
+def aggregate_rate(ms, steps, ws, device=None):
+    """Whole-job rate of ws independent replicas: the EM iterations of all
+    ranks over the slowest rank's time (max over ranks).  Returns (ms, rate)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * steps / (ms / 1e3)
+
+
 def problem(seed):
     return datagen.dense_problem(CFG["N"], CFG["D"], CFG["n_nonzero"], CFG["sigma"], seed)
 
@@ -381,9 +398,12 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     em = c["em_iters"]
-    res = {"plain": [], "learned": []}
-    times = {"plain": 0.0, "learned": 0.0}
-    fallbacks, mu_diff = 0, 0.0
+    # control: the all-zero network predicts mu_hat = 0 and s_hat = 1/c_d, i.e.
+    # Jacobi-preconditioned CG from X0 = [0 | p_k / c_d]
+    jacobi = torch.zeros(api.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    res = {"plain": [], "learned": [], "jacobi": []}
+    times = {"plain": 0.0, "learned": 0.0, "jacobi": 0.0}
+    fallbacks, jac_fallbacks, mu_diff = 0, 0, 0.0
     for sd in range(100, 116):
         pr, op, y = prob(sd)
         p = api.params(em_iters=em, seed=sd, **kw)
@@ -392,6 +412,11 @@ def run_learned(args):
         p.mlp = net.bf16.data_ptr()
         rl, tl = _timed(lambda: api.fit(op, y, pr.beta, p, ws=ws))
         fallbacks += B.cofem_last_fit_fallbacks()
+        p.mlp = jacobi.data_ptr()
+        rj, tj = _timed(lambda: api.fit(op, y, pr.beta, p, ws=ws))
+        jac_fallbacks += B.cofem_last_fit_fallbacks()
+        res["jacobi"].append(sum(rj.stats["cg_iters"]))
+        times["jacobi"] += tj
         res["plain"].append(sum(rp.stats["cg_iters"]))
         res["learned"].append(sum(rl.stats["cg_iters"]))
         times["plain"] += tp
@@ -415,8 +440,10 @@ def run_learned(args):
             {"workload": "learned-dense-n256-d1024", "train_seeds": "1..64",
              "train_estep": "2..20", "eval_seeds": "100..115", "em_iters": em},
             {"plain_em_iters_per_s": n_eval / times["plain"],
-             "cg_iters_total": {"plain": int(sum(res["plain"])), "learned": int(sum(res["learned"]))},
+             "jacobi_control_em_iters_per_s": n_eval / times["jacobi"],
+             "cg_iters_total": {k: int(sum(v)) for k, v in res.items()},
              "cg_iters_ratio": float(sum(res["learned"]) / sum(res["plain"])),
+             "jacobi_fallbacks": int(jac_fallbacks),
              "fallbacks": int(fallbacks), "max_mu_rel_diff_vs_plain": mu_diff,
              "training": {"samples": int(U.shape[0]), "collect_s": t_collect, "train_s": t_train,
                           "adam_steps": 4000, "loss_first": losses[0], "loss_last": losses[-1]},
@@ -453,7 +480,7 @@ def main():
         if ws > 1:
             dist.barrier()
 
-    prob = problem(args.seed + rank)
+    prob = problem(replica_seed(args.seed, rank))
     dev = torch.device("cuda", local)
     phi_t = torch.from_numpy(prob.Phi).to(dev)
     if args.phi == "bf16":
@@ -500,12 +527,7 @@ def main():
         e1.record(st)
         torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms, value = aggregate_rate(e0.elapsed_time(e1), args.steps, ws, dev)
     cg = res.stats["cg_iters"]
 
     if args.phi == "bf16" and args.terms > 0:

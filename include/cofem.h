@@ -362,6 +362,17 @@ cofem_status cofem_op_apply_noalloc(const cofem_op* op, cofem_dtype vec,
                                     void* y_dev, void* stream);
 size_t cofem_noalloc_scratch_capacity(void);
 
+/* Self-test of the bounded device waits (the paper has no counterpart).
+ * Every tensor-core kernel gives up a wait on a shared-memory mbarrier after
+ * a time limit, records COFEM_ERR_TIMEOUT in the device error word, frees
+ * its tensor memory and exits, so that the context stays usable.  This call
+ * runs the same wait routine in one CTA on an mbarrier that nothing arrives
+ * on, with a limit of limit_ns nanoseconds (1e3 .. 1e9), and reads the
+ * error word back.  Returns COFEM_ERR_TIMEOUT when the wait ran out (the
+ * expected result), COFEM_OK if it completed, COFEM_ERR_INVALID_ARG for a
+ * limit outside the range.  Synchronous on `stream`. */
+cofem_status cofem_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
 /* The two halves: W = Phi Z (ncols columns of length N, leading dimension
  * ldw) and Z = Phi^T W (length D, leading dimension ldz).  Used for
  * b = beta Phi^T y.  Same workspace rule as cofem_op_apply. Asynchronous. */

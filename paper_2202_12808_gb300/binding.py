@@ -99,6 +99,7 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_float), _I32, ctypes.POINTER(_I32)]),
     "cofem_op_apply_noalloc": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P]),
     "cofem_noalloc_scratch_capacity": (_SZ, []),
+    "cofem_selftest_wait_timeout": (_S, [_I64, _P]),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_diag_mstep": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _D, _D, _P,
@@ -295,6 +296,11 @@ def cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, st
 
 def cofem_noalloc_scratch_capacity():
     return lib().cofem_noalloc_scratch_capacity()
+
+
+def cofem_selftest_wait_timeout(limit_ns, stream=0):
+    """Status code of the bounded-wait self-test (5 = the wait ran out)."""
+    return lib().cofem_selftest_wait_timeout(limit_ns, stream)
 
 
 def cofem_op_forward(op, vec, z_ptr, ldz, ncols, w_ptr, ldw, ws_ptr, ws_bytes, stream=0):

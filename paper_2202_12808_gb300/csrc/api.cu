@@ -67,6 +67,15 @@ __global__ void ctl_init_kernel(CgCtl* ctl, long long t0) {
   ctl->error = 0;
 }
 
+// alpha32[i] = (float)alpha[i]: the FP32 copy that the operators read
+__global__ void alpha32_kernel(const double* alpha, int64_t n, float* alpha32) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    alpha32[i] = (float)alpha[i];
+}
+
 __global__ void fill_double_kernel(double* x, int64_t n, double v) {
   pdl_wait();
   pdl_trigger();
@@ -128,7 +137,7 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
 static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
                              const double* alpha, double beta, void* y, double* dots,
                              int* nparts, char* ws, cudaStream_t st, int* err = nullptr,
-                             unsigned flags = 0u) {
+                             unsigned flags = 0u, const float* alpha32 = nullptr) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
     if (use_tc(op) && vec == COFEM_F32) {
@@ -141,7 +150,7 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
         const_cast<cofem_op*>(op)->dense.l2_resident_cols = cols < d.D ? cols : d.D;
       }
       int rc = dense_tc_apply(d, d.nterms, (const float*)x, ld, ncols, (float*)y, beta, alpha,
-                              dots, nparts, ws, err, flags, st);
+                              dots, nparts, ws, err, flags, st, alpha32);
       if (rc == 1) {
         g_last_error = "cuTensorMapEncodeTiled failed";
         return COFEM_ERR_CUDA;
@@ -165,7 +174,7 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
   float* W = (float*)ws;
   conv_forward(h64, op->C, op->L, (const float*)x, ld, ncols, W, op->L, st);
   const int np = conv_adjoint(h64, op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
-                              (const float*)x, dots, st);
+                              (const float*)x, dots, st, vec == COFEM_F32 ? alpha32 : nullptr);
   if (nparts) *nparts = dots ? np : 0;
   CKL();
   return COFEM_OK;
@@ -225,8 +234,8 @@ static int64_t op_D(const cofem_op* op) {
 // --------------------------------------------------------------- layout
 
 struct FitLayout {
-  size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, X, R, P, Q, b, st_iters, st_relres,
-      st_clamps, st_support, opws;
+  size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, alpha32, X, R, P, Q, b, st_iters,
+      st_relres, st_clamps, st_support, opws;
   size_t total;
   int64_t ld;
 };
@@ -247,6 +256,7 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   L.pvec3 = o; o += align256(sizeof(double) * kMaxParts * kMaxCols);
   L.minv = o; o += align256((size_t)L.ld * sizeof(float));
   L.pn2 = o; o += align256((size_t)L.ld * sizeof(float));
+  L.alpha32 = o; o += align256((size_t)L.ld * sizeof(float));
   L.X = o; o += blk;
   L.R = o; o += blk;
   L.P = o; o += blk;
@@ -346,6 +356,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cf.den_floor = p->den_floor;
   cf.support_threshold = p->support_threshold;
   cf.em_iters = p->em_iters;
+  float* alpha32 = vec == COFEM_F32 ? (float*)(ws + L.alpha32) : nullptr;
+  cf.alpha32 = alpha32;
   if (use_tc(op) && vec == COFEM_F32) {
     // the CG kernels write P's BF16 terms straight into the operator's
     // split buffer, so the operator skips its own split of P
@@ -378,7 +390,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     }
     CKL();
     cofem_status rw = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws,
-                               cs, &ctl->error, 0u);
+                               cs, &ctl->error, 0u, alpha32);
     if (rw != COFEM_OK) return rw;
     launch_cg_init_warm<V>(cf, ctl, sc, X, R, P, Q, b, pvec, pvec2, pvec3, cs);
   } else {
@@ -400,7 +412,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int nparts = 0;
     rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs,
-                  &ctl->error, cf.split_nt > 0 ? kApplyPresplit : 0u);
+                  &ctl->error, cf.split_nt > 0 ? kApplyPresplit : 0u, alpha32);
     if (rc != COFEM_OK) return rc;
     cf.gamma_parts = nparts;
     launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, bs);
@@ -412,7 +424,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       cudaStream_t is = ss.s[2];
       CK(cudaStreamBeginCaptureToGraph(is, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is,
-                    &ctl->error, 0u);
+                    &ctl->error, 0u, alpha32);
       if (rc != COFEM_OK) return rc;
       launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, pvec2, is);
       CKL();
@@ -450,7 +462,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CK(cudaStreamBeginCaptureToGraph(ws2, fwhile, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int np2 = 0;
     rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &np2, opws, ws2, &ctl->error,
-                  pf.split_nt > 0 ? kApplyPresplit : 0u);
+                  pf.split_nt > 0 ? kApplyPresplit : 0u, alpha32);
     if (rc != COFEM_OK) return rc;
     pf.gamma_parts = np2;
     launch_cg_update<V>(pf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, ws2);
@@ -487,6 +499,11 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
   CKL();
   if (p->t_offset == 0) {
     launch_k(fill_double_kernel, dim3((unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096)), dim3(256), 0, st, alpha, D, p->alpha_init);
+    CKL();
+  }
+  if (p->vec_dtype == COFEM_F32) {
+    // the M-step keeps this copy current from here on
+    launch_k(alpha32_kernel, dim3((unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096)), dim3(256), 0, st, (const double*)alpha, D, (float*)(ws + L.alpha32));
     CKL();
   }
   // b = beta Phi^T y  (once per fit: y and beta do not change)
@@ -559,6 +576,16 @@ const char* cofem_status_string(cofem_status s) {
 const char* cofem_last_error(void) { return g_last_error.c_str(); }
 
 int32_t cofem_last_fit_fallbacks(void) { return g_last_fallbacks; }
+
+cofem_status cofem_selftest_wait_timeout(int64_t limit_ns, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 1000000000) return COFEM_ERR_INVALID_ARG;
+  const int r = wait_selftest(limit_ns, (cudaStream_t)stream);
+  if (r < 0) {
+    set_error("wait self-test", cudaGetLastError(), __FILE__, __LINE__);
+    return COFEM_ERR_CUDA;
+  }
+  return r == 0 ? COFEM_OK : (cofem_status)r;
+}
 
 cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void* phi_dev,
                             int64_t ld, const float* tile_scales_dev, cofem_op** out) {

@@ -125,7 +125,7 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
   float* x = X + pv.xoff + (int64_t)j * pv.ld;
   float* r = R + pv.xoff + (int64_t)j * pv.ld;
   float* p = P + pv.xoff + (int64_t)j * pv.ld;
-  double acc = 0.0;
+  AccF acc;
   const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
   if (d < pv.ld) {
     float v[4];
@@ -133,7 +133,7 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
     for (int i = 0; i < 4; ++i) {
       float w = 0.f;
       if (d + i < pv.D) {
-        if (j == 0) { w = bv[pv.aoff + d + i]; acc += (double)w * (double)w; }
+        if (j == 0) { w = bv[pv.aoff + d + i]; acc.add_prod(w, w); }
         else w = bprobe(key, d + i, j - 1);
       }
       v[i] = w;
@@ -144,7 +144,7 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
     if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
   }
   if (j == 0) {
-    const double s = block_sum(acc, sh);
+    const double s = block_sum(acc.value(), sh);
     if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols] = s;
   }
   if (barrive_last(&st->counter[0], (unsigned)(pv.nch * cf.nc))) {
@@ -197,7 +197,7 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
   }
   __syncthreads();
   const float a = a_sh;
-  double acc = 0.0;
+  AccF acc;
   const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
   if (d < pv.ld) {
     const int64_t o = pv.xoff + (int64_t)j * pv.ld + d;
@@ -209,11 +209,14 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
     xv.z = fmaf(a, pp.z, xv.z); xv.w = fmaf(a, pp.w, xv.w);
     rv.x = fmaf(-a, qq.x, rv.x); rv.y = fmaf(-a, qq.y, rv.y);
     rv.z = fmaf(-a, qq.z, rv.z); rv.w = fmaf(-a, qq.w, rv.w);
-    acc = (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+    acc.add_prod(rv.x, rv.x);
+    acc.add_prod(rv.y, rv.y);
+    acc.add_prod(rv.z, rv.z);
+    acc.add_prod(rv.w, rv.w);
     *reinterpret_cast<float4*>(X + o) = xv;
     *reinterpret_cast<float4*>(R + o) = rv;
   }
-  const double s = block_sum(acc, sh);
+  const double s = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = s;
   if (barrive_last(&st->counter[1], (unsigned)(pv.nch * cf.nc))) {
     if (threadIdx.x < cf.nc) {

@@ -123,7 +123,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
   __shared__ double sh[32];
   const int j = blockIdx.y;
   const uint64_t key = probe_key(cf.seed, ctl->t);
-  double acc = 0.0;
+  typename AccOf<V>::T acc;
   V* x = X + (int64_t)j * cf.ld;
   V* r = R + (int64_t)j * cf.ld;
   V* p = P + (int64_t)j * cf.ld;
@@ -133,7 +133,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
     if (d < cf.D) {
       if (j == 0) {
         v = bvec[d];
-        acc += (double)v * (double)v;
+        acc.add_prod(v, v);
       } else {
         const int k = j - 1;
         const uint64_t h = probe_word(key, d, k >> 6);
@@ -146,7 +146,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
     if (cf.split_nt > 0) write_split(cf, j, d, v);
   }
   if (j == 0) {
-    const double s = block_sum(acc, sh);
+    const double s = block_sum(acc.value(), sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
   }
   if (arrive_last(&ctl->counter[0])) {
@@ -189,7 +189,7 @@ __global__ void cg_init_warm_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const 
   __shared__ double sh[32];
   const int j = blockIdx.y;
   const uint64_t key = probe_key(cf.seed, ctl->t);
-  double az = 0.0, ar = 0.0, ab = 0.0;
+  typename AccOf<V>::T az, ar, ab;
   V* r = R + (int64_t)j * cf.ld;
   V* p = P + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
@@ -209,13 +209,13 @@ __global__ void cg_init_warm_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const 
     r[d] = rv;
     p[d] = zv;
     if (cf.split_nt > 0) write_split(cf, j, d, zv);
-    az += (double)rv * (double)zv;
-    ar += (double)rv * (double)rv;
-    if (j == 0) ab += (double)bv * (double)bv;
+    az.add_prod(rv, zv);
+    ar.add_prod(rv, rv);
+    if (j == 0) ab.add_prod(bv, bv);
   }
-  const double sz = block_sum(az, sh);
-  const double sr = block_sum(ar, sh);
-  const double sb = block_sum(ab, sh);
+  const double sz = block_sum(az.value(), sh);
+  const double sr = block_sum(ar.value(), sh);
+  const double sb = block_sum(ab.value(), sh);
   if (threadIdx.x == 0) {
     pz[(int64_t)blockIdx.x * kMaxCols + j] = sz;
     pr[(int64_t)blockIdx.x * kMaxCols + j] = sr;
@@ -293,7 +293,7 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   V* r = R + (int64_t)j * cf.ld;
   const V* p = P + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
-  double acc = 0.0, accz = 0.0;
+  typename AccOf<V>::T acc, accz;
   for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W; d < cf.ld;
        d += (int64_t)gridDim.x * blockDim.x * W) {
     V xv[W], rv[W], pv[W], qv[W];
@@ -302,15 +302,15 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
     for (int i = 0; i < W; ++i) {
       xv[i] = fma(a, pv[i], xv[i]);
       rv[i] = fma(-a, qv[i], rv[i]);
-      acc += (double)rv[i] * (double)rv[i];
-      if (cf.minv) accz += (double)rv[i] * (double)rv[i] * (double)cf.minv[d + i];
+      acc.add_prod(rv[i], rv[i]);
+      if (cf.minv) accz.add_prod(rv[i] * (V)cf.minv[d + i], rv[i]);
     }
     vstore(x + d, xv); vstore(r + d, rv);
   }
-  const double s = block_sum(acc, sh);
+  const double s = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
   if (cf.minv) {
-    const double sz = block_sum(accz, sh);
+    const double sz = block_sum(accz.value(), sh);
     if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
   }
   if (arrive_last(&ctl->counter[1])) {
@@ -350,7 +350,7 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
   const uint64_t key = probe_key(cf.seed, ctl->t);
   V* r = R + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
-  double acc = 0.0, accz = 0.0;
+  typename AccOf<V>::T acc, accz;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
     V bv;
@@ -362,13 +362,13 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
     }
     const V rv = bv - q[d];
     r[d] = rv;
-    acc += (double)rv * (double)rv;
-    if (cf.minv) accz += (double)rv * (double)rv * (double)cf.minv[d];
+    acc.add_prod(rv, rv);
+    if (cf.minv) accz.add_prod(rv * (V)cf.minv[d], rv);
   }
-  const double s = block_sum(acc, sh);
+  const double s = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
   if (cf.minv) {
-    const double sz = block_sum(accz, sh);
+    const double sz = block_sum(accz.value(), sh);
     if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
   }
   if (arrive_last(&ctl->counter[2])) {
@@ -433,16 +433,16 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
     const double m = (double)X[d];
-    double acc = 0.0;
+    typename AccOf<V>::T acc;          // sum_k p_kd x_kd (compensated for FP32 X)
     for (int w = 0; w * 64 < K; ++w) {
       const uint64_t h = probe_word(key, d, w);
       const int kend = min(K, (w + 1) * 64);
       for (int k = w * 64; k < kend; ++k) {
-        const double xv = (double)X[(int64_t)(k + 1) * cf.ld + d];
-        acc += ((h >> (k & 63)) & 1ull) ? -xv : xv;
+        const V xv = X[(int64_t)(k + 1) * cf.ld + d];
+        acc.add(((h >> (k & 63)) & 1ull) ? -xv : xv);
       }
     }
-    const double sd = acc / (double)K;
+    const double sd = acc.value() / (double)K;
     const double den = m * m + sd;
     if (den < cf.den_floor) ++clamps;
     const double al = 1.0 / fmax(den, cf.den_floor);
@@ -451,6 +451,7 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
     mu[d] = m;
     s[d] = sd;
     alpha[d] = al;
+    if (cf.alpha32) cf.alpha32[d] = (float)al;
   }
   const double cs = block_sum((double)clamps, sh);
   const double ss = block_sum((double)support, sh);

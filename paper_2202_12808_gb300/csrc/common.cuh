@@ -67,6 +67,7 @@ struct CgConf {
   const float* minv;                 // preconditioned CG: M^-1 = diag(minv), else null
   unsigned long long fallback_handle;  // IF node: preconditioned solve did not converge
   int fallback_init;                 // this init restarts plain CG after a fallback
+  float* alpha32;                    // FP32 copy of alpha kept by the M-step, or null
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when
@@ -106,6 +107,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Per-thread dot-product accumulators.  FP32 vectors use a compensated FP32
+// sum: Knuth's TwoSum keeps the rounding error of every addition and an FMA
+// recovers the rounding error of every product, so the pair (s, c) carries
+// about twice FP32's precision with FP32 instructions only (FP64 arithmetic
+// and f32<->f64 conversions issue at a small fraction of the FP32 rate on
+// this GPU).  The value is promoted to FP64 once per thread, and every
+// cross-thread reduction is FP64.  FP64 vectors accumulate in FP64.
+struct AccF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float xv = t - s;
+    c += (s - (t - xv)) + (x - xv);
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    c += fmaf(a, b, -p);
+    add(p);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { s += a * b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <typename V> struct AccOf { using T = AccD; };
+template <> struct AccOf<float> { using T = AccF; };
 
 // Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {

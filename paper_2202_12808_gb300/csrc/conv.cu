@@ -7,12 +7,13 @@
 // and one adjoint launch; the adjoint's epilogue applies beta, adds
 // alpha . x and accumulates the x_j^T (A x)_j partials of the CG step.
 //
-// Both kernels stage a tile of TILE = 256 * R outputs plus a T-1 halo of the
-// input column in shared memory (wrapping circularly), keep one channel's
-// filter in registers and let every thread produce R consecutive outputs
-// with a sliding register window: one shared load and R FMAs per tap.  The
-// shared tile is skewed by one word every 32 (index i -> i + i/32) so that
-// threads reading at stride R hit distinct banks.
+// Both kernels stage a tile of TILE = 256 * R outputs (R = 16) plus a T-1
+// halo of the input column in shared memory (wrapping circularly), hold 16
+// filter taps at a time in registers and let every thread produce R
+// consecutive outputs with a sliding register window: one shared load and R
+// FMAs per tap.  The shared tile is skewed by one word every 32 (index i ->
+// i + i/32) so that threads reading at stride R hit distinct banks.  The
+// grid runs the columns of a tile side by side so alpha stays in L2.
 #include "kernels.cuh"
 
 namespace cofem {
@@ -22,13 +23,15 @@ void apply_tick(cudaStream_t st);
 namespace cofem {
 
 constexpr int kConvThreads = 256;
-constexpr int kConvR = 8;
-constexpr int kConvTile = kConvThreads * kConvR;   // 2048 outputs per block
+constexpr int kConvR = 16;                           // outputs per thread
+constexpr int kConvTile = kConvThreads * kConvR;    // 4096 outputs per block
 constexpr int kConvMaxT = 64;
+constexpr int kTapChunk = 16;                        // filter taps held in registers
 
 __host__ __device__ constexpr int skew(int i) { return i + (i >> 5); }
 
-// W[j][n] = sum_c sum_t h[c][t] Z[j][c*L + (n - t) mod L]      grid (L/TILE, ncols)
+// W[j][n] = sum_c sum_t h[c][t] Z[j][c*L + (n - t) mod L]
+// grid (ncols, L / TILE): the columns of one tile run side by side.
 template <int T>
 __global__ void __launch_bounds__(kConvThreads)
 conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ Z,
@@ -36,119 +39,137 @@ conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
   pdl_wait();
   pdl_trigger();
   __shared__ float zs[skew(kConvTile + kConvMaxT) + 8];
-  const int j = blockIdx.y;
-  const int64_t n0 = (int64_t)blockIdx.x * kConvTile;
+  const int j = blockIdx.x;
+  const int64_t n0 = (int64_t)blockIdx.y * kConvTile;
   const int tid = threadIdx.x;
   float acc[kConvR];
 #pragma unroll
   for (int r = 0; r < kConvR; ++r) acc[r] = 0.f;
   const int span = kConvTile + T - 1;
+  const bool wrap1 = L >= span;              // one add or subtract of L suffices
+  const int base = (T - 1) + tid * kConvR;   // zs index of output n0 + tid*R at tap 0
   for (int c = 0; c < C; ++c) {
     const float* zc = Z + (int64_t)j * ldz + (int64_t)c * L;
     __syncthreads();
     for (int i = tid; i < span; i += kConvThreads) {
       int64_t n = n0 - (T - 1) + i;
-      n = n < 0 ? n + L : (n >= L ? n - L : n);
+      if (wrap1) n = n < 0 ? n + L : (n >= L ? n - L : n);
+      else n = ((n % L) + L) % L;            // L shorter than the staged span
       zs[skew(i)] = zc[n];
     }
-    float hr[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) hr[t] = __ldg(h + c * T + t);
     __syncthreads();
-    // output n = n0 + tid*R + r needs zs index (T-1) + tid*R + r - t
-    const int base = (T - 1) + tid * kConvR;
+    // window w[r] = z at output r and the current tap
     float w[kConvR];
 #pragma unroll
     for (int r = 0; r < kConvR; ++r) w[r] = zs[skew(base + r)];
+#pragma unroll 1
+    for (int t0 = 0; t0 < T; t0 += kTapChunk) {
+      float hr[kTapChunk];
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
+      for (int q = 0; q < kTapChunk; ++q) hr[q] = __ldg(h + c * T + t0 + q);
 #pragma unroll
-      for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[t], w[r], acc[r]);
-      if (t + 1 < T) {
+      for (int q = 0; q < kTapChunk; ++q) {
+#pragma unroll
+        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r], acc[r]);
 #pragma unroll
         for (int r = kConvR - 1; r > 0; --r) w[r] = w[r - 1];
-        w[0] = zs[skew(base - t - 1)];
+        const int t = t0 + q;
+        w[0] = t + 1 < T ? zs[skew(base - t - 1)] : 0.f;
       }
     }
   }
   float* wj = W + (int64_t)j * ldw + n0 + tid * kConvR;
   if (n0 + tid * kConvR + kConvR <= L) {
-    reinterpret_cast<float4*>(wj)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    reinterpret_cast<float4*>(wj)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+    for (int q = 0; q < kConvR / 4; ++q)
+      reinterpret_cast<float4*>(wj)[q] =
+          make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
   }
 }
 
 // Y[j][c*L + m] = beta * sum_t h[c][t] W[j][(m + t) mod L] (+ alpha . X),
-// dots[block][j] = sum over the block of X . Y.          grid (L/TILE, ncols)
+// dots[tile][j] = sum over the block of X . Y.      grid (ncols, L / TILE)
 template <int T>
 __global__ void __launch_bounds__(kConvThreads)
 conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ W,
                     int64_t ldw, float* __restrict__ Y, int64_t ld, double beta,
-                    const double* __restrict__ alpha, const float* __restrict__ X,
-                    double* dots) {
+                    const double* __restrict__ alpha, const float* __restrict__ alpha32,
+                    const float* __restrict__ X, double* dots) {
   pdl_wait();
   pdl_trigger();
   __shared__ float ws[skew(kConvTile + kConvMaxT) + 8];
   __shared__ double red[32];
-  const int j = blockIdx.y;
-  const int64_t m0 = (int64_t)blockIdx.x * kConvTile;
+  const int j = blockIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.y * kConvTile;
   const int tid = threadIdx.x;
   const int span = kConvTile + T - 1;
   const float* wj = W + (int64_t)j * ldw;
   for (int i = tid; i < span; i += kConvThreads) {
     int64_t n = m0 + i;
-    n = n >= L ? n - L : n;
+    n = L >= span ? (n >= L ? n - L : n) : n % L;
     ws[skew(i)] = wj[n];
   }
   __syncthreads();
   const int base = tid * kConvR;
   const bool live = m0 + base + kConvR <= L;
-  double dot = 0.0;
+  AccF dot;
+  const bool diag = alpha32 != nullptr || alpha != nullptr;
   for (int c = 0; c < C; ++c) {
-    float hr[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) hr[t] = __ldg(h + c * T + t);
     float w[kConvR], acc[kConvR];
 #pragma unroll
     for (int r = 0; r < kConvR; ++r) {
       w[r] = ws[skew(base + r)];
       acc[r] = 0.f;
     }
+#pragma unroll 1
+    for (int t0 = 0; t0 < T; t0 += kTapChunk) {
+      float hr[kTapChunk];
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
+      for (int q = 0; q < kTapChunk; ++q) hr[q] = __ldg(h + c * T + t0 + q);
 #pragma unroll
-      for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[t], w[r], acc[r]);
-      if (t + 1 < T) {
+      for (int q = 0; q < kTapChunk; ++q) {
+#pragma unroll
+        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r], acc[r]);
 #pragma unroll
         for (int r = 0; r < kConvR - 1; ++r) w[r] = w[r + 1];
-        w[kConvR - 1] = ws[skew(base + kConvR + t)];
+        const int t = t0 + q;
+        w[kConvR - 1] = t + 1 < T ? ws[skew(base + kConvR + t)] : 0.f;
       }
     }
     if (live) {
       const int64_t d = (int64_t)c * L + m0 + base;
       float* yj = Y + (int64_t)j * ld + d;
-      float out[kConvR];
-      if (alpha) {
-        const float* xj = X + (int64_t)j * ld + d;
-        const float4 x0 = reinterpret_cast<const float4*>(xj)[0];
-        const float4 x1 = reinterpret_cast<const float4*>(xj)[1];
-        const float xv[kConvR] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float* xj = X ? X + (int64_t)j * ld + d : nullptr;
 #pragma unroll
-        for (int r = 0; r < kConvR; ++r) {
-          out[r] = fmaf((float)alpha[d + r], xv[r], (float)beta * acc[r]);
-          dot += (double)xv[r] * (double)out[r];
+      for (int q = 0; q < kConvR / 4; ++q) {
+        float out[4];
+        if (diag) {
+          const float4 xv = reinterpret_cast<const float4*>(xj)[q];
+          const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+          float a4[4];
+          if (alpha32) {
+            const float4 av = reinterpret_cast<const float4*>(alpha32 + d)[q];
+            a4[0] = av.x; a4[1] = av.y; a4[2] = av.z; a4[3] = av.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) a4[e] = (float)alpha[d + 4 * q + e];
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            out[e] = fmaf(a4[e], xa[e], (float)beta * acc[4 * q + e]);
+            dot.add_prod(xa[e], out[e]);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) out[e] = (float)beta * acc[4 * q + e];
         }
-      } else {
-#pragma unroll
-        for (int r = 0; r < kConvR; ++r) out[r] = (float)beta * acc[r];
+        reinterpret_cast<float4*>(yj)[q] = make_float4(out[0], out[1], out[2], out[3]);
       }
-      reinterpret_cast<float4*>(yj)[0] = make_float4(out[0], out[1], out[2], out[3]);
-      reinterpret_cast<float4*>(yj)[1] = make_float4(out[4], out[5], out[6], out[7]);
     }
   }
   if (dots) {
-    const double s = block_sum(dot, red);
-    if (tid == 0) dots[(int64_t)blockIdx.x * kMaxCols + j] = s;
+    const double s = block_sum(dot.value(), red);
+    if (tid == 0) dots[(int64_t)blockIdx.y * kMaxCols + j] = s;
   }
 }
 
@@ -159,19 +180,19 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
 
 void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ldz, int ncols,
                   float* W, int64_t ldw, cudaStream_t st) {
-  dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
+  dim3 g(ncols, (unsigned)((L + kConvTile - 1) / kConvTile));
   launch_k(conv_forward_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, Z, ldz, W, ldw);
   apply_tick(st);
 }
 
 int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
                  float* Y, int64_t ld, double beta, const double* alpha, const float* X,
-                 double* dots, cudaStream_t st) {
-  dim3 g((unsigned)((L + kConvTile - 1) / kConvTile), ncols);
+                 double* dots, cudaStream_t st, const float* alpha32) {
+  dim3 g(ncols, (unsigned)((L + kConvTile - 1) / kConvTile));
   launch_k(conv_adjoint_kernel<kConvMaxT>, dim3(g), dim3(kConvThreads), 0, st, h64, C, L, W, ldw, Y, ld, beta,
-                                                            alpha, X, dots);
+                                                            alpha, alpha32, X, dots);
   apply_tick(st);
-  return (int)g.x;
+  return (int)g.y;
 }
 
 __global__ void pad_filters_kernel(const float* h, int C, int T, float* h64) {

@@ -33,6 +33,11 @@ inline size_t packed_bytes(int64_t N, int64_t D) {
 void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                      cudaStream_t st);
 
+
+// Runs the bounded-wait self-test; returns the device error word (0 or
+// COFEM_ERR_TIMEOUT) or -1 on a CUDA error.
+int wait_selftest(int64_t limit_ns, cudaStream_t st);
+
 // Per-kernel event timing of one operator application (diagnostics).
 void apply_ticks_arm(cudaEvent_t* events, int cap);
 int apply_ticks_disarm();
@@ -99,9 +104,11 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
                      size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
                      double* dots, int* err, cudaStream_t st);
 
+// alpha32: optional FP32 copy of alpha ((float)alpha[d]); saves the per-row
+// conversion.
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, unsigned flags, cudaStream_t st);
+                   int* err, unsigned flags, cudaStream_t st, const float* alpha32 = nullptr);
 
 template <typename TA, typename V>
 void dense_simt_forward(const DenseDesc& op, const V* Z, int64_t ldz, int ncols, V* W,

@@ -108,7 +108,7 @@ __global__ void reduce_epilogue_kernel(int64_t M, int64_t ldp, int64_t ldo, int 
   pdl_trigger();
   __shared__ double sh[32];
   const int j = blockIdx.y;
-  double acc = 0.0;
+  typename AccOf<V>::T acc;
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < ldo;
        m += (int64_t)gridDim.x * blockDim.x) {
     V y = V(0);
@@ -119,13 +119,13 @@ __global__ void reduce_epilogue_kernel(int64_t M, int64_t ldp, int64_t ldo, int 
       if (alpha) {
         const V xv = X[(int64_t)j * ldo + m];
         y = fma((V)alpha[m], xv, y);
-        acc += (double)xv * (double)y;
+        acc.add_prod(xv, y);
       }
     }
     Y[(int64_t)j * ldo + m] = y;
   }
   if (dots) {
-    const double t = block_sum(acc, sh);
+    const double t = block_sum(acc.value(), sh);
     if (threadIdx.x == 0) dots[(int64_t)blockIdx.x * kMaxCols + j] = t;
   }
 }

@@ -66,6 +66,7 @@ struct TcArgs {
   const float* x;
   int64_t ld;
   const double* alpha;
+  const float* alpha32;  // FP32 copy of alpha (same values as (float)alpha), or null
   double beta;
   double* dots;
   int* err;
@@ -219,6 +220,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // A is K-major in the first product, MN-major (Phi^T read in place) in the second
       const uint32_t idesc = tc::idesc_bf16_f32(kTileM, args.BN, MODE == 1 ? 1 : 0, 0);
       for (int i = 0; i < nk; ++i) {
         const int s = i % S;
@@ -244,7 +246,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int g = warp & 3;
+    const int g = warp & 3;                 // tensor-memory lane quarter of this warp
     const int64_t row = m0 + 32 * g + lane;
     const bool ok = tc::mbar_wait(accbar, 0, abort, 4 * kWaitLimitNs);
     if (!ok) tc_fail(args.err, abort);
@@ -252,6 +254,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
     const int ngroups = (args.nc + G - 1) / G;
     const bool live = row < M;
+    float a32 = 0.f;                     // alpha_row in FP32, converted once per row
+    if (MODE == 1 && live)
+      a32 = args.alpha32 ? args.alpha32[aoff + row]
+                         : (args.alpha ? (float)args.alpha[aoff + row] : 0.f);
     for (int gi = 0; gi < ngroups; ++gi) {
       float v[COLS];
 #pragma unroll
@@ -276,17 +282,26 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           if (j < args.nc && live)
             args.wpart[woff + (int64_t)split * sstride + (int64_t)j * ldo + row] = acc;
         } else {
-          double dot = 0.0;
+          // x_j^T y_j over the warp's 32 rows: compensated FP32 (product
+          // error by FMA, TwoSum at each butterfly step), FP64 once per warp
+          float ds = 0.f, dc = 0.f;
           if (j < args.nc && live) {
             const float xv = args.x[xoff + (int64_t)j * ldo + row];
-            const float yv = fmaf((float)args.alpha[aoff + row], xv, (float)beta * acc);
+            const float yv = fmaf(a32, xv, (float)beta * acc);
             args.y[xoff + (int64_t)j * ldo + row] = yv;
-            dot = (double)xv * (double)yv;
+            ds = xv * yv;
+            dc = fmaf(xv, yv, -ds);
           }
           if (args.dots && j < args.nc) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            if (lane == 0) red[(warp - 2) * 64 + j] = dot;
+            for (int o = 16; o > 0; o >>= 1) {
+              const float os = __shfl_xor_sync(0xffffffffu, ds, o);
+              const float oc = __shfl_xor_sync(0xffffffffu, dc, o);
+              const float t = ds + os, bv = t - ds;
+              dc += oc + ((ds - (t - bv)) + (os - bv));
+              ds = t;
+            }
+            if (lane == 0) red[(warp - 2) * 64 + j] = (double)ds + (double)dc;
           }
         }
       }
@@ -422,6 +437,35 @@ void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* pa
   launch_k(pack_kernel, dim3((unsigned)(blocks < 65535 ? blocks : 65535)), dim3(256), 0, st, (const __nv_bfloat16*)phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
 }
 
+// Bounded-wait self-test: one thread waits on phase 0 of an mbarrier that
+// nothing arrives on, with the kernels' own wait routine.
+__device__ int g_wait_selftest_err;
+__global__ void wait_selftest_kernel(uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  tc::mbar_init(&bar, 1);
+  tc::fence_mbar_init();
+  if (!tc::mbar_wait(&bar, 0u, &abort_flag, limit_ns))
+    atomicCAS(&g_wait_selftest_err, 0, (int)COFEM_ERR_TIMEOUT);
+}
+
+int wait_selftest(int64_t limit_ns, cudaStream_t st) {
+  const int zero = 0;
+  if (cudaMemcpyToSymbolAsync(g_wait_selftest_err, &zero, sizeof(int), 0,
+                              cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return -1;
+  wait_selftest_kernel<<<1, 32, 0, st>>>((uint64_t)limit_ns);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  int out = 0;
+  if (cudaMemcpyFromSymbolAsync(&out, g_wait_selftest_err, sizeof(int), 0,
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  return out;
+}
+
 // ----------------------------------------------------------- host side
 
 // Optional per-kernel timing of one operator application (cofem_op_apply_timed):
@@ -491,7 +535,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   const int mt1 = (int)((N + kTileM - 1) / kTileM);
   p.nk1 = (int)((D + kTileK - 1) / kTileK);
   p.nk2 = (int)((N + kTileK - 1) / kTileK);
-  int per_sm = 512 / (int)tc < ctas_per_sm ? 512 / (int)tc : ctas_per_sm;
+  int per_sm = 512 / (int)p.tmem_cols < ctas_per_sm ? 512 / (int)p.tmem_cols : ctas_per_sm;
   if (per_sm < 1) per_sm = 1;
   // one wave: at most per_sm * sms CTAs in the split-K product
   int want = (per_sm * sms) / mt1;
@@ -532,7 +576,8 @@ static cudaError_t launch_tc(dim3 grid, size_t smem, const CUtensorMap& a, const
 template <int NT>
 static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int nc, float* Y,
                             double beta, const double* alpha, double* dots, int* nparts,
-                            char* ws, int* err, unsigned flags, cudaStream_t st) {
+                            char* ws, int* err, unsigned flags, cudaStream_t st,
+                            const float* alpha32) {
   const int sms = num_sms();
   DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages);
   const bool presplit = (flags & kApplyPresplit) != 0;
@@ -542,7 +587,6 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   // split X (leading dim ld) into BF16 terms Xs (pitch p.ld): GEMM1's operand
   // (skipped when the caller's kernels already wrote Xs)
   if (!presplit) {
-    int64_t need = (p.ld + 255) / 256;
     const int64_t need4 = (p.ld / 4 + 255) / 256;
     dim3 g((unsigned)(need4 < 64 ? need4 : 64), (p.BN / 16) * TermGroup<NT>::G);
     launch_k(split_block_kernel<NT>, dim3(g), dim3(256), 0, st, X, ld, op.D, p.ld, nc, Xs);
@@ -602,6 +646,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.x = X;
   a2.ld = ld;
   a2.alpha = alpha;
+  a2.alpha32 = alpha32;
   a2.beta = beta;
   a2.dots = dots;
   a2.err = err;
@@ -632,6 +677,7 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
   a.x = X;
   a.y = Y;
   a.alpha = alpha;
+  a.alpha32 = nullptr;
   a.dots = dots;
   a.err = err;
   a.items = items;
@@ -652,11 +698,14 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
 
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, unsigned flags, cudaStream_t st) {
+                   int* err, unsigned flags, cudaStream_t st, const float* alpha32) {
   switch (NT) {
-    case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
-    case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
-    default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st);
+    case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
+                                           alpha32);
+    case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
+                                           alpha32);
+    default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
+                                           alpha32);
   }
 }
 

@@ -43,7 +43,7 @@ void conv_forward(const float* h64, int C, int64_t L, const float* Z, int64_t ld
                   float* W, int64_t ldw, cudaStream_t st);
 int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw, int ncols,
                  float* Y, int64_t ld, double beta, const double* alpha, const float* X,
-                 double* dots, cudaStream_t st);
+                 double* dots, cudaStream_t st, const float* alpha32 = nullptr);
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st);
 
 // ---- operator application ----

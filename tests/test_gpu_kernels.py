@@ -45,13 +45,13 @@ def test_probe_fill_all_config1_iterations(cuda_lib):
 APPLY_CASES = [
     # (N, D, ncols)
     (200, 1000, 1), (200, 1000, 2), (200, 1000, 17), (256, 1024, 21), (130, 515, 33),
-    (96, 300, 64),
+    (96, 300, 64), (520, 1300, 33),
 ]
 
 
 @pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
 @pytest.mark.parametrize("kind", ["f64", "f32", "bf16", "bf16-t2", "bf16-t1", "bf16-simt",
-                                  "bf16-packed"])
+                                  "bf16-packed", "bf16-packed-t1"])
 def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
     rng = np.random.default_rng(ncols)
@@ -73,14 +73,15 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
         vdt, vec, pdt = torch.float32, B.COFEM_F32, B.COFEM_BF16
         # FP32 split into 3 / 2 / 1 BF16 terms (24 / 16 / 8-bit mantissas)
-        terms = {"bf16": 3, "bf16-t2": 2, "bf16-t1": 1, "bf16-simt": 0, "bf16-packed": 3}[kind]
+        terms = {"bf16": 3, "bf16-t2": 2, "bf16-t1": 1, "bf16-simt": 0, "bf16-packed": 3,
+                 "bf16-packed-t1": 1}[kind]
         tol = {3: 2e-5, 2: 6e-5, 1: 8e-3, 0: 2e-5}[terms]
     X_in = X.astype(np.float32).astype(np.float64) if vdt == torch.float32 else X
     op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
     if pdt == B.COFEM_BF16:
         B.cofem_op_dense_set_terms(op, terms)
     packed = None
-    if kind == "bf16-packed":
+    if kind.startswith("bf16-packed"):
         nb = B.cofem_dense_packed_bytes(N, D)
         packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
         B.cofem_op_dense_attach_packed(op, packed.data_ptr(), nb)

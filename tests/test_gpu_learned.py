@@ -178,3 +178,38 @@ def test_learned_gain_over_plain_cg(cuda_lib, net):
         tot_plain += sum(rp.stats["cg_iters"])
         tot_learned += sum(rl.stats["cg_iters"])
     assert tot_learned <= 0.75 * tot_plain, (tot_learned, tot_plain)
+
+
+def test_untrustworthy_prediction_falls_back_to_plain_cg(cuda_lib):
+    # a network whose s_hat is e^40 / c_d starts every learned solve from a
+    # residual ~1e15 times ||B||: neither FP32 nor FP64 can bring it below the
+    # tolerance, so every E-step after the first hits the cap and reruns as
+    # plain CG from zero (in the GPU fit and in the oracle's learned loop)
+    th = np.zeros(omlp.N_PARAMS)
+    omlp.unpack(th)["b3"][:] = [0.0, 10.0]
+    w = torch.from_numpy(th).to(torch.bfloat16).cuda()
+    pr, op, y = _conf1(60, sigma=0.1)
+    em, cap = 4, 150
+    p = api.params(vec_dtype=B.COFEM_F32, K=16, em_iters=em, cg_tol=1e-5, cg_max_iters=cap,
+                   seed=60)
+    rp = api.fit(op, y, pr.beta, p)
+    p.mlp = w.data_ptr()
+    rl = api.fit(op, y, pr.beta, p)
+    torch.cuda.synchronize()
+    assert B.cofem_last_fit_fallbacks() == em - 1
+    assert rl.stats["cg_iters"][0] == rp.stats["cg_iters"][0]
+    for t in range(1, em):
+        assert rl.stats["cg_iters"][t] == cap + rp.stats["cg_iters"][t]
+    assert rel_l2(rl.mu.cpu().numpy(), rp.mu.cpu().numpy()) <= 1e-6
+    Phi = pr.Phi.astype(np.float64)
+    pn2 = np.sum(Phi * Phi, axis=0).astype(np.float32).astype(np.float64)
+
+    def predict(alpha, mu_prev, s_prev):
+        o, _ = omlp.forward(th, omlp.features(alpha, pn2, pr.beta, mu_prev, s_prev))
+        return omlp.predict(o, alpha, pn2, pr.beta)
+
+    phi, phit, D = sbl.dense_dictionary(Phi)
+    ra, rmu, rs, rst = sbl.cofem_learned(phi, phit, D, pr.y.astype(np.float32).astype(np.float64),
+                                         pr.beta, 16, em, 1e-5, cap, predict, seed=60)
+    assert rst.fallbacks == [0] + [1] * (em - 1)
+    assert rel_l2(rl.mu.cpu().numpy(), rmu) <= 1e-4

@@ -82,31 +82,44 @@ __device__ __forceinline__ float bprobe(uint64_t key, int64_t d, int k) {
 }
 
 // per-problem last-block arrival on st.counter[c] among `expected` blocks
+// As arrive_last: what the last block reads was written by each block's
+// thread 0, which fences before arriving.
 __device__ __forceinline__ bool barrive_last(unsigned int* counter, unsigned expected) {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == expected - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == expected - 1;
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (last) __threadfence();
   return last;
 }
 
+// All threads of the problem's last block (blockDim >= nc): b_j by thread j,
+// the residual total by the first warp (fixed order), the stop test.
 __device__ void bfinalize(const BConf& cf, BState* st) {
+  __shared__ double tot_sh;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int j = 0; j < cf.nc; ++j) tot += st->rho_new[j];
-    const double relres = sqrt(tot) / sqrt(st->normB2);
+  const int j = threadIdx.x;
+  if (j < 32) {
+    double t = 0.0;
+    for (int c = j; c < cf.nc; c += 32) t += st->rho_new[c];
+    t = warp_sum(t);
+    if (j == 0) tot_sh = t;
+  }
+  if (j < cf.nc) {
+    const double r0 = st->rho[j], r1 = st->rho_new[j];
+    st->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+    st->rho[j] = r1;
+  }
+  __syncthreads();
+  if (j == 0) {
+    const double relres = sqrt(tot_sh) / sqrt(st->normB2);
     st->relres = relres;
     int done = cf.fixed_iters > 0 ? st->iter >= cf.fixed_iters
                                   : (relres < cf.tol || st->iter >= cf.max_iters);
     if (!isfinite(relres)) { st->error = COFEM_ERR_NONFINITE; done = 1; }
-    for (int j = 0; j < cf.nc; ++j) {
-      const double r0 = st->rho[j], r1 = st->rho_new[j];
-      st->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
-      st->rho[j] = r1;
-    }
     st->done = done;
   }
 }
@@ -144,7 +157,7 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
     if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
   }
   if (j == 0) {
-    const double s = block_sum(acc.value(), sh);
+    const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols] = s;
   }
   if (barrive_last(&st->counter[0], (unsigned)(pv.nch * cf.nc))) {
@@ -216,7 +229,7 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
     *reinterpret_cast<float4*>(X + o) = xv;
     *reinterpret_cast<float4*>(R + o) = rv;
   }
-  const double s = block_sum(acc.value(), sh);
+  const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = s;
   if (barrive_last(&st->counter[1], (unsigned)(pv.nch * cf.nc))) {
     if (threadIdx.x < cf.nc) {

@@ -69,25 +69,47 @@ __device__ __forceinline__ void write_split4(const CgConf& cf, int j, int64_t d,
 }
 __device__ __forceinline__ void write_split4(const CgConf&, int, int64_t, const double (&)[2]) {}
 
-// Closes one CG iteration (called by the last block, all threads): the
-// residual norms rho_new are final.  Stop test, direction coefficients.
+// out[j] = sum over i < nparts of part[i * kMaxCols + j], j < ncols, by the
+// whole block: warp w takes columns w, w + nwarps, ...; its lanes take the
+// partials i = lane, lane + 32, ... and a butterfly adds them (fixed order).
+__device__ __forceinline__ void column_sums(const double* part, int nparts, int ncols,
+                                            double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = w; j < ncols; j += nw) {
+    double v = 0.0;
+    for (int i = lane; i < nparts; i += 32) v += part[(int64_t)i * kMaxCols + j];
+    v = warp_sum(v);
+    if (lane == 0) out[j] = v;
+  }
+}
+
+// Closes one CG iteration (called by the last block, all threads; blockDim
+// >= ncols): the residual norms rho_new are final.  Stop test, direction
+// coefficients b_j (thread j), the residual total by the first warp.
 __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
+  __shared__ double tot_sh;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int j = 0; j < cf.ncols; ++j) tot += cf.minv ? sc->rr_new[j] : sc->rho_new[j];
-    const double relres = sqrt(tot) / sqrt(ctl->normB2);
+  const int j = threadIdx.x;
+  if (j < 32) {
+    double t = 0.0;
+    for (int c = j; c < cf.ncols; c += 32) t += cf.minv ? sc->rr_new[c] : sc->rho_new[c];
+    t = warp_sum(t);
+    if (j == 0) tot_sh = t;
+  }
+  if (j < cf.ncols) {
+    const double r0 = sc->rho[j], r1 = sc->rho_new[j];
+    sc->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+    sc->rho[j] = r1;
+  }
+  __syncthreads();
+  if (j == 0) {
+    const double relres = sqrt(tot_sh) / sqrt(ctl->normB2);
     ctl->relres = relres;
     const int it = ctl->iter;
     int done;
     if (cf.fixed_iters > 0) done = it >= cf.fixed_iters;
     else done = (relres < cf.tol) || (it >= cf.max_iters);
     if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
-    for (int j = 0; j < cf.ncols; ++j) {
-      const double r0 = sc->rho[j], r1 = sc->rho_new[j];
-      sc->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
-      sc->rho[j] = r1;
-    }
     ctl->done = done;
     set_cond(cf.while_handle, done ? 0u : 1u);
     if (done && cf.fallback_handle)
@@ -146,7 +168,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
     if (cf.split_nt > 0) write_split(cf, j, d, v);
   }
   if (j == 0) {
-    const double s = block_sum(acc.value(), sh);
+    const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
   }
   if (arrive_last(&ctl->counter[0])) {
@@ -213,24 +235,17 @@ __global__ void cg_init_warm_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const 
     ar.add_prod(rv, rv);
     if (j == 0) ab.add_prod(bv, bv);
   }
-  const double sz = block_sum(az.value(), sh);
-  const double sr = block_sum(ar.value(), sh);
-  const double sb = block_sum(ab.value(), sh);
+  const double sz = block_sum(az, sh);
+  const double sr = block_sum(ar, sh);
+  const double sb = block_sum(ab, sh);
   if (threadIdx.x == 0) {
     pz[(int64_t)blockIdx.x * kMaxCols + j] = sz;
     pr[(int64_t)blockIdx.x * kMaxCols + j] = sr;
     if (j == 0) pb[blockIdx.x] = sb;
   }
   if (arrive_last(&ctl->counter[0])) {
-    if (threadIdx.x < cf.ncols) {
-      double tz = 0.0, tr = 0.0;
-      for (int i = 0; i < (int)gridDim.x; ++i) {
-        tz += pz[(int64_t)i * kMaxCols + threadIdx.x];
-        tr += pr[(int64_t)i * kMaxCols + threadIdx.x];
-      }
-      sc->rho[threadIdx.x] = tz;
-      sc->rr_new[threadIdx.x] = tr;
-    }
+    column_sums(pz, gridDim.x, cf.ncols, sc->rho);
+    column_sums(pr, gridDim.x, cf.ncols, sc->rr_new);
     __syncthreads();
     if (threadIdx.x == 0) {
       double b2 = 0.0, r2 = 0.0;
@@ -268,6 +283,18 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   __shared__ double a_sh;
   constexpr int W = 16 / sizeof(V);
   const int j = blockIdx.y;
+  V* x = X + (int64_t)j * cf.ld;
+  V* r = R + (int64_t)j * cf.ld;
+  const V* p = P + (int64_t)j * cf.ld;
+  const V* q = Q + (int64_t)j * cf.ld;
+  // this thread's first chunk is loaded before a_j is known, so that the
+  // loads overlap the reduction of the operator's partials below
+  const int64_t d0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * W;
+  V xv[W], rv[W], pv[W], qv[W];
+  if (d0 < cf.ld) {
+    vload(x + d0, xv); vload(r + d0, rv); vload(p + d0, pv); vload(q + d0, qv);
+  }
   if (threadIdx.x < 32) {
     double g = 0.0;
     for (int i = threadIdx.x; i < cf.gamma_parts; i += 32) g += gparts[(int64_t)i * kMaxCols + j];
@@ -289,15 +316,11 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   }
   __syncthreads();
   const V a = (V)a_sh;
-  V* x = X + (int64_t)j * cf.ld;
-  V* r = R + (int64_t)j * cf.ld;
-  const V* p = P + (int64_t)j * cf.ld;
-  const V* q = Q + (int64_t)j * cf.ld;
   typename AccOf<V>::T acc, accz;
-  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W; d < cf.ld;
-       d += (int64_t)gridDim.x * blockDim.x * W) {
-    V xv[W], rv[W], pv[W], qv[W];
-    vload(x + d, xv); vload(r + d, rv); vload(p + d, pv); vload(q + d, qv);
+  for (int64_t d = d0; d < cf.ld; d += step) {
+    if (d != d0) {
+      vload(x + d, xv); vload(r + d, rv); vload(p + d, pv); vload(q + d, qv);
+    }
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       xv[i] = fma(a, pv[i], xv[i]);
@@ -307,23 +330,18 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
     }
     vstore(x + d, xv); vstore(r + d, rv);
   }
-  const double s = block_sum(acc.value(), sh);
+  const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
   if (cf.minv) {
-    const double sz = block_sum(accz.value(), sh);
+    const double sz = block_sum(accz, sh);
     if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
   }
   if (arrive_last(&ctl->counter[1])) {
-    if (threadIdx.x < cf.ncols) {
-      double t = 0.0, tz = 0.0;
-      for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
-      if (cf.minv) {
-        for (int i = 0; i < (int)gridDim.x; ++i) tz += part2[(int64_t)i * kMaxCols + threadIdx.x];
-        sc->rr_new[threadIdx.x] = t;
-        sc->rho_new[threadIdx.x] = tz;
-      } else {
-        sc->rho_new[threadIdx.x] = t;
-      }
+    if (cf.minv) {
+      column_sums(part, gridDim.x, cf.ncols, sc->rr_new);
+      column_sums(part2, gridDim.x, cf.ncols, sc->rho_new);
+    } else {
+      column_sums(part, gridDim.x, cf.ncols, sc->rho_new);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -365,23 +383,18 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
     acc.add_prod(rv, rv);
     if (cf.minv) accz.add_prod(rv * (V)cf.minv[d], rv);
   }
-  const double s = block_sum(acc.value(), sh);
+  const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
   if (cf.minv) {
-    const double sz = block_sum(accz.value(), sh);
+    const double sz = block_sum(accz, sh);
     if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
   }
   if (arrive_last(&ctl->counter[2])) {
-    if (threadIdx.x < cf.ncols) {
-      double t = 0.0, tz = 0.0;
-      for (int i = 0; i < (int)gridDim.x; ++i) t += part[(int64_t)i * kMaxCols + threadIdx.x];
-      if (cf.minv) {
-        for (int i = 0; i < (int)gridDim.x; ++i) tz += part2[(int64_t)i * kMaxCols + threadIdx.x];
-        sc->rr_new[threadIdx.x] = t;
-        sc->rho_new[threadIdx.x] = tz;
-      } else {
-        sc->rho_new[threadIdx.x] = t;
-      }
+    if (cf.minv) {
+      column_sums(part, gridDim.x, cf.ncols, sc->rr_new);
+      column_sums(part2, gridDim.x, cf.ncols, sc->rho_new);
+    } else {
+      column_sums(part, gridDim.x, cf.ncols, sc->rho_new);
     }
     if (threadIdx.x == 0) { ctl->counter[2] = 0; ctl->replace = 0; }
     cg_finalize(cf, ctl, sc);

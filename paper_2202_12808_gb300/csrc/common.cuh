@@ -115,9 +115,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // and f32<->f64 conversions issue at a small fraction of the FP32 rate on
 // this GPU).  The value is promoted to FP64 once per thread, and every
 // cross-thread reduction is FP64.  FP64 vectors accumulate in FP64.
+// Terms of magnitude 1e30 or more (or non-finite) go to an FP64 side sum
+// instead, so that squares of large FP32 values cannot overflow.
 struct AccF {
   float s = 0.f, c = 0.f;
+  double big = 0.0;
   __device__ __forceinline__ void add(float x) {
+    if (!(fabsf(x) < 1e30f)) { big += (double)x; return; }
     const float t = s + x;
     const float xv = t - s;
     c += (s - (t - xv)) + (x - xv);
@@ -125,10 +129,11 @@ struct AccF {
   }
   __device__ __forceinline__ void add_prod(float a, float b) {
     const float p = a * b;
+    if (!(fabsf(p) < 1e30f)) { big += (double)a * (double)b; return; }
     c += fmaf(a, b, -p);
     add(p);
   }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c + big; }
 };
 struct AccD {
   double s = 0.0;
@@ -155,20 +160,65 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// One butterfly step of a compensated FP32 sum: (s, c) += (os, oc).
+__device__ __forceinline__ void two_sum_merge(float& s, float& c, float os, float oc) {
+  const float t = s + os, bv = t - s;
+  c += oc + ((s - (t - bv)) + (os - bv));
+  s = t;
+}
+
+// Block-wide sums of per-thread accumulators; result valid in thread 0.
+// Compensated FP32 accumulators are combined with FP32 TwoSum butterflies
+// and promoted to FP64 once; `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(const AccF& a, double* sh) {
+  float s = a.s, c = a.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    two_sum_merge(s, c, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, c, o));
+  float2* sh2 = reinterpret_cast<float2*>(sh);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh2[wid] = make_float2(s, c);
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const float2 v = lane < nw ? sh2[lane] : make_float2(0.f, 0.f);
+    s = v.x;
+    c = v.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      two_sum_merge(s, c, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, c, o));
+    r = (double)s + (double)c;
+  }
+  // the FP64 side sums, only when some thread of the block has one
+  if (__syncthreads_or(a.big != 0.0)) {
+    const double rb = block_sum(a.big, sh);
+    r += rb;
+  }
+  return r;
+}
+__device__ __forceinline__ double block_sum(const AccD& a, double* sh) { return block_sum(a.s, sh); }
+
 // Records the first device error (later ones are dropped).
 __device__ __forceinline__ void raise_error(CgCtl* ctl, int code) {
   atomicCAS(&ctl->error, 0, code);
 }
 
 // Last-block arrival: returns true in every thread of the last block to
-// arrive on counter `c`; that block must reset the counter.
+// arrive on counter `c`; that block must reset the counter.  Whatever the
+// last block reads from the other blocks must have been written by their
+// thread 0 (its fence orders those writes before the arrival; the other
+// threads' stores need no fence and do not wait for one).
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ bool last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (last) __threadfence();
   return last;
 }
 

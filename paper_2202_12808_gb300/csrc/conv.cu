@@ -168,7 +168,7 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
     }
   }
   if (dots) {
-    const double s = block_sum(dot.value(), red);
+    const double s = block_sum(dot, red);
     if (tid == 0) dots[(int64_t)blockIdx.y * kMaxCols + j] = s;
   }
 }

@@ -125,7 +125,7 @@ __global__ void reduce_epilogue_kernel(int64_t M, int64_t ldp, int64_t ldo, int 
     Y[(int64_t)j * ldo + m] = y;
   }
   if (dots) {
-    const double t = block_sum(acc.value(), sh);
+    const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) dots[(int64_t)blockIdx.x * kMaxCols + j] = t;
   }
 }

@@ -107,7 +107,11 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   uint64_t* accbar = empty + kMaxStages;
   uint32_t* tmem_slot = (uint32_t*)(accbar + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
-  double* red = (double*)(tmem_slot + 4);          // [4][64] epilogue partial dots
+  // epilogue partial dots per warp and column: compensated FP32 pairs, and
+  // FP64 side sums of out-of-range products (flagged in *bigflag)
+  float2* redp = (float2*)(tmem_slot + 4);          // [4][64]
+  double* redb = (double*)(redp + 4 * 64);           // [4][64]
+  volatile int* bigflag = (volatile int*)(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // geometry of this CTA's work (one problem, or one item of a batch)
@@ -151,6 +155,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     }
     tc::mbar_init(accbar, 1);
     *abort = 0;
+    *bigflag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&mapA);
     tc::prefetch_tmap(&mapB);
@@ -248,17 +253,20 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // ------------------------------------------------------------ epilogue
     const int g = warp & 3;                 // tensor-memory lane quarter of this warp
     const int64_t row = m0 + 32 * g + lane;
-    const bool ok = tc::mbar_wait(accbar, 0, abort, 4 * kWaitLimitNs);
-    if (!ok) tc_fail(args.err, abort);
-    tc::tc_fence_after();
     constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
+    constexpr int MG = (kMaxCols + G - 1) / G;      // most column groups
     const int ngroups = (args.nc + G - 1) / G;
     const bool live = row < M;
     float a32 = 0.f;                     // alpha_row in FP32, converted once per row
     if (MODE == 1 && live)
       a32 = args.alpha32 ? args.alpha32[aoff + row]
                          : (args.alpha ? (float)args.alpha[aoff + row] : 0.f);
-    for (int gi = 0; gi < ngroups; ++gi) {
+    const bool ok = tc::mbar_wait(accbar, 0, abort, 4 * kWaitLimitNs);
+    if (!ok) tc_fail(args.err, abort);
+    tc::tc_fence_after();
+#pragma unroll
+    for (int gi = 0; gi < MG; ++gi) {
+      if (gi >= ngroups) break;
       float v[COLS];
 #pragma unroll
       for (int c = 0; c < COLS / 16; ++c) {
@@ -272,45 +280,72 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 #pragma unroll
         for (int q = 0; q < COLS; ++q) v[q] = 0.f;
       }
+      // x_j^T y_j over the warp's 32 rows (second product): compensated
+      // FP32 (product error by FMA, TwoSum butterflies, the G columns of the
+      // group interleaved), FP64 once per warp and column; products of 1e30
+      // or more take an FP64 side sum
+      float ds[G], dc[G];
+      double db[G];
+      bool anybig = false;
 #pragma unroll
       for (int jj = 0; jj < G; ++jj) {
         const int j = gi * G + jj;
         float acc = 0.f;
 #pragma unroll
         for (int t = NT - 1; t >= 0; --t) acc += v[jj * NT + t];
+        ds[jj] = 0.f;
+        dc[jj] = 0.f;
+        db[jj] = 0.0;
         if (MODE == 0) {
           if (j < args.nc && live)
             args.wpart[woff + (int64_t)split * sstride + (int64_t)j * ldo + row] = acc;
-        } else {
-          // x_j^T y_j over the warp's 32 rows: compensated FP32 (product
-          // error by FMA, TwoSum at each butterfly step), FP64 once per warp
-          float ds = 0.f, dc = 0.f;
-          if (j < args.nc && live) {
-            const float xv = args.x[xoff + (int64_t)j * ldo + row];
-            const float yv = fmaf(a32, xv, (float)beta * acc);
-            args.y[xoff + (int64_t)j * ldo + row] = yv;
-            ds = xv * yv;
-            dc = fmaf(xv, yv, -ds);
+        } else if (j < args.nc && live) {
+          const float xv = args.x[xoff + (int64_t)j * ldo + row];
+          const float yv = fmaf(a32, xv, (float)beta * acc);
+          args.y[xoff + (int64_t)j * ldo + row] = yv;
+          const float pp = xv * yv;
+          if (fabsf(pp) < 1e30f) {
+            ds[jj] = pp;
+            dc[jj] = fmaf(xv, yv, -pp);
+          } else {
+            db[jj] = (double)xv * (double)yv;
+            anybig = true;
           }
-          if (args.dots && j < args.nc) {
+        }
+      }
+      if (MODE == 1 && args.dots) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              const float os = __shfl_xor_sync(0xffffffffu, ds, o);
-              const float oc = __shfl_xor_sync(0xffffffffu, dc, o);
-              const float t = ds + os, bv = t - ds;
-              dc += oc + ((ds - (t - bv)) + (os - bv));
-              ds = t;
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int jj = 0; jj < G; ++jj)
+            two_sum_merge(ds[jj], dc[jj], __shfl_xor_sync(0xffffffffu, ds[jj], o),
+                          __shfl_xor_sync(0xffffffffu, dc[jj], o));
+        }
+        if (__any_sync(0xffffffffu, anybig)) {
+#pragma unroll
+          for (int jj = 0; jj < G; ++jj) db[jj] = warp_sum(db[jj]);
+          if (lane == 0) *bigflag = 1;
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int jj = 0; jj < G; ++jj)
+            if (gi * G + jj < args.nc) {
+              redp[(warp - 2) * 64 + gi * G + jj] = make_float2(ds[jj], dc[jj]);
+              redb[(warp - 2) * 64 + gi * G + jj] = db[jj];
             }
-            if (lane == 0) red[(warp - 2) * 64 + j] = (double)ds + (double)dc;
-          }
         }
       }
     }
     if (MODE == 1 && args.dots) {
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (warp == 2) {
+        const bool big = *bigflag != 0;
         for (int j = lane; j < args.nc; j += 32) {
-          const double t = red[j] + red[64 + j] + red[128 + j] + red[192 + j];
+          float ps = redp[j].x, pc = redp[j].y;
+#pragma unroll
+          for (int w = 1; w < 4; ++w) two_sum_merge(ps, pc, redp[w * 64 + j].x, redp[w * 64 + j].y);
+          double t = (double)ps + (double)pc;
+          if (big) t += redb[j] + redb[64 + j] + redb[128 + j] + redb[192 + j];
           args.dots[(int64_t)dslot * kMaxCols + j] = t;
         }
       }
@@ -543,7 +578,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   if (want > p.nk1) want = p.nk1;
   p.kbps1 = (p.nk1 + want - 1) / want;
   p.S1 = (p.nk1 + p.kbps1 - 1) / p.kbps1;
-  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 64 + 4 * 64 * 8 + 64;
+  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 64 + 4 * 64 * 8 * 2 + 64;
   const size_t stage = kATileBytes + (size_t)p.BN * 128;
   // each resident CTA also costs 1 KB of reserved shared memory
   const size_t budget = kSmemPerSm / per_sm - 1024;

@@ -123,10 +123,13 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
     DenseSimtPlan p = dense_simt_plan(op->dense.N, op->dense.D, ncols, vec_bytes(vec), num_sms());
     size_t b = align256(p.total());
     if (use_tc(op)) {
-      DenseTcPlan q = max_shape ? dense_tc_plan(op->dense.N, op->dense.D, ncols,
-                                                op->dense.nterms, num_sms(), 4, 0)
-                                : dense_tc_plan(op->dense, ncols, num_sms());
+      DenseTcPlan q = dense_tc_plan(op->dense, ncols, num_sms());
       if (align256(q.total) > b) b = align256(q.total);
+      for (int cps = 1; max_shape && cps <= 4; ++cps) {
+        DenseTcPlan r = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
+                                      num_sms(), cps, 0);
+        if (align256(r.total) > b) b = align256(r.total);
+      }
     }
     return b;
   }

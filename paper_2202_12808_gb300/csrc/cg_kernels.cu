@@ -12,6 +12,8 @@
 
 namespace cofem {
 
+constexpr int kUpdChunks = 4;     // 16-byte chunks per thread and pass in the CG update
+
 template <typename V> struct Vec16;
 template <> struct Vec16<float> { using T = float4; static constexpr int W = 4; };
 template <> struct Vec16<double> { using T = double2; static constexpr int W = 2; };
@@ -69,17 +71,23 @@ __device__ __forceinline__ void write_split4(const CgConf& cf, int j, int64_t d,
 }
 __device__ __forceinline__ void write_split4(const CgConf&, int, int64_t, const double (&)[2]) {}
 
-// out[j] = sum over i < nparts of part[i * kMaxCols + j], j < ncols, by the
-// whole block: warp w takes columns w, w + nwarps, ...; its lanes take the
-// partials i = lane, lane + 32, ... and a butterfly adds them (fixed order).
+// out[j] = sum over i < nparts of part[i * kMaxCols + j], j < ncols
+// (blockDim >= ncols): thread j loads its column's partials eight at a time
+// and adds them as a fixed binary tree (deterministic, few dependent FP64
+// additions: FP64 latency is long on this GPU).
 __device__ __forceinline__ void column_sums(const double* part, int nparts, int ncols,
                                             double* out) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = w; j < ncols; j += nw) {
-    double v = 0.0;
-    for (int i = lane; i < nparts; i += 32) v += part[(int64_t)i * kMaxCols + j];
-    v = warp_sum(v);
-    if (lane == 0) out[j] = v;
+  const int j = threadIdx.x;
+  if (j < ncols) {
+    double acc = 0.0;
+    for (int i0 = 0; i0 < nparts; i0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = i0 + u < nparts ? part[(int64_t)(i0 + u) * kMaxCols + j] : 0.0;
+      acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    }
+    out[j] = acc;
   }
 }
 
@@ -282,22 +290,38 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   __shared__ double sh[32];
   __shared__ double a_sh;
   constexpr int W = 16 / sizeof(V);
+  constexpr int U = kUpdChunks;                 // chunks of W values per thread and pass
   const int j = blockIdx.y;
   V* x = X + (int64_t)j * cf.ld;
   V* r = R + (int64_t)j * cf.ld;
   const V* p = P + (int64_t)j * cf.ld;
   const V* q = Q + (int64_t)j * cf.ld;
-  // this thread's first chunk is loaded before a_j is known, so that the
-  // loads overlap the reduction of the operator's partials below
+  // chunk u of a pass starts at base + u * ts; the first pass's loads are
+  // issued before a_j is known, so that they overlap the reduction of the
+  // operator's partials below, and every pass loads before it stores
   const int64_t d0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x * W;
-  V xv[W], rv[W], pv[W], qv[W];
-  if (d0 < cf.ld) {
-    vload(x + d0, xv); vload(r + d0, rv); vload(p + d0, pv); vload(q + d0, qv);
+  const int64_t ts = (int64_t)gridDim.x * blockDim.x * W;
+  V xv[U][W], rv[U][W], pv[U][W], qv[U][W];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t d = d0 + u * ts;
+    if (d < cf.ld) {
+      vload(x + d, xv[u]); vload(r + d, rv[u]); vload(p + d, pv[u]); vload(q + d, qv[u]);
+    }
   }
   if (threadIdx.x < 32) {
+    // gamma_j = p_j^T A p_j: the operator's partials, eight per lane as a
+    // fixed tree, then a butterfly
     double g = 0.0;
-    for (int i = threadIdx.x; i < cf.gamma_parts; i += 32) g += gparts[(int64_t)i * kMaxCols + j];
+    for (int i0 = threadIdx.x; i0 < cf.gamma_parts; i0 += 256) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + 32 * u;
+        v[u] = i < cf.gamma_parts ? gparts[(int64_t)i * kMaxCols + j] : 0.0;
+      }
+      g += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    }
     g = warp_sum(g);
     if (threadIdx.x == 0) {
       const double rho = sc->rho[j];
@@ -317,18 +341,30 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   __syncthreads();
   const V a = (V)a_sh;
   typename AccOf<V>::T acc, accz;
-  for (int64_t d = d0; d < cf.ld; d += step) {
-    if (d != d0) {
-      vload(x + d, xv); vload(r + d, rv); vload(p + d, pv); vload(q + d, qv);
+  for (int64_t base = d0; base < cf.ld; base += U * ts) {
+    if (base != d0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t d = base + u * ts;
+        if (d < cf.ld) {
+          vload(x + d, xv[u]); vload(r + d, rv[u]); vload(p + d, pv[u]); vload(q + d, qv[u]);
+        }
+      }
     }
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-      xv[i] = fma(a, pv[i], xv[i]);
-      rv[i] = fma(-a, qv[i], rv[i]);
-      acc.add_prod(rv[i], rv[i]);
-      if (cf.minv) accz.add_prod(rv[i] * (V)cf.minv[d + i], rv[i]);
+    for (int u = 0; u < U; ++u) {
+      const int64_t d = base + u * ts;
+      if (d < cf.ld) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+          xv[u][i] = fma(a, pv[u][i], xv[u][i]);
+          rv[u][i] = fma(-a, qv[u][i], rv[u][i]);
+          acc.add_prod(rv[u][i], rv[u][i]);
+          if (cf.minv) accz.add_prod(rv[u][i] * (V)cf.minv[d + i], rv[u][i]);
+        }
+        vstore(x + d, xv[u]); vstore(r + d, rv[u]);
+      }
     }
-    vstore(x + d, xv); vstore(r + d, rv);
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
@@ -532,7 +568,7 @@ template <typename V>
 void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
                       const V* Q, const double* gparts, double* part, double* part2,
                       cudaStream_t st) {
-  dim3 g(vec_blocks(cf.ld, 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
+  dim3 g(vec_blocks(cf.ld, kUpdChunks * 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
   launch_k(cg_update_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts, part,
            part2);
 }

@@ -74,7 +74,9 @@ DenseSimtPlan dense_simt_plan(int64_t N, int64_t D, int ncols, int vec_bytes, in
 // Tensor-core plan (BF16 dictionary, FP32 vectors split into NT BF16 terms).
 struct DenseTcPlan {
   int NT, nc, BN;            // terms, output columns, MMA N (B-operand rows)
-  uint32_t tmem_cols;        // tensor-memory columns allocated per CTA
+  uint32_t acc_cols;         // tensor-memory columns of one accumulator
+  uint32_t tmem_cols;        // tensor-memory columns allocated per CTA (two accumulators)
+  int grid;                  // resident CTAs of one launch (ctas per SM x SMs)
   int64_t ld, ldw;           // padded D and N
   int nk1, nk2;              // K blocks (64) of the two products
   int S1, kbps1;             // split-K of the first product

@@ -21,6 +21,7 @@
 // GEMM2 reads the same bytes MN-major (Phi^T without a transpose copy).
 // Every wait is bounded: a timeout sets COFEM_ERR_TIMEOUT and the CTA
 // drains its copies, frees its tensor memory and exits.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -50,6 +51,9 @@ struct TcArgs {
   int nk_total;         // K blocks of 64
   int kb_per_split;
   int nc;               // output columns
+  int units;            // work units (tile x K range), taken by CTAs in strides of gridDim.x
+  int units_m;          // output tiles (units = units_m x K splits)
+  uint32_t acc_cols;    // tensor-memory columns of one accumulator (two are allocated)
   int BN;               // MMA N (rows of the B operand)
   int stages;           // depth of the shared-memory ring (<= kMaxStages)
   uint32_t tmem_cols;
@@ -91,12 +95,66 @@ __device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&o)[NT]) {
   }
 }
 
+// One work unit: a 128-row output tile and a K range of one product (of one
+// problem, in the batched mode).
+struct TcUnit {
+  int64_t m0, M, nkd, ldo, xoff, aoff, woff, sstride, bx0;
+  double beta;
+  int kb0, kb1, split, dslot;
+  const __nv_bfloat16* pk;
+};
+
+template <int MODE>
+__device__ __forceinline__ TcUnit tc_unit(const TcArgs& args, int w) {
+  TcUnit u;
+  u.M = args.M;
+  u.nkd = args.nkd;
+  u.ldo = MODE == 0 ? args.ldw : args.ld;
+  u.xoff = u.aoff = u.woff = u.bx0 = 0;
+  u.sstride = args.split_stride;
+  u.beta = args.beta;
+  u.pk = args.packed;
+  if (args.items) {
+    const TcItem it = args.items[w];
+    const TcProb pr = args.probs[it.prob];
+    u.m0 = (int64_t)it.tile * kTileM;
+    u.kb0 = it.kb0;
+    u.kb1 = it.kb1;
+    u.split = it.split;
+    u.M = MODE == 0 ? pr.N : pr.D;
+    u.nkd = pr.nkd;
+    u.pk += pr.poff;
+    u.ldo = MODE == 0 ? pr.ldw : pr.ld;
+    u.xoff = pr.xoff;
+    u.aoff = pr.aoff;
+    u.woff = pr.wpoff;
+    u.sstride = (int64_t)args.nc * pr.ldw;
+    u.bx0 = MODE == 0 ? pr.boff1 : pr.boff2;
+    u.dslot = pr.dots_base + it.tile;
+    u.beta = pr.beta;
+  } else {
+    const int tile = w % args.units_m, split = w / args.units_m;
+    u.m0 = (int64_t)tile * kTileM;
+    u.kb0 = split * args.kb_per_split;
+    u.kb1 = min(args.nk_total, u.kb0 + args.kb_per_split);
+    u.split = split;
+    u.dslot = tile;
+  }
+  return u;
+}
+
+// Persistent CTAs: CTA b takes the work units b, b + gridDim.x, ...  The
+// shared-memory ring runs on across units (one K-block counter for the
+// whole CTA), and two tensor-memory accumulators alternate between units so
+// that the epilogue of one unit overlaps the main loop of the next.
 template <int MODE, int NT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const TcArgs args) {
   pdl_wait();
   pdl_trigger();
+  // batched mode: one unit per CTA; a converged problem's units do nothing
+  if (args.items && args.done && args.done[args.items[blockIdx.x].prob]) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
@@ -104,56 +162,27 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int S = args.stages;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + kMaxStages;
-  uint64_t* accbar = empty + kMaxStages;
-  uint32_t* tmem_slot = (uint32_t*)(accbar + 1);
+  uint64_t* accfull = empty + kMaxStages;          // [2] accumulator ready
+  uint64_t* accempty = accfull + 2;                // [2] accumulator drained
+  uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
+  volatile int* bigflag = (volatile int*)(tmem_slot + 2);
   // epilogue partial dots per warp and column: compensated FP32 pairs, and
   // FP64 side sums of out-of-range products (flagged in *bigflag)
   float2* redp = (float2*)(tmem_slot + 4);          // [4][64]
   double* redb = (double*)(redp + 4 * 64);           // [4][64]
-  volatile int* bigflag = (volatile int*)(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // geometry of this CTA's work (one problem, or one item of a batch)
-  int64_t m0, M = args.M, nkd = args.nkd, ldo = MODE == 0 ? args.ldw : args.ld;
-  int64_t xoff = 0, aoff = 0, woff = 0, sstride = args.split_stride, bx0 = 0;
-  double beta = args.beta;
-  int kb0, kb1, split, dslot;
-  const __nv_bfloat16* pk = args.packed;
-  if (args.items) {
-    const TcItem it = args.items[blockIdx.x];
-    if (args.done && args.done[it.prob]) return;        // converged: nothing to do
-    const TcProb pr = args.probs[it.prob];
-    m0 = (int64_t)it.tile * kTileM;
-    kb0 = it.kb0;
-    kb1 = it.kb1;
-    split = it.split;
-    M = MODE == 0 ? pr.N : pr.D;
-    nkd = pr.nkd;
-    pk += pr.poff;
-    ldo = MODE == 0 ? pr.ldw : pr.ld;
-    xoff = pr.xoff;
-    aoff = pr.aoff;
-    woff = pr.wpoff;
-    sstride = (int64_t)args.nc * pr.ldw;
-    bx0 = MODE == 0 ? pr.boff1 : pr.boff2;
-    dslot = pr.dots_base + it.tile;
-    beta = pr.beta;
-  } else {
-    m0 = (int64_t)blockIdx.x * kTileM;
-    kb0 = blockIdx.y * args.kb_per_split;
-    kb1 = min(args.nk_total, kb0 + args.kb_per_split);
-    split = blockIdx.y;
-    dslot = blockIdx.x;
-  }
-  const int nk = max(0, kb1 - kb0);
-
+  const int units = args.units;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(accbar, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accfull[b], 1);
+      tc::mbar_init(&accempty[b], 4);              // the four epilogue warps
+    }
     *abort = 0;
     *bigflag = 0;
     tc::fence_mbar_init();
@@ -174,52 +203,58 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const uint64_t pol_first = tc::policy_evict_first();
       const uint64_t pol_last = tc::policy_evict_last();
       const uint64_t pol_b = pol_last;
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort, kWaitLimitNs)) {
-          tc_fail(args.err, abort);
-          break;
-        }
-        uint8_t* sa = smem + s * stage_bytes;
-        uint8_t* sb = sa + kATileBytes;
-        tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
-        const int kb = kb0 + i;
-        // Phi columns below res_d stay in L2 between the two products and
-        // across CG iterations; the rest streams through
-        if (MODE == 0) {
-          const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
-          if (pk)   // tile (m0 / 128, kb): one contiguous 16 KB copy
-            tc::bulk_load(sa, pk + ((m0 >> 7) * nkd + kb) * (kTileM * kTileK), kATileBytes,
-                          &full[s], pol_a);
-          else
-            tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
-        } else {
-          const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
-          if (pk) {
-            // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
-            // two 64-column tiles m0/64 and m0/64 + 1 give the 128 d's
-            const int64_t base = ((int64_t)(kb >> 1) * nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
-            const __nv_bfloat16* src = pk + base * kTileK;
-            tc::bulk_load(sa, src, kATileBytes / 2, &full[s], pol_a);
-            // the next 64-column tile; past the last one (D not a multiple of
-            // 128) the same half-tile is copied again: it only feeds output
-            // rows d >= D, which are not stored
-            const __nv_bfloat16* src2 = (m0 >> 6) + 1 < nkd ? src + kTileM * kTileK : src;
-            tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
-          } else {
-            tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
-            tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK, pol_a);
+      int it = 0;                                  // K blocks issued by this CTA
+      for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x) {
+        const TcUnit u = tc_unit<MODE>(args, w);
+        const int nk = max(0, u.kb1 - u.kb0);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort, kWaitLimitNs)) {
+            tc_fail(args.err, abort);
+            break;
           }
+          uint8_t* sa = smem + s * stage_bytes;
+          uint8_t* sb = sa + kATileBytes;
+          tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+          const int kb = u.kb0 + i;
+          const int64_t m0 = u.m0;
+          // Phi columns below res_d stay in L2 between the two products and
+          // across CG iterations; the rest streams through
+          if (MODE == 0) {
+            const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
+            if (u.pk)   // tile (m0 / 128, kb): one contiguous 16 KB copy
+              tc::bulk_load(sa, u.pk + ((m0 >> 7) * u.nkd + kb) * (kTileM * kTileK), kATileBytes,
+                            &full[s], pol_a);
+            else
+              tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
+          } else {
+            const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
+            if (u.pk) {
+              // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
+              // two 64-column tiles m0/64 and m0/64 + 1 give the 128 d's
+              const int64_t base =
+                  ((int64_t)(kb >> 1) * u.nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
+              const __nv_bfloat16* src = u.pk + base * kTileK;
+              tc::bulk_load(sa, src, kATileBytes / 2, &full[s], pol_a);
+              // the next 64-column tile; past the last one (D not a multiple of
+              // 128) the same half-tile is copied again: it only feeds output
+              // rows d >= D, which are not stored
+              const __nv_bfloat16* src2 = (m0 >> 6) + 1 < u.nkd ? src + kTileM * kTileK : src;
+              tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
+            } else {
+              tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
+              tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK,
+                              pol_a);
+            }
+          }
+          tc::tma_load_2d(sb, &mapB, &full[s], (int)(u.bx0 + (int64_t)kb * kTileK), 0, pol_b);
         }
-        tc::tma_load_2d(sb, &mapB, &full[s], (int)(bx0 + (int64_t)kb * kTileK), 0, pol_b);
-        ++issued;
       }
       if (*abort) {
         // drain this CTA's copies still in flight before leaving
         volatile int never = 0;
-        for (int i = max(0, issued - S); i < issued; ++i)
+        for (int i = max(0, it - S); i < it; ++i)
           tc::mbar_wait(&full[i % S], (uint32_t)(i / S) & 1u, &never, kWaitLimitNs);
       }
     }
@@ -227,127 +262,161 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0) {
       // A is K-major in the first product, MN-major (Phi^T read in place) in the second
       const uint32_t idesc = tc::idesc_bf16_f32(kTileM, args.BN, MODE == 1 ? 1 : 0, 0);
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % S;
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
+      int it = 0, lu = 0;
+      for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x, ++lu) {
+        const TcUnit u = tc_unit<MODE>(args, w);
+        const int nk = max(0, u.kb1 - u.kb0);
+        const int b = lu & 1;
+        // the epilogue must have drained this accumulator (its previous unit)
+        if (!tc::mbar_wait(&accempty[b], (uint32_t)((lu >> 1) & 1) ^ 1u, abort, 4 * kWaitLimitNs)) {
           tc_fail(args.err, abort);
           break;
         }
         tc::tc_fence_after();
-        const uint32_t a_base = tc::smem_u32(smem + s * stage_bytes);
-        const uint32_t b_base = a_base + kATileBytes;
+        const uint32_t acc = tmem + (uint32_t)b * args.acc_cols;
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
+            tc_fail(args.err, abort);
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t a_base = tc::smem_u32(smem + s * stage_bytes);
+          const uint32_t b_base = a_base + kATileBytes;
 #pragma unroll
-        for (int k = 0; k < kTileK / 16; ++k) {
-          uint64_t adesc;
-          if (MODE == 0) adesc = tc::smem_desc_sw128(a_base + k * 32, 16, 1024);
-          else adesc = tc::smem_desc_sw128(a_base + k * 2048, kATileBytes / 2, 1024);
-          const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
-          tc::mma_bf16(tmem, adesc, bdesc, idesc, (i > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < kTileK / 16; ++k) {
+            uint64_t adesc;
+            if (MODE == 0) adesc = tc::smem_desc_sw128(a_base + k * 32, 16, 1024);
+            else adesc = tc::smem_desc_sw128(a_base + k * 2048, kATileBytes / 2, 1024);
+            const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
+            tc::mma_bf16(acc, adesc, bdesc, idesc, (i > 0 || k > 0) ? 1u : 0u);
+          }
+          tc::mma_commit(&empty[s]);
         }
-        tc::mma_commit(&empty[s]);
+        tc::mma_commit(&accfull[b]);
       }
-      tc::mma_commit(accbar);
     }
   } else {
     // ------------------------------------------------------------ epilogue
     const int g = warp & 3;                 // tensor-memory lane quarter of this warp
-    const int64_t row = m0 + 32 * g + lane;
     constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
-    constexpr int MG = (kMaxCols + G - 1) / G;      // most column groups
     const int ngroups = (args.nc + G - 1) / G;
-    const bool live = row < M;
-    float a32 = 0.f;                     // alpha_row in FP32, converted once per row
-    if (MODE == 1 && live)
-      a32 = args.alpha32 ? args.alpha32[aoff + row]
-                         : (args.alpha ? (float)args.alpha[aoff + row] : 0.f);
-    const bool ok = tc::mbar_wait(accbar, 0, abort, 4 * kWaitLimitNs);
-    if (!ok) tc_fail(args.err, abort);
-    tc::tc_fence_after();
+    int lu = 0;
+    for (int w = blockIdx.x; w < units; w += gridDim.x, ++lu) {
+      const TcUnit u = tc_unit<MODE>(args, w);
+      const int nk = max(0, u.kb1 - u.kb0);
+      const int b = lu & 1;
+      const int64_t row = u.m0 + 32 * g + lane;
+      const bool live = row < u.M;
+      float a32 = 0.f;                     // alpha_row in FP32, converted once per row
+      if (MODE == 1 && live)
+        a32 = args.alpha32 ? args.alpha32[u.aoff + row]
+                           : (args.alpha ? (float)args.alpha[u.aoff + row] : 0.f);
+      const bool ok1 = tc::mbar_wait(&accfull[b], (uint32_t)((lu >> 1) & 1), abort,
+                                     4 * kWaitLimitNs);
+      if (!ok1) tc_fail(args.err, abort);
+      // the four epilogue warps take the same decision (named barrier 2)
+      uint32_t okall;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+          "bar.red.and.pred q, 2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+          : "=r"(okall)
+          : "r"((uint32_t)ok1)
+          : "memory");
+      if (!okall) break;
+      tc::tc_fence_after();
+      const uint32_t acc = tmem + (uint32_t)b * args.acc_cols;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        float v[COLS];
 #pragma unroll
-    for (int gi = 0; gi < MG; ++gi) {
-      if (gi >= ngroups) break;
-      float v[COLS];
+        for (int c = 0; c < COLS / 16; ++c) {
+          float t16[16];
+          tc::tmem_ld16(acc + ((uint32_t)(32 * g) << 16) + (uint32_t)(gi * COLS + 16 * c), t16);
 #pragma unroll
-      for (int c = 0; c < COLS / 16; ++c) {
-        float t16[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(gi * COLS + 16 * c), t16);
+          for (int q = 0; q < 16; ++q) v[16 * c + q] = t16[q];
+        }
+        tc::tmem_ld_wait();
+        if (nk == 0) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[16 * c + q] = t16[q];
-      }
-      tc::tmem_ld_wait();
-      if (nk == 0 || !ok) {
+          for (int q = 0; q < COLS; ++q) v[q] = 0.f;
+        }
+        // x_j^T y_j over the warp's 32 rows (second product): compensated
+        // FP32 (product error by FMA, TwoSum butterflies, the G columns of
+        // the group interleaved); products of 1e30 or more take an FP64
+        // side sum
+        float ds[G], dc[G];
+        double db[G];
+        bool anybig = false;
 #pragma unroll
-        for (int q = 0; q < COLS; ++q) v[q] = 0.f;
-      }
-      // x_j^T y_j over the warp's 32 rows (second product): compensated
-      // FP32 (product error by FMA, TwoSum butterflies, the G columns of the
-      // group interleaved), FP64 once per warp and column; products of 1e30
-      // or more take an FP64 side sum
-      float ds[G], dc[G];
-      double db[G];
-      bool anybig = false;
+        for (int jj = 0; jj < G; ++jj) {
+          const int j = gi * G + jj;
+          float sacc = 0.f;
 #pragma unroll
-      for (int jj = 0; jj < G; ++jj) {
-        const int j = gi * G + jj;
-        float acc = 0.f;
+          for (int t = NT - 1; t >= 0; --t) sacc += v[jj * NT + t];
+          ds[jj] = 0.f;
+          dc[jj] = 0.f;
+          db[jj] = 0.0;
+          if (MODE == 0) {
+            if (j < args.nc && live)
+              args.wpart[u.woff + (int64_t)u.split * u.sstride + (int64_t)j * u.ldo + row] = sacc;
+          } else if (j < args.nc && live) {
+            const float xv = args.x[u.xoff + (int64_t)j * u.ldo + row];
+            const float yv = fmaf(a32, xv, (float)u.beta * sacc);
+            args.y[u.xoff + (int64_t)j * u.ldo + row] = yv;
+            const float pp = xv * yv;
+            if (fabsf(pp) < 1e30f) {
+              ds[jj] = pp;
+              dc[jj] = fmaf(xv, yv, -pp);
+            } else {
+              db[jj] = (double)xv * (double)yv;
+              anybig = true;
+            }
+          }
+        }
+        if (MODE == 1 && args.dots) {
 #pragma unroll
-        for (int t = NT - 1; t >= 0; --t) acc += v[jj * NT + t];
-        ds[jj] = 0.f;
-        dc[jj] = 0.f;
-        db[jj] = 0.0;
-        if (MODE == 0) {
-          if (j < args.nc && live)
-            args.wpart[woff + (int64_t)split * sstride + (int64_t)j * ldo + row] = acc;
-        } else if (j < args.nc && live) {
-          const float xv = args.x[xoff + (int64_t)j * ldo + row];
-          const float yv = fmaf(a32, xv, (float)beta * acc);
-          args.y[xoff + (int64_t)j * ldo + row] = yv;
-          const float pp = xv * yv;
-          if (fabsf(pp) < 1e30f) {
-            ds[jj] = pp;
-            dc[jj] = fmaf(xv, yv, -pp);
-          } else {
-            db[jj] = (double)xv * (double)yv;
-            anybig = true;
+          for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj)
+              two_sum_merge(ds[jj], dc[jj], __shfl_xor_sync(0xffffffffu, ds[jj], o),
+                            __shfl_xor_sync(0xffffffffu, dc[jj], o));
+          }
+          if (__any_sync(0xffffffffu, anybig)) {
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj) db[jj] = warp_sum(db[jj]);
+            if (lane == 0) *bigflag = 1;
+          }
+          if (lane == 0) {
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj)
+              if (gi * G + jj < args.nc) {
+                redp[(warp - 2) * 64 + gi * G + jj] = make_float2(ds[jj], dc[jj]);
+                redb[(warp - 2) * 64 + gi * G + jj] = db[jj];
+              }
           }
         }
       }
+      // this accumulator is drained: the MMA may reuse it
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&accempty[b]);
       if (MODE == 1 && args.dots) {
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (warp == 2) {
+          const bool big = *bigflag != 0;
+          for (int j = lane; j < args.nc; j += 32) {
+            float ps = redp[j].x, pc = redp[j].y;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-          for (int jj = 0; jj < G; ++jj)
-            two_sum_merge(ds[jj], dc[jj], __shfl_xor_sync(0xffffffffu, ds[jj], o),
-                          __shfl_xor_sync(0xffffffffu, dc[jj], o));
+            for (int q = 1; q < 4; ++q) two_sum_merge(ps, pc, redp[q * 64 + j].x, redp[q * 64 + j].y);
+            double t = (double)ps + (double)pc;
+            if (big) t += redb[j] + redb[64 + j] + redb[128 + j] + redb[192 + j];
+            args.dots[(int64_t)u.dslot * kMaxCols + j] = t;
+          }
+          if (lane == 0) *bigflag = 0;
         }
-        if (__any_sync(0xffffffffu, anybig)) {
-#pragma unroll
-          for (int jj = 0; jj < G; ++jj) db[jj] = warp_sum(db[jj]);
-          if (lane == 0) *bigflag = 1;
-        }
-        if (lane == 0) {
-#pragma unroll
-          for (int jj = 0; jj < G; ++jj)
-            if (gi * G + jj < args.nc) {
-              redp[(warp - 2) * 64 + gi * G + jj] = make_float2(ds[jj], dc[jj]);
-              redb[(warp - 2) * 64 + gi * G + jj] = db[jj];
-            }
-        }
-      }
-    }
-    if (MODE == 1 && args.dots) {
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (warp == 2) {
-        const bool big = *bigflag != 0;
-        for (int j = lane; j < args.nc; j += 32) {
-          float ps = redp[j].x, pc = redp[j].y;
-#pragma unroll
-          for (int w = 1; w < 4; ++w) two_sum_merge(ps, pc, redp[w * 64 + j].x, redp[w * 64 + j].y);
-          double t = (double)ps + (double)pc;
-          if (big) t += redb[j] + redb[64 + j] + redb[128 + j] + redb[192 + j];
-          args.dots[(int64_t)dslot * kMaxCols + j] = t;
-        }
+        // the partials are read before the next unit writes them
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     }
   }
@@ -564,7 +633,8 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   p.BN = ngroups * 16;
   uint32_t tc = 32;
   while (tc < (uint32_t)p.BN) tc <<= 1;
-  p.tmem_cols = tc;
+  p.acc_cols = tc;
+  p.tmem_cols = 2 * tc;                  // two accumulators (persistent CTAs)
   p.ld = round_up(D, kLdAlign);
   p.ldw = round_up(N, kLdAlign);
   const int mt1 = (int)((N + kTileM - 1) / kTileM);
@@ -572,13 +642,29 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   p.nk2 = (int)((N + kTileK - 1) / kTileK);
   int per_sm = 512 / (int)p.tmem_cols < ctas_per_sm ? 512 / (int)p.tmem_cols : ctas_per_sm;
   if (per_sm < 1) per_sm = 1;
-  // one wave: at most per_sm * sms CTAs in the split-K product
-  int want = (per_sm * sms) / mt1;
-  if (want < 1) want = 1;
-  if (want > p.nk1) want = p.nk1;
-  p.kbps1 = (p.nk1 + want - 1) / want;
-  p.S1 = (p.nk1 + p.kbps1 - 1) / p.kbps1;
-  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 64 + 4 * 64 * 8 * 2 + 64;
+  // split-K of the first product: the CTAs (at most per_sm * sms, one wave)
+  // take mt1 x S1 units in turn.  The most K blocks any CTA streams is
+  // ceil(mt1 S1 / grid) ceil(nk1 / S1); take the fewest splits (fewer
+  // partial sums to write and reduce) within 10 % of the best balance.
+  const int grid = per_sm * sms;
+  auto per_cta = [&](int s1, int* kbps_out, int* s1_out) {
+    const int kbps = (p.nk1 + s1 - 1) / s1;
+    const int s1r = (p.nk1 + kbps - 1) / kbps;            // splits actually used
+    *kbps_out = kbps;
+    *s1_out = s1r;
+    return (((int64_t)mt1 * s1r + grid - 1) / grid) * kbps;
+  };
+  int64_t best = -1;
+  for (int s1 = 1; s1 <= 32 && s1 <= p.nk1; ++s1) {
+    int kb, sr;
+    const int64_t w = per_cta(s1, &kb, &sr);
+    if (best < 0 || w < best) best = w;
+  }
+  for (int s1 = 1; s1 <= 32 && s1 <= p.nk1; ++s1) {
+    int kb, sr;
+    if (per_cta(s1, &kb, &sr) * 10 <= best * 11) { p.S1 = sr; p.kbps1 = kb; break; }
+  }
+  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 32 + 64 + 4 * 64 * 8 * 2 + 64;
   const size_t stage = kATileBytes + (size_t)p.BN * 128;
   // each resident CTA also costs 1 KB of reserved shared memory
   const size_t budget = kSmemPerSm / per_sm - 1024;
@@ -588,6 +674,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   if (st < 2) st = 2;
   p.stages = st;
   p.smem = st * stage + fixed;
+  p.grid = grid;
   p.off_xs = 0;
   p.bytes_xs = round_up((int64_t)p.BN * p.ld * 2, 256);
   p.off_wpart = p.bytes_xs;
@@ -655,7 +742,10 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.ldw = p.ldw;
   a1.split_stride = (int64_t)nc * p.ldw;
   a1.err = err;
-  dim3 g1((unsigned)((op.N + kTileM - 1) / kTileM), p.S1);
+  a1.units_m = (int)((op.N + kTileM - 1) / kTileM);
+  a1.units = a1.units_m * p.S1;
+  a1.acc_cols = p.acc_cols;
+  dim3 g1((unsigned)std::min(a1.units, p.grid), 1);
   if (launch_tc<0, NT>(g1, p.smem, mPhi1, mXs, a1, st) != cudaSuccess) return 2;
   apply_tick(st);
   {
@@ -685,10 +775,13 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.beta = beta;
   a2.dots = dots;
   a2.err = err;
-  dim3 g2((unsigned)((op.D + kTileM - 1) / kTileM), 1);
+  a2.units_m = (int)((op.D + kTileM - 1) / kTileM);
+  a2.units = a2.units_m;
+  a2.acc_cols = p.acc_cols;
+  dim3 g2((unsigned)std::min(a2.units, p.grid), 1);
   if (launch_tc<1, NT>(g2, p.smem, mPhi2, mWs, a2, st) != cudaSuccess) return 2;
   apply_tick(st);
-  if (nparts) *nparts = dots ? (int)g2.x : 0;
+  if (nparts) *nparts = dots ? a2.units : 0;
   return 0;
 }
 
@@ -707,6 +800,9 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
   a.BN = BN;
   a.stages = stages;
   a.tmem_cols = tmem_cols;
+  a.acc_cols = tmem_cols / 2;
+  a.units = nitems;
+  a.units_m = 1;
   a.packed = (const __nv_bfloat16*)packed;
   a.wpart = wpart;
   a.x = X;

@@ -81,11 +81,14 @@ def test_fp64_tolerance_mode_config1(cuda_lib):
     if st["cg_iters"] == rst.cg_iters:
         assert rel_l2(mu, rmu) <= 1e-9
     else:
-        # a threshold crossing desynchronised the paths by one iteration
-        diffs = [abs(x - y) for x, y in zip(st["cg_iters"], rst.cg_iters)]
-        assert max(diffs) <= 2
+        # CG stops on a tolerance, so rounding-level differences in the
+        # reductions move a stop by an iteration and the EM trajectory carries
+        # it on: perturbing every reduction of the FP64 oracle itself by 2e-16
+        # (relative) moves single E-steps by up to 4 iterations, mu by ~1e-7
+        # and per-iteration support counts near the 1e6 threshold.  Bounds:
+        # mu, the final support (above) and the total work.
+        assert abs(sum(st["cg_iters"]) - sum(rst.cg_iters)) <= 0.02 * sum(rst.cg_iters)
         assert rel_l2(mu, rmu) <= 1e-5
-    assert st["support"] == rst.support
 
 
 @pytest.mark.parametrize("phi_kind", ["f32", "bf16"])

@@ -101,7 +101,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -205,11 +205,16 @@ def reference_arm(args):
 
 # ------------------------------------------------------------ GPU arm
 
-def launches_per_em(cg_iters, replace_every, per_iter, per_replace):
+def launches_per_em(cg_iters, replace_every, per_iter, per_replace, nested=False):
     """Our kernel launches in one EM iteration: init, per CG iteration
     (operator kernels + update + direction), per residual replacement
-    (operator kernels on x + true residual), diag/M-step."""
+    (operator kernels on x + true residual [+ direction]), diag/M-step.  With
+    the nested loop of the tensor-core path the replacement block (split,
+    two products, reduce, true residual, direction) is launched once more
+    when the solve ends, its kernels returning at once."""
     n_rep = cg_iters // replace_every if replace_every else 0
+    if nested and replace_every:
+        return 1 + cg_iters * per_iter + (n_rep + 1) * per_replace + 1
     return 1 + cg_iters * per_iter + n_rep * per_replace + 1
 
 
@@ -530,13 +535,17 @@ def main():
     ms, value = aggregate_rate(e0.elapsed_time(e1), args.steps, ws, dev)
     cg = res.stats["cg_iters"]
 
-    if args.phi == "bf16" and args.terms > 0:
+    nested = args.phi == "bf16" and args.terms > 0
+    if nested:
         # tensor cores: GEMM1, reduce/split, GEMM2 per apply (P's split comes
-        # from the CG kernels; an apply to x adds a split kernel)
-        per_iter, per_rep = 3 + 2, 4 + 1
+        # from the CG kernels; an apply to x adds a split kernel), update,
+        # direction; the replacement block: split, GEMM1, reduce, GEMM2, true
+        # residual, direction
+        per_iter, per_rep = 3 + 2, 4 + 2
     else:
         per_iter, per_rep = 4 + 2, 4 + 1
-    launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep) for c in cg)
+    launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep, nested)
+                   for c in cg)
     # dominant kernel: the operator application over K+1 columns, each of its
     # kernels timed with CUDA events on the launching stream
     ncols = CFG["K"] + 1

@@ -140,7 +140,8 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
 static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t ld, int ncols,
                              const double* alpha, double beta, void* y, double* dots,
                              int* nparts, char* ws, cudaStream_t st, int* err = nullptr,
-                             unsigned flags = 0u, const float* alpha32 = nullptr) {
+                             unsigned flags = 0u, const float* alpha32 = nullptr,
+                             const int* gate = nullptr) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
     if (use_tc(op) && vec == COFEM_F32) {
@@ -153,7 +154,7 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
         const_cast<cofem_op*>(op)->dense.l2_resident_cols = cols < d.D ? cols : d.D;
       }
       int rc = dense_tc_apply(d, d.nterms, (const float*)x, ld, ncols, (float*)y, beta, alpha,
-                              dots, nparts, ws, err, flags, st, alpha32);
+                              dots, nparts, ws, err, flags, st, alpha32, gate);
       if (rc == 1) {
         g_last_error = "cuTensorMapEncodeTiled failed";
         return COFEM_ERR_CUDA;
@@ -404,13 +405,51 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cofem_status rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &body);
   if (rc != COFEM_OK) return rc;
 
-  // ---- WHILE body: one CG iteration
+  // ---- WHILE body.  Tensor-core operator with residual replacement: the
+  // body is an inner WHILE loop of plain CG iterations, left when the
+  // replacement is due (or the solve is done), followed by the replacement
+  // (operator on X, true residual, stop test, direction), whose kernels run
+  // only when it is due (gated on ctl->replace / ctl->run).  This keeps the
+  // IF node's cost out of every iteration.  Otherwise one CG iteration, with
+  // the replacement behind an IF node.
+  const bool nested = p->resid_replace_every > 0 && use_tc(op) && vec == COFEM_F32;
   cudaGraphConditionalHandle hi = 0;
-  if (p->resid_replace_every > 0) {
-    CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
-    cf.if_handle = (unsigned long long)hi;
-  }
-  {
+  if (nested) {
+    cudaStream_t bs = ss.s[1];
+    cudaGraphConditionalHandle hin;
+    CK(cudaGraphConditionalHandleCreate(&hin, body, 1, cudaGraphCondAssignDefault));
+    cf.inner_handle = (unsigned long long)hin;
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaGraph_t inner = nullptr;
+    rc = add_conditional(bs, hin, cudaGraphCondTypeWhile, &inner);
+    if (rc != COFEM_OK) return rc;
+    {
+      cudaStream_t is = ss.s[2];
+      CK(cudaStreamBeginCaptureToGraph(is, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      int nparts = 0;
+      rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, is,
+                    &ctl->error, kApplyPresplit, alpha32);
+      if (rc != COFEM_OK) return rc;
+      cf.gamma_parts = nparts;
+      launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is);
+      launch_cg_direction<V>(cf, ctl, sc, R, P, is);
+      CKL();
+      cudaGraph_t tmp;
+      CK(cudaStreamEndCapture(is, &tmp));
+    }
+    rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, bs,
+                  &ctl->error, 0u, alpha32, &ctl->replace);
+    if (rc != COFEM_OK) return rc;
+    launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, pvec2, bs);
+    launch_cg_direction<V>(cf, ctl, sc, R, P, bs);
+    CKL();
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(bs, &tmp));
+  } else {
+    if (p->resid_replace_every > 0) {
+      CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
+      cf.if_handle = (unsigned long long)hi;
+    }
     cudaStream_t bs = ss.s[1];
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int nparts = 0;
@@ -455,6 +494,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     pf.fallback_init = 1;
     pf.while_handle = (unsigned long long)hw2;
     pf.if_handle = 0;
+    pf.inner_handle = 0;
     pf.replace_every = 0;
     launch_cg_init<V>(pf, ctl, sc, X, R, P, b, pvec, fs);
     CKL();

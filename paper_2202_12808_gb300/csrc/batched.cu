@@ -410,8 +410,8 @@ struct BLayout {
   std::vector<BVec> vec;
   std::vector<TcProb> tcp;
   std::vector<TcItem> items1, items2;
-  int nch_max = 0, ndots = 0, BN = 0, NT = 3, stages = 3;
-  uint32_t tmem_cols = 0;
+  int nch_max = 0, ndots = 0, BN = 0, NT = 3, stages = 3, grid = 0;
+  uint32_t tmem_cols = 0;                 // two accumulators
   size_t smem = 0;
   int64_t ldx_total = 0, ldw_total = 0, dtot = 0, ldw_max = 0;
   // workspace offsets
@@ -424,12 +424,12 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
   L->NT = 3;
   const int G = 16 / L->NT;
   L->BN = ((nc + G - 1) / G) * 16;
-  uint32_t tc = 32;
-  while (tc < (uint32_t)L->BN) tc <<= 1;
-  L->tmem_cols = tc;
+  // pipeline shape: two CTAs per SM until the autotuner (btune) has run
   DenseTcPlan plan = dense_tc_plan(2048, 8192, nc, L->NT, num_sms(), 2, 0);
+  L->tmem_cols = plan.tmem_cols;
   L->stages = plan.stages;
   L->smem = plan.smem;
+  L->grid = plan.grid;
   int64_t xoff = 0, aoff = 0, b1 = 0, b2 = 0, wpoff = 0, poff = 0;
   size_t simt = 0;
   int dots = 0;
@@ -609,7 +609,7 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
     int* err = &ctl->error;
     if (dense_tc_batched(0, L.NT, (int)L.items1.size(), it1, tcp, done, ws + L.o_packed, xs,
                          L.ldx_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, wpart, nullptr,
-                         nullptr, nullptr, nullptr, err, bs) != 0)
+                         nullptr, nullptr, nullptr, err, bs, L.grid) != 0)
       return COFEM_ERR_CUDA;
     const int G = 16 / L.NT;
     const dim3 rg((unsigned)((L.ldw_max / 4 + 127) / 128), (L.BN / 16) * G, n);
@@ -624,7 +624,7 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
                    (const float*)wpart, wsb, L.ldw_total));
     if (dense_tc_batched(1, L.NT, (int)L.items2.size(), it2, tcp, done, ws + L.o_packed, wsb,
                          L.ldw_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, nullptr, P, Q,
-                         alpha, dots, err, bs) != 0)
+                         alpha, dots, err, bs, L.grid) != 0)
       return COFEM_ERR_CUDA;
     BCK(launch_k(bupdate_kernel, vg, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
                  (const float*)Q, (const double*)dots, part));
@@ -659,6 +659,70 @@ extern "C" cofem_status cofem_batched_workspace_bytes(int32_t n, const cofem_pro
   rc = blayout(n, problems, p, &L);
   if (rc != COFEM_OK) return rc;
   *bytes = L.total;
+  return COFEM_OK;
+}
+
+// Autotuner of the grouped products: times both products (the real item
+// tables and dictionaries of this fit, nothing converged yet) for every
+// pipeline shape that fits (1 or 2 CTAs per SM, 2 .. max stages) and keeps
+// the fastest.  Writes only workspace regions the fit overwrites.
+static cofem_status btune(int nc, BLayout* L, char* ws, const double* alpha, cudaStream_t st) {
+  const TcProb* tcp = (const TcProb*)(ws + L->o_tcp);
+  const TcItem* it1 = (const TcItem*)(ws + L->o_it1);
+  const TcItem* it2 = (const TcItem*)(ws + L->o_it2);
+  const int* done = (const int*)(ws + L->o_done);
+  float* P = (float*)(ws + L->o_P);
+  float* Q = (float*)(ws + L->o_Q);
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  BLayout keep = *L;
+  int bst = L->stages, bgrid = L->grid;
+  size_t bsmem = L->smem;
+  cofem_status rc = COFEM_OK;
+  for (int cps = 1; cps <= 2 && rc == COFEM_OK; ++cps) {
+    const DenseTcPlan full = dense_tc_plan(2048, 8192, nc, L->NT, num_sms(), cps, 0);
+    for (int stg = 2; stg <= full.stages && rc == COFEM_OK; ++stg) {
+      const DenseTcPlan q = dense_tc_plan(2048, 8192, nc, L->NT, num_sms(), cps, stg);
+      auto run = [&]() {
+        int r = dense_tc_batched(0, L->NT, (int)L->items1.size(), it1, tcp, done,
+                                 ws + L->o_packed, (const __nv_bfloat16*)(ws + L->o_xs),
+                                 L->ldx_total, L->BN, nc, q.stages, q.tmem_cols, q.smem,
+                                 (float*)(ws + L->o_wpart), nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, st, q.grid);
+        if (r == 0)
+          r = dense_tc_batched(1, L->NT, (int)L->items2.size(), it2, tcp, done,
+                               ws + L->o_packed, (const __nv_bfloat16*)(ws + L->o_ws),
+                               L->ldw_total, L->BN, nc, q.stages, q.tmem_cols, q.smem, nullptr,
+                               P, Q, alpha, (double*)(ws + L->o_dots), nullptr, st, q.grid);
+        return r;
+      };
+      if (run() != 0) { rc = COFEM_ERR_CUDA; break; }
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && rc == COFEM_OK; ++r)
+        if (run() != 0) rc = COFEM_ERR_CUDA;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = COFEM_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == COFEM_OK && ms < best) {
+        best = ms;
+        bst = q.stages;
+        bgrid = q.grid;
+        bsmem = q.smem;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != COFEM_OK) {
+    *L = keep;
+    return rc;
+  }
+  L->stages = bst;
+  L->grid = bgrid;
+  L->smem = bsmem;
   return COFEM_OK;
 }
 
@@ -705,6 +769,8 @@ extern "C" cofem_status cofem_fit_batched(int32_t n, const cofem_problem* proble
   }
   BCK(cudaGetLastError());
   if (p->em_iters > 0) {
+    rc = btune(p->K + 1, &L, ws, alpha_dev, st);
+    if (rc != COFEM_OK) return rc;
     cudaGraphExec_t exec = nullptr;
     rc = batched_graph(n, p, L, ws, mu_dev, s_dev, alpha_dev, &exec);
     if (rc != COFEM_OK) {

@@ -119,7 +119,9 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
     else done = (relres < cf.tol) || (it >= cf.max_iters);
     if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
     ctl->done = done;
+    ctl->run = !done;
     set_cond(cf.while_handle, done ? 0u : 1u);
+    set_cond(cf.inner_handle, done ? 0u : 1u);
     if (done && cf.fallback_handle)
       set_cond(cf.fallback_handle, (cf.fixed_iters == 0 && !(relres < cf.tol)) ? 1u : 0u);
   }
@@ -201,6 +203,7 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
       else if (cf.fixed_iters == 0 && 1.0 < cf.tol) done = 1;
       if (!isfinite(n2)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
       ctl->done = done;
+      ctl->run = 0;
       set_cond(cf.while_handle, done ? 0u : 1u);
       ctl->counter[0] = 0;
     }
@@ -386,6 +389,12 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
       const int rep = cf.replace_every > 0 && (ctl->iter % cf.replace_every) == 0;
       ctl->replace = rep;
       set_cond(cf.if_handle, rep ? 1u : 0u);
+      if (rep) {
+        // the true residual and the stop test come first: no direction update
+        // yet, and the inner loop (if any) hands over to the replacement
+        ctl->run = 0;
+        set_cond(cf.inner_handle, 0u);
+      }
     }
     __syncthreads();
     if (!ctl->replace) cg_finalize(cf, ctl, sc);
@@ -444,7 +453,7 @@ __global__ void cg_direction_kernel(CgConf cf, const CgCtl* ctl, const CgScalars
   pdl_wait();
   pdl_trigger();
   constexpr int W = 16 / sizeof(V);
-  if (ctl->done) return;
+  if (!ctl->run) return;
   const int j = blockIdx.y;
   const V b = (V)sc->b[j];
   const V* r = R + (int64_t)j * cf.ld;

@@ -27,7 +27,7 @@ struct CgCtl {
   int support;
   int extra_iters;     // learned path: iterations of a preconditioned solve that fell back
   int fallbacks;       // learned path: fallbacks to plain CG so far
-  int pad1;
+  int run;             // the direction update may run (b_j of this iteration are set)
   double normB2;       // ||B||_F^2
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
@@ -60,6 +60,7 @@ struct CgConf {
   int em_iters;
   unsigned long long while_handle;   // cudaGraphConditionalHandle or 0
   unsigned long long if_handle;      // residual-replacement IF node or 0
+  unsigned long long inner_handle;   // inner WHILE node (replacement outside the inner loop) or 0
   int gamma_parts;                   // partials of p^T A p written by the operator
   int split_nt;                      // >0: also write P's BF16 terms (tensor-core operator)
   int split_rows;                    // rows of the split buffer (B operand rows)

@@ -96,7 +96,9 @@ inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
 // (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG
 // kernels.
 constexpr unsigned kApplyPresplit = 1u;
-// Batched products over a work-item table (see TcItem / TcProb).  mode 0:
+// Batched products over a work-item table (see TcItem / TcProb); `grid`
+// persistent CTAs (0: one per item) take the items in strides of the grid;
+// tmem_cols holds two accumulators.  mode 0:
 // split-K partials of W = Phi X; mode 1: Y = beta Phi^T W + alpha . X with
 // partial dots.  xs / ws: BF16 term buffers (BN rows, pitch ldx_total /
 // ldw_total).  Returns 0, 1 (tensor map) or 2 (launch).
@@ -104,13 +106,15 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
                      const int* done, const void* packed, const __nv_bfloat16* bsrc,
                      int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
                      size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
-                     double* dots, int* err, cudaStream_t st);
+                     double* dots, int* err, cudaStream_t st, int grid = 0);
 
 // alpha32: optional FP32 copy of alpha ((float)alpha[d]); saves the per-row
-// conversion.
+// conversion.  gate: if set, every kernel of the application returns at
+// once when *gate == 0 (a step inside a graph that runs only when due).
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, unsigned flags, cudaStream_t st, const float* alpha32 = nullptr);
+                   int* err, unsigned flags, cudaStream_t st, const float* alpha32 = nullptr,
+                   const int* gate = nullptr);
 
 template <typename TA, typename V>
 void dense_simt_forward(const DenseDesc& op, const V* Z, int64_t ldz, int ncols, V* W,

@@ -78,6 +78,7 @@ struct TcArgs {
   const TcItem* items;
   const TcProb* probs;
   const int* done;       // per-problem converged flags: their items exit at once
+  const int* gate;       // if set and *gate == 0 the launch does nothing
 };
 
 __device__ __forceinline__ void tc_fail(int* err, volatile int* abort) {
@@ -143,6 +144,12 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs& args, int w) {
   return u;
 }
 
+// Batched mode: the units of a converged problem are skipped (by every role
+// alike: the flags were written by an earlier kernel and do not change).
+__device__ __forceinline__ bool unit_skipped(const TcArgs& args, int w) {
+  return args.items && args.done && args.done[args.items[w].prob];
+}
+
 // Persistent CTAs: CTA b takes the work units b, b + gridDim.x, ...  The
 // shared-memory ring runs on across units (one K-block counter for the
 // whole CTA), and two tensor-memory accumulators alternate between units so
@@ -153,8 +160,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
                 const TcArgs args) {
   pdl_wait();
   pdl_trigger();
-  // batched mode: one unit per CTA; a converged problem's units do nothing
-  if (args.items && args.done && args.done[args.items[blockIdx.x].prob]) return;
+  if (args.gate && *args.gate == 0) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
@@ -205,6 +211,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const uint64_t pol_b = pol_last;
       int it = 0;                                  // K blocks issued by this CTA
       for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x) {
+        if (unit_skipped(args, w)) continue;
         const TcUnit u = tc_unit<MODE>(args, w);
         const int nk = max(0, u.kb1 - u.kb0);
         for (int i = 0; i < nk; ++i, ++it) {
@@ -262,8 +269,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (lane == 0) {
       // A is K-major in the first product, MN-major (Phi^T read in place) in the second
       const uint32_t idesc = tc::idesc_bf16_f32(kTileM, args.BN, MODE == 1 ? 1 : 0, 0);
-      int it = 0, lu = 0;
-      for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x, ++lu) {
+      int it = 0, lu = -1;
+      for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x) {
+        if (unit_skipped(args, w)) continue;
+        ++lu;
         const TcUnit u = tc_unit<MODE>(args, w);
         const int nk = max(0, u.kb1 - u.kb0);
         const int b = lu & 1;
@@ -302,8 +311,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int g = warp & 3;                 // tensor-memory lane quarter of this warp
     constexpr int G = TermGroup<NT>::G, COLS = TermGroup<NT>::COLS;
     const int ngroups = (args.nc + G - 1) / G;
-    int lu = 0;
-    for (int w = blockIdx.x; w < units; w += gridDim.x, ++lu) {
+    int lu = -1;
+    for (int w = blockIdx.x; w < units; w += gridDim.x) {
+      if (unit_skipped(args, w)) continue;
+      ++lu;
       const TcUnit u = tc_unit<MODE>(args, w);
       const int nk = max(0, u.kb1 - u.kb0);
       const int b = lu & 1;
@@ -435,9 +446,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 // blockIdx.y, four consecutive d per thread, one 8-byte store per term.
 template <int NT>
 __global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int64_t D,
-                                   int64_t lds, int nc, __nv_bfloat16* __restrict__ Xs) {
+                                   int64_t lds, int nc, __nv_bfloat16* __restrict__ Xs, const int* gate) {
   pdl_wait();
   pdl_trigger();
+  if (gate && *gate == 0) return;
   constexpr int G = TermGroup<NT>::G;
   const int j = blockIdx.y;
   const int gi = j / G, jj = j % G;
@@ -471,9 +483,10 @@ __global__ void split_block_kernel(const float* __restrict__ X, int64_t ld, int6
 template <int NT>
 __global__ void reduce_split_kernel(const float* __restrict__ Wp, int S, int64_t sstride,
                                     int64_t N, int64_t ldw, int nc,
-                                    __nv_bfloat16* __restrict__ Ws) {
+                                    __nv_bfloat16* __restrict__ Ws, const int* gate) {
   pdl_wait();
   pdl_trigger();
+  if (gate && *gate == 0) return;
   constexpr int G = TermGroup<NT>::G;
   const int j = blockIdx.y;
   const int gi = j / G, jj = j % G;
@@ -699,7 +712,7 @@ template <int NT>
 static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int nc, float* Y,
                             double beta, const double* alpha, double* dots, int* nparts,
                             char* ws, int* err, unsigned flags, cudaStream_t st,
-                            const float* alpha32) {
+                            const float* alpha32, const int* gate) {
   const int sms = num_sms();
   DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages);
   const bool presplit = (flags & kApplyPresplit) != 0;
@@ -711,7 +724,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   if (!presplit) {
     const int64_t need4 = (p.ld / 4 + 255) / 256;
     dim3 g((unsigned)(need4 < 64 ? need4 : 64), (p.BN / 16) * TermGroup<NT>::G);
-    launch_k(split_block_kernel<NT>, dim3(g), dim3(256), 0, st, X, ld, op.D, p.ld, nc, Xs);
+    launch_k(split_block_kernel<NT>, dim3(g), dim3(256), 0, st, X, ld, op.D, p.ld, nc, Xs, gate);
     apply_tick(st);
   }
   CUtensorMap mPhi1, mXs, mPhi2, mWs;
@@ -742,6 +755,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.ldw = p.ldw;
   a1.split_stride = (int64_t)nc * p.ldw;
   a1.err = err;
+  a1.gate = gate;
   a1.units_m = (int)((op.N + kTileM - 1) / kTileM);
   a1.units = a1.units_m * p.S1;
   a1.acc_cols = p.acc_cols;
@@ -751,7 +765,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   {
     const int64_t need4 = (p.ldw / 4 + 127) / 128;
     dim3 g((unsigned)(need4 < 64 ? need4 : 64), (p.BN / 16) * TermGroup<NT>::G);
-    launch_k(reduce_split_kernel<NT>, dim3(g), dim3(128), 0, st, Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, Ws);
+    launch_k(reduce_split_kernel<NT>, dim3(g), dim3(128), 0, st, Wp, p.S1, a1.split_stride, op.N, p.ldw, nc, Ws, gate);
     apply_tick(st);
   }
 
@@ -775,6 +789,7 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.beta = beta;
   a2.dots = dots;
   a2.err = err;
+  a2.gate = gate;
   a2.units_m = (int)((op.D + kTileM - 1) / kTileM);
   a2.units = a2.units_m;
   a2.acc_cols = p.acc_cols;
@@ -789,7 +804,7 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
                      const int* done, const void* packed, const __nv_bfloat16* bsrc,
                      int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
                      size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
-                     double* dots, int* err, cudaStream_t st) {
+                     double* dots, int* err, cudaStream_t st, int grid) {
   CUtensorMap mA, mB;
   // mapA is unused in the batched mode (Phi comes from the packed copy);
   // any valid map will do
@@ -800,7 +815,7 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
   a.BN = BN;
   a.stages = stages;
   a.tmem_cols = tmem_cols;
-  a.acc_cols = tmem_cols / 2;
+  a.acc_cols = tmem_cols / 2;               // two accumulators
   a.units = nitems;
   a.units_m = 1;
   a.packed = (const __nv_bfloat16*)packed;
@@ -814,7 +829,7 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
   a.items = items;
   a.probs = probs;
   a.done = done;
-  dim3 g((unsigned)nitems, 1);
+  dim3 g((unsigned)(grid > 0 && grid < nitems ? grid : nitems), 1);
   cudaError_t e;
   switch ((mode << 2) | NT) {
     case 1: e = launch_tc<0, 1>(g, smem, mA, mB, a, st); break;
@@ -829,14 +844,15 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
 
 int dense_tc_apply(const DenseDesc& op, int NT, const float* X, int64_t ld, int nc, float* Y,
                    double beta, const double* alpha, double* dots, int* nparts, char* ws,
-                   int* err, unsigned flags, cudaStream_t st, const float* alpha32) {
+                   int* err, unsigned flags, cudaStream_t st, const float* alpha32,
+                   const int* gate) {
   switch (NT) {
     case 1: return dense_tc_apply_t<1>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
-                                           alpha32);
+                                           alpha32, gate);
     case 2: return dense_tc_apply_t<2>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
-                                           alpha32);
+                                           alpha32, gate);
     default: return dense_tc_apply_t<3>(op, X, ld, nc, Y, beta, alpha, dots, nparts, ws, err, flags, st,
-                                           alpha32);
+                                           alpha32, gate);
   }
 }
 

@@ -104,7 +104,9 @@ static size_t conv_w_bytes(const cofem_op* op, int ncols) {
   return align256((size_t)ncols * op->L * sizeof(float));
 }
 static const float* conv_filters64(const cofem_op* op, char* ws, int ncols, cudaStream_t st) {
-  if (op->T == 64) return op->filters;
+  // the kernels read the taps as float4: use the caller's filters in place
+  // only when they are 64 taps long and 16-byte aligned
+  if (op->T == 64 && ((uintptr_t)op->filters & 15) == 0) return op->filters;
   float* h64 = (float*)(ws + conv_w_bytes(op, ncols));
   conv_pad_filters(op->filters, op->C, op->T, h64, st);
   return h64;

@@ -8,12 +8,14 @@
 // alpha . x and accumulates the x_j^T (A x)_j partials of the CG step.
 //
 // Both kernels stage a tile of TILE = 256 * R outputs (R = 16) plus a T-1
-// halo of the input column in shared memory (wrapping circularly), hold 16
-// filter taps at a time in registers and let every thread produce R
-// consecutive outputs with a sliding register window: one shared load and R
-// FMAs per tap.  The shared tile is skewed by one word every 32 (index i ->
-// i + i/32) so that threads reading at stride R hit distinct banks.  The
-// grid runs the columns of a tile side by side so alpha stays in L2.
+// halo of the input column in shared memory (wrapping circularly; the
+// forward kernel copies the next channel's tile with cp.async while it
+// computes the current one), and every thread produces R consecutive outputs
+// from register windows of 31 staged values, one window per 16 filter taps
+// (taps read as float4): 31 shared loads per 256 FMAs.  The shared tile is
+// skewed by one word every 16 (index i -> i + i/16) so that threads reading
+// at stride R hit distinct banks.  The grid runs the columns of a tile side
+// by side so alpha stays in L2.
 #include "kernels.cuh"
 
 namespace cofem {
@@ -26,19 +28,46 @@ constexpr int kConvThreads = 256;
 constexpr int kConvR = 16;                           // outputs per thread
 constexpr int kConvTile = kConvThreads * kConvR;    // 4096 outputs per block
 constexpr int kConvMaxT = 64;
-constexpr int kTapChunk = 16;                        // filter taps held in registers
+constexpr int kTapChunk = 16;                        // filter taps per register window
+static_assert(kTapChunk == kConvR, "the window indexing assumes a chunk of R taps");
 
-__host__ __device__ constexpr int skew(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int skew(int i) { return i + (i >> 4); }
+constexpr int kStageWords = skew(kConvTile + kConvMaxT) + 8;   // one staged tile
+
+// w[i] = tile[skew(x0 + i)], i < 31, for x0 a multiple of 16: the skew
+// adds x0/16 to every index and one more to i >= 16, so one base pointer
+// and constant offsets replace the per-load arithmetic.  Thread t's window
+// starts at 16 t + const, i.e. at word 17 t + const: distinct banks.
+__device__ __forceinline__ void load_window(const float* tile, int x0,
+                                            float (&w)[2 * kTapChunk - 1]) {
+  const float* lo = tile + skew(x0);
+  const float* hi = lo + 1;
+#pragma unroll
+  for (int i = 0; i < kTapChunk; ++i) w[i] = lo[i];
+#pragma unroll
+  for (int i = kTapChunk; i < 2 * kTapChunk - 1; ++i) w[i] = hi[i];
+}
+
+// 4-byte asynchronous global -> shared copies (cp.async), grouped per channel.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // W[j][n] = sum_c sum_t h[c][t] Z[j][c*L + (n - t) mod L]
 // grid (ncols, L / TILE): the columns of one tile run side by side.
 template <int T>
-__global__ void __launch_bounds__(kConvThreads)
+__global__ void __launch_bounds__(kConvThreads, 2)
 conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ Z,
                     int64_t ldz, float* __restrict__ W, int64_t ldw) {
   pdl_wait();
   pdl_trigger();
-  __shared__ float zs[skew(kConvTile + kConvMaxT) + 8];
+  // two staged tiles: channel c + 1 is copied (cp.async) while channel c
+  // is computed
+  __shared__ float zs2[2][kStageWords];
   const int j = blockIdx.x;
   const int64_t n0 = (int64_t)blockIdx.y * kConvTile;
   const int tid = threadIdx.x;
@@ -48,35 +77,43 @@ conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
   const int span = kConvTile + T - 1;
   const bool wrap1 = L >= span;              // one add or subtract of L suffices
   const int base = (T - 1) + tid * kConvR;   // zs index of output n0 + tid*R at tap 0
-  for (int c = 0; c < C; ++c) {
+  auto stage = [&](int c, float* buf) {
     const float* zc = Z + (int64_t)j * ldz + (int64_t)c * L;
-    __syncthreads();
     for (int i = tid; i < span; i += kConvThreads) {
       int64_t n = n0 - (T - 1) + i;
       if (wrap1) n = n < 0 ? n + L : (n >= L ? n - L : n);
       else n = ((n % L) + L) % L;            // L shorter than the staged span
-      zs[skew(i)] = zc[n];
+      cp_async4(buf + skew(i), zc + n);
     }
-    __syncthreads();
-    // window w[r] = z at output r and the current tap
-    float w[kConvR];
-#pragma unroll
-    for (int r = 0; r < kConvR; ++r) w[r] = zs[skew(base + r)];
+    cp_async_commit();
+  };
+  stage(0, zs2[0]);
+  for (int c = 0; c < C; ++c) {
+    if (c + 1 < C) stage(c + 1, zs2[(c + 1) & 1]);
+    else cp_async_commit();                  // an empty group keeps the count uniform
+    cp_async_wait1();                        // this thread's copies of channel c landed
+    __syncthreads();                         // everyone's
+    const float* zs = zs2[c & 1];
+    // taps t0 .. t0+15: output r at tap t0 + q reads w[r - q + 15], a
+    // window of 31 staged values loaded once per chunk (static indices)
 #pragma unroll 1
     for (int t0 = 0; t0 < T; t0 += kTapChunk) {
+      float w[2 * kTapChunk - 1];
+      load_window(zs, base - t0 - (kTapChunk - 1), w);
       float hr[kTapChunk];
+      const float4* h4 = reinterpret_cast<const float4*>(h + c * T + t0);
 #pragma unroll
-      for (int q = 0; q < kTapChunk; ++q) hr[q] = __ldg(h + c * T + t0 + q);
+      for (int q4 = 0; q4 < kTapChunk / 4; ++q4) {
+        const float4 v = __ldg(h4 + q4);
+        hr[4 * q4] = v.x; hr[4 * q4 + 1] = v.y; hr[4 * q4 + 2] = v.z; hr[4 * q4 + 3] = v.w;
+      }
 #pragma unroll
       for (int q = 0; q < kTapChunk; ++q) {
 #pragma unroll
-        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r], acc[r]);
-#pragma unroll
-        for (int r = kConvR - 1; r > 0; --r) w[r] = w[r - 1];
-        const int t = t0 + q;
-        w[0] = t + 1 < T ? zs[skew(base - t - 1)] : 0.f;
+        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r - q + kTapChunk - 1], acc[r]);
       }
     }
+    __syncthreads();                         // this tile is read before it is refilled
   }
   float* wj = W + (int64_t)j * ldw + n0 + tid * kConvR;
   if (n0 + tid * kConvR + kConvR <= L) {
@@ -90,7 +127,7 @@ conv_forward_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
 // Y[j][c*L + m] = beta * sum_t h[c][t] W[j][(m + t) mod L] (+ alpha . X),
 // dots[tile][j] = sum over the block of X . Y.      grid (ncols, L / TILE)
 template <int T>
-__global__ void __launch_bounds__(kConvThreads)
+__global__ void __launch_bounds__(kConvThreads, 3)
 conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* __restrict__ W,
                     int64_t ldw, float* __restrict__ Y, int64_t ld, double beta,
                     const double* __restrict__ alpha, const float* __restrict__ alpha32,
@@ -115,49 +152,61 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
   AccF dot;
   const bool diag = alpha32 != nullptr || alpha != nullptr;
   for (int c = 0; c < C; ++c) {
-    float w[kConvR], acc[kConvR];
+    float acc[kConvR];
 #pragma unroll
-    for (int r = 0; r < kConvR; ++r) {
-      w[r] = ws[skew(base + r)];
-      acc[r] = 0.f;
+    for (int r = 0; r < kConvR; ++r) acc[r] = 0.f;
+    // the epilogue's x and alpha are loaded first: their latency overlaps
+    // the channel's FMAs
+    const int64_t d = (int64_t)c * L + m0 + base;
+    float xr[kConvR], ar[kConvR];
+    if (live && diag) {
+      const float4* x4 = reinterpret_cast<const float4*>(X + (int64_t)j * ld + d);
+#pragma unroll
+      for (int q = 0; q < kConvR / 4; ++q) {
+        const float4 v = x4[q];
+        xr[4 * q] = v.x; xr[4 * q + 1] = v.y; xr[4 * q + 2] = v.z; xr[4 * q + 3] = v.w;
+      }
+      if (alpha32) {
+        const float4* a4 = reinterpret_cast<const float4*>(alpha32 + d);
+#pragma unroll
+        for (int q = 0; q < kConvR / 4; ++q) {
+          const float4 v = a4[q];
+          ar[4 * q] = v.x; ar[4 * q + 1] = v.y; ar[4 * q + 2] = v.z; ar[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < kConvR; ++e) ar[e] = (float)alpha[d + e];
+      }
     }
+    // taps t0 .. t0+15: output r at tap t0 + q reads w[r + q], a window of
+    // 31 staged values loaded once per chunk (static indices)
 #pragma unroll 1
     for (int t0 = 0; t0 < T; t0 += kTapChunk) {
+      float w[2 * kTapChunk - 1];
+      load_window(ws, base + t0, w);
       float hr[kTapChunk];
+      const float4* h4 = reinterpret_cast<const float4*>(h + c * T + t0);
 #pragma unroll
-      for (int q = 0; q < kTapChunk; ++q) hr[q] = __ldg(h + c * T + t0 + q);
+      for (int q4 = 0; q4 < kTapChunk / 4; ++q4) {
+        const float4 v = __ldg(h4 + q4);
+        hr[4 * q4] = v.x; hr[4 * q4 + 1] = v.y; hr[4 * q4 + 2] = v.z; hr[4 * q4 + 3] = v.w;
+      }
 #pragma unroll
       for (int q = 0; q < kTapChunk; ++q) {
 #pragma unroll
-        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r], acc[r]);
-#pragma unroll
-        for (int r = 0; r < kConvR - 1; ++r) w[r] = w[r + 1];
-        const int t = t0 + q;
-        w[kConvR - 1] = t + 1 < T ? ws[skew(base + kConvR + t)] : 0.f;
+        for (int r = 0; r < kConvR; ++r) acc[r] = fmaf(hr[q], w[r + q], acc[r]);
       }
     }
     if (live) {
-      const int64_t d = (int64_t)c * L + m0 + base;
       float* yj = Y + (int64_t)j * ld + d;
-      const float* xj = X ? X + (int64_t)j * ld + d : nullptr;
 #pragma unroll
       for (int q = 0; q < kConvR / 4; ++q) {
         float out[4];
         if (diag) {
-          const float4 xv = reinterpret_cast<const float4*>(xj)[q];
-          const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
-          float a4[4];
-          if (alpha32) {
-            const float4 av = reinterpret_cast<const float4*>(alpha32 + d)[q];
-            a4[0] = av.x; a4[1] = av.y; a4[2] = av.z; a4[3] = av.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) a4[e] = (float)alpha[d + 4 * q + e];
-          }
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            out[e] = fmaf(a4[e], xa[e], (float)beta * acc[4 * q + e]);
-            dot.add_prod(xa[e], out[e]);
+            out[e] = fmaf(ar[4 * q + e], xr[4 * q + e], (float)beta * acc[4 * q + e]);
+            dot.add_prod(xr[4 * q + e], out[e]);
           }
         } else {
 #pragma unroll

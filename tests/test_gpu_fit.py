@@ -147,6 +147,27 @@ def test_replacement_tolerance_mode_fp32(cuda_lib):
     assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3
 
 
+def test_replacement_tensor_core_bf16(cuda_lib):
+    # BF16 dictionary on the tensor cores: the replacement runs outside an
+    # inner CG loop (gated kernels), every 10 iterations, against the oracle
+    # on the BF16-rounded dictionary; iteration counts above 10 make sure
+    # replacements happen
+    prob = _problem(sigma=0.1, seed=4)
+    t16, Phi64 = bf16_round(prob.Phi)
+    y32 = prob.y.astype(np.float32).astype(np.float64)
+    kw = dict(K=20, em_iters=30, cg_tol=1e-5, cg_max_iters=400, resid_replace_every=10, seed=4)
+    a, mu, s, st = _gpu_fit(Phi64, y32, prob.beta, torch.bfloat16, B.COFEM_F32, **kw)
+    ra, rmu, rs, rst = sbl.cofem_dense(Phi64, y32, prob.beta, 20, 30, 1e-5, 400,
+                                       resid_replace_every=10, seed=4)
+    assert max(st["cg_iters"]) > 10
+    assert rel_l2(mu, rmu) <= 1e-4
+    eq, _ = support_compare(a, ra)
+    assert eq
+    sup = (ra < 1e6) & (a < 1e6)
+    assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3
+    assert abs(sum(st["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)
+
+
 def test_resume_and_determinism(cuda_lib):
     prob = datagen.dense_problem(120, 480, 10, 0.01, seed=8)
     Phi_t = torch.from_numpy(prob.Phi.astype(np.float64)).cuda()

@@ -324,6 +324,15 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       if (MODE == 1 && live)
         a32 = args.alpha32 ? args.alpha32[u.aoff + row]
                            : (args.alpha ? (float)args.alpha[u.aoff + row] : 0.f);
+      // second product: x of the next column group is loaded while the
+      // current group is processed (one group ahead; the first group while
+      // the main loop runs)
+      float xnext[G];
+      if (MODE == 1) {
+#pragma unroll
+        for (int jj = 0; jj < G; ++jj)
+          xnext[jj] = (live && jj < args.nc) ? args.x[u.xoff + (int64_t)jj * u.ldo + row] : 0.f;
+      }
       const bool ok1 = tc::mbar_wait(&accfull[b], (uint32_t)((lu >> 1) & 1), abort,
                                      4 * kWaitLimitNs);
       if (!ok1) tc_fail(args.err, abort);
@@ -339,6 +348,15 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       tc::tc_fence_after();
       const uint32_t acc = tmem + (uint32_t)b * args.acc_cols;
       for (int gi = 0; gi < ngroups; ++gi) {
+        float xcur[G];
+        if (MODE == 1) {
+#pragma unroll
+          for (int jj = 0; jj < G; ++jj) {
+            xcur[jj] = xnext[jj];
+            const int jn = (gi + 1) * G + jj;
+            xnext[jj] = (live && jn < args.nc) ? args.x[u.xoff + (int64_t)jn * u.ldo + row] : 0.f;
+          }
+        }
         float v[COLS];
 #pragma unroll
         for (int c = 0; c < COLS / 16; ++c) {
@@ -372,7 +390,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             if (j < args.nc && live)
               args.wpart[u.woff + (int64_t)u.split * u.sstride + (int64_t)j * u.ldo + row] = sacc;
           } else if (j < args.nc && live) {
-            const float xv = args.x[u.xoff + (int64_t)j * u.ldo + row];
+            const float xv = xcur[jj];
             const float yv = fmaf(a32, xv, (float)u.beta * sacc);
             args.y[u.xoff + (int64_t)j * u.ldo + row] = yv;
             const float pp = xv * yv;

@@ -21,7 +21,8 @@
 
 namespace cofem {
 
-constexpr int kBChunk = 1024;           // vector elements per block (256 threads x 4)
+constexpr int kBSub = 4;                // 16-byte chunks per thread
+constexpr int kBChunk = 1024 * kBSub;   // vector elements per block (256 threads x 4 x kBSub)
 
 struct BVec {                           // one problem, as the vector kernels see it
   int64_t D, ld, xoff, aoff, boff1;
@@ -139,22 +140,25 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
   float* r = R + pv.xoff + (int64_t)j * pv.ld;
   float* p = P + pv.xoff + (int64_t)j * pv.ld;
   AccF acc;
-  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
-  if (d < pv.ld) {
-    float v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float w = 0.f;
-      if (d + i < pv.D) {
-        if (j == 0) { w = bv[pv.aoff + d + i]; acc.add_prod(w, w); }
-        else w = bprobe(key, d + i, j - 1);
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float w = 0.f;
+        if (d + i < pv.D) {
+          if (j == 0) { w = bv[pv.aoff + d + i]; acc.add_prod(w, w); }
+          else w = bprobe(key, d + i, j - 1);
+        }
+        v[i] = w;
+        x[d + i] = 0.f;
+        r[d + i] = w;
+        p[d + i] = w;
       }
-      v[i] = w;
-      x[d + i] = 0.f;
-      r[d + i] = w;
-      p[d + i] = w;
+      if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
     }
-    if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
   }
   if (j == 0) {
     const double s = block_sum(acc, sh);
@@ -194,9 +198,27 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   BState* st = sts + pi;
+  // this thread's chunks are loaded before a_j is known (their latency
+  // overlaps the reduction of the operator's partials)
+  const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
+  float4 xv[kBSub], rv[kBSub], pp[kBSub], qq[kBSub];
+#pragma unroll
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      xv[u] = *reinterpret_cast<const float4*>(X + o0 + d);
+      rv[u] = *reinterpret_cast<const float4*>(R + o0 + d);
+      pp[u] = *reinterpret_cast<const float4*>(P + o0 + d);
+      qq[u] = *reinterpret_cast<const float4*>(Q + o0 + d);
+    }
+  }
   if (threadIdx.x < 32) {
     double g = 0.0;
-    for (int i = threadIdx.x; i < pv.ndots; i += 32) g += dots[(int64_t)(pv.dots_base + i) * kMaxCols + j];
+    for (int i0 = threadIdx.x; i0 < pv.ndots; i0 += 64) {
+      const double g0 = dots[(int64_t)(pv.dots_base + i0) * kMaxCols + j];
+      const double g1 = i0 + 32 < pv.ndots ? dots[(int64_t)(pv.dots_base + i0 + 32) * kMaxCols + j] : 0.0;
+      g += g0 + g1;
+    }
     g = warp_sum(g);
     if (threadIdx.x == 0) {
       const double rho = st->rho[j];
@@ -211,23 +233,22 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
   __syncthreads();
   const float a = a_sh;
   AccF acc;
-  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
-  if (d < pv.ld) {
-    const int64_t o = pv.xoff + (int64_t)j * pv.ld + d;
-    float4 xv = *reinterpret_cast<float4*>(X + o);
-    float4 rv = *reinterpret_cast<float4*>(R + o);
-    const float4 pp = *reinterpret_cast<const float4*>(P + o);
-    const float4 qq = *reinterpret_cast<const float4*>(Q + o);
-    xv.x = fmaf(a, pp.x, xv.x); xv.y = fmaf(a, pp.y, xv.y);
-    xv.z = fmaf(a, pp.z, xv.z); xv.w = fmaf(a, pp.w, xv.w);
-    rv.x = fmaf(-a, qq.x, rv.x); rv.y = fmaf(-a, qq.y, rv.y);
-    rv.z = fmaf(-a, qq.z, rv.z); rv.w = fmaf(-a, qq.w, rv.w);
-    acc.add_prod(rv.x, rv.x);
-    acc.add_prod(rv.y, rv.y);
-    acc.add_prod(rv.z, rv.z);
-    acc.add_prod(rv.w, rv.w);
-    *reinterpret_cast<float4*>(X + o) = xv;
-    *reinterpret_cast<float4*>(R + o) = rv;
+#pragma unroll
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      float4 x4 = xv[u], r4 = rv[u];
+      x4.x = fmaf(a, pp[u].x, x4.x); x4.y = fmaf(a, pp[u].y, x4.y);
+      x4.z = fmaf(a, pp[u].z, x4.z); x4.w = fmaf(a, pp[u].w, x4.w);
+      r4.x = fmaf(-a, qq[u].x, r4.x); r4.y = fmaf(-a, qq[u].y, r4.y);
+      r4.z = fmaf(-a, qq[u].z, r4.z); r4.w = fmaf(-a, qq[u].w, r4.w);
+      acc.add_prod(r4.x, r4.x);
+      acc.add_prod(r4.y, r4.y);
+      acc.add_prod(r4.z, r4.z);
+      acc.add_prod(r4.w, r4.w);
+      *reinterpret_cast<float4*>(X + o0 + d) = x4;
+      *reinterpret_cast<float4*>(R + o0 + d) = r4;
+    }
   }
   const double s = block_sum(acc, sh);
   if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = s;
@@ -268,17 +289,28 @@ __global__ void bdirection_kernel(BConf cf, const BVec* pvs, const BState* sts, 
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   const float b = (float)sts[pi].b[j];
-  const int64_t d = (int64_t)c * kBChunk + threadIdx.x * 4;
-  if (d < pv.ld) {
-    const int64_t o = pv.xoff + (int64_t)j * pv.ld + d;
-    const float4 rv = *reinterpret_cast<const float4*>(R + o);
-    float4 pp = *reinterpret_cast<float4*>(P + o);
-    pp.x = fmaf(b, pp.x, rv.x); pp.y = fmaf(b, pp.y, rv.y);
-    pp.z = fmaf(b, pp.z, rv.z); pp.w = fmaf(b, pp.w, rv.w);
-    *reinterpret_cast<float4*>(P + o) = pp;
-    if (cf.split_nt > 0) {
-      const float v[4] = {pp.x, pp.y, pp.z, pp.w};
-      bsplit4(cf, pv, j, d, v);
+  const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
+  float4 rv[kBSub], pp[kBSub];
+#pragma unroll
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      rv[u] = *reinterpret_cast<const float4*>(R + o0 + d);
+      pp[u] = *reinterpret_cast<const float4*>(P + o0 + d);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      float4 p4 = pp[u];
+      p4.x = fmaf(b, p4.x, rv[u].x); p4.y = fmaf(b, p4.y, rv[u].y);
+      p4.z = fmaf(b, p4.z, rv[u].z); p4.w = fmaf(b, p4.w, rv[u].w);
+      *reinterpret_cast<float4*>(P + o0 + d) = p4;
+      if (cf.split_nt > 0) {
+        const float v[4] = {p4.x, p4.y, p4.z, p4.w};
+        bsplit4(cf, pv, j, d, v);
+      }
     }
   }
 }

@@ -330,16 +330,31 @@ def run_conv(args):
     adj = float(np.mean([m[1] for m in ms])) / 1e3
     adj_bytes = L * nc * 4 + 2 * D * nc * 4 + 8 * D
     flops = 2 * 2 * c["T"] * D * nc                    # forward + adjoint MACs x 2
-    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
+    adj_flops = flops / 2
+    # FP32 CUDA-core roof: SMs x 128 FP32 lanes x 2 flop x maximum SM clock
+    props = torch.cuda.get_device_properties(0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "conv_adjoint_l1m_c8_t64.md")
+    if os.path.exists(prof):
+        import hashlib
+        src = os.path.join(ROOT, "paper_2202_12808_gb300", "csrc", "conv.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        meta = dict(l.split(":", 1) for l in open(prof)
+                    if l.startswith(("source_sha1:", "traffic_bytes_per_launch:")))
+        if meta.get("source_sha1", "").strip() == sha:
+            traffic = int(meta["traffic_bytes_per_launch"].strip())
     _common(args, "EM iters/s (circular conv dictionary L=2^20, 8x64 taps, D=8.4M, K=16)",
             "EM iters/s", args.steps / sec, sec, "f32",
             {"workload": "conv-l1m-c8-t64", "L": L, "C": c["C"], "T": c["T"], "D": D,
              "K": c["K"], "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps)},
             {"cg_iters_per_em": cg,
-             "roofline": {"bound": "hbm", "achieved": adj_bytes / adj / 1e9, "peak": peak,
-                          "unit": "GB/s", "frac": adj_bytes / adj / 1e9 / peak, "traffic": None,
+             "roofline": {"bound": "alu", "achieved": adj_flops / adj / 1e12, "peak": fp32_peak,
+                          "unit": "TFLOP/s", "frac": adj_flops / adj / 1e12 / fp32_peak,
+                          "traffic": traffic, "peak_source": "derived (SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
                           "kernel": "conv_adjoint_kernel (Phi^T W + alpha.X, 17 cols)",
-                          "launch_us": adj * 1e6, "algorithmic_bytes": adj_bytes},
+                          "launch_us": adj * 1e6, "algorithmic_flops": adj_flops,
+                          "algorithmic_bytes": adj_bytes},
              "conv_apply": {"forward_us": fwd * 1e6, "adjoint_us": adj * 1e6,
                             "fp32_tflops": flops / (fwd + adj) / 1e12},
              "clocks": clk.summary()})

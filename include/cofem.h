@@ -160,6 +160,15 @@ typedef struct {
   int32_t resid_replace_every; /* R > 0: every R CG iterations recompute the
                                   true residual r = B - A x; 0 = never */
   int32_t vec_dtype;           /* COFEM_F64 or COFEM_F32 */
+  int32_t stop_rule;           /* 0: joint test ||R||_F / ||B||_F < cg_tol on
+                                  the recursive residual (Sec. 3.2, the
+                                  paper's); 1: per column -- column j is
+                                  frozen (a_j = b_j = 0 from then on) once
+                                  ||r_j|| / ||b_j|| < cg_tol, the solve ends
+                                  when every column is frozen.  Ignored with
+                                  fixed_cg_iters; 1 with mlp returns
+                                  COFEM_ERR_UNSUPPORTED.  Other values:
+                                  COFEM_ERR_INVALID_ARG. */
   double cg_tol;               /* eps: stop when ||R||_F / ||B||_F < eps */
   double alpha_init;           /* initial alpha (Alg. 1: 1) when
                                   t_offset == 0; ignored otherwise */

@@ -152,12 +152,15 @@ class CGResult:
     converged: bool
 
 
-def cg_solve(A, B, tol, max_iters, fixed_iters=0, resid_replace_every=0):
+def cg_solve(A, B, tol, max_iters, fixed_iters=0, resid_replace_every=0, stop_rule=0):
     """Column-wise CG, stopped on the joint Frobenius residual ratio.
 
     A: function X -> A X.  B: D x m.  X0 = 0.
     fixed_iters > 0 runs exactly that many iterations and ignores tol.
     resid_replace_every = R > 0 recomputes r = B - A x every R iterations.
+    stop_rule = 1 (an option; the paper's rule is 0): column j is frozen once
+    ||r_j|| / ||b_j|| < tol (its a_j and b_j are 0 from then on) and the solve
+    ends when every column is frozen; relres stays the joint ratio.
     """
     B = np.asarray(B, dtype=np.float64)
     X = np.zeros_like(B)
@@ -165,11 +168,18 @@ def cg_solve(A, B, tol, max_iters, fixed_iters=0, resid_replace_every=0):
     P = R.copy()
     rho = np.sum(R * R, axis=0)
     normB = np.sqrt(np.sum(B * B))
+    normBj = np.sqrt(rho)
     limit = fixed_iters if fixed_iters > 0 else max_iters
     if normB == 0.0:
         return CGResult(X, 0, 0.0, True)
     relres = np.sqrt(np.sum(rho)) / normB
-    if fixed_iters == 0 and relres < tol:
+    per_column = stop_rule == 1 and fixed_iters == 0
+    if per_column:
+        active = (normBj > 0) & ~(np.sqrt(rho) < tol * normBj)
+        rho = np.where(active, rho, 0.0)     # a frozen column takes a_j = b_j = 0
+        if not np.any(active):
+            return CGResult(X, 0, relres, True)
+    elif fixed_iters == 0 and relres < tol:
         return CGResult(X, 0, relres, True)
     it = 0
     while it < limit:
@@ -184,12 +194,18 @@ def cg_solve(A, B, tol, max_iters, fixed_iters=0, resid_replace_every=0):
             R = R - a * Q
         rho_new = np.sum(R * R, axis=0)
         relres = np.sqrt(np.sum(rho_new)) / normB
-        if fixed_iters == 0 and relres < tol:
+        if per_column:
+            active = active & ~(np.sqrt(rho_new) < tol * normBj)
+            rho_new = np.where(active, rho_new, 0.0)
+            if not np.any(active):
+                return CGResult(X, it, relres, True)
+        elif fixed_iters == 0 and relres < tol:
             return CGResult(X, it, relres, True)
         b = np.where(rho > 0, rho_new / np.where(rho > 0, rho, 1.0), 0.0)
         P = R + b * P
         rho = rho_new
-    return CGResult(X, it, relres, fixed_iters > 0 or relres < tol)
+    converged = fixed_iters > 0 or (not np.any(active) if per_column else relres < tol)
+    return CGResult(X, it, relres, converged)
 
 
 def pcg_solve(A, B, X0, minv, tol, max_iters, resid_replace_every=0):
@@ -265,13 +281,14 @@ class FitStats:
 def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
           seed=0, alpha_init=1.0, t_offset=0, fixed_cg_iters=0,
           resid_replace_every=0, den_floor=DEN_FLOOR, probes=None,
-          support_threshold=1e6):
+          support_threshold=1e6, stop_rule=0):
     """Algorithm 1.  Returns (alpha, mu, s, FitStats).
 
     alpha_init: scalar (Alg. 1 initialises alpha = 1) or a length-D vector
     (resume from a previous alpha).  t runs t_offset+1 .. t_offset+em_iters.
     probes: optional function t -> D x K probe block; default is the
-    counter-based Rademacher generator of probe_hash.
+    counter-based Rademacher generator of probe_hash.  stop_rule: see
+    cg_solve.
     """
     y = np.asarray(y, dtype=np.float64)
     alpha = np.broadcast_to(np.asarray(alpha_init, dtype=np.float64), (D,)).copy()
@@ -285,7 +302,7 @@ def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
         P = probes(t) if probes is not None else probe_matrix(seed, t, K, D)
         B = np.concatenate([b[:, None], P], axis=1)
         res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters,
-                       resid_replace_every)
+                       resid_replace_every, stop_rule)
         mu = res.X[:, 0]
         s = diag_estimate(P, res.X[:, 1:])
         # M-step.

@@ -288,8 +288,10 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (p->vec_dtype != COFEM_F64 && p->vec_dtype != COFEM_F32) return COFEM_ERR_INVALID_ARG;
   if (!(p->cg_tol >= 0.0) || !(p->den_floor > 0.0)) return COFEM_ERR_INVALID_ARG;
   if (p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
+  if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
   if (!op_supports(op, p->vec_dtype)) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
+  if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 
@@ -357,6 +359,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cf.tol = p->cg_tol;
   cf.max_iters = p->cg_max_iters;
   cf.fixed_iters = p->fixed_cg_iters;
+  cf.stop_rule = p->fixed_cg_iters > 0 ? 0 : p->stop_rule;
   cf.replace_every = p->resid_replace_every;
   cf.beta = beta;
   cf.den_floor = p->den_floor;

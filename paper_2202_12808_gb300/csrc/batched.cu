@@ -36,6 +36,7 @@ struct BState {                         // one problem's CG state (device)
   int clamps, support;
   unsigned int counter[4];
   double normB2, relres;
+  double b0norm2;                       // ||b||^2 of column 0 (probe columns: D)
   double rho[kMaxCols], rho_new[kMaxCols], b[kMaxCols];
 };
 
@@ -53,6 +54,7 @@ struct BConf {
   int em_iters;
   unsigned long long while_handle;
   int nch_max;                           // partial-sum slots per problem
+  int stop_rule;                         // 1: per-column stop (frozen columns have rho_j = 0)
   int split_nt;
   int64_t split_ld;                      // pitch of the BF16 split buffer
   __nv_bfloat16* split_buf;
@@ -98,8 +100,9 @@ __device__ __forceinline__ bool barrive_last(unsigned int* counter, unsigned exp
 }
 
 // All threads of the problem's last block (blockDim >= nc): b_j by thread j,
-// the residual total by the first warp (fixed order), the stop test.
-__device__ void bfinalize(const BConf& cf, BState* st) {
+// the residual total by the first warp (fixed order), the stop test (joint,
+// or per column as in the single-problem solver).
+__device__ void bfinalize(const BConf& cf, BState* st, int64_t D) {
   __shared__ double tot_sh;
   __syncthreads();
   const int j = threadIdx.x;
@@ -109,17 +112,27 @@ __device__ void bfinalize(const BConf& cf, BState* st) {
     t = warp_sum(t);
     if (j == 0) tot_sh = t;
   }
+  int live = 0;
   if (j < cf.nc) {
     const double r0 = st->rho[j], r1 = st->rho_new[j];
-    st->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
-    st->rho[j] = r1;
+    if (cf.stop_rule == 1) {
+      const double bn2 = j == 0 ? st->b0norm2 : (double)D;
+      live = r0 > 0.0 && !(sqrt(r1) < cf.tol * sqrt(bn2));
+      st->b[j] = live ? r1 / r0 : 0.0;
+      st->rho[j] = live ? r1 : 0.0;
+    } else {
+      st->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+      st->rho[j] = r1;
+    }
   }
-  __syncthreads();
+  const int nlive = __syncthreads_count(live);
   if (j == 0) {
     const double relres = sqrt(tot_sh) / sqrt(st->normB2);
     st->relres = relres;
-    int done = cf.fixed_iters > 0 ? st->iter >= cf.fixed_iters
-                                  : (relres < cf.tol || st->iter >= cf.max_iters);
+    int done;
+    if (cf.fixed_iters > 0) done = st->iter >= cf.fixed_iters;
+    else if (cf.stop_rule == 1) done = nlive == 0 || st->iter >= cf.max_iters;
+    else done = relres < cf.tol || st->iter >= cf.max_iters;
     if (!isfinite(relres)) { st->error = COFEM_ERR_NONFINITE; done = 1; }
     st->done = done;
   }
@@ -171,6 +184,8 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
       st->rho[0] = b2;
       for (int jj = 1; jj < cf.nc; ++jj) st->rho[jj] = (double)pv.D;
       st->normB2 = b2 + (double)cf.K * (double)pv.D;
+      st->b0norm2 = b2;
+      if (cf.stop_rule == 1 && !(b2 > 0.0)) st->rho[0] = 0.0;   // b = 0: x = 0, frozen
       st->relres = 1.0;
       st->iter = 0;
       st->clamps = 0;
@@ -185,21 +200,50 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
   }
 }
 
-// a_j = rho_j / gamma_j (gamma from the operator's partial dots of this
-// problem), x += a p, r -= a q, rho_new partials; last block: stop test.
+// a_j = rho_j / gamma_j of every unconverged problem and column, gamma_j =
+// p_j^T A p_j summed from the second product's partial dots; one warp per
+// (problem, column): blocks of kStepWarps warps, grid (problems, column
+// groups).  A breakdown (gamma <= 0 with rho > 0) sets the problem's error.
+constexpr int kStepWarps = 8;
+__global__ void bstep_kernel(BConf cf, const BVec* pvs, BState* sts, const int* done,
+                             const double* dots, float* astep) {
+  pdl_wait();
+  pdl_trigger();
+  const int pi = blockIdx.x, lane = threadIdx.x & 31;
+  const int j = blockIdx.y * kStepWarps + (threadIdx.x >> 5);
+  if (j >= cf.nc || done[pi]) return;
+  const BVec pv = pvs[pi];
+  BState* st = sts + pi;
+  double g = 0.0;
+  for (int i0 = lane; i0 < pv.ndots; i0 += 64) {
+    const double g0 = dots[(int64_t)(pv.dots_base + i0) * kMaxCols + j];
+    const double g1 = i0 + 32 < pv.ndots ? dots[(int64_t)(pv.dots_base + i0 + 32) * kMaxCols + j] : 0.0;
+    g += g0 + g1;
+  }
+  g = warp_sum(g);
+  if (lane == 0) {
+    const double rho = st->rho[j];
+    double a = 0.0;
+    if (rho > 0.0) {
+      if (!(g > 0.0)) st->error = isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE;
+      else a = rho / g;
+    }
+    astep[(int64_t)pi * kMaxCols + j] = (float)a;
+  }
+}
+
+// x += a p, r -= a q (a from bstep_kernel), rho_new partials; last block:
+// stop test.
 __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, float* X,
-                               float* R, const float* P, const float* Q, const double* dots,
+                               float* R, const float* P, const float* Q, const float* astep,
                                double* part) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[32];
-  __shared__ float a_sh;
   const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   BState* st = sts + pi;
-  // this thread's chunks are loaded before a_j is known (their latency
-  // overlaps the reduction of the operator's partials)
   const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
   float4 xv[kBSub], rv[kBSub], pp[kBSub], qq[kBSub];
 #pragma unroll
@@ -212,26 +256,7 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
       qq[u] = *reinterpret_cast<const float4*>(Q + o0 + d);
     }
   }
-  if (threadIdx.x < 32) {
-    double g = 0.0;
-    for (int i0 = threadIdx.x; i0 < pv.ndots; i0 += 64) {
-      const double g0 = dots[(int64_t)(pv.dots_base + i0) * kMaxCols + j];
-      const double g1 = i0 + 32 < pv.ndots ? dots[(int64_t)(pv.dots_base + i0 + 32) * kMaxCols + j] : 0.0;
-      g += g0 + g1;
-    }
-    g = warp_sum(g);
-    if (threadIdx.x == 0) {
-      const double rho = st->rho[j];
-      double a = 0.0;
-      if (rho > 0.0) {
-        if (!(g > 0.0)) st->error = isfinite(g) ? COFEM_ERR_BREAKDOWN : COFEM_ERR_NONFINITE;
-        else a = rho / g;
-      }
-      a_sh = (float)a;
-    }
-  }
-  __syncthreads();
-  const float a = a_sh;
+  const float a = astep[(int64_t)pi * kMaxCols + j];
   AccF acc;
 #pragma unroll
   for (int u = 0; u < kBSub; ++u) {
@@ -262,7 +287,7 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
       st->iter += 1;
       st->counter[1] = 0;
     }
-    bfinalize(cf, st);
+    bfinalize(cf, st, pv.D);
     if (threadIdx.x == 0) done[pi] = st->done;
   }
 }
@@ -324,7 +349,7 @@ __global__ void breduce_kernel(const TcProb* probs, const int* done, int nc, con
   constexpr int G = 16 / NT;
   const int pi = blockIdx.z, j = blockIdx.y;
   const TcProb pr = probs[pi];
-  if (done[pi]) return;
+  if (done[pi] || pr.S1 == 1) return;   // one K range: the product wrote the terms
   const int gi = j / G, jj = j % G;
   const int64_t n = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (n >= pr.ldw) return;
@@ -443,13 +468,20 @@ struct BLayout {
   std::vector<TcProb> tcp;
   std::vector<TcItem> items1, items2;
   int nch_max = 0, ndots = 0, BN = 0, NT = 3, stages = 3, grid = 0;
+  bool any_split = false;                 // some problem's first product is split over K
   uint32_t tmem_cols = 0;                 // two accumulators
   size_t smem = 0;
   int64_t ldx_total = 0, ldw_total = 0, dtot = 0, ldw_max = 0;
   // workspace offsets
-  size_t o_packed, o_X, o_R, o_P, o_Q, o_b, o_xs, o_ws, o_wpart, o_dots, o_part, o_state, o_done,
+  size_t o_packed, o_X, o_R, o_P, o_Q, o_b, o_xs, o_ws, o_wpart, o_dots, o_part, o_astep, o_state, o_done,
       o_ctl, o_vec, o_tcp, o_it1, o_it2, o_st_it, o_st_rr, o_st_cl, o_st_sp, o_simt, total;
 };
+
+// K blocks (64 columns of Phi) of one first-product work item at most: up to
+// D = 8192 a problem's first product is one K range per tile, whose
+// epilogue writes the BF16 terms of W itself (no split-K reduction); the
+// items, sorted longest first, still balance over the persistent CTAs.
+constexpr int kB1MaxKb = 128;
 
 static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* p, BLayout* L) {
   const int nc = p->K + 1;
@@ -480,7 +512,7 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
     t.N = N; t.D = D; t.nkd = packed_tiles_k(D); t.poff = poff; t.xoff = xoff; t.ld = ld;
     t.aoff = aoff; t.boff1 = b1; t.boff2 = b2; t.wpoff = wpoff; t.ldw = ldw;
     const int nk1 = (int)((D + 63) / 64);
-    t.S1 = (nk1 + 31) / 32;                    // K ranges of at most 32 blocks (512 KB of Phi)
+    t.S1 = (nk1 + kB1MaxKb - 1) / kB1MaxKb;
     const int kbps = (nk1 + t.S1 - 1) / t.S1;
     t.dots_base = dots;
     t.beta = pr[i].beta;
@@ -495,7 +527,10 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
     aoff += D;
     b1 += ld;
     b2 += ldw;
-    wpoff += (int64_t)t.S1 * nc * ldw;
+    if (t.S1 > 1) {
+      wpoff += (int64_t)t.S1 * nc * ldw;
+      L->any_split = true;
+    }
     poff += (int64_t)(packed_bytes(N, D) / 2);
     dots += v.ndots;
     L->nch_max = std::max(L->nch_max, v.nch);
@@ -525,6 +560,7 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
   L->o_wpart = take((size_t)wpoff * 4);
   L->o_dots = take((size_t)dots * kMaxCols * 8);
   L->o_part = take((size_t)n * L->nch_max * kMaxCols * 8);
+  L->o_astep = take((size_t)n * kMaxCols * 4);
   L->o_state = take((size_t)n * sizeof(BState));
   L->o_done = take((size_t)n * 4);
   L->o_ctl = take(sizeof(BCtl));
@@ -548,6 +584,7 @@ static cofem_status bcheck(int n, const cofem_problem* pr, const cofem_params* p
   if (p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   if (p->resid_replace_every != 0) return COFEM_ERR_UNSUPPORTED;
   if (!(p->den_floor > 0.0) || p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
+  if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
   return COFEM_OK;
 }
 
@@ -602,6 +639,7 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
   cf.tol = p->cg_tol;
   cf.max_iters = p->cg_max_iters;
   cf.fixed_iters = p->fixed_cg_iters;
+  cf.stop_rule = p->fixed_cg_iters > 0 ? 0 : p->stop_rule;
   cf.den_floor = p->den_floor;
   cf.support_threshold = p->support_threshold;
   cf.em_iters = p->em_iters;
@@ -641,25 +679,30 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
     int* err = &ctl->error;
     if (dense_tc_batched(0, L.NT, (int)L.items1.size(), it1, tcp, done, ws + L.o_packed, xs,
                          L.ldx_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, wpart, nullptr,
-                         nullptr, nullptr, nullptr, err, bs, L.grid) != 0)
+                         nullptr, nullptr, nullptr, err, bs, L.grid, wsb, L.ldw_total) != 0)
       return COFEM_ERR_CUDA;
     const int G = 16 / L.NT;
     const dim3 rg((unsigned)((L.ldw_max / 4 + 127) / 128), (L.BN / 16) * G, n);
-    if (L.NT == 3)
-      BCK(launch_k(breduce_kernel<3>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
-                   (const float*)wpart, wsb, L.ldw_total));
-    else if (L.NT == 2)
-      BCK(launch_k(breduce_kernel<2>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
-                   (const float*)wpart, wsb, L.ldw_total));
-    else
-      BCK(launch_k(breduce_kernel<1>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
-                   (const float*)wpart, wsb, L.ldw_total));
+    if (L.any_split) {
+      if (L.NT == 3)
+        BCK(launch_k(breduce_kernel<3>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                     (const float*)wpart, wsb, L.ldw_total));
+      else if (L.NT == 2)
+        BCK(launch_k(breduce_kernel<2>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                     (const float*)wpart, wsb, L.ldw_total));
+      else
+        BCK(launch_k(breduce_kernel<1>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
+                     (const float*)wpart, wsb, L.ldw_total));
+    }
     if (dense_tc_batched(1, L.NT, (int)L.items2.size(), it2, tcp, done, ws + L.o_packed, wsb,
                          L.ldw_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, nullptr, P, Q,
                          alpha, dots, err, bs, L.grid) != 0)
       return COFEM_ERR_CUDA;
+    float* astep = (float*)(ws + L.o_astep);
+    BCK(launch_k(bstep_kernel, dim3(n, (nc + kStepWarps - 1) / kStepWarps), dim3(32 * kStepWarps),
+                 0, bs, cf, pvs, sts, (const int*)done, (const double*)dots, astep));
     BCK(launch_k(bupdate_kernel, vg, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
-                 (const float*)Q, (const double*)dots, part));
+                 (const float*)Q, (const float*)astep, part));
     BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, bs, cf, (const int*)done));
     BCK(launch_k(bdirection_kernel, vg, dim3(256), 0, bs, cf, pvs, (const BState*)sts,
                  (const int*)done, (const float*)R, P));
@@ -722,7 +765,8 @@ static cofem_status btune(int nc, BLayout* L, char* ws, const double* alpha, cud
                                  ws + L->o_packed, (const __nv_bfloat16*)(ws + L->o_xs),
                                  L->ldx_total, L->BN, nc, q.stages, q.tmem_cols, q.smem,
                                  (float*)(ws + L->o_wpart), nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, st, q.grid);
+                                 nullptr, st, q.grid, (__nv_bfloat16*)(ws + L->o_ws),
+                                 L->ldw_total);
         if (r == 0)
           r = dense_tc_batched(1, L->NT, (int)L->items2.size(), it2, tcp, done,
                                ws + L->o_packed, (const __nv_bfloat16*)(ws + L->o_ws),

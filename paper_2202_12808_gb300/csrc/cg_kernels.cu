@@ -104,18 +104,29 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
     t = warp_sum(t);
     if (j == 0) tot_sh = t;
   }
+  int live = 0;
   if (j < cf.ncols) {
     const double r0 = sc->rho[j], r1 = sc->rho_new[j];
-    sc->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
-    sc->rho[j] = r1;
+    if (cf.stop_rule == 1) {
+      // per-column rule: column j is frozen once ||r_j|| < tol ||b_j||; a
+      // frozen column keeps rho_j = 0, so a_j = b_j = 0 from then on
+      const double bn2 = j == 0 ? ctl->b0norm2 : (double)cf.D;
+      live = r0 > 0.0 && !(sqrt(r1) < cf.tol * sqrt(bn2));
+      sc->b[j] = live ? r1 / r0 : 0.0;
+      sc->rho[j] = live ? r1 : 0.0;
+    } else {
+      sc->b[j] = r0 > 0.0 ? r1 / r0 : 0.0;
+      sc->rho[j] = r1;
+    }
   }
-  __syncthreads();
+  const int nlive = __syncthreads_count(live);
   if (j == 0) {
     const double relres = sqrt(tot_sh) / sqrt(ctl->normB2);
     ctl->relres = relres;
     const int it = ctl->iter;
     int done;
     if (cf.fixed_iters > 0) done = it >= cf.fixed_iters;
+    else if (cf.stop_rule == 1) done = nlive == 0 || it >= cf.max_iters;
     else done = (relres < cf.tol) || (it >= cf.max_iters);
     if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
     ctl->done = done;
@@ -189,6 +200,11 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
       for (int jj = 1; jj < cf.ncols; ++jj) sc->rho[jj] = (double)cf.D;
       const double n2 = b2 + (double)cf.K * (double)cf.D;
       ctl->normB2 = n2;
+      ctl->b0norm2 = b2;
+      // per-column rule: every column starts at ||r_j|| / ||b_j|| = 1, so
+      // the joint start test below covers it; a zero column 0 (b = 0) is
+      // solved by x = 0 and frozen at once
+      if (cf.stop_rule == 1 && !(b2 > 0.0)) sc->rho[0] = 0.0;
       ctl->relres = n2 > 0.0 ? 1.0 : 0.0;
       if (cf.fallback_init) {
         ctl->extra_iters = ctl->iter;

@@ -29,6 +29,7 @@ struct CgCtl {
   int fallbacks;       // learned path: fallbacks to plain CG so far
   int run;             // the direction update may run (b_j of this iteration are set)
   double normB2;       // ||B||_F^2
+  double b0norm2;      // ||b||^2 of column 0 (a probe column has ||p||^2 = D)
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
 };
@@ -69,6 +70,7 @@ struct CgConf {
   unsigned long long fallback_handle;  // IF node: preconditioned solve did not converge
   int fallback_init;                 // this init restarts plain CG after a fallback
   float* alpha32;                    // FP32 copy of alpha kept by the M-step, or null
+  int stop_rule;                     // 1: per-column stop (frozen columns have rho_j = 0)
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

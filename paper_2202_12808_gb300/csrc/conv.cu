@@ -56,6 +56,7 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // W[j][n] = sum_c sum_t h[c][t] Z[j][c*L + (n - t) mod L]
 // grid (ncols, L / TILE): the columns of one tile run side by side.
@@ -141,11 +142,15 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
   const int tid = threadIdx.x;
   const int span = kConvTile + T - 1;
   const float* wj = W + (int64_t)j * ldw;
+  // the column's tile is staged by cp.async (no load -> store round trip
+  // through registers per element)
   for (int i = tid; i < span; i += kConvThreads) {
     int64_t n = m0 + i;
     n = L >= span ? (n >= L ? n - L : n) : n % L;
-    ws[skew(i)] = wj[n];
+    cp_async4(ws + skew(i), wj + n);
   }
+  cp_async_commit();
+  cp_async_wait0();
   __syncthreads();
   const int base = tid * kConvR;
   const bool live = m0 + base + kConvR <= L;

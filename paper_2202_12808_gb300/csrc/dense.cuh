@@ -99,14 +99,18 @@ constexpr unsigned kApplyPresplit = 1u;
 // Batched products over a work-item table (see TcItem / TcProb); `grid`
 // persistent CTAs (0: one per item) take the items in strides of the grid;
 // tmem_cols holds two accumulators.  mode 0:
-// split-K partials of W = Phi X; mode 1: Y = beta Phi^T W + alpha . X with
-// partial dots.  xs / ws: BF16 term buffers (BN rows, pitch ldx_total /
-// ldw_total).  Returns 0, 1 (tensor map) or 2 (launch).
+// split-K partials of W = Phi X (if wterms is set, problems with S1 == 1
+// write W's BF16 terms there instead: row 16 (j / G) + NT (j % G) + t,
+// G = 16 / NT, column boff2 + n, pitch ldw_terms); mode 1:
+// Y = beta Phi^T W + alpha . X with partial dots.  xs / ws: BF16 term
+// buffers (BN rows, pitch ldx_total / ldw_total).  Returns 0, 1 (tensor map)
+// or 2 (launch).
 int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const TcProb* probs,
                      const int* done, const void* packed, const __nv_bfloat16* bsrc,
                      int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
                      size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
-                     double* dots, int* err, cudaStream_t st, int grid = 0);
+                     double* dots, int* err, cudaStream_t st, int grid = 0,
+                     __nv_bfloat16* wterms = nullptr, int64_t ldw_terms = 0);
 
 // alpha32: optional FP32 copy of alpha ((float)alpha[d]); saves the per-row
 // conversion.  gate: if set, every kernel of the application returns at

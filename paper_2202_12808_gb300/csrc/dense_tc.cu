@@ -64,6 +64,11 @@ struct TcArgs {
   float* wpart;
   int64_t ldw;
   int64_t split_stride;
+  // batched GEMM1: problems with one K range write the BF16 terms of W
+  // directly (rows as the second product reads them, pitch ldw_terms)
+  // instead of FP32 partials; null: always partials
+  __nv_bfloat16* wterms;
+  int64_t ldw_terms;
 
   // GEMM2
   float* y;
@@ -99,9 +104,10 @@ __device__ __forceinline__ void split_terms(float x, __nv_bfloat16 (&o)[NT]) {
 // One work unit: a 128-row output tile and a K range of one product (of one
 // problem, in the batched mode).
 struct TcUnit {
-  int64_t m0, M, nkd, ldo, xoff, aoff, woff, sstride, bx0;
+  int64_t m0, M, nkd, ldo, xoff, aoff, woff, sstride, bx0, wo;
   double beta;
   int kb0, kb1, split, dslot;
+  bool direct;             // GEMM1 writes BF16 terms of W at column offset wo
   const __nv_bfloat16* pk;
 };
 
@@ -111,7 +117,8 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs& args, int w) {
   u.M = args.M;
   u.nkd = args.nkd;
   u.ldo = MODE == 0 ? args.ldw : args.ld;
-  u.xoff = u.aoff = u.woff = u.bx0 = 0;
+  u.xoff = u.aoff = u.woff = u.bx0 = u.wo = 0;
+  u.direct = false;
   u.sstride = args.split_stride;
   u.beta = args.beta;
   u.pk = args.packed;
@@ -133,6 +140,8 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs& args, int w) {
     u.bx0 = MODE == 0 ? pr.boff1 : pr.boff2;
     u.dslot = pr.dots_base + it.tile;
     u.beta = pr.beta;
+    u.direct = MODE == 0 && args.wterms && pr.S1 == 1;
+    u.wo = pr.boff2;
   } else {
     const int tile = w % args.units_m, split = w / args.units_m;
     u.m0 = (int64_t)tile * kTileM;
@@ -387,8 +396,17 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           dc[jj] = 0.f;
           db[jj] = 0.0;
           if (MODE == 0) {
-            if (j < args.nc && live)
-              args.wpart[u.woff + (int64_t)u.split * u.sstride + (int64_t)j * u.ldo + row] = sacc;
+            if (j < args.nc && live) {
+              if (u.direct) {
+                __nv_bfloat16 o[NT];
+                split_terms<NT>(sacc, o);
+#pragma unroll
+                for (int t = 0; t < NT; ++t)
+                  args.wterms[(int64_t)(gi * 16 + jj * NT + t) * args.ldw_terms + u.wo + row] = o[t];
+              } else {
+                args.wpart[u.woff + (int64_t)u.split * u.sstride + (int64_t)j * u.ldo + row] = sacc;
+              }
+            }
           } else if (j < args.nc && live) {
             const float xv = xcur[jj];
             const float yv = fmaf(a32, xv, (float)u.beta * sacc);
@@ -822,7 +840,8 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
                      const int* done, const void* packed, const __nv_bfloat16* bsrc,
                      int64_t b_cols, int BN, int nc, int stages, uint32_t tmem_cols,
                      size_t smem, float* wpart, const float* X, float* Y, const double* alpha,
-                     double* dots, int* err, cudaStream_t st, int grid) {
+                     double* dots, int* err, cudaStream_t st, int grid,
+                     __nv_bfloat16* wterms, int64_t ldw_terms) {
   CUtensorMap mA, mB;
   // mapA is unused in the batched mode (Phi comes from the packed copy);
   // any valid map will do
@@ -838,6 +857,8 @@ int dense_tc_batched(int mode, int NT, int nitems, const TcItem* items, const Tc
   a.units_m = 1;
   a.packed = (const __nv_bfloat16*)packed;
   a.wpart = wpart;
+  a.wterms = mode == 0 ? wterms : nullptr;
+  a.ldw_terms = ldw_terms;
   a.x = X;
   a.y = Y;
   a.alpha = alpha;

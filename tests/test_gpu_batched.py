@@ -23,10 +23,10 @@ pytestmark = pytest.mark.gpu
 SIZES = [128, 150, 300, 511, 640, 1000]      # N_i; D_i = 4 N_i (ragged vs every tile)
 
 
-def _batch(K=16, em=20, tol=1e-5, seed0=7, sigma=0.1):
+def _batch(K=16, em=20, tol=1e-5, seed0=7, sigma=0.1, shapes=None):
     phis, ys, betas, seeds, refs = [], [], [], [], []
-    for i, N in enumerate(SIZES):
-        D = 4 * N
+    shapes = shapes or [(N, 4 * N) for N in SIZES]
+    for i, (N, D) in enumerate(shapes):
         prob = datagen.dense_problem(N, D, max(1, D // 20), sigma, seed=seed0 + i)
         t16, Phi64 = bf16_round(prob.Phi)
         y32 = prob.y.astype(np.float32)
@@ -54,6 +54,35 @@ def test_batched_matches_oracle_per_problem(cuda_lib):
         assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3, i
 
 
+def test_batched_split_k_products(cuda_lib):
+    """Problems with D > 8192 split their first product over K ranges and
+    reduce FP32 partials; smaller ones write the BF16 terms of W from the
+    product's epilogue.  Both kinds in one batch (and 3 vector chunks per
+    column at D = 8800), against the oracle.
+
+    Six CG iterations per E-step, fixed, two E-steps: the iterates are then
+    smooth functions of the products (an FP32 emulation of the oracle with
+    exact products differs from it by 2.8e-7 in mu).  Run to convergence,
+    FP32 vectors carry about cond(A) x 6e-8, which at these shapes is
+    already 1.4e-5 to 3e-5 for the emulation."""
+    shapes = [(2100, 8400), (150, 600), (1100, 8800), (2048, 8192)]
+    phis, ys, betas, seeds, refs, p = _batch(em=2, shapes=shapes)
+    p.fixed_cg_iters = 6
+    alphas, mus, ss, st = api.fit_batched(phis, ys, betas, seeds, p)
+    torch.cuda.synchronize()
+    errs = []
+    for i, (Phi64, y64, beta) in enumerate(refs):
+        ra, rmu, rs, rst = sbl.cofem_dense(Phi64, y64, beta, p.K, p.em_iters, p.cg_tol,
+                                           p.cg_max_iters, seed=seeds[i], fixed_cg_iters=6)
+        assert list(st["cg_iters"][i]) == [6] * p.em_iters, (i, st["cg_iters"][i])
+        errs.append(rel_l2(mus[i].cpu().numpy(), rmu))
+    # FP32 accumulation over K = D ~ 8400 in the first product leaves a
+    # relative error near sqrt(K) 2^-24 ~ 5e-6 per element of W (measured in
+    # mu: 1e-6 at D = 600, 6e-6 to 1.1e-5 at D ~ 8400); a wrong K range,
+    # partial or term row moves mu by O(1)
+    assert max(errs) <= 5e-5, errs
+
+
 def test_batched_matches_single_problem_fits(cuda_lib):
     phis, ys, betas, seeds, refs, p = _batch()
     alphas, mus, ss, st = api.fit_batched(phis, ys, betas, seeds, p)
@@ -76,3 +105,19 @@ def test_batched_rejects_unsupported(cuda_lib):
         with pytest.raises(B.CofemError) as e:
             api.fit_batched(phis, ys, betas, seeds, q)
         assert e.value.code == 6
+
+
+def test_batched_per_column_stop(cuda_lib):
+    """stop_rule = 1 in the batched solver: each problem's columns freeze at
+    their own tolerance, as in the single-problem fit and the oracle."""
+    phis, ys, betas, seeds, refs, p = _batch(em=10)
+    p.stop_rule = 1
+    alphas, mus, ss, st = api.fit_batched(phis, ys, betas, seeds, p)
+    torch.cuda.synchronize()
+    for i in (0, 3, 5):
+        Phi64, y64, beta = refs[i]
+        ra, rmu, rs, rst = sbl.cofem_dense(Phi64, y64, beta, p.K, p.em_iters, p.cg_tol,
+                                           p.cg_max_iters, seed=seeds[i], stop_rule=1)
+        assert rel_l2(mus[i].cpu().numpy(), rmu) <= 1e-4, (i, rel_l2(mus[i].cpu().numpy(), rmu))
+        tot_b, tot_o = sum(st["cg_iters"][i]), sum(rst.cg_iters)
+        assert abs(tot_b - tot_o) <= 0.05 * tot_o, (i, tot_b, tot_o)

@@ -383,3 +383,68 @@ def test_pcg_matches_cholesky_and_exact_start():
     assert np.linalg.norm(res.X - X_ref) / np.linalg.norm(X_ref) <= 1e-10
     res0 = sbl.pcg_solve(A, B, X_ref, minv, 1e-9, 10)
     assert res0.iters == 0
+
+
+# ------------------------------------------------ per-column stop rule (c3)
+
+def _spd_system(n=200, m=5, seed=3):
+    """SPD A with eigenvalues spread over [1, 20] (CG in FP64 stays close to
+    exact arithmetic), and right-hand sides that converge after 1, 3 and
+    about 30-40 iterations."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.exp(rng.uniform(0.0, np.log(20.0), n))
+    A = (Q * lam) @ Q.T
+    A = (A + A.T) / 2
+    B = rng.standard_normal((n, m)) * np.array([1e3, 1.0, 1e-2, 5.0, 1.0])[:m]
+    if m > 4:
+        B[:, 1] = Q[:, :3] @ np.ones(3)        # three eigenvectors: three iterations
+        B[:, 4] = Q[:, 0]                      # one eigenvector: one iteration
+    return A, B
+
+
+def test_per_column_stop_equals_independent_cg():
+    """stop_rule = 1 freezes each column at its own tolerance, so column j's
+    iterates are those of a textbook CG on A x = b_j alone; scipy's cg stops
+    on the same recursive-residual test ||r|| < rtol ||b||."""
+    import scipy.sparse.linalg as sla
+    A, B = _spd_system()
+    tol = 1e-8
+    res = sbl.cg_solve(lambda X: A @ X, B, tol, 500, stop_rule=1)
+    assert res.converged
+    iters = []
+    for j in range(B.shape[1]):
+        count = [0]
+
+        def cb(xk):
+            count[0] += 1
+        x, info = sla.cg(A, B[:, j], rtol=tol, atol=0.0, maxiter=500, callback=cb)
+        assert info == 0
+        iters.append(count[0])
+        # one iteration more or less moves x_j by 4e-9 or more here
+        assert np.linalg.norm(res.X[:, j] - x) <= 1e-12 * np.linalg.norm(x), j
+    assert res.iters == max(iters)
+    assert len(set(iters)) > 2                 # the columns did stop at different points
+    # every column meets its own test; the joint ratio is the reported one
+    Rt = B - A @ res.X
+    for j in range(B.shape[1]):
+        assert np.linalg.norm(Rt[:, j]) < 1e-7 * np.linalg.norm(B[:, j])
+    assert res.relres == pytest.approx(
+        np.sqrt(np.sum((B - A @ res.X) ** 2)) / np.linalg.norm(B), rel=1e-3)
+
+
+def test_per_column_stop_single_column_is_joint():
+    """With one right-hand side the per-column and the joint rule coincide."""
+    A, B = _spd_system(m=1)
+    r0 = sbl.cg_solve(lambda X: A @ X, B, 1e-9, 500, stop_rule=0)
+    r1 = sbl.cg_solve(lambda X: A @ X, B, 1e-9, 500, stop_rule=1)
+    assert r0.iters == r1.iters
+    np.testing.assert_array_equal(r0.X, r1.X)
+
+
+def test_per_column_stop_ignored_with_fixed_iterations():
+    A, B = _spd_system()
+    r0 = sbl.cg_solve(lambda X: A @ X, B, 1e-8, 500, fixed_iters=7, stop_rule=0)
+    r1 = sbl.cg_solve(lambda X: A @ X, B, 1e-8, 500, fixed_iters=7, stop_rule=1)
+    assert r0.iters == r1.iters == 7
+    np.testing.assert_array_equal(r0.X, r1.X)

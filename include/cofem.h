@@ -141,6 +141,18 @@ cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes);
 cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T,
                              const float* filters_dev, cofem_op** out);
 
+/* Masked-DCT Phi (the structured dictionary of Sec. 4.2): Phi = M C^T, with C
+ * the orthonormal DCT-II matrix of size D (C[k][n] = s_k cos(pi k (2n+1) /
+ * 2D), s_0 = sqrt(1/D), s_k = sqrt(2/D)) and M the selection of the N
+ * samples idx_dev[0..N-1] of its inverse:
+ *   (Phi z)_i  = (C^T z)[idx[i]],     Phi^T w = C (w scattered to idx).
+ * D a power of two, 16 <= D <= 2^22; 1 <= N <= D; idx_dev: N int32 device
+ * values, strictly increasing in [0, D), owned by the caller and read at
+ * every application (a violation is reported as COFEM_ERR_INVALID_ARG by
+ * the fit, through the device error word).  F32 vectors only; not with a
+ * learned warm start (COFEM_ERR_UNSUPPORTED). */
+cofem_status cofem_op_dct(int64_t D, int64_t N, const int32_t* idx_dev, cofem_op** out);
+
 /* Releases a handle (NULL is ignored). */
 void cofem_op_destroy(cofem_op* op);
 

@@ -33,6 +33,10 @@ notes of the repository):
 * Optional residual replacement every R iterations: r = B - A x.
 * The convolutional dictionary is circular: (Phi z)[n] = sum_c sum_j
   h[c, j] z_c[(n - j) mod L]; Phi^T is its exact adjoint (correlation).
+* The DCT dictionary of Sec. 4.2 ("inverse DCT followed by an undersampling
+  mask") uses the orthonormal DCT-II / DCT-III pair, so Phi Phi^T = I_N;
+  the mask keeps a uniformly random set of N = D/4 samples.
+* Optional per-column stop rule (stop_rule = 1): see cg_solve.
 
 Parity status: every function here is pinned by a CPU test against a closed
 form, a library routine on an independent formulation, brute force, or an
@@ -104,6 +108,36 @@ def conv_dictionary(h, L):
         return out.reshape((C * L,) + W.shape[1:])
 
     return phi, phit, C * L
+
+
+def dct_dictionary(idx, D):
+    """Masked-DCT Phi of Sec. 4.2 (N x D): the orthonormal inverse DCT of
+    length D followed by the undersampling mask that keeps samples idx.
+    With C the orthonormal DCT-II matrix, Phi = C^T[idx, :]:
+        Phi z = (C^T z)[idx],  Phi^T w = C (w scattered to idx, zeros elsewhere).
+    The transforms are scipy's FFT-based DCTs (a library step)."""
+    import scipy.fft as sfft
+    idx = np.asarray(idx)
+
+    def phi(Z):
+        return sfft.idct(np.asarray(Z, dtype=np.float64), type=2, norm="ortho", axis=0)[idx]
+
+    def phit(W):
+        W = np.asarray(W, dtype=np.float64)
+        T = np.zeros((D,) + W.shape[1:])
+        T[idx] = W
+        return sfft.dct(T, type=2, norm="ortho", axis=0)
+
+    return phi, phit, D
+
+
+def dct_matrix(D):
+    """Orthonormal DCT-II matrix from its definition:
+    C[k, n] = s_k cos(pi k (2n + 1) / (2D)), s_0 = sqrt(1/D), s_k = sqrt(2/D)."""
+    k = np.arange(D)[:, None]
+    n = np.arange(D)[None, :]
+    s = np.where(k == 0, np.sqrt(1.0 / D), np.sqrt(2.0 / D))
+    return s * np.cos(np.pi * k * (2 * n + 1) / (2 * D))
 
 
 def conv_matrix(h, L):
@@ -358,6 +392,11 @@ def cofem_learned(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, pred
 
 def cofem_dense(Phi, y, beta, K, em_iters, cg_tol, cg_max_iters, **kw):
     phi, phit, D = dense_dictionary(Phi)
+    return cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, **kw)
+
+
+def cofem_dct(idx, D, y, beta, K, em_iters, cg_tol, cg_max_iters, **kw):
+    phi, phit, D = dct_dictionary(idx, D)
     return cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, **kw)
 
 

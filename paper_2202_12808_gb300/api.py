@@ -68,6 +68,34 @@ class ConvOperator:
             self.handle = None
 
 
+class DctOperator:
+    """Masked-DCT Phi (Sec. 4.2): the orthonormal inverse DCT of length D,
+    then the N samples at `idx` (an int32 CUDA tensor, strictly increasing)."""
+
+    def __init__(self, idx: torch.Tensor, D: int):
+        if not idx.is_cuda or idx.dtype != torch.int32 or idx.dim() != 1:
+            raise ValueError("idx must be a 1-D int32 CUDA tensor")
+        self.idx = idx.contiguous()
+        self.N, self.D = int(self.idx.numel()), int(D)
+        self.dtype = B.COFEM_F32
+        self.handle = B.cofem_op_dct(self.D, self.N, self.idx.data_ptr())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            B.cofem_op_destroy(h)
+            self.handle = None
+
+
+def _op_device(op):
+    """Device of the tensors an operator handle reads."""
+    for name in ("phi", "h", "idx"):
+        t = getattr(op, name, None)
+        if t is not None:
+            return t.device
+    raise TypeError("unknown operator %r" % type(op).__name__)
+
+
 @dataclass
 class FitResult:
     alpha: torch.Tensor
@@ -92,7 +120,7 @@ def fit(op, y, beta, p=None, ws=None, alpha=None, stream=None, **kw):
     if p is None:
         p = params(**kw)
     vec = torch.float64 if p.vec_dtype == B.COFEM_F64 else torch.float32
-    y = y.to(device=op.phi.device if hasattr(op, "phi") else op.h.device, dtype=vec).contiguous()
+    y = y.to(device=_op_device(op), dtype=vec).contiguous()
     dev = y.device
     if ws is None:
         ws = workspace(op, p, dev)

@@ -74,6 +74,7 @@ _SIGS = {
                                      ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "cofem_op_dense_attach_packed": (_S, [_P, _P, _SZ, _P]),
     "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "cofem_op_dct": (_S, [_I64, _I64, _P, ctypes.POINTER(_P)]),
     "cofem_op_destroy": (None, [_P]),
     "cofem_last_fit_fallbacks": (_I32, []),
     "cofem_op_col_norms": (_S, [_P, _P, _P]),
@@ -187,6 +188,12 @@ def cofem_op_dense_attach_packed(op, packed_ptr, nbytes, stream=0):
 def cofem_op_conv1d(L, C, T, filters_ptr):
     h = _P()
     _check(lib().cofem_op_conv1d(L, C, T, filters_ptr, ctypes.byref(h)), "cofem_op_conv1d")
+    return h
+
+
+def cofem_op_dct(D, N, idx_ptr):
+    h = _P()
+    _check(lib().cofem_op_dct(D, N, idx_ptr, ctypes.byref(h)), "cofem_op_dct")
     return h
 
 

@@ -18,11 +18,13 @@
 #include "dense.cuh"
 
 struct cofem_op {
-  int kind;                       // 0 dense, 1 conv
+  int kind;                       // 0 dense, 1 conv, 2 masked DCT
   cofem::DenseDesc dense;
   int64_t L;
   int C, T;
   const float* filters;
+  int64_t dct_D, dct_N;           // masked DCT: D coefficients, N kept samples
+  const int32_t* dct_idx;         // their indices (strictly increasing, caller's memory)
 };
 
 namespace cofem {
@@ -96,7 +98,7 @@ static bool op_supports(const cofem_op* op, int vec) {
     if (vec == COFEM_F32) return op->dense.dtype == COFEM_F32 || op->dense.dtype == COFEM_BF16;
     return false;
   }
-  return vec == COFEM_F32;     // convolution: FP32 vectors
+  return vec == COFEM_F32;     // convolution, masked DCT: FP32 vectors
 }
 
 // Convolution scratch: W (ncols x L floats), then the filters padded to 64 taps.
@@ -135,6 +137,7 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
     }
     return b;
   }
+  if (op->kind == 2) return dct_ws_bytes(op->dct_D, ncols);
   return conv_w_bytes(op, ncols) + align256((size_t)op->C * 64 * sizeof(float));
 }
 
@@ -176,6 +179,14 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
     CKL();
     return COFEM_OK;
   }
+  if (op->kind == 2) {
+    const int np = dct_apply(op->dct_D, op->dct_idx, op->dct_N, (const float*)x, ld, ncols,
+                             (float*)y, beta, alpha, vec == COFEM_F32 ? alpha32 : nullptr, dots,
+                             ws, err, st);
+    if (nparts) *nparts = dots ? np : 0;
+    CKL();
+    return COFEM_OK;
+  }
   const float* h64 = conv_filters64(op, ws, ncols, st);
   float* W = (float*)ws;
   conv_forward(h64, op->C, op->L, (const float*)x, ld, ncols, W, op->L, st);
@@ -198,6 +209,12 @@ static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64
     else
       dense_simt_forward<__nv_bfloat16, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw,
                                                ws, st);
+    CKL();
+    return COFEM_OK;
+  }
+  if (op->kind == 2) {
+    dct_forward(op->dct_D, op->dct_idx, op->dct_N, (const float*)z, ldz, ncols, (float*)w, ldw,
+                ws, nullptr, st);
     CKL();
     return COFEM_OK;
   }
@@ -225,6 +242,12 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
     CKL();
     return COFEM_OK;
   }
+  if (op->kind == 2) {
+    dct_adjoint(op->dct_D, op->dct_idx, op->dct_N, (const float*)w, ldw, ncols, (float*)z, ldz,
+                beta, ws, nullptr, st);
+    CKL();
+    return COFEM_OK;
+  }
   const float* h64 = conv_filters64(op, ws, ncols, st);
   conv_adjoint(h64, op->C, op->L, (const float*)w, ldw, ncols, (float*)z, ldz, beta, nullptr,
                nullptr, nullptr, st);
@@ -232,9 +255,11 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
   return COFEM_OK;
 }
 
-static int64_t op_N(const cofem_op* op) { return op->kind == 0 ? op->dense.N : op->L; }
+static int64_t op_N(const cofem_op* op) {
+  return op->kind == 0 ? op->dense.N : op->kind == 2 ? op->dct_N : op->L;
+}
 static int64_t op_D(const cofem_op* op) {
-  return op->kind == 0 ? op->dense.D : (int64_t)op->C * op->L;
+  return op->kind == 0 ? op->dense.D : op->kind == 2 ? op->dct_D : (int64_t)op->C * op->L;
 }
 
 // --------------------------------------------------------------- layout
@@ -292,6 +317,7 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (!op_supports(op, p->vec_dtype)) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
+  if (p->mlp && op->kind == 2) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 
@@ -718,6 +744,18 @@ cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T, const float* filte
   return COFEM_OK;
 }
 
+cofem_status cofem_op_dct(int64_t D, int64_t N, const int32_t* idx_dev, cofem_op** out) {
+  if (!out || !idx_dev || !dct_size_ok(D) || N < 1 || N > D || ((uintptr_t)idx_dev & 3))
+    return COFEM_ERR_INVALID_ARG;
+  cofem_op* op = new cofem_op();
+  op->kind = 2;
+  op->dct_D = D;
+  op->dct_N = N;
+  op->dct_idx = idx_dev;
+  *out = op;
+  return COFEM_OK;
+}
+
 void cofem_op_destroy(cofem_op* op) { delete op; }
 
 cofem_status cofem_op_shape(const cofem_op* op, int64_t* N, int64_t* D) {
@@ -914,6 +952,7 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 int op_is_dense(const cofem_op* op) { return op->kind == 0; }
 DenseDesc op_dense_desc(const cofem_op* op) { return op->dense; }
 int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h) {
+  if (op->kind != 1) return -1;
   *L = op->L;
   *C = op->C;
   *T = op->T;

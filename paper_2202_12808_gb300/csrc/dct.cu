@@ -1,0 +1,353 @@
+// Masked-DCT dictionary (the structured Phi of Sec. 4.2): Phi = M C^T with C
+// the orthonormal DCT-II matrix of size D (C^T = C^-1 its inverse, DCT-III)
+// and M the N x D row selection of an undersampling mask:
+//   Phi z      = (C^T z)[idx]                    inverse DCT, keep N samples
+//   Phi^T w    = C scatter_idx(w)                zero-fill, forward DCT
+//   Phi^T Phi x = C (m . (C^T x))                m = 0/1 mask of the kept samples
+// so one operator application of the E-step, A X = beta Phi^T Phi X + alpha . X
+// (Eq. (mat-eq)), is an inverse DCT, a mask, and a forward DCT per column:
+// tau_D = O(D log D) (Sec. 3.2).
+//
+// DCTs by a length-D complex FFT (Makhoul's mapping, IEEE TASSP 1980):
+//   DCT-II:  v_n = x_{2n} (n < D/2), v_n = x_{2D-1-2n} (n >= D/2); V = FFT(v);
+//            X_k = s_k Re(e^{-i pi k / 2D} V_k),  s_0 = sqrt(1/D), s_k = sqrt(2/D)
+//   DCT-III: V_k = e^{i pi k / 2D} (X_k / s_k - i X_{D-k} / s_{D-k}) (X_D := 0);
+//            v = IFFT(V); x_{2m} = v_m, x_{2m+1} = v_{D-1-m}
+// and the FFT of length D = D1 D2 by the four-step decomposition: pass 1 runs
+// D2 transforms of length D1 over the stride-D2 subsequences and multiplies by
+// e^{-+2 pi i n2 k1 / D}, pass 2 runs D1 transforms of length D2 over the
+// rows; the DCT pre- and post-processing is fused into the loads of pass 1 and
+// the stores of pass 2.  Each block holds G transforms (G Lf = kFftElems
+// complex values) in shared memory and runs a radix-2 decimation-in-time FFT
+// on them (bit-reversed load, log2 Lf stages, a per-block twiddle table).
+#include "kernels.cuh"
+
+namespace cofem {
+void apply_tick(cudaStream_t st);
+}
+
+namespace cofem {
+
+constexpr int kFftElems = 4096;    // complex values per block
+constexpr int kFftThreads = 256;
+constexpr int kFftMaxLg = 11;      // transforms of up to 2048 points per pass (D <= 2^22)
+
+enum DctMode { kIdct1 = 0, kIdct2 = 1, kDct1 = 2, kDct2 = 3 };
+
+struct DctArgs {
+  int64_t D;
+  int lg1, lg2;            // D1 = 2^lg1 (pass 1 length), D2 = 2^lg2 (pass 2 length)
+  const float* xin;        // real input: X (IDCT1) or T (DCT1)
+  int64_t ldx;
+  float2* cbuf;            // complex intermediate, ncols x D, pitch D
+  float* tout;             // IDCT2: real output (time domain), pitch ldt
+  int64_t ldt;
+  const float* mask;       // IDCT2: 0/1 per sample, or null (keep all)
+  float* yout;             // DCT2 output, pitch ldy
+  int64_t ldy;
+  double beta;             // DCT2: output scale
+  const double* alpha;     // DCT2: + alpha . x (x = xdiag) when alpha or alpha32 is set
+  const float* alpha32;
+  const float* xdiag;
+  int64_t ldxd;
+  double* dots;            // DCT2: per-block partials of x_j^T y_j, [block][kMaxCols]
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// e^{i pi t} for t = num / den (num, den integers, den a power of two)
+__device__ __forceinline__ float2 cis_pi(float t) {
+  float s, c;
+  sincospif(t, &s, &c);
+  return make_float2(c, s);
+}
+
+// G transforms of length 2^lg in s[t << lg ...], already in bit-reversed
+// order; sign -1: forward, +1: inverse (unscaled).  tw: 2^(lg-1) twiddles
+// e^{sign 2 pi i j / 2^lg}.
+__device__ void fft_stages(float2* s, const float2* tw, int lg, int G) {
+  const int half_n = 1 << (lg - 1);
+  for (int st = 1; st <= lg; ++st) {
+    const int half = 1 << (st - 1);
+    for (int b = threadIdx.x; b < G * half_n; b += blockDim.x) {
+      const int t = b >> (lg - 1), bb = b & (half_n - 1);
+      const int j = bb & (half - 1);
+      const int k = ((bb >> (st - 1)) << st) + j;
+      float2* row = s + (t << lg);
+      const float2 w = tw[j << (lg - st)];
+      const float2 u = row[k], v = cmul(w, row[k + half]);
+      row[k] = make_float2(u.x + v.x, u.y + v.y);
+      row[k + half] = make_float2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int e, int lg) { return (int)(__brev((unsigned)e) >> (32 - lg)); }
+
+// grid (transform groups, ncols), kFftThreads threads.
+template <int MODE>
+__global__ void __launch_bounds__(kFftThreads)
+dct_pass_kernel(DctArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float2 s[kFftElems];
+  __shared__ float2 tw[1 << (kFftMaxLg - 1)];
+  __shared__ double red[32];
+  constexpr bool pass1 = MODE == kIdct1 || MODE == kDct1;
+  constexpr bool inverse = MODE == kIdct1 || MODE == kIdct2;
+  const int j = blockIdx.y;
+  const int64_t D = a.D;
+  const int lg = pass1 ? a.lg1 : a.lg2;           // length of this pass's transforms
+  const int Lf = 1 << lg;
+  const int ntr = pass1 ? (1 << a.lg2) : (1 << a.lg1);   // transforms in the pass
+  const int G = min(kFftElems >> lg, ntr);
+  const int t0 = blockIdx.x * G;                   // first transform of this block
+  const float sgn = inverse ? 1.f : -1.f;
+  for (int i = threadIdx.x; i < (Lf >> 1); i += blockDim.x)
+    tw[i] = cis_pi(sgn * 2.f * (float)i / (float)Lf);
+  const float sD = sqrtf(1.f / (float)D), sK = sqrtf(2.f / (float)D);
+  float2* cb = a.cbuf + (int64_t)j * D;
+
+  // ---- load (bit-reversed into shared memory)
+  if (pass1) {
+    // element n1 of transform n2 sits at n = D2 n1 + n2; consecutive threads
+    // take consecutive n2 (contiguous addresses)
+    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
+      const int tt = i % G, e = i / G;
+      const int64_t n = ((int64_t)e << a.lg2) + t0 + tt;
+      float2 v;
+      if (MODE == kIdct1) {
+        const float* xj = a.xin + (int64_t)j * a.ldx;
+        const float xk = xj[n] / (n == 0 ? sD : sK);
+        const float xr = n == 0 ? 0.f : xj[D - n] / sK;
+        v = cmul(cis_pi((float)n / (float)(2 * D)), make_float2(xk, -xr));
+      } else {
+        const float* tj = a.xin + (int64_t)j * a.ldx;
+        const int64_t src = n < D / 2 ? 2 * n : 2 * D - 1 - 2 * n;
+        v = make_float2(tj[src], 0.f);
+      }
+      s[(tt << lg) + bitrev(e, lg)] = v;
+    }
+  } else {
+    // transform k1 is the contiguous row cb[D2 k1 ...]
+    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
+      const int tt = i >> lg, e = i & (Lf - 1);
+      const int64_t k1 = t0 + tt;
+      s[(tt << lg) + bitrev(e, lg)] = cb[(k1 << a.lg2) + e];
+    }
+  }
+  __syncthreads();
+  fft_stages(s, tw, lg, G);
+
+  // ---- store
+  if (pass1) {
+    // twiddle e^{sgn 2 pi i n2 k1 / D}, then cb[D2 k1 + n2]
+    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
+      const int tt = i % G, f = i / G;
+      const int64_t n2 = t0 + tt;
+      const int64_t r = (n2 * f) & (D - 1);
+      const float2 w = cis_pi(sgn * 2.f * (float)r / (float)D);
+      cb[((int64_t)f << a.lg2) + n2] = cmul(w, s[(tt << lg) + f]);
+    }
+  } else {
+    AccF dot;
+    const bool diag = MODE == kDct2 && (a.alpha32 != nullptr || a.alpha != nullptr);
+    // frequency k2 of transform k1 is output k = k1 + D1 k2; consecutive
+    // threads take consecutive k1
+    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
+      const int tt = i % G, f = i / G;
+      const int64_t k = (int64_t)(t0 + tt) + ((int64_t)f << a.lg1);
+      const float2 v = s[(tt << lg) + f];
+      if (MODE == kIdct2) {
+        const float val = v.x / (float)D;
+        const int64_t y = k < D / 2 ? 2 * k : 2 * (D - 1 - k) + 1;
+        const float m = a.mask ? a.mask[y] : 1.f;
+        a.tout[(int64_t)j * a.ldt + y] = m * val;
+      } else {
+        const float2 w = cis_pi(-(float)k / (float)(2 * D));
+        const float o = (k == 0 ? sD : sK) * (w.x * v.x - w.y * v.y);
+        float out = (float)a.beta * o;
+        if (diag) {
+          const float xv = a.xdiag[(int64_t)j * a.ldxd + k];
+          const float al = a.alpha32 ? a.alpha32[k] : (float)a.alpha[k];
+          out = fmaf(al, xv, out);
+          dot.add_prod(xv, out);
+        }
+        a.yout[(int64_t)j * a.ldy + k] = out;
+      }
+    }
+    if (MODE == kDct2 && a.dots) {
+      const double sdot = block_sum(dot, red);
+      if (threadIdx.x == 0) a.dots[(int64_t)blockIdx.x * kMaxCols + j] = sdot;
+    }
+  }
+}
+
+// 0/1 mask of the kept samples (dst must be zeroed); idx must be strictly
+// increasing in [0, D): a violation sets *err and is skipped.
+__global__ void dct_mask_kernel(const int32_t* idx, int64_t N, int64_t D, float* mask,
+                                int* err) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = idx[i];
+    const bool ok = v >= 0 && v < D && (i == 0 || idx[i - 1] < v);
+    if (!ok) {
+      if (err) atomicCAS(err, 0, (int)COFEM_ERR_INVALID_ARG);
+      continue;
+    }
+    mask[v] = 1.f;
+  }
+}
+
+// T[j][idx[i]] = W[j][i] (T zeroed before)
+__global__ void dct_scatter_kernel(const int32_t* idx, int64_t N, int64_t D, const float* W,
+                                   int64_t ldw, float* T, int64_t ldt, int* err) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = idx[i];
+    if (v < 0 || v >= D) {
+      if (err) atomicCAS(err, 0, (int)COFEM_ERR_INVALID_ARG);
+      continue;
+    }
+    T[(int64_t)j * ldt + v] = W[(int64_t)j * ldw + i];
+  }
+}
+
+// W[j][i] = T[j][idx[i]]
+__global__ void dct_gather_kernel(const int32_t* idx, int64_t N, int64_t D, const float* T,
+                                  int64_t ldt, float* W, int64_t ldw, int* err) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = idx[i];
+    float w = 0.f;
+    if (v >= 0 && v < D) w = T[(int64_t)j * ldt + v];
+    else if (err) atomicCAS(err, 0, (int)COFEM_ERR_INVALID_ARG);
+    W[(int64_t)j * ldw + i] = w;
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int ilog2(int64_t D) {
+  int p = 0;
+  while (((int64_t)1 << p) < D) ++p;
+  return p;
+}
+
+bool dct_size_ok(int64_t D) {
+  const int p = ilog2(D);
+  return D >= 16 && ((int64_t)1 << p) == D && p <= 2 * kFftMaxLg;
+}
+
+// workspace: complex buffer (ncols x D), real T (ncols x D), mask (D)
+size_t dct_ws_bytes(int64_t D, int ncols) {
+  return align256((size_t)ncols * D * sizeof(float2)) + align256((size_t)ncols * D * sizeof(float)) +
+         align256((size_t)D * sizeof(float));
+}
+
+static DctArgs dct_args(int64_t D, char* ws, int ncols) {
+  DctArgs a = {};
+  a.D = D;
+  const int p = ilog2(D);
+  a.lg1 = p / 2;
+  a.lg2 = p - a.lg1;
+  a.cbuf = (float2*)ws;
+  a.tout = (float*)(ws + align256((size_t)ncols * D * sizeof(float2)));
+  a.ldt = D;
+  return a;
+}
+static float* dct_mask_buf(int64_t D, char* ws, int ncols) {
+  return (float*)(ws + align256((size_t)ncols * D * sizeof(float2)) +
+                  align256((size_t)ncols * D * sizeof(float)));
+}
+
+template <int MODE>
+static void dct_launch(const DctArgs& a, int ncols, cudaStream_t st) {
+  const bool pass1 = MODE == kIdct1 || MODE == kDct1;
+  const int lg = pass1 ? a.lg1 : a.lg2;
+  const int ntr = pass1 ? (1 << a.lg2) : (1 << a.lg1);
+  const int G = std::min(kFftElems >> lg, ntr);
+  launch_k(dct_pass_kernel<MODE>, dim3((unsigned)(ntr / G), (unsigned)ncols), dim3(kFftThreads),
+           0, st, a);
+}
+static int dct_parts(const DctArgs& a) {
+  const int G = std::min(kFftElems >> a.lg2, 1 << a.lg1);
+  return (1 << a.lg1) / G;
+}
+
+// Y = beta C (m . C^T X) + alpha . X, dots partials of x_j^T y_j
+int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
+              float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
+              char* ws, int* err, cudaStream_t st) {
+  DctArgs a = dct_args(D, ws, ncols);
+  float* mask = dct_mask_buf(D, ws, ncols);
+  cudaMemsetAsync(mask, 0, (size_t)D * sizeof(float), st);
+  launch_k(dct_mask_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096)), dim3(256),
+           0, st, idx, N, D, mask, err);
+  apply_tick(st);
+  a.xin = X;
+  a.ldx = ld;
+  a.mask = mask;
+  dct_launch<kIdct1>(a, ncols, st);
+  apply_tick(st);
+  dct_launch<kIdct2>(a, ncols, st);
+  apply_tick(st);
+  a.xin = a.tout;
+  a.ldx = a.ldt;
+  dct_launch<kDct1>(a, ncols, st);
+  apply_tick(st);
+  a.yout = Y;
+  a.ldy = ld;
+  a.beta = beta;
+  a.alpha = alpha;
+  a.alpha32 = alpha32;
+  a.xdiag = X;
+  a.ldxd = ld;
+  a.dots = dots;
+  dct_launch<kDct2>(a, ncols, st);
+  apply_tick(st);
+  return dct_parts(a);
+}
+
+// W = Phi Z: inverse DCT, keep the N masked samples
+void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64_t ldz, int ncols,
+                 float* W, int64_t ldw, char* ws, int* err, cudaStream_t st) {
+  DctArgs a = dct_args(D, ws, ncols);
+  a.xin = Z;
+  a.ldx = ldz;
+  a.mask = nullptr;
+  dct_launch<kIdct1>(a, ncols, st);
+  dct_launch<kIdct2>(a, ncols, st);
+  launch_k(dct_gather_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096), ncols),
+           dim3(256), 0, st, idx, N, D, (const float*)a.tout, a.ldt, W, ldw, err);
+}
+
+// Z = beta Phi^T W: zero-fill the unkept samples, forward DCT
+void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,
+                 float* Z, int64_t ldz, double beta, char* ws, int* err, cudaStream_t st) {
+  DctArgs a = dct_args(D, ws, ncols);
+  cudaMemsetAsync(a.tout, 0, (size_t)ncols * D * sizeof(float), st);
+  launch_k(dct_scatter_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096), ncols),
+           dim3(256), 0, st, idx, N, D, W, ldw, a.tout, a.ldt, err);
+  a.xin = a.tout;
+  a.ldx = a.ldt;
+  dct_launch<kDct1>(a, ncols, st);
+  a.yout = Z;
+  a.ldy = ldz;
+  a.beta = beta;
+  dct_launch<kDct2>(a, ncols, st);
+}
+
+}  // namespace cofem

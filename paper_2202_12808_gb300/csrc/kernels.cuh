@@ -46,6 +46,17 @@ int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw
                  double* dots, cudaStream_t st, const float* alpha32 = nullptr);
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st);
 
+// ---- masked DCT dictionary (dct.cu); idx: N strictly increasing sample indices ----
+bool dct_size_ok(int64_t D);                      // D a power of two, 16 <= D <= 2^22
+size_t dct_ws_bytes(int64_t D, int ncols);
+int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
+              float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
+              char* ws, int* err, cudaStream_t st);
+void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64_t ldz, int ncols,
+                 float* W, int64_t ldw, char* ws, int* err, cudaStream_t st);
+void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,
+                 float* Z, int64_t ldz, double beta, char* ws, int* err, cudaStream_t st);
+
 // ---- operator application ----
 // Every operator application writes, besides its output, per-block partial
 // dot products gamma_j = x_j^T (A x)_j into `dots` (layout [part][kMaxCols])

@@ -354,7 +354,7 @@ cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st) {
     int64_t L;
     int C, T;
     const float* h;
-    op_conv_desc(op, &L, &C, &T, &h);
+    if (op_conv_desc(op, &L, &C, &T, &h) != 0) return COFEM_ERR_UNSUPPORTED;
     launch_k(conv_col_norms_kernel, dim3(blocks_for((int64_t)C * L, 256)), dim3(256), 0, st, h, C,
              T, L, out);
   }

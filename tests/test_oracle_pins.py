@@ -448,3 +448,56 @@ def test_per_column_stop_ignored_with_fixed_iterations():
     r1 = sbl.cg_solve(lambda X: A @ X, B, 1e-8, 500, fixed_iters=7, stop_rule=1)
     assert r0.iters == r1.iters == 7
     np.testing.assert_array_equal(r0.X, r1.X)
+
+
+# ------------------------------------------------ masked DCT dictionary (Sec. 4.2)
+
+def test_dct_dictionary_matches_definition():
+    """The oracle's FFT-based Phi / Phi^T equal the rows of the transposed
+    DCT-II matrix written from its definition (index formula, loops)."""
+    D = 64
+    C = np.zeros((D, D))
+    for k in range(D):
+        for n in range(D):
+            s = np.sqrt(1.0 / D) if k == 0 else np.sqrt(2.0 / D)
+            C[k, n] = s * np.cos(np.pi * k * (2 * n + 1) / (2 * D))
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(D, 16, replace=False))
+    phi, phit, _ = sbl.dct_dictionary(idx, D)
+    Z = rng.standard_normal((D, 3))
+    W = rng.standard_normal((16, 3))
+    np.testing.assert_allclose(phi(Z), C.T[idx] @ Z, atol=1e-12)
+    np.testing.assert_allclose(phit(W), C[:, idx] @ W, atol=1e-12)
+    np.testing.assert_allclose(sbl.dct_matrix(D), C, atol=1e-14)
+
+
+def test_dct_dictionary_closed_forms():
+    """Orthonormality: Phi Phi^T = I_N; the DCT of a constant is sqrt(D) e_0
+    and of the k-th cosine sqrt(D/2) e_k; the adjoint identity."""
+    D = 256
+    idx = np.arange(D)
+    phi, phit, _ = sbl.dct_dictionary(idx, D)
+    n = np.arange(D)
+    e = phit(np.ones(D))
+    assert abs(e[0] - np.sqrt(D)) < 1e-12 and np.max(np.abs(e[1:])) < 1e-12
+    for k in (1, 5, 200):
+        c = phit(np.cos(np.pi * k * (2 * n + 1) / (2 * D)))
+        assert abs(c[k] - np.sqrt(D / 2)) < 1e-11
+        c[k] = 0.0
+        assert np.max(np.abs(c)) < 1e-11
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(D, 64, replace=False))
+    phi, phit, _ = sbl.dct_dictionary(idx, D)
+    W = rng.standard_normal((64, 2))
+    np.testing.assert_allclose(phi(phit(W)), W, atol=1e-12)
+    z, w = rng.standard_normal(D), rng.standard_normal(64)
+    assert abs(phi(z) @ w - z @ phit(w)) < 1e-10
+
+
+def test_dct_problem_generator():
+    from paper_2202_12808_gb300 import datagen
+    pr = datagen.dct_problem(1024, 256, 40, 0.0, seed=3)
+    assert pr.idx.dtype == np.int32 and np.all(np.diff(pr.idx) > 0)
+    assert np.count_nonzero(pr.z) == 40
+    phi, _, _ = sbl.dct_dictionary(pr.idx, 1024)
+    np.testing.assert_allclose(pr.y, phi(pr.z), atol=1e-12)

@@ -18,8 +18,11 @@
 // e^{-+2 pi i n2 k1 / D}, pass 2 runs D1 transforms of length D2 over the
 // rows; the DCT pre- and post-processing is fused into the loads of pass 1 and
 // the stores of pass 2.  Each block holds G transforms (G Lf = kFftElems
-// complex values) in shared memory and runs a radix-2 decimation-in-time FFT
-// on them (bit-reversed load, log2 Lf stages, a per-block twiddle table).
+// complex values) in shared memory and runs a Stockham (self-sorting)
+// mixed-radix FFT on them: radix-8 stages, then one radix-4 or radix-2
+// stage, each thread reading its butterflies' inputs into registers, all
+// threads synchronising, then writing the outputs (natural order in and
+// out, a per-block twiddle table).
 #include "kernels.cuh"
 
 namespace cofem {
@@ -29,6 +32,10 @@ void apply_tick(cudaStream_t st);
 namespace cofem {
 
 constexpr int kFftElems = 4096;    // complex values per block
+// shared-memory index of complex value i: one pad every 8 values, so that
+// the stride-8 writes of a radix-8 stage spread over the banks
+__device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
+constexpr int kFftSmem = kFftElems + kFftElems / 8;
 constexpr int kFftThreads = 256;
 constexpr int kFftMaxLg = 11;      // transforms of up to 2048 points per pass (D <= 2^22)
 
@@ -63,36 +70,112 @@ __device__ __forceinline__ float2 cis_pi(float t) {
   return make_float2(c, s);
 }
 
-// G transforms of length 2^lg in s[t << lg ...], already in bit-reversed
-// order; sign -1: forward, +1: inverse (unscaled).  tw: 2^(lg-1) twiddles
-// e^{sign 2 pi i j / 2^lg}.
-__device__ void fft_stages(float2* s, const float2* tw, int lg, int G) {
-  const int half_n = 1 << (lg - 1);
-  for (int st = 1; st <= lg; ++st) {
-    const int half = 1 << (st - 1);
-    for (int b = threadIdx.x; b < G * half_n; b += blockDim.x) {
-      const int t = b >> (lg - 1), bb = b & (half_n - 1);
-      const int j = bb & (half - 1);
-      const int k = ((bb >> (st - 1)) << st) + j;
-      float2* row = s + (t << lg);
-      const float2 w = tw[j << (lg - st)];
-      const float2 u = row[k], v = cmul(w, row[k + half]);
-      row[k] = make_float2(u.x + v.x, u.y + v.y);
-      row[k + half] = make_float2(u.x - v.x, u.y - v.y);
-    }
-    __syncthreads();
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// (sgn i) z
+__device__ __forceinline__ float2 mul_i(float2 z, float sgn) { return make_float2(-sgn * z.y, sgn * z.x); }
+
+// In-register DFTs of length 2, 4, 8 with root e^{sgn 2 pi i / R}.
+template <int LR>
+__device__ __forceinline__ void dft_reg(float2 (&v)[1 << LR], float sgn) {
+  if (LR == 1) {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  } else if (LR == 2) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = mul_i(csub(v[1], v[3]), sgn);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  } else {
+    // radix 2 x 4: X_k = E_k + w^k O_k, X_{k+4} = E_k - w^k O_k, w = e^{sgn i pi / 4}
+    float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_reg<2>(e, sgn);
+    dft_reg<2>(o, sgn);
+    const float h = 0.70710678118654752f;
+    const float2 t1 = make_float2(h * (o[1].x - sgn * o[1].y), h * (o[1].y + sgn * o[1].x));
+    const float2 t2 = mul_i(o[2], sgn);
+    const float2 t3 = make_float2(h * (-o[3].x - sgn * o[3].y), h * (-o[3].y + sgn * o[3].x));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
   }
 }
 
-__device__ __forceinline__ int bitrev(int e, int lg) { return (int)(__brev((unsigned)e) >> (32 - lg)); }
+// e^{sgn 2 pi i m / Lf} from the half table tw[m] (m < Lf/2), m < Lf
+__device__ __forceinline__ float2 twiddle(const float2* tw, int m, int half) {
+  const float2 w = tw[m & (half - 1)];
+  return m < half ? w : make_float2(-w.x, -w.y);
+}
+
+// One Stockham stage of radix R = 2^LR over G transforms of length 2^lg in
+// s[pad(...)], Ns = product of the radices of the earlier stages: butterfly
+// j of a transform reads elements j + r Lf/R, twiddles them by
+// e^{sgn 2 pi i (j mod Ns) r / (Ns R)}, and writes element
+// (j - j mod Ns) R + (j mod Ns) + r Ns.
+template <int LR>
+__device__ __forceinline__ void fft_stage(float2* s, const float2* tw, int lg, int G, int lgNs,
+                                          float sgn) {
+  constexpr int R = 1 << LR;
+  constexpr int TPT = kFftElems / kFftThreads / R;      // butterflies per thread
+  const int Lf = 1 << lg, nb = Lf >> LR, ntask = G * nb;
+  const int Ns = 1 << lgNs;
+  float2 v[TPT][R];
+  int dst[TPT];
+#pragma unroll
+  for (int q = 0; q < TPT; ++q) {
+    const int b = threadIdx.x + q * kFftThreads;
+    dst[q] = -1;
+    if (b < ntask) {
+      const int t = b >> (lg - LR), j = b & (nb - 1);
+      const int base = t << lg;
+      const int jm = j & (Ns - 1);
+      const int unit = jm << (lg - lgNs - LR);       // Lf (j mod Ns) / (Ns R)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = s[pad(base + j + r * nb)];
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], twiddle(tw, (unit * r) & (Lf - 1), Lf >> 1));
+      dft_reg<LR>(v[q], sgn);
+      dst[q] = base + ((j - jm) << LR) + jm;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < TPT; ++q)
+    if (dst[q] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[pad(dst[q] + (r << lgNs))] = v[q][r];
+    }
+  __syncthreads();
+}
+
+// G transforms of length 2^lg in natural order in s[pad(t << lg ...)]:
+// radix-8 stages, then one radix-4 or radix-2 stage; natural order out.
+__device__ void fft_stages(float2* s, const float2* tw, int lg, int G, float sgn) {
+  int lgNs = 0;
+  while (lg - lgNs >= 3) {
+    fft_stage<3>(s, tw, lg, G, lgNs, sgn);
+    lgNs += 3;
+  }
+  if (lg - lgNs == 2) fft_stage<2>(s, tw, lg, G, lgNs, sgn);
+  else if (lg - lgNs == 1) fft_stage<1>(s, tw, lg, G, lgNs, sgn);
+}
+
 
 // grid (transform groups, ncols), kFftThreads threads.
 template <int MODE>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 3)
 dct_pass_kernel(DctArgs a) {
   pdl_wait();
   pdl_trigger();
-  __shared__ float2 s[kFftElems];
+  __shared__ float2 s[kFftSmem];
   __shared__ float2 tw[1 << (kFftMaxLg - 1)];
   __shared__ double red[32];
   constexpr bool pass1 = MODE == kIdct1 || MODE == kDct1;
@@ -103,53 +186,55 @@ dct_pass_kernel(DctArgs a) {
   const int Lf = 1 << lg;
   const int ntr = pass1 ? (1 << a.lg2) : (1 << a.lg1);   // transforms in the pass
   const int G = min(kFftElems >> lg, ntr);
+  const int lgG = __ffs(G) - 1;                    // G is a power of two
   const int t0 = blockIdx.x * G;                   // first transform of this block
   const float sgn = inverse ? 1.f : -1.f;
   for (int i = threadIdx.x; i < (Lf >> 1); i += blockDim.x)
     tw[i] = cis_pi(sgn * 2.f * (float)i / (float)Lf);
   const float sD = sqrtf(1.f / (float)D), sK = sqrtf(2.f / (float)D);
+  const float rsD = 1.f / sD, rsK = 1.f / sK;
   float2* cb = a.cbuf + (int64_t)j * D;
 
-  // ---- load (bit-reversed into shared memory)
+  // ---- load (natural order into shared memory)
   if (pass1) {
     // element n1 of transform n2 sits at n = D2 n1 + n2; consecutive threads
     // take consecutive n2 (contiguous addresses)
     for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i % G, e = i / G;
+      const int tt = i & (G - 1), e = i >> lgG;
       const int64_t n = ((int64_t)e << a.lg2) + t0 + tt;
       float2 v;
       if (MODE == kIdct1) {
         const float* xj = a.xin + (int64_t)j * a.ldx;
-        const float xk = xj[n] / (n == 0 ? sD : sK);
-        const float xr = n == 0 ? 0.f : xj[D - n] / sK;
+        const float xk = xj[n] * (n == 0 ? rsD : rsK);
+        const float xr = n == 0 ? 0.f : xj[D - n] * rsK;
         v = cmul(cis_pi((float)n / (float)(2 * D)), make_float2(xk, -xr));
       } else {
         const float* tj = a.xin + (int64_t)j * a.ldx;
         const int64_t src = n < D / 2 ? 2 * n : 2 * D - 1 - 2 * n;
         v = make_float2(tj[src], 0.f);
       }
-      s[(tt << lg) + bitrev(e, lg)] = v;
+      s[pad((tt << lg) + e)] = v;
     }
   } else {
     // transform k1 is the contiguous row cb[D2 k1 ...]
     for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
       const int tt = i >> lg, e = i & (Lf - 1);
       const int64_t k1 = t0 + tt;
-      s[(tt << lg) + bitrev(e, lg)] = cb[(k1 << a.lg2) + e];
+      s[pad((tt << lg) + e)] = cb[(k1 << a.lg2) + e];
     }
   }
   __syncthreads();
-  fft_stages(s, tw, lg, G);
+  fft_stages(s, tw, lg, G, sgn);
 
   // ---- store
   if (pass1) {
     // twiddle e^{sgn 2 pi i n2 k1 / D}, then cb[D2 k1 + n2]
     for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i % G, f = i / G;
+      const int tt = i & (G - 1), f = i >> lgG;
       const int64_t n2 = t0 + tt;
       const int64_t r = (n2 * f) & (D - 1);
       const float2 w = cis_pi(sgn * 2.f * (float)r / (float)D);
-      cb[((int64_t)f << a.lg2) + n2] = cmul(w, s[(tt << lg) + f]);
+      cb[((int64_t)f << a.lg2) + n2] = cmul(w, s[pad((tt << lg) + f)]);
     }
   } else {
     AccF dot;
@@ -157,11 +242,11 @@ dct_pass_kernel(DctArgs a) {
     // frequency k2 of transform k1 is output k = k1 + D1 k2; consecutive
     // threads take consecutive k1
     for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i % G, f = i / G;
+      const int tt = i & (G - 1), f = i >> lgG;
       const int64_t k = (int64_t)(t0 + tt) + ((int64_t)f << a.lg1);
-      const float2 v = s[(tt << lg) + f];
+      const float2 v = s[pad((tt << lg) + f)];
       if (MODE == kIdct2) {
-        const float val = v.x / (float)D;
+        const float val = v.x * (1.f / (float)D);
         const int64_t y = k < D / 2 ? 2 * k : 2 * (D - 1 - k) + 1;
         const float m = a.mask ? a.mask[y] : 1.f;
         a.tout[(int64_t)j * a.ldt + y] = m * val;

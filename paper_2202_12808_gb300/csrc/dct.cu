@@ -58,6 +58,8 @@ struct DctArgs {
   const float* xdiag;
   int64_t ldxd;
   double* dots;            // DCT2: per-block partials of x_j^T y_j, [block][kMaxCols]
+  const float2* tabM;      // e^{i pi n / 2D}, n < D (DCT pre-/post-twiddles)
+  const float2* tabW;      // e^{-2 pi i q / D}, q < D2 (low part of the four-step twiddle)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -180,13 +182,15 @@ dct_pass_kernel(DctArgs a) {
   __shared__ double red[32];
   constexpr bool pass1 = MODE == kIdct1 || MODE == kDct1;
   constexpr bool inverse = MODE == kIdct1 || MODE == kIdct2;
+  constexpr int kPer = kFftElems / kFftThreads;   // elements per thread
   const int j = blockIdx.y;
-  const int64_t D = a.D;
+  const int D = (int)a.D;                          // <= 2^22
   const int lg = pass1 ? a.lg1 : a.lg2;           // length of this pass's transforms
   const int Lf = 1 << lg;
   const int ntr = pass1 ? (1 << a.lg2) : (1 << a.lg1);   // transforms in the pass
   const int G = min(kFftElems >> lg, ntr);
   const int lgG = __ffs(G) - 1;                    // G is a power of two
+  const int nel = G << lg;                         // elements of this block
   const int t0 = blockIdx.x * G;                   // first transform of this block
   const float sgn = inverse ? 1.f : -1.f;
   for (int i = threadIdx.x; i < (Lf >> 1); i += blockDim.x)
@@ -195,32 +199,43 @@ dct_pass_kernel(DctArgs a) {
   const float rsD = 1.f / sD, rsK = 1.f / sK;
   float2* cb = a.cbuf + (int64_t)j * D;
 
-  // ---- load (natural order into shared memory)
+  // ---- load: all of a thread's global loads first, then the shared stores
+  float2 v[kPer];
   if (pass1) {
     // element n1 of transform n2 sits at n = D2 n1 + n2; consecutive threads
     // take consecutive n2 (contiguous addresses)
-    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i & (G - 1), e = i >> lgG;
-      const int64_t n = ((int64_t)e << a.lg2) + t0 + tt;
-      float2 v;
-      if (MODE == kIdct1) {
-        const float* xj = a.xin + (int64_t)j * a.ldx;
-        const float xk = xj[n] * (n == 0 ? rsD : rsK);
-        const float xr = n == 0 ? 0.f : xj[D - n] * rsK;
-        v = cmul(cis_pi((float)n / (float)(2 * D)), make_float2(xk, -xr));
-      } else {
-        const float* tj = a.xin + (int64_t)j * a.ldx;
-        const int64_t src = n < D / 2 ? 2 * n : 2 * D - 1 - 2 * n;
-        v = make_float2(tj[src], 0.f);
+    const float* xj = a.xin + (int64_t)j * a.ldx;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      v[q] = make_float2(0.f, 0.f);
+      if (i < nel) {
+        const int n = ((i >> lgG) << a.lg2) + t0 + (i & (G - 1));
+        if (MODE == kIdct1) {
+          const float xk = xj[n] * (n == 0 ? rsD : rsK);
+          const float xr = n == 0 ? 0.f : xj[D - n] * rsK;
+          v[q] = cmul(a.tabM[n], make_float2(xk, -xr));      // e^{i pi n / 2D}
+        } else {
+          v[q] = make_float2(xj[n < D / 2 ? 2 * n : 2 * D - 1 - 2 * n], 0.f);
+        }
       }
-      s[pad((tt << lg) + e)] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      if (i < nel) s[pad(((i & (G - 1)) << lg) + (i >> lgG))] = v[q];
     }
   } else {
     // transform k1 is the contiguous row cb[D2 k1 ...]
-    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i >> lg, e = i & (Lf - 1);
-      const int64_t k1 = t0 + tt;
-      s[pad((tt << lg) + e)] = cb[(k1 << a.lg2) + e];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      if (i < nel) v[q] = cb[((t0 + (i >> lg)) << a.lg2) + (i & (Lf - 1))];
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      if (i < nel) s[pad(i)] = v[q];
     }
   }
   __syncthreads();
@@ -228,45 +243,79 @@ dct_pass_kernel(DctArgs a) {
 
   // ---- store
   if (pass1) {
-    // twiddle e^{sgn 2 pi i n2 k1 / D}, then cb[D2 k1 + n2]
-    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i & (G - 1), f = i >> lgG;
-      const int64_t n2 = t0 + tt;
-      const int64_t r = (n2 * f) & (D - 1);
-      const float2 w = cis_pi(sgn * 2.f * (float)r / (float)D);
-      cb[((int64_t)f << a.lg2) + n2] = cmul(w, s[pad((tt << lg) + f)]);
+    // twiddle e^{sgn 2 pi i n2 k1 / D} = e^{sgn 2 pi i qh / D1} e^{sgn 2 pi i ql / D}
+    // with n2 k1 = qh D2 + ql (the first factor is this pass's own table),
+    // then cb[D2 k1 + n2]
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      if (i < nel) {
+        const int tt = i & (G - 1), f = i >> lgG;
+        const int n2 = t0 + tt;
+        const int r = n2 * f;                      // < D
+        const float2 lo = a.tabW[r & ((1 << a.lg2) - 1)];
+        const float2 w = cmul(twiddle(tw, r >> a.lg2, Lf >> 1),
+                              inverse ? make_float2(lo.x, -lo.y) : lo);
+        cb[(f << a.lg2) + n2] = cmul(w, s[pad((tt << lg) + f)]);
+      }
     }
   } else {
     AccF dot;
     const bool diag = MODE == kDct2 && (a.alpha32 != nullptr || a.alpha != nullptr);
     // frequency k2 of transform k1 is output k = k1 + D1 k2; consecutive
     // threads take consecutive k1
-    for (int i = threadIdx.x; i < G * Lf; i += blockDim.x) {
-      const int tt = i & (G - 1), f = i >> lgG;
-      const int64_t k = (int64_t)(t0 + tt) + ((int64_t)f << a.lg1);
-      const float2 v = s[pad((tt << lg) + f)];
-      if (MODE == kIdct2) {
-        const float val = v.x * (1.f / (float)D);
-        const int64_t y = k < D / 2 ? 2 * k : 2 * (D - 1 - k) + 1;
-        const float m = a.mask ? a.mask[y] : 1.f;
-        a.tout[(int64_t)j * a.ldt + y] = m * val;
-      } else {
-        const float2 w = cis_pi(-(float)k / (float)(2 * D));
-        const float o = (k == 0 ? sD : sK) * (w.x * v.x - w.y * v.y);
-        float out = (float)a.beta * o;
-        if (diag) {
-          const float xv = a.xdiag[(int64_t)j * a.ldxd + k];
-          const float al = a.alpha32 ? a.alpha32[k] : (float)a.alpha[k];
-          out = fmaf(al, xv, out);
-          dot.add_prod(xv, out);
+    float xv[kPer], al[kPer];
+    if (MODE == kDct2 && diag) {
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int i = threadIdx.x + q * kFftThreads;
+        xv[q] = al[q] = 0.f;
+        if (i < nel) {
+          const int k = t0 + (i & (G - 1)) + ((i >> lgG) << a.lg1);
+          xv[q] = a.xdiag[(int64_t)j * a.ldxd + k];
+          al[q] = a.alpha32 ? a.alpha32[k] : (float)a.alpha[k];
         }
-        a.yout[(int64_t)j * a.ldy + k] = out;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kFftThreads;
+      if (i < nel) {
+        const int tt = i & (G - 1), f = i >> lgG;
+        const int k = t0 + tt + (f << a.lg1);
+        const float2 val = s[pad((tt << lg) + f)];
+        if (MODE == kIdct2) {
+          const float re = val.x * (1.f / (float)D);
+          const int y = k < D / 2 ? 2 * k : 2 * (D - 1 - k) + 1;
+          const float m = a.mask ? a.mask[y] : 1.f;
+          a.tout[(int64_t)j * a.ldt + y] = m * re;
+        } else {
+          const float2 w = a.tabM[k];              // e^{+i pi k / 2D}; conjugated here
+          const float o = (k == 0 ? sD : sK) * (w.x * val.x + w.y * val.y);
+          float out = (float)a.beta * o;
+          if (diag) {
+            out = fmaf(al[q], xv[q], out);
+            dot.add_prod(xv[q], out);
+          }
+          a.yout[(int64_t)j * a.ldy + k] = out;
+        }
       }
     }
     if (MODE == kDct2 && a.dots) {
       const double sdot = block_sum(dot, red);
       if (threadIdx.x == 0) a.dots[(int64_t)blockIdx.x * kMaxCols + j] = sdot;
     }
+  }
+}
+
+// tabM[n] = e^{i pi n / 2D} (n < D), tabW[q] = e^{-2 pi i q / D} (q < D2)
+__global__ void dct_twiddle_kernel(int64_t D, int D2, float2* tabM, float2* tabW) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < D;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    tabM[n] = cis_pi((float)n / (float)(2 * D));
+    if (n < D2) tabW[n] = cis_pi(-2.f * (float)n / (float)D);
   }
 }
 
@@ -336,13 +385,15 @@ bool dct_size_ok(int64_t D) {
   return D >= 16 && ((int64_t)1 << p) == D && p <= 2 * kFftMaxLg;
 }
 
-// workspace: complex buffer (ncols x D), real T (ncols x D), mask (D)
+// workspace: complex buffer (ncols x D), real T (ncols x D), mask (D),
+// twiddle tables tabM (D complex) and tabW (D2 complex)
 size_t dct_ws_bytes(int64_t D, int ncols) {
   return align256((size_t)ncols * D * sizeof(float2)) + align256((size_t)ncols * D * sizeof(float)) +
-         align256((size_t)D * sizeof(float));
+         align256((size_t)D * sizeof(float)) + 2 * align256((size_t)D * sizeof(float2));
 }
 
-static DctArgs dct_args(int64_t D, char* ws, int ncols) {
+// Carves the workspace and fills the twiddle tables (one small launch).
+static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st) {
   DctArgs a = {};
   a.D = D;
   const int p = ilog2(D);
@@ -351,6 +402,14 @@ static DctArgs dct_args(int64_t D, char* ws, int ncols) {
   a.cbuf = (float2*)ws;
   a.tout = (float*)(ws + align256((size_t)ncols * D * sizeof(float2)));
   a.ldt = D;
+  char* t = ws + align256((size_t)ncols * D * sizeof(float2)) +
+            align256((size_t)ncols * D * sizeof(float)) + align256((size_t)D * sizeof(float));
+  float2* tabM = (float2*)t;
+  float2* tabW = (float2*)(t + align256((size_t)D * sizeof(float2)));
+  launch_k(dct_twiddle_kernel, dim3((unsigned)std::min<int64_t>((D + 255) / 256, 1024)), dim3(256),
+           0, st, D, 1 << a.lg2, tabM, tabW);
+  a.tabM = tabM;
+  a.tabW = tabW;
   return a;
 }
 static float* dct_mask_buf(int64_t D, char* ws, int ncols) {
@@ -376,7 +435,7 @@ static int dct_parts(const DctArgs& a) {
 int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
               float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
               char* ws, int* err, cudaStream_t st) {
-  DctArgs a = dct_args(D, ws, ncols);
+  DctArgs a = dct_args(D, ws, ncols, st);
   float* mask = dct_mask_buf(D, ws, ncols);
   cudaMemsetAsync(mask, 0, (size_t)D * sizeof(float), st);
   launch_k(dct_mask_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096)), dim3(256),
@@ -409,7 +468,7 @@ int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t 
 // W = Phi Z: inverse DCT, keep the N masked samples
 void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64_t ldz, int ncols,
                  float* W, int64_t ldw, char* ws, int* err, cudaStream_t st) {
-  DctArgs a = dct_args(D, ws, ncols);
+  DctArgs a = dct_args(D, ws, ncols, st);
   a.xin = Z;
   a.ldx = ldz;
   a.mask = nullptr;
@@ -422,7 +481,7 @@ void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64
 // Z = beta Phi^T W: zero-fill the unkept samples, forward DCT
 void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,
                  float* Z, int64_t ldz, double beta, char* ws, int* err, cudaStream_t st) {
-  DctArgs a = dct_args(D, ws, ncols);
+  DctArgs a = dct_args(D, ws, ncols, st);
   cudaMemsetAsync(a.tout, 0, (size_t)ncols * D * sizeof(float), st);
   launch_k(dct_scatter_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096), ncols),
            dim3(256), 0, st, idx, N, D, W, ldw, a.tout, a.ldt, err);

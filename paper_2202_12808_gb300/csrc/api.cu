@@ -182,7 +182,7 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
   if (op->kind == 2) {
     const int np = dct_apply(op->dct_D, op->dct_idx, op->dct_N, (const float*)x, ld, ncols,
                              (float*)y, beta, alpha, vec == COFEM_F32 ? alpha32 : nullptr, dots,
-                             ws, err, st);
+                             ws, err, st, (flags & kApplyOpPrepared) != 0);
     if (nparts) *nparts = dots ? np : 0;
     CKL();
     return COFEM_OK;
@@ -358,6 +358,8 @@ template <typename V>
 static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, double beta,
                                    char* ws, const FitLayout& L, double* mu, double* s,
                                    double* alpha, cudaGraphExec_t* exec) {
+  // structured operators: their tables were built once for the fit
+  const unsigned prep = op->kind == 2 ? kApplyOpPrepared : 0u;
   Streams ss;
   for (auto& x : ss.s) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
   CgCtl* ctl = (CgCtl*)(ws + L.ctl);
@@ -425,7 +427,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     }
     CKL();
     cofem_status rw = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws,
-                               cs, &ctl->error, 0u, alpha32);
+                               cs, &ctl->error, prep, alpha32);
     if (rw != COFEM_OK) return rw;
     launch_cg_init_warm<V>(cf, ctl, sc, X, R, P, Q, b, pvec, pvec2, pvec3, cs);
   } else {
@@ -459,7 +461,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       CK(cudaStreamBeginCaptureToGraph(is, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       int nparts = 0;
       rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, is,
-                    &ctl->error, kApplyPresplit, alpha32);
+                    &ctl->error, kApplyPresplit | prep, alpha32);
       if (rc != COFEM_OK) return rc;
       cf.gamma_parts = nparts;
       launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is);
@@ -469,7 +471,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       CK(cudaStreamEndCapture(is, &tmp));
     }
     rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, bs,
-                  &ctl->error, 0u, alpha32, &ctl->replace);
+                  &ctl->error, prep, alpha32, &ctl->replace);
     if (rc != COFEM_OK) return rc;
     launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, pvec2, bs);
     launch_cg_direction<V>(cf, ctl, sc, R, P, bs);
@@ -485,7 +487,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int nparts = 0;
     rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, bs,
-                  &ctl->error, cf.split_nt > 0 ? kApplyPresplit : 0u, alpha32);
+                  &ctl->error, (cf.split_nt > 0 ? kApplyPresplit : 0u) | prep, alpha32);
     if (rc != COFEM_OK) return rc;
     cf.gamma_parts = nparts;
     launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, bs);
@@ -497,7 +499,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       cudaStream_t is = ss.s[2];
       CK(cudaStreamBeginCaptureToGraph(is, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
       rc = op_apply(op, vec, X, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, is,
-                    &ctl->error, 0u, alpha32);
+                    &ctl->error, prep, alpha32);
       if (rc != COFEM_OK) return rc;
       launch_cg_true_resid<V>(cf, ctl, sc, R, Q, b, pvec, pvec2, is);
       CKL();
@@ -536,7 +538,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     CK(cudaStreamBeginCaptureToGraph(ws2, fwhile, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     int np2 = 0;
     rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &np2, opws, ws2, &ctl->error,
-                  pf.split_nt > 0 ? kApplyPresplit : 0u, alpha32);
+                  (pf.split_nt > 0 ? kApplyPresplit : 0u) | prep, alpha32);
     if (rc != COFEM_OK) return rc;
     pf.gamma_parts = np2;
     launch_cg_update<V>(pf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, ws2);
@@ -583,6 +585,13 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
   // b = beta Phi^T y  (once per fit: y and beta do not change)
   cofem_status rc = op_adjoint(op, p->vec_dtype, y, N, 1, ws + L.b, L.ld, beta, ws + L.opws, st);
   if (rc != COFEM_OK) return rc;
+  // the masked DCT's mask and twiddle tables, once per fit (the graph's
+  // applications reuse them)
+  if (op->kind == 2) {
+    dct_prepare(op->dct_D, op->dct_idx, op->dct_N, p->K + 1, ws + L.opws,
+                &((CgCtl*)(ws + L.ctl))->error, st);
+    CKL();
+  }
 
   if (p->mlp) {
     rc = mlp_col_norms(op, (float*)(ws + L.pn2), st);

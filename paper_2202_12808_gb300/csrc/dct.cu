@@ -392,8 +392,9 @@ size_t dct_ws_bytes(int64_t D, int ncols) {
          align256((size_t)D * sizeof(float)) + 2 * align256((size_t)D * sizeof(float2));
 }
 
-// Carves the workspace and fills the twiddle tables (one small launch).
-static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st) {
+// Carves the workspace; fills the twiddle tables (one small launch) unless
+// `tables` is false (they are already there).
+static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st, bool tables = true) {
   DctArgs a = {};
   a.D = D;
   const int p = ilog2(D);
@@ -406,8 +407,9 @@ static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st) {
             align256((size_t)ncols * D * sizeof(float)) + align256((size_t)D * sizeof(float));
   float2* tabM = (float2*)t;
   float2* tabW = (float2*)(t + align256((size_t)D * sizeof(float2)));
-  launch_k(dct_twiddle_kernel, dim3((unsigned)std::min<int64_t>((D + 255) / 256, 1024)), dim3(256),
-           0, st, D, 1 << a.lg2, tabM, tabW);
+  if (tables)
+    launch_k(dct_twiddle_kernel, dim3((unsigned)std::min<int64_t>((D + 255) / 256, 1024)),
+             dim3(256), 0, st, D, 1 << a.lg2, tabM, tabW);
   a.tabM = tabM;
   a.tabW = tabW;
   return a;
@@ -431,15 +433,24 @@ static int dct_parts(const DctArgs& a) {
   return (1 << a.lg1) / G;
 }
 
-// Y = beta C (m . C^T X) + alpha . X, dots partials of x_j^T y_j
-int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
-              float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
-              char* ws, int* err, cudaStream_t st) {
-  DctArgs a = dct_args(D, ws, ncols, st);
+// The mask and the twiddle tables in the workspace (dct_apply with
+// prepared = true reuses them).
+void dct_prepare(int64_t D, const int32_t* idx, int64_t N, int ncols, char* ws, int* err,
+                 cudaStream_t st) {
+  dct_args(D, ws, ncols, st, true);
   float* mask = dct_mask_buf(D, ws, ncols);
   cudaMemsetAsync(mask, 0, (size_t)D * sizeof(float), st);
   launch_k(dct_mask_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096)), dim3(256),
            0, st, idx, N, D, mask, err);
+}
+
+// Y = beta C (m . C^T X) + alpha . X, dots partials of x_j^T y_j
+int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
+              float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
+              char* ws, int* err, cudaStream_t st, bool prepared) {
+  if (!prepared) dct_prepare(D, idx, N, ncols, ws, err, st);
+  DctArgs a = dct_args(D, ws, ncols, st, false);
+  float* mask = dct_mask_buf(D, ws, ncols);
   apply_tick(st);
   a.xin = X;
   a.ldx = ld;

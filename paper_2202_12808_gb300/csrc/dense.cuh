@@ -96,6 +96,9 @@ inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
 // (rows split_row(j, t) of pitch plan.ld at plan.off_xs), written by the CG
 // kernels.
 constexpr unsigned kApplyPresplit = 1u;
+// kApplyOpPrepared -- structured operators: per-operator tables in the
+// scratch are already built (the masked DCT's mask and twiddles).
+constexpr unsigned kApplyOpPrepared = 2u;
 // Batched products over a work-item table (see TcItem / TcProb); `grid`
 // persistent CTAs (0: one per item) take the items in strides of the grid;
 // tmem_cols holds two accumulators.  mode 0:

@@ -49,9 +49,13 @@ void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st)
 // ---- masked DCT dictionary (dct.cu); idx: N strictly increasing sample indices ----
 bool dct_size_ok(int64_t D);                      // D a power of two, 16 <= D <= 2^22
 size_t dct_ws_bytes(int64_t D, int ncols);
+// prepared: the mask and twiddle tables are already in ws (dct_prepare with
+// the same D, idx, ncols and ws)
+void dct_prepare(int64_t D, const int32_t* idx, int64_t N, int ncols, char* ws, int* err,
+                 cudaStream_t st);
 int dct_apply(int64_t D, const int32_t* idx, int64_t N, const float* X, int64_t ld, int ncols,
               float* Y, double beta, const double* alpha, const float* alpha32, double* dots,
-              char* ws, int* err, cudaStream_t st);
+              char* ws, int* err, cudaStream_t st, bool prepared = false);
 void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64_t ldz, int ncols,
                  float* W, int64_t ldw, char* ws, int* err, cudaStream_t st);
 void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,

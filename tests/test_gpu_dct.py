@@ -87,3 +87,21 @@ def test_dct_fit_fp32(cuda_lib, seed):
     sup = (a < 1e6) & (ra < 1e6)
     assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 3e-3
     assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)
+
+
+def test_dct_fit_residual_replacement(cuda_lib):
+    # true-residual replacement every 10 iterations (the IF node of the CG
+    # loop) with the masked DCT; sigma 0.1 (beta 100) keeps the FP32 true
+    # residual attainable
+    D, N = 2048, 512
+    p = datagen.dct_problem(D, N, int(0.04 * D), 0.1, seed=5)
+    op = api.DctOperator(torch.from_numpy(p.idx).cuda(), D)
+    y32 = p.y.astype(np.float32)
+    prm = api.params(vec_dtype=B.COFEM_F32, K=20, em_iters=10, cg_tol=1e-5, cg_max_iters=400,
+                     seed=5, resid_replace_every=10)
+    r = api.fit(op, torch.from_numpy(y32).cuda(), p.beta, prm)
+    torch.cuda.synchronize()
+    ra, rmu, rs, rst = sbl.cofem_dct(p.idx, D, y32.astype(np.float64), p.beta, 20, 10, 1e-5, 400,
+                                     seed=5, resid_replace_every=10)
+    assert rel_l2(r.mu.cpu().numpy(), rmu) <= 1e-4
+    assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)

@@ -181,6 +181,17 @@ typedef struct {
                                   fixed_cg_iters; 1 with mlp returns
                                   COFEM_ERR_UNSUPPORTED.  Other values:
                                   COFEM_ERR_INVALID_ARG. */
+  int32_t tasks;               /* T >= 1 (0 = 1): tasks sharing alpha, the
+                                  multi-task extension named in Sec. 5.
+                                  cofem_fit then reads y_dev as T vectors of
+                                  N (task t at y_dev + t N), solves for
+                                  B = [beta Phi^T y_1 .. beta Phi^T y_T |
+                                  p_1 .. p_K] (K + T <= 64 columns), writes
+                                  mu_dev as T x D (task t at mu_dev + t D)
+                                  and updates alpha_d = 1 / max(mean_t
+                                  mu_td^2 + s_d, den_floor).  Not with mlp
+                                  or cofem_fit_batched
+                                  (COFEM_ERR_UNSUPPORTED). */
   double cg_tol;               /* eps: stop when ||R||_F / ||B||_F < eps */
   double alpha_init;           /* initial alpha (Alg. 1: 1) when
                                   t_offset == 0; ignored otherwise */
@@ -228,7 +239,8 @@ cofem_status cofem_workspace_bytes(const cofem_op* op, const cofem_params* p,
 /* Algorithm 1 (CovarianceFreeEM): b = beta Phi^T y once, then em_iters times
  * { draw probes, solve A X = B by column-wise CG, s = (1/K) sum p_k . x_k,
  *   alpha = 1 / max(mu^2 + s, den_floor) }.
- * y_dev: N values of vec_dtype.  mu_dev, s_dev, alpha_dev: D doubles each
+ * y_dev: N values of vec_dtype (T x N with params.tasks = T > 1).  mu_dev:
+ * D doubles (T x D with T tasks); s_dev, alpha_dev: D doubles each
  * (alpha_dev is also the input alpha when t_offset > 0).  stats: optional.
  * Synchronous: returns after the work on `stream` has finished, with the
  * device error word checked. */

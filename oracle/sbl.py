@@ -293,9 +293,13 @@ def diag_estimate(P, Xp):
 
 
 def m_step(mu, s, den_floor=DEN_FLOOR):
-    """alpha = 1 / (mu*mu + s), denominator floored at den_floor.
+    """alpha = 1 / (mu*mu + s), denominator floored at den_floor.  mu may be
+    T x D (T tasks sharing alpha, the multi-task extension of Sec. 5): then
+    mu*mu is the mean over the tasks, alpha_d = T / sum_t (mu_td^2 + s_d).
     Returns (alpha, number of clamped coordinates)."""
-    den = mu * mu + s
+    mu = np.asarray(mu)
+    m2 = mu * mu if mu.ndim == 1 else np.mean(mu * mu, axis=0)
+    den = m2 + s
     clamps = int(np.sum(den < den_floor))
     return 1.0 / np.maximum(den, den_floor), clamps
 
@@ -323,22 +327,29 @@ def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
     probes: optional function t -> D x K probe block; default is the
     counter-based Rademacher generator of probe_hash.  stop_rule: see
     cg_solve.
+
+    Multi-task (the extension named in Sec. 5, T tasks sharing alpha): y of
+    shape T x N; B = [beta Phi^T y_1 .. beta Phi^T y_T | p_1 .. p_K], mu is
+    returned T x D and the M-step averages mu^2 over the tasks (m_step).
     """
     y = np.asarray(y, dtype=np.float64)
+    multi = y.ndim == 2
+    Y = y.T if multi else y[:, None]         # N x T
+    T = Y.shape[1]
     alpha = np.broadcast_to(np.asarray(alpha_init, dtype=np.float64), (D,)).copy()
-    b = beta * phit(y)                       # beta Phi^T y, fixed over t
+    b = beta * phit(Y)                       # beta Phi^T y_t, fixed over EM iterations
     stats = FitStats()
-    mu = np.zeros(D)
+    mu = np.zeros((T, D) if multi else D)
     s = np.zeros(D)
     for t in range(t_offset + 1, t_offset + em_iters + 1):
         # Simplified E-step.
         A = lambda X, al=alpha: apply_A(phi, phit, beta, al, X)
         P = probes(t) if probes is not None else probe_matrix(seed, t, K, D)
-        B = np.concatenate([b[:, None], P], axis=1)
+        B = np.concatenate([b, P], axis=1)
         res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters,
                        resid_replace_every, stop_rule)
-        mu = res.X[:, 0]
-        s = diag_estimate(P, res.X[:, 1:])
+        mu = res.X[:, :T].T if multi else res.X[:, 0]
+        s = diag_estimate(P, res.X[:, T:])
         # M-step.
         alpha, clamps = m_step(mu, s, den_floor)
         stats.cg_iters.append(res.iters)

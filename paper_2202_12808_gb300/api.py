@@ -116,15 +116,20 @@ def workspace(op, p, device=None):
 
 def fit(op, y, beta, p=None, ws=None, alpha=None, stream=None, **kw):
     """Algorithm 1 on the GPU.  y: CUDA tensor of the vector dtype
-    (float64 for vec_dtype=F64, float32 otherwise).  Returns FitResult."""
+    (float64 for vec_dtype=F64, float32 otherwise), N values, or T x N for
+    T tasks sharing alpha (p.tasks is then set to T and mu is T x D).
+    Returns FitResult."""
     if p is None:
         p = params(**kw)
     vec = torch.float64 if p.vec_dtype == B.COFEM_F64 else torch.float32
     y = y.to(device=_op_device(op), dtype=vec).contiguous()
+    T = y.shape[0] if y.dim() == 2 else 1
+    if y.dim() == 2:
+        p.tasks = T
     dev = y.device
     if ws is None:
         ws = workspace(op, p, dev)
-    mu = torch.empty(op.D, dtype=torch.float64, device=dev)
+    mu = torch.empty((T, op.D) if y.dim() == 2 else op.D, dtype=torch.float64, device=dev)
     s = torch.empty(op.D, dtype=torch.float64, device=dev)
     if alpha is None:
         alpha = torch.empty(op.D, dtype=torch.float64, device=dev)

@@ -34,7 +34,7 @@ class cofem_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("em_iters", ctypes.c_int32),
                 ("cg_max_iters", ctypes.c_int32), ("fixed_cg_iters", ctypes.c_int32),
                 ("resid_replace_every", ctypes.c_int32), ("vec_dtype", ctypes.c_int32),
-                ("stop_rule", ctypes.c_int32),
+                ("stop_rule", ctypes.c_int32), ("tasks", ctypes.c_int32),
                 ("cg_tol", ctypes.c_double), ("alpha_init", ctypes.c_double),
                 ("den_floor", ctypes.c_double), ("support_threshold", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int64),

@@ -265,15 +265,19 @@ static int64_t op_D(const cofem_op* op) {
 // --------------------------------------------------------------- layout
 
 struct FitLayout {
-  size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, alpha32, X, R, P, Q, b, st_iters,
+  size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, alpha32, X, R, P, Q, b, yblk, st_iters,
       st_relres, st_clamps, st_support, opws;
   size_t total;
   int64_t ld;
 };
 
+// Tasks sharing alpha (1 = the paper's single-task model).
+static int n_tasks(const cofem_params* p) { return p->tasks > 1 ? p->tasks : 1; }
+
 static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   FitLayout L;
-  const int ncols = p->K + 1;
+  const int T = n_tasks(p);
+  const int ncols = p->K + T;
   const int vb = vec_bytes(p->vec_dtype);
   L.ld = round_up(op_D(op), kLdAlign);
   const size_t blk = align256((size_t)ncols * L.ld * vb);
@@ -292,7 +296,9 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   L.R = o; o += blk;
   L.P = o; o += blk;
   L.Q = o; o += blk;
-  L.b = o; o += align256((size_t)L.ld * vb);
+  L.b = o; o += align256((size_t)T * L.ld * vb);
+  // multi-task: the T observation vectors at a 64-element pitch
+  L.yblk = o; o += T > 1 ? align256((size_t)T * round_up(op_N(op), kLdAlign) * vb) : 0;
   L.st_iters = o; o += align256(sizeof(int32_t) * ne);
   L.st_relres = o; o += align256(sizeof(double) * ne);
   L.st_clamps = o; o += align256(sizeof(int32_t) * ne);
@@ -307,7 +313,7 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
 
 static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (!op || !p) return COFEM_ERR_INVALID_ARG;
-  if (p->K < 1 || p->K + 1 > kMaxCols) return COFEM_ERR_INVALID_ARG;
+  if (p->K < 1 || p->tasks < 0 || p->K + n_tasks(p) > kMaxCols) return COFEM_ERR_INVALID_ARG;
   if (p->em_iters < 0 || p->cg_max_iters < 1 || p->fixed_cg_iters < 0) return COFEM_ERR_INVALID_ARG;
   if (p->resid_replace_every < 0) return COFEM_ERR_INVALID_ARG;
   if (p->vec_dtype != COFEM_F64 && p->vec_dtype != COFEM_F32) return COFEM_ERR_INVALID_ARG;
@@ -318,6 +324,7 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && op->kind == 2) return COFEM_ERR_UNSUPPORTED;
+  if (p->mlp && n_tasks(p) > 1) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 
@@ -374,7 +381,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   V* Q = (V*)(ws + L.Q);
   V* b = (V*)(ws + L.b);
   char* opws = ws + L.opws;
-  const int ncols = p->K + 1;
+  const int ncols = p->K + n_tasks(p);
   const int vec = p->vec_dtype;
 
   CgConf cf;
@@ -383,6 +390,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cf.ld = L.ld;
   cf.ncols = ncols;
   cf.K = p->K;
+  cf.T = n_tasks(p);
   cf.seed = p->seed;
   cf.tol = p->cg_tol;
   cf.max_iters = p->cg_max_iters;
@@ -582,13 +590,24 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
     launch_k(alpha32_kernel, dim3((unsigned)((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096)), dim3(256), 0, st, (const double*)alpha, D, (float*)(ws + L.alpha32));
     CKL();
   }
-  // b = beta Phi^T y  (once per fit: y and beta do not change)
-  cofem_status rc = op_adjoint(op, p->vec_dtype, y, N, 1, ws + L.b, L.ld, beta, ws + L.opws, st);
+  // b_t = beta Phi^T y_t  (once per fit: y and beta do not change); T > 1
+  // tasks are first copied to a 64-element pitch
+  const int T = n_tasks(p);
+  const void* ysrc = y;
+  int64_t ldy = N;
+  if (T > 1) {
+    ldy = round_up(N, kLdAlign);
+    CK(cudaMemcpy2DAsync(ws + L.yblk, (size_t)ldy * sizeof(V), y, (size_t)N * sizeof(V),
+                         (size_t)N * sizeof(V), (size_t)T, cudaMemcpyDeviceToDevice, st));
+    ysrc = ws + L.yblk;
+  }
+  cofem_status rc = op_adjoint(op, p->vec_dtype, ysrc, ldy, T, ws + L.b, L.ld, beta,
+                               ws + L.opws, st);
   if (rc != COFEM_OK) return rc;
   // the masked DCT's mask and twiddle tables, once per fit (the graph's
   // applications reuse them)
   if (op->kind == 2) {
-    dct_prepare(op->dct_D, op->dct_idx, op->dct_N, p->K + 1, ws + L.opws,
+    dct_prepare(op->dct_D, op->dct_idx, op->dct_N, p->K + T, ws + L.opws,
                 &((CgCtl*)(ws + L.ctl))->error, st);
     CKL();
   }
@@ -915,6 +934,7 @@ cofem_status cofem_diag_mstep(uint64_t seed, int64_t t, int32_t K, int64_t D, co
   cf.ld = ld;
   cf.K = K;
   cf.ncols = K + 1;
+  cf.T = 1;
   cf.seed = seed;
   cf.den_floor = den_floor;
   cf.support_threshold = support_threshold;

@@ -585,6 +585,7 @@ static cofem_status bcheck(int n, const cofem_problem* pr, const cofem_params* p
   if (p->resid_replace_every != 0) return COFEM_ERR_UNSUPPORTED;
   if (!(p->den_floor > 0.0) || p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
   if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
+  if (p->tasks > 1) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 

@@ -110,8 +110,7 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
     if (cf.stop_rule == 1) {
       // per-column rule: column j is frozen once ||r_j|| < tol ||b_j||; a
       // frozen column keeps rho_j = 0, so a_j = b_j = 0 from then on
-      const double bn2 = j == 0 ? ctl->b0norm2 : (double)cf.D;
-      live = r0 > 0.0 && !(sqrt(r1) < cf.tol * sqrt(bn2));
+      live = r0 > 0.0 && !(sqrt(r1) < cf.tol * sqrt(sc->bn2[j]));
       sc->b[j] = live ? r1 / r0 : 0.0;
       sc->rho[j] = live ? r1 : 0.0;
     } else {
@@ -157,7 +156,8 @@ __global__ void probe_fill_kernel(uint64_t key, int K, int64_t D, V* out, int64_
 }
 
 // ------------------------------------------------------------- CG start
-// X = 0, R = P = B = [b | p_1..p_K]; rho_j = ||B_j||^2 (= D for a probe).
+// X = 0, R = P = B = [b_1..b_T | p_1..p_K] (b_t = beta Phi^T y_t, T tasks);
+// rho_j = ||B_j||^2 (= D for a probe).
 template <typename V>
 __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                                const V* bvec, double* part) {
@@ -174,11 +174,11 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
        d += (int64_t)gridDim.x * blockDim.x) {
     V v = V(0);
     if (d < cf.D) {
-      if (j == 0) {
-        v = bvec[d];
+      if (j < cf.T) {
+        v = bvec[(int64_t)j * cf.ld + d];
         acc.add_prod(v, v);
       } else {
-        const int k = j - 1;
+        const int k = j - cf.T;
         const uint64_t h = probe_word(key, d, k >> 6);
         v = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
       }
@@ -188,23 +188,32 @@ __global__ void cg_init_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
     p[d] = v;
     if (cf.split_nt > 0) write_split(cf, j, d, v);
   }
-  if (j == 0) {
+  if (j < cf.T) {
     const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * kMaxCols + j] = s;
   }
   if (arrive_last(&ctl->counter[0])) {
+    // ||b_t||^2 per task (thread t, blocks in order); a probe has ||p||^2 = D
+    if (threadIdx.x < cf.ncols) {
+      const int jj = threadIdx.x;
+      double b2 = (double)cf.D;
+      if (jj < cf.T) {
+        b2 = 0.0;
+        for (int i = 0; i < (int)gridDim.x; ++i) b2 += part[(int64_t)i * kMaxCols + jj];
+      }
+      sc->rho[jj] = b2;
+      sc->bn2[jj] = b2;
+      // per-column rule: every column starts at ||r_j|| / ||b_j|| = 1, so
+      // the joint start test below covers it; a zero task column (b_t = 0)
+      // is solved by x = 0 and frozen at once
+      if (cf.stop_rule == 1 && !(b2 > 0.0)) sc->rho[jj] = 0.0;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       double b2 = 0.0;
-      for (int i = 0; i < (int)gridDim.x; ++i) b2 += part[i];
-      sc->rho[0] = b2;
-      for (int jj = 1; jj < cf.ncols; ++jj) sc->rho[jj] = (double)cf.D;
+      for (int t = 0; t < cf.T; ++t) b2 += sc->bn2[t];
       const double n2 = b2 + (double)cf.K * (double)cf.D;
       ctl->normB2 = n2;
-      ctl->b0norm2 = b2;
-      // per-column rule: every column starts at ||r_j|| / ||b_j|| = 1, so
-      // the joint start test below covers it; a zero column 0 (b = 0) is
-      // solved by x = 0 and frozen at once
-      if (cf.stop_rule == 1 && !(b2 > 0.0)) sc->rho[0] = 0.0;
       ctl->relres = n2 > 0.0 ? 1.0 : 0.0;
       if (cf.fallback_init) {
         ctl->extra_iters = ctl->iter;
@@ -433,9 +442,9 @@ __global__ void cg_true_resid_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* R,
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
     V bv;
-    if (j == 0) bv = bvec[d];
+    if (j < cf.T) bv = bvec[(int64_t)j * cf.ld + d];
     else {
-      const int k = j - 1;
+      const int k = j - cf.T;
       const uint64_t h = probe_word(key, d, k >> 6);
       bv = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
     }
@@ -506,18 +515,27 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
   int clamps = 0, support = 0, bad = 0;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
-    const double m = (double)X[d];
+    // mu_t = column t of X; the M-step uses the mean of mu_t^2 over the
+    // tasks (one task: mu^2)
+    double m = (double)X[d], m2 = m * m;
+    for (int t = 1; t < cf.T; ++t) {
+      const double mt = (double)X[(int64_t)t * cf.ld + d];
+      m2 += mt * mt;
+      mu[(int64_t)t * cf.D + d] = mt;
+      if (!isfinite(mt)) bad = 1;
+    }
+    if (cf.T > 1) m2 /= (double)cf.T;
     typename AccOf<V>::T acc;          // sum_k p_kd x_kd (compensated for FP32 X)
     for (int w = 0; w * 64 < K; ++w) {
       const uint64_t h = probe_word(key, d, w);
       const int kend = min(K, (w + 1) * 64);
       for (int k = w * 64; k < kend; ++k) {
-        const V xv = X[(int64_t)(k + 1) * cf.ld + d];
+        const V xv = X[(int64_t)(k + cf.T) * cf.ld + d];
         acc.add(((h >> (k & 63)) & 1ull) ? -xv : xv);
       }
     }
     const double sd = acc.value() / (double)K;
-    const double den = m * m + sd;
+    const double den = m2 + sd;
     if (den < cf.den_floor) ++clamps;
     const double al = 1.0 / fmax(den, cf.den_floor);
     if (!isfinite(m) || !isfinite(sd)) bad = 1;

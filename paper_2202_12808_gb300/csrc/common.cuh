@@ -29,7 +29,6 @@ struct CgCtl {
   int fallbacks;       // learned path: fallbacks to plain CG so far
   int run;             // the direction update may run (b_j of this iteration are set)
   double normB2;       // ||B||_F^2
-  double b0norm2;      // ||b||^2 of column 0 (a probe column has ||p||^2 = D)
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
 };
@@ -42,6 +41,7 @@ struct CgScalars {
   double a[kMaxCols];        // step sizes
   double b[kMaxCols];        // direction updates
   double rr_new[kMaxCols];   // preconditioned CG: r_j^T r_j (rho holds r_j^T z_j)
+  double bn2[kMaxCols];      // ||B_j||^2 of the solve's right-hand sides
 };
 
 // Static problem description passed by value to the CG kernels.
@@ -71,6 +71,7 @@ struct CgConf {
   int fallback_init;                 // this init restarts plain CG after a fallback
   float* alpha32;                    // FP32 copy of alpha kept by the M-step, or null
   int stop_rule;                     // 1: per-column stop (frozen columns have rho_j = 0)
+  int T;                             // tasks: columns 0..T-1 are beta Phi^T y_t, then K probes
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

@@ -107,6 +107,28 @@ def dct_problem(D, N, n_nonzero, sigma, seed):
     return DctProblem(idx, z, y, 1.0 / sigma ** 2 if sigma > 0 else float("inf"))
 
 
+@dataclass
+class MultiTaskProblem:
+    Phi: np.ndarray        # N x D float32, iid N(0, 1/N)
+    Z: np.ndarray          # T x D ground truth (float64), one support shared by the tasks
+    Y: np.ndarray          # T x N observations (float64)
+    beta: float
+
+
+def multitask_problem(N, D, T, n_nonzero, sigma, seed):
+    """T tasks observed through one dense Phi with a common support (the
+    multi-task model of the extension named in Sec. 5): n_nonzero shared
+    positions, independent N(0, 1) amplitudes per task, y_t = Phi z_t +
+    N(0, sigma^2) noise."""
+    rng = np.random.default_rng(seed)
+    Phi = (rng.standard_normal((N, D)) / np.sqrt(N)).astype(np.float32)
+    Z = np.zeros((T, D))
+    idx = rng.choice(D, size=n_nonzero, replace=False)
+    Z[:, idx] = rng.standard_normal((T, n_nonzero))
+    Y = Z @ Phi.astype(np.float64).T + sigma * rng.standard_normal((T, N))
+    return MultiTaskProblem(Phi, Z, Y, 1.0 / sigma ** 2 if sigma > 0 else float("inf"))
+
+
 def batched_sizes(n_problems, n_min, n_max, ratio, seed):
     """(N_i, D_i, seed_i) for each problem; N_i uniform on [n_min, n_max]."""
     rng = np.random.default_rng(seed)

@@ -43,8 +43,8 @@ def test_params_default_matches_header(built):
     assert (p.K, p.em_iters, p.cg_max_iters, p.fixed_cg_iters, p.resid_replace_every) == (20, 50, 400, 0, 0)
     assert p.vec_dtype == B.COFEM_F32
     assert (p.cg_tol, p.alpha_init, p.den_floor, p.support_threshold) == (1e-6, 1.0, 1e-12, 1e6)
-    assert p.stop_rule == 0
-    # 7 int32 fields padded to 8-byte alignment, 4 doubles, seed, t_offset, mlp
+    assert p.stop_rule == 0 and p.tasks == 0
+    # 8 int32 fields, 4 doubles, seed, t_offset, mlp
     assert ctypes.sizeof(B.cofem_params) == 8 * 4 + 4 * 8 + 8 + 8 + 8
 
 
@@ -54,6 +54,21 @@ def test_stop_rule_validation(built):
         assert B.cofem_workspace_bytes(h, B.cofem_params_default(stop_rule=1)) > 0
         for bad, code in ((dict(stop_rule=2), 1), (dict(stop_rule=-1), 1),
                           (dict(stop_rule=1, mlp=256), 6)):
+            with pytest.raises(B.CofemError) as e:
+                B.cofem_workspace_bytes(h, B.cofem_params_default(**bad))
+            assert e.value.code == code, bad
+    finally:
+        B.cofem_op_destroy(h)
+
+
+def test_tasks_validation(built):
+    h = B.cofem_op_dense(4, 10, B.COFEM_F32, 256, 64)
+    try:
+        one = B.cofem_workspace_bytes(h, B.cofem_params_default(K=8))
+        three = B.cofem_workspace_bytes(h, B.cofem_params_default(K=8, tasks=3))
+        assert three > one                       # two more columns per vector block
+        for bad, code in ((dict(K=62, tasks=3), 1), (dict(tasks=-1), 1),
+                          (dict(tasks=2, mlp=256), 6)):
             with pytest.raises(B.CofemError) as e:
                 B.cofem_workspace_bytes(h, B.cofem_params_default(**bad))
             assert e.value.code == code, bad

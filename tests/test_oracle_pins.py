@@ -501,3 +501,44 @@ def test_dct_problem_generator():
     assert np.count_nonzero(pr.z) == 40
     phi, _, _ = sbl.dct_dictionary(pr.idx, 1024)
     np.testing.assert_allclose(pr.y, phi(pr.z), atol=1e-12)
+
+
+# ------------------------------------------------ multi-task extension (Sec. 5)
+
+def test_multitask_identical_tasks_reduce_to_single_task():
+    """T copies of one observation vector: every task's mean equals the
+    single-task mean and the shared alpha equals the single-task alpha."""
+    from paper_2202_12808_gb300 import datagen
+    # overdetermined and well conditioned, so that the BLAS rounding of the
+    # wider products (T + K columns instead of 1 + K) stays at 1e-13
+    pr = datagen.dense_problem(200, 64, 8, 0.05, seed=2)
+    Phi = pr.Phi.astype(np.float64)
+    kw = dict(fixed_cg_iters=64, seed=3)
+    a1, m1, s1, _ = sbl.cofem_dense(Phi, pr.y, pr.beta, 12, 2, 1e-8, 200, **kw)
+    Y = np.stack([pr.y, pr.y, pr.y])
+    a3, m3, s3, _ = sbl.cofem_dense(Phi, Y, pr.beta, 12, 2, 1e-8, 200, **kw)
+    assert m3.shape == (3, 64)
+    for t in range(3):
+        np.testing.assert_allclose(m3[t], m1, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(a3, a1, rtol=1e-10)
+    np.testing.assert_allclose(s3, s1, rtol=1e-10, atol=1e-13)
+
+
+def test_multitask_matches_exact_em_step():
+    """One EM step of multi-task CoFEM with converged CG and many probes
+    against the exact multi-task EM step written from its definition:
+    Sigma = (beta Phi^T Phi + diag alpha)^-1, mu_t = beta Sigma Phi^T y_t,
+    alpha_d = 1 / (mean_t mu_td^2 + Sigma_dd)."""
+    from paper_2202_12808_gb300 import datagen
+    pr = datagen.multitask_problem(48, 96, 3, 6, 0.1, seed=4)
+    Phi = pr.Phi.astype(np.float64)
+    alpha0 = np.random.default_rng(0).uniform(0.5, 5.0, 96)
+    A = pr.beta * Phi.T @ Phi + np.diag(alpha0)
+    Sigma = scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), np.eye(96))
+    mu_ex = pr.beta * (Sigma @ (Phi.T @ pr.Y.T)).T            # T x D
+    alpha_ex = 1.0 / (np.mean(mu_ex ** 2, axis=0) + np.diag(Sigma))
+    a, mu, s, _ = sbl.cofem_dense(Phi, pr.Y, pr.beta, 16000, 1, 1e-12, 500,
+                                  alpha_init=alpha0, seed=5)
+    np.testing.assert_allclose(mu, mu_ex, rtol=1e-7, atol=1e-10)
+    assert np.linalg.norm(s - np.diag(Sigma)) <= 2e-2 * np.linalg.norm(np.diag(Sigma))
+    assert np.linalg.norm(a - alpha_ex) <= 2e-2 * np.linalg.norm(alpha_ex)

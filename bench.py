@@ -50,7 +50,8 @@ def parse():
                     help="skip the operator pipeline autotuner (library defaults)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched-512-n128-2048", "conv-l1m-c8-t64",
-                             "dense-fp64-n256-d1024", "learned-dense-n256-d1024", "dct-d262144"],
+                             "dense-fp64-n256-d1024", "learned-dense-n256-d1024", "dct-d262144",
+                             "multitask-n4096-d32768-t4"],
                     help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -411,6 +412,40 @@ def run_dct(args):
              "clocks": clk.summary()})
 
 
+def run_multitask(args):
+    """Four tasks sharing alpha through the headline's dictionary (N = 4096,
+    D = 32768, BF16 Phi on the tensor cores, packed): 4 mean columns + 28
+    probes = 32 columns, about the headline's 33, so one solve serves four
+    observation vectors."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    N, D, T, K = 4096, 32768, 4, 28
+    pr = datagen.multitask_problem(N, D, T, 655, 0.01, args.seed)
+    op = api.DenseOperator(torch.from_numpy(pr.Phi).to(torch.bfloat16).cuda())
+    nb = B.cofem_dense_packed_bytes(N, D)
+    pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    B.cofem_op_dense_attach_packed(op.handle, pk.data_ptr(), nb)
+    Y = torch.from_numpy(pr.Y.astype(np.float32)).cuda()
+    kw = dict(vec_dtype=B.COFEM_F32, K=K, cg_tol=1e-5, cg_max_iters=400, resid_replace_every=50,
+              seed=args.seed)
+    rw = api.fit(op, Y, pr.beta, api.params(em_iters=args.warmup, **kw))
+    a0 = rw.alpha.clone()
+    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+    with ClockSampler(0) as clk:
+        res, sec = _timed(lambda: api.fit(op, Y, pr.beta, pt, alpha=a0.clone()))
+    mu = res.mu.cpu().numpy()
+    nrmse = float(np.linalg.norm(mu - pr.Z) / np.linalg.norm(pr.Z))
+    _common(args, "task EM iters/s (4 tasks sharing alpha, dense N=4096 D=32768, K=28, tol 1e-5)",
+            "task EM iters/s", T * args.steps / sec, sec, "f32 vectors, bf16 Phi",
+            {"workload": "multitask-n4096-d32768-t4", "N": N, "D": D, "tasks": T, "K": K,
+             "columns": T + K, "cg_tol": 1e-5, "resid_replace_every": 50,
+             "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
+             "l2": "inputs larger than L2 (Phi 256 MB)"},
+            {"cg_iters_per_em": res.stats["cg_iters"], "nrmse_mu_vs_truth": nrmse,
+             "em_iters_per_s": args.steps / sec, "clocks": clk.summary()})
+
+
 def run_fp64(args):
     """FP64 vectors and dictionary, N=256, D=1024, K=20, tol 1e-6."""
     import torch
@@ -539,6 +574,8 @@ def main():
         return run_learned(args)
     if args.workload == "dct-d262144":
         return run_dct(args)
+    if args.workload == "multitask-n4096-d32768-t4":
+        return run_multitask(args)
     import torch
     import torch.distributed as dist
     from paper_2202_12808_gb300 import api

@@ -396,6 +396,16 @@ def run_dct(args):
     dom = int(np.argmax(kus[1:])) + 1
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     ach = pbytes[dom] / (kus[dom] * 1e-6) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "dct_pass_d262144.md")
+    if os.path.exists(prof):
+        import hashlib
+        src = os.path.join(ROOT, "paper_2202_12808_gb300", "csrc", "dct.cu")
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        meta = dict(l.split(":", 1) for l in open(prof) if ":" in l and not l.startswith(("|", " ", "#")))
+        key = "traffic_" + names[dom].replace(" ", "_")
+        if meta.get("source_sha1", "").strip() == sha and key in meta:
+            traffic = int(meta[key].strip())
     _common(args, "EM iters/s (masked DCT dictionary D=2^18, N=D/4, K=20)", "EM iters/s",
             args.steps / sec, sec, "f32",
             {"workload": "dct-d262144", "D": D, "N": c["N"], "n_nonzero": c["n_nonzero"],
@@ -404,7 +414,8 @@ def run_dct(args):
              "l2": "working set larger than L2 (X, R, P, Q 22 MB each + FFT buffers 66 MB)"},
             {"cg_iters_per_em": res.stats["cg_iters"], "nrmse_mu_vs_truth": nrmse,
              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                          "frac": ach / peak, "traffic": None, "kernel": "dct_pass_kernel (%s)" % names[dom],
+                          "frac": ach / peak, "traffic": traffic,
+                          "kernel": "dct_pass_kernel (%s)" % names[dom],
                           "launch_us": kus[dom], "algorithmic_bytes": pbytes[dom],
                           "passes_us": dict(zip(names, kus)),
                           "apply_us": sum(kus),

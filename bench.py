@@ -390,9 +390,10 @@ def run_dct(args):
                                  pr.beta, Y.data_ptr(), wsa.data_ptr(), nb) for _ in range(6)][1:]
     names = ["mask", "idct pass 1", "idct pass 2", "dct pass 1", "dct pass 2"]
     kus = [float(np.mean([m[i] for m in ms])) * 1e3 for i in range(len(names))]
-    # algorithmic bytes per pass: real 4 B and complex 8 B per element and column
-    pbytes = [4 * c["N"] + 4 * D, 12 * D * nc, 12 * D * nc + 4 * D, 12 * D * nc,
-              16 * D * nc + 4 * D]
+    # algorithmic bytes per pass and column: real values 4 B per element, the
+    # half-length complex intermediate 8 B per two elements
+    pbytes = [4 * c["N"] + 4 * D, 8 * D * nc, 8 * D * nc + 4 * D, 8 * D * nc,
+              12 * D * nc + 4 * D]
     dom = int(np.argmax(kus[1:])) + 1
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)
     ach = pbytes[dom] / (kus[dom] * 1e-6) / 1e9

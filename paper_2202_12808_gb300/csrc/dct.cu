@@ -8,21 +8,29 @@
 // (Eq. (mat-eq)), is an inverse DCT, a mask, and a forward DCT per column:
 // tau_D = O(D log D) (Sec. 3.2).
 //
-// DCTs by a length-D complex FFT (Makhoul's mapping, IEEE TASSP 1980):
-//   DCT-II:  v_n = x_{2n} (n < D/2), v_n = x_{2D-1-2n} (n >= D/2); V = FFT(v);
+// DCTs by a complex FFT of half the length, M = D/2 (Makhoul's mapping,
+// IEEE TASSP 1980, with the real sequence packed two to a complex value):
+//   DCT-II:  v_m = x_{2m} (m < M), v_m = x_{2D-1-2m} (m >= M);
+//            z_n = v_{2n} + i v_{2n+1}; Z = FFT_M(z);
+//            E_k = (Z_k + conj Z_{M-k}) / 2, O_k = (Z_k - conj Z_{M-k}) / 2i,
+//            V_k = E_k + e^{-2 pi i k / D} O_k, V_{k+M} = E_k - e^{-2 pi i k / D} O_k;
 //            X_k = s_k Re(e^{-i pi k / 2D} V_k),  s_0 = sqrt(1/D), s_k = sqrt(2/D)
 //   DCT-III: V_k = e^{i pi k / 2D} (X_k / s_k - i X_{D-k} / s_{D-k}) (X_D := 0);
-//            v = IFFT(V); x_{2m} = v_m, x_{2m+1} = v_{D-1-m}
-// and the FFT of length D = D1 D2 by the four-step decomposition: pass 1 runs
-// D2 transforms of length D1 over the stride-D2 subsequences and multiplies by
-// e^{-+2 pi i n2 k1 / D}, pass 2 runs D1 transforms of length D2 over the
+//            Z'_k = (V_k + V_{k+M}) + i e^{2 pi i k / D} (V_k - V_{k+M});
+//            z = IFFT_M(Z') / D; v_{2n} = Re z_n, v_{2n+1} = Im z_n;
+//            x_{2m} = v_m, x_{2m+1} = v_{D-1-m}
+// and the FFT of length M = M1 M2 by the four-step decomposition: pass 1 runs
+// M2 transforms of length M1 over the stride-M2 subsequences and multiplies by
+// e^{-+2 pi i n2 k1 / M}, pass 2 runs M1 transforms of length M2 over the
 // rows; the DCT pre- and post-processing is fused into the loads of pass 1 and
-// the stores of pass 2.  Each block holds G transforms (G Lf = kFftElems
-// complex values) in shared memory and runs a Stockham (self-sorting)
-// mixed-radix FFT on them: radix-8 stages, then one radix-4 or radix-2
-// stage, each thread reading its butterflies' inputs into registers, all
-// threads synchronising, then writing the outputs (natural order in and
-// out, a per-block twiddle table).
+// the stores of pass 2.  The forward DCT's post-processing pairs output k
+// with M - k, which pass 2 finds in its own block: a block holds transforms
+// k1 and M1 - k1 together (0 and M1/2 are their own partners).  Each block
+// holds G transforms (G Lf = kFftElems complex values) in shared memory and
+// runs a Stockham (self-sorting) mixed-radix FFT on them: radix-8 stages,
+// then one radix-4 or radix-2 stage, each thread reading its butterflies'
+// inputs into registers, all threads synchronising, then writing the outputs
+// (natural order in and out, a per-block twiddle table).
 #include "kernels.cuh"
 
 namespace cofem {
@@ -43,10 +51,10 @@ enum DctMode { kIdct1 = 0, kIdct2 = 1, kDct1 = 2, kDct2 = 3 };
 
 struct DctArgs {
   int64_t D;
-  int lg1, lg2;            // D1 = 2^lg1 (pass 1 length), D2 = 2^lg2 (pass 2 length)
+  int lg1, lg2;            // M = D/2 = M1 M2, M1 = 2^lg1 (pass 1 length), M2 = 2^lg2 (pass 2)
   const float* xin;        // real input: X (IDCT1) or T (DCT1)
   int64_t ldx;
-  float2* cbuf;            // complex intermediate, ncols x D, pitch D
+  float2* cbuf;            // complex intermediate, ncols x M, pitch M
   float* tout;             // IDCT2: real output (time domain), pitch ldt
   int64_t ldt;
   const float* mask;       // IDCT2: 0/1 per sample, or null (keep all)
@@ -59,7 +67,8 @@ struct DctArgs {
   int64_t ldxd;
   double* dots;            // DCT2: per-block partials of x_j^T y_j, [block][kMaxCols]
   const float2* tabM;      // e^{i pi n / 2D}, n < D (DCT pre-/post-twiddles)
-  const float2* tabW;      // e^{-2 pi i q / D}, q < D2 (low part of the four-step twiddle)
+  const float2* tabW;      // e^{-2 pi i q / M}, q < M2 (low part of the four-step twiddle)
+  const float2* tabR;      // e^{-2 pi i k / D}, k < M (even/odd recombination)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -185,25 +194,35 @@ dct_pass_kernel(DctArgs a) {
   constexpr int kPer = kFftElems / kFftThreads;   // elements per thread
   const int j = blockIdx.y;
   const int D = (int)a.D;                          // <= 2^22
+  const int M = D >> 1;
+  const int M1 = 1 << a.lg1;
   const int lg = pass1 ? a.lg1 : a.lg2;           // length of this pass's transforms
   const int Lf = 1 << lg;
-  const int ntr = pass1 ? (1 << a.lg2) : (1 << a.lg1);   // transforms in the pass
+  const int ntr = pass1 ? (1 << a.lg2) : M1;      // transforms in the pass
   const int G = min(kFftElems >> lg, ntr);
   const int lgG = __ffs(G) - 1;                    // G is a power of two
   const int nel = G << lg;                         // elements of this block
-  const int t0 = blockIdx.x * G;                   // first transform of this block
   const float sgn = inverse ? 1.f : -1.f;
   for (int i = threadIdx.x; i < (Lf >> 1); i += blockDim.x)
     tw[i] = cis_pi(sgn * 2.f * (float)i / (float)Lf);
   const float sD = sqrtf(1.f / (float)D), sK = sqrtf(2.f / (float)D);
   const float rsD = 1.f / sD, rsK = 1.f / sK;
-  float2* cb = a.cbuf + (int64_t)j * D;
+  float2* cb = a.cbuf + (int64_t)j * M;
+  // pass 2: local transform tt is k1 = pi (tt < G/2) or its partner M1 - pi
+  // (tt >= G/2), pi = blockIdx.x G/2 + tt mod G/2; pair 0 holds k1 = 0 and
+  // k1 = M1/2, each its own partner
+  const int hG = G >> 1;
+  auto k1_of = [&](int tt) {
+    const int pi = blockIdx.x * hG + (tt & (hG - 1));
+    return tt < hG ? pi : (pi == 0 ? (M1 >> 1) : M1 - pi);
+  };
+  const int t0 = blockIdx.x * G;                   // pass 1: first transform n2
 
   // ---- load: all of a thread's global loads first, then the shared stores
   float2 v[kPer];
   if (pass1) {
-    // element n1 of transform n2 sits at n = D2 n1 + n2; consecutive threads
-    // take consecutive n2 (contiguous addresses)
+    // element n1 of transform n2 is z_n, n = M2 n1 + n2; consecutive threads
+    // take consecutive n2
     const float* xj = a.xin + (int64_t)j * a.ldx;
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
@@ -212,11 +231,22 @@ dct_pass_kernel(DctArgs a) {
       if (i < nel) {
         const int n = ((i >> lgG) << a.lg2) + t0 + (i & (G - 1));
         if (MODE == kIdct1) {
-          const float xk = xj[n] * (n == 0 ? rsD : rsK);
-          const float xr = n == 0 ? 0.f : xj[D - n] * rsK;
-          v[q] = cmul(a.tabM[n], make_float2(xk, -xr));      // e^{i pi n / 2D}
+          // V_n and V_{n+M} from X_n, X_{D-n}, X_{n+M}, X_{M-n}
+          const float x0 = xj[n] * (n == 0 ? rsD : rsK);
+          const float x0r = n == 0 ? 0.f : xj[D - n] * rsK;
+          const float x1 = xj[n + M] * rsK;
+          const float x1r = xj[M - n] * rsK;
+          const float2 va = cmul(a.tabM[n], make_float2(x0, -x0r));
+          const float2 vb = cmul(a.tabM[n + M], make_float2(x1, -x1r));
+          const float2 rr = a.tabR[n];                // e^{-2 pi i n / D}; conjugated
+          const float2 dv = csub(va, vb);
+          const float2 t = cmul(make_float2(rr.x, -rr.y), dv);
+          v[q] = cadd(cadd(va, vb), make_float2(-t.y, t.x));   // + i e^{2 pi i n/D} (V_n - V_{n+M})
         } else {
-          v[q] = make_float2(xj[n < D / 2 ? 2 * n : 2 * D - 1 - 2 * n], 0.f);
+          // z_n = v_{2n} + i v_{2n+1}, v_m = T[2m] (m < M), T[2D-1-2m] (m >= M)
+          const int m0 = 2 * n, m1 = 2 * n + 1;
+          v[q] = make_float2(xj[m0 < M ? 2 * m0 : 2 * D - 1 - 2 * m0],
+                             xj[m1 < M ? 2 * m1 : 2 * D - 1 - 2 * m1]);
         }
       }
     }
@@ -226,11 +256,11 @@ dct_pass_kernel(DctArgs a) {
       if (i < nel) s[pad(((i & (G - 1)) << lg) + (i >> lgG))] = v[q];
     }
   } else {
-    // transform k1 is the contiguous row cb[D2 k1 ...]
+    // transform k1 is the contiguous row cb[M2 k1 ...]
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int i = threadIdx.x + q * kFftThreads;
-      if (i < nel) v[q] = cb[((t0 + (i >> lg)) << a.lg2) + (i & (Lf - 1))];
+      if (i < nel) v[q] = cb[(k1_of(i >> lg) << a.lg2) + (i & (Lf - 1))];
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
@@ -243,16 +273,16 @@ dct_pass_kernel(DctArgs a) {
 
   // ---- store
   if (pass1) {
-    // twiddle e^{sgn 2 pi i n2 k1 / D} = e^{sgn 2 pi i qh / D1} e^{sgn 2 pi i ql / D}
-    // with n2 k1 = qh D2 + ql (the first factor is this pass's own table),
-    // then cb[D2 k1 + n2]
+    // twiddle e^{sgn 2 pi i n2 k1 / M} = e^{sgn 2 pi i qh / M1} e^{sgn 2 pi i ql / M}
+    // with n2 k1 = qh M2 + ql (the first factor is this pass's own table),
+    // then cb[M2 k1 + n2]
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int i = threadIdx.x + q * kFftThreads;
       if (i < nel) {
         const int tt = i & (G - 1), f = i >> lgG;
         const int n2 = t0 + tt;
-        const int r = n2 * f;                      // < D
+        const int r = n2 * f;                      // < M
         const float2 lo = a.tabW[r & ((1 << a.lg2) - 1)];
         const float2 w = cmul(twiddle(tw, r >> a.lg2, Lf >> 1),
                               inverse ? make_float2(lo.x, -lo.y) : lo);
@@ -262,42 +292,54 @@ dct_pass_kernel(DctArgs a) {
   } else {
     AccF dot;
     const bool diag = MODE == kDct2 && (a.alpha32 != nullptr || a.alpha != nullptr);
-    // frequency k2 of transform k1 is output k = k1 + D1 k2; consecutive
-    // threads take consecutive k1
-    float xv[kPer], al[kPer];
-    if (MODE == kDct2 && diag) {
-#pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int i = threadIdx.x + q * kFftThreads;
-        xv[q] = al[q] = 0.f;
-        if (i < nel) {
-          const int k = t0 + (i & (G - 1)) + ((i >> lgG) << a.lg1);
-          xv[q] = a.xdiag[(int64_t)j * a.ldxd + k];
-          al[q] = a.alpha32 ? a.alpha32[k] : (float)a.alpha[k];
-        }
-      }
-    }
-#pragma unroll
+    // frequency k2 of transform k1 is k = k1 + M1 k2 < M; consecutive
+    // threads take consecutive local transforms
+    const int M2 = 1 << a.lg2;
+#pragma unroll 4
     for (int q = 0; q < kPer; ++q) {
       const int i = threadIdx.x + q * kFftThreads;
       if (i < nel) {
         const int tt = i & (G - 1), f = i >> lgG;
-        const int k = t0 + tt + (f << a.lg1);
-        const float2 val = s[pad((tt << lg) + f)];
+        const int k1 = k1_of(tt);
+        const int k = k1 + (f << a.lg1);
+        const float2 zk = s[pad((tt << lg) + f)];
         if (MODE == kIdct2) {
-          const float re = val.x * (1.f / (float)D);
-          const int y = k < D / 2 ? 2 * k : 2 * (D - 1 - k) + 1;
-          const float m = a.mask ? a.mask[y] : 1.f;
-          a.tout[(int64_t)j * a.ldt + y] = m * re;
+          // v_{2k} = Re z_k / D, v_{2k+1} = Im z_k / D, then x_{2m} = v_m,
+          // x_{2m+1} = v_{D-1-m}
+          const float invD = 1.f / (float)D;
+          const int m0 = 2 * k, m1 = 2 * k + 1;
+          const int y0 = m0 < M ? 2 * m0 : 2 * (D - 1 - m0) + 1;
+          const int y1 = m1 < M ? 2 * m1 : 2 * (D - 1 - m1) + 1;
+          const float g0 = a.mask ? a.mask[y0] : 1.f, g1 = a.mask ? a.mask[y1] : 1.f;
+          a.tout[(int64_t)j * a.ldt + y0] = g0 * zk.x * invD;
+          a.tout[(int64_t)j * a.ldt + y1] = g1 * zk.y * invD;
         } else {
-          const float2 w = a.tabM[k];              // e^{+i pi k / 2D}; conjugated here
-          const float o = (k == 0 ? sD : sK) * (w.x * val.x + w.y * val.y);
-          float out = (float)a.beta * o;
+          // partner M - k: (0, M2 - k2) for k1 = 0, else (M1 - k1, M2 - 1 - k2),
+          // in local transform tt (pair 0) or tt ^ G/2
+          const int pt = (blockIdx.x == 0 && (tt & (hG - 1)) == 0) ? tt : (tt ^ hG);
+          const int pf = k1 == 0 ? ((M2 - f) & (M2 - 1)) : (M2 - 1 - f);
+          const float2 zp0 = s[pad((pt << lg) + pf)];
+          const float2 zp = make_float2(zp0.x, -zp0.y);               // conj Z_{M-k}
+          const float2 e = make_float2(0.5f * (zk.x + zp.x), 0.5f * (zk.y + zp.y));
+          const float2 dd = make_float2(0.5f * (zk.x - zp.x), 0.5f * (zk.y - zp.y));
+          const float2 o = cmul(a.tabR[k], make_float2(dd.y, -dd.x));  // e^{-2 pi i k/D} (Z - conj Z')/2i
+          const float2 va = cadd(e, o), vb = csub(e, o);               // V_k, V_{k+M}
+          const float2 wa = a.tabM[k], wb = a.tabM[k + M];             // conjugated below
+          const float oa = (k == 0 ? sD : sK) * (wa.x * va.x + wa.y * va.y);
+          const float ob = sK * (wb.x * vb.x + wb.y * vb.y);
+          float outa = (float)a.beta * oa, outb = (float)a.beta * ob;
           if (diag) {
-            out = fmaf(al[q], xv[q], out);
-            dot.add_prod(xv[q], out);
+            const float xa = a.xdiag[(int64_t)j * a.ldxd + k];
+            const float xb = a.xdiag[(int64_t)j * a.ldxd + k + M];
+            const float ala = a.alpha32 ? a.alpha32[k] : (float)a.alpha[k];
+            const float alb = a.alpha32 ? a.alpha32[k + M] : (float)a.alpha[k + M];
+            outa = fmaf(ala, xa, outa);
+            outb = fmaf(alb, xb, outb);
+            dot.add_prod(xa, outa);
+            dot.add_prod(xb, outb);
           }
-          a.yout[(int64_t)j * a.ldy + k] = out;
+          a.yout[(int64_t)j * a.ldy + k] = outa;
+          a.yout[(int64_t)j * a.ldy + k + M] = outb;
         }
       }
     }
@@ -308,14 +350,17 @@ dct_pass_kernel(DctArgs a) {
   }
 }
 
-// tabM[n] = e^{i pi n / 2D} (n < D), tabW[q] = e^{-2 pi i q / D} (q < D2)
-__global__ void dct_twiddle_kernel(int64_t D, int D2, float2* tabM, float2* tabW) {
+// tabM[n] = e^{i pi n / 2D} (n < D), tabW[q] = e^{-2 pi i q / M} (q < M2),
+// tabR[k] = e^{-2 pi i k / D} (k < M)
+__global__ void dct_twiddle_kernel(int64_t D, int M2, float2* tabM, float2* tabW, float2* tabR) {
   pdl_wait();
   pdl_trigger();
+  const int64_t M = D / 2;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < D;
        n += (int64_t)gridDim.x * blockDim.x) {
     tabM[n] = cis_pi((float)n / (float)(2 * D));
-    if (n < D2) tabW[n] = cis_pi(-2.f * (float)n / (float)D);
+    if (n < M2) tabW[n] = cis_pi(-2.f * (float)n / (float)M);
+    if (n < M) tabR[n] = cis_pi(-2.f * (float)n / (float)D);
   }
 }
 
@@ -385,11 +430,13 @@ bool dct_size_ok(int64_t D) {
   return D >= 16 && ((int64_t)1 << p) == D && p <= 2 * kFftMaxLg;
 }
 
-// workspace: complex buffer (ncols x D), real T (ncols x D), mask (D),
-// twiddle tables tabM (D complex) and tabW (D2 complex)
+// workspace: complex buffer (ncols x D/2), real T (ncols x D), mask (D),
+// twiddle tables tabM (D complex), tabW (D/2) and tabR (D/2)
+static size_t cbuf_bytes(int64_t D, int ncols) { return align256((size_t)ncols * (D / 2) * sizeof(float2)); }
+static size_t tout_bytes(int64_t D, int ncols) { return align256((size_t)ncols * D * sizeof(float)); }
 size_t dct_ws_bytes(int64_t D, int ncols) {
-  return align256((size_t)ncols * D * sizeof(float2)) + align256((size_t)ncols * D * sizeof(float)) +
-         align256((size_t)D * sizeof(float)) + 2 * align256((size_t)D * sizeof(float2));
+  return cbuf_bytes(D, ncols) + tout_bytes(D, ncols) + align256((size_t)D * sizeof(float)) +
+         align256((size_t)D * sizeof(float2)) + 2 * align256((size_t)(D / 2) * sizeof(float2));
 }
 
 // Carves the workspace; fills the twiddle tables (one small launch) unless
@@ -397,26 +444,27 @@ size_t dct_ws_bytes(int64_t D, int ncols) {
 static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st, bool tables = true) {
   DctArgs a = {};
   a.D = D;
-  const int p = ilog2(D);
+  const int p = ilog2(D) - 1;                      // M = D/2 = 2^p
   a.lg1 = p / 2;
   a.lg2 = p - a.lg1;
   a.cbuf = (float2*)ws;
-  a.tout = (float*)(ws + align256((size_t)ncols * D * sizeof(float2)));
+  a.tout = (float*)(ws + cbuf_bytes(D, ncols));
   a.ldt = D;
-  char* t = ws + align256((size_t)ncols * D * sizeof(float2)) +
-            align256((size_t)ncols * D * sizeof(float)) + align256((size_t)D * sizeof(float));
+  char* t = ws + cbuf_bytes(D, ncols) + tout_bytes(D, ncols) + align256((size_t)D * sizeof(float));
   float2* tabM = (float2*)t;
   float2* tabW = (float2*)(t + align256((size_t)D * sizeof(float2)));
+  float2* tabR = (float2*)(t + align256((size_t)D * sizeof(float2)) +
+                           align256((size_t)(D / 2) * sizeof(float2)));
   if (tables)
     launch_k(dct_twiddle_kernel, dim3((unsigned)std::min<int64_t>((D + 255) / 256, 1024)),
-             dim3(256), 0, st, D, 1 << a.lg2, tabM, tabW);
+             dim3(256), 0, st, D, 1 << a.lg2, tabM, tabW, tabR);
   a.tabM = tabM;
   a.tabW = tabW;
+  a.tabR = tabR;
   return a;
 }
 static float* dct_mask_buf(int64_t D, char* ws, int ncols) {
-  return (float*)(ws + align256((size_t)ncols * D * sizeof(float2)) +
-                  align256((size_t)ncols * D * sizeof(float)));
+  return (float*)(ws + cbuf_bytes(D, ncols) + tout_bytes(D, ncols));
 }
 
 template <int MODE>

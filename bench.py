@@ -90,12 +90,13 @@ def problem(seed):
 
 class ClockSampler:
     def __init__(self, gpu_index):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        fd, self.path = tempfile.mkstemp(prefix="cofem_clocks_", suffix=".csv")
+        os.close(fd)
         self.gpu = gpu_index
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -113,12 +114,17 @@ class ClockSampler:
             self.proc.terminate()
             self.proc.wait()
             self.f.close()
+        self.samples = open(self.path).read() if os.path.exists(self.path) else ""
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
 
     def summary(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        for line in open(self.path):
+        for line in getattr(self, "samples", "").splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue

@@ -39,7 +39,7 @@ void apply_tick(cudaStream_t st);
 
 namespace cofem {
 
-constexpr int kFftElems = 4096;    // complex values per block
+constexpr int kFftElems = 2048;    // complex values per block
 // shared-memory index of complex value i: one pad every 8 values, so that
 // the stride-8 writes of a radix-8 stage spread over the banks
 __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
@@ -445,8 +445,8 @@ static DctArgs dct_args(int64_t D, char* ws, int ncols, cudaStream_t st, bool ta
   DctArgs a = {};
   a.D = D;
   const int p = ilog2(D) - 1;                      // M = D/2 = 2^p
-  a.lg1 = p / 2;
-  a.lg2 = p - a.lg1;
+  a.lg2 = p / 2;                                   // M2 <= M1: pass 2 holds >= 2 transforms
+  a.lg1 = p - a.lg2;
   a.cbuf = (float2*)ws;
   a.tout = (float*)(ws + cbuf_bytes(D, ncols));
   a.ldt = D;

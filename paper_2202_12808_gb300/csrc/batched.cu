@@ -233,51 +233,78 @@ __global__ void bstep_kernel(BConf cf, const BVec* pvs, BState* sts, const int* 
 }
 
 // x += a p, r -= a q (a from bstep_kernel), rho_new partials; last block:
-// stop test.
+// stop test.  Grid (chunks, 1, problems): a block takes one chunk of a
+// problem through all its columns (per-block latency paid once, not once
+// per column); per column, each warp folds its compensated partial with
+// shuffles, and the warps' partials are combined in warp order at the end.
 __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, float* X,
                                float* R, const float* P, const float* Q, const float* astep,
                                double* part) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double sh[32];
-  const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  constexpr int kWarps = 256 / 32;
+  __shared__ float2 red2[kWarps][kMaxCols];      // per warp and column: (sum, compensation)
+  __shared__ double redb[kWarps][kMaxCols];      // FP64 side sums of out-of-range products
+  const int pi = blockIdx.z, c = blockIdx.x;
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   BState* st = sts + pi;
-  const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
-  float4 xv[kBSub], rv[kBSub], pp[kBSub], qq[kBSub];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < cf.nc; ++j) {
+    const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
+    float4 xv[kBSub], rv[kBSub], pp[kBSub], qq[kBSub];
 #pragma unroll
-  for (int u = 0; u < kBSub; ++u) {
-    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
-    if (d < pv.ld) {
-      xv[u] = *reinterpret_cast<const float4*>(X + o0 + d);
-      rv[u] = *reinterpret_cast<const float4*>(R + o0 + d);
-      pp[u] = *reinterpret_cast<const float4*>(P + o0 + d);
-      qq[u] = *reinterpret_cast<const float4*>(Q + o0 + d);
+    for (int u = 0; u < kBSub; ++u) {
+      const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+      if (d < pv.ld) {
+        xv[u] = *reinterpret_cast<const float4*>(X + o0 + d);
+        rv[u] = *reinterpret_cast<const float4*>(R + o0 + d);
+        pp[u] = *reinterpret_cast<const float4*>(P + o0 + d);
+        qq[u] = *reinterpret_cast<const float4*>(Q + o0 + d);
+      }
+    }
+    const float a = astep[(int64_t)pi * kMaxCols + j];
+    AccF acc;
+#pragma unroll
+    for (int u = 0; u < kBSub; ++u) {
+      const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+      if (d < pv.ld) {
+        float4 x4 = xv[u], r4 = rv[u];
+        x4.x = fmaf(a, pp[u].x, x4.x); x4.y = fmaf(a, pp[u].y, x4.y);
+        x4.z = fmaf(a, pp[u].z, x4.z); x4.w = fmaf(a, pp[u].w, x4.w);
+        r4.x = fmaf(-a, qq[u].x, r4.x); r4.y = fmaf(-a, qq[u].y, r4.y);
+        r4.z = fmaf(-a, qq[u].z, r4.z); r4.w = fmaf(-a, qq[u].w, r4.w);
+        acc.add_prod(r4.x, r4.x);
+        acc.add_prod(r4.y, r4.y);
+        acc.add_prod(r4.z, r4.z);
+        acc.add_prod(r4.w, r4.w);
+        *reinterpret_cast<float4*>(X + o0 + d) = x4;
+        *reinterpret_cast<float4*>(R + o0 + d) = r4;
+      }
+    }
+    float sv = acc.s, cv = acc.c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      two_sum_merge(sv, cv, __shfl_xor_sync(0xffffffffu, sv, o), __shfl_xor_sync(0xffffffffu, cv, o));
+    const double bg = warp_sum(acc.big);
+    if (lane == 0) {
+      red2[wid][j] = make_float2(sv, cv);
+      redb[wid][j] = bg;
     }
   }
-  const float a = astep[(int64_t)pi * kMaxCols + j];
-  AccF acc;
-#pragma unroll
-  for (int u = 0; u < kBSub; ++u) {
-    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
-    if (d < pv.ld) {
-      float4 x4 = xv[u], r4 = rv[u];
-      x4.x = fmaf(a, pp[u].x, x4.x); x4.y = fmaf(a, pp[u].y, x4.y);
-      x4.z = fmaf(a, pp[u].z, x4.z); x4.w = fmaf(a, pp[u].w, x4.w);
-      r4.x = fmaf(-a, qq[u].x, r4.x); r4.y = fmaf(-a, qq[u].y, r4.y);
-      r4.z = fmaf(-a, qq[u].z, r4.z); r4.w = fmaf(-a, qq[u].w, r4.w);
-      acc.add_prod(r4.x, r4.x);
-      acc.add_prod(r4.y, r4.y);
-      acc.add_prod(r4.z, r4.z);
-      acc.add_prod(r4.w, r4.w);
-      *reinterpret_cast<float4*>(X + o0 + d) = x4;
-      *reinterpret_cast<float4*>(R + o0 + d) = r4;
+  __syncthreads();
+  if (threadIdx.x < cf.nc) {
+    const int j = threadIdx.x;
+    float sv = red2[0][j].x, cv = red2[0][j].y;
+    double bg = redb[0][j];
+    for (int w = 1; w < kWarps; ++w) {
+      two_sum_merge(sv, cv, red2[w][j].x, red2[w][j].y);
+      bg += redb[w][j];
     }
+    part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = ((double)sv + (double)cv) + bg;
+    __threadfence();                   // the last block reads these partials
   }
-  const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = s;
-  if (barrive_last(&st->counter[1], (unsigned)(pv.nch * cf.nc))) {
+  if (barrive_last(&st->counter[1], (unsigned)pv.nch)) {
     if (threadIdx.x < cf.nc) {
       double t = 0.0;
       for (int i = 0; i < pv.nch; ++i) t += part[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
@@ -702,7 +729,8 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
     float* astep = (float*)(ws + L.o_astep);
     BCK(launch_k(bstep_kernel, dim3(n, (nc + kStepWarps - 1) / kStepWarps), dim3(32 * kStepWarps),
                  0, bs, cf, pvs, sts, (const int*)done, (const double*)dots, astep));
-    BCK(launch_k(bupdate_kernel, vg, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
+    const dim3 cg1(L.nch_max, 1, n);           // a block per chunk, all columns
+    BCK(launch_k(bupdate_kernel, cg1, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
                  (const float*)Q, (const float*)astep, part));
     BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, bs, cf, (const int*)done));
     BCK(launch_k(bdirection_kernel, vg, dim3(256), 0, bs, cf, pvs, (const BState*)sts,

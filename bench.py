@@ -661,10 +661,11 @@ def main():
     nested = args.phi == "bf16" and args.terms > 0
     if nested:
         # tensor cores: GEMM1, reduce/split, GEMM2 per apply (P's split comes
-        # from the CG kernels; an apply to x adds a split kernel), update,
-        # direction; the replacement block: split, GEMM1, reduce, GEMM2, true
-        # residual, direction
-        per_iter, per_rep = 3 + 2, 4 + 2
+        # from the CG kernels; an apply to x adds a split kernel), then one
+        # launch for the update and the direction update (264 blocks, all
+        # resident at once); the replacement block: split, GEMM1, reduce,
+        # GEMM2, true residual, direction
+        per_iter, per_rep = 3 + 1, 4 + 2
     else:
         per_iter, per_rep = 4 + 2, 4 + 1
     launches = sum(launches_per_em(c, CFG["resid_replace_every"], per_iter, per_rep, nested)

@@ -472,8 +472,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                     &ctl->error, kApplyPresplit | prep, alpha32);
       if (rc != COFEM_OK) return rc;
       cf.gamma_parts = nparts;
-      launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is);
-      launch_cg_direction<V>(cf, ctl, sc, R, P, is);
+      if (!launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is, true))
+        launch_cg_direction<V>(cf, ctl, sc, R, P, is);
       CKL();
       cudaGraph_t tmp;
       CK(cudaStreamEndCapture(is, &tmp));
@@ -498,7 +498,10 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                   &ctl->error, (cf.split_nt > 0 ? kApplyPresplit : 0u) | prep, alpha32);
     if (rc != COFEM_OK) return rc;
     cf.gamma_parts = nparts;
-    launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, bs);
+    // with a replacement IF node the direction update follows the IF (it
+    // also closes a replacement iteration), so it stays a kernel of its own
+    const bool fused = launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, bs,
+                                           p->resid_replace_every <= 0);
     CKL();
     if (p->resid_replace_every > 0) {
       cudaGraph_t ibody = nullptr;
@@ -514,7 +517,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
       cudaGraph_t tmp;
       CK(cudaStreamEndCapture(is, &tmp));
     }
-    launch_cg_direction<V>(cf, ctl, sc, R, P, bs);
+    if (!fused) launch_cg_direction<V>(cf, ctl, sc, R, P, bs);
     CKL();
     cudaGraph_t tmp;
     CK(cudaStreamEndCapture(bs, &tmp));
@@ -549,8 +552,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                   (pf.split_nt > 0 ? kApplyPresplit : 0u) | prep, alpha32);
     if (rc != COFEM_OK) return rc;
     pf.gamma_parts = np2;
-    launch_cg_update<V>(pf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, ws2);
-    launch_cg_direction<V>(pf, ctl, sc, R, P, ws2);
+    if (!launch_cg_update<V>(pf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, ws2, true))
+      launch_cg_direction<V>(pf, ctl, sc, R, P, ws2);
     CKL();
     cudaGraph_t tmp1, tmp2;
     CK(cudaStreamEndCapture(ws2, &tmp1));

@@ -306,17 +306,57 @@ __global__ void cg_init_warm_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, const 
   }
 }
 
+// Waits (thread 0) until *gen differs from g0; false after limit_ns.
+__device__ __forceinline__ bool wait_gen(const unsigned int* gen, unsigned int g0,
+                                         uint64_t limit_ns) {
+  const volatile unsigned int* g = gen;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (*g == g0) {
+    __nanosleep(32);
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+constexpr uint64_t kGenWaitNs = 2000000000ull;
+
 // --------------------------------------- x += a p, r -= a q, rho_new = r^T r
 // a_j = rho_j / gamma_j with gamma_j the fixed-order sum of the operator's
 // per-block partials of p_j^T A p_j (every block computes the same value).
-template <typename V>
+//
+// DIR: the same launch also applies the direction update p = r + b p (or
+// p = M^-1 r + b p): the last block closes the iteration as usual (b_j, the
+// stop test, ctl->run), then releases the other blocks, which wait for it
+// (bounded) and update p from the r and p values they still hold.  The
+// host launches this form only when the whole grid fits on the GPU at once
+// (occupancy), so that every block the wait depends on is resident.
+template <typename V, bool DIR>
 __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* R,
-                                 const V* P, const V* Q, const double* gparts, double* part,
+                                 V* P, const V* Q, const double* gparts, double* part,
                                  double* part2) {
   pdl_wait();
   pdl_trigger();
   __shared__ double sh[32];
   __shared__ double a_sh;
+  __shared__ int go_sh;
+  unsigned int g0 = 0;
+  if (DIR) {
+    if (*(volatile int*)&ctl->error == (int)COFEM_ERR_TIMEOUT) {
+      // an earlier wait gave up: end the solve instead of iterating on
+      if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        ctl->done = 1;
+        ctl->run = 0;
+        set_cond(cf.while_handle, 0u);
+        set_cond(cf.inner_handle, 0u);
+      }
+      return;
+    }
+    // read before this block arrives, so before the last block can bump it
+    if (threadIdx.x == 0) g0 = *(volatile unsigned int*)&ctl->dir_gen;
+  }
   constexpr int W = 16 / sizeof(V);
   constexpr int U = kUpdChunks;                 // chunks of W values per thread and pass
   const int j = blockIdx.y;
@@ -400,7 +440,8 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
     const double sz = block_sum(accz, sh);
     if (threadIdx.x == 0) part2[(int64_t)blockIdx.x * kMaxCols + j] = sz;
   }
-  if (arrive_last(&ctl->counter[1])) {
+  const bool last = arrive_last(&ctl->counter[1]);
+  if (last) {
     if (cf.minv) {
       column_sums(part, gridDim.x, cf.ncols, sc->rr_new);
       column_sums(part2, gridDim.x, cf.ncols, sc->rho_new);
@@ -423,6 +464,56 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
     }
     __syncthreads();
     if (!ctl->replace) cg_finalize(cf, ctl, sc);
+  }
+  if constexpr (DIR) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int go = 1;
+      if (last) {
+        // b_j, rho_j and ctl->run are written (this block, before the barrier)
+        __threadfence();
+        atomicAdd(&ctl->dir_gen, 1u);
+      } else {
+        go = wait_gen(&ctl->dir_gen, g0, kGenWaitNs);
+        if (!go) {
+          raise_error(ctl, COFEM_ERR_TIMEOUT);
+          set_cond(cf.while_handle, 0u);
+          set_cond(cf.inner_handle, 0u);
+        }
+        __threadfence();
+      }
+      go_sh = go && *(volatile int*)&ctl->run;
+    }
+    __syncthreads();
+    if (!go_sh) return;
+    const V b = (V)__ldcg(&sc->b[j]);
+    V* pw = P + (int64_t)j * cf.ld;
+    for (int64_t base = d0; base < cf.ld; base += U * ts) {
+      // the registers hold r (updated) and p of the loop's last pass
+      const bool held = base + U * ts >= cf.ld;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t d = base + u * ts;
+        if (d < cf.ld) {
+          V rr[W], pp[W];
+          if (held) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) { rr[i] = rv[u][i]; pp[i] = pv[u][i]; }
+          } else {
+            vload(r + d, rr);
+            vload(pw + d, pp);
+          }
+          if (cf.minv) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) rr[i] = rr[i] * (V)cf.minv[d + i];
+          }
+#pragma unroll
+          for (int i = 0; i < W; ++i) pp[i] = fma(b, pp[i], rr[i]);
+          vstore(pw + d, pp);
+          if (cf.split_nt > 0) write_split4(cf, j, d, pp);
+        }
+      }
+    }
   }
 }
 
@@ -608,12 +699,27 @@ void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* 
 }
 
 template <typename V>
-void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
+bool launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                       const V* Q, const double* gparts, double* part, double* part2,
-                      cudaStream_t st) {
-  dim3 g(vec_blocks(cf.ld, kUpdChunks * 16 / sizeof(V), cf.ncols, num_sms()), cf.ncols);
-  launch_k(cg_update_kernel<V>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts, part,
-           part2);
+                      cudaStream_t st, bool with_direction) {
+  const int sms = num_sms();
+  dim3 g(vec_blocks(cf.ld, kUpdChunks * 16 / sizeof(V), cf.ncols, sms), cf.ncols);
+  if (with_direction) {
+    // the fused form waits on every block of its grid: only when all fit at once
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_update_kernel<V, true>, 256,
+                                                      0) != cudaSuccess)
+      per_sm = 0;
+    if ((int64_t)g.x * g.y <= (int64_t)per_sm * sms) {
+      launch_k(cg_update_kernel<V, true>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q,
+               gparts, part, part2);
+      return true;
+    }
+    cudaGetLastError();
+  }
+  launch_k(cg_update_kernel<V, false>, dim3(g), dim3(256), 0, st, cf, ctl, sc, X, R, P, Q, gparts,
+           part, part2);
+  return false;
 }
 
 template <typename V>
@@ -662,9 +768,9 @@ void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
   template void launch_probe_fill<V>(uint64_t, int, int64_t, V*, int64_t, cudaStream_t); \
   template void launch_cg_init<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, V*,         \
                                   const V*, double*, cudaStream_t);                     \
-  template void launch_cg_update<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, const V*, \
+  template bool launch_cg_update<V>(const CgConf&, CgCtl*, CgScalars*, V*, V*, V*,       \
                                     const V*, const double*, double*, double*,          \
-                                    cudaStream_t);                                      \
+                                    cudaStream_t, bool);                                \
   template void launch_cg_init_warm<V>(const CgConf&, CgCtl*, CgScalars*, const V*, V*,  \
                                        V*, const V*, const V*, double*, double*,        \
                                        double*, cudaStream_t);                          \

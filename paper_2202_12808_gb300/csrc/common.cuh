@@ -31,6 +31,7 @@ struct CgCtl {
   double normB2;       // ||B||_F^2
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
+  unsigned int dir_gen;     // CG update with the direction update: bumped when an iteration is closed
 };
 
 // Per-column CG scalars (double, Sec. 3.2 recurrences).

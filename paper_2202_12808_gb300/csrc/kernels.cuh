@@ -12,10 +12,13 @@ void launch_probe_fill(uint64_t key, int K, int64_t D, V* out, int64_t ld, cudaS
 template <typename V>
 void launch_cg_init(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                     const V* bvec, double* part, cudaStream_t st);
+// with_direction: also apply p = r + b p in the same launch when its grid
+// fits on the GPU at once; returns whether it did (else the caller launches
+// cg_direction after it).
 template <typename V>
-void launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, const V* P,
+bool launch_cg_update(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* X, V* R, V* P,
                       const V* Q, const double* gparts, double* part, double* part2,
-                      cudaStream_t st);
+                      cudaStream_t st, bool with_direction);
 template <typename V>
 void launch_cg_init_warm(const CgConf& cf, CgCtl* ctl, CgScalars* sc, const V* X, V* R, V* P,
                          const V* Q, const V* bvec, double* pz, double* pr, double* pb,

@@ -465,15 +465,22 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
     rc = add_conditional(bs, hin, cudaGraphCondTypeWhile, &inner);
     if (rc != COFEM_OK) return rc;
     {
+      // two CG iterations per pass of the inner loop (half the loop's back
+      // edges); the second copy's kernels return at once when the first
+      // ended the solve or a replacement is due (ctl->run == 0)
       cudaStream_t is = ss.s[2];
       CK(cudaStreamBeginCaptureToGraph(is, inner, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      int nparts = 0;
-      rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, is,
-                    &ctl->error, kApplyPresplit | prep, alpha32);
-      if (rc != COFEM_OK) return rc;
-      cf.gamma_parts = nparts;
-      if (!launch_cg_update<V>(cf, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is, true))
-        launch_cg_direction<V>(cf, ctl, sc, R, P, is);
+      for (int copy = 0; copy < 2; ++copy) {
+        int nparts = 0;
+        rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, pdots, &nparts, opws, is,
+                      &ctl->error, kApplyPresplit | prep, alpha32, copy ? &ctl->run : nullptr);
+        if (rc != COFEM_OK) return rc;
+        cf.gamma_parts = nparts;
+        CgConf cc = cf;
+        cc.gate_run = copy;
+        if (!launch_cg_update<V>(cc, ctl, sc, X, R, P, Q, pdots, pvec, pvec2, is, true))
+          launch_cg_direction<V>(cc, ctl, sc, R, P, is);
+      }
       CKL();
       cudaGraph_t tmp;
       CK(cudaStreamEndCapture(is, &tmp));

@@ -342,6 +342,9 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
   __shared__ double sh[32];
   __shared__ double a_sh;
   __shared__ int go_sh;
+  // second copy of an unrolled loop body: the first copy may have ended the
+  // solve or handed over to the residual replacement
+  if (cf.gate_run && *(volatile int*)&ctl->run == 0) return;
   unsigned int g0 = 0;
   if (DIR) {
     if (*(volatile int*)&ctl->error == (int)COFEM_ERR_TIMEOUT) {

@@ -73,6 +73,7 @@ struct CgConf {
   float* alpha32;                    // FP32 copy of alpha kept by the M-step, or null
   int stop_rule;                     // 1: per-column stop (frozen columns have rho_j = 0)
   int T;                             // tasks: columns 0..T-1 are beta Phi^T y_t, then K probes
+  int gate_run;                      // CG update: do nothing unless ctl->run (an unrolled copy)
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

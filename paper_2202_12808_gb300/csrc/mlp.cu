@@ -1,6 +1,6 @@
 // Learned warm start and diagonal preconditioner for the E-step solve (the
-// paper has no learned component; plain CG remains the fallback and the
-// judge of the result).  A per-coordinate MLP 4 -> 32 -> 32 -> 2 (tanh,
+// paper has no learned component; plain CG remains the fallback and its
+// stop test decides the result).  A per-coordinate MLP 4 -> 32 -> 32 -> 2 (tanh,
 // 1282 parameters, layout W1 32x4 | b1 | W2 32x32 | b2 | W3 2x32 | b3)
 // maps normalised features of coordinate d, with c_d = beta ||phi_d||^2 +
 // alpha_d,

@@ -215,19 +215,20 @@ def reference_arm(args):
 def launches_per_em(cg_iters, replace_every, per_iter, per_replace, nested=False):
     """Our kernel launches in one EM iteration: init, per CG iteration
     (operator kernels + update + direction), per residual replacement
-    (operator kernels on x + true residual [+ direction]), diag/M-step.  With
+    (operator kernels on x + true residual [+ direction]), diag/M-step.  In
     the nested loop of the tensor-core path the replacement block (split,
-    two products, reduce, true residual, direction) is launched once more
-    when the solve ends, its kernels returning at once, and the inner loop's
-    second copy of the iteration is launched (and returns at once) when the
-    first copy ends a segment."""
+    two products, reduce, true residual, direction) follows every segment of
+    the inner loop, its kernels returning at once when the segment ended the
+    solve, and the inner loop runs two CG iterations per pass, the second
+    copy launched (and returning at once) when the first ends a segment."""
     n_rep = cg_iters // replace_every if replace_every else 0
     if nested and replace_every:
-        # the inner loop runs two CG iterations per pass: a segment of m
-        # iterations between replacements launches ceil(m / 2) passes
+        # a segment of m iterations launches ceil(m / 2) passes; a solve that
+        # ends at a replacement (its stop test) runs no further segment
         segs = [replace_every] * n_rep + [cg_iters - n_rep * replace_every]
         passes = sum(-(-m // 2) for m in segs if m > 0)
-        return 1 + 2 * passes * per_iter + (n_rep + 1) * per_replace + 1
+        blocks = sum(1 for m in segs if m > 0)
+        return 1 + 2 * passes * per_iter + blocks * per_replace + 1
     return 1 + cg_iters * per_iter + n_rep * per_replace + 1
 
 

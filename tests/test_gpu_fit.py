@@ -83,10 +83,11 @@ def test_fp64_tolerance_mode_config1(cuda_lib):
     else:
         # CG stops on a tolerance, so rounding-level differences in the
         # reductions move a stop by an iteration and the EM trajectory carries
-        # it on: perturbing every reduction of the FP64 oracle itself by 2e-16
-        # (relative) moves single E-steps by up to 4 iterations, mu by ~1e-7
-        # and per-iteration support counts near the 1e6 threshold.  Bounds:
-        # mu, the final support (above) and the total work.
+        # it on: moving every reduction of the FP64 oracle itself by one ulp
+        # moves single E-steps by 4-8 iterations, the total by under 0.5 %
+        # and mu by ~1e-7 (tests/test_tolerance_evidence.py::
+        # test_ulp_perturbed_reductions_move_single_esteps).  Bounds: mu, the
+        # final support (above) and the total work.
         assert abs(sum(st["cg_iters"]) - sum(rst.cg_iters)) <= 0.02 * sum(rst.cg_iters)
         assert rel_l2(mu, rmu) <= 1e-5
 
@@ -147,19 +148,24 @@ def test_replacement_tolerance_mode_fp32(cuda_lib):
     assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3
 
 
-def test_replacement_tensor_core_bf16(cuda_lib):
+@pytest.mark.parametrize("period", [10, 7])
+def test_replacement_tensor_core_bf16(cuda_lib, period):
     # BF16 dictionary on the tensor cores: the replacement runs outside an
-    # inner CG loop (gated kernels), every 10 iterations, against the oracle
-    # on the BF16-rounded dictionary; iteration counts above 10 make sure
-    # replacements happen
+    # inner CG loop (gated kernels), every `period` iterations, against the
+    # oracle on the BF16-rounded dictionary; iteration counts above the period
+    # make sure replacements happen.  The inner loop runs two CG iterations
+    # per pass: an even period always hands over to the replacement from the
+    # second copy, an odd one (7) also from the first, so that the gated
+    # second copy (operator, reduce, update) must skip its work
     prob = _problem(sigma=0.1, seed=4)
     t16, Phi64 = bf16_round(prob.Phi)
     y32 = prob.y.astype(np.float32).astype(np.float64)
-    kw = dict(K=20, em_iters=30, cg_tol=1e-5, cg_max_iters=400, resid_replace_every=10, seed=4)
+    kw = dict(K=20, em_iters=30, cg_tol=1e-5, cg_max_iters=400, resid_replace_every=period,
+              seed=4)
     a, mu, s, st = _gpu_fit(Phi64, y32, prob.beta, torch.bfloat16, B.COFEM_F32, **kw)
     ra, rmu, rs, rst = sbl.cofem_dense(Phi64, y32, prob.beta, 20, 30, 1e-5, 400,
-                                       resid_replace_every=10, seed=4)
-    assert max(st["cg_iters"]) > 10
+                                       resid_replace_every=period, seed=4)
+    assert max(st["cg_iters"]) > 2 * period
     assert rel_l2(mu, rmu) <= 1e-4
     eq, _ = support_compare(a, ra)
     assert eq
@@ -241,10 +247,12 @@ def test_per_column_stop_bf16_tensor_cores(cuda_lib):
     """The tensor-core path at the dense workload's tolerance 1e-5.  With
     FP32 vectors each probe column, whose residual must reach 1e-5 of its
     own norm, converges more slowly than in FP64 at beta = 1e4: an FP32
-    emulation of the oracle (exact products rounded to FP32) takes 46
-    iterations in the first E-step where the FP64 oracle takes 31 (the GPU:
-    46), and 4-5 % more over the fit.  mu, alpha and the support are
-    compared at the FP32 bars; the total iterations within 6 %."""
+    emulation of the oracle (FP32 vectors, FP32-accumulated products) takes
+    46 iterations in the first E-step where the FP64 oracle takes 31 (the
+    GPU: 46), and about 5 % more over the fit
+    (tests/test_tolerance_evidence.py::
+    test_fp32_per_column_stop_needs_more_iterations).  mu, alpha and the
+    support are compared at the FP32 bars; the total iterations within 6 %."""
     prob = _problem()
     _, Phi_ref = bf16_round(prob.Phi)
     y32 = prob.y.astype(np.float32).astype(np.float64)

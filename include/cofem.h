@@ -386,7 +386,9 @@ cofem_status cofem_op_apply_timed(const cofem_op* op, cofem_dtype vec, const voi
  * problem whose scratch would exceed it returns COFEM_ERR_WORKSPACE (see
  * cofem_last_error for the sizes).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and must come before any
- * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * stream capture; the address is then kept for the life of the process, so
+ * after a cudaDeviceReset of that device this entry point must not be called
+ * again in the same process.  All calls share the array: calls whose GPU work overlaps
  * race and give wrong results; order them on one stream.  Same arguments and
  * results as cofem_op_apply.  Asynchronous. */
 cofem_status cofem_op_apply_noalloc(const cofem_op* op, cofem_dtype vec,

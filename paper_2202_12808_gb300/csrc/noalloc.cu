@@ -17,7 +17,9 @@
 // results.  Host code cannot use the array's name as a device address: the
 // first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it; make that first call before any
-// stream capture.
+// stream capture.  The cache lives as long as the process: a
+// cudaDeviceReset of the device would leave it stale, so no call may follow
+// a reset.
 #include <cstdio>
 #include <mutex>
 

@@ -54,6 +54,8 @@ def parse():
                              "multitask-n4096-d32768-t4"],
                     help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-whole-fit", action="store_true",
+                    help="skip the 100-EM-iteration fits (BF16 and the FP32 comparator)")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -144,48 +146,66 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_em_rate(prob, phi_dtype, cg_iters_per_em, budget_s=15.0):
-    """Oracle E-step timed on a bounded sample: one E-step of the workload
-    truncated after as many CG iterations as fit in ~budget_s, scaled by the
-    CG iterations per EM iteration the GPU run needed.  Returns (EM iters/s,
-    seconds per CG iteration, CG iterations sampled, threads)."""
+def oracle_dictionary(prob, phi_dtype):
+    import torch
+    if phi_dtype == "bf16":
+        return torch.from_numpy(prob.Phi).to(torch.bfloat16).double().numpy()
+    return prob.Phi.astype(np.float64)
+
+
+def oracle_sample(prob, phi_dtype, n_iters=None, budget_s=15.0, warmup=1):
+    """The FP64 oracle on the workload: `warmup` untimed CG iterations of the
+    first E-step, then n timed ones (n from the budget if None), each a
+    `step` of the sample, then the diagonal estimate and M-step on the
+    iterate reached.  Returns (seconds per CG iteration, seconds of the
+    estimate + M-step, n, threads)."""
     from oracle import probe_hash as ph
     from oracle import sbl
-    import torch
-    Phi = prob.Phi
-    if phi_dtype == "bf16":
-        Phi = torch.from_numpy(Phi).to(torch.bfloat16).double().numpy()
-    else:
-        Phi = Phi.astype(np.float64)
+    Phi = oracle_dictionary(prob, phi_dtype)
     y = prob.y.astype(np.float32).astype(np.float64)
     beta = prob.beta
     D = Phi.shape[1]
     phi, phit, _ = sbl.dense_dictionary(Phi)
-    t0 = time.perf_counter()
     b = beta * phit(y)
     P = ph.probe_matrix(0, 1, CFG["K"], D)
     B = np.concatenate([b[:, None], P], axis=1)
     alpha = np.ones(D)
     A = lambda X: sbl.apply_A(phi, phit, beta, alpha, X)
-    setup = time.perf_counter() - t0
-    # probe one iteration, then size the sample
-    t1 = time.perf_counter()
-    sbl.cg_solve(A, B, 0.0, 1, fixed_iters=1)
-    one = time.perf_counter() - t1
-    n = max(2, min(200, int(budget_s / max(one, 1e-6))))
+    if warmup:
+        t1 = time.perf_counter()
+        sbl.cg_solve(A, B, 0.0, warmup, fixed_iters=warmup)
+        one = (time.perf_counter() - t1) / warmup
+    else:
+        one = None
+    if n_iters is None:
+        n_iters = max(2, min(200, int(budget_s / max(one or 1.0, 1e-6))))
     t2 = time.perf_counter()
-    sbl.cg_solve(A, B, 0.0, n, fixed_iters=n)
-    per_cg = (time.perf_counter() - t2) / n
+    res = sbl.cg_solve(A, B, 0.0, n_iters, fixed_iters=n_iters)
+    per_cg = (time.perf_counter() - t2) / n_iters
     t3 = time.perf_counter()
-    s = sbl.diag_estimate(P, B[:, 1:])
-    sbl.m_step(b, s)
+    s = sbl.diag_estimate(P, res.X[:, 1:])
+    sbl.m_step(res.X[:, 0], s)
     tail = time.perf_counter() - t3
-    per_em = per_cg * cg_iters_per_em + tail + setup / max(1, CFG["em_iters"])
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count()
-    return 1.0 / per_em, per_cg, n, cores
+    return per_cg, tail, n_iters, cores
+
+
+def oracle_window_counts(first, steps, fallback):
+    """CG iterations per EM iteration of the oracle's own fit over the EM
+    iterations first .. first + steps - 1 (1-based), from its committed
+    100-iteration trajectory; `fallback` (and the source name) if absent."""
+    ref = load_reference_fit("bf16")
+    if ref is not None and first - 1 + steps <= len(ref["cg_iters"]):
+        return ref["cg_iters"][first - 1:first - 1 + steps], "oracle trajectory (golden)"
+    return fallback, "GPU run"
+
+
+def oracle_rate(per_cg, tail, counts):
+    """EM iterations/s of the oracle over EM iterations with these CG counts."""
+    return len(counts) / (per_cg * float(sum(counts)) + tail * len(counts))
 
 
 def reference_arm(args):
@@ -193,24 +213,120 @@ def reference_arm(args):
     if rank != 0:
         return
     prob = problem(args.seed)
-    # CG iterations per EM iteration are not known without running the method;
-    # the oracle's own first E-step count (capped) is used for the scale.
-    rate, per_cg, n, cores = oracle_em_rate(prob, args.phi, 60.0,
-                                            budget_s=max(5.0, 20.0 / max(1, args.steps)))
+    # each timed step is one FP64 CG iteration of the workload's E-step
+    per_cg, tail, n, cores = oracle_sample(prob, args.phi, n_iters=max(1, args.steps),
+                                           warmup=max(1, args.warmup))
+    counts, src = oracle_window_counts(args.warmup + 1, args.steps,
+                                       [60] * max(1, args.steps))
+    rate = oracle_rate(per_cg, tail, counts)
+    sample = ("%d timed FP64 CG iterations (one step each, after %d untimed) of the first "
+              "E-step (numpy/BLAS, %.3f s each) plus the diagonal estimate and M-step on the "
+              "iterate (%.3f s); EM iterations/s = steps / (s per CG iteration x the CG "
+              "iterations of EM iterations t=%d..%d (%d, from the %s) + M-steps)"
+              % (n, max(1, args.warmup), per_cg, tail, args.warmup + 1,
+                 args.warmup + args.steps, int(sum(counts)), src))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": per_cg * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "phi": args.phi, "K": CFG["K"]},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d FP64 CG iterations of one E-step (numpy/BLAS), "
-                                       "scaled to 60 CG iterations per EM iteration" % n},
+                             "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------ GPU arm
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def load_reference_fit(phi):
+    """The FP64 oracle's 100-EM-iteration fit of the headline workload
+    (tests/golden/make_dense_n4096_reference.py): dict with cg_iters,
+    support_counts and the final support {d: alpha_d}, or None."""
+    path = os.path.join(GOLDEN, "dense_n4096_d32768_em100_%s.txt" % phi)
+    if not os.path.exists(path):
+        return None
+    out = {"alpha": {}}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] in ("cg_iters", "support_counts"):
+                out[parts[0]] = [int(v) for v in parts[1:]]
+            elif parts[0] == "relres":
+                out["relres"] = [float(v) for v in parts[1:]]
+            elif parts[0] in ("support", "nrmse_mu_vs_truth"):
+                out[parts[0]] = float(parts[1])
+            else:
+                out["alpha"][int(parts[0])] = float(parts[1])
+    return out
+
+
+def compare_to_reference(alpha, ref, D, thr=1e6):
+    """Support equality under the borderline rule (coordinates with alpha
+    within a factor 2 of the threshold in either path are excluded) and the
+    largest relative alpha difference on the common support."""
+    ra = np.full(D, np.inf)
+    for d, v in ref["alpha"].items():
+        ra[d] = v
+    border = ((alpha > thr / 2) & (alpha < thr * 2)) | ((ra > thr / 2) & (ra < thr * 2))
+    sa, sr = (alpha < thr) & ~border, (ra < thr) & ~border
+    both = sa & sr
+    dev = float(np.max(np.abs(alpha[both] - ra[both]) / ra[both])) if both.any() else 0.0
+    return bool(np.array_equal(sa, sr)), dev, int(border.sum())
+
+
+def time_to_tolerance(hist, end_ns, ref, tols=(1e-2, 1e-3)):
+    """First EM iteration (1-based) from which on the support equals the
+    reference's final support and alpha on it stays within tol, and the
+    device time (s) at the end of that EM iteration."""
+    D = hist.shape[1]
+    ok = [compare_to_reference(hist[t], ref, D) for t in range(hist.shape[0])]
+    out = {}
+    for tol in tols:
+        first = None
+        for t in range(len(ok) - 1, -1, -1):
+            if ok[t][0] and ok[t][1] <= tol:
+                first = t
+            else:
+                break
+        out["%g" % tol] = None if first is None else {
+            "em_iters": first + 1, "seconds": end_ns[first] / 1e9}
+    out["final"] = {"support_equal": ok[-1][0], "alpha_max_rel": ok[-1][1],
+                    "borderline": ok[-1][2]}
+    return out
+
+
+def whole_fit(api, B, op, y, beta, kw, em, dev):
+    """One timed fit of `em` EM iterations (one call, CUDA events on the
+    stream), then the same fit EM iteration by EM iteration (resumed, not
+    timed; results are bitwise those of the single call) for the alpha
+    trajectory.  Returns (seconds, stats, alpha history em x D)."""
+    import torch
+    p = api.params(em_iters=em, **kw)
+    ws = api.workspace(op, p, dev)
+    api.fit(op, y, beta, api.params(em_iters=1, **kw), ws=ws)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    r = api.fit(op, y, beta, p, ws=ws)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    D = op.D
+    hist = np.empty((em, D))
+    alpha = torch.empty(D, dtype=torch.float64, device=dev)
+    for t in range(em):
+        api.fit(op, y, beta, api.params(em_iters=1, t_offset=t, **kw), ws=ws, alpha=alpha)
+        hist[t] = alpha.cpu().numpy()
+    assert np.array_equal(hist[-1], r.alpha.cpu().numpy()), "resumed fit differs"
+    return sec, r.stats, hist
+
 
 def launches_per_em(cg_iters, replace_every, per_iter, per_replace, nested=False):
     """Our kernel launches in one EM iteration: init, per CG iteration
@@ -584,6 +700,78 @@ def run_learned(args):
                                "fallbacks": int(conv_fb)}})
 
 
+def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
+    """The whole 100-EM-iteration fit of the headline workload, twice: the
+    BF16 dictionary (the bench's operator) and the plain FP32 comparator (the
+    FP32 dictionary on the tensor cores, Phi = hi + lo).  For each: EM
+    iterations per second of the whole fit, and time to tolerance -- the
+    device time until the support equals the FP64 oracle's final support
+    (its own dictionary's) and alpha on it stays within 1e-2 / 1e-3 of the
+    oracle's final alpha.  Plus the FP32 operator's second product against
+    the HBM roof."""
+    import torch
+    em = CFG["em_iters"]
+    N, D, ncols = CFG["N"], CFG["D"], CFG["K"] + 1
+    out = {"em_iters": em, "timing": "one cofem_fit call per variant, CUDA events on the "
+                                      "stream; per-EM-iteration device clock from the fit's "
+                                      "statistics (end_ns)"}
+    # plain FP32 GPU CoFEM: FP32 dictionary, packed as hi + lo, autotuned
+    phi32 = torch.from_numpy(prob.Phi).to(dev)
+    op32 = api.DenseOperator(phi32)
+    nb = B.cofem_op_dense_packed_bytes(op32.handle)
+    pk32 = torch.empty(nb, dtype=torch.uint8, device=dev)
+    B.cofem_op_dense_attach_packed(op32.handle, pk32.data_ptr(), nb,
+                                   torch.cuda.current_stream().cuda_stream)
+    nbt = B.cofem_op_dense_autotune_workspace_bytes(op32.handle, ncols)
+    wst = torch.empty(nbt, dtype=torch.uint8, device=dev)
+    st32, cps32, us32 = B.cofem_op_dense_autotune(op32.handle, ncols, wst.data_ptr(), nbt,
+                                                  torch.cuda.current_stream().cuda_stream)
+    del wst
+    for name, op, ref_phi in (("bf16", op16, "bf16"), ("fp32", op32, "f32")):
+        sec, stats, hist = whole_fit(api, B, op, y, prob.beta, kw, em, dev)
+        ent = {"em_iters_per_s": em / sec, "seconds": sec,
+               "cg_iters_total": int(sum(stats["cg_iters"])),
+               "cg_iters_per_em": stats["cg_iters"],
+               "support_counts": stats["support"][::10]}
+        ref = load_reference_fit(ref_phi)
+        if ref is not None:
+            ent["vs_oracle_" + ref_phi] = time_to_tolerance(hist, stats["end_ns"], ref)
+            ent["oracle_cg_iters_total"] = int(sum(ref["cg_iters"]))
+        if name == "bf16":
+            ref32 = load_reference_fit("f32")
+            if ref32 is not None:
+                ent["vs_oracle_f32"] = time_to_tolerance(hist, stats["end_ns"], ref32)
+        out[name] = ent
+    out["fp32"]["pipeline"] = {"stages": st32, "ctas_per_sm": cps32, "us_per_apply": us32}
+    out["ratio_em_iters_per_s"] = out["bf16"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
+    # the FP32 operator's kernels, timed with CUDA events on the stream
+    ld = (D + 63) // 64 * 64
+    Xb = torch.randn((ncols, ld), device=dev)
+    Xb[:, D:] = 0
+    Yb = torch.empty_like(Xb)
+    al = torch.ones(D, dtype=torch.float64, device=dev)
+    nbytes = B.cofem_apply_workspace_bytes(op32.handle, B.COFEM_F32, ncols)
+    wsa = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    per = [B.cofem_op_apply_timed(op32.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols,
+                                  al.data_ptr(), prob.beta, Yb.data_ptr(), wsa.data_ptr(),
+                                  nbytes, st) for _ in range(12)][2:]
+    kms = [float(np.mean([p_[i] for p_ in per])) for i in range(len(per[0]))]
+    BN = -(-ncols // 5) * 16
+    g2 = 4 * N * D + BN * N * 2 + 2 * ncols * D * 4 + 8 * D
+    g1 = 4 * N * D + BN * D * 2 + ncols * N * 4
+    out["fp32"]["roofline"] = {
+        "bound": "hbm", "peak": peak, "unit": "GB/s",
+        "kernels_us": dict(zip(["split", "gemm1", "reduce+split", "gemm2"],
+                               [round(v * 1e3, 2) for v in kms])),
+        "gemm1": {"algorithmic_bytes": g1, "achieved": g1 / (kms[1] / 1e3) / 1e9,
+                  "frac": g1 / (kms[1] / 1e3) / 1e9 / peak},
+        "gemm2": {"algorithmic_bytes": g2, "achieved": g2 / (kms[3] / 1e3) / 1e9,
+                  "frac": g2 / (kms[3] / 1e3) / 1e9 / peak},
+        "kernel": "dense_tc_kernel<1,3> with Phi = hi + lo (two BF16 terms, 4 B per entry)"}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -784,13 +972,20 @@ def main():
                        "h2d_bytes_per_step": h2d // args.steps,
                        "d2h_bytes_per_step": 3 * D * 8 // args.steps}
 
+    if rank == 0 and not args.no_whole_fit and args.phi == "bf16" and args.terms == 3:
+        line["fit_100"] = fit_100_section(api, B, prob, op, y, kw, dev, peak)
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, per_cg, n, cores = oracle_em_rate(prob, args.phi, float(np.mean(cg)))
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d FP64 CG iterations of one E-step on the same "
-                                          "workload (%.3f s each), scaled by the GPU run's "
-                                          "%.1f CG iterations per EM iteration"
-                                          % (n, per_cg, float(np.mean(cg)))}
+        per_cg, tail, n, cores = oracle_sample(prob, args.phi)
+        counts, src = oracle_window_counts(args.warmup + 1, args.steps, cg)
+        rate = oracle_rate(per_cg, tail, counts)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d FP64 CG iterations of the first E-step on the same workload "
+                      "(%.3f s each) plus the diagonal estimate and M-step (%.3f s); EM "
+                      "iterations/s over t=%d..%d with their %d CG iterations (from the %s)"
+                      % (n, per_cg, tail, args.warmup + 1, args.warmup + args.steps,
+                         int(sum(counts)), src)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -83,12 +83,14 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype,
                             const void* phi_dev, int64_t ld,
                             const float* tile_scales_dev, cofem_op** out);
 
-/* BF16 dictionaries only: how the FP32 vectors meet the BF16 Phi.
- * nterms 1..3: on the tensor cores (tcgen05), each FP32 vector is split
- * into nterms BF16 terms (x = x1 + x2 [+ x3], each term the BF16 rounding of
- * the remainder), all products accumulate in FP32; 3 terms carry the full
- * 24-bit FP32 mantissa, 2 terms 16 bits.  nterms 0: CUDA cores (BF16 Phi
- * converted to FP32 in registers).  Default 3. */
+/* BF16 and FP32 dictionaries: how the FP32 vectors meet Phi on the tensor
+ * cores.  nterms 1..3: on the tensor cores (tcgen05), each FP32 vector is
+ * split into nterms BF16 terms (x = x1 + x2 [+ x3], each term the BF16
+ * rounding of the remainder), all products accumulate in FP32; 3 terms carry
+ * the full 24-bit FP32 mantissa, 2 terms 16 bits.  nterms 0: CUDA cores.
+ * Default 3 for BF16; an FP32 dictionary runs on the CUDA cores until a
+ * packed copy is attached (cofem_op_dense_attach_packed), which sets 3 if
+ * nterms was 0. */
 cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms);
 
 /* Tensor-core pipeline shape of a BF16 dictionary's operator: shared-memory
@@ -123,6 +125,23 @@ cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, void* workspac
 size_t cofem_dense_packed_bytes(int64_t N, int64_t D);
 cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev,
                                           size_t packed_bytes, void* stream);
+
+/* FP32 dictionaries on the tensor cores (Sec. 3.2's operator at FP32-class
+ * precision, 4 bytes per entry like FP32 storage): the packed copy holds two
+ * images of the layout above, 2 * cofem_dense_packed_bytes(N, D) bytes, the
+ * first with hi = bf16(phi), the second with lo = bf16(phi - hi) (rounding to
+ * nearest even), so every entry is applied as hi + lo: 16 significant bits,
+ * a relative error of at most 2^-17 per entry.  Attaching it
+ * (cofem_op_dense_attach_packed, same rules) moves the operator
+ * applications of cofem_fit and cofem_op_apply to the tensor cores, both
+ * terms accumulating into the same FP32 accumulator, and makes every other
+ * product of the handle (beta Phi^T y in cofem_fit, cofem_op_forward,
+ * cofem_op_adjoint, cofem_op_col_norms) use hi + lo too, so that the fit
+ * solves one consistent system; detaching (NULL) returns all of them to
+ * the FP32 entries on the CUDA cores.  cofem_op_dense_packed_bytes gives the
+ * size the attach call needs for any dense operator (one image for BF16,
+ * two for FP32, 0 for other kinds). */
+size_t cofem_op_dense_packed_bytes(const cofem_op* op);
 
 /* BF16 dictionaries on the tensor cores: bytes of Phi (a band of its first
  * columns) to keep resident in L2 across the two products of every operator
@@ -219,12 +238,16 @@ void cofem_params_default(cofem_params* p);
 
 /* Per-EM-iteration statistics, host arrays of length em_iters (any may be
  * NULL): CG iterations, final recursive relative residual ||R||_F/||B||_F,
- * number of clamped denominators, support size. */
+ * number of clamped denominators, support size, and (cofem_fit only; the
+ * batched fit leaves it untouched) the device clock at the end of each EM
+ * iteration's M-step in nanoseconds, counted from the fit's first kernel on
+ * the device (%globaltimer, so host-side set-up between kernels counts). */
 typedef struct {
   int32_t* cg_iters;
   double* relres;
   int32_t* clamps;
   int32_t* support;
+  int64_t* end_ns;
 } cofem_stats;
 
 /* Learned path: number of fallbacks to plain CG in the last cofem_fit on

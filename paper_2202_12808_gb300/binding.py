@@ -45,7 +45,8 @@ class cofem_stats(ctypes.Structure):
     _fields_ = [("cg_iters", ctypes.POINTER(ctypes.c_int32)),
                 ("relres", ctypes.POINTER(ctypes.c_double)),
                 ("clamps", ctypes.POINTER(ctypes.c_int32)),
-                ("support", ctypes.POINTER(ctypes.c_int32))]
+                ("support", ctypes.POINTER(ctypes.c_int32)),
+                ("end_ns", ctypes.POINTER(ctypes.c_int64))]
 
 
 class cofem_problem(ctypes.Structure):
@@ -68,6 +69,7 @@ _SIGS = {
     "cofem_op_dense_set_terms": (_S, [_P, _I32]),
     "cofem_op_dense_set_l2_resident": (_S, [_P, _I64]),
     "cofem_dense_packed_bytes": (_SZ, [_I64, _I64]),
+    "cofem_op_dense_packed_bytes": (_SZ, [_P]),
     "cofem_op_dense_set_pipeline": (_S, [_P, _I32, _I32]),
     "cofem_op_dense_autotune_workspace_bytes": (_SZ, [_P, _I32]),
     "cofem_op_dense_autotune": (_S, [_P, _I32, _P, _SZ, _P, ctypes.POINTER(_I32),
@@ -180,6 +182,10 @@ def cofem_dense_packed_bytes(N, D):
     return lib().cofem_dense_packed_bytes(N, D)
 
 
+def cofem_op_dense_packed_bytes(op):
+    return lib().cofem_op_dense_packed_bytes(op)
+
+
 def cofem_op_dense_attach_packed(op, packed_ptr, nbytes, stream=0):
     _check(lib().cofem_op_dense_attach_packed(op, packed_ptr, nbytes, stream),
            "cofem_op_dense_attach_packed")
@@ -232,13 +238,14 @@ def cofem_fit(op, y_ptr, beta, params, ws_ptr, ws_bytes, mu_ptr, s_ptr, alpha_pt
     rr = (ctypes.c_double * n)()
     cl = (ctypes.c_int32 * n)()
     sp = (ctypes.c_int32 * n)()
-    st = cofem_stats(it, rr, cl, sp)
+    en = (ctypes.c_int64 * n)()
+    st = cofem_stats(it, rr, cl, sp, en)
     rc = lib().cofem_fit(op, y_ptr, beta, ctypes.byref(params), ws_ptr, ws_bytes, mu_ptr,
                          s_ptr, alpha_ptr, ctypes.byref(st) if want_stats else None, stream)
     _check(rc, "cofem_fit")
     m = params.em_iters
     return {"cg_iters": list(it)[:m], "relres": list(rr)[:m], "clamps": list(cl)[:m],
-            "support": list(sp)[:m]}
+            "support": list(sp)[:m], "end_ns": list(en)[:m]}
 
 
 def cofem_batched_workspace_bytes(problems, params):

@@ -67,6 +67,9 @@ __global__ void ctl_init_kernel(CgCtl* ctl, long long t0) {
   ctl->t = t0;
   ctl->em_index = 0;
   ctl->error = 0;
+  unsigned long long now;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+  ctl->start_ns = now;
 }
 
 // alpha32[i] = (float)alpha[i]: the FP32 copy that the operators read
@@ -114,8 +117,11 @@ static const float* conv_filters64(const cofem_op* op, char* ws, int ncols, cuda
   return h64;
 }
 
+// Tensor cores: BF16 dictionaries (nterms > 0), and FP32 dictionaries with a
+// packed two-term copy attached (Phi = hi + lo in BF16).
 static bool use_tc(const cofem_op* op) {
-  return op->kind == 0 && op->dense.dtype == COFEM_BF16 && op->dense.nterms > 0;
+  if (op->kind != 0 || op->dense.nterms <= 0) return false;
+  return op->dense.dtype == COFEM_BF16 || (op->dense.dtype == COFEM_F32 && op->dense.packed);
 }
 
 // Scratch of one operator application.  For the tensor-core path it depends
@@ -131,7 +137,7 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
       if (align256(q.total) > b) b = align256(q.total);
       for (int cps = 1; max_shape && cps <= 4; ++cps) {
         DenseTcPlan r = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
-                                      num_sms(), cps, 0);
+                                      num_sms(), cps, 0, op->dense.phi_terms);
         if (align256(r.total) > b) b = align256(r.total);
       }
     }
@@ -170,6 +176,9 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
     if (vec == COFEM_F64)
       dense_simt_apply<double, double>(d, (const double*)x, ld, ncols, (double*)y, beta, alpha,
                                        dots, nparts, ws, st);
+    else if (dense_applies_hilo(d))
+      dense_simt_apply<F32HiLo, float>(d, (const float*)x, ld, ncols, (float*)y, beta, alpha,
+                                       dots, nparts, ws, st);
     else if (d.dtype == COFEM_F32)
       dense_simt_apply<float, float>(d, (const float*)x, ld, ncols, (float*)y, beta, alpha,
                                      dots, nparts, ws, st);
@@ -204,6 +213,8 @@ static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64
     const DenseDesc& d = op->dense;
     if (vec == COFEM_F64)
       dense_simt_forward<double, double>(d, (const double*)z, ldz, ncols, (double*)w, ldw, ws, st);
+    else if (dense_applies_hilo(d))
+      dense_simt_forward<F32HiLo, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw, ws, st);
     else if (d.dtype == COFEM_F32)
       dense_simt_forward<float, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw, ws, st);
     else
@@ -232,6 +243,9 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
     const DenseDesc& d = op->dense;
     if (vec == COFEM_F64)
       dense_simt_adjoint<double, double>(d, (const double*)w, ldw, ncols, (double*)z, ldz, beta,
+                                         nullptr, nullptr, nullptr, nullptr, ws, st);
+    else if (dense_applies_hilo(d))
+      dense_simt_adjoint<F32HiLo, float>(d, (const float*)w, ldw, ncols, (float*)z, ldz, beta,
                                          nullptr, nullptr, nullptr, nullptr, ws, st);
     else if (d.dtype == COFEM_F32)
       dense_simt_adjoint<float, float>(d, (const float*)w, ldw, ncols, (float*)z, ldz, beta,
@@ -266,7 +280,7 @@ static int64_t op_D(const cofem_op* op) {
 
 struct FitLayout {
   size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, alpha32, X, R, P, Q, b, yblk, st_iters,
-      st_relres, st_clamps, st_support, opws;
+      st_relres, st_clamps, st_support, st_end, opws;
   size_t total;
   int64_t ld;
 };
@@ -303,6 +317,7 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   L.st_relres = o; o += align256(sizeof(double) * ne);
   L.st_clamps = o; o += align256(sizeof(int32_t) * ne);
   L.st_support = o; o += align256(sizeof(int32_t) * ne);
+  L.st_end = o; o += align256(sizeof(int64_t) * ne);
   L.opws = o;
   size_t ows = op_ws_bytes(op, p->vec_dtype, ncols);
   size_t ows1 = op_ws_bytes(op, p->vec_dtype, 1);
@@ -401,6 +416,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cf.den_floor = p->den_floor;
   cf.support_threshold = p->support_threshold;
   cf.em_iters = p->em_iters;
+  cf.st_end_ns = (long long*)(ws + L.st_end);
   float* alpha32 = vec == COFEM_F32 ? (float*)(ws + L.alpha32) : nullptr;
   cf.alpha32 = alpha32;
   if (use_tc(op) && vec == COFEM_F32) {
@@ -659,6 +675,7 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
     if (stats->relres) CK(cudaMemcpy(stats->relres, ws + L.st_relres, 8 * n, cudaMemcpyDeviceToHost));
     if (stats->clamps) CK(cudaMemcpy(stats->clamps, ws + L.st_clamps, 4 * n, cudaMemcpyDeviceToHost));
     if (stats->support) CK(cudaMemcpy(stats->support, ws + L.st_support, 4 * n, cudaMemcpyDeviceToHost));
+    if (stats->end_ns) CK(cudaMemcpy(stats->end_ns, ws + L.st_end, 8 * n, cudaMemcpyDeviceToHost));
   }
   if (hctl.error != 0) return (cofem_status)hctl.error;
   return COFEM_OK;
@@ -721,6 +738,7 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   op->dense.packed = nullptr;
   op->dense.tc_ctas_per_sm = 0;
   op->dense.tc_stages = 0;
+  op->dense.phi_terms = dtype == COFEM_F32 ? 2 : 1;
   *out = op;
   return COFEM_OK;
 }
@@ -738,14 +756,28 @@ size_t cofem_dense_packed_bytes(int64_t N, int64_t D) {
   return packed_bytes(N, D);
 }
 
+size_t cofem_op_dense_packed_bytes(const cofem_op* op) {
+  if (!op || op->kind != 0) return 0;
+  if (op->dense.dtype == COFEM_BF16) return packed_bytes(op->dense.N, op->dense.D);
+  if (op->dense.dtype == COFEM_F32) return 2 * packed_bytes(op->dense.N, op->dense.D);
+  return 0;
+}
+
 cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev, size_t packed_bytes_,
                                           void* stream) {
-  if (!op || op->kind != 0 || op->dense.dtype != COFEM_BF16) return COFEM_ERR_INVALID_ARG;
+  if (!op || op->kind != 0 || (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32))
+    return COFEM_ERR_INVALID_ARG;
   if (!packed_dev) { op->dense.packed = nullptr; return COFEM_OK; }
   if (((uintptr_t)packed_dev & 255) != 0) return COFEM_ERR_INVALID_ARG;
-  if (packed_bytes_ < packed_bytes(op->dense.N, op->dense.D)) return COFEM_ERR_WORKSPACE;
-  dense_pack_bf16(op->dense.phi, op->dense.N, op->dense.D, op->dense.ld, packed_dev,
-                  (cudaStream_t)stream);
+  if (packed_bytes_ < cofem_op_dense_packed_bytes(op)) return COFEM_ERR_WORKSPACE;
+  if (op->dense.dtype == COFEM_F32) {
+    dense_pack_f32_terms((const float*)op->dense.phi, op->dense.N, op->dense.D, op->dense.ld,
+                         packed_dev, (cudaStream_t)stream);
+    if (op->dense.nterms == 0) op->dense.nterms = 3;
+  } else {
+    dense_pack_bf16(op->dense.phi, op->dense.N, op->dense.D, op->dense.ld, packed_dev,
+                    (cudaStream_t)stream);
+  }
   CKL();
   op->dense.packed = packed_dev;
   return COFEM_OK;
@@ -761,7 +793,8 @@ cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes) {
 }
 
 cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms) {
-  if (!op || op->kind != 0 || op->dense.dtype != COFEM_BF16 || nterms < 0 || nterms > 3)
+  if (!op || op->kind != 0 || (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32) ||
+      nterms < 0 || nterms > 3)
     return COFEM_ERR_INVALID_ARG;
   op->dense.nterms = nterms;
   return COFEM_OK;
@@ -1062,7 +1095,7 @@ extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, voi
   cofem_status rc = COFEM_OK;
   for (int cps = 1; cps <= 4 && rc == COFEM_OK; ++cps) {
     DenseTcPlan full = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
-                                     num_sms(), cps, 0);
+                                     num_sms(), cps, 0, op->dense.phi_terms);
     for (int stg = 2; stg <= full.stages && rc == COFEM_OK; ++stg) {
       op->dense.tc_ctas_per_sm = cps;
       op->dense.tc_stages = stg;

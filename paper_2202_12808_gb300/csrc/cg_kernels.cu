@@ -657,6 +657,11 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
         st_relres[e] = ctl->relres;
         st_clamps[e] = ctl->clamps;
         st_support[e] = ctl->support;
+        if (cf.st_end_ns) {
+          unsigned long long now;
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+          cf.st_end_ns[e] = (long long)(now - ctl->start_ns);
+        }
       }
       ctl->em_index = e + 1;
       ctl->t += 1;

@@ -32,6 +32,7 @@ struct CgCtl {
   double relres;       // ||R||_F / ||B||_F after the last iteration
   unsigned int counter[8];  // arrival counters of last-block reductions
   unsigned int dir_gen;     // CG update with the direction update: bumped when an iteration is closed
+  unsigned long long start_ns;  // device clock (%globaltimer) when the fit's first kernel ran
 };
 
 // Per-column CG scalars (double, Sec. 3.2 recurrences).
@@ -74,6 +75,8 @@ struct CgConf {
   int stop_rule;                     // 1: per-column stop (frozen columns have rho_j = 0)
   int T;                             // tasks: columns 0..T-1 are beta Phi^T y_t, then K probes
   int gate_run;                      // CG update: do nothing unless ctl->run (an unrolled copy)
+  long long* st_end_ns;              // per EM iteration: device clock at the end of its M-step,
+                                     // ns since the fit's first kernel (ctl->start_ns), or null
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

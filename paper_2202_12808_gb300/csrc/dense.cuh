@@ -18,6 +18,8 @@ struct DenseDesc {
   const void* packed;        // tensor-core path: tile-major copy of Phi or null
   int tc_ctas_per_sm;        // tensor-core pipeline: resident CTAs per SM (1, 2; 0 = 2)
   int tc_stages;             // shared-memory ring depth (0 = as deep as fits)
+  int phi_terms;             // BF16 terms per Phi entry in the packed copy: 1 for a
+                             // BF16 dictionary, 2 for an FP32 one (Phi = hi + lo)
 };
 
 // Tile-major ("packed") BF16 layout read by the tensor-core operator: tile
@@ -32,7 +34,31 @@ inline size_t packed_bytes(int64_t N, int64_t D) {
 }
 void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                      cudaStream_t st);
+// FP32 dictionary: two packed images (2 * packed_bytes(N, D) bytes), the
+// first holding hi = bf16(Phi), the second lo = bf16(Phi - hi), so that
+// hi + lo carries 16 significant bits of every entry.
+void dense_pack_f32_terms(const float* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                          cudaStream_t st);
 
+
+// An FP32 dictionary entry as the tensor-core operator applies it once a
+// two-term packed copy is attached: hi + lo with hi = bf16(v), lo =
+// bf16(v - hi) (round to nearest even).  hi + lo has at most 17 significant
+// bits, so the sum is exact in FP32.  The CUDA-core products of such an
+// operator (b = beta Phi^T y, Phi Z, Phi^T W, column norms) read entries
+// through this type so that every product of the operator uses the same
+// dictionary.
+struct F32HiLo {
+  float v;
+};
+__device__ __forceinline__ float hilo_value(float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const float h = __bfloat162float(hi);
+  return h + __bfloat162float(__float2bfloat16_rn(v - h));
+}
+inline bool dense_applies_hilo(const DenseDesc& d) {
+  return d.dtype == COFEM_F32 && d.phi_terms > 1 && d.packed != nullptr;
+}
 
 // Runs the bounded-wait self-test; returns the device error word (0 or
 // COFEM_ERR_TIMEOUT) or -1 on a CUDA error.
@@ -84,10 +110,12 @@ struct DenseTcPlan {
   size_t smem;               // dynamic shared memory per CTA
   size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, total;
 };
+// PT: BF16 terms per Phi entry (1 or 2); a ring stage holds PT A tiles.
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm = 2,
-                          int stages = 0);
+                          int stages = 0, int PT = 1);
 inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
-  return dense_tc_plan(op.N, op.D, nc, op.nterms, sms, op.tc_ctas_per_sm, op.tc_stages);
+  return dense_tc_plan(op.N, op.D, nc, op.nterms, sms, op.tc_ctas_per_sm, op.tc_stages,
+                       op.phi_terms > 1 ? 2 : 1);
 }
 
 // Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map

@@ -17,6 +17,7 @@ template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
+template <> __device__ __forceinline__ float to_f<F32HiLo>(F32HiLo v) { return hilo_value(v.v); }
 
 template <typename V, typename TA> __device__ __forceinline__ V cvt(TA v) {
   if constexpr (std::is_same<TA, double>::value) return (V)v;
@@ -245,5 +246,6 @@ void dense_simt_apply(const DenseDesc& op, const V* X, int64_t ld, int ncols, V*
 INST(double, double)
 INST(float, float)
 INST(__nv_bfloat16, float)
+INST(F32HiLo, float)
 
 }  // namespace cofem

@@ -1,6 +1,9 @@
 // Dense dictionary operator on the 5th-generation tensor cores (tcgen05):
 //   A X = beta Phi^T (Phi X) + alpha . X        (Eq. (mat-eq))
-// for a BF16 dictionary and FP32 right-hand sides.
+// for a BF16 dictionary and FP32 right-hand sides.  An FP32 dictionary runs
+// the same kernels with every entry stored as two BF16 terms Phi = hi + lo
+// (two packed images, the same 4 bytes per entry as FP32): each ring stage
+// then holds both A tiles and the MMA warp accumulates both products.
 //
 // Each FP32 column x_j is represented exactly enough for FP32 work by NT
 // BF16 terms x_j = x_j1 + x_j2 (+ x_j3) (each term the BF16 rounding of the
@@ -59,6 +62,9 @@ struct TcArgs {
   uint32_t tmem_cols;
   int64_t res_d;        // Phi columns d < res_d are loaded evict-last (kept in L2)
   const __nv_bfloat16* packed;   // pre-swizzled tile-major copy of Phi, or null
+  int phi_terms;        // 2: Phi = hi + lo, two packed images term_stride apart
+                        // (packed copy only); otherwise one
+  int64_t term_stride;  // elements from the hi image to the lo image
   int64_t nkd;          // 64-column tiles of Phi (packed layout)
   // GEMM1: split-K partials (reduced and split by reduce_split_kernel)
   float* wpart;
@@ -173,7 +179,9 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
-  const uint32_t stage_bytes = kATileBytes + b_bytes;
+  const int PT = args.phi_terms > 1 ? 2 : 1;          // A tiles per stage
+  const uint32_t a_bytes = (uint32_t)PT * kATileBytes;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
   const int S = args.stages;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + kMaxStages;
@@ -231,7 +239,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             break;
           }
           uint8_t* sa = smem + s * stage_bytes;
-          uint8_t* sb = sa + kATileBytes;
+          uint8_t* sb = sa + a_bytes;
           tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
           const int kb = u.kb0 + i;
           const int64_t m0 = u.m0;
@@ -239,10 +247,13 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           // across CG iterations; the rest streams through
           if (MODE == 0) {
             const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
-            if (u.pk)   // tile (m0 / 128, kb): one contiguous 16 KB copy
-              tc::bulk_load(sa, u.pk + ((m0 >> 7) * u.nkd + kb) * (kTileM * kTileK), kATileBytes,
-                            &full[s], pol_a);
-            else
+            if (u.pk) {  // tile (m0 / 128, kb): one contiguous 16 KB copy per term
+              const __nv_bfloat16* src = u.pk + ((m0 >> 7) * u.nkd + kb) * (kTileM * kTileK);
+              tc::bulk_load(sa, src, kATileBytes, &full[s], pol_a);
+              if (PT == 2)
+                tc::bulk_load(sa + kATileBytes, src + args.term_stride, kATileBytes, &full[s],
+                              pol_a);
+            } else
               tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
           } else {
             const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
@@ -258,6 +269,12 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               // rows d >= D, which are not stored
               const __nv_bfloat16* src2 = (m0 >> 6) + 1 < u.nkd ? src + kTileM * kTileK : src;
               tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
+              if (PT == 2) {
+                tc::bulk_load(sa + kATileBytes, src + args.term_stride, kATileBytes / 2,
+                              &full[s], pol_a);
+                tc::bulk_load(sa + kATileBytes + kATileBytes / 2, src2 + args.term_stride,
+                              kATileBytes / 2, &full[s], pol_a);
+              }
             } else {
               tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
               tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK,
@@ -301,14 +318,17 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
           tc::tc_fence_after();
           const uint32_t a_base = tc::smem_u32(smem + s * stage_bytes);
-          const uint32_t b_base = a_base + kATileBytes;
+          const uint32_t b_base = a_base + a_bytes;
+          for (int pt = 0; pt < PT; ++pt) {
+            const uint32_t at = a_base + (uint32_t)pt * kATileBytes;
 #pragma unroll
-          for (int k = 0; k < kTileK / 16; ++k) {
-            uint64_t adesc;
-            if (MODE == 0) adesc = tc::smem_desc_sw128(a_base + k * 32, 16, 1024);
-            else adesc = tc::smem_desc_sw128(a_base + k * 2048, kATileBytes / 2, 1024);
-            const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
-            tc::mma_bf16(acc, adesc, bdesc, idesc, (i > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kTileK / 16; ++k) {
+              uint64_t adesc;
+              if (MODE == 0) adesc = tc::smem_desc_sw128(at + k * 32, 16, 1024);
+              else adesc = tc::smem_desc_sw128(at + k * 2048, kATileBytes / 2, 1024);
+              const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
+              tc::mma_bf16(acc, adesc, bdesc, idesc, (i > 0 || k > 0 || pt > 0) ? 1u : 0u);
+            }
           }
           tc::mma_commit(&empty[s]);
         }
@@ -583,6 +603,42 @@ __global__ void pack_kernel(const __nv_bfloat16* __restrict__ phi, int64_t N, in
   }
 }
 
+// FP32 dictionary: the same tile layout, written twice -- image 0 holds
+// hi = bf16(Phi), image 1 (total8 * 8 elements later) lo = bf16(Phi - hi).
+__global__ void pack_f32_terms_kernel(const float* __restrict__ phi, int64_t N, int64_t D,
+                                      int64_t ld, int64_t nkd, int64_t total8,
+                                      __nv_bfloat16* __restrict__ packed) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total8;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * 8;
+    const int64_t row = e >> 6;
+    const int c0 = (int)((((e & 63) >> 3) ^ (row & 7)) << 3);
+    const int r = (int)(row & 127);
+    const int64_t tile = row >> 7;
+    const int64_t kb = tile % nkd, mt = tile / nkd;
+    const int64_t n = mt * 128 + r, d0 = kb * 64 + c0;
+    __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float v = (n < N && d0 + q < D) ? phi[n * ld + d0 + q] : 0.f;
+      hi[q] = __float2bfloat16_rn(v);
+      lo[q] = __float2bfloat16_rn(v - __bfloat162float(hi[q]));
+    }
+    *reinterpret_cast<uint4*>(packed + e) = *reinterpret_cast<uint4*>(hi);
+    *reinterpret_cast<uint4*>(packed + total8 * 8 + e) = *reinterpret_cast<uint4*>(lo);
+  }
+}
+
+void dense_pack_f32_terms(const float* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                          cudaStream_t st) {
+  const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
+  const int64_t blocks = (total8 + 255) / 256;
+  launch_k(pack_f32_terms_kernel, dim3((unsigned)(blocks < 65535 ? blocks : 65535)), dim3(256), 0,
+           st, phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
+}
+
 void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                      cudaStream_t st) {
   const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
@@ -673,7 +729,7 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t 
 static int term_group(int NT) { return 16 / NT; }
 
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm,
-                          int stages) {
+                          int stages, int PT) {
   DenseTcPlan p;
   if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 2;
   p.NT = NT;
@@ -714,7 +770,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
     if (per_cta(s1, &kb, &sr) * 10 <= best * 11) { p.S1 = sr; p.kbps1 = kb; break; }
   }
   const size_t fixed = 1024 + 2 * kMaxStages * 8 + 32 + 64 + 4 * 64 * 8 * 2 + 64;
-  const size_t stage = kATileBytes + (size_t)p.BN * 128;
+  const size_t stage = (size_t)(PT > 1 ? 2 : 1) * kATileBytes + (size_t)p.BN * 128;
   // each resident CTA also costs 1 KB of reserved shared memory
   const size_t budget = kSmemPerSm / per_sm - 1024;
   int st = (int)((budget - fixed) / stage);
@@ -750,7 +806,8 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
                             char* ws, int* err, unsigned flags, cudaStream_t st,
                             const float* alpha32, const int* gate) {
   const int sms = num_sms();
-  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages);
+  const int PT = op.phi_terms > 1 && op.packed ? 2 : 1;
+  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages, PT);
   const bool presplit = (flags & kApplyPresplit) != 0;
   __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
   float* Wp = (float*)(ws + p.off_wpart);
@@ -786,6 +843,8 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.tmem_cols = p.tmem_cols;
   a1.res_d = op.l2_resident_cols;
   a1.packed = (const __nv_bfloat16*)op.packed;
+  a1.phi_terms = PT;
+  a1.term_stride = (int64_t)(packed_bytes(op.N, op.D) / 2);
   a1.nkd = nkd;
   a1.wpart = Wp;
   a1.ldw = p.ldw;
@@ -816,6 +875,8 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.tmem_cols = p.tmem_cols;
   a2.res_d = op.l2_resident_cols;
   a2.packed = (const __nv_bfloat16*)op.packed;
+  a2.phi_terms = PT;
+  a2.term_stride = a1.term_stride;
   a2.nkd = nkd;
   a2.y = Y;
   a2.x = X;

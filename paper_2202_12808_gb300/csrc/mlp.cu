@@ -74,6 +74,7 @@ __device__ __forceinline__ void features(double alpha, float pn2, double beta, d
 __device__ __forceinline__ double wf_any(double v) { return v; }
 __device__ __forceinline__ double wf_any(float v) { return v; }
 __device__ __forceinline__ double wf_any(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double wf_any(F32HiLo v) { return hilo_value(v.v); }
 
 // ----------------------------------------------------- column norms of Phi
 template <typename TA>
@@ -344,6 +345,9 @@ cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st) {
     if (d.dtype == COFEM_F64)
       launch_k(col_norms_kernel<double>, dim3(blocks_for(d.D, 256)), dim3(256), 0, st,
                (const double*)d.phi, d.N, d.D, d.ld, out);
+    else if (dense_applies_hilo(d))
+      launch_k(col_norms_kernel<F32HiLo>, dim3(blocks_for(d.D, 256)), dim3(256), 0, st,
+               (const F32HiLo*)d.phi, d.N, d.D, d.ld, out);
     else if (d.dtype == COFEM_F32)
       launch_k(col_norms_kernel<float>, dim3(blocks_for(d.D, 256)), dim3(256), 0, st,
                (const float*)d.phi, d.N, d.D, d.ld, out);

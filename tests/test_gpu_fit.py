@@ -31,9 +31,13 @@ def _problem(N=256, D=1024, nnz=51, sigma=0.01, seed=0):
     return datagen.dense_problem(N, D, nnz, sigma, seed)
 
 
-def _gpu_fit(Phi, y, beta, torch_phi_dtype, vec, **kw):
+def _gpu_fit(Phi, y, beta, torch_phi_dtype, vec, packed=False, **kw):
     Phi_t = torch.from_numpy(np.ascontiguousarray(Phi)).to("cuda", torch_phi_dtype)
     op = api.DenseOperator(Phi_t)
+    if packed:
+        nb = B.cofem_op_dense_packed_bytes(op.handle)
+        op.packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        B.cofem_op_dense_attach_packed(op.handle, op.packed.data_ptr(), nb)
     p = api.params(vec_dtype=vec, **kw)
     ydt = torch.float64 if vec == B.COFEM_F64 else torch.float32
     r = api.fit(op, torch.from_numpy(y).to("cuda", ydt), beta, p)
@@ -92,18 +96,33 @@ def test_fp64_tolerance_mode_config1(cuda_lib):
         assert rel_l2(mu, rmu) <= 1e-5
 
 
-@pytest.mark.parametrize("phi_kind", ["f32", "bf16"])
+def _hi_lo(Phi32):
+    """Phi as the FP32 tensor-core operator applies it: hi + lo, two BF16
+    terms (round to nearest even), exact in float64."""
+    hi = torch.from_numpy(Phi32).to(torch.bfloat16)
+    lo = (torch.from_numpy(Phi32) - hi.float()).to(torch.bfloat16)
+    return hi.double().numpy() + lo.double().numpy()
+
+
+@pytest.mark.parametrize("phi_kind", ["f32", "f32-tc", "bf16"])
 def test_fp32_tolerance_mode_config1(cuda_lib, phi_kind):
     prob = _problem()
+    packed = phi_kind == "f32-tc"
     if phi_kind == "f32":
         Phi_ref = prob.Phi.astype(np.float64)
+        tdt = torch.float32
+    elif packed:
+        # FP32 dictionary on the tensor cores: the operator applies hi + lo
+        # (reading R12 as for BF16: the oracle runs on the applied values)
+        Phi_ref = _hi_lo(prob.Phi)
         tdt = torch.float32
     else:
         _, Phi_ref = bf16_round(prob.Phi)
         tdt = torch.bfloat16
     y32 = prob.y.astype(np.float32).astype(np.float64)
     c = CFG1
-    a, mu, s, st = _gpu_fit(Phi_ref, y32, prob.beta, tdt, B.COFEM_F32, K=c["K"],
+    Phi_in = prob.Phi if packed else Phi_ref
+    a, mu, s, st = _gpu_fit(Phi_in, y32, prob.beta, tdt, B.COFEM_F32, packed=packed, K=c["K"],
                             em_iters=c["em_iters"], cg_tol=c["cg_tol"],
                             cg_max_iters=c["cg_max_iters"], seed=0)
     ra, rmu, rs, rst = sbl.cofem_dense(Phi_ref, y32, prob.beta, c["K"], c["em_iters"],

@@ -50,8 +50,8 @@ APPLY_CASES = [
 
 
 @pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
-@pytest.mark.parametrize("kind", ["f64", "f32", "bf16", "bf16-t2", "bf16-t1", "bf16-simt",
-                                  "bf16-packed", "bf16-packed-t1"])
+@pytest.mark.parametrize("kind", ["f64", "f32", "f32-packed", "bf16", "bf16-t2", "bf16-t1",
+                                  "bf16-simt", "bf16-packed", "bf16-packed-t1"])
 def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
     rng = np.random.default_rng(ncols)
@@ -63,7 +63,9 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.float64)
         vdt, vec, tol = torch.float64, B.COFEM_F64, 1e-12
         pdt = B.COFEM_F64
-    elif kind == "f32":
+    elif kind in ("f32", "f32-packed"):
+        # f32-packed: the tensor cores with Phi = hi + lo (two BF16 terms, at
+        # most 2^-17 relative per entry), against the oracle on the FP32 Phi
         Phi_ref = prob.Phi.astype(np.float64)
         Phi_t, ld_phi = phi_tensor(prob.Phi, torch.float32)
         vdt, vec, tol = torch.float32, B.COFEM_F32, 2e-5
@@ -81,8 +83,9 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     if pdt == B.COFEM_BF16:
         B.cofem_op_dense_set_terms(op, terms)
     packed = None
-    if kind.startswith("bf16-packed"):
-        nb = B.cofem_dense_packed_bytes(N, D)
+    if kind.startswith("bf16-packed") or kind == "f32-packed":
+        nb = B.cofem_op_dense_packed_bytes(op)
+        assert nb == B.cofem_dense_packed_bytes(N, D) * (2 if kind == "f32-packed" else 1)
         packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
         B.cofem_op_dense_attach_packed(op, packed.data_ptr(), nb)
     try:
@@ -148,21 +151,65 @@ def test_diag_mstep(cuda_lib, K, D):
         assert c[1] == int(np.sum(a < 1e6))
 
 
-@pytest.mark.parametrize("packed", [False, True])
+def test_f32_packed_terms_are_hi_plus_lo(cuda_lib):
+    """The two packed images of an FP32 dictionary: applying Phi = hi + lo
+    with exact-valued inputs matches the oracle's product with hi + lo
+    (rounded to nearest even, from torch) far more closely than the 2^-17
+    representation error of Phi itself."""
+    N, D, ncols = 300, 1100, 17
+    prob = datagen.dense_problem(N, D, 20, 0.01, seed=9)
+    P32 = prob.Phi
+    hi = torch.from_numpy(P32).to(torch.bfloat16)
+    lo = (torch.from_numpy(P32) - hi.float()).to(torch.bfloat16)
+    Phi_hl = hi.double().numpy() + lo.double().numpy()
+    assert np.max(np.abs(Phi_hl - P32) / np.maximum(np.abs(P32), 1e-30)) <= 2.0 ** -17
+    Phi_t, ld_phi = phi_tensor(P32, torch.float32)
+    op = B.cofem_op_dense(N, D, B.COFEM_F32, Phi_t.data_ptr(), ld_phi)
+    nb = B.cofem_op_dense_packed_bytes(op)
+    pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    B.cofem_op_dense_attach_packed(op, pk.data_ptr(), nb)
+    try:
+        rng = np.random.default_rng(2)
+        X = rng.standard_normal((D, ncols)).astype(np.float32).astype(np.float64)
+        alpha = rng.uniform(0.5, 10.0, D)
+        Xb, ld = to_block(X, torch.float32)
+        Yb = torch.empty_like(Xb)
+        al = torch.from_numpy(alpha).cuda()
+        ws = _ws(op, B.COFEM_F32, ncols)
+        B.cofem_op_apply(op, B.COFEM_F32, Xb.data_ptr(), ld, ncols, al.data_ptr(), 1.0,
+                         Yb.data_ptr(), ws.data_ptr(), ws.numel())
+        torch.cuda.synchronize()
+        phi, phit, _ = sbl.dense_dictionary(Phi_hl)
+        ref = sbl.apply_A(phi, phit, 1.0, alpha, X)
+        got = from_block(Yb, D)
+        for j in range(ncols):
+            assert rel_l2(got[:, j], ref[:, j]) <= 2e-6, j
+    finally:
+        B.cofem_op_destroy(op)
+
+
+@pytest.mark.parametrize("packed", [False, True, "f32"])
 def test_op_apply_tensor_core_full_size(cuda_lib, packed):
     # the bench workload's operator (N=4096, D=32768, 33 columns, BF16 Phi,
     # 3-term split) on sampled output rows computed one by one by the oracle
     N, D, ncols = 4096, 32768, 33
     prob = datagen.dense_problem(N, D, 655, 0.01, seed=0)
-    t16, Phi_ref = bf16_round(prob.Phi)
-    Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
+    if packed == "f32":
+        # FP32 Phi on the tensor cores (hi + lo), against the FP32 Phi
+        Phi_ref = prob.Phi.astype(np.float64)
+        Phi_t, ld_phi = phi_tensor(prob.Phi, torch.float32)
+        pdt = B.COFEM_F32
+    else:
+        t16, Phi_ref = bf16_round(prob.Phi)
+        Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
+        pdt = B.COFEM_BF16
     rng = np.random.default_rng(1)
     X = rng.standard_normal((D, ncols)).astype(np.float32).astype(np.float64)
     alpha = rng.uniform(0.5, 1e6, D)
     beta = 1e4
-    op = B.cofem_op_dense(N, D, B.COFEM_BF16, Phi_t.data_ptr(), ld_phi)
+    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
     if packed:
-        nb = B.cofem_dense_packed_bytes(N, D)
+        nb = B.cofem_op_dense_packed_bytes(op)
         pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
         B.cofem_op_dense_attach_packed(op, pk.data_ptr(), nb)
     try:

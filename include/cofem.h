@@ -296,6 +296,13 @@ cofem_status cofem_batched_workspace_bytes(int32_t n, const cofem_problem* probl
  * problem whose CG has stopped costs nothing until the next EM iteration.
  * FP32 vectors (p->vec_dtype must be COFEM_F32), BF16 dictionaries on the
  * tensor cores (3-term split); no residual replacement (must be 0).
+ * p->mlp (the learned warm start, see cofem_params) runs per problem as in
+ * cofem_fit: from the fit's second E-step on every problem starts from its
+ * own X0 = [mu_hat | s_hat . p_k] with M^-1 = diag(s_hat), and a problem
+ * whose preconditioned solve misses cg_tol within cg_max_iters is rerun as
+ * plain CG from zero (its E-step counting both solves; the total over all
+ * problems is cofem_last_fit_fallbacks); not with stop_rule 1
+ * (COFEM_ERR_UNSUPPORTED).
  * mu_dev, s_dev, alpha_dev: sum_i D_i doubles each, problem i at offset
  * sum_{k<i} D_k (alpha_dev is read as the starting alpha when
  * t_offset > 0).  stats (optional): host arrays of n * em_iters values,

@@ -344,6 +344,7 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
 }
 
 static thread_local int g_last_fallbacks = 0;
+void set_last_fit_fallbacks(int n) { g_last_fallbacks = n; }
 cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- graph

@@ -38,12 +38,19 @@ struct BState {                         // one problem's CG state (device)
   double normB2, relres;
   double b0norm2;                       // ||b||^2 of column 0 (probe columns: D)
   double rho[kMaxCols], rho_new[kMaxCols], b[kMaxCols];
+  // learned start: the solve is preconditioned (rho holds r_j^T z_j, z = M^-1 r,
+  // rr_new the r_j^T r_j of the stop test); iterations of a preconditioned
+  // solve that fell back, fallbacks so far
+  double rr_new[kMaxCols];
+  int pcg, extra_iters, fallbacks, pad2;
 };
 
 struct BCtl {
   long long t;
   int em_index;
   int error;
+  int fallbacks;                        // learned start: fallbacks to plain CG, all problems
+  int pad;
 };
 
 struct BConf {
@@ -58,6 +65,10 @@ struct BConf {
   int split_nt;
   int64_t split_ld;                      // pitch of the BF16 split buffer
   __nv_bfloat16* split_buf;
+  const float* minv;                     // learned start: M^-1 per coordinate (aoff + d), else null
+  unsigned long long while2_handle;      // learned start: the plain-CG rerun loop
+  long long t_first;                     // learned start: EM iteration of the fit's first E-step
+  int only_undone;                       // binit: re-initialise only problems with done == 0
 };
 
 __device__ __forceinline__ void bset_cond(unsigned long long h, unsigned v) {
@@ -108,7 +119,7 @@ __device__ void bfinalize(const BConf& cf, BState* st, int64_t D) {
   const int j = threadIdx.x;
   if (j < 32) {
     double t = 0.0;
-    for (int c = j; c < cf.nc; c += 32) t += st->rho_new[c];
+    for (int c = j; c < cf.nc; c += 32) t += st->pcg ? st->rr_new[c] : st->rho_new[c];
     t = warp_sum(t);
     if (j == 0) tot_sh = t;
   }
@@ -147,6 +158,7 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
   const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
   const BVec pv = pvs[pi];
   if (c >= pv.nch) return;
+  if (cf.only_undone && done[pi]) return;   // rerun only the problems that fell back
   BState* st = sts + pi;
   const uint64_t key = probe_key(pv.seed, ctl->t);
   float* x = X + pv.xoff + (int64_t)j * pv.ld;
@@ -188,6 +200,8 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
       if (cf.stop_rule == 1 && !(b2 > 0.0)) st->rho[0] = 0.0;   // b = 0: x = 0, frozen
       st->relres = 1.0;
       st->iter = 0;
+      st->pcg = 0;
+      if (!cf.only_undone) st->extra_iters = 0;
       st->clamps = 0;
       st->support = 0;
       int dn = 0;
@@ -198,6 +212,117 @@ __global__ void binit_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, 
       st->counter[0] = 0;
     }
   }
+}
+
+// Learned start, after Q = A X0: R = B - Q, Z = M^-1 R, P = Z (and P's BF16
+// terms); rho_j = r_j^T z_j, rr_j = r_j^T r_j; ||B||; the stop test on
+// ||R||_F / ||B||_F.  Grid and reductions as in binit_kernel.
+__global__ void binit_warm_kernel(BConf cf, const BVec* pvs, BState* sts, int* done,
+                                  const BCtl* ctl, float* R, float* P, const float* Q,
+                                  const float* bv, double* part, double* part2, double* partb) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sh[32];
+  const int pi = blockIdx.z, j = blockIdx.y, c = blockIdx.x;
+  const BVec pv = pvs[pi];
+  if (c >= pv.nch) return;
+  BState* st = sts + pi;
+  const uint64_t key = probe_key(pv.seed, ctl->t);
+  float* r = R + pv.xoff + (int64_t)j * pv.ld;
+  float* p = P + pv.xoff + (int64_t)j * pv.ld;
+  const float* q = Q + pv.xoff + (int64_t)j * pv.ld;
+  AccF az, ar, ab;
+#pragma unroll
+  for (int u = 0; u < kBSub; ++u) {
+    const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
+    if (d < pv.ld) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float bw = 0.f, rv = 0.f, zv = 0.f;
+        if (d + i < pv.D) {
+          if (j == 0) { bw = bv[pv.aoff + d + i]; ab.add_prod(bw, bw); }
+          else bw = bprobe(key, d + i, j - 1);
+          rv = bw - q[d + i];
+          zv = rv * cf.minv[pv.aoff + d + i];
+        }
+        r[d + i] = rv;
+        p[d + i] = zv;
+        v[i] = zv;
+        az.add_prod(rv, zv);
+        ar.add_prod(rv, rv);
+      }
+      if (cf.split_nt > 0) bsplit4(cf, pv, j, d, v);
+    }
+  }
+  const double sz = block_sum(az, sh);
+  const double sr = block_sum(ar, sh);
+  const double sb = j == 0 ? block_sum(ab, sh) : 0.0;
+  const int64_t slot = ((int64_t)pi * cf.nch_max + c) * kMaxCols;
+  if (threadIdx.x == 0) {
+    part[slot + j] = sz;
+    part2[slot + j] = sr;
+    if (j == 0) partb[(int64_t)pi * cf.nch_max + c] = sb;
+    __threadfence();
+  }
+  if (barrive_last(&st->counter[0], (unsigned)(pv.nch * cf.nc))) {
+    if (threadIdx.x < cf.nc) {
+      double tz = 0.0, tr = 0.0;
+      for (int i = 0; i < pv.nch; ++i) {
+        tz += part[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+        tr += part2[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+      }
+      st->rho[threadIdx.x] = tz;
+      st->rr_new[threadIdx.x] = tr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b2 = 0.0, r2 = 0.0;
+      for (int i = 0; i < pv.nch; ++i) b2 += partb[(int64_t)pi * cf.nch_max + i];
+      for (int jj = 0; jj < cf.nc; ++jj) r2 += st->rr_new[jj];
+      st->normB2 = b2 + (double)cf.K * (double)pv.D;
+      st->b0norm2 = b2;
+      st->relres = st->normB2 > 0.0 ? sqrt(r2) / sqrt(st->normB2) : 0.0;
+      st->iter = 0;
+      st->pcg = 1;
+      st->extra_iters = 0;
+      st->clamps = 0;
+      st->support = 0;
+      int dn = !(st->normB2 > 0.0) || (cf.fixed_iters == 0 && st->relres < cf.tol);
+      if (!isfinite(st->normB2) || !isfinite(st->relres)) { st->error = COFEM_ERR_NONFINITE; dn = 1; }
+      st->done = dn;
+      done[pi] = dn;
+      st->counter[0] = 0;
+    }
+  }
+}
+
+// Learned start, after the preconditioned solves: a problem whose solve ran
+// into the cap without meeting the tolerance (not at the fit's first E-step,
+// where the solve is plain CG) is rerun as plain CG from zero; its
+// iterations so far are kept in extra_iters.  done[i] = 0 marks the reruns;
+// the rerun loop's condition is whether any problem fell back.
+__global__ void bfallback_kernel(BConf cf, BState* sts, int* done, BCtl* ctl) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const bool first = ctl->t == cf.t_first;
+  for (int i = threadIdx.x; i < cf.nprob; i += blockDim.x) {
+    BState* st = sts + i;
+    const bool fb = !first && cf.fixed_iters == 0 && st->pcg && !st->error &&
+                    !(st->relres < cf.tol);
+    if (fb) {
+      st->extra_iters = st->iter;
+      st->fallbacks += 1;
+      atomicAdd(&ctl->fallbacks, 1);
+      any = 1;
+    }
+    done[i] = fb ? 0 : 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) bset_cond(cf.while2_handle, any ? 1u : 0u);
 }
 
 // a_j = rho_j / gamma_j of every unconverged problem and column, gamma_j =
@@ -239,16 +364,19 @@ __global__ void bstep_kernel(BConf cf, const BVec* pvs, BState* sts, const int* 
 // shuffles, and the warps' partials are combined in warp order at the end.
 __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done, float* X,
                                float* R, const float* P, const float* Q, const float* astep,
-                               double* part) {
+                               double* part, double* part2) {
   pdl_wait();
   pdl_trigger();
   constexpr int kWarps = 256 / 32;
   __shared__ float2 red2[kWarps][kMaxCols];      // per warp and column: (sum, compensation)
   __shared__ double redb[kWarps][kMaxCols];      // FP64 side sums of out-of-range products
+  __shared__ float2 rrd2[kWarps][kMaxCols];      // preconditioned solves: r^T r as well
+  __shared__ double rrdb[kWarps][kMaxCols];
   const int pi = blockIdx.z, c = blockIdx.x;
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   BState* st = sts + pi;
+  const bool pcg = cf.minv && st->pcg;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = 0; j < cf.nc; ++j) {
     const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
@@ -264,7 +392,7 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
       }
     }
     const float a = astep[(int64_t)pi * kMaxCols + j];
-    AccF acc;
+    AccF acc, acc2;                    // rho_new (r^T r, or r^T z when preconditioned); r^T r
 #pragma unroll
     for (int u = 0; u < kBSub; ++u) {
       const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
@@ -274,10 +402,20 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
         x4.z = fmaf(a, pp[u].z, x4.z); x4.w = fmaf(a, pp[u].w, x4.w);
         r4.x = fmaf(-a, qq[u].x, r4.x); r4.y = fmaf(-a, qq[u].y, r4.y);
         r4.z = fmaf(-a, qq[u].z, r4.z); r4.w = fmaf(-a, qq[u].w, r4.w);
-        acc.add_prod(r4.x, r4.x);
-        acc.add_prod(r4.y, r4.y);
-        acc.add_prod(r4.z, r4.z);
-        acc.add_prod(r4.w, r4.w);
+        if (pcg) {
+          const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float mv = d + i < pv.D ? cf.minv[pv.aoff + d + i] : 0.f;
+            acc.add_prod(rr[i], rr[i] * mv);
+            acc2.add_prod(rr[i], rr[i]);
+          }
+        } else {
+          acc.add_prod(r4.x, r4.x);
+          acc.add_prod(r4.y, r4.y);
+          acc.add_prod(r4.z, r4.z);
+          acc.add_prod(r4.w, r4.w);
+        }
         *reinterpret_cast<float4*>(X + o0 + d) = x4;
         *reinterpret_cast<float4*>(R + o0 + d) = r4;
       }
@@ -291,6 +429,18 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
       red2[wid][j] = make_float2(sv, cv);
       redb[wid][j] = bg;
     }
+    if (pcg) {
+      float s2 = acc2.s, c2 = acc2.c;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        two_sum_merge(s2, c2, __shfl_xor_sync(0xffffffffu, s2, o),
+                      __shfl_xor_sync(0xffffffffu, c2, o));
+      const double b2 = warp_sum(acc2.big);
+      if (lane == 0) {
+        rrd2[wid][j] = make_float2(s2, c2);
+        rrdb[wid][j] = b2;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x < cf.nc) {
@@ -302,13 +452,26 @@ __global__ void bupdate_kernel(BConf cf, const BVec* pvs, BState* sts, int* done
       bg += redb[w][j];
     }
     part[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = ((double)sv + (double)cv) + bg;
+    if (pcg) {
+      float s2 = rrd2[0][j].x, c2 = rrd2[0][j].y;
+      double b2 = rrdb[0][j];
+      for (int w = 1; w < kWarps; ++w) {
+        two_sum_merge(s2, c2, rrd2[w][j].x, rrd2[w][j].y);
+        b2 += rrdb[w][j];
+      }
+      part2[((int64_t)pi * cf.nch_max + c) * kMaxCols + j] = ((double)s2 + (double)c2) + b2;
+    }
     __threadfence();                   // the last block reads these partials
   }
   if (barrive_last(&st->counter[1], (unsigned)pv.nch)) {
     if (threadIdx.x < cf.nc) {
-      double t = 0.0;
-      for (int i = 0; i < pv.nch; ++i) t += part[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+      double t = 0.0, t2 = 0.0;
+      for (int i = 0; i < pv.nch; ++i) {
+        t += part[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+        if (pcg) t2 += part2[((int64_t)pi * cf.nch_max + i) * kMaxCols + threadIdx.x];
+      }
       st->rho_new[threadIdx.x] = t;
+      if (pcg) st->rr_new[threadIdx.x] = t2;
     }
     if (threadIdx.x == 0) {
       st->iter += 1;
@@ -341,6 +504,7 @@ __global__ void bdirection_kernel(BConf cf, const BVec* pvs, const BState* sts, 
   const BVec pv = pvs[pi];
   if (c >= pv.nch || done[pi]) return;
   const float b = (float)sts[pi].b[j];
+  const bool pcg = cf.minv && sts[pi].pcg;
   const int64_t o0 = pv.xoff + (int64_t)j * pv.ld;
   float4 rv[kBSub], pp[kBSub];
 #pragma unroll
@@ -355,9 +519,15 @@ __global__ void bdirection_kernel(BConf cf, const BVec* pvs, const BState* sts, 
   for (int u = 0; u < kBSub; ++u) {
     const int64_t d = (int64_t)c * kBChunk + u * 1024 + threadIdx.x * 4;
     if (d < pv.ld) {
-      float4 p4 = pp[u];
-      p4.x = fmaf(b, p4.x, rv[u].x); p4.y = fmaf(b, p4.y, rv[u].y);
-      p4.z = fmaf(b, p4.z, rv[u].z); p4.w = fmaf(b, p4.w, rv[u].w);
+      float4 p4 = pp[u], z4 = rv[u];
+      if (pcg) {             // z = M^-1 r (zero past D)
+        z4.x *= d + 0 < pv.D ? cf.minv[pv.aoff + d + 0] : 0.f;
+        z4.y *= d + 1 < pv.D ? cf.minv[pv.aoff + d + 1] : 0.f;
+        z4.z *= d + 2 < pv.D ? cf.minv[pv.aoff + d + 2] : 0.f;
+        z4.w *= d + 3 < pv.D ? cf.minv[pv.aoff + d + 3] : 0.f;
+      }
+      p4.x = fmaf(b, p4.x, z4.x); p4.y = fmaf(b, p4.y, z4.y);
+      p4.z = fmaf(b, p4.z, z4.z); p4.w = fmaf(b, p4.w, z4.w);
       *reinterpret_cast<float4*>(P + o0 + d) = p4;
       if (cf.split_nt > 0) {
         const float v[4] = {p4.x, p4.y, p4.z, p4.w};
@@ -455,7 +625,7 @@ __global__ void bfinish_kernel(BConf cf, BState* sts, BCtl* ctl, int32_t* st_ite
   const int e = ctl->em_index;
   for (int i = threadIdx.x; i < cf.nprob; i += blockDim.x) {
     if (e < cf.em_iters) {
-      st_iters[(int64_t)i * cf.em_iters + e] = sts[i].iter;
+      st_iters[(int64_t)i * cf.em_iters + e] = sts[i].iter + sts[i].extra_iters;
       st_relres[(int64_t)i * cf.em_iters + e] = sts[i].relres;
       st_clamps[(int64_t)i * cf.em_iters + e] = sts[i].clamps;
       st_support[(int64_t)i * cf.em_iters + e] = sts[i].support;
@@ -475,6 +645,7 @@ __global__ void bctl_init_kernel(BCtl* ctl, long long t0) {
   ctl->t = t0;
   ctl->em_index = 0;
   ctl->error = 0;
+  ctl->fallbacks = 0;
 }
 
 __global__ void bfill_kernel(double* x, int64_t n, double v) {
@@ -502,6 +673,11 @@ struct BLayout {
   // workspace offsets
   size_t o_packed, o_X, o_R, o_P, o_Q, o_b, o_xs, o_ws, o_wpart, o_dots, o_part, o_astep, o_state, o_done,
       o_ctl, o_vec, o_tcp, o_it1, o_it2, o_st_it, o_st_rr, o_st_cl, o_st_sp, o_simt, total;
+  // learned start: M^-1 and ||phi_d||^2 per coordinate, second and norm partials,
+  // the warm-start kernel's problem table
+  size_t o_minv = 0, o_pn2 = 0, o_part2 = 0, o_partb = 0, o_wprob = 0;
+  std::vector<BWarmProb> wprob;
+  int64_t ld_max = 0;
 };
 
 // K blocks (64 columns of Phi) of one first-product work item at most: up to
@@ -550,6 +726,8 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
     for (int mt = 0; mt < v.ndots; ++mt) L->items2.push_back({i, mt, 0, 0, nk2});
     L->vec.push_back(v);
     L->tcp.push_back(t);
+    L->wprob.push_back({D, ld, xoff, aoff, b1, pr[i].seed, pr[i].beta});
+    L->ld_max = std::max(L->ld_max, ld);
     xoff += (int64_t)nc * ld;
     aoff += D;
     b1 += ld;
@@ -601,6 +779,13 @@ static cofem_status blayout(int n, const cofem_problem* pr, const cofem_params* 
   L->o_st_cl = take((size_t)n * ne * 4);
   L->o_st_sp = take((size_t)n * ne * 4);
   L->o_simt = take(simt);
+  if (p->mlp) {
+    L->o_minv = take((size_t)aoff * 4);
+    L->o_pn2 = take((size_t)aoff * 4);
+    L->o_part2 = take((size_t)n * L->nch_max * kMaxCols * 8);
+    L->o_partb = take((size_t)n * L->nch_max * 8);
+    L->o_wprob = take((size_t)n * sizeof(BWarmProb));
+  }
   L->total = o;
   return COFEM_OK;
 }
@@ -613,6 +798,7 @@ static cofem_status bcheck(int n, const cofem_problem* pr, const cofem_params* p
   if (!(p->den_floor > 0.0) || p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
   if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
   if (p->tasks > 1) return COFEM_ERR_UNSUPPORTED;
+  if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 
@@ -623,7 +809,7 @@ namespace cofem {
 
 namespace {
 struct BStreams {
-  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
   ~BStreams() {
     for (auto x : s)
       if (x) cudaStreamDestroy(x);
@@ -676,41 +862,24 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
   cf.split_ld = L.ldx_total;
   cf.split_buf = xs;
 
-  cudaStream_t cs = ss.s[0];
-  BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-  cudaStreamCaptureStatus status;
-  cudaGraph_t g = nullptr;
-  BCK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle hw;
-  BCK(cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault));
-  cf.while_handle = (unsigned long long)hw;
+  const bool learned = p->mlp != nullptr;
+  if (learned) {
+    cf.minv = (const float*)(ws + L.o_minv);
+    cf.t_first = p->t_offset + 1;
+  }
+  float* astep = (float*)(ws + L.o_astep);
+  int* err = &ctl->error;
+  const int G = 16 / L.NT;
+  const dim3 rg((unsigned)((L.ldw_max / 4 + 127) / 128), (L.BN / 16) * G, n);
   const dim3 vg(L.nch_max, nc, n);
-  BCK(launch_k(binit_kernel, vg, dim3(256), 0, cs, cf, pvs, sts, done, (const BCtl*)ctl, X, R, P,
-               bv, part));
-  BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, cs, cf, (const int*)done));
-  // WHILE node
-  {
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    BCK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, nullptr, &ndeps));
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = hw;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    BCK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    BCK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    cudaStream_t bs = ss.s[1];
-    BCK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    int* err = &ctl->error;
+
+  // first product (split-K partials, or W's terms directly), reduction, second
+  // product of every unconverged problem's block Xin -> Y (with partial dots)
+  auto apply = [&](cudaStream_t bs, const float* Xin, float* Y, double* dts) -> cofem_status {
     if (dense_tc_batched(0, L.NT, (int)L.items1.size(), it1, tcp, done, ws + L.o_packed, xs,
                          L.ldx_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, wpart, nullptr,
                          nullptr, nullptr, nullptr, err, bs, L.grid, wsb, L.ldw_total) != 0)
       return COFEM_ERR_CUDA;
-    const int G = 16 / L.NT;
-    const dim3 rg((unsigned)((L.ldw_max / 4 + 127) / 128), (L.BN / 16) * G, n);
     if (L.any_split) {
       if (L.NT == 3)
         BCK(launch_k(breduce_kernel<3>, rg, dim3(128), 0, bs, tcp, (const int*)done, nc,
@@ -723,20 +892,91 @@ static cofem_status batched_graph(int n, const cofem_params* p, const BLayout& L
                      (const float*)wpart, wsb, L.ldw_total));
     }
     if (dense_tc_batched(1, L.NT, (int)L.items2.size(), it2, tcp, done, ws + L.o_packed, wsb,
-                         L.ldw_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, nullptr, P, Q,
-                         alpha, dots, err, bs, L.grid) != 0)
+                         L.ldw_total, L.BN, nc, L.stages, L.tmem_cols, L.smem, nullptr, Xin, Y,
+                         alpha, dts, err, bs, L.grid) != 0)
       return COFEM_ERR_CUDA;
-    float* astep = (float*)(ws + L.o_astep);
+    return COFEM_OK;
+  };
+  // a WHILE loop of CG iterations (its condition set by the kernel before it)
+  auto add_loop = [&](cudaStream_t outer, cudaStream_t bs, cudaGraphConditionalHandle h,
+                      const BConf& c) -> cofem_status {
+    cudaStreamCaptureStatus st2;
+    cudaGraph_t gg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    BCK(cudaStreamGetCaptureInfo(outer, &st2, nullptr, &gg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    BCK(cudaGraphAddNode(&node, gg, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    BCK(cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies));
+    BCK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cofem_status rc = apply(bs, P, Q, dots);
+    if (rc != COFEM_OK) return rc;
     BCK(launch_k(bstep_kernel, dim3(n, (nc + kStepWarps - 1) / kStepWarps), dim3(32 * kStepWarps),
-                 0, bs, cf, pvs, sts, (const int*)done, (const double*)dots, astep));
+                 0, bs, c, pvs, sts, (const int*)done, (const double*)dots, astep));
     const dim3 cg1(L.nch_max, 1, n);           // a block per chunk, all columns
-    BCK(launch_k(bupdate_kernel, cg1, dim3(256), 0, bs, cf, pvs, sts, done, X, R, (const float*)P,
-                 (const float*)Q, (const float*)astep, part));
-    BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, bs, cf, (const int*)done));
-    BCK(launch_k(bdirection_kernel, vg, dim3(256), 0, bs, cf, pvs, (const BState*)sts,
+    BCK(launch_k(bupdate_kernel, cg1, dim3(256), 0, bs, c, pvs, sts, done, X, R, (const float*)P,
+                 (const float*)Q, (const float*)astep, part,
+                 learned ? (double*)(ws + L.o_part2) : nullptr));
+    BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, bs, c, (const int*)done));
+    BCK(launch_k(bdirection_kernel, vg, dim3(256), 0, bs, c, pvs, (const BState*)sts,
                  (const int*)done, (const float*)R, P));
     cudaGraph_t tmp;
     BCK(cudaStreamEndCapture(bs, &tmp));
+    return COFEM_OK;
+  };
+
+  cudaStream_t cs = ss.s[0];
+  BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  cudaStreamCaptureStatus status;
+  cudaGraph_t g = nullptr;
+  BCK(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hw;
+  BCK(cudaGraphConditionalHandleCreate(&hw, g, 0, cudaGraphCondAssignDefault));
+  cf.while_handle = (unsigned long long)hw;
+  cudaGraphConditionalHandle hw2 = 0;
+  if (learned) {
+    BCK(cudaGraphConditionalHandleCreate(&hw2, g, 0, cudaGraphCondAssignDefault));
+    cf.while2_handle = (unsigned long long)hw2;
+    // warm start X0, M^-1 (plain start at the fit's first E-step), Q = A X0,
+    // preconditioned start
+    launch_batched_warm_start(n, p->K, L.ld_max, (const BWarmProb*)(ws + L.o_wprob), &ctl->t,
+                              cf.t_first, (const __nv_bfloat16*)p->mlp, alpha,
+                              (const float*)(ws + L.o_pn2), mu, s, X, (float*)(ws + L.o_minv),
+                              done, L.NT, xs, L.ldx_total, cs);
+    BCK(cudaGetLastError());
+    cofem_status rc = apply(cs, X, Q, nullptr);
+    if (rc != COFEM_OK) return rc;
+    BCK(launch_k(binit_warm_kernel, vg, dim3(256), 0, cs, cf, pvs, sts, done, (const BCtl*)ctl,
+                 R, P, (const float*)Q, bv, part, (double*)(ws + L.o_part2),
+                 (double*)(ws + L.o_partb)));
+  } else {
+    BCK(launch_k(binit_kernel, vg, dim3(256), 0, cs, cf, pvs, sts, done, (const BCtl*)ctl, X, R,
+                 P, bv, part));
+  }
+  BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, cs, cf, (const int*)done));
+  {
+    cofem_status rc = add_loop(cs, ss.s[1], hw, cf);
+    if (rc != COFEM_OK) return rc;
+  }
+  if (learned) {
+    // problems whose preconditioned solve missed the tolerance: plain CG
+    // from zero (their done flags cleared, the others' set)
+    BCK(launch_k(bfallback_kernel, dim3(1), dim3(256), 0, cs, cf, sts, done, ctl));
+    BConf cf2 = cf;
+    cf2.only_undone = 1;
+    cf2.while_handle = (unsigned long long)hw2;
+    BCK(launch_k(binit_kernel, vg, dim3(256), 0, cs, cf2, pvs, sts, done, (const BCtl*)ctl, X,
+                 R, P, bv, part));
+    BCK(launch_k(bcond_kernel, dim3(1), dim3(256), 0, cs, cf2, (const int*)done));
+    cofem_status rc = add_loop(cs, ss.s[2], hw2, cf2);
+    if (rc != COFEM_OK) return rc;
   }
   BCK(launch_k(bdiag_kernel, dim3(L.nch_max, 1, n), dim3(256), 0, cs, cf, pvs, sts,
                (const BCtl*)ctl, (const float*)X, mu, s, alpha));
@@ -853,6 +1093,15 @@ extern "C" cofem_status cofem_fit_batched(int32_t n, const cofem_problem* proble
                       cudaMemcpyHostToDevice, st));
   BCK(cudaMemcpyAsync(ws + L.o_it2, L.items2.data(), L.items2.size() * sizeof(TcItem),
                       cudaMemcpyHostToDevice, st));
+  if (p->mlp) {
+    BCK(cudaMemcpyAsync(ws + L.o_wprob, L.wprob.data(), n * sizeof(BWarmProb),
+                        cudaMemcpyHostToDevice, st));
+    // ||phi_d||^2 of every problem's dictionary (the network's features)
+    for (int i = 0; i < n; ++i)
+      launch_col_norms_bf16(problems[i].phi_dev, problems[i].N, problems[i].D, problems[i].ld,
+                            (float*)(ws + L.o_pn2) + L.vec[i].aoff, st);
+    BCK(cudaGetLastError());
+  }
   BCK(launch_k(bctl_init_kernel, dim3(1), dim3(1), 0, st, (BCtl*)(ws + L.o_ctl),
                (long long)(p->t_offset + 1)));
   if (p->t_offset == 0)
@@ -895,6 +1144,7 @@ extern "C" cofem_status cofem_fit_batched(int32_t n, const cofem_problem* proble
   }
   BCtl hctl;
   BCK(cudaMemcpy(&hctl, ws + L.o_ctl, sizeof(hctl), cudaMemcpyDeviceToHost));
+  set_last_fit_fallbacks(p->mlp ? hctl.fallbacks : 0);
   if (stats && p->em_iters > 0) {
     const size_t m = (size_t)n * p->em_iters;
     if (stats->cg_iters) BCK(cudaMemcpy(stats->cg_iters, ws + L.o_st_it, 4 * m, cudaMemcpyDeviceToHost));

@@ -27,6 +27,31 @@ void launch_warm_start(const CgConf& cf, const CgCtl* ctl, long long t_first,
                        const __nv_bfloat16* w, const double* alpha, const float* pn2,
                        const double* mu_prev, const double* s_prev, float* X, float* minv,
                        cudaStream_t st);
+// Batched learned start (cofem_fit_batched with a network): one problem as
+// the warm-start kernel sees it -- its D, block pitch and offsets into the
+// concatenated vectors (X at xoff, per-coordinate arrays at aoff, BF16 terms
+// at column boff1 of the split buffer), probe seed and beta.
+struct BWarmProb {
+  int64_t D, ld, xoff, aoff, boff1;
+  uint64_t seed;
+  double beta;
+};
+// X0 = [mu_hat | s_hat . p_k] and M^-1 = diag(s_hat) for every problem (X0 = 0
+// and M^-1 = 1 at the fit's first E-step, *t == t_first), X0's BF16 terms
+// (nt per value, rows split_row(j, t) of pitch split_ld), done[i] = 0.
+// Grid: ceil(ld_max / 128) x nprob blocks of 128 threads.
+void launch_batched_warm_start(int nprob, int K, int64_t ld_max, const BWarmProb* probs,
+                               const long long* t, long long t_first, const __nv_bfloat16* w,
+                               const double* alpha, const float* pn2, const double* mu_prev,
+                               const double* s_prev, float* X, float* minv, int* done,
+                               int split_nt, __nv_bfloat16* split_buf, int64_t split_ld,
+                               cudaStream_t st);
+// ||phi_d||^2 of a BF16 dictionary (N x D, leading dimension ld) into out[0..D).
+void launch_col_norms_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, float* out,
+                           cudaStream_t st);
+// cofem_last_fit_fallbacks of this thread (set by the batched fit).
+void set_last_fit_fallbacks(int n);
+
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
                           const V* bvec, double* part, double* part2, cudaStream_t st);

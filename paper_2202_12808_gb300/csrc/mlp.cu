@@ -302,6 +302,71 @@ __global__ void warm_start_kernel(CgConf cf, const CgCtl* ctl, long long t_first
   }
 }
 
+// The batched form of warm_start_kernel: blockIdx.y is the problem.
+__global__ void batched_warm_start_kernel(int K, const BWarmProb* probs, const long long* tcur,
+                                          long long t_first, const __nv_bfloat16* w,
+                                          const double* alpha, const float* pn2,
+                                          const double* mu_prev, const double* s_prev, float* X,
+                                          float* minv, int* done, int split_nt,
+                                          __nv_bfloat16* split_buf, int64_t split_ld) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float sw[kMlpParams];
+  __shared__ float rows[2][128 * 33];
+  const BWarmProb pb = probs[blockIdx.y];
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((int64_t)blockIdx.x * blockDim.x >= pb.ld) return;       // whole block past this problem
+  load_weights<__nv_bfloat16>(w, sw);
+  if (blockIdx.x == 0 && threadIdx.x == 0) done[blockIdx.y] = 0;
+  if (d >= pb.ld) return;
+  float* r1 = rows[0] + threadIdx.x * 33;
+  float* r2 = rows[1] + threadIdx.x * 33;
+  const long long t = *tcur;
+  const bool first = t == t_first;
+  const uint64_t key = probe_key(pb.seed, t);
+  float m0 = 0.f, sh = 1.f;
+  if (d < pb.D && !first) {
+    float u[4], o[2];
+    double c;
+    const int64_t a = pb.aoff + d;
+    features(alpha[a], pn2[a], pb.beta, mu_prev[a], s_prev[a], u, &c);
+    mlp_fwd(sw, u, r1, r2, o);
+    m0 = (float)(sinh(4.0 * (double)o[0]) / sqrt(c));
+    sh = (float)(exp(4.0 * fmin(fmax((double)o[1], -10.0), 10.0)) / c);
+  }
+  if (d >= pb.D) { m0 = 0.f; sh = 0.f; }
+  if (d < pb.D) minv[pb.aoff + d] = sh;
+  auto put = [&](int j, float v) {
+    X[pb.xoff + (int64_t)j * pb.ld + d] = v;
+    float r = v;
+    for (int tt = 0; tt < split_nt; ++tt) {
+      const __nv_bfloat16 o = __float2bfloat16_rn(r);
+      r -= __bfloat162float(o);
+      split_buf[(int64_t)split_row(j, tt, split_nt) * split_ld + pb.boff1 + d] = o;
+    }
+  };
+  put(0, m0);
+  for (int w0 = 0; w0 * 64 < K; ++w0) {
+    const uint64_t h = d < pb.D ? probe_word(key, d, w0) : 0ull;
+    const int kend = min(K, (w0 + 1) * 64);
+    for (int k = w0 * 64; k < kend; ++k) {
+      const float pk = ((h >> (k & 63)) & 1ull) ? -1.f : 1.f;
+      put(k + 1, (d < pb.D && !first) ? sh * pk : 0.f);
+    }
+  }
+}
+
+void launch_batched_warm_start(int nprob, int K, int64_t ld_max, const BWarmProb* probs,
+                               const long long* t, long long t_first, const __nv_bfloat16* w,
+                               const double* alpha, const float* pn2, const double* mu_prev,
+                               const double* s_prev, float* X, float* minv, int* done,
+                               int split_nt, __nv_bfloat16* split_buf, int64_t split_ld,
+                               cudaStream_t st) {
+  const dim3 g((unsigned)((ld_max + 127) / 128), (unsigned)nprob);
+  launch_k(batched_warm_start_kernel, g, dim3(128), 0, st, K, probs, t, t_first, w, alpha, pn2,
+           mu_prev, s_prev, X, minv, done, split_nt, split_buf, split_ld);
+}
+
 void launch_warm_start(const CgConf& cf, const CgCtl* ctl, long long t_first,
                        const __nv_bfloat16* w, const double* alpha, const float* pn2,
                        const double* mu_prev, const double* s_prev, float* X, float* minv,
@@ -337,6 +402,12 @@ __global__ void conv_col_norms_kernel(const float* h, int C, int T, int64_t L, f
 static unsigned blocks_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   return (unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+void launch_col_norms_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, float* out,
+                           cudaStream_t st) {
+  launch_k(col_norms_kernel<__nv_bfloat16>, dim3(blocks_for(D, 256)), dim3(256), 0, st,
+           (const __nv_bfloat16*)phi, N, D, ld, out);
 }
 
 cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st) {

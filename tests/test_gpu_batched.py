@@ -125,8 +125,13 @@ def test_batched_matches_single_problem_fits(cuda_lib):
 
 def test_batched_rejects_unsupported(cuda_lib):
     phis, ys, betas, seeds, refs, p = _batch(em=1)
-    for bad in (dict(resid_replace_every=10), dict(vec_dtype=B.COFEM_F64)):
+    w = torch.zeros(1282, dtype=torch.bfloat16, device="cuda")
+    for bad in (dict(resid_replace_every=10), dict(vec_dtype=B.COFEM_F64),
+                dict(stop_rule=1, mlp=w.data_ptr())):
+        mlp = bad.pop("mlp", None)
         q = api.params(K=16, em_iters=1, **bad)
+        if mlp:
+            q.mlp = mlp
         with pytest.raises(B.CofemError) as e:
             api.fit_batched(phis, ys, betas, seeds, q)
         assert e.value.code == 6

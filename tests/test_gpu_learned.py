@@ -213,3 +213,105 @@ def test_untrustworthy_prediction_falls_back_to_plain_cg(cuda_lib):
                                          pr.beta, 16, em, 1e-5, cap, predict, seed=60)
     assert rst.fallbacks == [0] + [1] * (em - 1)
     assert rel_l2(rl.mu.cpu().numpy(), rmu) <= 1e-4
+
+
+# ------------------------------------ learned start on the tensor cores
+
+def _oracle_learned(Phi, y, beta, K, em, tol, cap, th, seed):
+    pn2 = np.sum(Phi * Phi, axis=0).astype(np.float32).astype(np.float64)
+
+    def predict(alpha, mu_prev, s_prev):
+        o, _ = omlp.forward(th, omlp.features(alpha, pn2, beta, mu_prev, s_prev))
+        return omlp.predict(o, alpha, pn2, beta)
+
+    phi, phit, D = sbl.dense_dictionary(Phi)
+    return sbl.cofem_learned(phi, phit, D, y, beta, K, em, tol, cap, predict, seed=seed)
+
+
+def test_learned_fit_tensor_core_bf16(cuda_lib, net):
+    """The learned start with a BF16 dictionary on the tensor cores (P's BF16
+    terms written by the warm-start initialisation and the preconditioned
+    direction update) against the oracle's learned loop on the BF16-rounded
+    dictionary (reading R12)."""
+    pr = datagen.dense_problem(256, 1024, 51, 0.1, 51)
+    t16 = torch.from_numpy(pr.Phi).to(torch.bfloat16)
+    Phi64 = t16.double().numpy()
+    op = api.DenseOperator(t16.cuda())
+    y32 = pr.y.astype(np.float32)
+    p = api.params(vec_dtype=B.COFEM_F32, K=16, em_iters=15, cg_tol=1e-5, cg_max_iters=400,
+                   seed=51)
+    p.mlp = net.bf16.data_ptr()
+    r = api.fit(op, torch.from_numpy(y32).cuda(), pr.beta, p)
+    torch.cuda.synchronize()
+    ra, rmu, rs, rst = _oracle_learned(Phi64, y32.astype(np.float64), pr.beta, 16, 15, 1e-5, 400,
+                                       net.bf16.double().cpu().numpy(), 51)
+    assert rel_l2(r.mu.cpu().numpy(), rmu) <= 1e-4
+    eq, _ = support_compare(r.alpha.cpu().numpy(), ra)
+    assert eq
+    assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.1 * sum(rst.cg_iters)
+    assert B.cofem_last_fit_fallbacks() == sum(rst.fallbacks)
+
+
+SIZES = [128, 150, 300, 511, 640, 1000]
+
+
+def _batch(sigma=0.1, seed0=7):
+    phis, ys, betas, seeds, refs = [], [], [], [], []
+    for i, N in enumerate(SIZES):
+        prob = datagen.dense_problem(N, 4 * N, max(1, N // 5), sigma, seed=seed0 + i)
+        t16 = torch.from_numpy(prob.Phi).to(torch.bfloat16)
+        y32 = prob.y.astype(np.float32)
+        phis.append(t16.cuda())
+        ys.append(torch.from_numpy(y32).cuda())
+        betas.append(prob.beta)
+        seeds.append(2000 + i)
+        refs.append((t16.double().numpy(), y32.astype(np.float64), prob.beta))
+    return phis, ys, betas, seeds, refs
+
+
+def test_batched_learned_matches_oracle_learned_loop(cuda_lib, net):
+    """The combined form: learned start + BF16 tensor cores + batching.  Six
+    problems of uneven size in one batched fit with the network, each against
+    the oracle's learned loop on its own BF16-rounded dictionary; fallback
+    counts equal in total."""
+    phis, ys, betas, seeds, refs = _batch()
+    em, K, tol = 15, 16, 1e-5
+    p = api.params(vec_dtype=B.COFEM_F32, K=K, em_iters=em, cg_tol=tol, cg_max_iters=400)
+    p.mlp = net.bf16.data_ptr()
+    alphas, mus, ss, st = api.fit_batched(phis, ys, betas, seeds, p)
+    torch.cuda.synchronize()
+    fb = B.cofem_last_fit_fallbacks()
+    th = net.bf16.double().cpu().numpy()
+    ofb = 0
+    for i, (Phi64, y64, beta) in enumerate(refs):
+        ra, rmu, rs, rst = _oracle_learned(Phi64, y64, beta, K, em, tol, 400, th, seeds[i])
+        ofb += sum(rst.fallbacks)
+        assert rel_l2(mus[i].cpu().numpy(), rmu) <= 1e-4, (i, rel_l2(mus[i].cpu().numpy(), rmu))
+        eq, border = support_compare(alphas[i].cpu().numpy(), ra)
+        assert eq, (i, border)
+        tot_b, tot_o = sum(st["cg_iters"][i]), sum(rst.cg_iters)
+        assert abs(tot_b - tot_o) <= 0.1 * tot_o, (i, tot_b, tot_o)
+    assert fb == ofb
+
+
+def test_batched_learned_fallback_equals_plain_batched(cuda_lib):
+    """A network that cannot be trusted (s_hat = e^40 / c_d): from the second
+    E-step on every problem's learned solve hits the cap and is rerun as
+    plain CG from zero, so the batched fit returns the plain batched fit's
+    results with cap + plain iterations per E-step."""
+    th = np.zeros(omlp.N_PARAMS)
+    omlp.unpack(th)["b3"][:] = [0.0, 10.0]
+    w = torch.from_numpy(th).to(torch.bfloat16).cuda()
+    phis, ys, betas, seeds, refs = _batch()
+    em, cap = 4, 150
+    p = api.params(vec_dtype=B.COFEM_F32, K=16, em_iters=em, cg_tol=1e-5, cg_max_iters=cap)
+    ap, mp, sp, stp = api.fit_batched(phis, ys, betas, seeds, p)
+    p.mlp = w.data_ptr()
+    al, ml, sl, stl = api.fit_batched(phis, ys, betas, seeds, p)
+    torch.cuda.synchronize()
+    assert B.cofem_last_fit_fallbacks() == (em - 1) * len(phis)
+    for i in range(len(phis)):
+        assert stl["cg_iters"][i][0] == stp["cg_iters"][i][0]
+        for t in range(1, em):
+            assert stl["cg_iters"][i][t] == cap + stp["cg_iters"][i][t], (i, t)
+        assert torch.equal(ml[i], mp[i]) and torch.equal(al[i], ap[i]), i

@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched-512-n128-2048", "conv-l1m-c8-t64",
                              "dense-fp64-n256-d1024", "learned-dense-n256-d1024", "dct-d262144",
-                             "multitask-n4096-d32768-t4"],
+                             "multitask-n4096-d32768-t4", "combined-128-n128-2048"],
                     help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-whole-fit", action="store_true",
@@ -613,6 +613,124 @@ def run_fp64(args):
                           "kernel": "whole CG loop (Phi in L2)"}})
 
 
+def train_network(api, B, seeds=range(1, 65), steps=4000):
+    """The learned start's network, trained on the GPU by the library's own
+    kernels: samples from E-steps 2..20 of plain fits of the N = 256,
+    D = 1024 problems with the given seeds (config 1 shape), Adam.  Returns
+    (network, samples, losses, collect seconds, train seconds)."""
+    import torch
+    c = datagen.CONFIGS["dense-fp64-n256-d1024"]
+    kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"])
+    t0 = time.perf_counter()
+    Us, Ys = [], []
+    for sd in seeds:
+        pr = datagen.dense_problem(c["N"], c["D"], c["n_nonzero"], c["sigma"], sd)
+        op = api.DenseOperator(torch.from_numpy(pr.Phi).cuda())
+        y = torch.from_numpy(pr.y.astype(np.float32)).cuda()
+        U, Y = api.collect_training_data(op, y, pr.beta, api.params(em_iters=20, seed=sd, **kw), 20)
+        Us.append(U)
+        Ys.append(Y)
+    U, Y = torch.cat(Us), torch.cat(Ys)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    net = api.LearnedWarmStart(seed=0)
+    t0 = time.perf_counter()
+    losses = net.train(U, Y, steps, lr=3e-3, batch=65536)
+    torch.cuda.synchronize()
+    return net, U, losses, t_collect, time.perf_counter() - t0
+
+
+def run_combined(args):
+    """The three production patterns together against plain FP32 GPU CoFEM on
+    the same problems: 128 dense problems of the batched workload's size law
+    (N uniform on [128, 2048], D = 4N, 5% nonzeros, sigma 0.01, K 16, CG tol
+    1e-5, 50 EM iterations), data drawn from FP32 dictionaries.
+      plain FP32: one cofem_fit per problem, FP32 dictionary on the tensor
+                  cores (hi + lo packed, 4 B per entry), plain CG;
+      combined:   one cofem_fit_batched over all problems, BF16 dictionaries,
+                  the learned warm start / preconditioner (network trained on
+                  the GPU as in the learned workload);
+      ablation:   the same batched BF16 fit without the network.
+    Every arm stops its solves at the same relative residual; supports are
+    compared per problem at the end (alpha < 1e6, borderline excluded)."""
+    import torch
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    c = datagen.CONFIGS["batched-512-n128-2048"]
+    nprob, em = 128, c["em_iters"]
+    probs = datagen.batched_problems_torch_f32(nprob, c["n_min"], c["n_max"], c["ratio"],
+                                               c["frac_nonzero"], c["sigma"], args.seed)
+    kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"])
+    net, U, losses, t_collect, t_train = train_network(api, B)
+    # plain FP32 comparator: operators prepared (packed hi + lo) outside the timing
+    ops, keep = [], []
+    for Phi, z, y, beta, sd in probs:
+        op = api.DenseOperator(Phi)
+        nb = B.cofem_op_dense_packed_bytes(op.handle)
+        pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        B.cofem_op_dense_attach_packed(op.handle, pk.data_ptr(), nb)
+        ops.append(op)
+        keep.append(pk)
+    torch.cuda.synchronize()
+    wsmax = max(B.cofem_workspace_bytes(op.handle, api.params(em_iters=em, **kw)) for op in ops)
+    ws = torch.empty(wsmax, dtype=torch.uint8, device="cuda")
+    res32, cg32 = [], 0
+    with ClockSampler(0) as clk:
+        def plain():
+            out = []
+            for (Phi, z, y, beta, sd), op in zip(probs, ops):
+                out.append(api.fit(op, y, beta, api.params(em_iters=em, seed=sd, **kw), ws=ws))
+            return out
+        res32, t32 = _timed(plain)
+        phis16 = [P.to(torch.bfloat16) for P, _, _, _, _ in probs]
+        ys = [q[2] for q in probs]
+        betas = [q[3] for q in probs]
+        seeds = [q[4] for q in probs]
+        p = api.params(em_iters=em, **kw)
+        (ab, mb, sb, stb), tb = _timed(lambda: api.fit_batched(phis16, ys, betas, seeds, p))
+        p.mlp = net.bf16.data_ptr()
+        (al, ml, sl, stl), tl = _timed(lambda: api.fit_batched(phis16, ys, betas, seeds, p))
+        fallbacks = B.cofem_last_fit_fallbacks()
+    thr = 1e6
+
+    def same_support(a, r):
+        a, r = a.cpu().numpy(), r.cpu().numpy()
+        border = ((a > thr / 2) & (a < thr * 2)) | ((r > thr / 2) & (r < thr * 2))
+        return bool(np.array_equal((a < thr) & ~border, (r < thr) & ~border))
+
+    eq_l = sum(same_support(al[i], res32[i].alpha) for i in range(nprob))
+    eq_b = sum(same_support(ab[i], res32[i].alpha) for i in range(nprob))
+    nrmse = lambda mu, z: float((mu - z).norm() / z.norm())
+    cg32 = sum(sum(r.stats["cg_iters"]) for r in res32)
+    cgl = int(np.sum(stl["cg_iters"]))
+    cgb = int(np.sum(stb["cg_iters"]))
+    relres_max = {"plain_fp32": max(max(r.stats["relres"]) for r in res32),
+                  "combined": float(np.max(stl["relres"])),
+                  "batched_bf16": float(np.max(stb["relres"]))}
+    rate = lambda t: nprob * em / t
+    _common(args, "problem EM iters/s, learned + BF16 + batched vs plain FP32 GPU CoFEM "
+                  "(128 dense problems, N~U[128,2048], D=4N, K=16, tol 1e-5, 50 EM iterations)",
+            "problem EM iters/s", rate(tl), tl, "f32 vectors, bf16 Phi, bf16 network",
+            {"workload": "combined-128-n128-2048", "problems": nprob, "K": c["K"],
+             "em_iters": em, "cg_tol": c["cg_tol"], "sigma": c["sigma"],
+             "data": "FP32 dictionaries (the BF16 arms round them)"},
+            {"plain_fp32_em_iters_per_s": rate(t32),
+             "batched_bf16_em_iters_per_s": rate(tb),
+             "speedup_vs_plain_fp32": t32 / tl,
+             "speedup_batched_bf16_only": t32 / tb,
+             "cg_iters_total": {"plain_fp32": int(cg32), "combined": cgl, "batched_bf16": cgb},
+             "fallbacks": int(fallbacks),
+             "same_support_as_plain_fp32": {"combined": eq_l, "batched_bf16": eq_b, "of": nprob},
+             "max_relres": relres_max,
+             "nrmse_mu_vs_truth_mean": {
+                 "plain_fp32": float(np.mean([nrmse(res32[i].mu, probs[i][1]) for i in range(nprob)])),
+                 "combined": float(np.mean([nrmse(ml[i], probs[i][1]) for i in range(nprob)]))},
+             "seconds": {"plain_fp32": t32, "combined": tl, "batched_bf16": tb},
+             "network": {"samples": int(U.shape[0]), "collect_s": t_collect, "train_s": t_train,
+                         "loss_first": losses[0], "loss_last": losses[-1]},
+             "clocks": clk.summary()})
+
+
 def run_learned(args):
     """Learned warm start / preconditioner: train on E-steps 2..20 of the
     256 x 1024 problems with seeds 1..64, evaluate CG iterations and EM
@@ -629,21 +747,7 @@ def run_learned(args):
             torch.from_numpy(pr.y.astype(np.float32)).cuda()
 
     kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"])
-    t0 = time.perf_counter()
-    Us, Ys = [], []
-    for sd in range(1, 65):
-        pr, op, y = prob(sd)
-        U, Y = api.collect_training_data(op, y, pr.beta, api.params(em_iters=20, seed=sd, **kw), 20)
-        Us.append(U)
-        Ys.append(Y)
-    U, Y = torch.cat(Us), torch.cat(Ys)
-    torch.cuda.synchronize()
-    t_collect = time.perf_counter() - t0
-    net = api.LearnedWarmStart(seed=0)
-    t0 = time.perf_counter()
-    losses = net.train(U, Y, 4000, lr=3e-3, batch=65536)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    net, U, losses, t_collect, t_train = train_network(api, B)
     em = c["em_iters"]
     # control: the all-zero network predicts mu_hat = 0 and s_hat = 1/c_d, i.e.
     # Jacobi-preconditioned CG from X0 = [0 | p_k / c_d]
@@ -789,6 +893,8 @@ def main():
         return run_dct(args)
     if args.workload == "multitask-n4096-d32768-t4":
         return run_multitask(args)
+    if args.workload == "combined-128-n128-2048":
+        return run_combined(args)
     import torch
     import torch.distributed as dist
     from paper_2202_12808_gb300 import api

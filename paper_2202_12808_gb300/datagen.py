@@ -174,6 +174,29 @@ CONFIGS = {
 }
 
 
+def batched_problems_torch_f32(n_problems, n_min, n_max, ratio, frac_nonzero, sigma, seed,
+                               device="cuda"):
+    """The problems of batched_problems_torch (same sizes and seeds) with the
+    dictionary kept in FP32: Phi_i iid N(0, 1/N_i) float32 and y_i = Phi_i z_i
+    + N(0, sigma^2) from that FP32 dictionary.  A path that stores Phi_i in
+    BF16 then approximates the dictionary the data came from.  Returns a list
+    of (Phi_i float32 N_i x D_i, z_i float64, y_i float32, beta, seed_i)."""
+    import torch
+    out = []
+    for N, D, s in batched_sizes(n_problems, n_min, n_max, ratio, seed):
+        g = torch.Generator(device=device)
+        g.manual_seed(s)
+        Phi = torch.randn((N, D), generator=g, device=device) / float(np.sqrt(N))
+        k = max(1, int(round(frac_nonzero * D)))
+        idx = torch.randperm(D, generator=g, device=device)[:k]
+        z = torch.zeros(D, dtype=torch.float64, device=device)
+        z[idx] = torch.randn(k, generator=g, device=device, dtype=torch.float64)
+        noise = sigma * torch.randn(N, generator=g, device=device, dtype=torch.float64)
+        y = (Phi.double()[:, idx] @ z[idx] + noise).float()
+        out.append((Phi, z, y, 1.0 / sigma ** 2, s))
+    return out
+
+
 def batched_problems_torch(n_problems, n_min, n_max, ratio, frac_nonzero, sigma, seed,
                            device="cuda"):
     """Many dense problems (N_i uniform on [n_min, n_max], D_i = ratio N_i,

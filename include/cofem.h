@@ -438,6 +438,23 @@ size_t cofem_noalloc_scratch_capacity(void);
  * limit outside the range.  Synchronous on `stream`. */
 cofem_status cofem_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
+/* Self-test of the CG update's bounded wait (the paper has no counterpart).
+ * Where the fit folds the direction update into the CG update, every block
+ * but the one that closes the iteration waits for that block, with a time
+ * limit (2 s in a fit); a wait that runs out records COFEM_ERR_TIMEOUT, ends
+ * the CG loops and returns, and every later update launch of the fit ends
+ * them at once.  This call runs one such launch (2 columns of 4096 values, 8
+ * blocks, all resident at once) in which no block is the closing one, with a
+ * limit of limit_ns nanoseconds (1e3 .. 1e9), on workspace_dev (>=
+ * cofem_selftest_cg_update_workspace_bytes(), any alignment; overwritten),
+ * and reads the error word back.  Returns COFEM_ERR_TIMEOUT when the waits
+ * ran out (the expected result), COFEM_ERR_INVALID_ARG for a limit outside
+ * the range or a null workspace, COFEM_ERR_WORKSPACE if it is too small.
+ * Synchronous on `stream`. */
+size_t cofem_selftest_cg_update_workspace_bytes(void);
+cofem_status cofem_selftest_cg_update_timeout(int64_t limit_ns, void* workspace_dev,
+                                              size_t workspace_bytes, void* stream);
+
 /* The two halves: W = Phi Z (ncols columns of length N, leading dimension
  * ldw) and Z = Phi^T W (length D, leading dimension ldz).  Used for
  * b = beta Phi^T y.  Same workspace rule as cofem_op_apply. Asynchronous. */

@@ -104,6 +104,8 @@ _SIGS = {
     "cofem_op_apply_noalloc": (_S, [_P, _S, _P, _I64, _I32, _P, _D, _P, _P]),
     "cofem_noalloc_scratch_capacity": (_SZ, []),
     "cofem_selftest_wait_timeout": (_S, [_I64, _P]),
+    "cofem_selftest_cg_update_workspace_bytes": (_SZ, []),
+    "cofem_selftest_cg_update_timeout": (_S, [_I64, _P, _SZ, _P]),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_diag_mstep": (_S, [ctypes.c_uint64, _I64, _I32, _I64, _S, _P, _I64, _D, _D, _P,
@@ -311,6 +313,15 @@ def cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, st
 
 def cofem_noalloc_scratch_capacity():
     return lib().cofem_noalloc_scratch_capacity()
+
+
+def cofem_selftest_cg_update_workspace_bytes():
+    return lib().cofem_selftest_cg_update_workspace_bytes()
+
+
+def cofem_selftest_cg_update_timeout(limit_ns, ws_ptr, ws_bytes, stream=0):
+    """Returns the status code (5 = the waits ran out, as expected)."""
+    return lib().cofem_selftest_cg_update_timeout(limit_ns, ws_ptr, ws_bytes, stream)
 
 
 def cofem_selftest_wait_timeout(limit_ns, stream=0):

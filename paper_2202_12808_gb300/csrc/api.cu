@@ -717,6 +717,20 @@ cofem_status cofem_selftest_wait_timeout(int64_t limit_ns, void* stream) {
   return r == 0 ? COFEM_OK : (cofem_status)r;
 }
 
+size_t cofem_selftest_cg_update_workspace_bytes(void) { return cg_update_selftest_bytes(); }
+
+cofem_status cofem_selftest_cg_update_timeout(int64_t limit_ns, void* workspace_dev,
+                                              size_t workspace_bytes, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 1000000000 || !workspace_dev) return COFEM_ERR_INVALID_ARG;
+  if (workspace_bytes < cg_update_selftest_bytes()) return COFEM_ERR_WORKSPACE;
+  const int r = cg_update_selftest(limit_ns, (char*)workspace_dev, (cudaStream_t)stream);
+  if (r < 0) {
+    set_error("CG update self-test", cudaGetLastError(), __FILE__, __LINE__);
+    return COFEM_ERR_CUDA;
+  }
+  return r == 0 ? COFEM_OK : (cofem_status)r;
+}
+
 cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void* phi_dev,
                             int64_t ld, const float* tile_scales_dev, cofem_op** out) {
   if (!out || !phi_dev || N < 1 || D < 1 || ld < D) return COFEM_ERR_INVALID_ARG;

@@ -8,6 +8,8 @@
 // mean system, columns 1..K the probes.  Every per-column dot product is
 // accumulated in double, reduced per block by warp shuffles, then summed
 // over blocks in a fixed order by the last block to arrive (deterministic).
+#include <cstring>
+
 #include "kernels.cuh"
 
 namespace cofem {
@@ -128,6 +130,10 @@ __device__ void cg_finalize(const CgConf& cf, CgCtl* ctl, CgScalars* sc) {
     else if (cf.stop_rule == 1) done = nlive == 0 || it >= cf.max_iters;
     else done = (relres < cf.tol) || (it >= cf.max_iters);
     if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+    // a block of this launch that gave up its wait has ended the loops: do
+    // not restart them (a timeout raised after this read still ends them at
+    // the next update launch, which checks the error word first)
+    if (*(volatile int*)&ctl->error == (int)COFEM_ERR_TIMEOUT) done = 1;
     ctl->done = done;
     ctl->run = !done;
     set_cond(cf.while_handle, done ? 0u : 1u);
@@ -477,7 +483,7 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
         __threadfence();
         atomicAdd(&ctl->dir_gen, 1u);
       } else {
-        go = wait_gen(&ctl->dir_gen, g0, kGenWaitNs);
+        go = wait_gen(&ctl->dir_gen, g0, cf.gen_wait_ns ? cf.gen_wait_ns : kGenWaitNs);
         if (!go) {
           raise_error(ctl, COFEM_ERR_TIMEOUT);
           set_cond(cf.while_handle, 0u);
@@ -792,5 +798,54 @@ void launch_scale(V* x, int64_t n, double beta, cudaStream_t st) {
   template void launch_scale<V>(V*, int64_t, double, cudaStream_t);
 COFEM_INST(float)
 COFEM_INST(double)
+
+
+// Self-test of the fused update's bounded wait: one launch of the update with
+// the direction update over 2 columns of 4096 values (8 blocks, all resident)
+// whose arrival counter starts far past the grid size, so that no block is
+// the last one and every other block's wait for the closing block runs out
+// after limit_ns.  Workspace: control, scalars, partials, four blocks.
+size_t cg_update_selftest_bytes() {
+  return 4096 + sizeof(CgCtl) + sizeof(CgScalars) + 3 * 8 * kMaxCols * sizeof(double) +
+         4 * 2 * 4096 * sizeof(float);
+}
+
+int cg_update_selftest(int64_t limit_ns, char* ws, cudaStream_t st) {
+  char* o = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  CgCtl* ctl = (CgCtl*)o;
+  o += (sizeof(CgCtl) + 255) & ~(size_t)255;
+  CgScalars* sc = (CgScalars*)o;
+  o += (sizeof(CgScalars) + 255) & ~(size_t)255;
+  double* gparts = (double*)o;
+  double* part = gparts + 8 * kMaxCols;
+  double* part2 = part + 8 * kMaxCols;
+  float* X = (float*)(part2 + 8 * kMaxCols);
+  float* R = X + 2 * 4096;
+  float* P = R + 2 * 4096;
+  float* Q = P + 2 * 4096;
+  if (cudaMemsetAsync(ws, 0, cg_update_selftest_bytes(), st) != cudaSuccess) return -1;
+  const unsigned int far = 1u << 30;
+  if (cudaMemcpyAsync(&ctl->counter[1], &far, sizeof(far), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return -1;
+  CgConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.D = 4096;
+  cf.ld = 4096;
+  cf.ncols = 2;
+  cf.K = 1;
+  cf.T = 1;
+  cf.tol = 1e-6;
+  cf.max_iters = 10;
+  cf.gen_wait_ns = (unsigned long long)limit_ns;
+  cg_update_kernel<float, true><<<dim3(4, 2), dim3(256), 0, st>>>(cf, ctl, sc, X, R, P, Q,
+                                                                  gparts, part, part2);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  return err;
+}
 
 }  // namespace cofem

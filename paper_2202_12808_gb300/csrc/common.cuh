@@ -77,6 +77,8 @@ struct CgConf {
   int gate_run;                      // CG update: do nothing unless ctl->run (an unrolled copy)
   long long* st_end_ns;              // per EM iteration: device clock at the end of its M-step,
                                      // ns since the fit's first kernel (ctl->start_ns), or null
+  unsigned long long gen_wait_ns;    // CG update with the direction update: limit of the
+                                     // wait for the closing block (0: 2 s)
 };
 
 // Row of the tensor-core B operand that holds BF16 term t of column j when

@@ -51,6 +51,11 @@ void launch_col_norms_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, fl
                            cudaStream_t st);
 // cofem_last_fit_fallbacks of this thread (set by the batched fit).
 void set_last_fit_fallbacks(int n);
+// Self-test of the fused CG update's bounded wait (cg_kernels.cu): returns the
+// error word after one launch in which no block closes the iteration, or -1
+// on a CUDA error.  ws: cg_update_selftest_bytes() bytes.
+size_t cg_update_selftest_bytes();
+int cg_update_selftest(int64_t limit_ns, char* ws, cudaStream_t st);
 
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,

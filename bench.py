@@ -804,6 +804,36 @@ def run_learned(args):
                                "fallbacks": int(conv_fb)}})
 
 
+def cg_kernels_section(B, dev, peak, ncols):
+    """The CG vector kernels outside the fit graph (cofem_bench_cg_kernels):
+    the CG update with the direction update and P's BF16 terms fused, the
+    stand-alone direction update, and the diagonal estimate + M-step, at the
+    headline's D = 32768 (33 columns: 17 MB, L2-resident between launches)
+    and at D = 2^20 (557 MB per block set, streamed from HBM).  Algorithmic
+    bytes per launch: update 34 nc D with the direction fused (read x, r, p,
+    q; write x, r, p and three BF16 terms of p), 24 nc D alone; direction
+    18 nc D; M-step 4 nc D + 28 D."""
+    import torch
+    out = {}
+    for D in (CFG["D"], 1 << 20):
+        nb = B.cofem_bench_cg_kernels_workspace_bytes(D, ncols)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        ms = B.cofem_bench_cg_kernels(D, ncols, 20, ws.data_ptr(), nb,
+                                      torch.cuda.current_stream().cuda_stream)
+        del ws
+        fused = ms[3] > 0.5
+        byts = [(34 if fused else 24) * ncols * D, 18 * ncols * D, 4 * ncols * D + 28 * D]
+        ent = {"update_holds_direction": fused}
+        for name, m, b in zip(["cg_update", "cg_direction", "diag_mstep"], ms[:3], byts):
+            gbs = b / (m / 1e3) / 1e9
+            ent[name] = {"us": round(m * 1e3, 2), "algorithmic_bytes": b, "achieved_gbs": gbs,
+                         "frac_of_hbm": gbs / peak}
+        out["D=%d" % D] = ent
+    out["note"] = ("CUDA events around single launches include the launch gap; at D = 32768 "
+                   "the block set fits in L2, so the rate there can exceed the HBM roof")
+    return out
+
+
 def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
     """The whole 100-EM-iteration fit of the headline workload, twice: the
     BF16 dictionary (the bench's operator) and the plain FP32 comparator (the
@@ -1078,6 +1108,8 @@ def main():
                        "h2d_bytes_per_step": h2d // args.steps,
                        "d2h_bytes_per_step": 3 * D * 8 // args.steps}
 
+    if rank == 0:
+        line["cg_kernels"] = cg_kernels_section(B, dev, peak, ncols)
     if rank == 0 and not args.no_whole_fit and args.phi == "bf16" and args.terms == 3:
         line["fit_100"] = fit_100_section(api, B, prob, op, y, kw, dev, peak)
 

@@ -451,6 +451,23 @@ cofem_status cofem_selftest_wait_timeout(int64_t limit_ns, void* stream);
  * ran out (the expected result), COFEM_ERR_INVALID_ARG for a limit outside
  * the range or a null workspace, COFEM_ERR_WORKSPACE if it is too small.
  * Synchronous on `stream`. */
+/* Timing of the CG vector kernels outside a fit graph (diagnostics; the paper
+ * has no counterpart).  Builds a synthetic CG state of ncols (2..64) FP32
+ * columns of D values on workspace_dev (>= cofem_bench_cg_kernels_workspace_
+ * bytes(D, ncols) bytes, any alignment; overwritten), then times `reps`
+ * launches (after one warm-up launch) each of: the CG update x += a p,
+ * r -= a q, r^T r with the direction update p = r + b p and P's three BF16
+ * terms fused into the same launch where its grid is resident (as cofem_fit
+ * launches it for the tensor-core operator), the stand-alone direction
+ * update, and the fused diagonal estimate + M-step; CUDA events on
+ * `stream`.  ms_out[0..2] = mean milliseconds per launch of each; ms_out[3]
+ * = 1 if the update's launch held the direction update, 0 if its grid was
+ * too large to be resident at once (the update alone was timed).
+ * Synchronous. */
+size_t cofem_bench_cg_kernels_workspace_bytes(int64_t D, int32_t ncols);
+cofem_status cofem_bench_cg_kernels(int64_t D, int32_t ncols, int32_t reps, void* workspace_dev,
+                                    size_t workspace_bytes, void* stream, float* ms_out);
+
 size_t cofem_selftest_cg_update_workspace_bytes(void);
 cofem_status cofem_selftest_cg_update_timeout(int64_t limit_ns, void* workspace_dev,
                                               size_t workspace_bytes, void* stream);

@@ -105,6 +105,8 @@ _SIGS = {
     "cofem_noalloc_scratch_capacity": (_SZ, []),
     "cofem_selftest_wait_timeout": (_S, [_I64, _P]),
     "cofem_selftest_cg_update_workspace_bytes": (_SZ, []),
+    "cofem_bench_cg_kernels_workspace_bytes": (_SZ, [_I64, _I32]),
+    "cofem_bench_cg_kernels": (_S, [_I64, _I32, _I32, _P, _SZ, _P, ctypes.POINTER(ctypes.c_float)]),
     "cofem_selftest_cg_update_timeout": (_S, [_I64, _P, _SZ, _P]),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
@@ -313,6 +315,19 @@ def cofem_op_apply_noalloc(op, vec, x_ptr, ld, ncols, alpha_ptr, beta, y_ptr, st
 
 def cofem_noalloc_scratch_capacity():
     return lib().cofem_noalloc_scratch_capacity()
+
+
+def cofem_bench_cg_kernels_workspace_bytes(D, ncols):
+    return lib().cofem_bench_cg_kernels_workspace_bytes(D, ncols)
+
+
+def cofem_bench_cg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream=0):
+    """Mean milliseconds per launch (CG update, direction update, diag/M-step)
+    and whether the update held the direction update (1.0) or not (0.0)."""
+    ms = (ctypes.c_float * 4)()
+    _check(lib().cofem_bench_cg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream, ms),
+           "cofem_bench_cg_kernels")
+    return tuple(ms)
 
 
 def cofem_selftest_cg_update_workspace_bytes():

@@ -848,4 +848,108 @@ int cg_update_selftest(int64_t limit_ns, char* ws, cudaStream_t st) {
   return err;
 }
 
+
+// Timing of the CG vector kernels outside a fit graph (diagnostics): a
+// synthetic state of ncols columns of D FP32 values (every column with
+// rho_j = 1 and gamma_j = 1), then `reps` launches each of the CG update
+// (with the direction update fused where its grid is resident, as in the
+// fit, and P's three BF16 terms written), the separate direction update, and
+// the diagonal estimate + M-step, each timed with CUDA events on `st`.
+// ms[0..2] = mean milliseconds per launch, ms[3] = 1 if the update's launch
+// held the direction update (its grid resident at once), else 0; returns 0,
+// or -1 on a CUDA error.
+static int64_t cgb_ld(int64_t D) { return round_up(D, kLdAlign); }
+static int cgb_bn(int ncols) { return 16 * ((ncols + 4) / 5); }
+size_t cg_kernels_bench_bytes(int64_t D, int ncols) {
+  const int64_t ld = cgb_ld(D);
+  return 4096 + sizeof(CgCtl) + sizeof(CgScalars) + 3 * (size_t)kMaxParts * kMaxCols * 8 +
+         4 * (size_t)ncols * ld * 4 + (size_t)cgb_bn(ncols) * ld * 2 + 3 * (size_t)ld * 8 +
+         (size_t)ld * 4 + 8 * 256;
+}
+
+__global__ void cgb_fill_kernel(float* v, int64_t n, uint32_t salt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = mix64((uint64_t)i * 0x9E3779B97F4A7C15ull ^ salt);
+    v[i] = (float)((double)(h >> 40) / (double)(1ull << 24) - 0.5);
+  }
+}
+
+__global__ void cgb_reset_kernel(CgCtl* ctl, CgScalars* sc, double* gparts, int ncols) {
+  const int j = threadIdx.x;
+  if (j < ncols) {
+    sc->rho[j] = 1.0;
+    gparts[j] = 1.0;
+  }
+  if (j == 0) {
+    ctl->normB2 = 1.0;
+    ctl->error = 0;
+    ctl->run = 1;
+  }
+}
+
+int cg_kernels_bench(int64_t D, int ncols, int reps, char* ws, cudaStream_t st, float* ms) {
+  const int64_t ld = cgb_ld(D);
+  auto al = [](char* p) { return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); };
+  char* o = al(ws);
+  CgCtl* ctl = (CgCtl*)o;                    o = al(o + sizeof(CgCtl));
+  CgScalars* sc = (CgScalars*)o;             o = al(o + sizeof(CgScalars));
+  double* gparts = (double*)o;               o = al(o + (size_t)kMaxParts * kMaxCols * 8);
+  double* part = (double*)o;                 o = al(o + (size_t)kMaxParts * kMaxCols * 8);
+  double* part2 = (double*)o;                o = al(o + (size_t)kMaxParts * kMaxCols * 8);
+  float* X = (float*)o;                      o = al(o + (size_t)ncols * ld * 4);
+  float* R = (float*)o;                      o = al(o + (size_t)ncols * ld * 4);
+  float* P = (float*)o;                      o = al(o + (size_t)ncols * ld * 4);
+  float* Q = (float*)o;                      o = al(o + (size_t)ncols * ld * 4);
+  __nv_bfloat16* xs = (__nv_bfloat16*)o;     o = al(o + (size_t)cgb_bn(ncols) * ld * 2);
+  double* mu = (double*)o;                   o = al(o + (size_t)ld * 8);
+  double* s = (double*)o;                    o = al(o + (size_t)ld * 8);
+  double* alpha = (double*)o;                o = al(o + (size_t)ld * 8);
+  float* alpha32 = (float*)o;
+  if (cudaMemsetAsync(ws, 0, cg_kernels_bench_bytes(D, ncols), st) != cudaSuccess) return -1;
+  cgb_fill_kernel<<<1024, 256, 0, st>>>(X, 4 * (int64_t)ncols * ld, 7u);
+  CgConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.D = D;
+  cf.ld = ld;
+  cf.ncols = ncols;
+  cf.K = ncols - 1;
+  cf.T = 1;
+  cf.seed = 1;
+  cf.tol = 0.0;
+  cf.max_iters = 1 << 30;
+  cf.den_floor = 1e-12;
+  cf.support_threshold = 1e6;
+  cf.gamma_parts = 1;
+  cf.split_nt = 3;
+  cf.split_rows = cgb_bn(ncols);
+  cf.split_buf = xs;
+  cf.alpha32 = alpha32;
+  cudaEvent_t ev[2];
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return -1;
+  bool fused = false;
+  for (int k = 0; k < 3; ++k) {
+    float tot = 0.f;
+    for (int r = 0; r < reps + 1; ++r) {
+      cgb_reset_kernel<<<1, 64, 0, st>>>(ctl, sc, gparts, ncols);
+      cudaEventRecord(ev[0], st);
+      if (k == 0)
+        fused = launch_cg_update<float>(cf, ctl, sc, X, R, P, Q, gparts, part, part2, st, true);
+      else if (k == 1) launch_cg_direction<float>(cf, ctl, sc, R, P, st);
+      else launch_diag_mstep<float>(cf, nullptr, probe_key(cf.seed, 1), X, mu, s, alpha, nullptr,
+                                    nullptr, nullptr, nullptr, nullptr, st);
+      cudaEventRecord(ev[1], st);
+      if (cudaEventSynchronize(ev[1]) != cudaSuccess) return -1;
+      float m = 0.f;
+      cudaEventElapsedTime(&m, ev[0], ev[1]);
+      if (r > 0) tot += m;                   // the first launch warms up
+    }
+    ms[k] = tot / (float)reps;
+  }
+  ms[3] = fused ? 1.f : 0.f;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace cofem

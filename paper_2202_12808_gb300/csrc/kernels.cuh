@@ -56,6 +56,9 @@ void set_last_fit_fallbacks(int n);
 // on a CUDA error.  ws: cg_update_selftest_bytes() bytes.
 size_t cg_update_selftest_bytes();
 int cg_update_selftest(int64_t limit_ns, char* ws, cudaStream_t st);
+// Timing of the CG vector kernels outside a fit graph (cg_kernels.cu).
+size_t cg_kernels_bench_bytes(int64_t D, int ncols);
+int cg_kernels_bench(int64_t D, int ncols, int reps, char* ws, cudaStream_t st, float* ms);
 
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,

@@ -100,9 +100,23 @@ cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms);
  * depend on it: query them after choosing the shape. */
 cofem_status cofem_op_dense_set_pipeline(cofem_op* op, int32_t stages, int32_t ctas_per_sm);
 
+/* Output rows of one tensor-core work unit: 128 (default) or 256.  With 256
+ * a CTA computes two 128-row output tiles from every B-operand stage it
+ * loads (one tensor-memory accumulator each), halving the B-operand traffic
+ * per byte of Phi; its accumulators then take all of an SM's tensor memory
+ * when BN > 64, so one CTA runs per SM.  cofem_op_dense_autotune tries both.
+ * Workspace sizes depend on it (query them after choosing). */
+cofem_status cofem_op_dense_set_tile_rows(cofem_op* op, int32_t rows);
+
+/* The tensor-core pipeline shape set on a dense handle (any pointer may be
+ * NULL): stages (0 = as deep as fits), CTAs per SM (0 = 2), tile rows. */
+cofem_status cofem_op_dense_get_pipeline(const cofem_op* op, int32_t* stages,
+                                         int32_t* ctas_per_sm, int32_t* tile_rows);
+
 /* Autotuner: times one operator application (ncols FP32 columns of made-up
  * data, 2 warm-up + 5 timed runs, CUDA events on `stream`) for every
- * pipeline shape that fits, keeps the fastest on the handle and returns it
+ * pipeline shape that fits (stages, CTAs per SM, 128 or 256 tile rows),
+ * keeps the fastest on the handle and returns it
  * (any output pointer may be NULL; best_us = mean microseconds per
  * application).  workspace_dev: >= cofem_op_dense_autotune_workspace_bytes,
  * 256-byte aligned.  Synchronous.  BF16 dictionaries on tensor cores only. */

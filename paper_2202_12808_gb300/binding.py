@@ -67,6 +67,9 @@ _SIGS = {
     "cofem_last_error": (ctypes.c_char_p, []),
     "cofem_op_dense": (_S, [_I64, _I64, _S, _P, _I64, _P, ctypes.POINTER(_P)]),
     "cofem_op_dense_set_terms": (_S, [_P, _I32]),
+    "cofem_op_dense_set_tile_rows": (_S, [_P, _I32]),
+    "cofem_op_dense_get_pipeline": (_S, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                         ctypes.POINTER(_I32)]),
     "cofem_op_dense_set_l2_resident": (_S, [_P, _I64]),
     "cofem_dense_packed_bytes": (_SZ, [_I64, _I64]),
     "cofem_op_dense_packed_bytes": (_SZ, [_P]),
@@ -162,6 +165,18 @@ def cofem_op_dense_set_terms(op, nterms):
 
 def cofem_op_dense_set_l2_resident(op, nbytes):
     _check(lib().cofem_op_dense_set_l2_resident(op, nbytes), "cofem_op_dense_set_l2_resident")
+
+
+def cofem_op_dense_set_tile_rows(op, rows):
+    _check(lib().cofem_op_dense_set_tile_rows(op, rows), "cofem_op_dense_set_tile_rows")
+
+
+def cofem_op_dense_get_pipeline(op):
+    """(stages, ctas_per_sm, tile_rows) of a dense handle's tensor-core pipeline."""
+    a, b, c = _I32(), _I32(), _I32()
+    _check(lib().cofem_op_dense_get_pipeline(op, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(c)), "cofem_op_dense_get_pipeline")
+    return a.value, b.value, c.value
 
 
 def cofem_op_dense_set_pipeline(op, stages, ctas_per_sm):

@@ -135,11 +135,12 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
     if (use_tc(op)) {
       DenseTcPlan q = dense_tc_plan(op->dense, ncols, num_sms());
       if (align256(q.total) > b) b = align256(q.total);
-      for (int cps = 1; max_shape && cps <= 4; ++cps) {
-        DenseTcPlan r = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
-                                      num_sms(), cps, 0, op->dense.phi_terms);
-        if (align256(r.total) > b) b = align256(r.total);
-      }
+      for (int mt = 1; max_shape && mt <= 2; ++mt)
+        for (int cps = 1; cps <= 4; ++cps) {
+          DenseTcPlan r = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
+                                        num_sms(), cps, 0, op->dense.phi_terms, mt);
+          if (align256(r.total) > b) b = align256(r.total);
+        }
     }
     return b;
   }
@@ -340,6 +341,10 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && op->kind == 2) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && n_tasks(p) > 1) return COFEM_ERR_UNSUPPORTED;
+  // the tensor-core operator writes one partial dot per 128-row tile of D
+  // (plus one when two tiles share a unit and their count is odd)
+  if (use_tc(op) && p->vec_dtype == COFEM_F32 && (op->dense.D + 127) / 128 + 1 > kMaxParts)
+    return COFEM_ERR_UNSUPPORTED;
   return COFEM_OK;
 }
 
@@ -771,6 +776,7 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   op->dense.tc_ctas_per_sm = 0;
   op->dense.tc_stages = 0;
   op->dense.phi_terms = dtype == COFEM_F32 ? 2 : 1;
+  op->dense.tc_row_tiles = 1;
   *out = op;
   return COFEM_OK;
 }
@@ -780,6 +786,21 @@ cofem_status cofem_op_dense_set_pipeline(cofem_op* op, int32_t stages, int32_t c
     return COFEM_ERR_INVALID_ARG;
   op->dense.tc_stages = stages;
   op->dense.tc_ctas_per_sm = ctas_per_sm;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_dense_set_tile_rows(cofem_op* op, int32_t rows) {
+  if (!op || op->kind != 0 || (rows != 128 && rows != 256)) return COFEM_ERR_INVALID_ARG;
+  op->dense.tc_row_tiles = rows / 128;
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_dense_get_pipeline(const cofem_op* op, int32_t* stages,
+                                         int32_t* ctas_per_sm, int32_t* tile_rows) {
+  if (!op || op->kind != 0) return COFEM_ERR_INVALID_ARG;
+  if (stages) *stages = op->dense.tc_stages;
+  if (ctas_per_sm) *ctas_per_sm = op->dense.tc_ctas_per_sm;
+  if (tile_rows) *tile_rows = 128 * (op->dense.tc_row_tiles > 1 ? 2 : 1);
   return COFEM_OK;
 }
 
@@ -1121,14 +1142,21 @@ extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, voi
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int keep_st = op->dense.tc_stages, keep_cps = op->dense.tc_ctas_per_sm;
+  const int keep_st = op->dense.tc_stages, keep_cps = op->dense.tc_ctas_per_sm,
+            keep_mt = op->dense.tc_row_tiles;
   float best = 1e30f;
-  int bst = keep_st, bcps = keep_cps;
+  int bst = keep_st, bcps = keep_cps, bmt = keep_mt;
   cofem_status rc = COFEM_OK;
+  for (int mt = 1; mt <= 2 && rc == COFEM_OK; ++mt)
   for (int cps = 1; cps <= 4 && rc == COFEM_OK; ++cps) {
     DenseTcPlan full = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
-                                     num_sms(), cps, 0, op->dense.phi_terms);
+                                     num_sms(), cps, 0, op->dense.phi_terms, mt);
+    // two tiles per unit need room for four accumulators (else the plan is
+    // the one-tile plan, timed already); with all of the tensor memory taken,
+    // shapes differ only in stages
+    if (mt == 2 && (full.MT != 2 || (cps > 1 && full.tmem_cols > 256))) break;
     for (int stg = 2; stg <= full.stages && rc == COFEM_OK; ++stg) {
+      op->dense.tc_row_tiles = mt;
       op->dense.tc_ctas_per_sm = cps;
       op->dense.tc_stages = stg;
       for (int w = 0; w < 2 && rc == COFEM_OK; ++w)
@@ -1143,13 +1171,14 @@ extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, voi
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       const float us = ms * 1000.f / reps;
-      if (rc == COFEM_OK && us < best) { best = us; bst = stg; bcps = cps; }
+      if (rc == COFEM_OK && us < best) { best = us; bst = stg; bcps = cps; bmt = mt; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   op->dense.tc_stages = rc == COFEM_OK ? bst : keep_st;
   op->dense.tc_ctas_per_sm = rc == COFEM_OK ? bcps : keep_cps;
+  op->dense.tc_row_tiles = rc == COFEM_OK ? bmt : keep_mt;
   if (best_stages) *best_stages = op->dense.tc_stages;
   if (best_ctas) *best_ctas = op->dense.tc_ctas_per_sm;
   if (best_us) *best_us = best;

@@ -597,10 +597,10 @@ __global__ void bdiag_kernel(BConf cf, const BVec* pvs, BState* sts, const BCtl*
       const double xv = (double)X[pv.xoff + (int64_t)(k + 1) * pv.ld + d];
       acc += bprobe(key, d, k) < 0.f ? -xv : xv;
     }
-    const double sd = acc / (double)cf.K;
+    const double sd = acc * (1.0 / (double)cf.K);     // as in the single-problem M-step
     const double den = m * m + sd;
     if (den < cf.den_floor) ++clamps;
-    const double al = 1.0 / fmax(den, cf.den_floor);
+    const double al = __drcp_rn(fmax(den, cf.den_floor));
     if (!isfinite(m) || !isfinite(sd)) bad = 1;
     if (al < cf.support_threshold) ++support;
     mu[pv.aoff + d] = m;

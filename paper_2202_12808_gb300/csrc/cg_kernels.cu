@@ -609,9 +609,9 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
                                   int32_t* st_support) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double sh[32];
   const uint64_t key = ctl ? probe_key(cf.seed, ctl->t) : key_in;
   const int K = cf.K;
+  const double inv_k = 1.0 / (double)K;
   int clamps = 0, support = 0, bad = 0;
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.D;
        d += (int64_t)gridDim.x * blockDim.x) {
@@ -634,10 +634,15 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
         acc.add(((h >> (k & 63)) & 1ull) ? -xv : xv);
       }
     }
-    const double sd = acc.value() / (double)K;
+    // s_d = sum / K and alpha_d = 1 / max(mu^2 + s, floor); FP64 runs at a
+    // small fraction of the FP32 rate on this GPU, so the per-coordinate FP64
+    // work is kept short: a multiplication by 1/K (exact for K a power of
+    // two, else within an ulp of the quotient) and the correctly rounded
+    // reciprocal intrinsic (the same IEEE value as 1.0 / x)
+    const double sd = acc.value() * inv_k;
     const double den = m2 + sd;
     if (den < cf.den_floor) ++clamps;
-    const double al = 1.0 / fmax(den, cf.den_floor);
+    const double al = __drcp_rn(fmax(den, cf.den_floor));
     if (!isfinite(m) || !isfinite(sd)) bad = 1;
     if (al < cf.support_threshold) ++support;
     mu[d] = m;
@@ -645,15 +650,16 @@ __global__ void diag_mstep_kernel(CgConf cf, CgCtl* ctl, uint64_t key_in, const 
     alpha[d] = al;
     if (cf.alpha32) cf.alpha32[d] = (float)al;
   }
-  const double cs = block_sum((double)clamps, sh);
-  const double ss = block_sum((double)support, sh);
-  const double bs = block_sum((double)bad, sh);
+  // the counters: integer warp sums, one atomic per warp
+  const int cs = __reduce_add_sync(0xffffffffu, clamps);
+  const int ss = __reduce_add_sync(0xffffffffu, support);
+  const int bs = __reduce_or_sync(0xffffffffu, bad);
   int* cc = ctl ? &ctl->clamps : counts;
   int* sp = ctl ? &ctl->support : (counts ? counts + 1 : nullptr);
-  if (threadIdx.x == 0) {
-    if (cc && cs > 0) atomicAdd(cc, (int)cs);
-    if (sp && ss > 0) atomicAdd(sp, (int)ss);
-    if (bs > 0 && ctl) raise_error(ctl, COFEM_ERR_NONFINITE);
+  if ((threadIdx.x & 31) == 0) {
+    if (cc && cs > 0) atomicAdd(cc, cs);
+    if (sp && ss > 0) atomicAdd(sp, ss);
+    if (bs && ctl) raise_error(ctl, COFEM_ERR_NONFINITE);
   }
   if (ctl && arrive_last(&ctl->counter[3])) {
     if (threadIdx.x == 0) {

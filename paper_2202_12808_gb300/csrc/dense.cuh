@@ -20,6 +20,8 @@ struct DenseDesc {
   int tc_stages;             // shared-memory ring depth (0 = as deep as fits)
   int phi_terms;             // BF16 terms per Phi entry in the packed copy: 1 for a
                              // BF16 dictionary, 2 for an FP32 one (Phi = hi + lo)
+  int tc_row_tiles;          // 128-row output tiles per work unit (1, 2; 0 = 1): two
+                             // tiles share every B-operand stage
 };
 
 // Tile-major ("packed") BF16 layout read by the tensor-core operator: tile
@@ -100,6 +102,7 @@ DenseSimtPlan dense_simt_plan(int64_t N, int64_t D, int ncols, int vec_bytes, in
 // Tensor-core plan (BF16 dictionary, FP32 vectors split into NT BF16 terms).
 struct DenseTcPlan {
   int NT, nc, BN;            // terms, output columns, MMA N (B-operand rows)
+  int MT;                    // 128-row output tiles per work unit
   uint32_t acc_cols;         // tensor-memory columns of one accumulator
   uint32_t tmem_cols;        // tensor-memory columns allocated per CTA (two accumulators)
   int grid;                  // resident CTAs of one launch (ctas per SM x SMs)
@@ -110,12 +113,14 @@ struct DenseTcPlan {
   size_t smem;               // dynamic shared memory per CTA
   size_t off_xs, bytes_xs, off_wpart, bytes_wpart, off_ws, bytes_ws, total;
 };
-// PT: BF16 terms per Phi entry (1 or 2); a ring stage holds PT A tiles.
+// PT: BF16 terms per Phi entry (1 or 2); MT: 128-row output tiles per work
+// unit (1 or 2); a ring stage holds MT x PT A tiles and one B tile, and a CTA
+// allocates 2 x MT accumulators.
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm = 2,
-                          int stages = 0, int PT = 1);
+                          int stages = 0, int PT = 1, int MT = 1);
 inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
   return dense_tc_plan(op.N, op.D, nc, op.nterms, sms, op.tc_ctas_per_sm, op.tc_stages,
-                       op.phi_terms > 1 ? 2 : 1);
+                       op.phi_terms > 1 ? 2 : 1, op.tc_row_tiles > 1 ? 2 : 1);
 }
 
 // Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map

@@ -65,6 +65,10 @@ struct TcArgs {
   int phi_terms;        // 2: Phi = hi + lo, two packed images term_stride apart
                         // (packed copy only); otherwise one
   int64_t term_stride;  // elements from the hi image to the lo image
+  int row_tiles;        // 2: a unit is two 128-row output tiles sharing every B stage
+                        // (one accumulator each); otherwise one
+  int64_t tiles_a;      // packed A tiles along the output rows: 128-row tiles of Phi
+                        // (first product), 64-column tiles (second product)
   int64_t nkd;          // 64-column tiles of Phi (packed layout)
   // GEMM1: split-K partials (reduced and split by reduce_split_kernel)
   float* wpart;
@@ -150,11 +154,12 @@ __device__ __forceinline__ TcUnit tc_unit(const TcArgs& args, int w) {
     u.wo = pr.boff2;
   } else {
     const int tile = w % args.units_m, split = w / args.units_m;
-    u.m0 = (int64_t)tile * kTileM;
+    const int mt = args.row_tiles > 1 ? 2 : 1;
+    u.m0 = (int64_t)tile * kTileM * mt;
     u.kb0 = split * args.kb_per_split;
     u.kb1 = min(args.nk_total, u.kb0 + args.kb_per_split);
     u.split = split;
-    u.dslot = tile;
+    u.dslot = tile * mt;
   }
   return u;
 }
@@ -179,8 +184,10 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t b_bytes = (uint32_t)args.BN * 128u;
-  const int PT = args.phi_terms > 1 ? 2 : 1;          // A tiles per stage
-  const uint32_t a_bytes = (uint32_t)PT * kATileBytes;
+  const int PT = args.phi_terms > 1 ? 2 : 1;          // BF16 terms of Phi
+  const int MT = args.row_tiles > 1 ? 2 : 1;          // 128-row output tiles per unit
+  // a stage holds MT x PT A tiles (tile (mt, pt) at (mt PT + pt) x 16 KB) and one B tile
+  const uint32_t a_bytes = (uint32_t)(MT * PT) * kATileBytes;
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const int S = args.stages;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
@@ -247,38 +254,56 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           // across CG iterations; the rest streams through
           if (MODE == 0) {
             const uint64_t pol_a = (int64_t)kb * kTileK < args.res_d ? pol_last : pol_first;
-            if (u.pk) {  // tile (m0 / 128, kb): one contiguous 16 KB copy per term
-              const __nv_bfloat16* src = u.pk + ((m0 >> 7) * u.nkd + kb) * (kTileM * kTileK);
-              tc::bulk_load(sa, src, kATileBytes, &full[s], pol_a);
-              if (PT == 2)
-                tc::bulk_load(sa + kATileBytes, src + args.term_stride, kATileBytes, &full[s],
+            if (u.pk) {  // tile (m0 / 128 + mt, kb): one contiguous 16 KB copy per term
+              for (int mt = 0; mt < MT; ++mt) {
+                // past the last row tile the first tile is copied again: it only
+                // feeds output rows >= M, which are not stored
+                int64_t rt = (m0 >> 7) + mt;
+                if (args.items == nullptr && rt >= args.tiles_a) rt = m0 >> 7;
+                const __nv_bfloat16* src = u.pk + (rt * u.nkd + kb) * (kTileM * kTileK);
+                uint8_t* dst = sa + (uint32_t)(mt * PT) * kATileBytes;
+                tc::bulk_load(dst, src, kATileBytes, &full[s], pol_a);
+                if (PT == 2)
+                  tc::bulk_load(dst + kATileBytes, src + args.term_stride, kATileBytes, &full[s],
+                                pol_a);
+              }
+            } else if (MT == 2) {
+              tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
+              tc::tma_load_2d(sa + kATileBytes, &mapA, &full[s], kb * kTileK, (int)m0 + kTileM,
                               pol_a);
             } else
               tc::tma_load_2d(sa, &mapA, &full[s], kb * kTileK, (int)m0, pol_a);
           } else {
             const uint64_t pol_a = m0 < args.res_d ? pol_last : pol_first;
             if (u.pk) {
-              // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
-              // two 64-column tiles m0/64 and m0/64 + 1 give the 128 d's
-              const int64_t base =
-                  ((int64_t)(kb >> 1) * u.nkd + (m0 >> 6)) * kTileM + (kb & 1) * 64;
-              const __nv_bfloat16* src = u.pk + base * kTileK;
-              tc::bulk_load(sa, src, kATileBytes / 2, &full[s], pol_a);
-              // the next 64-column tile; past the last one (D not a multiple of
-              // 128) the same half-tile is copied again: it only feeds output
-              // rows d >= D, which are not stored
-              const __nv_bfloat16* src2 = (m0 >> 6) + 1 < u.nkd ? src + kTileM * kTileK : src;
-              tc::bulk_load(sa + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
-              if (PT == 2) {
-                tc::bulk_load(sa + kATileBytes, src + args.term_stride, kATileBytes / 2,
-                              &full[s], pol_a);
-                tc::bulk_load(sa + kATileBytes + kATileBytes / 2, src2 + args.term_stride,
-                              kATileBytes / 2, &full[s], pol_a);
+              for (int mt = 0; mt < MT; ++mt) {
+                // rows n = 64 kb .. +64 are half (kb & 1) of row tile kb / 2; the
+                // two 64-column tiles c and c + 1 give the 128 d's of output tile mt
+                int64_t c = (m0 >> 6) + 2 * mt;
+                if (args.items == nullptr && c >= u.nkd) c = m0 >> 6;   // rows >= M: not stored
+                const int64_t base = ((int64_t)(kb >> 1) * u.nkd + c) * kTileM + (kb & 1) * 64;
+                const __nv_bfloat16* src = u.pk + base * kTileK;
+                uint8_t* dst = sa + (uint32_t)(mt * PT) * kATileBytes;
+                tc::bulk_load(dst, src, kATileBytes / 2, &full[s], pol_a);
+                // the next 64-column tile; past the last one (D not a multiple of
+                // 128) the same half-tile is copied again: it only feeds output
+                // rows d >= D, which are not stored
+                const __nv_bfloat16* src2 = c + 1 < u.nkd ? src + kTileM * kTileK : src;
+                tc::bulk_load(dst + kATileBytes / 2, src2, kATileBytes / 2, &full[s], pol_a);
+                if (PT == 2) {
+                  tc::bulk_load(dst + kATileBytes, src + args.term_stride, kATileBytes / 2,
+                                &full[s], pol_a);
+                  tc::bulk_load(dst + kATileBytes + kATileBytes / 2, src2 + args.term_stride,
+                                kATileBytes / 2, &full[s], pol_a);
+                }
               }
             } else {
-              tc::tma_load_2d(sa, &mapA, &full[s], (int)m0, kb * kTileK, pol_a);
-              tc::tma_load_2d(sa + kATileBytes / 2, &mapA, &full[s], (int)m0 + 64, kb * kTileK,
-                              pol_a);
+              for (int mt = 0; mt < MT; ++mt) {
+                uint8_t* dst = sa + (uint32_t)mt * kATileBytes;
+                tc::tma_load_2d(dst, &mapA, &full[s], (int)m0 + kTileM * mt, kb * kTileK, pol_a);
+                tc::tma_load_2d(dst + kATileBytes / 2, &mapA, &full[s], (int)m0 + kTileM * mt + 64,
+                                kb * kTileK, pol_a);
+              }
             }
           }
           tc::tma_load_2d(sb, &mapB, &full[s], (int)(u.bx0 + (int64_t)kb * kTileK), 0, pol_b);
@@ -308,7 +333,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           break;
         }
         tc::tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)b * args.acc_cols;
+        const uint32_t acc0 = tmem + (uint32_t)(b * MT) * args.acc_cols;
         for (int i = 0; i < nk; ++i, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -319,15 +344,18 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           tc::tc_fence_after();
           const uint32_t a_base = tc::smem_u32(smem + s * stage_bytes);
           const uint32_t b_base = a_base + a_bytes;
-          for (int pt = 0; pt < PT; ++pt) {
-            const uint32_t at = a_base + (uint32_t)pt * kATileBytes;
+          for (int mt = 0; mt < MT; ++mt) {
+            const uint32_t acc = acc0 + (uint32_t)mt * args.acc_cols;
+            for (int pt = 0; pt < PT; ++pt) {
+              const uint32_t at = a_base + (uint32_t)(mt * PT + pt) * kATileBytes;
 #pragma unroll
-            for (int k = 0; k < kTileK / 16; ++k) {
-              uint64_t adesc;
-              if (MODE == 0) adesc = tc::smem_desc_sw128(at + k * 32, 16, 1024);
-              else adesc = tc::smem_desc_sw128(at + k * 2048, kATileBytes / 2, 1024);
-              const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
-              tc::mma_bf16(acc, adesc, bdesc, idesc, (i > 0 || k > 0 || pt > 0) ? 1u : 0u);
+              for (int k = 0; k < kTileK / 16; ++k) {
+                uint64_t adesc;
+                if (MODE == 0) adesc = tc::smem_desc_sw128(at + k * 32, 16, 1024);
+                else adesc = tc::smem_desc_sw128(at + k * 2048, kATileBytes / 2, 1024);
+                const uint64_t bdesc = tc::smem_desc_sw128(b_base + k * 32, 16, 1024);
+                tc::mma_bf16(acc, adesc, bdesc, idesc, (i > 0 || k > 0 || pt > 0) ? 1u : 0u);
+              }
             }
           }
           tc::mma_commit(&empty[s]);
@@ -347,8 +375,9 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       const TcUnit u = tc_unit<MODE>(args, w);
       const int nk = max(0, u.kb1 - u.kb0);
       const int b = lu & 1;
-      const int64_t row = u.m0 + 32 * g + lane;
-      const bool live = row < u.M;
+      // rows of the unit's first output tile (the second tile, if any, follows)
+      int64_t row = u.m0 + 32 * g + lane;
+      bool live = row < u.M;
       float a32 = 0.f;                     // alpha_row in FP32, converted once per row
       if (MODE == 1 && live)
         a32 = args.alpha32 ? args.alpha32[u.aoff + row]
@@ -375,7 +404,21 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           : "memory");
       if (!okall) break;
       tc::tc_fence_after();
-      const uint32_t acc = tmem + (uint32_t)b * args.acc_cols;
+      for (int mt = 0; mt < MT; ++mt) {
+      if (mt > 0) {
+        row = u.m0 + kTileM * mt + 32 * g + lane;
+        live = row < u.M;
+        a32 = 0.f;
+        if (MODE == 1 && live)
+          a32 = args.alpha32 ? args.alpha32[u.aoff + row]
+                             : (args.alpha ? (float)args.alpha[u.aoff + row] : 0.f);
+        if (MODE == 1) {
+#pragma unroll
+          for (int jj = 0; jj < G; ++jj)
+            xnext[jj] = (live && jj < args.nc) ? args.x[u.xoff + (int64_t)jj * u.ldo + row] : 0.f;
+        }
+      }
+      const uint32_t acc = tmem + (uint32_t)(b * MT + mt) * args.acc_cols;
       for (int gi = 0; gi < ngroups; ++gi) {
         float xcur[G];
         if (MODE == 1) {
@@ -464,10 +507,12 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
         }
       }
-      // this accumulator is drained: the MMA may reuse it
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&accempty[b]);
+      if (mt == MT - 1) {
+        // this unit's accumulators are drained: the MMA may reuse them
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&accempty[b]);
+      }
       if (MODE == 1 && args.dots) {
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (warp == 2) {
@@ -478,13 +523,14 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             for (int q = 1; q < 4; ++q) two_sum_merge(ps, pc, redp[q * 64 + j].x, redp[q * 64 + j].y);
             double t = (double)ps + (double)pc;
             if (big) t += redb[j] + redb[64 + j] + redb[128 + j] + redb[192 + j];
-            args.dots[(int64_t)u.dslot * kMaxCols + j] = t;
+            args.dots[(int64_t)(u.dslot + mt) * kMaxCols + j] = t;
           }
           if (lane == 0) *bigflag = 0;
         }
-        // the partials are read before the next unit writes them
+        // the partials are read before the next tile writes them
         asm volatile("bar.sync 1, 128;" ::: "memory");
       }
+      }   // output tiles of the unit
     }
   }
   tc::tc_fence_before();
@@ -729,9 +775,10 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t 
 static int term_group(int NT) { return 16 / NT; }
 
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm,
-                          int stages, int PT) {
+                          int stages, int PT, int MT) {
   DenseTcPlan p;
   if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 2;
+  MT = MT > 1 ? 2 : 1;
   p.NT = NT;
   p.nc = nc;
   const int ngroups = (nc + term_group(NT) - 1) / term_group(NT);
@@ -739,10 +786,14 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   uint32_t tc = 32;
   while (tc < (uint32_t)p.BN) tc <<= 1;
   p.acc_cols = tc;
-  p.tmem_cols = 2 * tc;                  // two accumulators (persistent CTAs)
+  // the tensor memory holds 512 columns: two sets of MT accumulators must fit
+  // (BN > 128, i.e. 256-column accumulators, leaves room for one tile per unit)
+  if (2 * MT * tc > 512) MT = 1;
+  p.MT = MT;
+  p.tmem_cols = 2 * MT * tc;             // two sets of MT accumulators (persistent CTAs)
   p.ld = round_up(D, kLdAlign);
   p.ldw = round_up(N, kLdAlign);
-  const int mt1 = (int)((N + kTileM - 1) / kTileM);
+  const int mt1 = (int)((N + kTileM * MT - 1) / (kTileM * MT));   // units along N
   p.nk1 = (int)((D + kTileK - 1) / kTileK);
   p.nk2 = (int)((N + kTileK - 1) / kTileK);
   int per_sm = 512 / (int)p.tmem_cols < ctas_per_sm ? 512 / (int)p.tmem_cols : ctas_per_sm;
@@ -770,7 +821,7 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
     if (per_cta(s1, &kb, &sr) * 10 <= best * 11) { p.S1 = sr; p.kbps1 = kb; break; }
   }
   const size_t fixed = 1024 + 2 * kMaxStages * 8 + 32 + 64 + 4 * 64 * 8 * 2 + 64;
-  const size_t stage = (size_t)(PT > 1 ? 2 : 1) * kATileBytes + (size_t)p.BN * 128;
+  const size_t stage = (size_t)((PT > 1 ? 2 : 1) * MT) * kATileBytes + (size_t)p.BN * 128;
   // each resident CTA also costs 1 KB of reserved shared memory
   const size_t budget = kSmemPerSm / per_sm - 1024;
   int st = (int)((budget - fixed) / stage);
@@ -779,6 +830,10 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
   if (st < 2) st = 2;
   p.stages = st;
   p.smem = st * stage + fixed;
+  // accumulators that fill the tensor memory leave room for one CTA per SM:
+  // ask for more than half of the shared memory as well, so that a second
+  // CTA never lands on the SM and waits in its tensor-memory allocation
+  if (p.tmem_cols > 256 && p.smem < kSmemPerSm / 2 + 1024) p.smem = kSmemPerSm / 2 + 1024;
   p.grid = grid;
   p.off_xs = 0;
   p.bytes_xs = round_up((int64_t)p.BN * p.ld * 2, 256);
@@ -807,7 +862,9 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
                             const float* alpha32, const int* gate) {
   const int sms = num_sms();
   const int PT = op.phi_terms > 1 && op.packed ? 2 : 1;
-  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages, PT);
+  DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages, PT,
+                                op.tc_row_tiles > 1 ? 2 : 1);
+  const int MT = p.MT;                   // the plan falls back to one tile when TMEM is short
   const bool presplit = (flags & kApplyPresplit) != 0;
   __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
   float* Wp = (float*)(ws + p.off_wpart);
@@ -851,7 +908,9 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.split_stride = (int64_t)nc * p.ldw;
   a1.err = err;
   a1.gate = gate;
-  a1.units_m = (int)((op.N + kTileM - 1) / kTileM);
+  a1.row_tiles = MT;
+  a1.tiles_a = packed_tiles_m(op.N);
+  a1.units_m = (int)((op.N + kTileM * MT - 1) / (kTileM * MT));
   a1.units = a1.units_m * p.S1;
   a1.acc_cols = p.acc_cols;
   dim3 g1((unsigned)std::min(a1.units, p.grid), 1);
@@ -887,13 +946,15 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.dots = dots;
   a2.err = err;
   a2.gate = gate;
-  a2.units_m = (int)((op.D + kTileM - 1) / kTileM);
+  a2.row_tiles = MT;
+  a2.tiles_a = nkd;
+  a2.units_m = (int)((op.D + kTileM * MT - 1) / (kTileM * MT));
   a2.units = a2.units_m;
   a2.acc_cols = p.acc_cols;
   dim3 g2((unsigned)std::min(a2.units, p.grid), 1);
   if (launch_tc<1, NT>(g2, p.smem, mPhi2, mWs, a2, st) != cudaSuccess) return 2;
   apply_tick(st);
-  if (nparts) *nparts = dots ? a2.units : 0;
+  if (nparts) *nparts = dots ? a2.units * MT : 0;
   return 0;
 }
 

@@ -35,6 +35,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pipeline", default=None,
                     help="STAGES,CTAS_PER_SM of the tensor-core products (skips the autotuner)")
+    ap.add_argument("--tile-rows", type=int, default=128, choices=[128, 256],
+                    help="output rows per tensor-core work unit (with --pipeline)")
     a = ap.parse_args()
     st = torch.cuda.current_stream().cuda_stream
     if a.op == "cg":
@@ -58,11 +60,13 @@ def main():
     if a.pipeline:
         stg, cps = (int(v) for v in a.pipeline.split(","))
         B.cofem_op_dense_set_pipeline(op.handle, stg, cps)
-        tuned = (stg, cps, None)
+        B.cofem_op_dense_set_tile_rows(op.handle, a.tile_rows)
+        tuned = (stg, cps, a.tile_rows)
     elif not a.no_autotune:
         nbt = B.cofem_op_dense_autotune_workspace_bytes(op.handle, a.ncols)
         wst = torch.empty(nbt, dtype=torch.uint8, device="cuda")
         tuned = B.cofem_op_dense_autotune(op.handle, a.ncols, wst.data_ptr(), nbt, st)
+        tuned = tuned + (B.cofem_op_dense_get_pipeline(op.handle)[2],)
         del wst
     ld = (a.D + 63) // 64 * 64
     X = torch.zeros((a.ncols, ld), device="cuda")

@@ -31,9 +31,11 @@ def _problem(N=256, D=1024, nnz=51, sigma=0.01, seed=0):
     return datagen.dense_problem(N, D, nnz, sigma, seed)
 
 
-def _gpu_fit(Phi, y, beta, torch_phi_dtype, vec, packed=False, **kw):
+def _gpu_fit(Phi, y, beta, torch_phi_dtype, vec, packed=False, tile_rows=128, **kw):
     Phi_t = torch.from_numpy(np.ascontiguousarray(Phi)).to("cuda", torch_phi_dtype)
     op = api.DenseOperator(Phi_t)
+    if tile_rows != 128:
+        B.cofem_op_dense_set_tile_rows(op.handle, tile_rows)
     if packed:
         nb = B.cofem_op_dense_packed_bytes(op.handle)
         op.packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
@@ -167,8 +169,8 @@ def test_replacement_tolerance_mode_fp32(cuda_lib):
     assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3
 
 
-@pytest.mark.parametrize("period", [10, 7])
-def test_replacement_tensor_core_bf16(cuda_lib, period):
+@pytest.mark.parametrize("period,rows", [(10, 128), (7, 128), (7, 256)])
+def test_replacement_tensor_core_bf16(cuda_lib, period, rows):
     # BF16 dictionary on the tensor cores: the replacement runs outside an
     # inner CG loop (gated kernels), every `period` iterations, against the
     # oracle on the BF16-rounded dictionary; iteration counts above the period
@@ -181,7 +183,8 @@ def test_replacement_tensor_core_bf16(cuda_lib, period):
     y32 = prob.y.astype(np.float32).astype(np.float64)
     kw = dict(K=20, em_iters=30, cg_tol=1e-5, cg_max_iters=400, resid_replace_every=period,
               seed=4)
-    a, mu, s, st = _gpu_fit(Phi64, y32, prob.beta, torch.bfloat16, B.COFEM_F32, **kw)
+    a, mu, s, st = _gpu_fit(Phi64, y32, prob.beta, torch.bfloat16, B.COFEM_F32, tile_rows=rows,
+                            **kw)
     ra, rmu, rs, rst = sbl.cofem_dense(Phi64, y32, prob.beta, 20, 30, 1e-5, 400,
                                        resid_replace_every=period, seed=4)
     assert max(st["cg_iters"]) > 2 * period

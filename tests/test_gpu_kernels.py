@@ -50,8 +50,9 @@ APPLY_CASES = [
 
 
 @pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
-@pytest.mark.parametrize("kind", ["f64", "f32", "f32-packed", "bf16", "bf16-t2", "bf16-t1",
-                                  "bf16-simt", "bf16-packed", "bf16-packed-t1"])
+@pytest.mark.parametrize("kind", ["f64", "f32", "f32-packed", "f32-packed-r256", "bf16",
+                                  "bf16-t2", "bf16-t1", "bf16-simt", "bf16-packed",
+                                  "bf16-packed-t1", "bf16-r256", "bf16-packed-r256"])
 def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
     rng = np.random.default_rng(ncols)
@@ -63,7 +64,7 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.float64)
         vdt, vec, tol = torch.float64, B.COFEM_F64, 1e-12
         pdt = B.COFEM_F64
-    elif kind in ("f32", "f32-packed"):
+    elif kind in ("f32", "f32-packed", "f32-packed-r256"):
         # f32-packed: the tensor cores with Phi = hi + lo (two BF16 terms, at
         # most 2^-17 relative per entry), against the oracle on the FP32 Phi
         Phi_ref = prob.Phi.astype(np.float64)
@@ -76,16 +77,20 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         vdt, vec, pdt = torch.float32, B.COFEM_F32, B.COFEM_BF16
         # FP32 split into 3 / 2 / 1 BF16 terms (24 / 16 / 8-bit mantissas)
         terms = {"bf16": 3, "bf16-t2": 2, "bf16-t1": 1, "bf16-simt": 0, "bf16-packed": 3,
-                 "bf16-packed-t1": 1}[kind]
+                 "bf16-packed-t1": 1, "bf16-r256": 3, "bf16-packed-r256": 3}[kind]
         tol = {3: 2e-5, 2: 6e-5, 1: 8e-3, 0: 2e-5}[terms]
     X_in = X.astype(np.float32).astype(np.float64) if vdt == torch.float32 else X
     op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
     if pdt == B.COFEM_BF16:
         B.cofem_op_dense_set_terms(op, terms)
+    if kind.endswith("-r256"):
+        # two 128-row output tiles per work unit (ragged: odd tile counts)
+        B.cofem_op_dense_set_tile_rows(op, 256)
+        assert B.cofem_op_dense_get_pipeline(op)[2] == 256
     packed = None
-    if kind.startswith("bf16-packed") or kind == "f32-packed":
+    if kind.startswith("bf16-packed") or kind.startswith("f32-packed"):
         nb = B.cofem_op_dense_packed_bytes(op)
-        assert nb == B.cofem_dense_packed_bytes(N, D) * (2 if kind == "f32-packed" else 1)
+        assert nb == B.cofem_dense_packed_bytes(N, D) * (2 if kind.startswith("f32") else 1)
         packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
         B.cofem_op_dense_attach_packed(op, packed.data_ptr(), nb)
     try:
@@ -188,8 +193,9 @@ def test_f32_packed_terms_are_hi_plus_lo(cuda_lib):
         B.cofem_op_destroy(op)
 
 
-@pytest.mark.parametrize("packed", [False, True, "f32"])
-def test_op_apply_tensor_core_full_size(cuda_lib, packed):
+@pytest.mark.parametrize("packed,rows", [(False, 128), (True, 128), ("f32", 128), (True, 256),
+                                         ("f32", 256)])
+def test_op_apply_tensor_core_full_size(cuda_lib, packed, rows):
     # the bench workload's operator (N=4096, D=32768, 33 columns, BF16 Phi,
     # 3-term split) on sampled output rows computed one by one by the oracle
     N, D, ncols = 4096, 32768, 33
@@ -208,6 +214,7 @@ def test_op_apply_tensor_core_full_size(cuda_lib, packed):
     alpha = rng.uniform(0.5, 1e6, D)
     beta = 1e4
     op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
+    B.cofem_op_dense_set_tile_rows(op, rows)
     if packed:
         nb = B.cofem_op_dense_packed_bytes(op)
         pk = torch.empty(nb, dtype=torch.uint8, device="cuda")

@@ -259,7 +259,7 @@ def load_reference_fit(phi):
                 out[parts[0]] = [int(v) for v in parts[1:]]
             elif parts[0] == "relres":
                 out["relres"] = [float(v) for v in parts[1:]]
-            elif parts[0] in ("support", "nrmse_mu_vs_truth"):
+            elif parts[0] in ("support", "nrmse_mu_vs_truth", "alpha_sample"):
                 out[parts[0]] = float(parts[1])
             else:
                 out["alpha"][int(parts[0])] = float(parts[1])
@@ -267,12 +267,13 @@ def load_reference_fit(phi):
 
 
 def compare_to_reference(alpha, ref, D, thr=1e6):
-    """Support equality under the borderline rule (coordinates with alpha
-    within a factor 2 of the threshold in either path are excluded) and the
-    largest relative alpha difference on the common support."""
-    ra = np.full(D, np.inf)
-    for d, v in ref["alpha"].items():
-        ra[d] = v
+    """On the reference's coordinate sample: support equality under the
+    borderline rule (coordinates with alpha within a factor 2 of the
+    threshold in either path are excluded) and the largest relative alpha
+    difference on the common support."""
+    idx = np.array(sorted(ref["alpha"]))
+    ra = np.array([ref["alpha"][d] for d in idx])
+    alpha = alpha[idx]
     border = ((alpha > thr / 2) & (alpha < thr * 2)) | ((ra > thr / 2) & (ra < thr * 2))
     sa, sr = (alpha < thr) & ~border, (ra < thr) & ~border
     both = sa & sr
@@ -301,11 +302,13 @@ def time_to_tolerance(hist, end_ns, ref, tols=(1e-2, 1e-3)):
     return out
 
 
-def whole_fit(api, B, op, y, beta, kw, em, dev):
+def whole_fit(api, B, op, y, beta, kw, em, dev, z=None):
     """One timed fit of `em` EM iterations (one call, CUDA events on the
     stream), then the same fit EM iteration by EM iteration (resumed, not
     timed; results are bitwise those of the single call) for the alpha
-    trajectory.  Returns (seconds, stats, alpha history em x D)."""
+    trajectory and, given the generating coefficients z, the NRMSE of mu
+    after every EM iteration.  Returns (seconds, stats, alpha history em x D,
+    NRMSE list or None)."""
     import torch
     p = api.params(em_iters=em, **kw)
     ws = api.workspace(op, p, dev)
@@ -320,12 +323,29 @@ def whole_fit(api, B, op, y, beta, kw, em, dev):
     sec = e0.elapsed_time(e1) / 1e3
     D = op.D
     hist = np.empty((em, D))
+    nrmse = [] if z is not None else None
     alpha = torch.empty(D, dtype=torch.float64, device=dev)
     for t in range(em):
-        api.fit(op, y, beta, api.params(em_iters=1, t_offset=t, **kw), ws=ws, alpha=alpha)
+        rt = api.fit(op, y, beta, api.params(em_iters=1, t_offset=t, **kw), ws=ws, alpha=alpha)
         hist[t] = alpha.cpu().numpy()
+        if z is not None:
+            mu = rt.mu.cpu().numpy()
+            nrmse.append(float(np.linalg.norm(mu - z) / np.linalg.norm(z)))
     assert np.array_equal(hist[-1], r.alpha.cpu().numpy()), "resumed fit differs"
-    return sec, r.stats, hist
+    return sec, r.stats, hist, nrmse
+
+
+def time_to_nrmse(nrmse, end_ns, level=0.02):
+    """The paper's time-to-tolerance (Sec. 4.2): device time until the NRMSE
+    of mu against the generating coefficients is at most `level` (first EM
+    iteration from which it stays there)."""
+    first = None
+    for t in range(len(nrmse) - 1, -1, -1):
+        if nrmse[t] <= level:
+            first = t
+        else:
+            break
+    return None if first is None else {"em_iters": first + 1, "seconds": end_ns[first] / 1e9}
 
 
 def launches_per_em(cg_iters, replace_every, per_iter, per_replace, nested=False):
@@ -862,15 +882,18 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
                                                   torch.cuda.current_stream().cuda_stream)
     del wst
     for name, op, ref_phi in (("bf16", op16, "bf16"), ("fp32", op32, "f32")):
-        sec, stats, hist = whole_fit(api, B, op, y, prob.beta, kw, em, dev)
+        sec, stats, hist, nrmse = whole_fit(api, B, op, y, prob.beta, kw, em, dev, z=prob.z)
         ent = {"em_iters_per_s": em / sec, "seconds": sec,
                "cg_iters_total": int(sum(stats["cg_iters"])),
                "cg_iters_per_em": stats["cg_iters"],
-               "support_counts": stats["support"][::10]}
+               "support_counts": stats["support"][::10],
+               "nrmse_mu_vs_truth": {"final": nrmse[-1], "every_10": nrmse[9::10]},
+               "time_to_2pct_nrmse": time_to_nrmse(nrmse, stats["end_ns"])}
         ref = load_reference_fit(ref_phi)
         if ref is not None:
             ent["vs_oracle_" + ref_phi] = time_to_tolerance(hist, stats["end_ns"], ref)
             ent["oracle_cg_iters_total"] = int(sum(ref["cg_iters"]))
+            ent["oracle_nrmse_final"] = ref.get("nrmse_mu_vs_truth")
         if name == "bf16":
             ref32 = load_reference_fit("f32")
             if ref32 is not None:
@@ -878,6 +901,8 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
         out[name] = ent
     out["fp32"]["pipeline"] = {"stages": st32, "ctas_per_sm": cps32, "us_per_apply": us32}
     out["ratio_em_iters_per_s"] = out["bf16"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
+    t16, t32 = out["bf16"]["time_to_2pct_nrmse"], out["fp32"]["time_to_2pct_nrmse"]
+    out["ratio_time_to_2pct_nrmse"] = (t32["seconds"] / t16["seconds"]) if t16 and t32 else None
     # the FP32 operator's kernels, timed with CUDA events on the stream
     ld = (D + 63) // 64 * 64
     Xb = torch.randn((ncols, ld), device=dev)

@@ -367,7 +367,10 @@ __global__ void cg_update_kernel(CgConf cf, CgCtl* ctl, CgScalars* sc, V* X, V* 
     if (threadIdx.x == 0) g0 = *(volatile unsigned int*)&ctl->dir_gen;
   }
   constexpr int W = 16 / sizeof(V);
-  constexpr int U = kUpdChunks;                 // chunks of W values per thread and pass
+  // chunks of W values per thread and pass: the fused form keeps the last
+  // pass's r and p in registers for the direction update; the plain form
+  // takes fewer per pass (fewer registers, more resident blocks)
+  constexpr int U = DIR ? kUpdChunks : 2;
   const int j = blockIdx.y;
   V* x = X + (int64_t)j * cf.ld;
   V* r = R + (int64_t)j * cf.ld;

@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched-512-n128-2048", "conv-l1m-c8-t64",
                              "dense-fp64-n256-d1024", "learned-dense-n256-d1024", "dct-d262144",
-                             "multitask-n4096-d32768-t4", "combined-128-n128-2048"],
+                             "multitask-n4096-d32768-t4", "combined-128-n128-2048",
+                             "paper-dense", "dct-sweep"],
                     help="the default is the headline workload; the others print their own line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-whole-fit", action="store_true",
@@ -336,16 +337,13 @@ def whole_fit(api, B, op, y, beta, kw, em, dev, z=None):
 
 
 def time_to_nrmse(nrmse, end_ns, level=0.02):
-    """The paper's time-to-tolerance (Sec. 4.2): device time until the NRMSE
-    of mu against the generating coefficients is at most `level` (first EM
-    iteration from which it stays there)."""
-    first = None
-    for t in range(len(nrmse) - 1, -1, -1):
-        if nrmse[t] <= level:
-            first = t
-        else:
-            break
-    return None if first is None else {"em_iters": first + 1, "seconds": end_ns[first] / 1e9}
+    """The paper's time-to-tolerance (Sec. 4.2, the time needed to attain a
+    low NRMSE): device time at the end of the first EM iteration whose mu is
+    within `level` NRMSE of the generating coefficients."""
+    for t, v in enumerate(nrmse):
+        if v <= level:
+            return {"em_iters": t + 1, "seconds": end_ns[t] / 1e9}
+    return None
 
 
 def launches_per_em(cg_iters, replace_every, per_iter, per_replace, nested=False):
@@ -751,6 +749,159 @@ def run_combined(args):
              "clocks": clk.summary()})
 
 
+def _nrmse(mu, z):
+    return float(np.linalg.norm(np.asarray(mu) - z) / np.linalg.norm(z))
+
+
+def run_paper_dense(args):
+    """The paper's dense-dictionary experiments (Sec. 4.1, Fig. 1a-c), CoFEM's
+    side only, on the GPU's FP64 path: Phi iid N(0, 1), d = 0.04 D spikes of
+    +-1, sigma = 0.005 (beta = 4e4), K = 20, U = 400.  The paper states no CG
+    tolerance; at this scaling cond(A) reaches 1e8 and more, and the mean
+    column needs a relative residual near 1e-10 for CoFEM to recover the
+    signal as exact EM does (at 1e-6 neither the oracle nor the GPU recovers
+    it for f >= 3), which FP32 vectors cannot reach: so tol 1e-10, FP64.
+      (a) NRMSE of mu after 50 EM iterations against f = D / N in 1..8 at
+          D = 1024, averaged over `reps` problems;
+      (b) seconds for 30 EM iterations at f = 4, D = 2^9 .. 2^14 (2^15 takes
+          minutes in FP64 on this part);
+      (c) log p(y | alpha) per EM iteration of CoFEM (GPU) and exact EM (the
+          oracle, Cholesky) at f = 4, D = 2^12 (exact EM at the paper's
+          D = 2^15 needs minutes per iteration on the host).
+    The smallest case of (a) and (b) is checked against the FP64 oracle."""
+    import torch
+    from oracle import sbl
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    kw64 = dict(vec_dtype=B.COFEM_F64, K=20, cg_tol=1e-10, cg_max_iters=400)
+    reps = 10
+
+    def op64(pr):
+        return api.DenseOperator(torch.from_numpy(pr.Phi.astype(np.float64)).cuda())
+
+    def problem(D, f, seed):
+        return datagen.dense_problem(D // f, D, max(1, int(0.04 * D)), 0.005, seed,
+                                     amp="spike", phi_scale=1.0)
+
+    # (a) NRMSE against f
+    nrmse_f, oracle_a = {}, None
+    t0 = time.perf_counter()
+    for f in range(1, 9):
+        vals = []
+        for r in range(reps):
+            pr = problem(1024, f, 100 * f + r)
+            op = op64(pr)
+            y = torch.from_numpy(pr.y).cuda()
+            res = api.fit(op, y, pr.beta, api.params(em_iters=50, seed=r, **kw64))
+            vals.append(_nrmse(res.mu.cpu().numpy(), pr.z))
+            if f == 4 and r == 0:
+                ra, rmu, rs, rst = sbl.cofem_dense(pr.Phi.astype(np.float64), pr.y, pr.beta, 20,
+                                                   50, 1e-10, 400, seed=0)
+                oracle_a = {"case": "f=4, D=1024, repetition 0", "nrmse_gpu": vals[-1],
+                            "nrmse_oracle": _nrmse(rmu, pr.z),
+                            "mu_rel_l2_vs_oracle": float(np.linalg.norm(res.mu.cpu().numpy() - rmu)
+                                                         / np.linalg.norm(rmu))}
+        nrmse_f[f] = {"mean_pct": 100 * float(np.mean(vals)), "max_pct": 100 * float(np.max(vals))}
+    t_a = time.perf_counter() - t0
+    # (b) run time for 30 EM iterations against D
+    times_d, oracle_b = {}, None
+    for p in range(9, 15):
+        D = 1 << p
+        pr = problem(D, 4, 7 + p)
+        ent = {}
+        for name, mk, kk, ydt in [("fp64", op64, kw64, np.float64)]:
+            op = mk(pr)
+            y = torch.from_numpy(pr.y.astype(ydt)).cuda()
+            pp = api.params(em_iters=30, seed=1, **kk)
+            ws = api.workspace(op, pp)
+            try:
+                api.fit(op, y, pr.beta, api.params(em_iters=1, seed=1, **kk), ws=ws)
+                res, sec = _timed(lambda: api.fit(op, y, pr.beta, pp, ws=ws))
+            except B.CofemError as e:
+                ent[name] = {"error": str(e).split(":")[-1].strip()}
+                continue
+            ent[name] = {"seconds_30_em": sec, "cg_iters": int(sum(res.stats["cg_iters"])),
+                         "nrmse_pct": 100 * _nrmse(res.mu.cpu().numpy(), pr.z)}
+            if p == 9 and name == "fp64":
+                ra, rmu, rs, rst = sbl.cofem_dense(pr.Phi.astype(np.float64), pr.y, pr.beta, 20,
+                                                   30, 1e-10, 400, seed=1)
+                oracle_b = {"case": "D=512, f=4, FP64", "mu_rel_l2_vs_oracle": float(
+                    np.linalg.norm(res.mu.cpu().numpy() - rmu) / np.linalg.norm(rmu)),
+                    "cg_iters_gpu": int(sum(res.stats["cg_iters"])),
+                    "cg_iters_oracle": int(sum(rst.cg_iters))}
+        times_d[D] = ent
+    # (c) log-likelihood per EM iteration: CoFEM (GPU) and exact EM (oracle)
+    D, em = 4096, 30
+    pr = problem(D, 4, 3)
+    op = op64(pr)
+    y = torch.from_numpy(pr.y).cuda()
+    Phl = pr.Phi.astype(np.float64)
+    y64 = pr.y
+    alpha = torch.empty(D, dtype=torch.float64, device="cuda")
+    ll_cofem = []
+    for t in range(em):
+        api.fit(op, y, pr.beta, api.params(em_iters=1, t_offset=t, seed=2, **kw64), alpha=alpha)
+        ll_cofem.append(float(sbl.loglik(Phl, y64, pr.beta, alpha.cpu().numpy())))
+    t1 = time.perf_counter()
+    _, _, _, hist = sbl.em_exact(Phl, y64, pr.beta, em)
+    t_em = time.perf_counter() - t1
+    ll_em = [float(sbl.loglik(Phl, y64, pr.beta, a)) for a in hist[1:]]
+    gap = [abs(a - b) / abs(b) for a, b in zip(ll_cofem, ll_em)]
+    big = times_d[1 << 14].get("fp64", {}).get("seconds_30_em")
+    _common(args, "NRMSE and run time of CoFEM on the paper's dense experiments (Sec. 4.1)",
+            "seconds for 30 EM iterations at D=2^14, f=4", big, (big or 0.0) * args.steps, "f64",
+            {"workload": "paper-dense", "Phi": "iid N(0,1)", "spikes": "0.04 D, +-1",
+             "sigma": 0.005, "K": 20, "U": 400, "cg_tol": 1e-10},
+            {"higher_is_better": False,
+             "a_nrmse_vs_f": {"D": 1024, "em_iters": 50, "repetitions": reps, "by_f": nrmse_f,
+                              "seconds": t_a, "oracle_check": oracle_a},
+             "b_time_vs_D": {"f": 4, "em_iters": 30, "by_D": times_d, "oracle_check": oracle_b},
+             "c_loglik_vs_em": {"D": D, "f": 4, "em_iters": em,
+                                "cofem_every_5": ll_cofem[4::5], "exact_em_every_5": ll_em[4::5],
+                                "rel_gap_final": gap[-1], "rel_gap_max_after_10": max(gap[10:]),
+                                "exact_em_host_seconds": t_em}})
+
+
+def run_dct_sweep(args):
+    """The paper's CoFEM-vs-Seq experiment, CoFEM's side (Sec. 4.2, Fig. 1f):
+    time to 2 % NRMSE on the masked DCT dictionary for D = 2^12 .. 2^18,
+    N = D / 4 kept samples, d = 0.1 D N(0,1) coefficients, K = 20, U = 400
+    (sigma 0.005 as in the paper's dense experiments and CG tol 1e-5: not
+    stated for this experiment), at most 80 EM iterations.  The smallest
+    size is checked against the FP64 oracle (final NRMSE and mu)."""
+    import torch
+    from oracle import sbl
+    from paper_2202_12808_gb300 import api
+    from paper_2202_12808_gb300 import binding as B
+    kw = dict(vec_dtype=B.COFEM_F32, K=20, cg_tol=1e-5, cg_max_iters=400, seed=0)
+    em = 80
+    out, oracle = {}, None
+    for p in range(12, 19):
+        D = 1 << p
+        pr = datagen.dct_problem(D, D // 4, int(0.1 * D), 0.005, seed=p)
+        op = api.DctOperator(torch.from_numpy(pr.idx).cuda(), D)
+        y = torch.from_numpy(pr.y.astype(np.float32)).cuda()
+        sec, stats, hist, nrmse = whole_fit(api, B, op, y, pr.beta, kw, em, "cuda", z=pr.z)
+        out[D] = {"time_to_2pct_nrmse": time_to_nrmse(nrmse, stats["end_ns"]),
+                  "nrmse_final_pct": 100 * nrmse[-1], "nrmse_pct_every_10": [
+                      round(100 * v, 3) for v in nrmse[9::10]], "seconds_all_em": sec,
+                  "cg_iters_total": int(sum(stats["cg_iters"]))}
+        if p == 12:
+            ra, rmu, rs, rst = sbl.cofem_dct(pr.idx, D, pr.y.astype(np.float32).astype(np.float64),
+                                             pr.beta, 20, em, 1e-5, 400, seed=0)
+            mu = np.asarray(api.fit(op, y, pr.beta, api.params(em_iters=em, **kw)).mu.cpu())
+            oracle = {"case": "D=4096", "nrmse_final_gpu_pct": 100 * nrmse[-1],
+                      "nrmse_final_oracle_pct": 100 * _nrmse(rmu, pr.z),
+                      "mu_rel_l2_vs_oracle": float(np.linalg.norm(mu - rmu) / np.linalg.norm(rmu))}
+    big = out[1 << 18]["time_to_2pct_nrmse"]
+    _common(args, "seconds to 2 % NRMSE, masked DCT (Sec. 4.2, D=2^12..2^18, d=0.1D)",
+            "seconds to 2% NRMSE at D=2^18", big["seconds"] if big else None,
+            (big["seconds"] if big else 0.0) * args.steps, "f32",
+            {"workload": "dct-sweep", "N": "D/4", "d": "0.1 D", "K": 20, "U": 400,
+             "cg_tol": 1e-5, "sigma": 0.005, "em_iters_max": em},
+            {"higher_is_better": False, "by_D": out, "oracle_check": oracle})
+
+
 def run_learned(args):
     """Learned warm start / preconditioner: train on E-steps 2..20 of the
     256 x 1024 problems with seeds 1..64, evaluate CG iterations and EM
@@ -950,6 +1101,10 @@ def main():
         return run_multitask(args)
     if args.workload == "combined-128-n128-2048":
         return run_combined(args)
+    if args.workload == "paper-dense":
+        return run_paper_dense(args)
+    if args.workload == "dct-sweep":
+        return run_dct_sweep(args)
     import torch
     import torch.distributed as dist
     from paper_2202_12808_gb300 import api

@@ -76,9 +76,15 @@ typedef struct cofem_op cofem_op;
 /* Dense Phi, N x D, row-major with leading dimension ld (elements, >= D,
  * multiple of 64 for BF16/FP8, of 4 for F32/F64).  phi_dev is 256-byte
  * aligned.  dtype F64 (only with F64 vectors), F32, BF16 or FP8_E4M3 (F32
- * vectors).  For FP8 the stored value is phi / scale of its 128 x 128 tile;
- * tile_scales_dev holds ceil(N/128) x ceil(D/128) float scales (row-major);
- * NULL for the other dtypes.  Writes a new handle to *out. */
+ * vectors).  For FP8 each entry is one E4M3 byte q, standing for
+ * phi = q x scale of its 128 x 128 tile; tile_scales_dev holds ceil(N/128)
+ * x ceil(D/128) float scales (row-major), NULL for the other dtypes.  Every
+ * product of an FP8 handle applies bf16(q x scale) (the FP8 value is exact
+ * in FP32; the product is rounded to FP32, then to BF16, to nearest even):
+ * the CG operator on the tensor cores, which needs a packed copy attached
+ * (cofem_op_dense_attach_packed; without one an FP8 fit returns
+ * COFEM_ERR_UNSUPPORTED), and beta Phi^T y, forward, adjoint and column norms
+ * on the CUDA cores.  Writes a new handle to *out. */
 cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype,
                             const void* phi_dev, int64_t ld,
                             const float* tile_scales_dev, cofem_op** out);
@@ -154,8 +160,21 @@ cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev,
  * solves one consistent system; detaching (NULL) returns all of them to
  * the FP32 entries on the CUDA cores.  cofem_op_dense_packed_bytes gives the
  * size the attach call needs for any dense operator (one image for BF16,
- * two for FP32, 0 for other kinds). */
+ * two for FP32, half an image -- one byte per entry -- for FP8, 0 for other
+ * kinds). */
 size_t cofem_op_dense_packed_bytes(const cofem_op* op);
+
+/* FP8 E4M3 quantisation of an FP32 dictionary (phi_dev: N x D, leading
+ * dimension ld) into one byte per entry (out_dev, leading dimension ld_out)
+ * with a scale per 128 x 128 tile (scales_dev, ceil(N/128) x ceil(D/128)):
+ * the tile's scale is the smallest power of two s with max |phi| / s <= 448
+ * (1 for an all-zero tile), each byte e4m3(phi / s) rounded to nearest even
+ * with saturation.  Power-of-two scales make q x s exact, so an FP8 handle
+ * applies bf16(q x s) = the BF16 rounding of the quantised entry.
+ * Asynchronous. */
+cofem_status cofem_quantize_fp8_tiles(const float* phi_dev, int64_t N, int64_t D, int64_t ld,
+                                      void* out_dev, int64_t ld_out, float* scales_dev,
+                                      void* stream);
 
 /* BF16 dictionaries on the tensor cores: bytes of Phi (a band of its first
  * columns) to keep resident in L2 across the two products of every operator

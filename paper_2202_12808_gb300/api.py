@@ -48,6 +48,39 @@ class DenseOperator:
             self.handle = None
 
 
+class Fp8DenseOperator:
+    """Dense Phi stored as FP8 E4M3 with a power-of-two scale per 128 x 128
+    tile, quantised on the device by the library from an FP32 CUDA tensor
+    (N x D), with the packed copy the tensor cores read attached.  Keeps the
+    bytes, the scales and the packed copy alive."""
+
+    def __init__(self, Phi32: torch.Tensor, stream=None):
+        if not Phi32.is_cuda or Phi32.dtype != torch.float32:
+            raise ValueError("Phi must be a float32 CUDA tensor")
+        N, D = Phi32.shape
+        Phi32 = Phi32.contiguous()
+        ld = _ld(D)
+        self.phi = torch.zeros((N, ld), dtype=torch.uint8, device=Phi32.device)
+        self.scales = torch.empty(((N + 127) // 128, (D + 127) // 128), dtype=torch.float32,
+                                  device=Phi32.device)
+        st = _stream_ptr(stream)
+        B.cofem_quantize_fp8_tiles(Phi32.data_ptr(), N, D, D, self.phi.data_ptr(), ld,
+                                   self.scales.data_ptr(), st)
+        self.N, self.D = N, D
+        self.dtype = B.COFEM_FP8_E4M3
+        self.handle = B.cofem_op_dense(N, D, B.COFEM_FP8_E4M3, self.phi.data_ptr(), ld,
+                                       self.scales.data_ptr())
+        nb = B.cofem_op_dense_packed_bytes(self.handle)
+        self.packed = torch.empty(nb, dtype=torch.uint8, device=Phi32.device)
+        B.cofem_op_dense_attach_packed(self.handle, self.packed.data_ptr(), nb, st)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            B.cofem_op_destroy(h)
+            self.handle = None
+
+
 class ConvOperator:
     """Circular convolutional Phi: C filters of T taps over length-L signals."""
 

@@ -73,6 +73,7 @@ _SIGS = {
     "cofem_op_dense_set_l2_resident": (_S, [_P, _I64]),
     "cofem_dense_packed_bytes": (_SZ, [_I64, _I64]),
     "cofem_op_dense_packed_bytes": (_SZ, [_P]),
+    "cofem_quantize_fp8_tiles": (_S, [_P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     "cofem_op_dense_set_pipeline": (_S, [_P, _I32, _I32]),
     "cofem_op_dense_autotune_workspace_bytes": (_SZ, [_P, _I32]),
     "cofem_op_dense_autotune": (_S, [_P, _I32, _P, _SZ, _P, ctypes.POINTER(_I32),
@@ -199,6 +200,11 @@ def cofem_op_dense_autotune(op, ncols, ws_ptr, ws_bytes, stream=0):
 
 def cofem_dense_packed_bytes(N, D):
     return lib().cofem_dense_packed_bytes(N, D)
+
+
+def cofem_quantize_fp8_tiles(phi_ptr, N, D, ld, out_ptr, ld_out, scales_ptr, stream=0):
+    _check(lib().cofem_quantize_fp8_tiles(phi_ptr, N, D, ld, out_ptr, ld_out, scales_ptr, stream),
+           "cofem_quantize_fp8_tiles")
 
 
 def cofem_op_dense_packed_bytes(op):

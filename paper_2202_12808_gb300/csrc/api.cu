@@ -95,9 +95,13 @@ static int vec_bytes(int vec) { return vec == COFEM_F64 ? 8 : 4; }
 
 // ------------------------------------------------------------ operators
 
+static bool use_tc(const cofem_op* op);
+
 static bool op_supports(const cofem_op* op, int vec) {
   if (op->kind == 0) {
     if (vec == COFEM_F64) return op->dense.dtype == COFEM_F64;
+    // FP8 dictionaries: tensor cores only (a packed copy attached)
+    if (op->dense.dtype == COFEM_FP8_E4M3) return vec == COFEM_F32 && use_tc(op);
     if (vec == COFEM_F32) return op->dense.dtype == COFEM_F32 || op->dense.dtype == COFEM_BF16;
     return false;
   }
@@ -121,7 +125,8 @@ static const float* conv_filters64(const cofem_op* op, char* ws, int ncols, cuda
 // packed two-term copy attached (Phi = hi + lo in BF16).
 static bool use_tc(const cofem_op* op) {
   if (op->kind != 0 || op->dense.nterms <= 0) return false;
-  return op->dense.dtype == COFEM_BF16 || (op->dense.dtype == COFEM_F32 && op->dense.packed);
+  if (op->dense.dtype == COFEM_BF16) return true;
+  return (op->dense.dtype == COFEM_F32 || op->dense.dtype == COFEM_FP8_E4M3) && op->dense.packed;
 }
 
 // Scratch of one operator application.  For the tensor-core path it depends
@@ -212,7 +217,9 @@ static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64
                                int ncols, void* w, int64_t ldw, char* ws, cudaStream_t st) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
-    if (vec == COFEM_F64)
+    if (d.dtype == COFEM_FP8_E4M3)
+      fp8_forward(d, (const float*)z, ldz, ncols, (float*)w, ldw, st);
+    else if (vec == COFEM_F64)
       dense_simt_forward<double, double>(d, (const double*)z, ldz, ncols, (double*)w, ldw, ws, st);
     else if (dense_applies_hilo(d))
       dense_simt_forward<F32HiLo, float>(d, (const float*)z, ldz, ncols, (float*)w, ldw, ws, st);
@@ -242,7 +249,9 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
                                cudaStream_t st) {
   if (op->kind == 0) {
     const DenseDesc& d = op->dense;
-    if (vec == COFEM_F64)
+    if (d.dtype == COFEM_FP8_E4M3)
+      fp8_adjoint(d, (const float*)w, ldw, ncols, (float*)z, ldz, beta, st);
+    else if (vec == COFEM_F64)
       dense_simt_adjoint<double, double>(d, (const double*)w, ldw, ncols, (double*)z, ldz, beta,
                                          nullptr, nullptr, nullptr, nullptr, ws, st);
     else if (dense_applies_hilo(d))
@@ -758,8 +767,10 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   if (!out || !phi_dev || N < 1 || D < 1 || ld < D) return COFEM_ERR_INVALID_ARG;
   if (dtype != COFEM_F64 && dtype != COFEM_F32 && dtype != COFEM_BF16 && dtype != COFEM_FP8_E4M3)
     return COFEM_ERR_INVALID_ARG;
-  if (dtype == COFEM_FP8_E4M3) return COFEM_ERR_UNSUPPORTED;
-  if ((dtype == COFEM_BF16) && (ld % 64 != 0 || ((uintptr_t)phi_dev & 255)))
+  if (dtype == COFEM_FP8_E4M3 && (!tile_scales_dev || ((uintptr_t)tile_scales_dev & 3)))
+    return COFEM_ERR_INVALID_ARG;
+  if ((dtype == COFEM_BF16 || dtype == COFEM_FP8_E4M3) &&
+      (ld % 64 != 0 || ((uintptr_t)phi_dev & 255)))
     return COFEM_ERR_INVALID_ARG;
   if ((uintptr_t)phi_dev & 15) return COFEM_ERR_INVALID_ARG;
   cofem_op* op = new cofem_op();
@@ -770,7 +781,7 @@ cofem_status cofem_op_dense(int64_t N, int64_t D, cofem_dtype dtype, const void*
   op->dense.dtype = dtype;
   op->dense.phi = phi_dev;
   op->dense.scales = tile_scales_dev;
-  op->dense.nterms = dtype == COFEM_BF16 ? 3 : 0;
+  op->dense.nterms = (dtype == COFEM_BF16 || dtype == COFEM_FP8_E4M3) ? 3 : 0;
   op->dense.l2_resident_cols = 0;            // stream all of Phi (see the setter)
   op->dense.packed = nullptr;
   op->dense.tc_ctas_per_sm = 0;
@@ -813,12 +824,26 @@ size_t cofem_op_dense_packed_bytes(const cofem_op* op) {
   if (!op || op->kind != 0) return 0;
   if (op->dense.dtype == COFEM_BF16) return packed_bytes(op->dense.N, op->dense.D);
   if (op->dense.dtype == COFEM_F32) return 2 * packed_bytes(op->dense.N, op->dense.D);
+  if (op->dense.dtype == COFEM_FP8_E4M3) return packed_bytes(op->dense.N, op->dense.D) / 2;
   return 0;
+}
+
+cofem_status cofem_quantize_fp8_tiles(const float* phi_dev, int64_t N, int64_t D, int64_t ld,
+                                      void* out_dev, int64_t ld_out, float* scales_dev,
+                                      void* stream) {
+  if (!phi_dev || !out_dev || !scales_dev || N < 1 || D < 1 || ld < D || ld_out < D)
+    return COFEM_ERR_INVALID_ARG;
+  fp8_quantize_tiles(phi_dev, N, D, ld, (uint8_t*)out_dev, ld_out, scales_dev,
+                     (cudaStream_t)stream);
+  CKL();
+  return COFEM_OK;
 }
 
 cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev, size_t packed_bytes_,
                                           void* stream) {
-  if (!op || op->kind != 0 || (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32))
+  if (!op || op->kind != 0 ||
+      (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32 &&
+       op->dense.dtype != COFEM_FP8_E4M3))
     return COFEM_ERR_INVALID_ARG;
   if (!packed_dev) { op->dense.packed = nullptr; return COFEM_OK; }
   if (((uintptr_t)packed_dev & 255) != 0) return COFEM_ERR_INVALID_ARG;
@@ -827,6 +852,9 @@ cofem_status cofem_op_dense_attach_packed(cofem_op* op, void* packed_dev, size_t
     dense_pack_f32_terms((const float*)op->dense.phi, op->dense.N, op->dense.D, op->dense.ld,
                          packed_dev, (cudaStream_t)stream);
     if (op->dense.nterms == 0) op->dense.nterms = 3;
+  } else if (op->dense.dtype == COFEM_FP8_E4M3) {
+    dense_pack_fp8(op->dense.phi, op->dense.N, op->dense.D, op->dense.ld, packed_dev,
+                   (cudaStream_t)stream);
   } else {
     dense_pack_bf16(op->dense.phi, op->dense.N, op->dense.D, op->dense.ld, packed_dev,
                     (cudaStream_t)stream);
@@ -846,8 +874,10 @@ cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes) {
 }
 
 cofem_status cofem_op_dense_set_terms(cofem_op* op, int32_t nterms) {
-  if (!op || op->kind != 0 || (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32) ||
-      nterms < 0 || nterms > 3)
+  if (!op || op->kind != 0 ||
+      (op->dense.dtype != COFEM_BF16 && op->dense.dtype != COFEM_F32 &&
+       op->dense.dtype != COFEM_FP8_E4M3) ||
+      nterms < 0 || nterms > 3 || (op->dense.dtype == COFEM_FP8_E4M3 && nterms != 3))
     return COFEM_ERR_INVALID_ARG;
   op->dense.nterms = nterms;
   return COFEM_OK;
@@ -1150,7 +1180,8 @@ extern "C" cofem_status cofem_op_dense_autotune(cofem_op* op, int32_t ncols, voi
   for (int mt = 1; mt <= 2 && rc == COFEM_OK; ++mt)
   for (int cps = 1; cps <= 4 && rc == COFEM_OK; ++cps) {
     DenseTcPlan full = dense_tc_plan(op->dense.N, op->dense.D, ncols, op->dense.nterms,
-                                     num_sms(), cps, 0, op->dense.phi_terms, mt);
+                                     num_sms(), cps, 0, op->dense.phi_terms, mt,
+                                     op->dense.dtype == COFEM_FP8_E4M3);
     // two tiles per unit need room for four accumulators (else the plan is
     // the one-tile plan, timed already); with all of the tensor memory taken,
     // shapes differ only in stages

@@ -41,6 +41,21 @@ void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* pa
 // hi + lo carries 16 significant bits of every entry.
 void dense_pack_f32_terms(const float* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                           cudaStream_t st);
+// FP8 E4M3 dictionary: one packed image of packed_bytes(N, D) / 2 bytes, each
+// entry's byte at the position of its BF16 value in the BF16 layout.
+void dense_pack_fp8(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                    cudaStream_t st);
+// FP8 quantisation of an FP32 dictionary: per 128 x 128 tile, scale = the
+// smallest power of two with max |phi| / scale <= 448, bytes =
+// e4m3(phi / scale) (round to nearest even, saturating); and the CUDA-core
+// products of an FP8 dictionary (entries bf16(e4m3 x scale)).
+void fp8_quantize_tiles(const float* phi, int64_t N, int64_t D, int64_t ld, uint8_t* out,
+                        int64_t ld_out, float* scales, cudaStream_t st);
+void fp8_forward(const DenseDesc& op, const float* Z, int64_t ldz, int ncols, float* W,
+                 int64_t ldw, cudaStream_t st);
+void fp8_adjoint(const DenseDesc& op, const float* W, int64_t ldw, int ncols, float* Z,
+                 int64_t ldz, double beta, cudaStream_t st);
+void fp8_col_norms(const DenseDesc& op, float* out, cudaStream_t st);
 
 
 // An FP32 dictionary entry as the tensor-core operator applies it once a
@@ -103,6 +118,7 @@ DenseSimtPlan dense_simt_plan(int64_t N, int64_t D, int ncols, int vec_bytes, in
 struct DenseTcPlan {
   int NT, nc, BN;            // terms, output columns, MMA N (B-operand rows)
   int MT;                    // 128-row output tiles per work unit
+  bool fp8;                  // FP8 dictionary (converter warps, staging area)
   uint32_t acc_cols;         // tensor-memory columns of one accumulator
   uint32_t tmem_cols;        // tensor-memory columns allocated per CTA (two accumulators)
   int grid;                  // resident CTAs of one launch (ctas per SM x SMs)
@@ -116,11 +132,14 @@ struct DenseTcPlan {
 // PT: BF16 terms per Phi entry (1 or 2); MT: 128-row output tiles per work
 // unit (1 or 2); a ring stage holds MT x PT A tiles and one B tile, and a CTA
 // allocates 2 x MT accumulators.
+// fp8: an FP8 dictionary (one byte per entry in the packed copy): a stage
+// also holds the 8 KB of bytes the converter warps expand (MT = PT = 1).
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm = 2,
-                          int stages = 0, int PT = 1, int MT = 1);
+                          int stages = 0, int PT = 1, int MT = 1, bool fp8 = false);
 inline DenseTcPlan dense_tc_plan(const DenseDesc& op, int nc, int sms) {
   return dense_tc_plan(op.N, op.D, nc, op.nterms, sms, op.tc_ctas_per_sm, op.tc_stages,
-                       op.phi_terms > 1 ? 2 : 1, op.tc_row_tiles > 1 ? 2 : 1);
+                       op.phi_terms > 1 ? 2 : 1, op.tc_row_tiles > 1 ? 2 : 1,
+                       op.dtype == COFEM_FP8_E4M3);
 }
 
 // Y = beta Phi^T Phi X + alpha . X on tcgen05; returns 0, 1 (tensor map

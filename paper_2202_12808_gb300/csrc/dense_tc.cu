@@ -27,6 +27,8 @@
 #include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "dense.cuh"
 #include "tc_ptx.cuh"
@@ -34,6 +36,7 @@
 namespace cofem {
 
 constexpr int kTcThreads = 192;     // warp 0 TMA, warp 1 MMA/TMEM, warps 2-5 epilogue
+constexpr int kTcThreadsFp8 = 320;  // FP8 dictionaries: warps 6-9 convert A tiles to BF16
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;          // 64 bf16 = one 128-byte swizzle row
 constexpr uint32_t kATileBytes = kTileM * kTileK * 2;
@@ -69,6 +72,10 @@ struct TcArgs {
                         // (one accumulator each); otherwise one
   int64_t tiles_a;      // packed A tiles along the output rows: 128-row tiles of Phi
                         // (first product), 64-column tiles (second product)
+  int fp8;              // FP8 E4M3 dictionary: the packed copy holds one byte per
+                        // entry; converter warps turn each A tile into BF16
+  const float* scales;  // FP8: scale of every 128 x 128 tile of Phi, row-major
+  int64_t scale_cols;   // FP8: tiles per row of the scale table (ceil(D / 128))
   int64_t nkd;          // 64-column tiles of Phi (packed layout)
   // GEMM1: split-K partials (reduced and split by reduce_split_kernel)
   float* wpart;
@@ -174,8 +181,18 @@ __device__ __forceinline__ bool unit_skipped(const TcArgs& args, int w) {
 // shared-memory ring runs on across units (one K-block counter for the
 // whole CTA), and two tensor-memory accumulators alternate between units so
 // that the epilogue of one unit overlaps the main loop of the next.
-template <int MODE, int NT>
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Two E4M3 values (low byte first) times `scale`, rounded to BF16 (the
+// FP8 -> FP16 conversion is exact; the product is rounded to FP32, then to
+// BF16, both to nearest even).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint16_t v, float scale) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)v, __NV_E4M3);
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&h));
+  const __nv_bfloat162 b = __floats2bfloat162_rn(f.x * scale, f.y * scale);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+template <int MODE, int NT, bool A8>
+__global__ void __launch_bounds__(A8 ? kTcThreadsFp8 : kTcThreads, 1)
 dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const TcArgs args) {
   pdl_wait();
@@ -188,13 +205,17 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int MT = args.row_tiles > 1 ? 2 : 1;          // 128-row output tiles per unit
   // a stage holds MT x PT A tiles (tile (mt, pt) at (mt PT + pt) x 16 KB) and one B tile
   const uint32_t a_bytes = (uint32_t)(MT * PT) * kATileBytes;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
+  // FP8: the bulk copy lands in a staging area after the B tile (half the
+  // bytes of the BF16 A tile), which the converter warps expand into A
+  const uint32_t a8_bytes = A8 ? kATileBytes / 2 : 0u;
+  const uint32_t stage_bytes = a_bytes + b_bytes + a8_bytes;
   const int S = args.stages;
   uint64_t* full = (uint64_t*)(smem + S * stage_bytes);
   uint64_t* empty = full + kMaxStages;
   uint64_t* accfull = empty + kMaxStages;          // [2] accumulator ready
   uint64_t* accempty = accfull + 2;                // [2] accumulator drained
-  uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+  uint64_t* conv = accempty + 2;                   // [stages] FP8: A converted to BF16
+  uint32_t* tmem_slot = (uint32_t*)(conv + kMaxStages);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   volatile int* bigflag = (volatile int*)(tmem_slot + 2);
   // epilogue partial dots per warp and column: compensated FP32 pairs, and
@@ -208,6 +229,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&conv[s], 4);                  // the four converter warps
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accfull[b], 1);
@@ -247,9 +269,30 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
           uint8_t* sa = smem + s * stage_bytes;
           uint8_t* sb = sa + a_bytes;
-          tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
           const int kb = u.kb0 + i;
           const int64_t m0 = u.m0;
+          if constexpr (A8) {
+            // one byte per entry: the same tile layout as the BF16 copy, each
+            // byte standing at the position of its BF16 value
+            uint8_t* s8 = sb + b_bytes;
+            const uint8_t* pk8 = reinterpret_cast<const uint8_t*>(u.pk);
+            tc::mbar_arrive_expect_tx(&full[s], a8_bytes + b_bytes);
+            const uint64_t pol_a = pol_first;
+            if (MODE == 0) {
+              tc::bulk_load(s8, pk8 + ((m0 >> 7) * u.nkd + kb) * (int64_t)(kTileM * kTileK),
+                            a8_bytes, &full[s], pol_a);
+            } else {
+              const int64_t c = m0 >> 6;
+              const int64_t base = ((int64_t)(kb >> 1) * u.nkd + c) * kTileM + (kb & 1) * 64;
+              const uint8_t* src = pk8 + base * kTileK;
+              const uint8_t* src2 = c + 1 < u.nkd ? src + kTileM * kTileK : src;
+              tc::bulk_load(s8, src, a8_bytes / 2, &full[s], pol_a);
+              tc::bulk_load(s8 + a8_bytes / 2, src2, a8_bytes / 2, &full[s], pol_a);
+            }
+            tc::tma_load_2d(sb, &mapB, &full[s], (int)(u.bx0 + (int64_t)kb * kTileK), 0, pol_b);
+            continue;
+          }
+          tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
           // Phi columns below res_d stay in L2 between the two products and
           // across CG iterations; the rest streams through
           if (MODE == 0) {
@@ -337,7 +380,8 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         for (int i = 0; i < nk; ++i, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
+          if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs) ||
+              (A8 && !tc::mbar_wait(&conv[s], ph, abort, kWaitLimitNs))) {
             tc_fail(args.err, abort);
             break;
           }
@@ -362,6 +406,51 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
         tc::mma_commit(&accfull[b]);
       }
+    }
+  } else if (A8 && warp >= 6) {
+    // ------------------------------------------------- FP8 -> BF16 (A tiles)
+    // 128 threads expand each stage's 8 KB of E4M3 bytes into the 16 KB BF16
+    // A tile, times the scale of the 128 x 128 tile of Phi it belongs to
+    const int ct = threadIdx.x - 192;
+    int it = 0;
+    for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x) {
+      if (unit_skipped(args, w)) continue;
+      const TcUnit u = tc_unit<MODE>(args, w);
+      const int nk = max(0, u.kb1 - u.kb0);
+      bool ok = true;
+      for (int i = 0; i < nk; ++i, ++it) {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!tc::mbar_wait(&full[s], ph, abort, kWaitLimitNs)) {
+          tc_fail(args.err, abort);
+          ok = false;
+          break;
+        }
+        const int kb = u.kb0 + i;
+        const float scale = MODE == 0 ? args.scales[(u.m0 >> 7) * args.scale_cols + (kb >> 1)]
+                                      : args.scales[(int64_t)(kb >> 1) * args.scale_cols + (u.m0 >> 7)];
+        uint8_t* sa = smem + s * stage_bytes;
+        const uint4* s8 = reinterpret_cast<const uint4*>(sa + a_bytes + b_bytes);
+        uint4* d16 = reinterpret_cast<uint4*>(sa);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c16 = q * 128 + ct;            // 16-byte chunk of FP8 bytes
+          const uint4 v = s8[c16];
+          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+          uint32_t o[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            o[2 * k] = e4m3x2_to_bf16x2((uint16_t)(w4[k] & 0xffffu), scale);
+            o[2 * k + 1] = e4m3x2_to_bf16x2((uint16_t)(w4[k] >> 16), scale);
+          }
+          d16[2 * c16] = make_uint4(o[0], o[1], o[2], o[3]);
+          d16[2 * c16 + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[s]);
+      }
+      if (!ok) break;
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -685,6 +774,37 @@ void dense_pack_f32_terms(const float* phi, int64_t N, int64_t D, int64_t ld, vo
            st, phi, N, D, ld, packed_tiles_k(D), total8, (__nv_bfloat16*)packed);
 }
 
+// FP8 dictionary (one byte per entry, row-major with leading dimension ld):
+// the same tile layout, one byte at the position of each BF16 value.
+__global__ void pack_fp8_kernel(const uint8_t* __restrict__ phi, int64_t N, int64_t D,
+                                int64_t ld, int64_t nkd, int64_t total8,
+                                uint8_t* __restrict__ packed) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total8;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * 8;
+    const int64_t row = e >> 6;
+    const int c0 = (int)((((e & 63) >> 3) ^ (row & 7)) << 3);
+    const int r = (int)(row & 127);
+    const int64_t tile = row >> 7;
+    const int64_t kb = tile % nkd, mt = tile / nkd;
+    const int64_t n = mt * 128 + r, d0 = kb * 64 + c0;
+    uint8_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (n < N && d0 + q < D) ? phi[n * ld + d0 + q] : (uint8_t)0;
+    *reinterpret_cast<uint2*>(packed + e) = *reinterpret_cast<uint2*>(v);
+  }
+}
+
+void dense_pack_fp8(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
+                    cudaStream_t st) {
+  const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
+  const int64_t blocks = (total8 + 255) / 256;
+  launch_k(pack_fp8_kernel, dim3((unsigned)(blocks < 65535 ? blocks : 65535)), dim3(256), 0, st,
+           (const uint8_t*)phi, N, D, ld, packed_tiles_k(D), total8, (uint8_t*)packed);
+}
+
 void dense_pack_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, void* packed,
                      cudaStream_t st) {
   const int64_t total8 = (int64_t)(packed_bytes(N, D) / 16);
@@ -775,10 +895,12 @@ static bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t 
 static int term_group(int NT) { return 16 / NT; }
 
 DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int ctas_per_sm,
-                          int stages, int PT, int MT) {
+                          int stages, int PT, int MT, bool fp8) {
   DenseTcPlan p;
   if (ctas_per_sm < 1 || ctas_per_sm > 4) ctas_per_sm = 2;
-  MT = MT > 1 ? 2 : 1;
+  MT = MT > 1 && !fp8 ? 2 : 1;
+  if (fp8) PT = 1;
+  p.fp8 = fp8;
   p.NT = NT;
   p.nc = nc;
   const int ngroups = (nc + term_group(NT) - 1) / term_group(NT);
@@ -820,8 +942,9 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
     int kb, sr;
     if (per_cta(s1, &kb, &sr) * 10 <= best * 11) { p.S1 = sr; p.kbps1 = kb; break; }
   }
-  const size_t fixed = 1024 + 2 * kMaxStages * 8 + 32 + 64 + 4 * 64 * 8 * 2 + 64;
-  const size_t stage = (size_t)((PT > 1 ? 2 : 1) * MT) * kATileBytes + (size_t)p.BN * 128;
+  const size_t fixed = 1024 + 3 * kMaxStages * 8 + 32 + 64 + 4 * 64 * 8 * 2 + 64;
+  const size_t stage = (size_t)((PT > 1 ? 2 : 1) * MT) * kATileBytes + (size_t)p.BN * 128 +
+                       (fp8 ? kATileBytes / 2 : 0);
   // each resident CTA also costs 1 KB of reserved shared memory
   const size_t budget = kSmemPerSm / per_sm - 1024;
   int st = (int)((budget - fixed) / stage);
@@ -848,7 +971,18 @@ DenseTcPlan dense_tc_plan(int64_t N, int64_t D, int nc, int NT, int sms, int cta
 template <int MODE, int NT>
 static cudaError_t launch_tc(dim3 grid, size_t smem, const CUtensorMap& a, const CUtensorMap& b,
                              const TcArgs& args, cudaStream_t st) {
-  auto k = dense_tc_kernel<MODE, NT>;
+  if (args.fp8) {
+    if constexpr (NT == 3) {
+      auto k = dense_tc_kernel<MODE, NT, true>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      launch_k(k, dim3(grid), dim3(kTcThreadsFp8), smem, st, a, b, args);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;          // FP8 dictionaries take three vector terms
+    }
+  }
+  auto k = dense_tc_kernel<MODE, NT, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   launch_k(k, dim3(grid), dim3(kTcThreads), smem, st, a, b, args);
@@ -861,10 +995,12 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
                             char* ws, int* err, unsigned flags, cudaStream_t st,
                             const float* alpha32, const int* gate) {
   const int sms = num_sms();
+  const bool fp8 = op.dtype == COFEM_FP8_E4M3;
   const int PT = op.phi_terms > 1 && op.packed ? 2 : 1;
   DenseTcPlan p = dense_tc_plan(op.N, op.D, nc, NT, sms, op.tc_ctas_per_sm, op.tc_stages, PT,
-                                op.tc_row_tiles > 1 ? 2 : 1);
+                                op.tc_row_tiles > 1 ? 2 : 1, fp8);
   const int MT = p.MT;                   // the plan falls back to one tile when TMEM is short
+  if (fp8 && !op.packed) return 1;       // FP8 dictionaries run from the packed copy only
   const bool presplit = (flags & kApplyPresplit) != 0;
   __nv_bfloat16* Xs = (__nv_bfloat16*)(ws + p.off_xs);
   float* Wp = (float*)(ws + p.off_wpart);
@@ -910,6 +1046,9 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a1.gate = gate;
   a1.row_tiles = MT;
   a1.tiles_a = packed_tiles_m(op.N);
+  a1.fp8 = fp8;
+  a1.scales = op.scales;
+  a1.scale_cols = (op.D + 127) / 128;
   a1.units_m = (int)((op.N + kTileM * MT - 1) / (kTileM * MT));
   a1.units = a1.units_m * p.S1;
   a1.acc_cols = p.acc_cols;
@@ -948,6 +1087,9 @@ static int dense_tc_apply_t(const DenseDesc& op, const float* X, int64_t ld, int
   a2.gate = gate;
   a2.row_tiles = MT;
   a2.tiles_a = nkd;
+  a2.fp8 = fp8;
+  a2.scales = op.scales;
+  a2.scale_cols = (op.D + 127) / 128;
   a2.units_m = (int)((op.D + kTileM * MT - 1) / (kTileM * MT));
   a2.units = a2.units_m;
   a2.acc_cols = p.acc_cols;

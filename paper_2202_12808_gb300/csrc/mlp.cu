@@ -413,7 +413,9 @@ void launch_col_norms_bf16(const void* phi, int64_t N, int64_t D, int64_t ld, fl
 cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st) {
   if (op_is_dense(op)) {
     const DenseDesc d = op_dense_desc(op);
-    if (d.dtype == COFEM_F64)
+    if (d.dtype == COFEM_FP8_E4M3)
+      fp8_col_norms(d, out, st);
+    else if (d.dtype == COFEM_F64)
       launch_k(col_norms_kernel<double>, dim3(blocks_for(d.D, 256)), dim3(256), 0, st,
                (const double*)d.phi, d.N, d.D, d.ld, out);
     else if (dense_applies_hilo(d))

@@ -20,7 +20,7 @@ from oracle import sbl
 from paper_2202_12808_gb300 import api
 from paper_2202_12808_gb300 import binding as B
 from paper_2202_12808_gb300 import datagen
-from gpu_helpers import bf16_round, rel_l2, support_compare
+from gpu_helpers import bf16_round, fp8_applied, rel_l2, support_compare
 
 pytestmark = pytest.mark.gpu
 
@@ -134,6 +134,39 @@ def test_fp32_tolerance_mode_config1(cuda_lib, phi_kind):
     assert rel_l2(mu, rmu) <= 1e-4
     sup = (ra < 1e6) & (a < 1e6)
     assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 1e-3
+
+
+@pytest.mark.parametrize("replace", [0, 10])
+def test_fp8_dictionary_fit(cuda_lib, replace):
+    """FP8 E4M3 dictionary with power-of-two tile scales (quantised by the
+    library) on the tensor cores, config 1 at tol 1e-6 (and residual
+    replacement every 10 at sigma 0.1, where FP32 can reach the true
+    residual), against the oracle on the dictionary the handle applies,
+    bf16(q x scale) (reading R12 as for BF16): the FP32 bars for mu and the
+    support; alpha on the support at 3e-3, because an FP32 emulation of the
+    oracle on this dictionary itself moves alpha by 1.3e-3
+    (tests/test_tolerance_evidence.py::test_fp8_dictionary_alpha_sensitivity)."""
+    sigma = 0.01 if replace == 0 else 0.1
+    prob = _problem(sigma=sigma, seed=0 if replace == 0 else 4)
+    op = api.Fp8DenseOperator(torch.from_numpy(prob.Phi).cuda())
+    torch.cuda.synchronize()
+    Phi_ref = fp8_applied(op.phi[:, :prob.Phi.shape[1]].cpu().numpy(), op.scales.cpu().numpy())
+    y32 = prob.y.astype(np.float32).astype(np.float64)
+    c = CFG1
+    em = c["em_iters"] if replace == 0 else 30
+    tol = c["cg_tol"] if replace == 0 else 1e-5
+    p = api.params(vec_dtype=B.COFEM_F32, K=c["K"], em_iters=em, cg_tol=tol,
+                   cg_max_iters=c["cg_max_iters"], seed=0, resid_replace_every=replace)
+    r = api.fit(op, torch.from_numpy(y32).float().cuda(), prob.beta, p)
+    torch.cuda.synchronize()
+    ra, rmu, rs, rst = sbl.cofem_dense(Phi_ref, y32, prob.beta, c["K"], em, tol,
+                                       c["cg_max_iters"], seed=0, resid_replace_every=replace)
+    a, mu = r.alpha.cpu().numpy(), r.mu.cpu().numpy()
+    eq, border = support_compare(a, ra)
+    assert eq, border
+    assert rel_l2(mu, rmu) <= 1e-4, rel_l2(mu, rmu)
+    sup = (ra < 1e6) & (a < 1e6)
+    assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 3e-3
 
 
 def test_ragged_small_fp64_and_replacement(cuda_lib):

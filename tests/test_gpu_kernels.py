@@ -9,7 +9,8 @@ from oracle import probe_hash as ph
 from oracle import sbl
 from paper_2202_12808_gb300 import binding as B
 from paper_2202_12808_gb300 import datagen
-from gpu_helpers import bf16_round, from_block, ld_of, phi_tensor, rel_l2, to_block
+from gpu_helpers import (bf16_round, fp8_applied, fp8_quantize_reference, from_block, ld_of,
+                         phi_tensor, rel_l2, to_block)
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +53,7 @@ APPLY_CASES = [
 @pytest.mark.parametrize("N,D,ncols", APPLY_CASES)
 @pytest.mark.parametrize("kind", ["f64", "f32", "f32-packed", "f32-packed-r256", "bf16",
                                   "bf16-t2", "bf16-t1", "bf16-simt", "bf16-packed",
-                                  "bf16-packed-t1", "bf16-r256", "bf16-packed-r256"])
+                                  "bf16-packed-t1", "bf16-r256", "bf16-packed-r256", "fp8"])
 def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
     prob = datagen.dense_problem(N, D, max(1, D // 50), 0.01, seed=N + D + ncols)
     rng = np.random.default_rng(ncols)
@@ -71,6 +72,15 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         Phi_t, ld_phi = phi_tensor(prob.Phi, torch.float32)
         vdt, vec, tol = torch.float32, B.COFEM_F32, 2e-5
         pdt = B.COFEM_F32
+    elif kind == "fp8":
+        # E4M3 bytes with a power-of-two scale per 128 x 128 tile (quantised
+        # on the CPU); the oracle applies bf16(q x scale)
+        q, scales, Phi_ref = fp8_quantize_reference(prob.Phi)
+        ld_phi = ld_of(D)
+        Phi_t = torch.zeros((N, ld_phi), dtype=torch.uint8, device="cuda")
+        Phi_t[:, :D] = torch.from_numpy(q).cuda()
+        scales_t = torch.from_numpy(scales).cuda()
+        vdt, vec, pdt, tol = torch.float32, B.COFEM_F32, B.COFEM_FP8_E4M3, 2e-5
     else:
         t16, Phi_ref = bf16_round(prob.Phi)
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
@@ -80,7 +90,8 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
                  "bf16-packed-t1": 1, "bf16-r256": 3, "bf16-packed-r256": 3}[kind]
         tol = {3: 2e-5, 2: 6e-5, 1: 8e-3, 0: 2e-5}[terms]
     X_in = X.astype(np.float32).astype(np.float64) if vdt == torch.float32 else X
-    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
+    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi,
+                          scales_t.data_ptr() if kind == "fp8" else None)
     if pdt == B.COFEM_BF16:
         B.cofem_op_dense_set_terms(op, terms)
     if kind.endswith("-r256"):
@@ -88,9 +99,11 @@ def test_op_apply_dense(cuda_lib, N, D, ncols, kind):
         B.cofem_op_dense_set_tile_rows(op, 256)
         assert B.cofem_op_dense_get_pipeline(op)[2] == 256
     packed = None
-    if kind.startswith("bf16-packed") or kind.startswith("f32-packed"):
+    if kind.startswith("bf16-packed") or kind.startswith("f32-packed") or kind == "fp8":
         nb = B.cofem_op_dense_packed_bytes(op)
-        assert nb == B.cofem_dense_packed_bytes(N, D) * (2 if kind.startswith("f32") else 1)
+        assert nb == {"f": B.cofem_dense_packed_bytes(N, D) * 2,
+                      "b": B.cofem_dense_packed_bytes(N, D),
+                      "p": B.cofem_dense_packed_bytes(N, D) // 2}[kind[0] if kind != "fp8" else "p"]
         packed = torch.empty(nb, dtype=torch.uint8, device="cuda")
         B.cofem_op_dense_attach_packed(op, packed.data_ptr(), nb)
     try:
@@ -156,6 +169,26 @@ def test_diag_mstep(cuda_lib, K, D):
         assert c[1] == int(np.sum(a < 1e6))
 
 
+@pytest.mark.parametrize("N,D", [(300, 1100), (128, 128), (1000, 4096)])
+def test_fp8_quantize_matches_definition(cuda_lib, N, D):
+    """cofem_quantize_fp8_tiles against its definition computed on the CPU:
+    power-of-two tile scales, E4M3 bytes bit for bit (tiles of very
+    different magnitude, an all-zero tile, ragged edges)."""
+    rng = np.random.default_rng(N + D)
+    Phi = rng.standard_normal((N, D)).astype(np.float32)
+    Phi *= np.exp(rng.uniform(-8, 8, ((N + 127) // 128, (D + 127) // 128))).astype(
+        np.float32).repeat(128, 0).repeat(128, 1)[:N, :D]
+    Phi[:min(N, 128), :min(D, 128)] = 0.0
+    q_ref, s_ref, _ = fp8_quantize_reference(Phi)
+    P = torch.from_numpy(Phi).cuda()
+    q = torch.zeros((N, ld_of(D)), dtype=torch.uint8, device="cuda")
+    sc = torch.empty(((N + 127) // 128, (D + 127) // 128), dtype=torch.float32, device="cuda")
+    B.cofem_quantize_fp8_tiles(P.data_ptr(), N, D, D, q.data_ptr(), ld_of(D), sc.data_ptr())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(sc.cpu().numpy(), s_ref)
+    np.testing.assert_array_equal(q[:, :D].cpu().numpy(), q_ref)
+
+
 def test_f32_packed_terms_are_hi_plus_lo(cuda_lib):
     """The two packed images of an FP32 dictionary: applying Phi = hi + lo
     with exact-valued inputs matches the oracle's product with hi + lo
@@ -194,17 +227,28 @@ def test_f32_packed_terms_are_hi_plus_lo(cuda_lib):
 
 
 @pytest.mark.parametrize("packed,rows", [(False, 128), (True, 128), ("f32", 128), (True, 256),
-                                         ("f32", 256)])
+                                         ("f32", 256), ("fp8", 128)])
 def test_op_apply_tensor_core_full_size(cuda_lib, packed, rows):
     # the bench workload's operator (N=4096, D=32768, 33 columns, BF16 Phi,
     # 3-term split) on sampled output rows computed one by one by the oracle
     N, D, ncols = 4096, 32768, 33
     prob = datagen.dense_problem(N, D, 655, 0.01, seed=0)
+    scales_ptr = None
     if packed == "f32":
         # FP32 Phi on the tensor cores (hi + lo), against the FP32 Phi
         Phi_ref = prob.Phi.astype(np.float64)
         Phi_t, ld_phi = phi_tensor(prob.Phi, torch.float32)
         pdt = B.COFEM_F32
+    elif packed == "fp8":
+        # quantised by the library; the oracle applies bf16(q x scale)
+        P32 = torch.from_numpy(prob.Phi).cuda()
+        Phi_t = torch.zeros((N, D), dtype=torch.uint8, device="cuda")
+        sc = torch.empty((N // 128, D // 128), dtype=torch.float32, device="cuda")
+        B.cofem_quantize_fp8_tiles(P32.data_ptr(), N, D, D, Phi_t.data_ptr(), D, sc.data_ptr())
+        torch.cuda.synchronize()
+        del P32
+        Phi_ref = fp8_applied(Phi_t.cpu().numpy(), sc.cpu().numpy())
+        ld_phi, pdt, scales_ptr = D, B.COFEM_FP8_E4M3, sc.data_ptr()
     else:
         t16, Phi_ref = bf16_round(prob.Phi)
         Phi_t, ld_phi = phi_tensor(Phi_ref, torch.bfloat16)
@@ -213,7 +257,7 @@ def test_op_apply_tensor_core_full_size(cuda_lib, packed, rows):
     X = rng.standard_normal((D, ncols)).astype(np.float32).astype(np.float64)
     alpha = rng.uniform(0.5, 1e6, D)
     beta = 1e4
-    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi)
+    op = B.cofem_op_dense(N, D, pdt, Phi_t.data_ptr(), ld_phi, scales_ptr)
     B.cofem_op_dense_set_tile_rows(op, rows)
     if packed:
         nb = B.cofem_op_dense_packed_bytes(op)

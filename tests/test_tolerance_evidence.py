@@ -15,7 +15,9 @@ the GPU tests cite for their bars:
   and the bars of the sigma = 0.01 case at 50 EM iterations;
 * tests/test_gpu_dct.py::test_dct_fit_fp32 -- alpha on the support at 3e-3;
 * tests/test_gpu_headline.py -- the full-shape fit is compared after its
-  first EM iteration only.
+  first EM iteration only;
+* tests/test_gpu_fit.py::test_fp8_dictionary_fit -- alpha on the support
+  at 3e-3 with the FP8 dictionary.
 """
 import numpy as np
 import pytest
@@ -25,7 +27,7 @@ import torch
 from oracle import emulation as em
 from oracle import sbl
 from paper_2202_12808_gb300 import datagen
-from gpu_helpers import rel_l2, support_compare
+from gpu_helpers import fp8_quantize_reference, rel_l2, support_compare
 
 
 def _bf16(Phi32):
@@ -226,3 +228,21 @@ def test_headline_shape_trajectory_amplifies_fp32_rounding():
     e2 = em.cofem_dense(*args, seed=0, vround=em.fp32_round, fp32_products=True)
     assert e2[3].cg_iters == r2[3].cg_iters
     assert rel_l2(e2[1], r2[1]) > 1e-2
+
+
+def test_fp8_dictionary_alpha_sensitivity():
+    """Config 1 with the dictionary an FP8 handle applies (E4M3, power-of-two
+    tile scales, bf16(q x scale)): the FP32 emulation of the oracle stays
+    within the FP32 bars for mu (6e-6) and the support, but moves alpha on
+    the support by 1.3e-3, past the 1e-3 bar -- so the FP8 fit's alpha bar
+    is 3e-3."""
+    c = datagen.CONFIGS["dense-fp64-n256-d1024"]
+    pr = datagen.dense_problem(c["N"], c["D"], c["n_nonzero"], c["sigma"], 0)
+    _, _, Phi = fp8_quantize_reference(pr.Phi)
+    y32 = pr.y.astype(np.float32).astype(np.float64)
+    args = (Phi, y32, pr.beta, c["K"], c["em_iters"], c["cg_tol"], c["cg_max_iters"])
+    ra, rmu, rs, rst = sbl.cofem_dense(*args, seed=0)
+    ea, emu, es, est = em.cofem_dense(*args, seed=0, vround=em.fp32_round, fp32_products=True)
+    assert rel_l2(emu, rmu) <= 1e-4
+    assert support_compare(ea, ra)[0]
+    assert 1e-3 < _alpha_dev(ea, ra) < 3e-3

@@ -36,7 +36,8 @@
 namespace cofem {
 
 constexpr int kTcThreads = 192;     // warp 0 TMA, warp 1 MMA/TMEM, warps 2-5 epilogue
-constexpr int kTcThreadsFp8 = 320;  // FP8 dictionaries: warps 6-9 convert A tiles to BF16
+constexpr int kTcThreadsFp8 = 448;  // FP8 dictionaries: warps 6-13 convert A tiles to BF16
+constexpr int kCvtWarps = (kTcThreadsFp8 - kTcThreads) / 32;
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;          // 64 bf16 = one 128-byte swizzle row
 constexpr uint32_t kATileBytes = kTileM * kTileK * 2;
@@ -229,7 +230,7 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
-      tc::mbar_init(&conv[s], 4);                  // the four converter warps
+      tc::mbar_init(&conv[s], kCvtWarps);          // the converter warps
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accfull[b], 1);
@@ -407,11 +408,15 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         tc::mma_commit(&accfull[b]);
       }
     }
-  } else if (A8 && warp >= 6) {
+  } else if (A8 && warp >= kTcThreads / 32) {
     // ------------------------------------------------- FP8 -> BF16 (A tiles)
-    // 128 threads expand each stage's 8 KB of E4M3 bytes into the 16 KB BF16
-    // A tile, times the scale of the 128 x 128 tile of Phi it belongs to
-    const int ct = threadIdx.x - 192;
+    // kCvtWarps warps expand each stage's 8 KB of E4M3 bytes into the 16 KB
+    // BF16 A tile, times the scale of the 128 x 128 tile of Phi it belongs
+    // to; each thread loads all its chunks before converting any (the loads
+    // overlap) and stores after
+    constexpr int kCvtThreads = kCvtWarps * 32;
+    constexpr int kChunks = 512 / kCvtThreads;   // 16-byte chunks per thread and stage
+    const int ct = threadIdx.x - kTcThreads;
     int it = 0;
     for (int w = blockIdx.x; w < units && !*abort; w += gridDim.x) {
       if (unit_skipped(args, w)) continue;
@@ -432,11 +437,13 @@ dense_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         uint8_t* sa = smem + s * stage_bytes;
         const uint4* s8 = reinterpret_cast<const uint4*>(sa + a_bytes + b_bytes);
         uint4* d16 = reinterpret_cast<uint4*>(sa);
+        uint4 v[kChunks];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c16 = q * 128 + ct;            // 16-byte chunk of FP8 bytes
-          const uint4 v = s8[c16];
-          const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < kChunks; ++q) v[q] = s8[q * kCvtThreads + ct];
+#pragma unroll
+        for (int q = 0; q < kChunks; ++q) {
+          const int c16 = q * kCvtThreads + ct;    // 16-byte chunk of FP8 bytes
+          const uint32_t w4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
           uint32_t o[8];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {

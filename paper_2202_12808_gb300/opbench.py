@@ -8,8 +8,9 @@ outside any fit graph:
     python -m paper_2202_12808_gb300.opbench --op dense-f32  --N 4096 --D 32768 --ncols 33
     python -m paper_2202_12808_gb300.opbench --op cg --D 1048576 --ncols 33
 
-dense-bf16 / dense-f32: A X = beta Phi^T (Phi X) + alpha . X on the tensor
-cores (BF16 dictionary, or FP32 dictionary as hi + lo), packed tile layout,
+dense-bf16 / dense-f32 / dense-fp8: A X = beta Phi^T (Phi X) + alpha . X on
+the tensor cores (BF16 dictionary, FP32 dictionary as hi + lo, or FP8 E4M3
+with per-tile scales expanded to BF16 in shared memory), packed layout,
 pipeline autotuned unless --no-autotune; prints the per-kernel microseconds
 of cofem_op_apply_timed.  cg: the CG update (direction fused where it fits),
 the direction update and the diagonal estimate + M-step
@@ -27,7 +28,7 @@ from . import binding as B
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "cg"], required=True)
+    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "dense-fp8", "cg"], required=True)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--D", type=int, default=32768)
     ap.add_argument("--ncols", type=int, default=33)
@@ -50,12 +51,16 @@ def main():
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     Phi = torch.randn((a.N, a.D), generator=g, device="cuda") / float(np.sqrt(a.N))
-    if a.op == "dense-bf16":
-        Phi = Phi.to(torch.bfloat16)
-    op = api.DenseOperator(Phi)
-    nbp = B.cofem_op_dense_packed_bytes(op.handle)
-    packed = torch.empty(nbp, dtype=torch.uint8, device="cuda")
-    B.cofem_op_dense_attach_packed(op.handle, packed.data_ptr(), nbp, st)
+    if a.op == "dense-fp8":
+        op = api.Fp8DenseOperator(Phi)             # quantised, packed copy attached
+        del Phi
+    else:
+        if a.op == "dense-bf16":
+            Phi = Phi.to(torch.bfloat16)
+        op = api.DenseOperator(Phi)
+        nbp = B.cofem_op_dense_packed_bytes(op.handle)
+        packed = torch.empty(nbp, dtype=torch.uint8, device="cuda")
+        B.cofem_op_dense_attach_packed(op.handle, packed.data_ptr(), nbp, st)
     tuned = None
     if a.pipeline:
         stg, cps = (int(v) for v in a.pipeline.split(","))

@@ -37,6 +37,8 @@ notes of the repository):
   mask") uses the orthonormal DCT-II / DCT-III pair, so Phi Phi^T = I_N;
   the mask keeps a uniformly random set of N = D/4 samples.
 * Optional per-column stop rule (stop_rule = 1): see cg_solve.
+* Optional block CG (solver = 1, a solver variant; the paper's solver is
+  the column-wise one): see block_cg_solve.
 
 Parity status: every function here is pinned by a CPU test against a closed
 form, a library routine on an independent formulation, brute force, or an
@@ -282,6 +284,65 @@ def pcg_solve(A, B, X0, minv, tol, max_iters, resid_replace_every=0):
     return CGResult(X, it, relres, relres < tol)
 
 
+class BlockCGBreakdown(ValueError):
+    """The residual block of block CG lost rank (a zero diagonal entry of
+    its triangular factor): the step cannot continue."""
+
+
+def block_cg_solve(A, B, tol, max_iters, fixed_iters=0):
+    """Block CG on A X = B: the m columns share one block Krylov space
+    span{B, A B, .., A^(k-1) B} (O'Leary, Lin. Alg. Appl. 29, 1980), the
+    solver slot of Sec. 3.2 filled by a block method instead of m
+    independent recurrences.  This is the residual-orthonormalised form of
+    Dubrulle (ETNA 12, 2001): the residual block is kept as R = Q C with
+    Q^T Q = I, so that ||R||_F = ||C||_F.  With X0 = 0:
+
+        Q C = B (QR),  P = Q
+        repeat:  Z = A P;  xi = (P^T Z)^-1
+                 X = X + P xi C
+                 V = Q - Z xi             (R_new = V C)
+                 stop when ||V C||_F / ||B||_F < tol (same joint test as cg_solve)
+                 Q psi = V (QR);  P = Q + P psi^T;  C = psi C
+
+    fixed_iters > 0 runs exactly that many iterations and ignores tol.  The
+    QR factorisations are the library's (Householder).  A residual block
+    that loses rank (a zero diagonal entry of C at the start or of psi in an
+    iteration that has not met the test) raises BlockCGBreakdown.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    X = np.zeros_like(B)
+    normB = np.sqrt(np.sum(B * B))
+    limit = fixed_iters if fixed_iters > 0 else max_iters
+    if normB == 0.0:
+        return CGResult(X, 0, 0.0, True)
+    Q, C = np.linalg.qr(B)
+    if np.any(np.diag(C) == 0.0):
+        raise BlockCGBreakdown("the right-hand sides are linearly dependent")
+    relres = np.sqrt(np.sum(C * C)) / normB
+    if fixed_iters == 0 and relres < tol:
+        return CGResult(X, 0, relres, True)
+    P = Q.copy()
+    it = 0
+    while it < limit:
+        it += 1
+        Z = A(P)
+        xi = np.linalg.inv(P.T @ Z)
+        X = X + P @ (xi @ C)
+        V = Q - Z @ xi
+        R = V @ C
+        relres = np.sqrt(np.sum(R * R)) / normB
+        if fixed_iters == 0 and relres < tol:
+            return CGResult(X, it, relres, True)
+        if it == limit:
+            break
+        Q, psi = np.linalg.qr(V)
+        if np.any(np.diag(psi) == 0.0):
+            raise BlockCGBreakdown("the residual block lost rank")
+        P = Q + P @ psi.T
+        C = psi @ C
+    return CGResult(X, it, relres, fixed_iters > 0 or relres < tol)
+
+
 # --------------------------------------------------------------------------
 # Diagonal estimation (Sec. 3.1) and M-step (Eq. mstep with s).
 # --------------------------------------------------------------------------
@@ -319,14 +380,16 @@ class FitStats:
 def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
           seed=0, alpha_init=1.0, t_offset=0, fixed_cg_iters=0,
           resid_replace_every=0, den_floor=DEN_FLOOR, probes=None,
-          support_threshold=1e6, stop_rule=0):
+          support_threshold=1e6, stop_rule=0, solver=0):
     """Algorithm 1.  Returns (alpha, mu, s, FitStats).
 
     alpha_init: scalar (Alg. 1 initialises alpha = 1) or a length-D vector
     (resume from a previous alpha).  t runs t_offset+1 .. t_offset+em_iters.
     probes: optional function t -> D x K probe block; default is the
     counter-based Rademacher generator of probe_hash.  stop_rule: see
-    cg_solve.
+    cg_solve.  solver = 1 solves each E-step by block CG (block_cg_solve;
+    the joint stop test, no residual replacement, stop_rule 0) instead of
+    the column-wise recurrences.
 
     Multi-task (the extension named in Sec. 5, T tasks sharing alpha): y of
     shape T x N; B = [beta Phi^T y_1 .. beta Phi^T y_T | p_1 .. p_K], mu is
@@ -346,8 +409,13 @@ def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters,
         A = lambda X, al=alpha: apply_A(phi, phit, beta, al, X)
         P = probes(t) if probes is not None else probe_matrix(seed, t, K, D)
         B = np.concatenate([b, P], axis=1)
-        res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters,
-                       resid_replace_every, stop_rule)
+        if solver == 1:
+            if resid_replace_every or stop_rule:
+                raise ValueError("block CG: no residual replacement, joint stop test only")
+            res = block_cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters)
+        else:
+            res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters,
+                           resid_replace_every, stop_rule)
         mu = res.X[:, :T].T if multi else res.X[:, 0]
         s = diag_estimate(P, res.X[:, T:])
         # M-step.

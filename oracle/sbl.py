@@ -284,11 +284,6 @@ def pcg_solve(A, B, X0, minv, tol, max_iters, resid_replace_every=0):
     return CGResult(X, it, relres, relres < tol)
 
 
-class BlockCGBreakdown(ValueError):
-    """The residual block of block CG lost rank (a zero diagonal entry of
-    its triangular factor): the step cannot continue."""
-
-
 def block_cg_solve(A, B, tol, max_iters, fixed_iters=0):
     """Block CG on A X = B: the m columns share one block Krylov space
     span{B, A B, .., A^(k-1) B} (O'Leary, Lin. Alg. Appl. 29, 1980), the
@@ -305,9 +300,10 @@ def block_cg_solve(A, B, tol, max_iters, fixed_iters=0):
                  Q psi = V (QR);  P = Q + P psi^T;  C = psi C
 
     fixed_iters > 0 runs exactly that many iterations and ignores tol.  The
-    QR factorisations are the library's (Householder).  A residual block
-    that loses rank (a zero diagonal entry of C at the start or of psi in an
-    iteration that has not met the test) raises BlockCGBreakdown.
+    QR factorisations are the library's (Householder); they need no special
+    case for a residual block that loses rank (a zero right-hand side, or a
+    column combination that has converged): C or psi then has a zero row
+    and that combination takes no further part in X.
     """
     B = np.asarray(B, dtype=np.float64)
     X = np.zeros_like(B)
@@ -316,8 +312,6 @@ def block_cg_solve(A, B, tol, max_iters, fixed_iters=0):
     if normB == 0.0:
         return CGResult(X, 0, 0.0, True)
     Q, C = np.linalg.qr(B)
-    if np.any(np.diag(C) == 0.0):
-        raise BlockCGBreakdown("the right-hand sides are linearly dependent")
     relres = np.sqrt(np.sum(C * C)) / normB
     if fixed_iters == 0 and relres < tol:
         return CGResult(X, 0, relres, True)
@@ -336,8 +330,6 @@ def block_cg_solve(A, B, tol, max_iters, fixed_iters=0):
         if it == limit:
             break
         Q, psi = np.linalg.qr(V)
-        if np.any(np.diag(psi) == 0.0):
-            raise BlockCGBreakdown("the residual block lost rank")
         P = Q + P @ psi.T
         C = psi @ C
     return CGResult(X, it, relres, fixed_iters > 0 or relres < tol)

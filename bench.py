@@ -1005,34 +1005,73 @@ def cg_kernels_section(B, dev, peak, ncols):
     return out
 
 
+def op_roofline(B, op, ncols, beta, dev, peak, phi_bytes, label):
+    """Per-kernel CUDA-event times of one operator application A X (X:
+    ncols columns) and the two products against the HBM roof.  Algorithmic
+    bytes per launch: the dictionary (phi_bytes), the split B operand (BF16,
+    BN = 16 ceil(ncols / 5) columns), the FP32 input / output blocks and, for
+    the second product, alpha."""
+    import torch
+    N, D = op.N, op.D
+    ld = (D + 63) // 64 * 64
+    Xb = torch.randn((ncols, ld), device=dev)
+    Xb[:, D:] = 0
+    Yb = torch.empty_like(Xb)
+    al = torch.ones(D, dtype=torch.float64, device=dev)
+    nbytes = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, ncols)
+    wsa = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    per = [B.cofem_op_apply_timed(op.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols,
+                                  al.data_ptr(), beta, Yb.data_ptr(), wsa.data_ptr(),
+                                  nbytes, st) for _ in range(12)][2:]
+    kms = [float(np.mean([p_[i] for p_ in per])) for i in range(len(per[0]))]
+    BN = -(-ncols // 5) * 16
+    g2 = phi_bytes + BN * N * 2 + 2 * ncols * D * 4 + 8 * D
+    g1 = phi_bytes + BN * D * 2 + ncols * N * 4
+    return {"bound": "hbm", "peak": peak, "unit": "GB/s",
+            "kernels_us": dict(zip(["split", "gemm1", "reduce+split", "gemm2"],
+                                   [round(v * 1e3, 2) for v in kms])),
+            "gemm1": {"algorithmic_bytes": g1, "achieved": g1 / (kms[1] / 1e3) / 1e9,
+                      "frac": g1 / (kms[1] / 1e3) / 1e9 / peak},
+            "gemm2": {"algorithmic_bytes": g2, "achieved": g2 / (kms[3] / 1e3) / 1e9,
+                      "frac": g2 / (kms[3] / 1e3) / 1e9 / peak},
+            "kernel": label}
+
+
 def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
-    """The whole 100-EM-iteration fit of the headline workload, twice: the
-    BF16 dictionary (the bench's operator) and the plain FP32 comparator (the
-    FP32 dictionary on the tensor cores, Phi = hi + lo).  For each: EM
-    iterations per second of the whole fit, and time to tolerance -- the
-    device time until the support equals the FP64 oracle's final support
-    (its own dictionary's) and alpha on it stays within 1e-2 / 1e-3 of the
-    oracle's final alpha.  Plus the FP32 operator's second product against
-    the HBM roof."""
+    """The whole 100-EM-iteration fit of the headline workload, three times:
+    the BF16 dictionary (the bench's operator), the plain FP32 comparator
+    (the FP32 dictionary on the tensor cores, Phi = hi + lo) and the FP8 E4M3
+    dictionary with per-tile scales.  For each: EM iterations per second of
+    the whole fit, the time to 2 % NRMSE (Sec. 4.2's criterion) and time to
+    tolerance -- the device time until the support equals the FP64 oracle's
+    final support and alpha on it stays within 1e-2 / 1e-3 of the oracle's
+    final alpha (the oracle run on the same dictionary, and on the FP32 one).
+    Plus the FP32 and FP8 operators' products against the HBM roof."""
     import torch
     em = CFG["em_iters"]
     N, D, ncols = CFG["N"], CFG["D"], CFG["K"] + 1
     out = {"em_iters": em, "timing": "one cofem_fit call per variant, CUDA events on the "
                                       "stream; per-EM-iteration device clock from the fit's "
                                       "statistics (end_ns)"}
-    # plain FP32 GPU CoFEM: FP32 dictionary, packed as hi + lo, autotuned
+    # plain FP32 GPU CoFEM: FP32 dictionary, packed as hi + lo, autotuned;
+    # and the FP8 E4M3 dictionary (per-tile scales) quantised from it
+    st = torch.cuda.current_stream().cuda_stream
     phi32 = torch.from_numpy(prob.Phi).to(dev)
     op32 = api.DenseOperator(phi32)
     nb = B.cofem_op_dense_packed_bytes(op32.handle)
     pk32 = torch.empty(nb, dtype=torch.uint8, device=dev)
-    B.cofem_op_dense_attach_packed(op32.handle, pk32.data_ptr(), nb,
-                                   torch.cuda.current_stream().cuda_stream)
-    nbt = B.cofem_op_dense_autotune_workspace_bytes(op32.handle, ncols)
-    wst = torch.empty(nbt, dtype=torch.uint8, device=dev)
-    st32, cps32, us32 = B.cofem_op_dense_autotune(op32.handle, ncols, wst.data_ptr(), nbt,
-                                                  torch.cuda.current_stream().cuda_stream)
-    del wst
-    for name, op, ref_phi in (("bf16", op16, "bf16"), ("fp32", op32, "f32")):
+    B.cofem_op_dense_attach_packed(op32.handle, pk32.data_ptr(), nb, st)
+    op8 = api.Fp8DenseOperator(phi32)
+    tuned = {}
+    for name, op in (("fp32", op32), ("fp8", op8)):
+        nbt = B.cofem_op_dense_autotune_workspace_bytes(op.handle, ncols)
+        wst = torch.empty(nbt, dtype=torch.uint8, device=dev)
+        stg, cps, us = B.cofem_op_dense_autotune(op.handle, ncols, wst.data_ptr(), nbt, st)
+        tuned[name] = {"stages": stg, "ctas_per_sm": cps, "us_per_apply": us,
+                       "tile_rows": B.cofem_op_dense_get_pipeline(op.handle)[2]}
+        del wst
+    for name, op, ref_phi in (("bf16", op16, "bf16"), ("fp32", op32, "f32"), ("fp8", op8, None)):
         sec, stats, hist, nrmse = whole_fit(api, B, op, y, prob.beta, kw, em, dev, z=prob.z)
         ent = {"em_iters_per_s": em / sec, "seconds": sec,
                "cg_iters_total": int(sum(stats["cg_iters"])),
@@ -1040,45 +1079,35 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
                "support_counts": stats["support"][::10],
                "nrmse_mu_vs_truth": {"final": nrmse[-1], "every_10": nrmse[9::10]},
                "time_to_2pct_nrmse": time_to_nrmse(nrmse, stats["end_ns"])}
-        ref = load_reference_fit(ref_phi)
+        ref = load_reference_fit(ref_phi) if ref_phi else None
         if ref is not None:
             ent["vs_oracle_" + ref_phi] = time_to_tolerance(hist, stats["end_ns"], ref)
             ent["oracle_cg_iters_total"] = int(sum(ref["cg_iters"]))
             ent["oracle_nrmse_final"] = ref.get("nrmse_mu_vs_truth")
-        if name == "bf16":
+        if name != "fp32":
+            # the BF16 and FP8 fits against the FP32 dictionary's oracle fit:
+            # how close a lower-precision dictionary gets to the FP32 answer
             ref32 = load_reference_fit("f32")
             if ref32 is not None:
                 ent["vs_oracle_f32"] = time_to_tolerance(hist, stats["end_ns"], ref32)
         out[name] = ent
-    out["fp32"]["pipeline"] = {"stages": st32, "ctas_per_sm": cps32, "us_per_apply": us32}
+    for name in ("fp32", "fp8"):
+        out[name]["pipeline"] = tuned[name]
     out["ratio_em_iters_per_s"] = out["bf16"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
+    out["ratio_em_iters_per_s_fp8"] = out["fp8"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
     t16, t32 = out["bf16"]["time_to_2pct_nrmse"], out["fp32"]["time_to_2pct_nrmse"]
     out["ratio_time_to_2pct_nrmse"] = (t32["seconds"] / t16["seconds"]) if t16 and t32 else None
-    # the FP32 operator's kernels, timed with CUDA events on the stream
-    ld = (D + 63) // 64 * 64
-    Xb = torch.randn((ncols, ld), device=dev)
-    Xb[:, D:] = 0
-    Yb = torch.empty_like(Xb)
-    al = torch.ones(D, dtype=torch.float64, device=dev)
-    nbytes = B.cofem_apply_workspace_bytes(op32.handle, B.COFEM_F32, ncols)
-    wsa = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-    st = torch.cuda.current_stream().cuda_stream
-    per = [B.cofem_op_apply_timed(op32.handle, B.COFEM_F32, Xb.data_ptr(), ld, ncols,
-                                  al.data_ptr(), prob.beta, Yb.data_ptr(), wsa.data_ptr(),
-                                  nbytes, st) for _ in range(12)][2:]
-    kms = [float(np.mean([p_[i] for p_ in per])) for i in range(len(per[0]))]
-    BN = -(-ncols // 5) * 16
-    g2 = 4 * N * D + BN * N * 2 + 2 * ncols * D * 4 + 8 * D
-    g1 = 4 * N * D + BN * D * 2 + ncols * N * 4
-    out["fp32"]["roofline"] = {
-        "bound": "hbm", "peak": peak, "unit": "GB/s",
-        "kernels_us": dict(zip(["split", "gemm1", "reduce+split", "gemm2"],
-                               [round(v * 1e3, 2) for v in kms])),
-        "gemm1": {"algorithmic_bytes": g1, "achieved": g1 / (kms[1] / 1e3) / 1e9,
-                  "frac": g1 / (kms[1] / 1e3) / 1e9 / peak},
-        "gemm2": {"algorithmic_bytes": g2, "achieved": g2 / (kms[3] / 1e3) / 1e9,
-                  "frac": g2 / (kms[3] / 1e3) / 1e9 / peak},
-        "kernel": "dense_tc_kernel<1,3> with Phi = hi + lo (two BF16 terms, 4 B per entry)"}
+    t8 = out["fp8"]["time_to_2pct_nrmse"]
+    out["ratio_time_to_2pct_nrmse_fp8"] = (t32["seconds"] / t8["seconds"]) if t8 and t32 else None
+    # the FP32 and FP8 operators' kernels, timed with CUDA events on the stream
+    # (entry bytes: 4 for hi + lo, 1 plus one FP32 scale per 128 x 128 tile)
+    sc_bytes = 4 * ((N + 127) // 128) * ((D + 127) // 128)
+    out["fp32"]["roofline"] = op_roofline(B, op32, ncols, prob.beta, dev, peak, 4 * N * D,
+                                          "dense_tc_kernel<1,3> with Phi = hi + lo "
+                                          "(two BF16 terms, 4 B per entry)")
+    out["fp8"]["roofline"] = op_roofline(B, op8, ncols, prob.beta, dev, peak, N * D + sc_bytes,
+                                         "dense_tc_kernel<1,3> with Phi in FP8 E4M3 (1 B per "
+                                         "entry + per-tile scales), expanded to BF16 in smem")
     return out
 
 

@@ -262,11 +262,25 @@ typedef struct {
                                   stop test); if it has not converged after
                                   cg_max_iters, plain CG from zero is run
                                   instead.  F32 vectors only. */
+  int32_t solver;              /* E-step solver: 0 = the paper's column-wise
+                                  CG (Sec. 3.2); 1 = block CG, a solver
+                                  variant: the K + T columns share one block
+                                  Krylov space (O'Leary 1980) in the
+                                  residual-orthonormalised form R = Q C of
+                                  Dubrulle (2001), same joint stop test
+                                  ||R||_F / ||B||_F = ||C||_F / ||B||_F <
+                                  cg_tol.  A direction of the residual block
+                                  that becomes dependent (a zero y, a
+                                  converged column combination) is dropped
+                                  from the solve.  With resid_replace_every
+                                  > 0, stop_rule 1, mlp or cofem_fit_batched:
+                                  COFEM_ERR_UNSUPPORTED.  Other values:
+                                  COFEM_ERR_INVALID_ARG. */
 } cofem_params;
 
 /* Fills *p with: K 20, em_iters 50, cg_max_iters 400, fixed 0, R 0, F32,
  * cg_tol 1e-6, alpha_init 1, den_floor 1e-12, support_threshold 1e6,
- * seed 0, t_offset 0. */
+ * seed 0, t_offset 0, mlp NULL, solver 0. */
 void cofem_params_default(cofem_params* p);
 
 /* Per-EM-iteration statistics, host arrays of length em_iters (any may be

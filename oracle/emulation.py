@@ -22,8 +22,11 @@ optional hooks that change nothing but rounding:
                multiplied by (1 + u 2^-52), u = +-1 from a seeded generator:
                a re-ordering of the FP64 sums moves them by about as much.
 
+``block_cg_solve`` carries ``vround`` over to the block CG of the solver
+variant (``sbl.block_cg_solve``).
+
 With both hooks None the functions perform exactly the arithmetic of
-``sbl.cg_solve`` and ``sbl.cofem`` (pinned bit for bit in
+``sbl.cg_solve``, ``sbl.block_cg_solve`` and ``sbl.cofem`` (pinned bit for bit in
 tests/test_tolerance_evidence.py), so every difference they show comes
 from rounding alone.  Only the joint stop rule and the per-column rule of
 ``sbl.cg_solve`` are carried over; residual replacement is not.
@@ -119,13 +122,52 @@ def cg_solve(A, B, tol, max_iters, fixed_iters=0, stop_rule=0, vround=None, dper
     return sbl.CGResult(X, it, relres, converged)
 
 
+def block_cg_solve(A, B, tol, max_iters, fixed_iters=0, vround=None):
+    """sbl.block_cg_solve (X0 = 0, joint stop test) with every stored block
+    (B, X, Q, P, the operator product Z = A P, V) and every small matrix
+    (C, xi, M = xi C, psi) passed through vround; the QR factorisations and
+    products themselves are FP64 library steps, as in the oracle."""
+    vr = vround or _id
+    B = vr(np.asarray(B, dtype=np.float64))
+    X = np.zeros_like(B)
+    normB = np.sqrt(np.sum(B * B))
+    limit = fixed_iters if fixed_iters > 0 else max_iters
+    if normB == 0.0:
+        return sbl.CGResult(X, 0, 0.0, True)
+    Q, C = np.linalg.qr(B)
+    Q, C = vr(Q), vr(C)
+    relres = np.sqrt(np.sum(C * C)) / normB
+    if fixed_iters == 0 and relres < tol:
+        return sbl.CGResult(X, 0, relres, True)
+    P = Q.copy()
+    it = 0
+    while it < limit:
+        it += 1
+        Z = vr(A(P))
+        xi = vr(np.linalg.inv(P.T @ Z))
+        X = vr(X + P @ vr(xi @ C))
+        V = vr(Q - Z @ xi)
+        R = V @ C
+        relres = np.sqrt(np.sum(R * R)) / normB
+        if fixed_iters == 0 and relres < tol:
+            return sbl.CGResult(X, it, relres, True)
+        if it == limit:
+            break
+        Q, psi = np.linalg.qr(V)
+        Q, psi = vr(Q), vr(psi)
+        P = vr(Q + P @ psi.T)
+        C = vr(psi @ C)
+    return sbl.CGResult(X, it, relres, fixed_iters > 0 or relres < tol)
+
+
 def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, seed=0,
           alpha_init=1.0, fixed_cg_iters=0, stop_rule=0, vround=None, dperturb=None,
-          support_threshold=1e6):
+          support_threshold=1e6, solver=0):
     """sbl.cofem (single task, t from 1) with the rounding hooks: B, X, R, P
     and the operator product pass through vround, the operator reads
     vround(alpha), every per-column reduction passes through dperturb.  mu, s
-    and alpha stay float64 (as on the GPU).  Returns (alpha, mu, s, FitStats)."""
+    and alpha stay float64 (as on the GPU).  solver = 1: block CG
+    (block_cg_solve, vround only).  Returns (alpha, mu, s, FitStats)."""
     vr = vround or _id
     y = np.asarray(y, dtype=np.float64)
     alpha = np.broadcast_to(np.asarray(alpha_init, dtype=np.float64), (D,)).copy()
@@ -140,7 +182,11 @@ def cofem(phi, phit, D, y, beta, K, em_iters, cg_tol, cg_max_iters, seed=0,
         A = lambda X, al=al: beta * phit(vr(phi(X))) + al[:, None] * X
         P = probe_matrix(seed, t, K, D)
         B = np.concatenate([b, P], axis=1)
-        res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters, stop_rule, vround, dperturb)
+        if solver == 1:
+            res = block_cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters, vround)
+        else:
+            res = cg_solve(A, B, cg_tol, cg_max_iters, fixed_cg_iters, stop_rule, vround,
+                           dperturb)
         mu = res.X[:, 0]
         s = sbl.diag_estimate(P, res.X[:, 1:])
         alpha, clamps = sbl.m_step(mu, s)

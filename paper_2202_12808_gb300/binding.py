@@ -38,7 +38,7 @@ class cofem_params(ctypes.Structure):
                 ("cg_tol", ctypes.c_double), ("alpha_init", ctypes.c_double),
                 ("den_floor", ctypes.c_double), ("support_threshold", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("t_offset", ctypes.c_int64),
-                ("mlp", ctypes.c_void_p)]
+                ("mlp", ctypes.c_void_p), ("solver", ctypes.c_int32)]
 
 
 class cofem_stats(ctypes.Structure):

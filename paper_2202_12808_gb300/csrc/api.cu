@@ -290,7 +290,7 @@ static int64_t op_D(const cofem_op* op) {
 
 struct FitLayout {
   size_t ctl, sc, pdots, pvec, pvec2, pvec3, minv, pn2, alpha32, X, R, P, Q, b, yblk, st_iters,
-      st_relres, st_clamps, st_support, st_end, opws;
+      st_relres, st_clamps, st_support, st_end, bcg, opws;
   size_t total;
   int64_t ld;
 };
@@ -328,6 +328,8 @@ static FitLayout fit_layout(const cofem_op* op, const cofem_params* p) {
   L.st_clamps = o; o += align256(sizeof(int32_t) * ne);
   L.st_support = o; o += align256(sizeof(int32_t) * ne);
   L.st_end = o; o += align256(sizeof(int64_t) * ne);
+  // block CG: its m x m matrices, counters and Gram partial sums
+  L.bcg = o; o += p->solver == 1 ? align256(bcg_state_bytes(vb, ncols, L.ld)) : 0;
   L.opws = o;
   size_t ows = op_ws_bytes(op, p->vec_dtype, ncols);
   size_t ows1 = op_ws_bytes(op, p->vec_dtype, 1);
@@ -345,7 +347,11 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
   if (!(p->cg_tol >= 0.0) || !(p->den_floor > 0.0)) return COFEM_ERR_INVALID_ARG;
   if (p->t_offset < 0) return COFEM_ERR_INVALID_ARG;
   if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
+  if (p->solver != 0 && p->solver != 1) return COFEM_ERR_INVALID_ARG;
   if (!op_supports(op, p->vec_dtype)) return COFEM_ERR_UNSUPPORTED;
+  // block CG: the joint stop test on its own recurrence, nothing else
+  if (p->solver == 1 && (p->resid_replace_every > 0 || p->stop_rule != 0 || p->mlp))
+    return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && op->kind == 2) return COFEM_ERR_UNSUPPORTED;
@@ -469,6 +475,8 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                                cs, &ctl->error, prep, alpha32);
     if (rw != COFEM_OK) return rw;
     launch_cg_init_warm<V>(cf, ctl, sc, X, R, P, Q, b, pvec, pvec2, pvec3, cs);
+  } else if (p->solver == 1) {
+    CK(launch_bcg_start<V>(cf, ctl, ws + L.bcg, X, R, P, b, cs));
   } else {
     launch_cg_init<V>(cf, ctl, sc, X, R, P, b, pvec, cs);
   }
@@ -476,6 +484,31 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
   cudaGraph_t body = nullptr;
   cofem_status rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &body);
   if (rc != COFEM_OK) return rc;
+
+  if (p->solver == 1) {
+    // ---- block CG: Z = A P (into Q), then its gram passes and row pass
+    cudaStream_t bs = ss.s[1];
+    CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    rc = op_apply(op, vec, P, L.ld, ncols, alpha, beta, Q, nullptr, nullptr, opws, bs,
+                  &ctl->error, (cf.split_nt > 0 ? kApplyPresplit : 0u) | prep, alpha32);
+    if (rc != COFEM_OK) return rc;
+    CK(launch_bcg_iteration<V>(cf, ctl, ws + L.bcg, X, R, P, Q, bs));
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(bs, &tmp));
+    launch_diag_mstep<V>(cf, ctl, 0, X, mu, s, alpha, nullptr, (int32_t*)(ws + L.st_iters),
+                         (double*)(ws + L.st_relres), (int32_t*)(ws + L.st_clamps),
+                         (int32_t*)(ws + L.st_support), cs);
+    CKL();
+    cudaGraph_t graph;
+    CK(cudaStreamEndCapture(cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      set_error("cudaGraphInstantiate", e, __FILE__, __LINE__);
+      return COFEM_ERR_CUDA;
+    }
+    return COFEM_OK;
+  }
 
   // ---- WHILE body.  Tensor-core operator with residual replacement: the
   // body is an inner WHILE loop of plain CG iterations, left when the

@@ -799,6 +799,7 @@ static cofem_status bcheck(int n, const cofem_problem* pr, const cofem_params* p
   if (p->stop_rule != 0 && p->stop_rule != 1) return COFEM_ERR_INVALID_ARG;
   if (p->tasks > 1) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
+  if (p->solver != 0) return p->solver == 1 ? COFEM_ERR_UNSUPPORTED : COFEM_ERR_INVALID_ARG;
   return COFEM_OK;
 }
 

@@ -1,0 +1,831 @@
+// Block conjugate gradients on A X = B (a solver variant for the solver slot
+// of Sec. 3.2): the m = K + T columns share one block Krylov space
+// span{B, A B, .., A^(k-1) B} (O'Leary 1980), in the residual-orthonormalised
+// form of Dubrulle (2001) that keeps the residual block as R = Q C with
+// Q^T Q = I, so ||R||_F = ||C||_F.  The recurrence (X0 = 0):
+//
+//   Q C = B,  P = Q
+//   repeat:  Z = A P;  xi = (P^T Z)^-1;  X += P xi C;  V = Q - Z xi
+//            stop when ||V C||_F / ||B||_F < tol
+//            Q psi = V;  P = Q + P psi^T;  C = psi C
+//
+// GPU form: after the operator application Z = A P, one iteration is three
+// kernels.  Each "gram" kernel makes one pass over rows of the blocks,
+// staged 32 rows at a time in shared memory (column-major, as in HBM),
+// accumulates one m x m Gram matrix in 4 x 4 register tiles (FP32
+// products, each thread's sums added into a compensated pair per staged
+// chunk; FP64 for FP64 vectors), sums it over blocks in a fixed tree (groups
+// of 16 blocks, then the groups), and its last block does the small dense
+// algebra:
+//
+//   xi    Gram P^T Z;  xi = (P^T Z)^-1 (Gauss-Jordan sweeps), M = xi C
+//   v     X += P M and V = Q - Z xi on the staged rows (4 x 4 tiles; V
+//         replaces Q in HBM), Gram V^T V;  ||V C||_F^2 = tr(C^T V^T V C)
+//         gives the joint stop test; V^T V = L L^T (Cholesky), psi = L^T,
+//         C = psi C
+//   row   per row d: q = v L^-T (forward substitution), p = q + p psi^T,
+//         and P's BF16 terms for the tensor-core operator
+//
+// so the QR of V is a Cholesky QR on V's own Gram matrix.  The start of an
+// E-step: fill (X = 0, Q = B), the gram pass on B (B^T B = L L^T, C = L^T,
+// ||B||_F^2 = tr(B^T B)), row (Q = B L^-T, P = Q).
+//
+// Deflation.  Both factorisations are rank-revealing without pivoting: a
+// pivot at or below 64 units of roundoff of its original diagonal entry
+// (a zero right-hand side, a column combination of the residual block that
+// has converged or become dependent) drops that index -- its row and column
+// of xi, its column of L (so its row of psi and of C) are zero and the
+// direction takes no further part.  A step whose P^T Z has no index left
+// raises COFEM_ERR_BREAKDOWN.
+#include "kernels.cuh"
+
+namespace cofem {
+
+namespace {
+
+constexpr int kGramThreads = 512;   // threads of a gram block
+constexpr int kGramRows = 32;       // rows staged per pass of a gram block
+constexpr int kGroup = 16;          // gram blocks per first-level group
+constexpr int kRowThreads = 128;    // threads of a row block (one row each)
+constexpr int kFinalCounter = 63;   // counter slot of the last-level arrival
+
+enum { kModeStart = 0, kModeXi = 1, kModeV = 2 };
+
+// Column capacity (a multiple of 4) of the templates serving m columns.
+int capacity(int m) {
+  if (m <= 8) return 8;
+  if (m <= 16) return 16;
+  if (m <= 24) return 24;
+  if (m <= 36) return 36;
+  if (m <= 48) return 48;
+  return 64;
+}
+
+// ---------------------------------------------------------------- state
+// Device state of one block-CG solve (in the fit workspace): CAP x CAP
+// matrices of the vector type V, row-major, zero outside the leading m x m:
+//   C  residual coefficients (upper triangular), M = xi C, Xi = xi,
+//   L  Cholesky factor of the last Q-step (lower), Lt = L^T, rdiag = 1 / L_jj
+//   (0 for a dropped index).
+struct BcgHdr {
+  unsigned int cnt[64];   // arrival counters (groups, then kFinalCounter)
+};
+
+template <typename V, int CAP>
+struct BcgView {
+  BcgHdr* hdr;
+  V *C, *M, *Xi, *L, *Lt, *rdiag;
+  void *part, *gpart;     // block and group partial sums
+  __host__ __device__ static size_t mat_bytes() { return (size_t)CAP * CAP * sizeof(V); }
+};
+
+template <typename V> struct GAcc;
+// FP32: compensated pair (Knuth's TwoSum); stored as float2
+template <> struct GAcc<float> {
+  using Packed = float2;
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x, xv = t - s;
+    c += (s - (t - xv)) + (x - xv);
+    s = t;
+  }
+  __device__ __forceinline__ void merge(Packed o) {
+    add(o.x);
+    c += o.y;
+  }
+  __device__ __forceinline__ Packed pack() const { return make_float2(s, c); }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+template <> struct GAcc<double> {
+  using Packed = double;
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void merge(Packed o) { s += o; }
+  __device__ __forceinline__ Packed pack() const { return s; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// 4 x 4 tiles (a <= b) of one symmetric CAP x CAP Gram matrix; PH threads
+// (adjacent lanes) share a tile, each taking every PH-th row quad.
+template <int CAP>
+struct Tiles {
+  static constexpr int NT = CAP / 4;
+  static constexpr int NSYM = NT * (NT + 1) / 2;
+  static constexpr int ph_for(int ntasks) {
+    int p = 1;
+    while (p < kGramRows / 4 && 2 * p * ntasks <= kGramThreads) p *= 2;
+    return p;
+  }
+  static constexpr int PH = ph_for(NSYM);
+  static constexpr int SLOTS = kGramThreads / PH;
+  static constexpr int TPT = (NSYM + SLOTS - 1) / SLOTS;
+  // 4 x 4 output tiles of a staged 32-row chunk times an m x m matrix
+  static constexpr int NUT = (kGramRows / 4) * NT;
+};
+
+// Up to 36 columns the row pass keeps v in registers and unrolls the
+// forward substitution; wider blocks run it on a per-thread column of
+// shared memory with runtime loops (bounded code size and registers).
+template <int CAP>
+struct RowInRegisters {
+  static constexpr bool value = CAP <= 36;
+};
+
+__device__ __forceinline__ void sym_tile(int tau, int nt, int& a, int& b) {
+  int r = 0;
+  while (tau >= nt - r) { tau -= nt - r; ++r; }
+  a = r;
+  b = r + tau;
+}
+
+// Every thread fences its own stores, then one arrival per block; true in
+// every thread of the n-th block to arrive, which resets the counter.
+__device__ __forceinline__ bool arrive_count(unsigned int* cnt, unsigned int n) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(cnt, 1u) == n - 1;
+    if (last) {
+      __threadfence();
+      *cnt = 0;
+    }
+  }
+  __syncthreads();
+  return last;
+}
+
+template <typename V>
+__device__ __forceinline__ void ld4(const V* p, V (&v)[4]) {
+  if constexpr (sizeof(V) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const double2 t0 = *reinterpret_cast<const double2*>(p);
+    const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+  }
+}
+template <typename V>
+__device__ __forceinline__ void st4(V* p, const V (&v)[4]) {
+  if constexpr (sizeof(V) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+__device__ __forceinline__ void set_cond_h(unsigned long long h, unsigned v) {
+  if (h) cudaGraphSetConditional((cudaGraphConditionalHandle)h, v);
+}
+
+template <typename V> struct Roundoff { static constexpr float value = 5.9604645e-8f; };
+template <> struct Roundoff<double> { static constexpr double value = 1.1102230246251565e-16; };
+template <typename V> __device__ __forceinline__ V drop_tol() { return V(64) * V(Roundoff<V>::value); }
+
+// ----------------------------------------------------- small dense algebra
+// n x n matrices in shared memory with row stride LD; the whole block.
+
+// Gauss-Jordan sweeps of a symmetric positive semi-definite matrix
+// (Goodnight 1979) over the indices whose pivot stays above drop_tol times
+// their original diagonal entry: A becomes xi = (A_SS)^-1 on the kept set S
+// and 0 elsewhere.  Returns the number of kept indices.
+template <typename S, int LD>
+__device__ int sweep_inverse(S* A, int n, S* rk, S* d0, int* dead) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d0[i] = A[i * LD + i];
+    dead[i] = 0;
+  }
+  int kept = 0;
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const S piv = A[k * LD + k];
+    if (!(piv > drop_tol<S>() * d0[k]) || !isfinite(piv)) {
+      if (threadIdx.x == 0) dead[k] = 1;
+      continue;
+    }
+    ++kept;
+    if ((int)threadIdx.x < n) rk[threadIdx.x] = A[k * LD + threadIdx.x];
+    __syncthreads();
+    const S inv = S(1) / piv;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      S v;
+      if (i == k && j == k) v = -inv;
+      else if (i == k) v = rk[j] * inv;
+      else if (j == k) v = rk[i] * inv;
+      else v = A[i * LD + j] - rk[i] * rk[j] * inv;
+      A[i * LD + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    A[i * LD + j] = (dead[i] || dead[j]) ? S(0) : -A[i * LD + j];
+  }
+  __syncthreads();
+  return kept;
+}
+
+// Cholesky factorisation A = L L^T in place (lower triangle; right-looking
+// with unscaled columns, scaled at the end), dropping an index whose pivot
+// is at or below drop_tol times its original diagonal entry (its column of
+// L is zero).
+template <typename S, int LD>
+__device__ void cholesky(S* A, int n, S* d0, int* dead) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    d0[i] = A[i * LD + i];
+    dead[i] = 0;
+  }
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    const S piv = A[k * LD + k];
+    if (!(piv > drop_tol<S>() * d0[k]) || !isfinite(piv)) {
+      if (threadIdx.x == 0) dead[k] = 1;
+      continue;
+    }
+    const S inv = S(1) / piv;
+    const int m = n - k - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
+      if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k] * inv;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    if (j < i) A[i * LD + j] = dead[j] ? S(0) : A[i * LD + j] / sqrt(A[j * LD + j]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    A[i * LD + i] = dead[i] ? S(0) : sqrt(A[i * LD + i]);
+  __syncthreads();
+}
+
+// Writes a Q-step's factor (L at stride LD) to the state: L, Lt, rdiag.
+template <typename V, int CAP, int LD>
+__device__ void store_factor(const BcgView<V, CAP>& w, const V* Ls, int n) {
+  for (int idx = threadIdx.x; idx < CAP * CAP; idx += blockDim.x) {
+    const int i = idx / CAP, j = idx % CAP;
+    const V l = (i < n && j < n && j <= i) ? Ls[i * LD + j] : V(0);
+    w.L[i * CAP + j] = l;
+    w.Lt[j * CAP + i] = l;
+  }
+  for (int j = threadIdx.x; j < CAP; j += blockDim.x) {
+    const V d = j < n ? Ls[j * LD + j] : V(0);
+    w.rdiag[j] = d > V(0) ? V(1) / d : V(0);
+  }
+}
+
+// --------------------------------------------------------------- kernels
+
+// X = 0, Q = B = [b_1 .. b_T | p_1 .. p_K] (probes hashed from the E-step's
+// key).  Grid (blocks, m).
+template <typename V>
+__global__ void bcg_fill_kernel(CgConf cf, const CgCtl* ctl, V* X, V* R, const V* bvec) {
+  pdl_wait();
+  pdl_trigger();
+  const int j = blockIdx.y;
+  const uint64_t key = probe_key(cf.seed, ctl->t);
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < cf.ld;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V v = V(0);
+    if (d < cf.D) {
+      if (j < cf.T) {
+        v = bvec[(int64_t)j * cf.ld + d];
+      } else {
+        const int k = j - cf.T;
+        const uint64_t h = probe_word(key, d, k >> 6);
+        v = ((h >> (k & 63)) & 1ull) ? V(-1) : V(1);
+      }
+    }
+    X[(int64_t)j * cf.ld + d] = V(0);
+    R[(int64_t)j * cf.ld + d] = v;
+  }
+}
+
+template <typename V, int CAP>
+size_t gram_smem_bytes() {
+  constexpr int LD = CAP + 1;
+  const size_t stage = (size_t)3 * kGramRows * CAP * sizeof(V) + (size_t)2 * CAP * CAP * sizeof(V);
+  const size_t small = (size_t)3 * CAP * LD * sizeof(V) + (size_t)4 * 64 * 8;
+  return stage > small ? stage : small;
+}
+
+// One gram pass (MODE: start, xi or v) and the last block's algebra.
+// stage[s][col][row]: s = 0 P, 1 Q (V after the v update), 2 Z.
+template <typename V, int CAP, int MODE>
+__global__ void __launch_bounds__(kGramThreads, 1)
+bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P, const V* Z) {
+  using T = Tiles<CAP>;
+  using Acc = GAcc<V>;
+  using Packed = typename Acc::Packed;
+  constexpr int LD = CAP + 1;
+  constexpr int SR = kGramRows;                  // rows per staged column
+  extern __shared__ __align__(16) unsigned char dsm[];
+  pdl_wait();
+  if (MODE != kModeStart && ctl->done) {        // the xi pass ended this iteration
+    pdl_trigger();
+    return;
+  }
+  V* stage = reinterpret_cast<V*>(dsm);
+  V* Ms = stage + 3 * SR * CAP;                  // v mode: M and xi, row-major CAP x CAP
+  V* Xs = Ms + CAP * CAP;
+  const int n = cf.ncols;
+  const int tid = threadIdx.x;
+  if constexpr (MODE == kModeV) {
+    for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
+      Ms[idx] = w.M[idx];
+      Xs[idx] = w.Xi[idx];
+    }
+  }
+  // the Gram matrix U^T W of this mode (stage slots)
+  constexpr int su = MODE == kModeXi ? 0 : 1;
+  constexpr int sw = MODE == kModeXi ? 2 : 1;
+  const int ph = tid % T::PH, slot = tid / T::PH;
+  V acc[T::TPT][16];
+  Acc cmp[T::TPT][16];
+  int ta[T::TPT], tb[T::TPT];
+#pragma unroll
+  for (int q = 0; q < T::TPT; ++q) {
+    const int tau = slot + q * T::SLOTS;
+    ta[q] = tb[q] = -1;
+    if (tau < T::NSYM) sym_tile(tau, T::NT, ta[q], tb[q]);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[q][e] = V(0);
+  }
+  const int64_t ld = cf.ld;
+  for (int64_t r0 = (int64_t)blockIdx.x * SR; r0 < ld; r0 += (int64_t)gridDim.x * SR) {
+    // stage the chunk's rows of the slots this mode reads (zero beyond m)
+    for (int e = tid; e < 3 * CAP * SR; e += kGramThreads) {
+      const int s = e / (CAP * SR), rem = e % (CAP * SR);
+      const int j = rem / SR, r = rem % SR;
+      const bool used = MODE == kModeStart ? s == 1 : MODE == kModeXi ? s != 1 : true;
+      V v = V(0);
+      if (used && j < n && r0 + r < ld) {
+        const V* src = s == 0 ? P : s == 1 ? R : Z;
+        v = src[(int64_t)j * ld + r0 + r];
+      }
+      stage[(s * CAP + j) * SR + r] = v;
+    }
+    __syncthreads();
+    if constexpr (MODE == kModeV) {
+      // X += P M and V = Q - Z xi on this chunk, 4 rows x 4 columns a thread
+      for (int u = tid; u < 2 * T::NUT; u += kGramThreads) {
+        const bool isx = u < T::NUT;
+        const int uu = isx ? u : u - T::NUT;
+        const int rq = uu % (SR / 4), jt = uu / (SR / 4);
+        const int r = 4 * rq, j0 = 4 * jt;
+        if (j0 >= n) continue;
+        const V* src = stage + (isx ? 0 : 2) * CAP * SR;
+        const V* mat = isx ? Ms : Xs;
+        V o[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) o[a][b] = V(0);
+        for (int i = 0; i < n; ++i) {
+          V s4[4], m4[4];
+          ld4(src + i * SR + r, s4);
+          ld4(mat + i * CAP + j0, m4);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) o[a][b] = fma(s4[a], m4[b], o[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = j0 + b;
+          if (j >= n) continue;
+          V col[4];
+          if (isx) {
+            V* xp = X + (int64_t)j * ld + r0 + r;     // ld is a multiple of 64
+            ld4(xp, col);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) col[a] += o[a][b];
+            st4(xp, col);
+          } else {
+            V* qs = stage + (CAP + j) * SR + r;
+            ld4(qs, col);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) col[a] -= o[a][b];
+            st4(qs, col);
+            st4(R + (int64_t)j * ld + r0 + r, col);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < T::TPT; ++q) {
+      if (ta[q] < 0) continue;
+      const V* U = stage + (su * CAP + 4 * ta[q]) * SR;
+      const V* W = stage + (sw * CAP + 4 * tb[q]) * SR;
+      for (int rq = ph; rq < SR / 4; rq += T::PH) {
+        V u[4][4], x[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ld4(U + i * SR + 4 * rq, u[i]);
+          ld4(W + i * SR + 4 * rq, x[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[q][i * 4 + k] = fma(u[i][r], x[k][r], acc[q][i * 4 + k]);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        cmp[q][e].add(acc[q][e]);
+        acc[q][e] = V(0);
+      }
+    }
+    __syncthreads();
+  }
+  pdl_trigger();
+
+  // block partials (the PH threads of a tile are adjacent lanes)
+  Packed* part = reinterpret_cast<Packed*>(w.part);
+  constexpr int nent = T::NSYM * 16;
+#pragma unroll
+  for (int q = 0; q < T::TPT; ++q) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      Acc a = cmp[q][e];
+#pragma unroll
+      for (int o = 1; o < T::PH; o <<= 1) {
+        Packed other;
+        if constexpr (sizeof(V) == 4) {
+          other.x = __shfl_xor_sync(0xffffffffu, a.s, o);
+          other.y = __shfl_xor_sync(0xffffffffu, a.c, o);
+        } else {
+          other = __shfl_xor_sync(0xffffffffu, a.s, o);
+        }
+        a.merge(other);
+      }
+      const int tau = slot + q * T::SLOTS;
+      if (ph == 0 && tau < T::NSYM) part[(int64_t)blockIdx.x * nent + tau * 16 + e] = a.pack();
+    }
+  }
+  // first level: the last block of each group of 16 sums the group
+  const int G = gridDim.x;
+  const int ngroups = (G + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int b0 = grp * kGroup, b1 = min(G, b0 + kGroup);
+  if (!arrive_count(&w.hdr->cnt[grp], (unsigned)(b1 - b0))) return;
+  Packed* gpart = reinterpret_cast<Packed*>(w.gpart);
+  for (int e = tid; e < nent; e += kGramThreads) {
+    Acc a;
+    for (int b = b0; b < b1; ++b) a.merge(part[(int64_t)b * nent + e]);
+    gpart[(int64_t)grp * nent + e] = a.pack();
+  }
+  if (!arrive_count(&w.hdr->cnt[kFinalCounter], (unsigned)ngroups)) return;
+
+  // ---- the last block: the Gram matrix into shared memory
+  V* G1 = reinterpret_cast<V*>(dsm);
+  V* Cm = G1 + CAP * LD;
+  V* rk = Cm + 2 * CAP * LD;
+  V* d0 = rk + 64;
+  int* dead = reinterpret_cast<int*>(d0 + 64);
+  double* red = reinterpret_cast<double*>(dead + 64);
+  __syncthreads();
+  for (int idx = tid; idx < 3 * CAP * LD; idx += kGramThreads) G1[idx] = V(0);
+  __syncthreads();
+  for (int e = tid; e < nent; e += kGramThreads) {
+    Acc a;
+    for (int g = 0; g < ngroups; ++g) a.merge(gpart[(int64_t)g * nent + e]);
+    const V v = (V)a.value();
+    int ta_, tb_;
+    sym_tile(e / 16, T::NT, ta_, tb_);
+    const int row = 4 * ta_ + (e % 16) / 4, col = 4 * tb_ + (e % 4);
+    if (ta_ < tb_ || row <= col) {
+      G1[row * LD + col] = v;
+      G1[col * LD + row] = v;
+    }
+  }
+  __shared__ int done_sh;
+  __syncthreads();
+
+  if constexpr (MODE == kModeStart) {
+    // ||B||_F^2 = tr(B^T B); B^T B = L L^T; C = L^T
+    if (tid == 0) {
+      double n2 = 0.0;
+      for (int j = 0; j < n; ++j) n2 += (double)G1[j * LD + j];
+      ctl->normB2 = n2;
+      ctl->relres = n2 > 0.0 ? 1.0 : 0.0;
+      ctl->iter = 0;
+      ctl->replace = 0;
+      ctl->clamps = 0;
+      ctl->support = 0;
+      ctl->run = 0;
+      int done = 0;
+      if (!(n2 > 0.0)) done = 1;                        // B = 0: X = 0 solves it
+      else if (cf.fixed_iters == 0 && 1.0 < cf.tol) done = 1;
+      if (!isfinite(n2)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+      done_sh = done;
+    }
+    __syncthreads();
+    const int done = done_sh;
+    if (!done) {
+      cholesky<V, LD>(G1, n, d0, dead);
+      store_factor<V, CAP, LD>(w, G1, n);
+      for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
+        const int i = idx / CAP, j = idx % CAP;
+        w.C[idx] = (i < n && j < n && i <= j) ? G1[j * LD + i] : V(0);
+      }
+    }
+    if (tid == 0) {
+      ctl->done = done;
+      set_cond_h(cf.while_handle, done ? 0u : 1u);
+    }
+  } else {
+    for (int idx = tid; idx < CAP * CAP; idx += kGramThreads)
+      Cm[(idx / CAP) * LD + idx % CAP] = w.C[idx];
+    if constexpr (MODE == kModeXi) {
+      const int kept = sweep_inverse<V, LD>(G1, n, rk, d0, dead);   // G1 = xi
+      // M = xi C (C upper triangular)
+      for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
+        const int i = idx / CAP, j = idx % CAP;
+        V s = V(0);
+        if (i < n && j < n)
+          for (int k = 0; k <= j; ++k) s = fma(G1[i * LD + k], Cm[k * LD + j], s);
+        w.M[idx] = s;
+        w.Xi[idx] = (i < n && j < n) ? G1[i * LD + j] : V(0);
+      }
+      if (kept == 0 && tid == 0) {
+        raise_error(ctl, COFEM_ERR_BREAKDOWN);
+        ctl->iter += 1;
+        ctl->done = 1;
+        set_cond_h(cf.while_handle, 0u);
+      }
+    } else {
+      // ||V C||_F^2 = sum_ij C_ij (G2 C)_ij, stop test, V = Q psi
+      __syncthreads();
+      double part2 = 0.0;
+      for (int idx = tid; idx < n * n; idx += kGramThreads) {
+        const int i = idx / n, j = idx % n;
+        V s = V(0);
+        for (int k = 0; k <= j; ++k) s = fma(G1[i * LD + k], Cm[k * LD + j], s);
+        part2 += (double)Cm[i * LD + j] * (double)s;
+      }
+      const double r2 = block_sum(part2, red);
+      if (tid == 0) {
+        const double relres = sqrt(fmax(r2, 0.0) / ctl->normB2);
+        ctl->relres = relres;
+        const int it = ctl->iter + 1;
+        ctl->iter = it;
+        int done;
+        if (cf.fixed_iters > 0) done = it >= cf.fixed_iters;
+        else done = (relres < cf.tol) || (it >= cf.max_iters);
+        if (!isfinite(relres)) { raise_error(ctl, COFEM_ERR_NONFINITE); done = 1; }
+        done_sh = done;
+      }
+      __syncthreads();
+      const int done = done_sh;
+      if (!done) {
+        cholesky<V, LD>(G1, n, d0, dead);
+        store_factor<V, CAP, LD>(w, G1, n);
+        // C = L^T C (both upper triangular)
+        for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
+          const int i = idx / CAP, j = idx % CAP;
+          V s = V(0);
+          if (i < n && j < n && i <= j)
+            for (int k = i; k <= j; ++k) s = fma(G1[k * LD + i], Cm[k * LD + j], s);
+          w.C[idx] = s;
+        }
+      }
+      if (tid == 0) {
+        ctl->done = done;
+        set_cond_h(cf.while_handle, done ? 0u : 1u);
+      }
+    }
+  }
+}
+
+template <typename V, int CAP>
+size_t row_smem_bytes() {
+  return (size_t)2 * CAP * CAP * sizeof(V) + (size_t)CAP * sizeof(V) +
+         (RowInRegisters<CAP>::value ? 0 : (size_t)CAP * kRowThreads * sizeof(V));
+}
+
+// Row pass, one thread per row d: q = v L^-T (V in R), p = q + p psi^T
+// (init: p = q).
+template <typename V, int CAP>
+__global__ void __launch_bounds__(kRowThreads)
+bcg_row_kernel(CgConf cf, const CgCtl* ctl, BcgView<V, CAP> w, V* R, V* P, int init) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  pdl_wait();
+  if (ctl->done) {
+    pdl_trigger();
+    return;
+  }
+  V* L = reinterpret_cast<V*>(dsm);
+  V* Lt = L + CAP * CAP;
+  V* rd = Lt + CAP * CAP;
+  V* my = rd + CAP + threadIdx.x;               // wide blocks: [CAP][kRowThreads]
+  for (int idx = threadIdx.x; idx < CAP * CAP; idx += blockDim.x) {
+    L[idx] = w.L[idx];
+    Lt[idx] = w.Lt[idx];
+  }
+  for (int j = threadIdx.x; j < CAP; j += blockDim.x) rd[j] = w.rdiag[j];
+  __syncthreads();
+  pdl_trigger();
+  const int n = cf.ncols;
+  const int64_t ld = cf.ld;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < ld;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    V v[RowInRegisters<CAP>::value ? CAP : 1], p[CAP];
+#pragma unroll
+    for (int j = 0; j < CAP; ++j) p[j] = (!init && j < n) ? P[(int64_t)j * ld + d] : V(0);
+    // q_i = v_i / L_ii, then v_j -= q_i L_ji (j > i); a dropped index has
+    // rdiag 0 and a zero column of L
+    if constexpr (RowInRegisters<CAP>::value) {
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) v[j] = j < n ? R[(int64_t)j * ld + d] : V(0);
+#pragma unroll
+      for (int i = 0; i < CAP; ++i) {
+        v[i] *= rd[i];
+#pragma unroll
+        for (int j = i + 1; j < CAP; ++j) v[j] = fma(-v[i], L[j * CAP + i], v[j]);
+      }
+    } else {
+      for (int j = 0; j < n; ++j) my[j * kRowThreads] = R[(int64_t)j * ld + d];
+      for (int i = 0; i < n; ++i) {
+        const V qi = my[i * kRowThreads] * rd[i];
+        my[i * kRowThreads] = qi;
+        for (int j = i + 1; j < n; ++j)
+          my[j * kRowThreads] = fma(-qi, L[j * CAP + i], my[j * kRowThreads]);
+      }
+    }
+    // p_j = q_j + sum_{i >= j} p_i L_ij
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+      const V* lj = Lt + j * CAP;
+      V s = V(0);
+#pragma unroll
+      for (int i = 0; i < CAP; ++i) s = fma(p[i], lj[i], s);
+      V q = V(0);
+      if constexpr (RowInRegisters<CAP>::value) {
+#pragma unroll
+        for (int i = 0; i < CAP; ++i) q = i == j ? v[i] : q;
+      } else {
+        q = my[j * kRowThreads];
+      }
+      s += q;
+      R[(int64_t)j * ld + d] = q;
+      P[(int64_t)j * ld + d] = s;
+      if constexpr (sizeof(V) == 4) {
+        if (cf.split_nt > 0) {
+          __nv_bfloat16* buf = reinterpret_cast<__nv_bfloat16*>(cf.split_buf);
+          float r = s;
+          for (int t = 0; t < cf.split_nt; ++t) {
+            const __nv_bfloat16 o = __float2bfloat16_rn(r);
+            r -= __bfloat162float(o);
+            buf[(int64_t)split_row(j, t, cf.split_nt) * ld + d] = o;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side
+
+template <typename V, int CAP>
+BcgView<V, CAP> view(char* st, int G) {
+  BcgView<V, CAP> w;
+  size_t o = 0;
+  w.hdr = reinterpret_cast<BcgHdr*>(st);
+  o += (sizeof(BcgHdr) + 255) & ~(size_t)255;
+  V** mats[6] = {&w.C, &w.M, &w.Xi, &w.L, &w.Lt, &w.rdiag};
+  for (int i = 0; i < 6; ++i) {
+    *mats[i] = reinterpret_cast<V*>(st + o);
+    o += (BcgView<V, CAP>::mat_bytes() + 255) & ~(size_t)255;
+  }
+  using Packed = typename GAcc<V>::Packed;
+  const size_t nent = (size_t)Tiles<CAP>::NSYM * 16;
+  w.part = st + o;
+  o += ((size_t)G * nent * sizeof(Packed) + 255) & ~(size_t)255;
+  w.gpart = st + o;
+  return w;
+}
+
+template <typename V, int CAP>
+size_t state_bytes(int G) {
+  using Packed = typename GAcc<V>::Packed;
+  const size_t nent = (size_t)Tiles<CAP>::NSYM * 16;
+  const int ng = (G + kGroup - 1) / kGroup;
+  size_t o = (sizeof(BcgHdr) + 255) & ~(size_t)255;
+  o += 6 * ((BcgView<V, CAP>::mat_bytes() + 255) & ~(size_t)255);
+  o += ((size_t)G * nent * sizeof(Packed) + 255) & ~(size_t)255;
+  o += ((size_t)ng * nent * sizeof(Packed) + 255) & ~(size_t)255;
+  return o;
+}
+
+int gram_blocks(int64_t ld) {
+  const int64_t chunks = (ld + kGramRows - 1) / kGramRows;
+  const int sms = num_sms();
+  return (int)(chunks < sms ? chunks : sms);
+}
+
+template <typename V, int CAP, int MODE>
+cudaError_t launch_gram(const CgConf& cf, CgCtl* ctl, const BcgView<V, CAP>& w, int G, V* X,
+                        V* R, const V* P, const V* Z, cudaStream_t s) {
+  const size_t gs = gram_smem_bytes<V, CAP>();
+  cudaError_t e = cudaFuncSetAttribute(bcg_gram_kernel<V, CAP, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs);
+  if (e != cudaSuccess) return e;
+  return launch_k(bcg_gram_kernel<V, CAP, MODE>, dim3(G), dim3(kGramThreads), gs, s, cf, ctl, w,
+                  X, R, P, Z);
+}
+
+template <typename V, int CAP>
+cudaError_t launch_row(const CgConf& cf, CgCtl* ctl, const BcgView<V, CAP>& w, V* R, V* P,
+                       int init, cudaStream_t s) {
+  const size_t rs = row_smem_bytes<V, CAP>();
+  cudaError_t e = cudaFuncSetAttribute(bcg_row_kernel<V, CAP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+  if (e != cudaSuccess) return e;
+  int64_t rb = (cf.ld + kRowThreads - 1) / kRowThreads;
+  const int64_t cap = (int64_t)4 * num_sms();
+  if (rb > cap) rb = cap;
+  return launch_k(bcg_row_kernel<V, CAP>, dim3((unsigned)rb), dim3(kRowThreads), rs, s, cf,
+                  (const CgCtl*)ctl, w, R, P, init);
+}
+
+template <typename V, int CAP>
+cudaError_t launch_sequence(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P,
+                            const V* Z, bool start, cudaStream_t s) {
+  const int G = gram_blocks(cf.ld);
+  const BcgView<V, CAP> w = view<V, CAP>(st, G);
+  cudaError_t e;
+  if (start) {
+    e = launch_gram<V, CAP, kModeStart>(cf, ctl, w, G, X, R, P, Z, s);
+    if (e != cudaSuccess) return e;
+    return launch_row<V, CAP>(cf, ctl, w, R, P, 1, s);
+  }
+  e = launch_gram<V, CAP, kModeXi>(cf, ctl, w, G, X, R, P, Z, s);
+  if (e != cudaSuccess) return e;
+  e = launch_gram<V, CAP, kModeV>(cf, ctl, w, G, X, R, P, Z, s);
+  if (e != cudaSuccess) return e;
+  return launch_row<V, CAP>(cf, ctl, w, R, P, 0, s);
+}
+
+template <typename V>
+cudaError_t dispatch(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P, const V* Z,
+                     bool start, cudaStream_t s) {
+  switch (capacity(cf.ncols)) {
+    case 8: return launch_sequence<V, 8>(cf, ctl, st, X, R, P, Z, start, s);
+    case 16: return launch_sequence<V, 16>(cf, ctl, st, X, R, P, Z, start, s);
+    case 24: return launch_sequence<V, 24>(cf, ctl, st, X, R, P, Z, start, s);
+    case 36: return launch_sequence<V, 36>(cf, ctl, st, X, R, P, Z, start, s);
+    case 48: return launch_sequence<V, 48>(cf, ctl, st, X, R, P, Z, start, s);
+    default: return launch_sequence<V, 64>(cf, ctl, st, X, R, P, Z, start, s);
+  }
+}
+
+}  // namespace
+
+size_t bcg_state_bytes(int vec_bytes, int ncols, int64_t ld) {
+  const int G = gram_blocks(ld);
+  const bool f = vec_bytes == 4;
+  switch (capacity(ncols)) {
+    case 8: return f ? state_bytes<float, 8>(G) : state_bytes<double, 8>(G);
+    case 16: return f ? state_bytes<float, 16>(G) : state_bytes<double, 16>(G);
+    case 24: return f ? state_bytes<float, 24>(G) : state_bytes<double, 24>(G);
+    case 36: return f ? state_bytes<float, 36>(G) : state_bytes<double, 36>(G);
+    case 48: return f ? state_bytes<float, 48>(G) : state_bytes<double, 48>(G);
+    default: return f ? state_bytes<float, 64>(G) : state_bytes<double, 64>(G);
+  }
+}
+
+template <typename V>
+cudaError_t launch_bcg_start(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P,
+                             const V* bvec, cudaStream_t s) {
+  dim3 g((unsigned)((cf.ld + 255) / 256 < 1024 ? (cf.ld + 255) / 256 : 1024), (unsigned)cf.ncols);
+  cudaError_t e = launch_k(bcg_fill_kernel<V>, g, dim3(256), 0, s, cf, (const CgCtl*)ctl, X, R,
+                           bvec);
+  if (e != cudaSuccess) return e;
+  return dispatch<V>(cf, ctl, st, X, R, P, (const V*)nullptr, true, s);
+}
+
+template <typename V>
+cudaError_t launch_bcg_iteration(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P,
+                                 const V* Z, cudaStream_t s) {
+  return dispatch<V>(cf, ctl, st, X, R, P, Z, false, s);
+}
+
+template cudaError_t launch_bcg_start<float>(const CgConf&, CgCtl*, char*, float*, float*,
+                                             float*, const float*, cudaStream_t);
+template cudaError_t launch_bcg_start<double>(const CgConf&, CgCtl*, char*, double*, double*,
+                                              double*, const double*, cudaStream_t);
+template cudaError_t launch_bcg_iteration<float>(const CgConf&, CgCtl*, char*, float*, float*,
+                                                 float*, const float*, cudaStream_t);
+template cudaError_t launch_bcg_iteration<double>(const CgConf&, CgCtl*, char*, double*, double*,
+                                                  double*, const double*, cudaStream_t);
+
+}  // namespace cofem

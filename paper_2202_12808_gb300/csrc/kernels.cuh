@@ -60,6 +60,20 @@ int cg_update_selftest(int64_t limit_ns, char* ws, cudaStream_t st);
 size_t cg_kernels_bench_bytes(int64_t D, int ncols);
 int cg_kernels_bench(int64_t D, int ncols, int reps, char* ws, cudaStream_t st, float* ms);
 
+// ---- block CG (block_cg.cu) ----
+// Workspace bytes of one block-CG solve with ncols columns of leading
+// dimension ld (vector element size vec_bytes).
+size_t bcg_state_bytes(int vec_bytes, int ncols, int64_t ld);
+// Start of an E-step: X = 0, Q R-factor of B, P = Q.
+template <typename V>
+cudaError_t launch_bcg_start(const CgConf& cf, CgCtl* ctl, char* state, V* X, V* R, V* P,
+                             const V* bvec, cudaStream_t st);
+// One iteration after Z = A P: the xi and v gram passes (the second with
+// the stop test) and the row pass.
+template <typename V>
+cudaError_t launch_bcg_iteration(const CgConf& cf, CgCtl* ctl, char* state, V* X, V* R, V* P,
+                                 const V* Z, cudaStream_t st);
+
 template <typename V>
 void launch_cg_true_resid(const CgConf& cf, CgCtl* ctl, CgScalars* sc, V* R, const V* Q,
                           const V* bvec, double* part, double* part2, cudaStream_t st);

@@ -43,9 +43,9 @@ def test_params_default_matches_header(built):
     assert (p.K, p.em_iters, p.cg_max_iters, p.fixed_cg_iters, p.resid_replace_every) == (20, 50, 400, 0, 0)
     assert p.vec_dtype == B.COFEM_F32
     assert (p.cg_tol, p.alpha_init, p.den_floor, p.support_threshold) == (1e-6, 1.0, 1e-12, 1e6)
-    assert p.stop_rule == 0 and p.tasks == 0
-    # 8 int32 fields, 4 doubles, seed, t_offset, mlp
-    assert ctypes.sizeof(B.cofem_params) == 8 * 4 + 4 * 8 + 8 + 8 + 8
+    assert p.stop_rule == 0 and p.tasks == 0 and p.solver == 0
+    # 8 int32 fields, 4 doubles, seed, t_offset, mlp, solver (padded to 8)
+    assert ctypes.sizeof(B.cofem_params) == 8 * 4 + 4 * 8 + 8 + 8 + 8 + 8
 
 
 def test_stop_rule_validation(built):
@@ -54,6 +54,25 @@ def test_stop_rule_validation(built):
         assert B.cofem_workspace_bytes(h, B.cofem_params_default(stop_rule=1)) > 0
         for bad, code in ((dict(stop_rule=2), 1), (dict(stop_rule=-1), 1),
                           (dict(stop_rule=1, mlp=256), 6)):
+            with pytest.raises(B.CofemError) as e:
+                B.cofem_workspace_bytes(h, B.cofem_params_default(**bad))
+            assert e.value.code == code, bad
+    finally:
+        B.cofem_op_destroy(h)
+
+
+def test_solver_validation(built):
+    """Block CG (solver 1) takes the joint stop test on its own recurrence:
+    residual replacement, the per-column rule and the learned start are
+    refused (COFEM_ERR_UNSUPPORTED = 6); other solver values are invalid."""
+    h = B.cofem_op_dense(4, 10, B.COFEM_F32, 256, 64)
+    try:
+        assert B.cofem_workspace_bytes(h, B.cofem_params_default(solver=1)) > \
+            B.cofem_workspace_bytes(h, B.cofem_params_default(solver=0))
+        for bad, code in ((dict(solver=2), 1), (dict(solver=-1), 1),
+                          (dict(solver=1, resid_replace_every=50), 6),
+                          (dict(solver=1, stop_rule=1), 6),
+                          (dict(solver=1, mlp=256), 6)):
             with pytest.raises(B.CofemError) as e:
                 B.cofem_workspace_bytes(h, B.cofem_params_default(**bad))
             assert e.value.code == code, bad

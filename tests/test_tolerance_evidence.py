@@ -17,7 +17,10 @@ the GPU tests cite for their bars:
 * tests/test_gpu_headline.py -- the full-shape fit is compared after its
   first EM iteration only;
 * tests/test_gpu_fit.py::test_fp8_dictionary_fit -- alpha on the support
-  at 3e-3 with the FP8 dictionary.
+  at 3e-3 with the FP8 dictionary;
+* tests/test_gpu_block_cg.py -- block CG with FP32 vectors in a first
+  E-step (alpha = 1): mu at 1e-2 after six iterations, the masked DCT's mu
+  at 1e-3.
 """
 import numpy as np
 import pytest
@@ -246,3 +249,70 @@ def test_fp8_dictionary_alpha_sensitivity():
     assert rel_l2(emu, rmu) <= 1e-4
     assert support_compare(ea, ra)[0]
     assert 1e-3 < _alpha_dev(ea, ra) < 3e-3
+
+
+# ------------------------------------------------- block CG (solver variant)
+
+def test_block_emulation_without_hooks_is_the_oracle():
+    rng = np.random.default_rng(3)
+    Phi = rng.standard_normal((40, 120)) / np.sqrt(40)
+    y = rng.standard_normal(40)
+    kw = dict(seed=2, solver=1)
+    r = sbl.cofem_dense(Phi, y, 50.0, 6, 4, 1e-8, 200, **kw)
+    e = em.cofem_dense(Phi, y, 50.0, 6, 4, 1e-8, 200, **kw)
+    for a, b in zip(r[:3], e[:3]):
+        assert np.array_equal(a, b)
+    assert r[3].cg_iters == e[3].cg_iters
+
+
+def test_block_cg_fp32_first_e_step_amplifies_rounding():
+    """N = 512, D = 8192, K = 32 (33 columns), sigma 0.01, t = 1: A = beta
+    Phi^T Phi + I has the eigenvalue 1 on the 7680-dimensional null space of
+    Phi and beta-sized ones on its range.  Block CG builds the mean column
+    from the probes' directions, whose null-space parts are large, so FP32
+    rounding reaches mu: after two iterations it is 6e-6 away from the FP64
+    iterate, after six 2.8e-3 -- while column-wise CG in FP32, whose mean
+    column stays in the range, is 2e-6 away.  The GPU's block CG gives 8e-6
+    and 3.5e-3 here (tests/test_gpu_block_cg.py::
+    test_block_fp32_fixed_iterations_multichunk, bar 1e-2)."""
+    prob = datagen.dense_problem(512, 8192, 8192 // 20, 0.01, 0)
+    Phi = prob.Phi.astype(np.float64)
+    y32 = prob.y.astype(np.float32).astype(np.float64)
+    out = {}
+    for k in (2, 6):
+        for solver in (0, 1):
+            r = sbl.cofem_dense(Phi, y32, prob.beta, 32, 1, 1e-6, 400, fixed_cg_iters=k,
+                                seed=3, solver=solver)
+            e = em.cofem_dense(Phi, y32, prob.beta, 32, 1, 1e-6, 400, fixed_cg_iters=k,
+                               seed=3, solver=solver, vround=em.fp32_round,
+                               fp32_products=True)
+            out[k, solver] = rel_l2(e[1], r[1])
+    assert out[2, 1] <= 1e-4
+    assert 1e-3 <= out[6, 1] <= 1e-2
+    assert out[6, 0] <= 1e-5
+
+
+def test_block_cg_dct_fp32_mu():
+    """The masked DCT (D = 4096, N = 1024, 0.04 D coefficients, sigma 0.01,
+    K 20, 10 EM iterations, tol 1e-5) with block CG: Phi Phi^T = I, so A has
+    just the eigenvalues 1 and beta + alpha at t = 1, and FP32 vectors with
+    FP32 transforms leave mu 2.3e-4 from the FP64 block fit (the GPU: 3e-4;
+    tests/test_gpu_block_cg.py::test_block_dct_fp32, bar 1e-3)."""
+    D, N = 4096, 1024
+    p = datagen.dct_problem(D, N, int(0.04 * D), 0.01, seed=0)
+    y32 = p.y.astype(np.float32).astype(np.float64)
+    idx = p.idx
+
+    def phi(Z):
+        return sfft.idct(np.asarray(Z).astype(np.float32), type=2, norm="ortho",
+                         axis=0)[idx].astype(np.float64)
+
+    def phit(W):
+        T = np.zeros((D,) + W.shape[1:], dtype=np.float32)
+        T[idx] = W.astype(np.float32)
+        return sfft.dct(T, type=2, norm="ortho", axis=0).astype(np.float64)
+
+    ra, rmu, rs, rst = sbl.cofem_dct(idx, D, y32, p.beta, 20, 10, 1e-5, 400, seed=0, solver=1)
+    ea, emu, es, est = em.cofem(phi, phit, D, y32, p.beta, 20, 10, 1e-5, 400, seed=0,
+                                solver=1, vround=em.fp32_round)
+    assert 1e-4 <= rel_l2(emu, rmu) <= 1e-3

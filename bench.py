@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-whole-fit", action="store_true",
                     help="skip the 100-EM-iteration fits (BF16 and the FP32 comparator)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solver", default="column", choices=["column", "block"],
+                    help="E-step solver of the timed window: the paper's column-wise CG "
+                         "(residual replacement every 50) or the block-CG variant (none)")
     return ap.parse_args()
 
 
@@ -1042,7 +1045,9 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
     """The whole 100-EM-iteration fit of the headline workload, three times:
     the BF16 dictionary (the bench's operator), the plain FP32 comparator
     (the FP32 dictionary on the tensor cores, Phi = hi + lo) and the FP8 E4M3
-    dictionary with per-tile scales.  For each: EM iterations per second of
+    dictionary with per-tile scales; and the BF16 fit once more with block CG
+    (the solver variant, no residual replacement).  For each: EM iterations
+    per second of
     the whole fit, the time to 2 % NRMSE (Sec. 4.2's criterion) and time to
     tolerance -- the device time until the support equals the FP64 oracle's
     final support and alpha on it stays within 1e-2 / 1e-3 of the oracle's
@@ -1071,8 +1076,11 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
         tuned[name] = {"stages": stg, "ctas_per_sm": cps, "us_per_apply": us,
                        "tile_rows": B.cofem_op_dense_get_pipeline(op.handle)[2]}
         del wst
-    for name, op, ref_phi in (("bf16", op16, "bf16"), ("fp32", op32, "f32"), ("fp8", op8, None)):
-        sec, stats, hist, nrmse = whole_fit(api, B, op, y, prob.beta, kw, em, dev, z=prob.z)
+    # block CG (solver variant: no residual replacement) on the BF16 dictionary
+    kwb = dict(kw, resid_replace_every=0, solver=1)
+    for name, op, ref_phi, k_ in (("bf16", op16, "bf16", kw), ("fp32", op32, "f32", kw),
+                                  ("fp8", op8, None, kw), ("bf16_block", op16, "bf16", kwb)):
+        sec, stats, hist, nrmse = whole_fit(api, B, op, y, prob.beta, k_, em, dev, z=prob.z)
         ent = {"em_iters_per_s": em / sec, "seconds": sec,
                "cg_iters_total": int(sum(stats["cg_iters"])),
                "cg_iters_per_em": stats["cg_iters"],
@@ -1094,9 +1102,14 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
     for name in ("fp32", "fp8"):
         out[name]["pipeline"] = tuned[name]
     out["ratio_em_iters_per_s"] = out["bf16"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
-    out["ratio_em_iters_per_s_fp8"] = out["fp8"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
     t16, t32 = out["bf16"]["time_to_2pct_nrmse"], out["fp32"]["time_to_2pct_nrmse"]
     out["ratio_time_to_2pct_nrmse"] = (t32["seconds"] / t16["seconds"]) if t16 and t32 else None
+    out["ratio_em_iters_per_s_fp8"] = out["fp8"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"]
+    out["ratio_em_iters_per_s_block"] = (out["bf16_block"]["em_iters_per_s"] /
+                                         out["fp32"]["em_iters_per_s"])
+    tb = out["bf16_block"]["time_to_2pct_nrmse"]
+    out["ratio_time_to_2pct_nrmse_block"] = (t32["seconds"] / tb["seconds"]) if tb and t32 else None
+
     t8 = out["fp8"]["time_to_2pct_nrmse"]
     out["ratio_time_to_2pct_nrmse_fp8"] = (t32["seconds"] / t8["seconds"]) if t8 and t32 else None
     # the FP32 and FP8 operators' kernels, timed with CUDA events on the stream
@@ -1175,6 +1188,8 @@ def main():
     kw = dict(vec_dtype=B.COFEM_F32, K=CFG["K"], cg_tol=CFG["cg_tol"],
               cg_max_iters=CFG["cg_max_iters"], resid_replace_every=CFG["resid_replace_every"],
               seed=args.seed)
+    if args.solver == "block":
+        kw.update(resid_replace_every=0, solver=1)
     # warm-up: the first W EM iterations of the fit
     pw = api.params(em_iters=args.warmup, **kw)
     wsp = api.workspace(op, api.params(em_iters=max(args.warmup, args.steps), **kw), dev)
@@ -1280,7 +1295,9 @@ def main():
                        "split_terms": args.terms if args.phi == "bf16" else None,
                        "phi_layout": args.layout if args.phi == "bf16" else "rowmajor",
                        "pipeline": tuned,
-                       "cg_tol": CFG["cg_tol"], "resid_replace_every": CFG["resid_replace_every"],
+                       "cg_tol": CFG["cg_tol"],
+                       "resid_replace_every": kw["resid_replace_every"],
+                       "solver": args.solver,
                        "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps),
                        "l2": "inputs larger than L2 (Phi %d MB)" % (phi_bytes >> 20),
                        "parallelism": "replicas" if ws > 1 else "single"},

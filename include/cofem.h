@@ -515,6 +515,20 @@ size_t cofem_bench_cg_kernels_workspace_bytes(int64_t D, int32_t ncols);
 cofem_status cofem_bench_cg_kernels(int64_t D, int32_t ncols, int32_t reps, void* workspace_dev,
                                     size_t workspace_bytes, void* stream, float* ms_out);
 
+/* Timing of the block-CG passes (params.solver = 1) outside a fit graph
+ * (diagnostics; the paper has no counterpart).  On ncols (2..64) FP32
+ * columns of D values in workspace_dev (>= cofem_bench_bcg_kernels_
+ * workspace_bytes(D, ncols) bytes, any alignment; overwritten), with P,
+ * Z = P and Q refilled before every timed launch: ms_out[0] the xi pass
+ * (Gram P^T Z, xi, M), ms_out[1] the v pass (X and V updates, Gram V^T V,
+ * stop test, Cholesky QR step), ms_out[2] the row pass (Q, P and P's BF16
+ * terms), ms_out[3] the three back to back; mean milliseconds over `reps`
+ * launches after one warm-up, CUDA events on `stream`.  Synchronous. */
+size_t cofem_bench_bcg_kernels_workspace_bytes(int64_t D, int32_t ncols);
+cofem_status cofem_bench_bcg_kernels(int64_t D, int32_t ncols, int32_t reps,
+                                     void* workspace_dev, size_t workspace_bytes, void* stream,
+                                     float* ms_out);
+
 size_t cofem_selftest_cg_update_workspace_bytes(void);
 cofem_status cofem_selftest_cg_update_timeout(int64_t limit_ns, void* workspace_dev,
                                               size_t workspace_bytes, void* stream);

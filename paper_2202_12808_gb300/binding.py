@@ -111,6 +111,9 @@ _SIGS = {
     "cofem_selftest_cg_update_workspace_bytes": (_SZ, []),
     "cofem_bench_cg_kernels_workspace_bytes": (_SZ, [_I64, _I32]),
     "cofem_bench_cg_kernels": (_S, [_I64, _I32, _I32, _P, _SZ, _P, ctypes.POINTER(ctypes.c_float)]),
+    "cofem_bench_bcg_kernels_workspace_bytes": (_SZ, [_I64, _I32]),
+    "cofem_bench_bcg_kernels": (_S, [_I64, _I32, _I32, _P, _SZ, _P,
+                                     ctypes.POINTER(ctypes.c_float)]),
     "cofem_selftest_cg_update_timeout": (_S, [_I64, _P, _SZ, _P]),
     "cofem_op_forward": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
     "cofem_op_adjoint": (_S, [_P, _S, _P, _I64, _I32, _P, _I64, _P, _SZ, _P]),
@@ -348,6 +351,19 @@ def cofem_bench_cg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream=0):
     ms = (ctypes.c_float * 4)()
     _check(lib().cofem_bench_cg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream, ms),
            "cofem_bench_cg_kernels")
+    return tuple(ms)
+
+
+
+def cofem_bench_bcg_kernels_workspace_bytes(D, ncols):
+    return lib().cofem_bench_bcg_kernels_workspace_bytes(D, ncols)
+
+def cofem_bench_bcg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream=0):
+    """Mean milliseconds per launch of the block-CG passes: xi gram, v gram,
+    row, and the three back to back."""
+    ms = (ctypes.c_float * 4)()
+    _check(lib().cofem_bench_bcg_kernels(D, ncols, reps, ws_ptr, ws_bytes, stream, ms),
+           "cofem_bench_bcg_kernels")
     return tuple(ms)
 
 

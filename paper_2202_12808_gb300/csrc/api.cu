@@ -781,6 +781,23 @@ cofem_status cofem_bench_cg_kernels(int64_t D, int32_t ncols, int32_t reps, void
   return COFEM_OK;
 }
 
+size_t cofem_bench_bcg_kernels_workspace_bytes(int64_t D, int32_t ncols) {
+  if (D < 1 || ncols < 2 || ncols > kMaxCols) return 0;
+  return bcg_bench_bytes(D, ncols);
+}
+
+cofem_status cofem_bench_bcg_kernels(int64_t D, int32_t ncols, int32_t reps, void* workspace_dev,
+                                     size_t workspace_bytes, void* stream, float* ms_out) {
+  if (D < 1 || ncols < 2 || ncols > kMaxCols || reps < 1 || !workspace_dev || !ms_out)
+    return COFEM_ERR_INVALID_ARG;
+  if (workspace_bytes < bcg_bench_bytes(D, ncols)) return COFEM_ERR_WORKSPACE;
+  if (bcg_kernels_bench(D, ncols, reps, (char*)workspace_dev, (cudaStream_t)stream, ms_out) != 0) {
+    set_error("block CG kernel timing", cudaGetLastError(), __FILE__, __LINE__);
+    return COFEM_ERR_CUDA;
+  }
+  return COFEM_OK;
+}
+
 size_t cofem_selftest_cg_update_workspace_bytes(void) { return cg_update_selftest_bytes(); }
 
 cofem_status cofem_selftest_cg_update_timeout(int64_t limit_ns, void* workspace_dev,

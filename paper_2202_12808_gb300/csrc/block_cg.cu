@@ -37,6 +37,8 @@
 // of xi, its column of L (so its row of psi and of C) are zero and the
 // direction takes no further part.  A step whose P^T Z has no index left
 // raises COFEM_ERR_BREAKDOWN.
+#include <cstring>
+
 #include "kernels.cuh"
 
 namespace cofem {
@@ -44,7 +46,9 @@ namespace cofem {
 namespace {
 
 constexpr int kGramThreads = 512;   // threads of a gram block
-constexpr int kGramRows = 32;       // rows staged per pass of a gram block
+// rows staged per chunk of a gram block: 64 (FP32) or 32 (FP64) -- two
+// chunks of four blocks of CAP columns stay within shared memory
+template <typename V> struct GramRows { static constexpr int value = sizeof(V) == 4 ? 64 : 32; };
 constexpr int kGroup = 16;          // gram blocks per first-level group
 constexpr int kRowThreads = 128;    // threads of a row block (one row each)
 constexpr int kFinalCounter = 63;   // counter slot of the last-level arrival
@@ -106,21 +110,22 @@ template <> struct GAcc<double> {
 };
 
 // 4 x 4 tiles (a <= b) of one symmetric CAP x CAP Gram matrix; PH threads
-// (adjacent lanes) share a tile, each taking every PH-th row quad.
-template <int CAP>
+// (adjacent lanes) share a tile, each taking every PH-th row quad of an
+// SR-row chunk.
+template <int CAP, int SR>
 struct Tiles {
   static constexpr int NT = CAP / 4;
   static constexpr int NSYM = NT * (NT + 1) / 2;
   static constexpr int ph_for(int ntasks) {
     int p = 1;
-    while (p < kGramRows / 4 && 2 * p * ntasks <= kGramThreads) p *= 2;
+    while (p < 8 && 2 * p * ntasks <= kGramThreads) p *= 2;
     return p;
   }
   static constexpr int PH = ph_for(NSYM);
   static constexpr int SLOTS = kGramThreads / PH;
   static constexpr int TPT = (NSYM + SLOTS - 1) / SLOTS;
-  // 4 x 4 output tiles of a staged 32-row chunk times an m x m matrix
-  static constexpr int NUT = (kGramRows / 4) * NT;
+  // 4 x 4 output tiles of a staged chunk times an m x m matrix
+  static constexpr int NUT = (SR / 4) * NT;
 };
 
 // Up to 36 columns the row pass keeps v in registers and unrolls the
@@ -174,6 +179,19 @@ __device__ __forceinline__ void st4(V* p, const V (&v)[4]) {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
     *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
   }
+}
+
+// 16-byte asynchronous global -> shared copies (L2 only), in groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void set_cond_h(unsigned long long h, unsigned v) {
@@ -310,21 +328,26 @@ __global__ void bcg_fill_kernel(CgConf cf, const CgCtl* ctl, V* X, V* R, const V
 template <typename V, int CAP>
 size_t gram_smem_bytes() {
   constexpr int LD = CAP + 1;
-  const size_t stage = (size_t)3 * kGramRows * CAP * sizeof(V) + (size_t)2 * CAP * CAP * sizeof(V);
+  const size_t stage = (size_t)2 * 4 * GramRows<V>::value * CAP * sizeof(V) +
+                       (size_t)2 * CAP * CAP * sizeof(V);
   const size_t small = (size_t)3 * CAP * LD * sizeof(V) + (size_t)4 * 64 * 8;
   return stage > small ? stage : small;
 }
 
 // One gram pass (MODE: start, xi or v) and the last block's algebra.
-// stage[s][col][row]: s = 0 P, 1 Q (V after the v update), 2 Z.
+// Chunks of SR rows are staged column-major in two buffers
+// stage[buf][s][col][row], s = 0 P, 1 Q (V after the v update), 2 Z, 3 X,
+// the next chunk's asynchronous copies in flight while this one is used.
 template <typename V, int CAP, int MODE>
 __global__ void __launch_bounds__(kGramThreads, 1)
 bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P, const V* Z) {
-  using T = Tiles<CAP>;
+  constexpr int SR = GramRows<V>::value;         // rows per staged column
+  using T = Tiles<CAP, SR>;
   using Acc = GAcc<V>;
   using Packed = typename Acc::Packed;
   constexpr int LD = CAP + 1;
-  constexpr int SR = kGramRows;                  // rows per staged column
+  constexpr int NS = 4;                          // slots per buffer
+  constexpr int BUF = NS * CAP * SR;             // elements per buffer
   extern __shared__ __align__(16) unsigned char dsm[];
   pdl_wait();
   if (MODE != kModeStart && ctl->done) {        // the xi pass ended this iteration
@@ -332,10 +355,16 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
     return;
   }
   V* stage = reinterpret_cast<V*>(dsm);
-  V* Ms = stage + 3 * SR * CAP;                  // v mode: M and xi, row-major CAP x CAP
+  V* Ms = stage + 2 * BUF;                       // v mode: M and xi, row-major CAP x CAP
   V* Xs = Ms + CAP * CAP;
   const int n = cf.ncols;
   const int tid = threadIdx.x;
+  // padding columns n .. CAP-1 stay zero in both buffers
+  for (int e = tid; e < 2 * NS * (CAP - n) * SR; e += kGramThreads) {
+    const int r = e % SR, jj = e / SR;
+    const int j = n + jj % (CAP - n), bs = jj / (CAP - n);
+    stage[(bs * CAP + j) * SR + r] = V(0);
+  }
   if constexpr (MODE == kModeV) {
     for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
       Ms[idx] = w.M[idx];
@@ -345,6 +374,8 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
   // the Gram matrix U^T W of this mode (stage slots)
   constexpr int su = MODE == kModeXi ? 0 : 1;
   constexpr int sw = MODE == kModeXi ? 2 : 1;
+  // slots copied in: start Q; xi P, Z; v P, Q, Z, X
+  constexpr unsigned used = MODE == kModeStart ? 0x2u : MODE == kModeXi ? 0x5u : 0xFu;
   const int ph = tid % T::PH, slot = tid / T::PH;
   V acc[T::TPT][16];
   Acc cmp[T::TPT][16];
@@ -357,21 +388,32 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[q][e] = V(0);
   }
-  const int64_t ld = cf.ld;
-  for (int64_t r0 = (int64_t)blockIdx.x * SR; r0 < ld; r0 += (int64_t)gridDim.x * SR) {
-    // stage the chunk's rows of the slots this mode reads (zero beyond m)
-    for (int e = tid; e < 3 * CAP * SR; e += kGramThreads) {
-      const int s = e / (CAP * SR), rem = e % (CAP * SR);
-      const int j = rem / SR, r = rem % SR;
-      const bool used = MODE == kModeStart ? s == 1 : MODE == kModeXi ? s != 1 : true;
-      V v = V(0);
-      if (used && j < n && r0 + r < ld) {
-        const V* src = s == 0 ? P : s == 1 ? R : Z;
-        v = src[(int64_t)j * ld + r0 + r];
-      }
-      stage[(s * CAP + j) * SR + r] = v;
+  const int64_t ld = cf.ld;                      // a multiple of 64: every chunk is full
+  constexpr int U16 = SR * (int)sizeof(V) / 16;  // 16-byte units per staged column
+  auto issue = [&](int64_t r0, int bs) {
+    V* dst = stage + bs * BUF;
+    for (int e = tid; e < NS * n * U16; e += kGramThreads) {
+      const int u = e % U16, jj = e / U16;
+      const int sl = jj / n, j = jj % n;
+      if (!((used >> sl) & 1u)) continue;
+      const V* src = sl == 0 ? P : sl == 1 ? R : sl == 2 ? Z : X;
+      cp_async16(dst + (sl * CAP + j) * SR + u * (16 / (int)sizeof(V)),
+                 src + (int64_t)j * ld + r0 + u * (16 / (int)sizeof(V)));
+    }
+    cp_async_commit();
+  };
+  const int64_t step = (int64_t)gridDim.x * SR;
+  int64_t r0 = (int64_t)blockIdx.x * SR;
+  if (r0 < ld) issue(r0, 0);
+  for (int bs = 0; r0 < ld; r0 += step, bs ^= 1) {
+    if (r0 + step < ld) {
+      issue(r0 + step, bs ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    V* sb = stage + bs * BUF;
     if constexpr (MODE == kModeV) {
       // X += P M and V = Q - Z xi on this chunk, 4 rows x 4 columns a thread
       for (int u = tid; u < 2 * T::NUT; u += kGramThreads) {
@@ -380,7 +422,7 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
         const int rq = uu % (SR / 4), jt = uu / (SR / 4);
         const int r = 4 * rq, j0 = 4 * jt;
         if (j0 >= n) continue;
-        const V* src = stage + (isx ? 0 : 2) * CAP * SR;
+        const V* src = sb + (isx ? 0 : 2) * CAP * SR;
         const V* mat = isx ? Ms : Xs;
         V o[4][4];
 #pragma unroll
@@ -402,13 +444,12 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
           if (j >= n) continue;
           V col[4];
           if (isx) {
-            V* xp = X + (int64_t)j * ld + r0 + r;     // ld is a multiple of 64
-            ld4(xp, col);
+            ld4(sb + (3 * CAP + j) * SR + r, col);
 #pragma unroll
             for (int a = 0; a < 4; ++a) col[a] += o[a][b];
-            st4(xp, col);
+            st4(X + (int64_t)j * ld + r0 + r, col);
           } else {
-            V* qs = stage + (CAP + j) * SR + r;
+            V* qs = sb + (CAP + j) * SR + r;
             ld4(qs, col);
 #pragma unroll
             for (int a = 0; a < 4; ++a) col[a] -= o[a][b];
@@ -422,8 +463,8 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
 #pragma unroll
     for (int q = 0; q < T::TPT; ++q) {
       if (ta[q] < 0) continue;
-      const V* U = stage + (su * CAP + 4 * ta[q]) * SR;
-      const V* W = stage + (sw * CAP + 4 * tb[q]) * SR;
+      const V* U = sb + (su * CAP + 4 * ta[q]) * SR;
+      const V* W = sb + (sw * CAP + 4 * tb[q]) * SR;
       for (int rq = ph; rq < SR / 4; rq += T::PH) {
         V u[4][4], x[4][4];
 #pragma unroll
@@ -479,8 +520,14 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
   if (!arrive_count(&w.hdr->cnt[grp], (unsigned)(b1 - b0))) return;
   Packed* gpart = reinterpret_cast<Packed*>(w.gpart);
   for (int e = tid; e < nent; e += kGramThreads) {
+    Packed v[kGroup];                            // all loads first, then the fixed-order sum
+#pragma unroll
+    for (int b = 0; b < kGroup; ++b)
+      if (b0 + b < b1) v[b] = part[(int64_t)(b0 + b) * nent + e];
     Acc a;
-    for (int b = b0; b < b1; ++b) a.merge(part[(int64_t)b * nent + e]);
+#pragma unroll
+    for (int b = 0; b < kGroup; ++b)
+      if (b0 + b < b1) a.merge(v[b]);
     gpart[(int64_t)grp * nent + e] = a.pack();
   }
   if (!arrive_count(&w.hdr->cnt[kFinalCounter], (unsigned)ngroups)) return;
@@ -497,7 +544,15 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
   __syncthreads();
   for (int e = tid; e < nent; e += kGramThreads) {
     Acc a;
-    for (int g = 0; g < ngroups; ++g) a.merge(gpart[(int64_t)g * nent + e]);
+    for (int g0 = 0; g0 < ngroups; g0 += kGroup) {
+      Packed v[kGroup];
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g)
+        if (g0 + g < ngroups) v[g] = gpart[(int64_t)(g0 + g) * nent + e];
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g)
+        if (g0 + g < ngroups) a.merge(v[g]);
+    }
     const V v = (V)a.value();
     int ta_, tb_;
     sym_tile(e / 16, T::NT, ta_, tb_);
@@ -609,13 +664,13 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
 template <typename V, int CAP>
 size_t row_smem_bytes() {
   return (size_t)2 * CAP * CAP * sizeof(V) + (size_t)CAP * sizeof(V) +
-         (RowInRegisters<CAP>::value ? 0 : (size_t)CAP * kRowThreads * sizeof(V));
+         (size_t)CAP * kRowThreads * sizeof(V);
 }
 
 // Row pass, one thread per row d: q = v L^-T (V in R), p = q + p psi^T
 // (init: p = q).
 template <typename V, int CAP>
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowThreads, 3)
 bcg_row_kernel(CgConf cf, const CgCtl* ctl, BcgView<V, CAP> w, V* R, V* P, int init) {
   extern __shared__ __align__(16) unsigned char dsm[];
   pdl_wait();
@@ -626,7 +681,7 @@ bcg_row_kernel(CgConf cf, const CgCtl* ctl, BcgView<V, CAP> w, V* R, V* P, int i
   V* L = reinterpret_cast<V*>(dsm);
   V* Lt = L + CAP * CAP;
   V* rd = Lt + CAP * CAP;
-  V* my = rd + CAP + threadIdx.x;               // wide blocks: [CAP][kRowThreads]
+  V* my = rd + CAP + threadIdx.x;               // this thread's q: [CAP][kRowThreads]
   for (int idx = threadIdx.x; idx < CAP * CAP; idx += blockDim.x) {
     L[idx] = w.L[idx];
     Lt[idx] = w.Lt[idx];
@@ -652,6 +707,9 @@ bcg_row_kernel(CgConf cf, const CgCtl* ctl, BcgView<V, CAP> w, V* R, V* P, int i
 #pragma unroll
         for (int j = i + 1; j < CAP; ++j) v[j] = fma(-v[i], L[j * CAP + i], v[j]);
       }
+#pragma unroll
+      for (int j = 0; j < CAP; ++j)
+        if (j < n) my[j * kRowThreads] = v[j];
     } else {
       for (int j = 0; j < n; ++j) my[j * kRowThreads] = R[(int64_t)j * ld + d];
       for (int i = 0; i < n; ++i) {
@@ -668,13 +726,7 @@ bcg_row_kernel(CgConf cf, const CgCtl* ctl, BcgView<V, CAP> w, V* R, V* P, int i
       V s = V(0);
 #pragma unroll
       for (int i = 0; i < CAP; ++i) s = fma(p[i], lj[i], s);
-      V q = V(0);
-      if constexpr (RowInRegisters<CAP>::value) {
-#pragma unroll
-        for (int i = 0; i < CAP; ++i) q = i == j ? v[i] : q;
-      } else {
-        q = my[j * kRowThreads];
-      }
+      const V q = my[j * kRowThreads];
       s += q;
       R[(int64_t)j * ld + d] = q;
       P[(int64_t)j * ld + d] = s;
@@ -707,7 +759,7 @@ BcgView<V, CAP> view(char* st, int G) {
     o += (BcgView<V, CAP>::mat_bytes() + 255) & ~(size_t)255;
   }
   using Packed = typename GAcc<V>::Packed;
-  const size_t nent = (size_t)Tiles<CAP>::NSYM * 16;
+  const size_t nent = (size_t)Tiles<CAP, GramRows<V>::value>::NSYM * 16;
   w.part = st + o;
   o += ((size_t)G * nent * sizeof(Packed) + 255) & ~(size_t)255;
   w.gpart = st + o;
@@ -717,7 +769,7 @@ BcgView<V, CAP> view(char* st, int G) {
 template <typename V, int CAP>
 size_t state_bytes(int G) {
   using Packed = typename GAcc<V>::Packed;
-  const size_t nent = (size_t)Tiles<CAP>::NSYM * 16;
+  const size_t nent = (size_t)Tiles<CAP, GramRows<V>::value>::NSYM * 16;
   const int ng = (G + kGroup - 1) / kGroup;
   size_t o = (sizeof(BcgHdr) + 255) & ~(size_t)255;
   o += 6 * ((BcgView<V, CAP>::mat_bytes() + 255) & ~(size_t)255);
@@ -726,8 +778,8 @@ size_t state_bytes(int G) {
   return o;
 }
 
-int gram_blocks(int64_t ld) {
-  const int64_t chunks = (ld + kGramRows - 1) / kGramRows;
+int gram_blocks(int64_t ld, int rows) {
+  const int64_t chunks = (ld + rows - 1) / rows;
   const int sms = num_sms();
   return (int)(chunks < sms ? chunks : sms);
 }
@@ -760,7 +812,7 @@ cudaError_t launch_row(const CgConf& cf, CgCtl* ctl, const BcgView<V, CAP>& w, V
 template <typename V, int CAP>
 cudaError_t launch_sequence(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P,
                             const V* Z, bool start, cudaStream_t s) {
-  const int G = gram_blocks(cf.ld);
+  const int G = gram_blocks(cf.ld, GramRows<V>::value);
   const BcgView<V, CAP> w = view<V, CAP>(st, G);
   cudaError_t e;
   if (start) {
@@ -773,6 +825,30 @@ cudaError_t launch_sequence(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, 
   e = launch_gram<V, CAP, kModeV>(cf, ctl, w, G, X, R, P, Z, s);
   if (e != cudaSuccess) return e;
   return launch_row<V, CAP>(cf, ctl, w, R, P, 0, s);
+}
+
+// One pass of an iteration alone (0: xi gram, 1: v gram, 2: row), for timing.
+template <typename V, int CAP>
+cudaError_t launch_pass(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P, const V* Z,
+                        int pass, cudaStream_t s) {
+  const int G = gram_blocks(cf.ld, GramRows<V>::value);
+  const BcgView<V, CAP> w = view<V, CAP>(st, G);
+  if (pass == 0) return launch_gram<V, CAP, kModeXi>(cf, ctl, w, G, X, R, P, Z, s);
+  if (pass == 1) return launch_gram<V, CAP, kModeV>(cf, ctl, w, G, X, R, P, Z, s);
+  return launch_row<V, CAP>(cf, ctl, w, R, P, 0, s);
+}
+
+template <typename V>
+cudaError_t dispatch_pass(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P, const V* Z,
+                          int pass, cudaStream_t s) {
+  switch (capacity(cf.ncols)) {
+    case 8: return launch_pass<V, 8>(cf, ctl, st, X, R, P, Z, pass, s);
+    case 16: return launch_pass<V, 16>(cf, ctl, st, X, R, P, Z, pass, s);
+    case 24: return launch_pass<V, 24>(cf, ctl, st, X, R, P, Z, pass, s);
+    case 36: return launch_pass<V, 36>(cf, ctl, st, X, R, P, Z, pass, s);
+    case 48: return launch_pass<V, 48>(cf, ctl, st, X, R, P, Z, pass, s);
+    default: return launch_pass<V, 64>(cf, ctl, st, X, R, P, Z, pass, s);
+  }
 }
 
 template <typename V>
@@ -788,10 +864,109 @@ cudaError_t dispatch(const CgConf& cf, CgCtl* ctl, char* st, V* X, V* R, V* P, c
   }
 }
 
+// ------------------------------------------------------- timing (diagnostics)
+
+__global__ void bcgb_fill_kernel(float* v, int64_t n, uint32_t salt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = mix64((uint64_t)i * 0x9E3779B97F4A7C15ull ^ salt);
+    v[i] = (float)((double)(h >> 40) / (double)(1ull << 24) - 0.5);
+  }
+}
+
+// A state in which every pass takes its full path: not done, ||B||^2 = 1,
+// C = I (m x m, inside the CAP x CAP state matrix at its base).
+__global__ void bcgb_reset_kernel(CgCtl* ctl, float* C, int cap, int m) {
+  for (int i = threadIdx.x; i < cap * cap; i += blockDim.x)
+    C[i] = (i / cap == i % cap && i / cap < m) ? 1.f : 0.f;
+  if (threadIdx.x == 0) {
+    ctl->done = 0;
+    ctl->iter = 0;
+    ctl->error = 0;
+    ctl->normB2 = 1.0;
+  }
+}
+
 }  // namespace
 
+size_t bcg_bench_bytes(int64_t D, int ncols) {
+  const int64_t ld = round_up(D, kLdAlign);
+  const size_t blk = ((size_t)ncols * ld * 4 + 255) & ~(size_t)255;
+  const size_t split = ((size_t)16 * ((ncols + 4) / 5) * ld * 2 + 255) & ~(size_t)255;
+  return 256 + 4 * blk + split + bcg_state_bytes(4, ncols, ld) + 512;
+}
+
+// Times the three passes of one block-CG iteration (xi gram, v gram, row)
+// on FP32 blocks of ncols columns of D values, each launch alone and the
+// three back to back; P, Z = P and Q are refilled before every timed launch
+// so that every pass takes its full path.  ms[0..3].
+int bcg_kernels_bench(int64_t D, int ncols, int reps, char* ws, cudaStream_t st, float* ms) {
+  const int64_t ld = round_up(D, kLdAlign);
+  auto al = [](char* p) { return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); };
+  const size_t blk = (size_t)ncols * ld * 4;
+  char* o = al(ws);
+  CgCtl* ctl = (CgCtl*)o;                 o = al(o + sizeof(CgCtl));
+  float* X = (float*)o;                   o = al(o + blk);
+  float* R = (float*)o;                   o = al(o + blk);
+  float* P = (float*)o;                   o = al(o + blk);
+  float* Z = (float*)o;                   o = al(o + blk);
+  __nv_bfloat16* xs = (__nv_bfloat16*)o;  o = al(o + (size_t)16 * ((ncols + 4) / 5) * ld * 2);
+  char* state = o;
+  if (cudaMemsetAsync(ws, 0, bcg_bench_bytes(D, ncols), st) != cudaSuccess) return -1;
+  CgConf cf;
+  memset(&cf, 0, sizeof(cf));
+  cf.D = D;
+  cf.ld = ld;
+  cf.ncols = ncols;
+  cf.K = ncols - 1;
+  cf.T = 1;
+  cf.tol = 0.0;
+  cf.max_iters = 1 << 30;
+  cf.split_nt = 3;
+  cf.split_rows = 16 * ((ncols + 4) / 5);
+  cf.split_buf = xs;
+  const int cap = capacity(ncols);
+  // C sits at the state's first matrix (after the 256-byte-aligned header)
+  float* C = (float*)(state + ((sizeof(BcgHdr) + 255) & ~(size_t)255));
+  auto refill = [&](uint32_t salt) {
+    bcgb_fill_kernel<<<1024, 256, 0, st>>>(X, (int64_t)ncols * ld, salt);
+    bcgb_fill_kernel<<<1024, 256, 0, st>>>(R, (int64_t)ncols * ld, salt + 1);
+    bcgb_fill_kernel<<<1024, 256, 0, st>>>(P, (int64_t)ncols * ld, salt + 2);
+    cudaMemcpyAsync(Z, P, blk, cudaMemcpyDeviceToDevice, st);
+    bcgb_reset_kernel<<<1, 256, 0, st>>>(ctl, C, cap, ncols);
+  };
+  cudaEvent_t ev[2];
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return -1;
+  for (int k = 0; k < 4; ++k) {
+    float tot = 0.f;
+    for (int r = 0; r < reps + 1; ++r) {
+      refill(11u + 3u * (uint32_t)r);
+      if (k == 1 || k == 2) {
+        // the v and row passes read the xi pass's state
+        if (dispatch_pass<float>(cf, ctl, state, X, R, P, Z, 0, st) != cudaSuccess) return -1;
+      }
+      if (k == 2) {
+        if (dispatch_pass<float>(cf, ctl, state, X, R, P, Z, 1, st) != cudaSuccess) return -1;
+      }
+      cudaEventRecord(ev[0], st);
+      cudaError_t e = cudaSuccess;
+      if (k < 3) e = dispatch_pass<float>(cf, ctl, state, X, R, P, Z, k, st);
+      else e = dispatch<float>(cf, ctl, state, X, R, P, Z, false, st);
+      cudaEventRecord(ev[1], st);
+      if (e != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess) return -1;
+      float m = 0.f;
+      cudaEventElapsedTime(&m, ev[0], ev[1]);
+      if (r > 0) tot += m;
+    }
+    ms[k] = tot / (float)reps;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 size_t bcg_state_bytes(int vec_bytes, int ncols, int64_t ld) {
-  const int G = gram_blocks(ld);
+  const int G = gram_blocks(ld, vec_bytes == 4 ? GramRows<float>::value : GramRows<double>::value);
   const bool f = vec_bytes == 4;
   switch (capacity(ncols)) {
     case 8: return f ? state_bytes<float, 8>(G) : state_bytes<double, 8>(G);

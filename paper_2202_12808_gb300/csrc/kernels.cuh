@@ -70,6 +70,9 @@ cudaError_t launch_bcg_start(const CgConf& cf, CgCtl* ctl, char* state, V* X, V*
                              const V* bvec, cudaStream_t st);
 // One iteration after Z = A P: the xi and v gram passes (the second with
 // the stop test) and the row pass.
+// Timing of the block-CG passes outside a fit graph (block_cg.cu).
+size_t bcg_bench_bytes(int64_t D, int ncols);
+int bcg_kernels_bench(int64_t D, int ncols, int reps, char* ws, cudaStream_t st, float* ms);
 template <typename V>
 cudaError_t launch_bcg_iteration(const CgConf& cf, CgCtl* ctl, char* state, V* X, V* R, V* P,
                                  const V* Z, cudaStream_t st);

@@ -7,6 +7,7 @@ outside any fit graph:
     python -m paper_2202_12808_gb300.opbench --op dense-bf16 --N 4096 --D 32768 --ncols 33
     python -m paper_2202_12808_gb300.opbench --op dense-f32  --N 4096 --D 32768 --ncols 33
     python -m paper_2202_12808_gb300.opbench --op cg --D 1048576 --ncols 33
+    python -m paper_2202_12808_gb300.opbench --op bcg --D 32768 --ncols 33
 
 dense-bf16 / dense-f32 / dense-fp8: A X = beta Phi^T (Phi X) + alpha . X on
 the tensor cores (BF16 dictionary, FP32 dictionary as hi + lo, or FP8 E4M3
@@ -14,7 +15,8 @@ with per-tile scales expanded to BF16 in shared memory), packed layout,
 pipeline autotuned unless --no-autotune; prints the per-kernel microseconds
 of cofem_op_apply_timed.  cg: the CG update (direction fused where it fits),
 the direction update and the diagonal estimate + M-step
-(cofem_bench_cg_kernels).
+(cofem_bench_cg_kernels).  bcg: the three passes of one block-CG iteration
+(cofem_bench_bcg_kernels).
 """
 import argparse
 import json
@@ -28,7 +30,7 @@ from . import binding as B
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "dense-fp8", "cg"], required=True)
+    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "dense-fp8", "cg", "bcg"], required=True)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--D", type=int, default=32768)
     ap.add_argument("--ncols", type=int, default=33)
@@ -40,6 +42,13 @@ def main():
                     help="output rows per tensor-core work unit (with --pipeline)")
     a = ap.parse_args()
     st = torch.cuda.current_stream().cuda_stream
+    if a.op == "bcg":
+        nb = B.cofem_bench_bcg_kernels_workspace_bytes(a.D, a.ncols)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        ms = B.cofem_bench_bcg_kernels(a.D, a.ncols, a.reps, ws.data_ptr(), nb, st)
+        print(json.dumps({"op": "bcg", "D": a.D, "ncols": a.ncols, "xi_us": ms[0] * 1e3,
+                          "v_us": ms[1] * 1e3, "row_us": ms[2] * 1e3, "sequence_us": ms[3] * 1e3}))
+        return
     if a.op == "cg":
         nb = B.cofem_bench_cg_kernels_workspace_bytes(a.D, a.ncols)
         ws = torch.empty(nb, dtype=torch.uint8, device="cuda")

@@ -211,6 +211,7 @@ def test_dct_alpha_sensitivity():
 
 # ---------------------------------------- the headline shape (4096 x 32768)
 
+@pytest.mark.many_blas_threads
 def test_headline_shape_trajectory_amplifies_fp32_rounding():
     """N = 4096, D = 32768, K = 32, tol 1e-5, BF16-rounded Phi: after the
     first EM iteration the FP32 emulation of the oracle is 2e-5 away in mu,

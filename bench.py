@@ -1041,12 +1041,79 @@ def op_roofline(B, op, ncols, beta, dev, peak, phi_bytes, label):
             "kernel": label}
 
 
+def learned_fit_section(api, B, prob, op16, y, kw, em, dev, ref, t32):
+    """The headline fit with the learned warm start and preconditioner on
+    the BF16 dictionary (the benchmark spec's learned + mixed-precision form on
+    one large problem): the network is trained on the GPU by the library's
+    own kernels on the learned workload's N = 256, D = 1024 problems (seeds
+    1..64, outside the timing; its time is reported), then one timed
+    100-EM-iteration fit.  A learned fit cannot be resumed EM iteration by
+    EM iteration (the first E-step of any fit is plain CG), so mu after EM
+    iteration k comes from a separate fit of k EM iterations (the same
+    iterations: the fit is deterministic): every 10 EM iterations, refined
+    iteration by iteration to the first that reaches 2 % NRMSE."""
+    import torch
+    net, U, losses, t_collect, t_train = train_network(api, B)
+    p = api.params(em_iters=em, **kw)
+    p.mlp = net.bf16.data_ptr()
+    ws = api.workspace(op16, p, dev)
+    q1 = api.params(em_iters=1, **kw)
+    q1.mlp = net.bf16.data_ptr()
+    api.fit(op16, y, prob.beta, q1, ws=ws)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    r = api.fit(op16, y, prob.beta, p, ws=ws)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    fallbacks = int(B.lib().cofem_last_fit_fallbacks())
+    z = prob.z
+
+    def nrmse_after(k):
+        qk = api.params(em_iters=k, **kw)
+        qk.mlp = net.bf16.data_ptr()
+        rk = api.fit(op16, y, prob.beta, qk, ws=ws)
+        mu = rk.mu.cpu().numpy()
+        return float(np.linalg.norm(mu - z) / np.linalg.norm(z))
+
+    marks = {k: nrmse_after(k) for k in range(10, em + 1, 10)}
+    first = next((k for k in sorted(marks) if marks[k] <= 0.02), None)
+    t2 = None
+    if first is not None:
+        k = first
+        while k > 1 and nrmse_after(k - 1) <= 0.02:
+            k -= 1
+        t2 = {"em_iters": k, "seconds": r.stats["end_ns"][k - 1] / 1e9}
+    ent = {"em_iters_per_s": em / sec, "seconds": sec,
+           "cg_iters_total": int(sum(r.stats["cg_iters"])),
+           "cg_iters_per_em": r.stats["cg_iters"], "fallbacks": fallbacks,
+           "max_relres": max(r.stats["relres"]),
+           "support_counts": r.stats["support"][::10],
+           "nrmse_mu_vs_truth": {"final": float(np.linalg.norm(r.mu.cpu().numpy() - z) /
+                                                np.linalg.norm(z)),
+                                 "every_10": [marks[k] for k in sorted(marks)]},
+           "time_to_2pct_nrmse": t2,
+           "network": {"samples": int(U.shape[0]), "loss_first": float(losses[0]),
+                       "loss_last": float(losses[-1]), "collect_s": t_collect,
+                       "train_s": t_train, "trained_on": "N=256 D=1024 seeds 1-64, E-steps 2-20"}}
+    if ref is not None:
+        eq, dev_, bord = compare_to_reference(r.alpha.cpu().numpy(), ref, op16.D)
+        ent["vs_oracle_bf16"] = {"final": {"support_equal": eq, "alpha_max_rel": dev_,
+                                           "borderline": bord}}
+    ent["ratio_em_iters_per_s_vs_fp32"] = None
+    ent["ratio_time_to_2pct_nrmse_vs_fp32"] = (t32["seconds"] / t2["seconds"]) if t2 and t32 else None
+    return ent
+
+
 def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
     """The whole 100-EM-iteration fit of the headline workload, three times:
     the BF16 dictionary (the bench's operator), the plain FP32 comparator
     (the FP32 dictionary on the tensor cores, Phi = hi + lo) and the FP8 E4M3
-    dictionary with per-tile scales; and the BF16 fit once more with block CG
-    (the solver variant, no residual replacement).  For each: EM iterations
+    dictionary with per-tile scales; the BF16 fit once more with block CG
+    (the solver variant, no residual replacement), and once with the learned
+    warm start and preconditioner (learned_fit_section).  For each: EM iterations
     per second of
     the whole fit, the time to 2 % NRMSE (Sec. 4.2's criterion) and time to
     tolerance -- the device time until the support equals the FP64 oracle's
@@ -1112,6 +1179,11 @@ def fit_100_section(api, B, prob, op16, y, kw, dev, peak):
 
     t8 = out["fp8"]["time_to_2pct_nrmse"]
     out["ratio_time_to_2pct_nrmse_fp8"] = (t32["seconds"] / t8["seconds"]) if t8 and t32 else None
+    # the learned warm start on the BF16 dictionary
+    out["bf16_learned"] = learned_fit_section(api, B, prob, op16, y, kw, em, dev,
+                                              load_reference_fit("bf16"), t32)
+    out["bf16_learned"]["ratio_em_iters_per_s_vs_fp32"] = (
+        out["bf16_learned"]["em_iters_per_s"] / out["fp32"]["em_iters_per_s"])
     # the FP32 and FP8 operators' kernels, timed with CUDA events on the stream
     # (entry bytes: 4 for hi + lo, 1 plus one FP32 scale per 128 x 128 tile)
     sc_bytes = 4 * ((N + 127) // 128) * ((D + 127) // 128)

@@ -870,8 +870,11 @@ def run_dct_sweep(args):
     time to 2 % NRMSE on the masked DCT dictionary for D = 2^12 .. 2^18,
     N = D / 4 kept samples, d = 0.1 D N(0,1) coefficients, K = 20, U = 400
     (sigma 0.005 as in the paper's dense experiments and CG tol 1e-5: not
-    stated for this experiment), at most 80 EM iterations.  The smallest
-    size is checked against the FP64 oracle (final NRMSE and mu)."""
+    stated for this experiment), at most 80 EM iterations.  Where U = 400
+    truncates the E-step solves so that 2 % is never reached (D = 2^18:
+    reading R26), the same fit also runs with U = 1000, and the headline
+    figure of the line is that fit's.  The smallest size is checked against
+    the FP64 oracle (final NRMSE and mu)."""
     import torch
     from oracle import sbl
     from paper_2202_12808_gb300 import api
@@ -888,7 +891,19 @@ def run_dct_sweep(args):
         out[D] = {"time_to_2pct_nrmse": time_to_nrmse(nrmse, stats["end_ns"]),
                   "nrmse_final_pct": 100 * nrmse[-1], "nrmse_pct_every_10": [
                       round(100 * v, 3) for v in nrmse[9::10]], "seconds_all_em": sec,
-                  "cg_iters_total": int(sum(stats["cg_iters"]))}
+                  "cg_iters_total": int(sum(stats["cg_iters"])),
+                  "e_steps_at_cap": int(sum(1 for v in stats["cg_iters"] if v >= 400))}
+        if out[D]["time_to_2pct_nrmse"] is None:
+            # the cap U = 400 truncates the E-step solves here (reading R26):
+            # the same fit with U = 1000
+            kw2 = dict(kw, cg_max_iters=1000)
+            sec2, st2, h2, nr2 = whole_fit(api, B, op, y, pr.beta, kw2, em, "cuda", z=pr.z)
+            out[D]["with_U_1000"] = {
+                "time_to_2pct_nrmse": time_to_nrmse(nr2, st2["end_ns"]),
+                "nrmse_final_pct": 100 * nr2[-1],
+                "nrmse_pct_every_10": [round(100 * v, 3) for v in nr2[9::10]],
+                "seconds_all_em": sec2, "cg_iters_total": int(sum(st2["cg_iters"])),
+                "e_steps_at_cap": int(sum(1 for v in st2["cg_iters"] if v >= 1000))}
         if p == 12:
             ra, rmu, rs, rst = sbl.cofem_dct(pr.idx, D, pr.y.astype(np.float32).astype(np.float64),
                                              pr.beta, 20, em, 1e-5, 400, seed=0)
@@ -896,11 +911,13 @@ def run_dct_sweep(args):
             oracle = {"case": "D=4096", "nrmse_final_gpu_pct": 100 * nrmse[-1],
                       "nrmse_final_oracle_pct": 100 * _nrmse(rmu, pr.z),
                       "mu_rel_l2_vs_oracle": float(np.linalg.norm(mu - rmu) / np.linalg.norm(rmu))}
-    big = out[1 << 18]["time_to_2pct_nrmse"]
+    big = out[1 << 18]["time_to_2pct_nrmse"] or out[1 << 18].get("with_U_1000", {}).get(
+        "time_to_2pct_nrmse")
     _common(args, "seconds to 2 % NRMSE, masked DCT (Sec. 4.2, D=2^12..2^18, d=0.1D)",
             "seconds to 2% NRMSE at D=2^18", big["seconds"] if big else None,
             (big["seconds"] if big else 0.0) * args.steps, "f32",
-            {"workload": "dct-sweep", "N": "D/4", "d": "0.1 D", "K": 20, "U": 400,
+            {"workload": "dct-sweep", "N": "D/4", "d": "0.1 D", "K": 20,
+             "U": "400 (1000 where 400 never reaches 2 %)",
              "cg_tol": 1e-5, "sigma": 0.005, "em_iters_max": em},
             {"higher_is_better": False, "by_D": out, "oracle_check": oracle})
 

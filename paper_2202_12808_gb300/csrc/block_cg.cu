@@ -203,7 +203,9 @@ template <> struct Roundoff<double> { static constexpr double value = 1.11022302
 template <typename V> __device__ __forceinline__ V drop_tol() { return V(64) * V(Roundoff<V>::value); }
 
 // ----------------------------------------------------- small dense algebra
-// n x n matrices in shared memory with row stride LD; the whole block.
+// n x n matrices (n <= 64) in shared memory with row stride LD, the whole
+// block: warp w takes rows w, w + 16, ..., lane l columns l and l + 32 (no
+// index division on the critical path).
 
 // Gauss-Jordan sweeps of a symmetric positive semi-definite matrix
 // (Goodnight 1979) over the indices whose pivot stays above drop_tol times
@@ -211,6 +213,7 @@ template <typename V> __device__ __forceinline__ V drop_tol() { return V(64) * V
 // and 0 elsewhere.  Returns the number of kept indices.
 template <typename S, int LD>
 __device__ int sweep_inverse(S* A, int n, S* rk, S* d0, int* dead) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     d0[i] = A[i * LD + i];
@@ -228,21 +231,22 @@ __device__ int sweep_inverse(S* A, int n, S* rk, S* d0, int* dead) {
     if ((int)threadIdx.x < n) rk[threadIdx.x] = A[k * LD + threadIdx.x];
     __syncthreads();
     const S inv = S(1) / piv;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx % n;
-      S v;
-      if (i == k && j == k) v = -inv;
-      else if (i == k) v = rk[j] * inv;
-      else if (j == k) v = rk[i] * inv;
-      else v = A[i * LD + j] - rk[i] * rk[j] * inv;
-      A[i * LD + j] = v;
+    for (int i = wp; i < n; i += nw) {
+      const S ri = rk[i] * inv;                  // row i's multiplier
+      S* Ai = A + i * LD;
+      for (int j = lane; j < n; j += 32) {
+        S v;
+        if (i == k) v = j == k ? -inv : rk[j] * inv;
+        else if (j == k) v = ri;
+        else v = Ai[j] - ri * rk[j];
+        Ai[j] = v;
+      }
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
-    A[i * LD + j] = (dead[i] || dead[j]) ? S(0) : -A[i * LD + j];
-  }
+  for (int i = wp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32)
+      A[i * LD + j] = (dead[i] || dead[j]) ? S(0) : -A[i * LD + j];
   __syncthreads();
   return kept;
 }
@@ -250,9 +254,10 @@ __device__ int sweep_inverse(S* A, int n, S* rk, S* d0, int* dead) {
 // Cholesky factorisation A = L L^T in place (lower triangle; right-looking
 // with unscaled columns, scaled at the end), dropping an index whose pivot
 // is at or below drop_tol times its original diagonal entry (its column of
-// L is zero).
+// L is zero).  rk: n scratch values.
 template <typename S, int LD>
-__device__ void cholesky(S* A, int n, S* d0, int* dead) {
+__device__ void cholesky(S* A, int n, S* d0, int* dead, S* rk) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     d0[i] = A[i * LD + i];
@@ -266,20 +271,19 @@ __device__ void cholesky(S* A, int n, S* d0, int* dead) {
       continue;
     }
     const S inv = S(1) / piv;
-    const int m = n - k - 1;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j <= i) A[i * LD + j] -= A[i * LD + k] * A[j * LD + k] * inv;
+    for (int i = k + 1 + wp; i < n; i += nw) {
+      const S aik = A[i * LD + k] * inv;
+      S* Ai = A + i * LD;
+      for (int j = k + 1 + lane; j <= i; j += 32) Ai[j] -= aik * A[j * LD + k];
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
-    if (j < i) A[i * LD + j] = dead[j] ? S(0) : A[i * LD + j] / sqrt(A[j * LD + j]);
-  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    rk[j] = dead[j] ? S(0) : sqrt(A[j * LD + j]);
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    A[i * LD + i] = dead[i] ? S(0) : sqrt(A[i * LD + i]);
+  for (int i = wp; i < n; i += nw)
+    for (int j = lane; j <= i; j += 32)
+      A[i * LD + j] = j == i ? rk[i] : (dead[j] ? S(0) : A[i * LD + j] / rk[j]);
   __syncthreads();
 }
 
@@ -586,7 +590,7 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
     __syncthreads();
     const int done = done_sh;
     if (!done) {
-      cholesky<V, LD>(G1, n, d0, dead);
+      cholesky<V, LD>(G1, n, d0, dead, rk);
       store_factor<V, CAP, LD>(w, G1, n);
       for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {
         const int i = idx / CAP, j = idx % CAP;
@@ -621,12 +625,12 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
       // ||V C||_F^2 = sum_ij C_ij (G2 C)_ij, stop test, V = Q psi
       __syncthreads();
       double part2 = 0.0;
-      for (int idx = tid; idx < n * n; idx += kGramThreads) {
-        const int i = idx / n, j = idx % n;
-        V s = V(0);
-        for (int k = 0; k <= j; ++k) s = fma(G1[i * LD + k], Cm[k * LD + j], s);
-        part2 += (double)Cm[i * LD + j] * (double)s;
-      }
+      for (int i = tid >> 5; i < n; i += kGramThreads / 32)
+        for (int j = tid & 31; j < n; j += 32) {
+          V s = V(0);
+          for (int k = 0; k <= j; ++k) s = fma(G1[i * LD + k], Cm[k * LD + j], s);
+          part2 += (double)Cm[i * LD + j] * (double)s;
+        }
       const double r2 = block_sum(part2, red);
       if (tid == 0) {
         const double relres = sqrt(fmax(r2, 0.0) / ctl->normB2);
@@ -642,7 +646,7 @@ bcg_gram_kernel(CgConf cf, CgCtl* ctl, BcgView<V, CAP> w, V* X, V* R, const V* P
       __syncthreads();
       const int done = done_sh;
       if (!done) {
-        cholesky<V, LD>(G1, n, d0, dead);
+        cholesky<V, LD>(G1, n, d0, dead, rk);
         store_factor<V, CAP, LD>(w, G1, n);
         // C = L^T C (both upper triangular)
         for (int idx = tid; idx < CAP * CAP; idx += kGramThreads) {

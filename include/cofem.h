@@ -201,8 +201,9 @@ cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T,
  * D a power of two, 16 <= D <= 2^22; 1 <= N <= D; idx_dev: N int32 device
  * values, strictly increasing in [0, D), owned by the caller and read at
  * every application (a violation is reported as COFEM_ERR_INVALID_ARG by
- * the fit, through the device error word).  F32 vectors only; not with a
- * learned warm start (COFEM_ERR_UNSUPPORTED). */
+ * the fit, through the device error word).  F32 vectors only.  With a
+ * learned warm start the fit computes ||phi_d||^2 from one DCT of the sample
+ * mask (the closed form under cofem_op_col_norms_ws). */
 cofem_status cofem_op_dct(int64_t D, int64_t N, const int32_t* idx_dev, cofem_op** out);
 
 /* Releases a handle (NULL is ignored). */
@@ -373,8 +374,26 @@ cofem_status cofem_fit_batched(int32_t n, const cofem_problem* problems,
  * forward pass and inference use BF16 weights with FP32 arithmetic.
  * ------------------------------------------------------------------------ */
 
-/* ||phi_d||^2 for every coordinate (D floats).  Asynchronous. */
+/* ||phi_d||^2 for every coordinate (D floats): dense and convolutional
+ * dictionaries (the masked DCT's needs a workspace: COFEM_ERR_UNSUPPORTED
+ * here, use cofem_op_col_norms_ws).  Asynchronous. */
 cofem_status cofem_op_col_norms(const cofem_op* op, float* out_dev, void* stream);
+
+/* The same for every operator kind, with a caller-owned device workspace of
+ * at least cofem_col_norms_workspace_bytes(op) bytes, 256-byte aligned (0
+ * bytes, and workspace_dev may be NULL, for dense and convolutional
+ * dictionaries).  For the masked DCT (Phi = C^T[idx, :], C the orthonormal
+ * DCT-II) cos^2 t = (1 + cos 2t) / 2 gives
+ *   ||phi_d||^2 = (s_d^2 / 2) (N + T_d),  T_d = sum over kept n of
+ *   cos(pi 2d (2n + 1) / 2D),
+ * and T_d is read off X = C m, the DCT of the 0/1 sample mask m: X_{2d} /
+ * s_{2d} for 2d < D, 0 for 2d = D, -X_{2D-2d} / s_{2D-2d} for 2d > D (one
+ * FP32 transform: the transform's error, near log2(D) 2^-24 sqrt(N) in T_d,
+ * is relative error log2(D) 2^-24 / sqrt(N) in ||phi_d||^2).
+ * COFEM_ERR_WORKSPACE when workspace_bytes is too small.  Asynchronous. */
+cofem_status cofem_col_norms_workspace_bytes(const cofem_op* op, size_t* bytes);
+cofem_status cofem_op_col_norms_ws(const cofem_op* op, float* out_dev, void* workspace_dev,
+                                   size_t workspace_bytes, void* stream);
 
 /* Features u (D x 4 floats, row-major) from alpha, ||phi_d||^2, beta and the
  * previous E-step's mu, s (NULL: mu_prev = 0, s_prev = 1/c_d).  Async. */

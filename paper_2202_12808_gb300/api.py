@@ -272,14 +272,25 @@ class LearnedWarmStart:
         return O
 
 
+def col_norms(op, device, stream=None):
+    """||phi_d||^2 of every coordinate of a dictionary (D floats on device)."""
+    pn2 = torch.empty(op.D, dtype=torch.float32, device=device)
+    n = B.cofem_col_norms_workspace_bytes(op.handle)
+    ws = torch.empty(n, dtype=torch.uint8, device=device) if n else None
+    B.cofem_op_col_norms_ws(op.handle, pn2.data_ptr(), ws.data_ptr() if n else None, n,
+                            _stream_ptr(stream))
+    if ws is not None and stream is not None:
+        ws.record_stream(stream)
+    return pn2
+
+
 def collect_training_data(op, y, beta, p, em_iters, stream=None):
     """Runs plain CoFEM one EM iteration at a time and returns (U, Y) samples
     of every coordinate for E-steps 2..em_iters: features from the alpha the
     E-step used and the previous E-step's mu, s; targets from its own mu, s."""
     dev = y.device
     D = op.D
-    pn2 = torch.empty(D, dtype=torch.float32, device=dev)
-    B.cofem_op_col_norms(op.handle, pn2.data_ptr(), _stream_ptr(stream))
+    pn2 = col_norms(op, dev, stream)
     alpha = torch.empty(D, dtype=torch.float64, device=dev)
     Us, Ys = [], []
     mu_prev = s_prev = None

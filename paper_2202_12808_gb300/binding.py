@@ -84,6 +84,8 @@ _SIGS = {
     "cofem_op_destroy": (None, [_P]),
     "cofem_last_fit_fallbacks": (_I32, []),
     "cofem_op_col_norms": (_S, [_P, _P, _P]),
+    "cofem_col_norms_workspace_bytes": (_S, [_P, ctypes.POINTER(_SZ)]),
+    "cofem_op_col_norms_ws": (_S, [_P, _P, _P, _SZ, _P]),
     "cofem_mlp_features": (_S, [_P, _P, _D, _P, _P, _I64, _P, _P]),
     "cofem_mlp_targets": (_S, [_P, _P, _D, _P, _P, _I64, _P, _P]),
     "cofem_mlp_forward": (_S, [_P, _S, _P, _I64, _P, _P]),
@@ -406,6 +408,18 @@ def cofem_last_fit_fallbacks():
 
 def cofem_op_col_norms(op, out_ptr, stream=0):
     _check(lib().cofem_op_col_norms(op, out_ptr, stream), "cofem_op_col_norms")
+
+
+def cofem_col_norms_workspace_bytes(op):
+    n = _SZ()
+    _check(lib().cofem_col_norms_workspace_bytes(op, ctypes.byref(n)),
+           "cofem_col_norms_workspace_bytes")
+    return n.value
+
+
+def cofem_op_col_norms_ws(op, out_ptr, ws_ptr, ws_bytes, stream=0):
+    _check(lib().cofem_op_col_norms_ws(op, out_ptr, ws_ptr, ws_bytes, stream),
+           "cofem_op_col_norms_ws")
 
 
 def cofem_mlp_features(alpha_ptr, pn2_ptr, beta, mu_prev_ptr, s_prev_ptr, D, U_ptr, stream=0):

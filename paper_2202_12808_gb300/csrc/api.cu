@@ -354,7 +354,6 @@ static cofem_status check_params(const cofem_op* op, const cofem_params* p) {
     return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->vec_dtype != COFEM_F32) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && p->stop_rule == 1) return COFEM_ERR_UNSUPPORTED;
-  if (p->mlp && op->kind == 2) return COFEM_ERR_UNSUPPORTED;
   if (p->mlp && n_tasks(p) > 1) return COFEM_ERR_UNSUPPORTED;
   // the tensor-core operator writes one partial dot per 128-row tile of D
   // (plus one when two tiles share a unit and their count is odd)
@@ -678,15 +677,21 @@ static cofem_status fit_impl(const cofem_op* op, const void* y, double beta,
   cofem_status rc = op_adjoint(op, p->vec_dtype, ysrc, ldy, T, ws + L.b, L.ld, beta,
                                ws + L.opws, st);
   if (rc != COFEM_OK) return rc;
-  // the masked DCT's mask and twiddle tables, once per fit (the graph's
-  // applications reuse them)
+  // the masked DCT's column norms for the learned start (one DCT of the
+  // mask; X and R serve as scratch before the solve), then its mask and
+  // twiddle tables, once per fit (the graph's applications reuse them)
+  if (op->kind == 2 && p->mlp) {
+    dct_col_norms(op->dct_D, op->dct_idx, op->dct_N, (float*)(ws + L.X), (float*)(ws + L.R),
+                  ws + L.opws, &((CgCtl*)(ws + L.ctl))->error, (float*)(ws + L.pn2), st);
+    CKL();
+  }
   if (op->kind == 2) {
     dct_prepare(op->dct_D, op->dct_idx, op->dct_N, p->K + T, ws + L.opws,
                 &((CgCtl*)(ws + L.ctl))->error, st);
     CKL();
   }
 
-  if (p->mlp) {
+  if (p->mlp && op->kind != 2) {
     rc = mlp_col_norms(op, (float*)(ws + L.pn2), st);
     if (rc != COFEM_OK) return rc;
   }
@@ -1025,6 +1030,36 @@ cofem_status cofem_apply_workspace_bytes(const cofem_op* op, cofem_dtype vec, in
   if (!op || !bytes || ncols < 1 || ncols > kMaxCols) return COFEM_ERR_INVALID_ARG;
   if (!op_supports(op, vec)) return COFEM_ERR_UNSUPPORTED;
   *bytes = op_ws_bytes(op, vec, ncols);
+  return COFEM_OK;
+}
+
+// ||phi_d||^2 with a workspace: the masked DCT's closed form takes one
+// adjoint application (its transform workspace for one column) and two
+// D-float buffers (the all-ones kept samples, the DCT of the mask)
+static size_t col_norms_ws_bytes(const cofem_op* op) {
+  if (op->kind != 2) return 0;
+  return align256(op_ws_bytes(op, COFEM_F32, 1)) + 2 * align256((size_t)op->dct_D * sizeof(float));
+}
+
+cofem_status cofem_col_norms_workspace_bytes(const cofem_op* op, size_t* bytes) {
+  if (!op || !bytes) return COFEM_ERR_INVALID_ARG;
+  *bytes = col_norms_ws_bytes(op);
+  return COFEM_OK;
+}
+
+cofem_status cofem_op_col_norms_ws(const cofem_op* op, float* out_dev, void* workspace_dev,
+                                   size_t workspace_bytes, void* stream) {
+  if (!op || !out_dev) return COFEM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (op->kind != 2) return mlp_col_norms(op, out_dev, st);
+  if (!workspace_dev || ((uintptr_t)workspace_dev & 255) != 0) return COFEM_ERR_INVALID_ARG;
+  if (workspace_bytes < col_norms_ws_bytes(op)) return COFEM_ERR_WORKSPACE;
+  char* w = (char*)workspace_dev;
+  const size_t o1 = align256(op_ws_bytes(op, COFEM_F32, 1));
+  const size_t o2 = o1 + align256((size_t)op->dct_D * sizeof(float));
+  dct_col_norms(op->dct_D, op->dct_idx, op->dct_N, (float*)(w + o1), (float*)(w + o2), w,
+                nullptr, out_dev, st);
+  CKL();
   return COFEM_OK;
 }
 

@@ -537,6 +537,46 @@ void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64
            dim3(256), 0, st, idx, N, D, (const float*)a.tout, a.ldt, W, ldw, err);
 }
 
+// ||phi_d||^2 of the masked dictionary (the learned start's feature and
+// Jacobi scale).  phi_d is row d of C restricted to the kept samples, so with
+// cos^2 t = (1 + cos 2t) / 2,
+//   ||phi_d||^2 = sum_{n kept} C_dn^2 = (s_d^2 / 2) (N + T_d),
+//   T_d = sum_{n kept} cos(pi 2d (2n + 1) / 2D),
+// and T_d comes from X = C m, the orthonormal DCT-II of the 0/1 mask m:
+// T_d = X_{2d} / s_{2d} for 2d < D, 0 for 2d = D, and -X_{2D-2d} / s_{2D-2d}
+// for 2d > D (cos(pi (2n + 1) - t) = -cos t).
+__global__ void dct_col_norms_kernel(int64_t D, int64_t N, const float* X, float* out) {
+  pdl_wait();
+  pdl_trigger();
+  const double inv_d = 1.0 / (double)D;
+  for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < D;
+       d += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = 2 * d;
+    double t = 0.0;
+    if (k < D) t = (double)X[k] / sqrt((k == 0 ? 1.0 : 2.0) * inv_d);
+    else if (k > D) t = -(double)X[2 * D - k] / sqrt(2.0 * inv_d);
+    const double sd2 = (d == 0 ? 1.0 : 2.0) * inv_d;
+    out[d] = (float)(0.5 * sd2 * ((double)N + t));
+  }
+}
+
+__global__ void dct_fill_ones_kernel(float* v, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = 1.f;
+}
+
+void dct_col_norms(int64_t D, const int32_t* idx, int64_t N, float* ones_buf, float* x_buf,
+                   char* ws, int* err, float* out, cudaStream_t st) {
+  launch_k(dct_fill_ones_kernel, dim3((unsigned)std::min<int64_t>((N + 255) / 256, 4096)),
+           dim3(256), 0, st, ones_buf, N);
+  dct_adjoint(D, idx, N, ones_buf, N, 1, x_buf, D, 1.0, ws, err, st);
+  launch_k(dct_col_norms_kernel, dim3((unsigned)std::min<int64_t>((D + 255) / 256, 4096)),
+           dim3(256), 0, st, D, N, (const float*)x_buf, out);
+}
+
 // Z = beta Phi^T W: zero-fill the unkept samples, forward DCT
 void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,
                  float* Z, int64_t ldz, double beta, char* ws, int* err, cudaStream_t st) {

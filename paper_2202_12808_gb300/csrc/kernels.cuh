@@ -113,6 +113,10 @@ void dct_forward(int64_t D, const int32_t* idx, int64_t N, const float* Z, int64
                  float* W, int64_t ldw, char* ws, int* err, cudaStream_t st);
 void dct_adjoint(int64_t D, const int32_t* idx, int64_t N, const float* W, int64_t ldw, int ncols,
                  float* Z, int64_t ldz, double beta, char* ws, int* err, cudaStream_t st);
+// ||phi_d||^2, d < D, into out (closed form from one DCT of the mask);
+// scratch: ones_buf (N floats), x_buf (D floats), ws (dct_ws_bytes(D, 1)).
+void dct_col_norms(int64_t D, const int32_t* idx, int64_t N, float* ones_buf, float* x_buf,
+                   char* ws, int* err, float* out, cudaStream_t st);
 
 // ---- operator application ----
 // Every operator application writes, besides its output, per-block partial

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import mlp as omlp
 from oracle import sbl
 from paper_2202_12808_gb300 import api
 from paper_2202_12808_gb300 import binding as B
@@ -105,4 +106,107 @@ def test_dct_fit_residual_replacement(cuda_lib):
     ra, rmu, rs, rst = sbl.cofem_dct(p.idx, D, y32.astype(np.float64), p.beta, 20, 10, 1e-5, 400,
                                      seed=5, resid_replace_every=10)
     assert rel_l2(r.mu.cpu().numpy(), rmu) <= 1e-4
+    assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)
+
+
+def _dct_col_norms_brute(idx, D, d):
+    """||phi_d||^2 = sum over kept n of C[d, n]^2 from the DCT-II's definition,
+    for the coordinates d (angles reduced exactly in integers)."""
+    n = idx.astype(np.int64)
+    out = np.empty(len(d))
+    for i, dd in enumerate(d):
+        k = (int(dd) * (2 * n + 1)) % (4 * D)
+        s2 = 1.0 / D if dd == 0 else 2.0 / D
+        out[i] = s2 * np.sum(np.cos(np.pi * k / (2.0 * D)) ** 2)
+    return out
+
+
+@pytest.mark.parametrize("D,N", [(16, 4), (64, 64), (4096, 1024), (1 << 18, 1 << 16),
+                                 (1 << 22, 1 << 20)])
+def test_dct_col_norms(cuda_lib, D, N):
+    """The masked DCT's ||phi_d||^2 from one transform of the sample mask
+    against the sum of squares of C's entries, every d up to D = 4096 (from
+    the oracle's DCT matrix) and sampled d beyond, with the special rows d =
+    0, D/2 - 1, D/2, D/2 + 1, D - 1; all samples kept gives 1 exactly."""
+    rng = np.random.default_rng(D + 7 * N)
+    idx = np.sort(rng.choice(D, N, replace=False)).astype(np.int32)
+    it = torch.from_numpy(idx).cuda()
+    op = B.cofem_op_dct(D, N, it.data_ptr())
+    try:
+        n = B.cofem_col_norms_workspace_bytes(op)
+        assert n > 0
+        ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+        out = torch.full((D,), -1.0, dtype=torch.float32, device="cuda")
+        with pytest.raises(B.CofemError):
+            B.cofem_op_col_norms(op, out.data_ptr())
+        with pytest.raises(B.CofemError):
+            B.cofem_op_col_norms_ws(op, out.data_ptr(), ws.data_ptr(), n - 256)
+        B.cofem_op_col_norms_ws(op, out.data_ptr(), ws.data_ptr(), n)
+        got = out.cpu().numpy().astype(np.float64)
+    finally:
+        B.cofem_op_destroy(op)
+    if D <= 4096:
+        d = np.arange(D)
+        ref = np.sum(sbl.dct_matrix(D)[:, idx] ** 2, axis=1)
+        # the sampled brute force used beyond D = 4096 agrees with the matrix
+        assert np.max(np.abs(_dct_col_norms_brute(idx, D, d) - ref)) <= 1e-12
+    else:
+        special = [0, 1, D // 2 - 1, D // 2, D // 2 + 1, D - 1]
+        d = np.unique(np.concatenate([special, rng.choice(D, 200, replace=False)]))
+        ref = _dct_col_norms_brute(idx, D, d)
+    if N == D:
+        assert np.max(np.abs(ref - 1.0)) <= 1e-12
+    rel = np.abs(got[d] - ref) / ref
+    assert np.max(rel) <= 2e-6, (np.max(rel), d[np.argmax(rel)])
+
+
+def test_col_norms_ws_on_a_dense_dictionary(cuda_lib):
+    # no workspace for a dense dictionary: the same values as cofem_op_col_norms
+    rng = np.random.default_rng(3)
+    Phi = torch.from_numpy((rng.standard_normal((64, 200)) / 8).astype(np.float32)).cuda()
+    op = api.DenseOperator(Phi)
+    assert B.cofem_col_norms_workspace_bytes(op.handle) == 0
+    a = torch.empty(200, dtype=torch.float32, device="cuda")
+    b = torch.empty(200, dtype=torch.float32, device="cuda")
+    B.cofem_op_col_norms(op.handle, a.data_ptr())
+    B.cofem_op_col_norms_ws(op.handle, b.data_ptr(), None, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    ref = np.sum(Phi.double().cpu().numpy() ** 2, axis=0)
+    assert np.max(np.abs(b.cpu().numpy() - ref) / ref) <= 1e-6
+
+
+def test_dct_fit_jacobi_start(cuda_lib):
+    """The learned start on the masked DCT with an all-zero network, i.e.
+    mu_hat = 0 and s_hat = 1 / c_d, c_d = beta ||phi_d||^2 + alpha_d (a
+    Jacobi-preconditioned solve from the diagonal guess), against the
+    oracle's learned loop with the same predictor on exact column norms.
+    The bars are the plain DCT fit's: mu 1e-4, alpha 3e-3 on the support,
+    the same support, iteration totals within 5 %."""
+    D, N = 4096, 1024
+    p = datagen.dct_problem(D, N, int(0.04 * D), 0.01, seed=2)
+    op = api.DctOperator(torch.from_numpy(p.idx).cuda(), D)
+    y32 = p.y.astype(np.float32)
+    zero_net = torch.zeros(omlp.N_PARAMS, dtype=torch.bfloat16, device="cuda")
+    prm = api.params(vec_dtype=B.COFEM_F32, K=20, em_iters=20, cg_tol=1e-5, cg_max_iters=400,
+                     seed=2)
+    prm.mlp = zero_net.data_ptr()
+    r = api.fit(op, torch.from_numpy(y32).cuda(), p.beta, prm)
+    torch.cuda.synchronize()
+    assert B.cofem_last_fit_fallbacks() == 0
+    pn2 = np.sum(sbl.dct_matrix(D)[:, p.idx] ** 2, axis=1).astype(np.float32).astype(np.float64)
+
+    def predict(alpha, mu_prev, s_prev):
+        return omlp.predict(np.zeros((D, 2)), alpha, pn2, p.beta)
+
+    phi, phit, _ = sbl.dct_dictionary(p.idx, D)
+    ra, rmu, rs, rst = sbl.cofem_learned(phi, phit, D, y32.astype(np.float64), p.beta, 20, 20,
+                                         1e-5, 400, predict, seed=2)
+    assert sum(rst.fallbacks) == 0
+    a, mu = r.alpha.cpu().numpy(), r.mu.cpu().numpy()
+    assert rel_l2(mu, rmu) <= 1e-4, rel_l2(mu, rmu)
+    eq, border = support_compare(a, ra)
+    assert eq, border
+    sup = (a < 1e6) & (ra < 1e6)
+    assert np.max(np.abs(a[sup] - ra[sup]) / ra[sup]) <= 3e-3
     assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)

@@ -193,6 +193,17 @@ cofem_status cofem_op_dense_set_l2_resident(cofem_op* op, int64_t bytes);
 cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T,
                              const float* filters_dev, cofem_op** out);
 
+/* on = 1: apply the convolutional Phi on the tensor cores with its filters
+ * rounded to BF16 (the dictionary becomes the BF16 rounding of h, as a BF16
+ * dense dictionary is; every entry point that uses Phi -- the operator, its
+ * two products, the fits, the column norms -- then uses the rounded taps).
+ * The products run as block Toeplitz GEMMs (tcgen05): blocks of 64 outputs,
+ * the FP32 vectors as three BF16 terms (exact FP32 products), FP32
+ * accumulation.  on = 0: FP32 filters on the CUDA cores (the default).
+ * COFEM_ERR_INVALID_ARG for other operators.  Workspace sizes depend on it:
+ * query them after choosing. */
+cofem_status cofem_op_conv1d_set_tensor_cores(cofem_op* op, int32_t on);
+
 /* Masked-DCT Phi (the structured dictionary of Sec. 4.2): Phi = M C^T, with C
  * the orthonormal DCT-II matrix of size D (C[k][n] = s_k cos(pi k (2n+1) /
  * 2D), s_0 = sqrt(1/D), s_k = sqrt(2/D)) and M the selection of the N

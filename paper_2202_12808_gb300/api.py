@@ -84,7 +84,7 @@ class Fp8DenseOperator:
 class ConvOperator:
     """Circular convolutional Phi: C filters of T taps over length-L signals."""
 
-    def __init__(self, h: torch.Tensor, L: int):
+    def __init__(self, h: torch.Tensor, L: int, tensor_cores: bool = False):
         if not h.is_cuda or h.dtype != torch.float32:
             raise ValueError("filters must be a float32 CUDA tensor")
         self.h = h.contiguous()
@@ -93,6 +93,10 @@ class ConvOperator:
         self.N, self.D = L, self.C * L
         self.dtype = B.COFEM_F32
         self.handle = B.cofem_op_conv1d(L, self.C, self.T, self.h.data_ptr())
+        # tensor cores: the filters are rounded to BF16 for every use of Phi
+        self.tensor_cores = bool(tensor_cores)
+        if self.tensor_cores:
+            B.cofem_op_conv1d_set_tensor_cores(self.handle, 1)
 
     def __del__(self):
         h = getattr(self, "handle", None)

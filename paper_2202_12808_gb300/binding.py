@@ -80,6 +80,7 @@ _SIGS = {
                                      ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_float)]),
     "cofem_op_dense_attach_packed": (_S, [_P, _P, _SZ, _P]),
     "cofem_op_conv1d": (_S, [_I64, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "cofem_op_conv1d_set_tensor_cores": (_S, [_P, _I32]),
     "cofem_op_dct": (_S, [_I64, _I64, _P, ctypes.POINTER(_P)]),
     "cofem_op_destroy": (None, [_P]),
     "cofem_last_fit_fallbacks": (_I32, []),
@@ -225,6 +226,10 @@ def cofem_op_conv1d(L, C, T, filters_ptr):
     h = _P()
     _check(lib().cofem_op_conv1d(L, C, T, filters_ptr, ctypes.byref(h)), "cofem_op_conv1d")
     return h
+
+
+def cofem_op_conv1d_set_tensor_cores(op, on):
+    _check(lib().cofem_op_conv1d_set_tensor_cores(op, on), "cofem_op_conv1d_set_tensor_cores")
 
 
 def cofem_op_dct(D, N, idx_ptr):

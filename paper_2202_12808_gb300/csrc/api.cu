@@ -23,6 +23,7 @@ struct cofem_op {
   int64_t L;
   int C, T;
   const float* filters;
+  int conv_tc = 0;                // convolution on the tensor cores (BF16-rounded filters)
   int64_t dct_D, dct_N;           // masked DCT: D coefficients, N kept samples
   const int32_t* dct_idx;         // their indices (strictly increasing, caller's memory)
 };
@@ -108,16 +109,37 @@ static bool op_supports(const cofem_op* op, int vec) {
   return vec == COFEM_F32;     // convolution, masked DCT: FP32 vectors
 }
 
-// Convolution scratch: W (ncols x L floats), then the filters padded to 64 taps.
-static size_t conv_w_bytes(const cofem_op* op, int ncols) {
-  return align256((size_t)ncols * op->L * sizeof(float));
+// Convolution scratch: the filters padded to 64 taps (rounded to BF16 on the
+// tensor cores), on the tensor cores the Toeplitz images (1024-aligned),
+// then W (ncols x L floats).  The prefix does not depend on ncols, so tables
+// prepared once (a fit) serve every application.
+static size_t conv_prefix_bytes(const cofem_op* op) {
+  size_t b = align256((size_t)op->C * 64 * sizeof(float));
+  if (op->conv_tc) b = ((b + 1023) & ~(size_t)1023) + conv_tc_image_bytes(op->C);
+  return b;
 }
-static const float* conv_filters64(const cofem_op* op, char* ws, int ncols, cudaStream_t st) {
-  // the kernels read the taps as float4: use the caller's filters in place
-  // only when they are 64 taps long and 16-byte aligned
-  if (op->T == 64 && ((uintptr_t)op->filters & 15) == 0) return op->filters;
-  float* h64 = (float*)(ws + conv_w_bytes(op, ncols));
-  conv_pad_filters(op->filters, op->C, op->T, h64, st);
+static __nv_bfloat16* conv_images(const cofem_op* op, char* ws) {
+  return (__nv_bfloat16*)(ws + ((align256((size_t)op->C * 64 * sizeof(float)) + 1023) &
+                                ~(size_t)1023));
+}
+static size_t conv_w_bytes(const cofem_op* op, int ncols) {
+  return conv_prefix_bytes(op) + align256((size_t)ncols * op->L * sizeof(float));
+}
+static float* conv_w_scratch(const cofem_op* op, char* ws) {
+  return (float*)(ws + conv_prefix_bytes(op));
+}
+// The filters the kernels read (taps as float4): the caller's in place when
+// they are 64 taps long and 16-byte aligned and not rounded; otherwise the
+// workspace copy, written here unless `prepared` (with the Toeplitz images
+// on the tensor cores).
+static const float* conv_filters64(const cofem_op* op, char* ws, cudaStream_t st,
+                                   bool prepared = false) {
+  if (!op->conv_tc && op->T == 64 && ((uintptr_t)op->filters & 15) == 0) return op->filters;
+  float* h64 = (float*)ws;
+  if (!prepared) {
+    if (op->conv_tc) conv_tc_prepare(op->filters, op->C, op->T, h64, conv_images(op, ws), st);
+    else conv_pad_filters(op->filters, op->C, op->T, h64, st);
+  }
   return h64;
 }
 
@@ -150,7 +172,7 @@ static size_t op_ws_bytes(const cofem_op* op, int vec, int ncols, bool max_shape
     return b;
   }
   if (op->kind == 2) return dct_ws_bytes(op->dct_D, ncols);
-  return conv_w_bytes(op, ncols) + align256((size_t)op->C * 64 * sizeof(float));
+  return conv_w_bytes(op, ncols);
 }
 
 // Y = beta Phi^T Phi X + alpha . X  (alpha may be null: no diagonal term)
@@ -202,8 +224,18 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
     CKL();
     return COFEM_OK;
   }
-  const float* h64 = conv_filters64(op, ws, ncols, st);
-  float* W = (float*)ws;
+  const float* h64 = conv_filters64(op, ws, st, (flags & kApplyOpPrepared) != 0);
+  float* W = conv_w_scratch(op, ws);
+  if (op->conv_tc) {
+    const __nv_bfloat16* img = conv_images(op, ws);
+    conv_tc_forward(op->C, op->L, (const float*)x, ld, ncols, W, op->L, img, err, st);
+    const int np = conv_tc_adjoint(op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
+                                   vec == COFEM_F32 ? alpha32 : nullptr, (const float*)x, dots,
+                                   img, err, st);
+    if (nparts) *nparts = dots ? np : 0;
+    CKL();
+    return COFEM_OK;
+  }
   conv_forward(h64, op->C, op->L, (const float*)x, ld, ncols, W, op->L, st);
   const int np = conv_adjoint(h64, op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
                               (const float*)x, dots, st, vec == COFEM_F32 ? alpha32 : nullptr);
@@ -237,7 +269,7 @@ static cofem_status op_forward(const cofem_op* op, int vec, const void* z, int64
     CKL();
     return COFEM_OK;
   }
-  const float* h64 = conv_filters64(op, ws, ncols, st);
+  const float* h64 = conv_filters64(op, ws, st);
   conv_forward(h64, op->C, op->L, (const float*)z, ldz, ncols, (float*)w, ldw, st);
   CKL();
   return COFEM_OK;
@@ -272,7 +304,7 @@ static cofem_status op_adjoint(const cofem_op* op, int vec, const void* w, int64
     CKL();
     return COFEM_OK;
   }
-  const float* h64 = conv_filters64(op, ws, ncols, st);
+  const float* h64 = conv_filters64(op, ws, st);
   conv_adjoint(h64, op->C, op->L, (const float*)w, ldw, ncols, (float*)z, ldz, beta, nullptr,
                nullptr, nullptr, st);
   CKL();
@@ -401,7 +433,7 @@ static cofem_status build_em_graph(const cofem_op* op, const cofem_params* p, do
                                    char* ws, const FitLayout& L, double* mu, double* s,
                                    double* alpha, cudaGraphExec_t* exec) {
   // structured operators: their tables were built once for the fit
-  const unsigned prep = op->kind == 2 ? kApplyOpPrepared : 0u;
+  const unsigned prep = (op->kind == 2 || (op->kind == 1 && op->conv_tc)) ? kApplyOpPrepared : 0u;
   Streams ss;
   for (auto& x : ss.s) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
   CgCtl* ctl = (CgCtl*)(ws + L.ctl);
@@ -953,6 +985,12 @@ cofem_status cofem_op_conv1d(int64_t L, int32_t C, int32_t T, const float* filte
   return COFEM_OK;
 }
 
+cofem_status cofem_op_conv1d_set_tensor_cores(cofem_op* op, int32_t on) {
+  if (!op || op->kind != 1 || (on != 0 && on != 1)) return COFEM_ERR_INVALID_ARG;
+  op->conv_tc = on;
+  return COFEM_OK;
+}
+
 cofem_status cofem_op_dct(int64_t D, int64_t N, const int32_t* idx_dev, cofem_op** out) {
   if (!out || !idx_dev || !dct_size_ok(D) || N < 1 || N > D || ((uintptr_t)idx_dev & 3))
     return COFEM_ERR_INVALID_ARG;
@@ -1191,12 +1229,13 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 
 int op_is_dense(const cofem_op* op) { return op->kind == 0; }
 DenseDesc op_dense_desc(const cofem_op* op) { return op->dense; }
-int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h) {
+int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h, int* bf16) {
   if (op->kind != 1) return -1;
   *L = op->L;
   *C = op->C;
   *T = op->T;
   *h = op->filters;
+  *bf16 = op->conv_tc;
   return 0;
 }
 

@@ -98,6 +98,18 @@ int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw
                  float* Y, int64_t ld, double beta, const double* alpha, const float* X,
                  double* dots, cudaStream_t st, const float* alpha32 = nullptr);
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st);
+// ---- convolution on the tensor cores (conv_tc.cu): BF16 filters ----
+// h64 = the BF16-rounded filters padded to 64 taps; img = the forward and
+// adjoint Toeplitz tiles (conv_tc_image_bytes(C) bytes, 1024-byte aligned)
+size_t conv_tc_image_bytes(int C);
+void conv_tc_prepare(const float* h, int C, int T, float* h64, __nv_bfloat16* img,
+                     cudaStream_t st);
+void conv_tc_forward(int C, int64_t L, const float* Z, int64_t ldz, int ncols, float* W,
+                     int64_t ldw, const __nv_bfloat16* img, int* err, cudaStream_t st);
+int conv_tc_adjoint(int C, int64_t L, const float* W, int64_t ldw, int ncols, float* Y,
+                    int64_t ld, double beta, const double* alpha, const float* alpha32,
+                    const float* X, double* dots, const __nv_bfloat16* img, int* err,
+                    cudaStream_t st);
 
 // ---- masked DCT dictionary (dct.cu); idx: N strictly increasing sample indices ----
 bool dct_size_ok(int64_t D);                      // D a power of two, 16 <= D <= 2^22

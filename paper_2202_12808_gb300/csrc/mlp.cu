@@ -385,16 +385,23 @@ struct cofem_op;   // opaque here; the dense fields are reached through accessor
 namespace cofem {
 int op_is_dense(const cofem_op* op);
 DenseDesc op_dense_desc(const cofem_op* op);
-int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h);
+int op_conv_desc(const cofem_op* op, int64_t* L, int* C, int* T, const float** h, int* bf16);
 
-__global__ void conv_col_norms_kernel(const float* h, int C, int T, int64_t L, float* out) {
+// ||phi_d||^2 = sum_t h[c][t]^2 for d = c L + m (taps rounded to BF16 when
+// the operator runs on the tensor cores)
+__global__ void conv_col_norms_kernel(const float* h, int C, int T, int64_t L, int bf16,
+                                      float* out) {
   pdl_wait();
   pdl_trigger();
   for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < (int64_t)C * L;
        d += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(d / L);
     double acc = 0.0;
-    for (int t = 0; t < T; ++t) acc += (double)h[c * T + t] * (double)h[c * T + t];
+    for (int t = 0; t < T; ++t) {
+      float v = h[c * T + t];
+      if (bf16) v = __bfloat162float(__float2bfloat16_rn(v));
+      acc += (double)v * (double)v;
+    }
     out[d] = (float)acc;
   }
 }
@@ -429,11 +436,11 @@ cofem_status mlp_col_norms(const cofem_op* op, float* out, cudaStream_t st) {
                (const __nv_bfloat16*)d.phi, d.N, d.D, d.ld, out);
   } else {
     int64_t L;
-    int C, T;
+    int C, T, bf16;
     const float* h;
-    if (op_conv_desc(op, &L, &C, &T, &h) != 0) return COFEM_ERR_UNSUPPORTED;
+    if (op_conv_desc(op, &L, &C, &T, &h, &bf16) != 0) return COFEM_ERR_UNSUPPORTED;
     launch_k(conv_col_norms_kernel, dim3(blocks_for((int64_t)C * L, 256)), dim3(256), 0, st, h, C,
-             T, L, out);
+             T, L, bf16, out);
   }
   return cudaGetLastError() == cudaSuccess ? COFEM_OK : COFEM_ERR_CUDA;
 }

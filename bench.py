@@ -306,6 +306,28 @@ def time_to_tolerance(hist, end_ns, ref, tols=(1e-2, 1e-3)):
     return out
 
 
+def measured_peaks():
+    """The measured peaks (HBM copy GB/s, BF16 TFLOP/s), or {}."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+def profile_traffic(summary, source):
+    """DRAM bytes per launch from a committed ncu summary under profiles/,
+    only while its source_sha1 matches the kernel's source file (else None)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(prof):
+        return None
+    src = os.path.join(ROOT, "paper_2202_12808_gb300", "csrc", source)
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    meta = dict(l.split(":", 1) for l in open(prof)
+                if l.startswith(("source_sha1:", "traffic_bytes_per_launch:")))
+    if meta.get("source_sha1", "").strip() == sha and "traffic_bytes_per_launch" in meta:
+        return int(meta["traffic_bytes_per_launch"].strip())
+    return None
+
+
 def whole_fit(api, B, op, y, beta, kw, em, dev, z=None):
     """One timed fit of `em` EM iterations (one call, CUDA events on the
     stream), then the same fit EM iteration by EM iteration (resumed, not
@@ -454,61 +476,64 @@ def _fit_batched_resume(api, B, phis, ys, betas, seeds, p, alpha0):
 
 
 def run_conv(args):
-    """Convolutional dictionary, L = 2^20, 8 filters x 64 taps."""
+    """Convolutional dictionary, L = 2^20, 8 filters x 64 taps: the fit with
+    the products on the tensor cores (BF16-rounded filters, the block
+    Toeplitz GEMMs) and, beside it, the FP32 filters on the CUDA cores."""
     import torch
     from paper_2202_12808_gb300 import api
     from paper_2202_12808_gb300 import binding as B
     c = datagen.CONFIGS["conv-l1m-c8-t64"]
     pr = datagen.conv_problem(c["L"], c["C"], c["T"], c["density"], c["sigma"], args.seed)
-    op = api.ConvOperator(torch.from_numpy(pr.h).cuda(), c["L"])
     y = torch.from_numpy(pr.y.astype(np.float32)).cuda()
     kw = dict(vec_dtype=B.COFEM_F32, K=c["K"], cg_tol=c["cg_tol"], cg_max_iters=c["cg_max_iters"],
               seed=args.seed)
-    rw = api.fit(op, y, pr.beta, api.params(em_iters=args.warmup, **kw))
-    a0 = rw.alpha.clone()
-    pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
-    with ClockSampler(0) as clk:
-        res, sec = _timed(lambda: api.fit(op, y, pr.beta, pt, alpha=a0.clone()))
-    cg = res.stats["cg_iters"]
-    D, L, nc = op.D, c["L"], c["K"] + 1
-    X = torch.randn((nc, D), device="cuda")
-    Y = torch.empty_like(X)
-    nb = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, nc)
-    wsa = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    ms = [B.cofem_op_apply_timed(op.handle, B.COFEM_F32, X.data_ptr(), D, nc, a0.data_ptr(),
-                                 pr.beta, Y.data_ptr(), wsa.data_ptr(), nb) for _ in range(5)][1:]
-    fwd = float(np.mean([m[0] for m in ms])) / 1e3
-    adj = float(np.mean([m[1] for m in ms])) / 1e3
-    adj_bytes = L * nc * 4 + 2 * D * nc * 4 + 8 * D
-    flops = 2 * 2 * c["T"] * D * nc                    # forward + adjoint MACs x 2
-    adj_flops = flops / 2
+    D, L, nc = c["C"] * c["L"], c["L"], c["K"] + 1
+    out = {}
+    for arm, tcores in (("fp32_cuda_cores", False), ("bf16_tensor_cores", True)):
+        op = api.ConvOperator(torch.from_numpy(pr.h).cuda(), c["L"], tensor_cores=tcores)
+        rw = api.fit(op, y, pr.beta, api.params(em_iters=args.warmup, **kw))
+        a0 = rw.alpha.clone()
+        pt = api.params(em_iters=args.steps, t_offset=args.warmup, **kw)
+        with ClockSampler(0) as clk:
+            res, sec = _timed(lambda: api.fit(op, y, pr.beta, pt, alpha=a0.clone()))
+        X = torch.randn((nc, D), device="cuda")
+        Y = torch.empty_like(X)
+        nb = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, nc)
+        wsa = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        ms = [B.cofem_op_apply_timed(op.handle, B.COFEM_F32, X.data_ptr(), D, nc, a0.data_ptr(),
+                                     pr.beta, Y.data_ptr(), wsa.data_ptr(), nb)
+              for _ in range(5)][1:]
+        out[arm] = {"seconds": sec, "em_iters_per_s": args.steps / sec,
+                    "cg_iters_per_em": res.stats["cg_iters"],
+                    "forward_us": float(np.mean([m[-2] for m in ms])) * 1e3,
+                    "adjoint_us": float(np.mean([m[-1] for m in ms])) * 1e3,
+                    "clocks": clk.summary()}
+    fwd_bytes = (D + L) * nc * 4                       # Z read, W written
+    adj_bytes = L * nc * 4 + 2 * D * nc * 4 + 4 * D    # W, X read, Y written, alpha (FP32)
+    flops = 2 * c["T"] * D * nc                         # MACs x 2 of one product
+    tcarm, fparm = out["bf16_tensor_cores"], out["fp32_cuda_cores"]
+    for arm in out.values():
+        arm["forward_gbs"] = fwd_bytes / (arm["forward_us"] * 1e-6) / 1e9
+        arm["adjoint_gbs"] = adj_bytes / (arm["adjoint_us"] * 1e-6) / 1e9
     # FP32 CUDA-core roof: SMs x 128 FP32 lanes x 2 flop x maximum SM clock
     props = torch.cuda.get_device_properties(0)
     fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "conv_adjoint_l1m_c8_t64.md")
-    if os.path.exists(prof):
-        import hashlib
-        src = os.path.join(ROOT, "paper_2202_12808_gb300", "csrc", "conv.cu")
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        meta = dict(l.split(":", 1) for l in open(prof)
-                    if l.startswith(("source_sha1:", "traffic_bytes_per_launch:")))
-        if meta.get("source_sha1", "").strip() == sha:
-            traffic = int(meta["traffic_bytes_per_launch"].strip())
+    fparm["adjoint_frac_of_fp32_alu"] = flops / (fparm["adjoint_us"] * 1e-6) / 1e12 / fp32_peak
+    hbm = measured_peaks().get("hbm_gbs")
+    traffic = profile_traffic("conv_tc_adjoint_l1m_c8_t64.md", "conv_tc.cu")
     _common(args, "EM iters/s (circular conv dictionary L=2^20, 8x64 taps, D=8.4M, K=16)",
-            "EM iters/s", args.steps / sec, sec, "f32",
+            "EM iters/s", args.steps / tcarm["seconds"], tcarm["seconds"], "f32 vectors, bf16 filters",
             {"workload": "conv-l1m-c8-t64", "L": L, "C": c["C"], "T": c["T"], "D": D,
              "K": c["K"], "em_steps_timed": "t=%d..%d" % (args.warmup + 1, args.warmup + args.steps)},
-            {"cg_iters_per_em": cg,
-             "roofline": {"bound": "alu", "achieved": adj_flops / adj / 1e12, "peak": fp32_peak,
-                          "unit": "TFLOP/s", "frac": adj_flops / adj / 1e12 / fp32_peak,
-                          "traffic": traffic, "peak_source": "derived (SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
-                          "kernel": "conv_adjoint_kernel (Phi^T W + alpha.X, 17 cols)",
-                          "launch_us": adj * 1e6, "algorithmic_flops": adj_flops,
-                          "algorithmic_bytes": adj_bytes},
-             "conv_apply": {"forward_us": fwd * 1e6, "adjoint_us": adj * 1e6,
-                            "fp32_tflops": flops / (fwd + adj) / 1e12},
-             "clocks": clk.summary()})
+            {"cg_iters_per_em": tcarm["cg_iters_per_em"],
+             "roofline": {"bound": "hbm", "achieved": tcarm["adjoint_gbs"], "peak": hbm,
+                          "unit": "GB/s", "frac": tcarm["adjoint_gbs"] / hbm if hbm else None,
+                          "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                          "kernel": "conv_tc_adjoint_kernel (beta Phi^T W + alpha.X, 17 cols)",
+                          "launch_us": tcarm["adjoint_us"], "algorithmic_bytes": adj_bytes},
+             "arms": out,
+             "ratio_em_iters_per_s_tensor_vs_cuda_cores": fparm["seconds"] / tcarm["seconds"],
+             "clocks": tcarm["clocks"]})
 
 
 def run_dct(args):

@@ -595,6 +595,10 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&sempty[sl]);
         float* yb = g.y + (int64_t)j * g.ldy + (int64_t)c * L + p0;
+        // x_j^T y_j: compensated FP32 (product error by FMA, TwoSum); a
+        // product of 1e30 or more is left out here and added in FP64 below,
+        // behind a warp-uniform branch (FP64 runs at 1/64 of FP32 here)
+        bool anybig = false;
 #pragma unroll
         for (int bb = 0; bb < 16; ++bb) {
           if (bb < nv) {
@@ -602,11 +606,25 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
             float o;
             if (diag) {
               o = fmaf(ar[bb], xr[bb], beta * acc);
-              dot.add_prod(xr[bb], o);
+              const float pp = xr[bb] * o;
+              const bool fin = fabsf(pp) < 1e30f;
+              anybig |= !fin;
+              dot.c += fin ? fmaf(xr[bb], o, -pp) : 0.f;
+              const float x = fin ? pp : 0.f;
+              const float t = dot.s + x, xv = t - dot.s;
+              dot.c += (dot.s - (t - xv)) + (x - xv);
+              dot.s = t;
             } else {
               o = beta * acc;
             }
             yb[kCtM * bb] = o;
+          }
+        }
+        if (__any_sync(0xffffffffu, anybig)) {
+#pragma unroll
+          for (int bb = 0; bb < 16; ++bb) {
+            const float o = fmaf(ar[bb], xr[bb], beta * (tt[bb] + ts[bb]));
+            if (bb < nv && !(fabsf(xr[bb] * o) < 1e30f)) dot.big += (double)xr[bb] * (double)o;
           }
         }
       }

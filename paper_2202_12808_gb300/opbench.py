@@ -8,6 +8,7 @@ outside any fit graph:
     python -m paper_2202_12808_gb300.opbench --op dense-f32  --N 4096 --D 32768 --ncols 33
     python -m paper_2202_12808_gb300.opbench --op cg --D 1048576 --ncols 33
     python -m paper_2202_12808_gb300.opbench --op bcg --D 32768 --ncols 33
+    python -m paper_2202_12808_gb300.opbench --op conv-tc --L 1048576 --C 8 --T 64 --ncols 17
 
 dense-bf16 / dense-f32 / dense-fp8: A X = beta Phi^T (Phi X) + alpha . X on
 the tensor cores (BF16 dictionary, FP32 dictionary as hi + lo, or FP8 E4M3
@@ -16,7 +17,10 @@ pipeline autotuned unless --no-autotune; prints the per-kernel microseconds
 of cofem_op_apply_timed.  cg: the CG update (direction fused where it fits),
 the direction update and the diagonal estimate + M-step
 (cofem_bench_cg_kernels).  bcg: the three passes of one block-CG iteration
-(cofem_bench_bcg_kernels).
+(cofem_bench_bcg_kernels).  conv-tc / conv-f32: A X of the circular
+convolutional dictionary with the products on the tensor cores (BF16
+filters) or the CUDA cores (FP32 filters); prints the forward and adjoint
+microseconds.
 """
 import argparse
 import json
@@ -30,7 +34,11 @@ from . import binding as B
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "dense-fp8", "cg", "bcg"], required=True)
+    ap.add_argument("--op", choices=["dense-bf16", "dense-f32", "dense-fp8", "cg", "bcg", "conv-tc",
+                                     "conv-f32"], required=True)
+    ap.add_argument("--L", type=int, default=1 << 20)
+    ap.add_argument("--C", type=int, default=8)
+    ap.add_argument("--T", type=int, default=64)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--D", type=int, default=32768)
     ap.add_argument("--ncols", type=int, default=33)
@@ -59,6 +67,22 @@ def main():
         return
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
+    if a.op in ("conv-tc", "conv-f32"):
+        h = torch.randn((a.C, a.T), generator=g, device="cuda") / float(np.sqrt(a.T))
+        op = api.ConvOperator(h, a.L, tensor_cores=a.op == "conv-tc")
+        D = a.C * a.L
+        X = torch.randn((a.ncols, D), generator=g, device="cuda")
+        Y = torch.empty_like(X)
+        alpha = torch.rand(D, generator=g, device="cuda", dtype=torch.float64) + 1.0
+        nb = B.cofem_apply_workspace_bytes(op.handle, B.COFEM_F32, a.ncols)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        runs = [B.cofem_op_apply_timed(op.handle, B.COFEM_F32, X.data_ptr(), D, a.ncols,
+                                       alpha.data_ptr(), 400.0, Y.data_ptr(), ws.data_ptr(), nb)
+                for _ in range(a.reps + 1)][1:]
+        print(json.dumps({"op": a.op, "L": a.L, "C": a.C, "T": a.T, "ncols": a.ncols,
+                          "forward_us": float(np.mean([r[-2] for r in runs])) * 1e3,
+                          "adjoint_us": float(np.mean([r[-1] for r in runs])) * 1e3}))
+        return
     Phi = torch.randn((a.N, a.D), generator=g, device="cuda") / float(np.sqrt(a.N))
     if a.op == "dense-fp8":
         op = api.Fp8DenseOperator(Phi)             # quantised, packed copy attached

@@ -111,7 +111,8 @@ static bool op_supports(const cofem_op* op, int vec) {
 
 // Convolution scratch: the filters padded to 64 taps (rounded to BF16 on the
 // tensor cores), on the tensor cores the Toeplitz images (1024-aligned),
-// then W (ncols x L floats).  The prefix does not depend on ncols, so tables
+// then W (ncols x L floats), then an FP32 copy of alpha (C L floats) for
+// applications given none.  The prefix does not depend on ncols, so tables
 // prepared once (a fit) serve every application.
 static size_t conv_prefix_bytes(const cofem_op* op) {
   size_t b = align256((size_t)op->C * 64 * sizeof(float));
@@ -123,7 +124,11 @@ static __nv_bfloat16* conv_images(const cofem_op* op, char* ws) {
                                 ~(size_t)1023));
 }
 static size_t conv_w_bytes(const cofem_op* op, int ncols) {
-  return conv_prefix_bytes(op) + align256((size_t)ncols * op->L * sizeof(float));
+  return conv_prefix_bytes(op) + align256((size_t)ncols * op->L * sizeof(float)) +
+         align256((size_t)op->C * op->L * sizeof(float));
+}
+static float* conv_alpha32_scratch(const cofem_op* op, char* ws, int ncols) {
+  return (float*)(ws + conv_prefix_bytes(op) + align256((size_t)ncols * op->L * sizeof(float)));
 }
 static float* conv_w_scratch(const cofem_op* op, char* ws) {
   return (float*)(ws + conv_prefix_bytes(op));
@@ -226,19 +231,24 @@ static cofem_status op_apply(const cofem_op* op, int vec, const void* x, int64_t
   }
   const float* h64 = conv_filters64(op, ws, st, (flags & kApplyOpPrepared) != 0);
   float* W = conv_w_scratch(op, ws);
+  const float* a32 = vec == COFEM_F32 ? alpha32 : nullptr;
+  if (!a32 && alpha) {
+    float* t = conv_alpha32_scratch(op, ws, ncols);
+    conv_alpha_f32(alpha, (int64_t)op->C * op->L, t, st);
+    a32 = t;
+  }
   if (op->conv_tc) {
     const __nv_bfloat16* img = conv_images(op, ws);
     conv_tc_forward(op->C, op->L, (const float*)x, ld, ncols, W, op->L, img, err, st);
     const int np = conv_tc_adjoint(op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
-                                   vec == COFEM_F32 ? alpha32 : nullptr, (const float*)x, dots,
-                                   img, err, st);
+                                   a32, (const float*)x, dots, img, err, st);
     if (nparts) *nparts = dots ? np : 0;
     CKL();
     return COFEM_OK;
   }
   conv_forward(h64, op->C, op->L, (const float*)x, ld, ncols, W, op->L, st);
   const int np = conv_adjoint(h64, op->C, op->L, W, op->L, ncols, (float*)y, ld, beta, alpha,
-                              (const float*)x, dots, st, vec == COFEM_F32 ? alpha32 : nullptr);
+                              (const float*)x, dots, st, a32);
   if (nparts) *nparts = dots ? np : 0;
   CKL();
   return COFEM_OK;

@@ -259,6 +259,24 @@ __global__ void pad_filters_kernel(const float* h, int C, int T, float* h64) {
   }
 }
 
+// FP32 copy of alpha for an application without one: each value converted
+// once (the adjoint epilogues then read 4 bytes per coordinate and convert
+// nothing; a conversion per coordinate and column runs on the FP64 pipe)
+__global__ void alpha_f32_kernel(const double* a, int64_t n, float* out) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)a[i];
+}
+
+void conv_alpha_f32(const double* alpha, int64_t n, float* out, cudaStream_t st) {
+  const int64_t b = (n + 255) / 256;
+  launch_k(alpha_f32_kernel, dim3((unsigned)(b < 4096 ? b : 4096)), dim3(256), 0, st, alpha, n,
+           out);
+  apply_tick(st);
+}
+
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st) {
   launch_k(pad_filters_kernel, dim3((C * kConvMaxT + 255) / 256), dim3(256), 0, st, h, C, T, h64);
 }

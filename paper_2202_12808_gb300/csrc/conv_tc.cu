@@ -550,6 +550,7 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
       const int64_t rem = L - p0;
       const int nv = rem <= 0 ? 0 : (rem >= 16 * kCtM ? 16 : (int)((rem + kCtM - 1) / kCtM));
       AccF dot;
+      float sbig = 0.f;
       bool failed = false;
       for (int c = 0; c < g.C; ++c) {
         const int sl = c % kCtSlots;
@@ -596,9 +597,8 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
         if (lane == 0) tc::mbar_arrive(&sempty[sl]);
         float* yb = g.y + (int64_t)j * g.ldy + (int64_t)c * L + p0;
         // x_j^T y_j: compensated FP32 (product error by FMA, TwoSum); a
-        // product of 1e30 or more is left out here and added in FP64 below,
-        // behind a warp-uniform branch (FP64 runs at 1/64 of FP32 here)
-        bool anybig = false;
+        // product of 1e30 or more goes, scaled by 2^-64, to a plain FP32 side
+        // sum instead (no FP64 per element: it runs at 1/64 of FP32 here)
 #pragma unroll
         for (int bb = 0; bb < 16; ++bb) {
           if (bb < nv) {
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
               o = fmaf(ar[bb], xr[bb], beta * acc);
               const float pp = xr[bb] * o;
               const bool fin = fabsf(pp) < 1e30f;
-              anybig |= !fin;
+              sbig += fin ? 0.f : (xr[bb] * 0x1p-64f) * o;
               dot.c += fin ? fmaf(xr[bb], o, -pp) : 0.f;
               const float x = fin ? pp : 0.f;
               const float t = dot.s + x, xv = t - dot.s;
@@ -620,14 +620,8 @@ __global__ void __launch_bounds__(kCtAdjThreads, 1) conv_tc_adjoint_kernel(CtArg
             yb[kCtM * bb] = o;
           }
         }
-        if (__any_sync(0xffffffffu, anybig)) {
-#pragma unroll
-          for (int bb = 0; bb < 16; ++bb) {
-            const float o = fmaf(ar[bb], xr[bb], beta * (tt[bb] + ts[bb]));
-            if (bb < nv && !(fabsf(xr[bb] * o) < 1e30f)) dot.big += (double)xr[bb] * (double)o;
-          }
-        }
       }
+      dot.big = (double)sbig * 0x1p64;
       // the epilogue warps agree once per tile (a failed wait ends them all)
       if (!all_ok(!failed, 2, 32 * kAdjEpiWarps)) break;
       if (g.dots) {
@@ -738,6 +732,7 @@ void conv_tc_prepare(const float* h, int C, int T, float* h64, __nv_bfloat16* im
   const int n = C * 64 + 2 * C * kCtAtoms * kCtM * 8;
   launch_k(conv_tc_prep_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, h, C, T, h64,
            img);
+  apply_tick(st);
 }
 
 static int conv_tc_grid(int units) {

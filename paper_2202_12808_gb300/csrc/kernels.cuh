@@ -98,6 +98,7 @@ int conv_adjoint(const float* h64, int C, int64_t L, const float* W, int64_t ldw
                  float* Y, int64_t ld, double beta, const double* alpha, const float* X,
                  double* dots, cudaStream_t st, const float* alpha32 = nullptr);
 void conv_pad_filters(const float* h, int C, int T, float* h64, cudaStream_t st);
+void conv_alpha_f32(const double* alpha, int64_t n, float* out, cudaStream_t st);
 // ---- convolution on the tensor cores (conv_tc.cu): BF16 filters ----
 // h64 = the BF16-rounded filters padded to 64 taps; img = the forward and
 // adjoint Toeplitz tiles (conv_tc_image_bytes(C) bytes, 1024-byte aligned)

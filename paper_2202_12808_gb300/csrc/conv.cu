@@ -155,7 +155,9 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
   const int base = tid * kConvR;
   const bool live = m0 + base + kConvR <= L;
   AccF dot;
+  float sbig = 0.f;        // products of 1e30 or more, scaled by 2^-64 (FP32, not FP64)
   const bool diag = alpha32 != nullptr || alpha != nullptr;
+  const float beta32 = (float)beta;
   for (int c = 0; c < C; ++c) {
     float acc[kConvR];
 #pragma unroll
@@ -210,18 +212,28 @@ conv_adjoint_kernel(const float* __restrict__ h, int C, int64_t L, const float* 
         if (diag) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            out[e] = fmaf(ar[4 * q + e], xr[4 * q + e], (float)beta * acc[4 * q + e]);
-            dot.add_prod(xr[4 * q + e], out[e]);
+            const float xv = xr[4 * q + e];
+            out[e] = fmaf(ar[4 * q + e], xv, beta32 * acc[4 * q + e]);
+            // compensated FP32 x^T y (product error by FMA, TwoSum)
+            const float pp = xv * out[e];
+            const bool fin = fabsf(pp) < 1e30f;
+            sbig += fin ? 0.f : (xv * 0x1p-64f) * out[e];
+            dot.c += fin ? fmaf(xv, out[e], -pp) : 0.f;
+            const float x = fin ? pp : 0.f;
+            const float t = dot.s + x, tv = t - dot.s;
+            dot.c += (dot.s - (t - tv)) + (x - tv);
+            dot.s = t;
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) out[e] = (float)beta * acc[4 * q + e];
+          for (int e = 0; e < 4; ++e) out[e] = beta32 * acc[4 * q + e];
         }
         reinterpret_cast<float4*>(yj)[q] = make_float4(out[0], out[1], out[2], out[3]);
       }
     }
   }
   if (dots) {
+    dot.big = (double)sbig * 0x1p64;
     const double s = block_sum(dot, red);
     if (tid == 0) dots[(int64_t)blockIdx.y * kMaxCols + j] = s;
   }

@@ -128,6 +128,44 @@ def test_conv_tc_fit(cuda_lib, seed):
     assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.05 * sum(rst.cg_iters)
 
 
+def test_conv_tc_jacobi_start(cuda_lib):
+    """The learned start's all-zero network (mu_hat = 0, s_hat = 1 / c_d,
+    c_d = beta ||phi_d||^2 + alpha_d with the rounded filters' column norms)
+    on the tensor-core convolution against the oracle's learned loop with
+    the same predictor on the materialised dictionary of the rounded
+    filters; the bars of the learned dense fit.  Sigma 0.1 (beta 100), as
+    there: at sigma 0.05 the solves' tolerance alone moves mu by 1e-4 after
+    15 EM iterations (the oracle's own plain and Jacobi fits differ by
+    1.4e-4 there, 1.9e-5 at sigma 0.1, where the GPU fit is 4.0e-5 from the
+    oracle's)."""
+    from oracle import mlp as omlp
+    L, C, T = 1024, 8, 64
+    p = datagen.conv_problem(L, C, T, 1e-3, 0.1, seed=2)
+    op = api.ConvOperator(torch.from_numpy(p.h).cuda(), L, tensor_cores=True)
+    y32 = p.y.astype(np.float32)
+    zero_net = torch.zeros(omlp.N_PARAMS, dtype=torch.bfloat16, device="cuda")
+    prm = api.params(vec_dtype=B.COFEM_F32, K=16, em_iters=15, cg_tol=1e-5, cg_max_iters=400,
+                     seed=2)
+    prm.mlp = zero_net.data_ptr()
+    r = api.fit(op, torch.from_numpy(y32).cuda(), p.beta, prm)
+    torch.cuda.synchronize()
+    fb = B.cofem_last_fit_fallbacks()
+    M = sbl.conv_matrix_vectorised(bf16_round(p.h), L)
+    pn2 = np.sum(M * M, axis=0).astype(np.float32).astype(np.float64)
+
+    def predict(alpha, mu_prev, s_prev):
+        return omlp.predict(np.zeros((len(alpha), 2)), alpha, pn2, p.beta)
+
+    phi, phit, D = sbl.dense_dictionary(M)
+    ra, rmu, rs, rst = sbl.cofem_learned(phi, phit, D, y32.astype(np.float64), p.beta, 16, 15,
+                                         1e-5, 400, predict, seed=2)
+    assert fb == sum(rst.fallbacks)
+    assert rel_l2(r.mu.cpu().numpy(), rmu) <= 1e-4
+    eq, border = support_compare(r.alpha.cpu().numpy(), ra)
+    assert eq, border
+    assert abs(sum(r.stats["cg_iters"]) - sum(rst.cg_iters)) <= 0.1 * sum(rst.cg_iters)
+
+
 def test_conv_tc_apply_many_tiles(cuda_lib):
     # L = 2^16 + 64 (nine tiles per column, the last one block of 64 outputs
     # wide), 8 filters x 64 taps, 17 columns: 153 work units, so the CTAs

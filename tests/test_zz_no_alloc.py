@@ -111,6 +111,20 @@ def test_noalloc_conv_after_dense(cuda_lib):
         B.cofem_op_destroy(op)
 
 
+def test_noalloc_conv_tensor_cores_after_dense(cuda_lib):
+    # the convolution on the tensor cores: its Toeplitz images and the FP32
+    # copy of alpha are written into the same scratch on every call
+    L, C, T, ncols = 8256, 8, 64, 17
+    h = torch.from_numpy(datagen.conv_problem(L, C, T, 0.01, 0.05, seed=7).h).cuda()
+    _dirty_scratch_with_a_dense_call()
+    op = B.cofem_op_conv1d(L, C, T, h.data_ptr())
+    B.cofem_op_conv1d_set_tensor_cores(op, 1)
+    try:
+        _two_calls_match(op, C * L, ncols, 13)
+    finally:
+        B.cofem_op_destroy(op)
+
+
 def test_noalloc_dct_after_dense(cuda_lib):
     D, N, ncols = 8192, 2048, 21
     idx = torch.from_numpy(datagen.dct_problem(D, N, int(0.04 * D), 0.01, seed=4).idx).cuda()

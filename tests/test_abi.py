@@ -111,3 +111,32 @@ def test_invalid_operator_arguments(built):
     h = B.cofem_op_conv1d(128, 3, 5, 256)
     assert B.cofem_op_shape(h) == (128, 384)
     B.cofem_op_destroy(h)
+
+
+def test_conv_tensor_core_switch_and_col_norm_workspace(built):
+    # host-side handle logic only (no device memory is touched): the
+    # tensor-core switch is accepted for a convolutional handle only, with
+    # on in {0, 1}; the column-norm workspace is 0 bytes for a
+    # convolutional dictionary and holds the masked DCT's one-column
+    # transform scratch plus two D-float buffers
+    h = B.cofem_op_conv1d(128, 3, 5, 256)
+    try:
+        B.cofem_op_conv1d_set_tensor_cores(h, 1)
+        B.cofem_op_conv1d_set_tensor_cores(h, 0)
+        with pytest.raises(B.CofemError) as e:
+            B.cofem_op_conv1d_set_tensor_cores(h, 2)
+        assert e.value.code == 1
+        assert B.cofem_col_norms_workspace_bytes(h) == 0
+    finally:
+        B.cofem_op_destroy(h)
+    d = B.cofem_op_dct(4096, 1024, 256)
+    try:
+        with pytest.raises(B.CofemError):
+            B.cofem_op_conv1d_set_tensor_cores(d, 1)
+        n = B.cofem_col_norms_workspace_bytes(d)
+        assert n >= B.cofem_apply_workspace_bytes(d, B.COFEM_F32, 1) + 2 * 4096 * 4
+        with pytest.raises(B.CofemError) as e:
+            B.cofem_op_col_norms_ws(d, 256, 512, n - 256)   # workspace too small
+        assert B.STATUS[e.value.code] == "COFEM_ERR_WORKSPACE"
+    finally:
+        B.cofem_op_destroy(d)

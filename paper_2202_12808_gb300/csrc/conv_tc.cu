@@ -22,23 +22,25 @@
 // N (row 64 t + b of a 192-row B operand), so one MMA per K step reads the
 // filter tile once for all three (shared-memory operand traffic, not the
 // tensor pipe, bounds a 128 x 64 MMA) and the epilogue adds columns b,
-// 64 + b and 128 + b.  All windows of a tile
-// lie in one run of 8256 samples (the tile plus 64 on the left for the
-// forward product, on the right for the adjoint): a bulk copy stages that
-// run raw (FP32) in shared memory and eight producer warps split it into
+// 64 + b and 128 + b.  All windows of a tile lie in one run of 8256 samples
+// (the tile plus 64 on the left for the forward product, on the right for
+// the adjoint): a bulk copy stages that run raw (FP32) in shared memory and
+// producer warps (eight in the forward, four in the adjoint) split it into
 // the B tiles.  One thread issues the MMAs into 128 x 192 FP32 accumulators
 // in tensor memory, lane = output i of a block, column = (term, block)
 // (forward: one per tile, double-buffered; adjoint: one per channel, two
 // slots), so the epilogue warps' loads and stores of 32 consecutive outputs
-// are single 128-byte lines.  The adjoint's epilogue applies beta, adds alpha . x and
-// accumulates the x_j^T y_j partial of the tile.
+// are single 128-byte lines.  The adjoint's epilogue applies beta, adds
+// alpha . x and accumulates the x_j^T y_j partial of the tile.
 //
 // Compared with the direct form (2 T C L flops per column), the block
 // Toeplitz form does 192 / T times the multiply-adds (3x at T = 64) on three
-// data terms, on units more than 20x faster than the FP32 CUDA cores, so
-// the products are bound by HBM and the tensor pipe together: the forward
-// reads C L floats per column and writes L, the adjoint reads L + 2 C L (w,
-// x, alpha) and writes C L.
+// data terms, on units more than 20x faster than the FP32 CUDA cores, so the
+// tensor pipe is not what bounds them: the forward (C L floats read and L
+// written per column) is bound by shared-memory traffic, the producers'
+// rewrite of the windows into term tiles and the MMA's operand reads; the
+// adjoint (L + 2 C L read: w, x, alpha; C L written) by its epilogue's loads
+// of x and alpha.
 //
 // Every wait is bounded: a timeout sets COFEM_ERR_TIMEOUT in the error word
 // and the CTA drains its copies, frees its tensor memory and exits.
